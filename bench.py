@@ -1,0 +1,343 @@
+"""Benchmark: interface Monte Carlo mesh steps of the moving-front workload on GB300.
+
+Workload (one "step" = one mesh step of the method, Sec. 4): w = 1 + 10
+exp(-(x - 0.3 - 0.4 t)^2 / 0.05^2) on a 257 x 257 FP32 grid sampled at
+t_{n-1}, 2 x 2 subdomains, the 509 interface nodes with 1e4 paths each,
+dt = 1e-4, Delta t = 1e-2 (100 sub-steps), the paper's boundary test; then
+the FP64 implicit subdomain solves. The default run times the workload's 50
+mesh steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Metric: Euler--Maruyama path-steps per second
+over whole mesh steps (interface nodes per second alongside). Each rank runs
+its own instance (its own seed); the ranks share no data.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "path-steps/s (interface Monte Carlo, whole mesh steps)"
+UNIT = "path-steps/s"
+WL = W.FRONT257
+# Algorithmic lane operations per path-step of the path kernel (see the design doc,
+# "Roofline"): half a Philox4x32-10 block (20), one Box-Muller pair (12), cell
+# location (12), bilinear drift (6), Euler-Maruyama update (4), exit test (4).
+ALG_OPS_PER_PATH_STEP = 58
+SM_LANES_PER_CLK = 128       # 4 schedulers x 32 lanes issue per SM per clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=WL.steps)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--paths", type=int, default=WL.paths)
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce(vals, op, world):
+    if world == 1:
+        return vals
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(vals, dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return t.tolist()
+
+
+# ------------------------------------------------------------------ oracle leg
+
+def oracle_sample(target_s: float, nodes_per_call: int | None, step_cap: int):
+    """Time the FP64 oracle on samples of the workload's interface estimate."""
+    import oracle
+    n = WL.n
+    xi0, eta0 = W.identity_fields(n)
+    xs, ys = W.interface_node_coords(n, n, WL.sub, WL.sub)
+    ids = np.arange(xs.size, dtype=np.uint32)
+    if nodes_per_call:
+        pick = np.linspace(0, xs.size - 1, nodes_per_call).round().astype(np.int64)
+    else:
+        pick = np.arange(xs.size)
+    total_steps = 0
+    t0 = time.perf_counter()
+    calls = 0
+    while True:
+        w = W.w_front(n, (calls % WL.steps) * WL.Dt)
+        P = oracle.Problem(w, xi0, eta0)
+        r = oracle.interface_mc(P, xs[pick], ys[pick], WL.paths, dt=WL.dt, Dt=WL.Dt, seed=0, step_index=calls,
+                                node_ids=ids[pick])
+        total_steps += int(r["path_steps"].sum())
+        calls += 1
+        if time.perf_counter() - t0 >= target_s or calls >= step_cap:
+            break
+    el = time.perf_counter() - t0
+    return total_steps, el, calls, pick.size
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    per_call_nodes = 32
+    # untimed warm-up, then K timed steps (each: the oracle's estimate at a node sample of one mesh step)
+    oracle_sample(0.0, per_call_nodes, max(1, args.warmup))
+    steps_done, el, calls, nn = oracle_sample(1e9, per_call_nodes, args.steps)
+    value = steps_done / el
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el / max(calls, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": f"front257: {WL.n}x{WL.n} grid, 2x2 subdomains, interface estimate at a sample of "
+                               f"{nn} of 509 nodes per step, {WL.paths} paths/node, dt={WL.dt}, Dt={WL.Dt}",
+                   "global_batch": nn * WL.paths, "seq_len": WL.K, "parallelism": "cpu threads"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{nn} evenly spaced interface nodes x {WL.paths} paths per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU leg
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    import paper_1402_0266_gb300 as sdd
+    from paper_1402_0266_gb300 import build as b
+    b.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n, K, Wm = WL.n, args.steps, args.warmup
+    seed = WL.seed + rank
+    stream = torch.cuda.current_stream()
+    xi0, eta0 = W.identity_fields(n)
+    xi0_d = torch.from_numpy(xi0).to(dev)
+    eta0_d = torch.from_numpy(eta0).to(dev)
+    # the mesh density of every step, resident on the device before timing
+    nsteps = max(K, Wm)
+    w_all = torch.from_numpy(np.stack([W.w_front(n, k * WL.Dt) for k in range(nsteps)])).to(dev)
+    ctx = sdd.sdd_init(n, n, WL.sub, WL.sub, w=w_all[0], xi0=xi0_d, eta0=eta0_d)
+    sp = dict(dt=WL.dt, Dt=WL.Dt, seed=seed, paths_per_node=args.paths, exit_mode=0, rtol=1e-12, max_iter=20000)
+
+    def reset():
+        sdd.sdd_set_fields(ctx, xi0_d, eta0_d)
+        sdd.sdd_set_step_index(ctx, 0)
+
+    for k in range(Wm):
+        sdd.sdd_set_w(ctx, w_all[k])
+        sdd.sdd_step(ctx, **sp)
+    sdd.sdd_sync(ctx)
+    reset()
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    steps_dev = torch.zeros(K, dtype=torch.int64, device=dev)
+    paths_ms = []
+    kernel_nodes = 0
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(K):
+        flush.zero_()
+        ev0[k].record(stream)
+        sdd.sdd_set_w(ctx, w_all[k])
+        sdd.sdd_step(ctx, **sp)
+        ev1[k].record(stream)
+        st = sdd.sdd_last_interface_stats(ctx)
+        steps_dev[k] = st["path_steps"].sum()
+        info = sdd.sdd_last_step_info(ctx)   # waits: outside the event pair
+        paths_ms.append(info["paths_ms"])
+        kernel_nodes = info["kernel_nodes"]
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    sdd.sdd_sync(ctx)
+    step_ms = [ev0[k].elapsed_time(ev1[k]) for k in range(K)]
+    total_ms = sum(step_ms)
+    path_steps = int(steps_dev.sum().item())
+    tot_steps, max_ms = allreduce([float(path_steps), 0.0], "sum", world)[0], allreduce([total_ms], "max", world)[0]
+    value = tot_steps / (max_ms / 1e3)
+    nodes = len(sdd.sdd_interface_nodes(ctx)[0])
+    nodes_per_s = world * nodes * K / (max_ms / 1e3)
+
+    # dominant kernel: the path kernel, timed by events recorded inside the step graph
+    mean_paths_ms = statistics.mean(paths_ms)
+    steps_per_launch = path_steps / K
+    achieved = ALG_OPS_PER_PATH_STEP * steps_per_launch / (mean_paths_ms / 1e3) / 1e12
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = 2070.0
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        sm_max = float(mp.get("sm_max_mhz", sm_max))
+    except Exception:
+        pass
+    peak = props.multi_processor_count * SM_LANES_PER_CLK * sm_max * 1e6 / 1e12
+    traffic = None
+    try:
+        prof = json.load(open(os.path.join(ROOT, "profiles", "paths_front257_traffic.json")))
+        traffic = prof.get("bytes_per_launch")
+    except Exception:
+        pass
+
+    # end to end through the C ABI with host buffers: w in from pinned host memory,
+    # the interface statistics back to pinned host memory, every step
+    e2e = None
+    if not args.no_e2e:
+        reset()
+        w_host = torch.from_numpy(np.stack([W.w_front(n, k * WL.Dt) for k in range(K)])).pin_memory()
+        nn = nodes
+        host = {k: torch.empty(nn, dtype=torch.float64).pin_memory() for k in ("mean_xi", "mean_eta", "se_xi", "se_eta")}
+        host["n_exit"] = torch.empty(nn, dtype=torch.int64).pin_memory()
+        host["path_steps"] = torch.empty(nn, dtype=torch.int64).pin_memory()
+        e2e_steps = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(K):
+            sdd.sdd_set_w_host(ctx, w_host[k])
+            sdd.sdd_step(ctx, **sp)
+            sdd.sdd_last_interface_stats(ctx, out=host)
+            torch.cuda.current_stream().synchronize()
+            e2e_steps += int(host["path_steps"].sum())
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        e2e_tot, e2e_max = allreduce([float(e2e_steps), 0.0], "sum", world)[0], allreduce([el], "max", world)[0]
+        e2e = {"value": e2e_tot / e2e_max, "unit": UNIT, "h2d_bytes_per_step": n * n * 4,
+               "d2h_bytes_per_step": nn * 48}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        steps_c, el_c, calls, nnc = oracle_sample(10.0, None, 3)
+        cpu = {"value": steps_c / el_c, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
+               "sample": f"{calls} mesh step(s) of the interface estimate, all {nnc} nodes x {WL.paths} paths "
+                         f"({steps_c} path-steps, {el_c:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
+            "ms_per_step": max_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"front257: w=1+10exp(-(x-0.3-0.4t)^2/0.05^2) on {n}x{n} FP32, 2x2 subdomains, "
+                                   f"{nodes} interface nodes x {args.paths} paths, dt={WL.dt}, Dt={WL.Dt} "
+                                   f"(K={WL.K}), plain exit test, FP64 PCG subdomain solves (rtol 1e-12)",
+                       "global_batch": world * nodes * args.paths, "seq_len": WL.K,
+                       "parallelism": f"{world} independent instance(s), one per GPU",
+                       "l2": "flushed before every step (256 MB write, outside the step's events)"},
+            "interface_nodes_per_s": nodes_per_s,
+            "path_steps_per_step": tot_steps / K / world,
+            "paths_kernel_ms": mean_paths_ms,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_paths", "ops_per_path_step": ALG_OPS_PER_PATH_STEP,
+                         "peak_basis": f"{props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz"},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": kernel_nodes * K,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        # the CPU oracle: rank 0 alone runs; other ranks exit without work
+        run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")))
+        return
+    world, rank, local = dist_init()
+    run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,261 @@
+/*
+ * sdd.h -- C ABI of the GB300 interface Monte Carlo library (libsdd.so).
+ *
+ * The library evaluates, at subdomain-interface nodes, the stochastic
+ * (Feynman--Kac) representation of the relaxed Winslow mesh PDE
+ *
+ *     xi_t = -(1/w) grad w . grad xi + lap xi,   eta likewise          (Eq. 3)
+ *
+ * from Bihlo & Haynes, "A stochastic domain decomposition method for time
+ * dependent mesh generation" (arXiv:1402.0266), and runs the implicit
+ * per-subdomain solves that the interface values feed (Sec. 4).
+ *
+ * Conventions (all entry points):
+ *   - The domain is the unit square; a grid has nx x ny nodes, node (i, j) at
+ *     (i / (nx-1), j / (ny-1)). Grid arrays are row-major, x fastest:
+ *     a[j * nx + i].
+ *   - "DEVICE" pointers are CUDA device (or managed) memory on the device the
+ *     context was created on; "HOST" pointers are ordinary host memory.
+ *     The caller owns every pointer it passes; the library never frees them
+ *     and keeps none of them after the call returns.
+ *   - Work is enqueued on the context's stream (a cudaStream_t passed as
+ *     void*; NULL means the legacy default stream) and runs asynchronously.
+ *     Output buffers are valid once the stream has reached the call.
+ *   - A rejected argument returns SDD_EINVAL and enqueues nothing. A failed
+ *     CUDA call returns SDD_ECUDA; sdd_last_error() then names it. Errors
+ *     found on the device are reported by sdd_sync() and by the next call.
+ *   - No entry point is thread-safe for one context; distinct contexts may be
+ *     used from distinct threads.
+ */
+#ifndef SDD_H
+#define SDD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sdd_ctx sdd_ctx;
+
+typedef enum {
+    SDD_OK = 0,
+    SDD_EINVAL = 1,   /* argument rejected on the host; nothing enqueued        */
+    SDD_ENOMEM = 2,   /* a device or host allocation failed                      */
+    SDD_ECUDA = 3,    /* a CUDA runtime call failed                              */
+    SDD_ENOCONV = 4,  /* a subdomain solve stopped at max_iter before rtol       */
+    SDD_ETIMEOUT = 5, /* a bounded device wait ran out                           */
+    SDD_EDEVICE = 6   /* a device-side check failed                              */
+} sdd_status;
+
+/* Grid and domain decomposition. The interface lines sit on the grid columns
+ * round(k (nx-1) / sub_x), k = 1 .. sub_x-1, and the grid rows
+ * round(k (ny-1) / sub_y); a value of 1 means no interface in that direction.
+ * nx, ny >= 3; 1 <= sub_x <= nx-1; 1 <= sub_y <= ny-1. */
+typedef struct {
+    int32_t nx, ny;
+    int32_t sub_x, sub_y;
+} sdd_grid;
+
+/* A set of evaluation nodes (HOST arrays of `count` entries). Coordinates must
+ * lie in [0, 1]; a node on the boundary returns its Dirichlet value with a
+ * standard error of 0 and no path steps. n_paths[k] in [1, 2^31 - 1]. The
+ * node's position k in the arrays is its index in the random stream. */
+typedef struct {
+    const double* x;
+    const double* y;
+    const int64_t* n_paths;
+    int64_t count;
+} sdd_nodes;
+
+/* Per-node results (DEVICE arrays of `count` entries; any may be NULL):
+ * the Monte Carlo means of the two scored fields (Sec. 4, "the expected values
+ * are then replaced by arithmetic means"), their standard errors
+ * s / sqrt(N) with s^2 the N-1 sample variance, the number of paths that left
+ * the domain and the number of Euler--Maruyama sub-steps taken in total. */
+typedef struct {
+    double* mean_xi;
+    double* mean_eta;
+    double* se_xi;
+    double* se_eta;
+    int64_t* n_exit;
+    int64_t* path_steps;
+} sdd_node_stats;
+
+/* Per-path records (DEVICE arrays, one entry per path, node after node in the
+ * order of sdd_nodes; any may be NULL): sub-steps taken; exit code (-1 survived
+ * the mesh step, 0..3 left through face left/right/bottom/top at a sub-step
+ * end, 4..7 left through face k-4 by the bridge test); the two scores; the end
+ * point (exit point or X at the end of the step). */
+typedef struct {
+    int32_t* steps;
+    int32_t* code;
+    float* score_xi;
+    float* score_eta;
+    float* x_end;
+    float* y_end;
+} sdd_path_records;
+
+/* Parameters of one evaluation over a mesh step (Sec. 4).
+ *   dt          Euler--Maruyama sub-step, > 0.
+ *   Dt          the mesh step; Dt / dt must be an integer K within 1e-9
+ *               relative, 1 <= K <= 2^20.
+ *   seed        Philox key: key = (seed low 32 bits, high 32 bits ^ instance).
+ *   step_index  mesh step number n, the last word of the Philox counter
+ *               (counter = (path, node, draw, n)).
+ *   exit_mode   0: the paper's boundary test after every sub-step;
+ *               1: that test plus a Brownian-bridge test between sub-steps.
+ *   block_threads, paths_per_task: launch shape; 0 picks the tuned default.
+ *               block_threads in {64, 128, 256, 512}; paths_per_task a
+ *               multiple of 32. */
+typedef struct {
+    double dt;
+    double Dt;
+    uint64_t seed;
+    uint32_t step_index;
+    int32_t exit_mode;
+    int32_t block_threads;
+    int32_t paths_per_task;
+} sdd_mc_params;
+
+/* Create a context on the current CUDA device.
+ *   g        grid and decomposition (HOST).
+ *   w        DEVICE nx*ny float, the mesh density at the start of the first
+ *            mesh step; every value finite and > 0. NULL means w = 1.
+ *   xi0,eta0 DEVICE nx*ny double, the computational coordinates at the start
+ *            of the first mesh step. NULL means the uniform mesh xi = x,
+ *            eta = y (Sec. 3, initial conditions).
+ *   stream   cudaStream_t for all work of this context.
+ * Boundary data default to the paper's (Sec. 3): xi = 0 / 1 on x = 0 / 1,
+ * eta = 0 / 1 on y = 0 / 1, the 1D Winslow solution on the other faces.
+ * The inputs are copied; the call waits for the copies. */
+sdd_status sdd_init(sdd_ctx** out, const sdd_grid* g, const float* w, const double* xi0, const double* eta0,
+                    void* stream);
+
+/* Replace the mesh density (held fixed over a mesh step, Sec. 4). DEVICE
+ * nx*ny floats; copied on the context stream. Values are checked on the device
+ * (finite and > 0); a violation is reported as SDD_EDEVICE. */
+sdd_status sdd_set_w(sdd_ctx* ctx, const float* w);
+
+/* As sdd_set_w, from HOST memory (pinned memory copies asynchronously). */
+sdd_status sdd_set_w_host(sdd_ctx* ctx, const float* w);
+
+/* Replace xi and eta at the start of the next mesh step (DEVICE nx*ny doubles). */
+sdd_status sdd_set_fields(sdd_ctx* ctx, const double* xi, const double* eta);
+
+/* Boundary data f, g (Sec. 3). faces: DEVICE doubles in the layout
+ *   xi_left[ny] xi_right[ny] xi_bottom[nx] xi_top[nx]
+ *   eta_left[ny] eta_right[ny] eta_bottom[nx] eta_top[nx]
+ * (left/right: x = 0 / 1, indexed by j; bottom/top: y = 0 / 1, indexed by i),
+ * linear between nodes. NULL returns to the paper's data, recomputed from w
+ * whenever w changes. The values are copied. */
+sdd_status sdd_set_boundary(sdd_ctx* ctx, const double* faces);
+
+/* The face data in use (DEVICE output, 2 (2 nx + 2 ny) doubles, layout above). */
+sdd_status sdd_get_faces(sdd_ctx* ctx, double* faces);
+
+/* Copy out xi, eta at the start of the next mesh step (DEVICE or HOST outputs,
+ * nx*ny doubles each; the _host form waits for the copy). */
+sdd_status sdd_get_fields(sdd_ctx* ctx, double* xi, double* eta);
+sdd_status sdd_get_fields_host(sdd_ctx* ctx, double* xi, double* eta);
+
+/* The Monte Carlo estimate of Eq. (7b) at the given nodes over one mesh step
+ * (Sec. 4): from each node, n_paths Euler--Maruyama paths of
+ * dX = -(1/w) grad w dt + sqrt(2) dW (Eq. 7a) with drift from finite
+ * differences of w at the nodes and bilinear interpolation between them,
+ * K = Dt / dt sub-steps and a boundary test after each; a path that leaves
+ * scores the boundary data at its exit point, a path that stays scores the
+ * bilinear interpolant of xi, eta at its end point; the means and standard
+ * errors go to `out`. Uses the context's current w, xi, eta and face data. */
+sdd_status sdd_interface_mc(sdd_ctx* ctx, const sdd_nodes* nodes, const sdd_mc_params* p, sdd_node_stats* out);
+
+/* As sdd_interface_mc, and also write every path's record. */
+sdd_status sdd_interface_mc_record(sdd_ctx* ctx, const sdd_nodes* nodes, const sdd_mc_params* p,
+                                   sdd_node_stats* out, const sdd_path_records* rec);
+
+/* The interface nodes of the context's decomposition (each once): first the
+ * vertical lines left to right, each bottom to top (j = 1 .. ny-2), then the
+ * horizontal lines bottom to top, each left to right (i = 1 .. nx-2), skipping
+ * nodes already listed. With x, y NULL only the count is returned. HOST
+ * outputs of *count entries. */
+sdd_status sdd_interface_nodes(sdd_ctx* ctx, double* x, double* y, int64_t* count);
+
+/* Deterministic single-domain solves (Sec. 4): one implicit Euler step of
+ * Eq. (3) on every subdomain, in the symmetric form
+ *   (xi_ij - xi^{n-1}_ij) / (w_ij Dt) = sum_nb (xi_nb - xi_ij) / (wbar h^2),
+ * wbar the average of w over the two nodes, with Dirichlet data from the face
+ * data on the outer boundary and from iface_xi / iface_eta (DEVICE, one
+ * double per interface node in the order of sdd_interface_nodes) on the
+ * interfaces. Solved in double precision by Jacobi-preconditioned conjugate
+ * gradients to ||r|| <= rtol ||b|| or max_iter iterations.
+ * Outputs xi_out, eta_out: DEVICE nx*ny doubles (full fields). iters_out
+ * (HOST, may be NULL): the largest iteration count over the systems; asking
+ * for it waits for the solve. The context's fields are not changed.
+ * Non-convergence returns SDD_ENOCONV when iters_out is given, else it is
+ * reported by sdd_sync(). */
+sdd_status sdd_subdomain_solve(sdd_ctx* ctx, double Dt, const double* iface_xi, const double* iface_eta,
+                               double rtol, int32_t max_iter, double* xi_out, double* eta_out,
+                               int32_t* iters_out);
+
+/* One mesh step t_{n-1} -> t_n (Sec. 4): the interface estimate at every
+ * interface node with paths_per_node paths, the subdomain solves with those
+ * values, then xi, eta advance and the step counter n (the Philox counter's
+ * last word) increases by one. The sequence is recorded once into a CUDA
+ * graph and replayed while the parameters stay the same. The interface
+ * statistics of the step can be read with sdd_last_interface_stats. */
+typedef struct {
+    double dt;
+    double Dt;
+    uint64_t seed;
+    int64_t paths_per_node;
+    int32_t exit_mode;
+    int32_t max_iter;
+    double rtol;
+} sdd_step_params;
+
+sdd_status sdd_step(sdd_ctx* ctx, const sdd_step_params* p);
+
+/* Statistics of the interface nodes from the last sdd_step (DEVICE outputs in
+ * the order of sdd_interface_nodes). */
+sdd_status sdd_last_interface_stats(sdd_ctx* ctx, sdd_node_stats* out);
+
+/* Facts about the last sdd_step, for profiling (waits for the stream):
+ * the number of kernel launches in the step graph and the device time of the
+ * step's parts, taken with events recorded inside the graph. */
+typedef struct {
+    int32_t kernel_nodes;  /* kernels launched per step                          */
+    float paths_ms;        /* the path kernel                                    */
+    float estimate_ms;     /* the whole interface estimate (tables, paths, means) */
+    float solve_ms;        /* the subdomain solves                               */
+    float step_ms;         /* the whole step                                     */
+} sdd_step_info;
+
+sdd_status sdd_last_step_info(sdd_ctx* ctx, sdd_step_info* out);
+
+/* Mesh step counter n. */
+sdd_status sdd_set_step_index(sdd_ctx* ctx, uint32_t n);
+uint32_t sdd_get_step_index(const sdd_ctx* ctx);
+
+/* Wait for the context stream and return the first device-side error since
+ * the last sdd_sync (SDD_EDEVICE, SDD_ENOCONV, SDD_ETIMEOUT) or SDD_OK. */
+sdd_status sdd_sync(sdd_ctx* ctx);
+
+/* Last error message of the context (static storage until the next call). */
+const char* sdd_last_error(const sdd_ctx* ctx);
+
+/* Release the context and everything it allocated (waits for its stream). */
+void sdd_destroy(sdd_ctx* ctx);
+
+/* The variates of the estimator, for checking: for each counter
+ * (path, node, draw, step) in `ctrs` (DEVICE, 4 uint32 per entry), the Philox
+ * block (`words`, DEVICE, 4 uint32 per entry) and the four normals of its two
+ * Box--Muller pairs, unscaled (`normals`, DEVICE, 4 float per entry; may be
+ * NULL). key = (seed low, seed high ^ instance). */
+sdd_status sdd_rng_draw(uint64_t seed, uint32_t instance, const uint32_t* ctrs, int64_t count, uint32_t* words,
+                        float* normals, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDD_H */

@@ -287,3 +287,40 @@ def interface_mc(problem: Problem, xs, ys, n_paths, *, dt: float, Dt: float, see
     if recs is not None:
         out.update(recs)
     return out
+
+
+# --------------------------------------------------------------------------
+# One mesh step of the decomposition method
+# --------------------------------------------------------------------------
+
+def boundary_grid(faces, nx: int, ny: int, field: int, inner):
+    """A grid holding `inner` inside and the face data on the boundary ring
+    (left, right, bottom, top: the first that holds wins at the corners)."""
+    seg = split_faces(faces, nx, ny)
+    g = np.array(inner, dtype=np.float64, copy=True)
+    g[-1, :] = seg[(field, 3)]
+    g[0, :] = seg[(field, 2)]
+    g[:, -1] = seg[(field, 1)]
+    g[:, 0] = seg[(field, 0)]
+    return g
+
+
+def dd_step(w, xi, eta, *, sub_x: int, sub_y: int, dt: float, Dt: float, n_paths: int, seed: int,
+            step_index: int, nodes_ij, exit_mode: int = 0, faces=None, threads=None):
+    """One mesh step t_{n-1} -> t_n of the method (Sec. 4): the interface
+    estimate at the nodes nodes_ij = (i, j) (their position is their node index
+    in the random stream), then the implicit subdomain solves by LU with those
+    values and the face data as Dirichlet data. Returns ([xi_n, eta_n], stats)."""
+    from . import solver
+    P = Problem(w, xi, eta, faces)
+    ii, jj = (np.asarray(a) for a in nodes_ij)
+    xs = ii / (P.nx - 1)
+    ys = jj / (P.ny - 1)
+    r = interface_mc(P, xs, ys, n_paths, dt=dt, Dt=Dt, seed=seed, exit_mode=exit_mode, step_index=step_index,
+                     threads=threads)
+    bx = boundary_grid(P.faces, P.nx, P.ny, 0, P.xi0)
+    be = boundary_grid(P.faces, P.nx, P.ny, 1, P.eta0)
+    bx[jj, ii] = r["mean_xi"]
+    be[jj, ii] = r["mean_eta"]
+    new = solver.subdomain_solve(P.w, [P.xi0, P.eta0], [bx, be], sub_x, sub_y, Dt)
+    return new, r

@@ -1,0 +1,384 @@
+"""Python binding of libsdd (include/sdd.h): argument marshalling only.
+
+Every step of the computation runs in the CUDA library; this module only
+turns torch tensors into device pointers, allocates outputs with torch and
+checks status codes. There is no CPU fallback: if the library is missing the
+first call raises.
+
+    import torch, paper_1402_0266_gb300 as sdd
+    ctx = sdd.sdd_init(nx=257, ny=257, sub_x=2, sub_y=2, w=w_dev)   # w: cuda float32 (ny, nx)
+    out = sdd.sdd_interface_mc(ctx, x, y, n_paths, dt=1e-4, Dt=1e-2, seed=0)
+    sdd.sdd_step(ctx, dt=1e-4, Dt=1e-2, seed=0, paths_per_node=10000)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsdd.so")
+
+SDD_OK, SDD_EINVAL, SDD_ENOMEM, SDD_ECUDA, SDD_ENOCONV, SDD_ETIMEOUT, SDD_EDEVICE = range(7)
+STATUS_NAMES = {0: "SDD_OK", 1: "SDD_EINVAL", 2: "SDD_ENOMEM", 3: "SDD_ECUDA", 4: "SDD_ENOCONV",
+                5: "SDD_ETIMEOUT", 6: "SDD_EDEVICE"}
+
+# every entry point declared in include/sdd.h
+EXPORTS = [
+    "sdd_init", "sdd_set_w", "sdd_set_w_host", "sdd_set_fields", "sdd_set_boundary", "sdd_get_faces",
+    "sdd_get_fields", "sdd_get_fields_host", "sdd_interface_mc", "sdd_interface_mc_record", "sdd_interface_nodes",
+    "sdd_subdomain_solve", "sdd_step", "sdd_last_interface_stats", "sdd_last_step_info", "sdd_set_step_index",
+    "sdd_get_step_index",
+    "sdd_sync", "sdd_last_error", "sdd_destroy", "sdd_rng_draw",
+]
+
+
+class SddError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("sub_x", ctypes.c_int32), ("sub_y", ctypes.c_int32)]
+
+
+class _Nodes(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("n_paths", ctypes.c_void_p), ("count", ctypes.c_int64)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("mean_xi", ctypes.c_void_p), ("mean_eta", ctypes.c_void_p), ("se_xi", ctypes.c_void_p),
+                ("se_eta", ctypes.c_void_p), ("n_exit", ctypes.c_void_p), ("path_steps", ctypes.c_void_p)]
+
+
+class _Records(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_void_p), ("code", ctypes.c_void_p), ("score_xi", ctypes.c_void_p),
+                ("score_eta", ctypes.c_void_p), ("x_end", ctypes.c_void_p), ("y_end", ctypes.c_void_p)]
+
+
+class _McParams(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("Dt", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("step_index", ctypes.c_uint32), ("exit_mode", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+                ("paths_per_task", ctypes.c_int32)]
+
+
+class _StepInfo(ctypes.Structure):
+    _fields_ = [("kernel_nodes", ctypes.c_int32), ("paths_ms", ctypes.c_float), ("estimate_ms", ctypes.c_float),
+                ("solve_ms", ctypes.c_float), ("step_ms", ctypes.c_float)]
+
+
+class _StepParams(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("Dt", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("paths_per_node", ctypes.c_int64), ("exit_mode", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("rtol", ctypes.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """The loaded libsdd.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libsdd.so not found at {LIB_PATH}: build it with "
+                                   "`python -m paper_1402_0266_gb300.build` (no CPU fallback exists)")
+            L = ctypes.CDLL(LIB_PATH)
+            vp, i32, i64, u32, u64, dbl = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                           ctypes.c_uint64, ctypes.c_double)
+            sig = {
+                "sdd_init": [ctypes.POINTER(vp), ctypes.POINTER(_Grid), vp, vp, vp, vp],
+                "sdd_set_w": [vp, vp],
+                "sdd_set_w_host": [vp, vp],
+                "sdd_set_fields": [vp, vp, vp],
+                "sdd_set_boundary": [vp, vp],
+                "sdd_get_faces": [vp, vp],
+                "sdd_get_fields": [vp, vp, vp],
+                "sdd_get_fields_host": [vp, vp, vp],
+                "sdd_interface_mc": [vp, ctypes.POINTER(_Nodes), ctypes.POINTER(_McParams), ctypes.POINTER(_Stats)],
+                "sdd_interface_mc_record": [vp, ctypes.POINTER(_Nodes), ctypes.POINTER(_McParams),
+                                            ctypes.POINTER(_Stats), ctypes.POINTER(_Records)],
+                "sdd_interface_nodes": [vp, vp, vp, ctypes.POINTER(i64)],
+                "sdd_subdomain_solve": [vp, dbl, vp, vp, dbl, i32, vp, vp, ctypes.POINTER(i32)],
+                "sdd_step": [vp, ctypes.POINTER(_StepParams)],
+                "sdd_last_interface_stats": [vp, ctypes.POINTER(_Stats)],
+                "sdd_last_step_info": [vp, ctypes.POINTER(_StepInfo)],
+                "sdd_set_step_index": [vp, u32],
+                "sdd_get_step_index": [vp],
+                "sdd_sync": [vp],
+                "sdd_last_error": [vp],
+                "sdd_destroy": [vp],
+                "sdd_rng_draw": [u64, u32, vp, i64, vp, vp, vp],
+            }
+            for name, args in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = ctypes.c_int
+            L.sdd_get_step_index.restype = ctypes.c_uint32
+            L.sdd_last_error.restype = ctypes.c_char_p
+            L.sdd_destroy.restype = None
+            _lib = L
+    return _lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0) if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _check_dev(t, dtype, shape, name):
+    torch = _torch()
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"{name}: expected a contiguous cuda {dtype} tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape) and t.numel() != int(np.prod(shape)):
+        raise ValueError(f"{name}: expected shape {shape}, got {tuple(t.shape)}")
+    return t
+
+
+class Ctx:
+    """An sdd_ctx handle with its grid shape."""
+
+    def __init__(self, handle, nx, ny, sub_x, sub_y, stream):
+        self.handle = handle
+        self.nx, self.ny, self.sub_x, self.sub_y = nx, ny, sub_x, sub_y
+        self.stream = stream
+
+    def _check(self, st):
+        if st != SDD_OK:
+            msg = lib().sdd_last_error(self.handle)
+            raise SddError(st, msg.decode() if msg else "")
+
+    def __del__(self):
+        try:
+            sdd_destroy(self)
+        except Exception:
+            pass
+
+
+def sdd_init(nx, ny=None, sub_x=1, sub_y=None, w=None, xi0=None, eta0=None, stream=None) -> Ctx:
+    ny = nx if ny is None else ny
+    sub_y = sub_x if sub_y is None else sub_y
+    torch = _torch()
+    for t, dt, name in ((w, torch.float32, "w"), (xi0, torch.float64, "xi0"), (eta0, torch.float64, "eta0")):
+        if t is not None:
+            _check_dev(t, dt, (ny, nx), name)
+    h = ctypes.c_void_p()
+    g = _Grid(nx, ny, sub_x, sub_y)
+    st = lib().sdd_init(ctypes.byref(h), ctypes.byref(g), _ptr(w), _ptr(xi0), _ptr(eta0), _stream(stream))
+    if st != SDD_OK:
+        raise SddError(st, "sdd_init failed")
+    return Ctx(h, nx, ny, sub_x, sub_y, stream)
+
+
+def sdd_set_w(ctx: Ctx, w):
+    _check_dev(w, _torch().float32, (ctx.ny, ctx.nx), "w")
+    ctx._check(lib().sdd_set_w(ctx.handle, _ptr(w)))
+
+
+def sdd_set_w_host(ctx: Ctx, w):
+    """w: a CPU tensor (pinned for an asynchronous copy) or numpy float32 array."""
+    if hasattr(w, "data_ptr"):
+        assert w.dtype == _torch().float32 and w.is_contiguous() and w.numel() == ctx.nx * ctx.ny
+        p = ctypes.c_void_p(w.data_ptr())
+    else:
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        p = ctypes.c_void_p(w.ctypes.data)
+    ctx._check(lib().sdd_set_w_host(ctx.handle, p))
+
+
+def sdd_set_fields(ctx: Ctx, xi, eta):
+    torch = _torch()
+    _check_dev(xi, torch.float64, (ctx.ny, ctx.nx), "xi")
+    _check_dev(eta, torch.float64, (ctx.ny, ctx.nx), "eta")
+    ctx._check(lib().sdd_set_fields(ctx.handle, _ptr(xi), _ptr(eta)))
+
+
+def faces_len(nx, ny):
+    return 2 * (2 * nx + 2 * ny)
+
+
+def sdd_set_boundary(ctx: Ctx, faces=None):
+    if faces is not None:
+        _check_dev(faces, _torch().float64, (faces_len(ctx.nx, ctx.ny),), "faces")
+    ctx._check(lib().sdd_set_boundary(ctx.handle, _ptr(faces)))
+
+
+def sdd_get_faces(ctx: Ctx):
+    torch = _torch()
+    out = torch.empty(faces_len(ctx.nx, ctx.ny), dtype=torch.float64, device="cuda")
+    ctx._check(lib().sdd_get_faces(ctx.handle, _ptr(out)))
+    return out
+
+
+def sdd_get_fields(ctx: Ctx):
+    torch = _torch()
+    xi = torch.empty((ctx.ny, ctx.nx), dtype=torch.float64, device="cuda")
+    eta = torch.empty_like(xi)
+    ctx._check(lib().sdd_get_fields(ctx.handle, _ptr(xi), _ptr(eta)))
+    return xi, eta
+
+
+def sdd_get_fields_host(ctx: Ctx):
+    xi = np.empty((ctx.ny, ctx.nx), np.float64)
+    eta = np.empty_like(xi)
+    ctx._check(lib().sdd_get_fields_host(ctx.handle, ctypes.c_void_p(xi.ctypes.data), ctypes.c_void_p(eta.ctypes.data)))
+    return xi, eta
+
+
+def _nodes(x, y, n_paths):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    n = np.ascontiguousarray(np.broadcast_to(np.asarray(n_paths, dtype=np.int64), x.shape))
+    keep = (x, y, n)
+    return _Nodes(x.ctypes.data, y.ctypes.data, n.ctypes.data, x.size), keep
+
+
+def _alloc_stats(count):
+    torch = _torch()
+    d = {k: torch.empty(count, dtype=torch.float64, device="cuda") for k in ("mean_xi", "mean_eta", "se_xi", "se_eta")}
+    d["n_exit"] = torch.empty(count, dtype=torch.int64, device="cuda")
+    d["path_steps"] = torch.empty(count, dtype=torch.int64, device="cuda")
+    s = _Stats(*(d[k].data_ptr() for k in ("mean_xi", "mean_eta", "se_xi", "se_eta", "n_exit", "path_steps")))
+    return d, s
+
+
+def mc_params(dt, Dt, seed=0, step_index=0, exit_mode=0, block_threads=0, paths_per_task=0):
+    return _McParams(dt, Dt, seed, step_index, exit_mode, block_threads, paths_per_task)
+
+
+def sdd_interface_mc(ctx: Ctx, x, y, n_paths, dt, Dt, seed=0, step_index=0, exit_mode=0, block_threads=0,
+                     paths_per_task=0, out=None):
+    """Interface estimate at nodes (x, y) (host arrays). Returns a dict of cuda tensors."""
+    nodes, keep = _nodes(x, y, n_paths)
+    if out is None:
+        out, s = _alloc_stats(nodes.count)
+    else:
+        s = _Stats(*(out[k].data_ptr() for k in ("mean_xi", "mean_eta", "se_xi", "se_eta", "n_exit", "path_steps")))
+    p = mc_params(dt, Dt, seed, step_index, exit_mode, block_threads, paths_per_task)
+    ctx._check(lib().sdd_interface_mc(ctx.handle, ctypes.byref(nodes), ctypes.byref(p), ctypes.byref(s)))
+    del keep
+    return out
+
+
+def sdd_interface_mc_record(ctx: Ctx, x, y, n_paths, dt, Dt, seed=0, step_index=0, exit_mode=0, block_threads=0,
+                            paths_per_task=0):
+    """As sdd_interface_mc, plus per-path records (node after node)."""
+    torch = _torch()
+    nodes, keep = _nodes(x, y, n_paths)
+    out, s = _alloc_stats(nodes.count)
+    total = int(keep[2].sum())
+    rec = {"steps": torch.empty(total, dtype=torch.int32, device="cuda"),
+           "code": torch.empty(total, dtype=torch.int32, device="cuda")}
+    for k in ("score_xi", "score_eta", "x_end", "y_end"):
+        rec[k] = torch.empty(total, dtype=torch.float32, device="cuda")
+    r = _Records(*(rec[k].data_ptr() for k in ("steps", "code", "score_xi", "score_eta", "x_end", "y_end")))
+    p = mc_params(dt, Dt, seed, step_index, exit_mode, block_threads, paths_per_task)
+    ctx._check(lib().sdd_interface_mc_record(ctx.handle, ctypes.byref(nodes), ctypes.byref(p), ctypes.byref(s),
+                                             ctypes.byref(r)))
+    del keep
+    out.update(rec)
+    return out
+
+
+def sdd_interface_nodes(ctx: Ctx):
+    n = ctypes.c_int64()
+    ctx._check(lib().sdd_interface_nodes(ctx.handle, None, None, ctypes.byref(n)))
+    x = np.empty(n.value)
+    y = np.empty(n.value)
+    ctx._check(lib().sdd_interface_nodes(ctx.handle, ctypes.c_void_p(x.ctypes.data), ctypes.c_void_p(y.ctypes.data),
+                                         ctypes.byref(n)))
+    return x, y
+
+
+def sdd_subdomain_solve(ctx: Ctx, Dt, iface_xi, iface_eta, rtol=1e-12, max_iter=20000, want_iters=True):
+    torch = _torch()
+    xi = torch.empty((ctx.ny, ctx.nx), dtype=torch.float64, device="cuda")
+    eta = torch.empty_like(xi)
+    it = ctypes.c_int32(-1)
+    st = lib().sdd_subdomain_solve(ctx.handle, Dt, _ptr(iface_xi), _ptr(iface_eta), rtol, max_iter, _ptr(xi),
+                                   _ptr(eta), ctypes.byref(it) if want_iters else None)
+    ctx._check(st)
+    return xi, eta, it.value
+
+
+def step_params(dt, Dt, seed=0, paths_per_node=10000, exit_mode=0, max_iter=20000, rtol=1e-12):
+    return _StepParams(dt, Dt, seed, paths_per_node, exit_mode, max_iter, rtol)
+
+
+def sdd_step(ctx: Ctx, dt, Dt, seed=0, paths_per_node=10000, exit_mode=0, max_iter=20000, rtol=1e-12):
+    p = step_params(dt, Dt, seed, paths_per_node, exit_mode, max_iter, rtol)
+    ctx._check(lib().sdd_step(ctx.handle, ctypes.byref(p)))
+
+
+def sdd_last_interface_stats(ctx: Ctx, out=None):
+    """Interface statistics of the last sdd_step. `out`: optional dict of cuda or
+    pinned host tensors (mean_xi, mean_eta, se_xi, se_eta float64; n_exit, path_steps int64)."""
+    if out is None:
+        n = ctypes.c_int64()
+        ctx._check(lib().sdd_interface_nodes(ctx.handle, None, None, ctypes.byref(n)))
+        out, s = _alloc_stats(n.value)
+    else:
+        s = _Stats(*(out[k].data_ptr() for k in ("mean_xi", "mean_eta", "se_xi", "se_eta", "n_exit", "path_steps")))
+    ctx._check(lib().sdd_last_interface_stats(ctx.handle, ctypes.byref(s)))
+    return out
+
+
+def sdd_last_step_info(ctx: Ctx) -> dict:
+    info = _StepInfo()
+    ctx._check(lib().sdd_last_step_info(ctx.handle, ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in _StepInfo._fields_}
+
+
+def sdd_set_step_index(ctx: Ctx, n: int):
+    ctx._check(lib().sdd_set_step_index(ctx.handle, n))
+
+
+def sdd_get_step_index(ctx: Ctx) -> int:
+    return int(lib().sdd_get_step_index(ctx.handle))
+
+
+def sdd_sync(ctx: Ctx):
+    ctx._check(lib().sdd_sync(ctx.handle))
+
+
+def sdd_last_error(ctx: Ctx) -> str:
+    m = lib().sdd_last_error(ctx.handle)
+    return m.decode() if m else ""
+
+
+def sdd_destroy(ctx: Ctx):
+    if ctx.handle is not None and ctx.handle.value:
+        lib().sdd_destroy(ctx.handle)
+    ctx.handle = ctypes.c_void_p(0)
+
+
+def sdd_rng_draw(seed, instance, counters, stream=None):
+    """Philox words and unit normals for counters (n, 4) uint32 (cuda int32 tensor or numpy)."""
+    torch = _torch()
+    if isinstance(counters, np.ndarray):
+        c = torch.from_numpy(np.ascontiguousarray(counters, dtype=np.uint32).view(np.int32)).cuda()
+    else:
+        c = counters.contiguous()
+    n = c.numel() // 4
+    words = torch.empty((n, 4), dtype=torch.int32, device="cuda")
+    normals = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    st = lib().sdd_rng_draw(seed, instance, _ptr(c), n, _ptr(words), _ptr(normals), _stream(stream))
+    if st != SDD_OK:
+        raise SddError(st, "sdd_rng_draw failed")
+    return words, normals

@@ -1,0 +1,848 @@
+// api.cu -- the C ABI of libsdd (include/sdd.h): contexts, node plans, launches,
+// the subdomain solve and the per-mesh-step CUDA graph.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sdd.h"
+#include "common.cuh"
+
+using namespace sdd;
+
+namespace {
+
+template <typename T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    cudaError_t alloc(size_t count)
+    {
+        if (count <= n && p) return cudaSuccess;
+        release();
+        if (count == 0) return cudaSuccess;
+        cudaError_t e = cudaMalloc((void**)&p, count * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            n = 0;
+            return e;
+        }
+        n = count;
+        return cudaSuccess;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+// A node set turned into tasks, with the device tables the kernels read.
+struct Plan {
+    std::vector<double> hx, hy;
+    std::vector<int64_t> hp;
+    int ppt_req = -1, block_req = -1, exit_mode = -1;
+    bool valid = false;
+
+    int block = 256, grid = 0, ppt = 0;
+    int64_t nnodes = 0, ntasks = 0, total_paths = 0;
+    std::vector<NodeDev> nodes;
+    std::vector<Task> tasks;
+    DevBuf<NodeDev> d_nodes;
+    DevBuf<Task> d_tasks;
+    DevBuf<Partial> d_partials;
+    DevBuf<int> d_queue;
+
+    void release()
+    {
+        d_nodes.release();
+        d_tasks.release();
+        d_partials.release();
+        d_queue.release();
+        valid = false;
+    }
+};
+
+struct GraphSlot {
+    cudaGraphExec_t exec = nullptr;
+    void release()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+    }
+};
+
+}  // namespace
+
+struct sdd_ctx {
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    int nx = 0, ny = 0, sub_x = 1, sub_y = 1;
+
+    DevBuf<float> w;
+    DevBuf<double> fld[2][2];  // [buffer][field]: the current fields are fld[cur]
+    int cur = 0;
+    DevBuf<double> faces64;
+    DevBuf<float> faces32;
+    DevBuf<float4> bcoef, fcoef;
+    DevBuf<InstDev> d_inst;
+    DevBuf<int> d_status;
+    DevBuf<uint32_t> d_step;
+    bool user_faces = false;
+    bool dirty_w = true, dirty_fields = true;
+
+    Plan mc_plan;     // sdd_interface_mc
+    Plan step_plan;   // the interface nodes of sdd_step
+    std::vector<double> iface_x, iface_y;
+    std::vector<int32_t> iface_idx;
+    DevBuf<int32_t> d_iface_idx;
+    DevBuf<double> iface_stats[4];  // mean_xi, mean_eta, se_xi, se_eta
+    DevBuf<long long> iface_counts[2];
+
+    // solver
+    DevBuf<double> cx, cy, dg, rhs0, r[2], p[2], q[2];
+    std::vector<SolveSys> systems;
+    DevBuf<SolveSys> d_systems;
+    DevBuf<int32_t> d_iters;
+
+    // step graph (one per parity of the current field buffer)
+    GraphSlot graph[2];
+    int graph_kernels = 0;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // step start, paths start/end, estimate end, step end
+    sdd_step_params graph_params{};
+    bool graph_ok = false;
+    uint32_t step_index = 0;
+
+    std::string err;
+};
+
+namespace {
+
+sdd_status fail(sdd_ctx* c, sdd_status s, const char* fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+#define CU(c, expr)                                                                                       \
+    do {                                                                                                  \
+        cudaError_t e_ = (expr);                                                                          \
+        if (e_ != cudaSuccess)                                                                            \
+            return fail((c), e_ == cudaErrorMemoryAllocation ? SDD_ENOMEM : SDD_ECUDA, "%s: %s (%s:%d)", \
+                        #expr, cudaGetErrorString(e_), __FILE__, __LINE__);                               \
+    } while (0)
+
+std::vector<int> interface_lines(int n, int parts)
+{
+    std::vector<int> v;
+    for (int k = 1; k < parts; ++k) v.push_back((int)std::lround((double)k * (n - 1) / parts));
+    return v;
+}
+
+std::vector<int> block_edges(int n, int parts)
+{
+    std::vector<int> v{0};
+    for (int k : interface_lines(n, parts)) v.push_back(k);
+    v.push_back(n - 1);
+    return v;
+}
+
+float below(float v) { return std::nextafter(v, 0.0f); }
+
+sdd_status upload_inst(sdd_ctx* c)
+{
+    InstDev I{};
+    I.bcoef = c->bcoef.p;
+    I.fcoef = c->fcoef.p;
+    I.faces32 = c->faces32.p;
+    I.faces64 = c->faces64.p;
+    I.nx = c->nx;
+    I.ny = c->ny;
+    I.sx = (float)(c->nx - 1);
+    I.sy = (float)(c->ny - 1);
+    I.gxmax = below((float)(c->nx - 1));
+    I.gymax = below((float)(c->ny - 1));
+    CU(c, c->d_inst.alloc(1));
+    CU(c, cudaMemcpy(c->d_inst.p, &I, sizeof I, cudaMemcpyHostToDevice));
+    return SDD_OK;
+}
+
+int64_t faces_len(const sdd_ctx* c) { return 2LL * (2LL * c->nx + 2LL * c->ny); }
+
+// Field tables for the current w, fields and face data (enqueued on s).
+sdd_status prepare(sdd_ctx* c, cudaStream_t s)
+{
+    if (c->dirty_w && !c->user_faces) {
+        CU(c, launch_winslow_faces(c->w.p, c->nx, c->ny, c->faces64.p, s));
+        CU(c, launch_faces32(c->faces64.p, c->faces32.p, (int)faces_len(c), s));
+    }
+    if (c->dirty_w || c->dirty_fields) {
+        CU(c, launch_prep_cells(c->w.p, c->fld[c->cur][0].p, c->fld[c->cur][1].p, c->nx, c->ny, c->bcoef.p,
+                                c->fcoef.p, c->d_status.p, s));
+    }
+    c->dirty_w = c->dirty_fields = false;
+    return SDD_OK;
+}
+
+bool valid_params(sdd_ctx* c, double dt, double Dt, int exit_mode, int* K)
+{
+    if (!(dt > 0.0) || !(Dt > 0.0) || !std::isfinite(dt) || !std::isfinite(Dt)) return false;
+    const double k = Dt / dt;
+    const double kr = std::round(k);
+    if (kr < 1.0 || kr > (double)(1 << 20) || std::fabs(kr - k) > 1e-9 * k) return false;
+    if (exit_mode != 0 && exit_mode != 1) return false;
+    *K = (int)kr;
+    (void)c;
+    return true;
+}
+
+// Build (or reuse) the plan of a node set.
+sdd_status build_plan(sdd_ctx* c, Plan& P, const double* x, const double* y, const int64_t* np, int64_t count,
+                      int ppt_req, int block_req, int exit_mode, bool record)
+{
+    if (count < 0 || count > (1LL << 30)) return fail(c, SDD_EINVAL, "node count out of range");
+    for (int64_t k = 0; k < count; ++k) {
+        if (!(x[k] >= 0.0 && x[k] <= 1.0 && y[k] >= 0.0 && y[k] <= 1.0))
+            return fail(c, SDD_EINVAL, "node %lld lies outside the unit square", (long long)k);
+        if (np[k] < 1 || np[k] > 0x7fffffffLL) return fail(c, SDD_EINVAL, "node %lld: n_paths out of range", (long long)k);
+    }
+    if (block_req != 0 && block_req != 64 && block_req != 128 && block_req != 256 && block_req != 512)
+        return fail(c, SDD_EINVAL, "block_threads must be 0, 64, 128, 256 or 512");
+    if (ppt_req < 0 || (ppt_req % 32) != 0) return fail(c, SDD_EINVAL, "paths_per_task must be a multiple of 32");
+
+    const bool same = P.valid && P.ppt_req == ppt_req && P.block_req == block_req && P.exit_mode == exit_mode &&
+                      (int64_t)P.hx.size() == count && std::equal(P.hx.begin(), P.hx.end(), x) &&
+                      std::equal(P.hy.begin(), P.hy.end(), y) && std::equal(P.hp.begin(), P.hp.end(), np);
+    if (same) return SDD_OK;
+
+    P.hx.assign(x, x + count);
+    P.hy.assign(y, y + count);
+    P.hp.assign(np, np + count);
+    P.ppt_req = ppt_req;
+    P.block_req = block_req;
+    P.exit_mode = exit_mode;
+    P.valid = false;
+
+    int64_t total = 0;
+    for (int64_t k = 0; k < count; ++k) total += np[k];
+    P.block = block_req ? block_req : 256;
+    const int per_sm = path_kernel_blocks_per_sm(exit_mode, record, P.block);
+    P.grid = c->sm_count * per_sm;
+    if (ppt_req) {
+        P.ppt = ppt_req;
+    } else {
+        // about 8 tasks per resident warp, 32..2048 paths per task
+        const int64_t warps = (int64_t)P.grid * (P.block / 32);
+        int64_t q = total / (32LL * 8 * std::max<int64_t>(warps, 1));
+        q = std::min<int64_t>(std::max<int64_t>(q, 1), 64);
+        P.ppt = (int)(32 * q);
+    }
+    P.nodes.resize(count);
+    P.tasks.clear();
+    int64_t rec = 0;
+    for (int64_t k = 0; k < count; ++k) {
+        NodeDev& nd = P.nodes[k];
+        nd.x = x[k];
+        nd.y = y[k];
+        nd.xf = (float)x[k];
+        nd.yf = (float)y[k];
+        nd.inst = 0;
+        nd.ctr = (uint32_t)k;
+        nd.n_paths = (int32_t)np[k];
+        nd.local = (int32_t)k;
+        nd.rec0 = rec;
+        rec += np[k];
+        const bool bnd = x[k] <= 0.0 || x[k] >= 1.0 || y[k] <= 0.0 || y[k] >= 1.0;
+        nd.task0 = (int32_t)P.tasks.size();
+        if (bnd) {
+            nd.ntasks = 0;
+            continue;
+        }
+        for (int64_t p0 = 0; p0 < np[k]; p0 += P.ppt) {
+            Task t{};
+            t.node = (int32_t)k;
+            t.path0 = (int32_t)p0;
+            t.npaths = (int32_t)std::min<int64_t>(P.ppt, np[k] - p0);
+            P.tasks.push_back(t);
+        }
+        nd.ntasks = (int32_t)(P.tasks.size() - nd.task0);
+        if (P.tasks.size() > 0x7fffffffULL) return fail(c, SDD_EINVAL, "too many tasks");
+    }
+    P.nnodes = count;
+    P.ntasks = (int64_t)P.tasks.size();
+    P.total_paths = total;
+    CU(c, P.d_nodes.alloc(std::max<int64_t>(count, 1)));
+    CU(c, P.d_tasks.alloc(std::max<int64_t>(P.ntasks, 1)));
+    CU(c, P.d_partials.alloc(std::max<int64_t>(P.ntasks, 1)));
+    CU(c, P.d_queue.alloc(1));
+    if (count) CU(c, cudaMemcpy(P.d_nodes.p, P.nodes.data(), count * sizeof(NodeDev), cudaMemcpyHostToDevice));
+    if (P.ntasks)
+        CU(c, cudaMemcpy(P.d_tasks.p, P.tasks.data(), P.ntasks * sizeof(Task), cudaMemcpyHostToDevice));
+    P.valid = true;
+    return SDD_OK;
+}
+
+// Enqueue the estimate for a built plan.
+sdd_status run_plan(sdd_ctx* c, Plan& P, double dt, int K, uint64_t seed, uint32_t step_index,
+                    const uint32_t* step_ptr, int exit_mode, const OutDev& out, const RecDev* rec, cudaStream_t s,
+                    cudaEvent_t ev_a = nullptr, cudaEvent_t ev_b = nullptr)
+{
+    if (P.nnodes == 0) return SDD_OK;
+    if (P.ntasks > 0) {
+        PathArgs a{};
+        a.inst = c->d_inst.p;
+        a.nodes = P.d_nodes.p;
+        a.tasks = P.d_tasks.p;
+        a.partials = P.d_partials.p;
+        a.queue = P.d_queue.p;
+        a.ntasks = (int32_t)P.ntasks;
+        a.K = K;
+        a.dt = (float)dt;
+        a.bm_scale = (float)(-4.0 * dt * std::log(2.0));
+        a.bridge_cut = (float)(18.0 * dt);
+        a.key0 = (uint32_t)(seed & 0xffffffffu);
+        a.key1 = (uint32_t)(seed >> 32);
+        a.step_index = step_index;
+        a.step_ptr = step_ptr;
+        if (rec) a.rec = *rec;
+        CU(c, cudaMemsetAsync(P.d_queue.p, 0, sizeof(int), s));
+        const int grid = (int)std::min<int64_t>(P.grid, std::max<int64_t>(1, (P.ntasks * 32 + P.block - 1) / P.block));
+        if (ev_a) CU(c, cudaEventRecord(ev_a, s));
+        CU(c, launch_paths(a, exit_mode, rec != nullptr, grid, P.block, s));
+        if (ev_b) CU(c, cudaEventRecord(ev_b, s));
+    }
+    FinalArgs f{};
+    f.inst = c->d_inst.p;
+    f.nodes = P.d_nodes.p;
+    f.partials = P.d_partials.p;
+    f.out_table = nullptr;
+    f.out0 = out;
+    f.nnodes = (int32_t)P.nnodes;
+    CU(c, launch_finalize(f, s));
+    return SDD_OK;
+}
+
+sdd_status setup_solver(sdd_ctx* c)
+{
+    const size_t N = (size_t)c->nx * c->ny;
+    CU(c, c->cx.alloc(N));
+    CU(c, c->cy.alloc(N));
+    CU(c, c->dg.alloc(N));
+    CU(c, c->rhs0.alloc(2 * N));
+    for (int f = 0; f < 2; ++f) {
+        CU(c, c->r[f].alloc(N));
+        CU(c, c->p[f].alloc(N));
+        CU(c, c->q[f].alloc(N));
+    }
+    const std::vector<int> xs = block_edges(c->nx, c->sub_x), ys = block_edges(c->ny, c->sub_y);
+    c->systems.clear();
+    for (int field = 0; field < 2; ++field)
+        for (int b = 0; b < c->sub_y; ++b)
+            for (int a = 0; a < c->sub_x; ++a) {
+                SolveSys S{};
+                S.i0 = xs[a] + 1;
+                S.i1 = xs[a + 1];
+                S.j0 = ys[b] + 1;
+                S.j1 = ys[b + 1];
+                S.field = field;
+                if (S.i1 > S.i0 && S.j1 > S.j0) c->systems.push_back(S);
+            }
+    CU(c, c->d_systems.alloc(std::max<size_t>(c->systems.size(), 1)));
+    if (!c->systems.empty())
+        CU(c, cudaMemcpy(c->d_systems.p, c->systems.data(), c->systems.size() * sizeof(SolveSys),
+                         cudaMemcpyHostToDevice));
+    CU(c, c->d_iters.alloc(std::max<size_t>(c->systems.size(), 1)));
+    return SDD_OK;
+}
+
+void build_interface(sdd_ctx* c)
+{
+    const std::vector<int> vi = interface_lines(c->nx, c->sub_x), hj = interface_lines(c->ny, c->sub_y);
+    c->iface_x.clear();
+    c->iface_y.clear();
+    c->iface_idx.clear();
+    for (int I : vi)
+        for (int j = 1; j < c->ny - 1; ++j) {
+            c->iface_x.push_back((double)I / (c->nx - 1));
+            c->iface_y.push_back((double)j / (c->ny - 1));
+            c->iface_idx.push_back(j * c->nx + I);
+        }
+    for (int J : hj)
+        for (int i = 1; i < c->nx - 1; ++i) {
+            bool on_v = false;
+            for (int I : vi) on_v |= (I == i);
+            if (on_v) continue;
+            c->iface_x.push_back((double)i / (c->nx - 1));
+            c->iface_y.push_back((double)J / (c->ny - 1));
+            c->iface_idx.push_back(J * c->nx + i);
+        }
+}
+
+// The implicit subdomain step on stream s: Dirichlet data from the faces and the
+// interface values, then the batched PCG. xo/eo receive the new fields.
+sdd_status enqueue_solve(sdd_ctx* c, double Dt, const double* ix, const double* ie, double rtol, int max_iter,
+                         double* xo, double* eo, cudaStream_t s)
+{
+    const double* px = c->fld[c->cur][0].p;
+    const double* pe = c->fld[c->cur][1].p;
+    CU(c, launch_solve_setup(c->w.p, px, pe, c->nx, c->ny, Dt, c->cx.p, c->cy.p, c->dg.p, c->rhs0.p, s));
+    CU(c, launch_dirichlet(c->faces64.p, px, pe, ix, ie, c->d_iface_idx.p, (int)c->iface_idx.size(), c->nx, c->ny,
+                           xo, eo, s));
+    SolveArgs a{};
+    a.nx = c->nx;
+    a.ny = c->ny;
+    a.cx = c->cx.p;
+    a.cy = c->cy.p;
+    a.dg = c->dg.p;
+    a.rhs0 = c->rhs0.p;
+    a.x[0] = xo;
+    a.x[1] = eo;
+    for (int f = 0; f < 2; ++f) {
+        a.r[f] = c->r[f].p;
+        a.p[f] = c->p[f].p;
+        a.q[f] = c->q[f].p;
+    }
+    a.sys = c->d_systems.p;
+    a.nsys = (int32_t)c->systems.size();
+    a.max_iter = max_iter;
+    a.rtol = rtol;
+    a.iters = c->d_iters.p;
+    a.status = c->d_status.p;
+    CU(c, launch_pcg(a, s));
+    return SDD_OK;
+}
+
+OutDev out_from(const sdd_node_stats* o)
+{
+    OutDev d{};
+    if (o) {
+        d.mean_xi = o->mean_xi;
+        d.mean_eta = o->mean_eta;
+        d.se_xi = o->se_xi;
+        d.se_eta = o->se_eta;
+        d.n_exit = (long long*)o->n_exit;
+        d.path_steps = (long long*)o->path_steps;
+    }
+    return d;
+}
+
+}  // namespace
+
+extern "C" {
+
+sdd_status sdd_init(sdd_ctx** out, const sdd_grid* g, const float* w, const double* xi0, const double* eta0,
+                    void* stream)
+{
+    if (!out || !g) return SDD_EINVAL;
+    *out = nullptr;
+    if (g->nx < 3 || g->ny < 3 || g->nx > 32768 || g->ny > 32768) return SDD_EINVAL;
+    if (g->sub_x < 1 || g->sub_y < 1 || g->sub_x > g->nx - 1 || g->sub_y > g->ny - 1) return SDD_EINVAL;
+    if ((long long)g->nx * g->ny > (1LL << 30)) return SDD_EINVAL;
+    sdd_ctx* c = new (std::nothrow) sdd_ctx();
+    if (!c) return SDD_ENOMEM;
+    c->nx = g->nx;
+    c->ny = g->ny;
+    c->sub_x = g->sub_x;
+    c->sub_y = g->sub_y;
+    c->stream = (cudaStream_t)stream;
+    sdd_status st = SDD_OK;
+    auto bail = [&](sdd_status s) {
+        sdd_destroy(c);
+        return s;
+    };
+#define INIT_CU(expr)                                                             \
+    do {                                                                          \
+        cudaError_t e_ = (expr);                                                  \
+        if (e_ != cudaSuccess)                                                    \
+            return bail(e_ == cudaErrorMemoryAllocation ? SDD_ENOMEM : SDD_ECUDA); \
+    } while (0)
+    INIT_CU(cudaGetDevice(&c->device));
+    INIT_CU(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
+    INIT_CU(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    for (int k = 0; k < 5; ++k) INIT_CU(cudaEventCreate(&c->ev[k]));
+    const size_t N = (size_t)c->nx * c->ny;
+    const size_t cells = (size_t)(c->nx - 1) * (c->ny - 1);
+    INIT_CU(c->w.alloc(N));
+    for (int b = 0; b < 2; ++b)
+        for (int f = 0; f < 2; ++f) INIT_CU(c->fld[b][f].alloc(N));
+    INIT_CU(c->faces64.alloc(faces_len(c)));
+    INIT_CU(c->faces32.alloc(faces_len(c)));
+    INIT_CU(c->bcoef.alloc(2 * cells));
+    INIT_CU(c->fcoef.alloc(2 * cells));
+    INIT_CU(c->d_status.alloc(1));
+    INIT_CU(c->d_step.alloc(1));
+    INIT_CU(cudaMemset(c->d_status.p, 0, sizeof(int)));
+    INIT_CU(cudaMemset(c->d_step.p, 0, sizeof(uint32_t)));
+    // inputs (defaults: w = 1, xi = x, eta = y)
+    {
+        std::vector<float> hw;
+        std::vector<double> hx, hy;
+        if (!w) hw.assign(N, 1.0f);
+        if (!xi0 || !eta0) {
+            hx.resize(N);
+            hy.resize(N);
+            for (int j = 0; j < c->ny; ++j)
+                for (int i = 0; i < c->nx; ++i) {
+                    hx[(size_t)j * c->nx + i] = (double)i / (c->nx - 1);
+                    hy[(size_t)j * c->nx + i] = (double)j / (c->ny - 1);
+                }
+        }
+        INIT_CU(cudaMemcpy(c->w.p, w ? (const void*)w : (const void*)hw.data(), N * sizeof(float),
+                           w ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+        INIT_CU(cudaMemcpy(c->fld[0][0].p, xi0 ? (const void*)xi0 : (const void*)hx.data(), N * sizeof(double),
+                           xi0 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+        INIT_CU(cudaMemcpy(c->fld[0][1].p, eta0 ? (const void*)eta0 : (const void*)hy.data(), N * sizeof(double),
+                           eta0 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+    }
+    if ((st = upload_inst(c)) != SDD_OK) return bail(st);
+    if ((st = setup_solver(c)) != SDD_OK) return bail(st);
+    build_interface(c);
+    INIT_CU(c->d_iface_idx.alloc(std::max<size_t>(c->iface_idx.size(), 1)));
+    if (!c->iface_idx.empty())
+        INIT_CU(cudaMemcpy(c->d_iface_idx.p, c->iface_idx.data(), c->iface_idx.size() * sizeof(int32_t),
+                           cudaMemcpyHostToDevice));
+    for (int k = 0; k < 4; ++k) INIT_CU(c->iface_stats[k].alloc(std::max<size_t>(c->iface_idx.size(), 1)));
+    for (int k = 0; k < 2; ++k) INIT_CU(c->iface_counts[k].alloc(std::max<size_t>(c->iface_idx.size(), 1)));
+    c->dirty_w = c->dirty_fields = true;
+    if ((st = prepare(c, c->stream)) != SDD_OK) return bail(st);
+    INIT_CU(cudaStreamSynchronize(c->stream));
+#undef INIT_CU
+    *out = c;
+    return SDD_OK;
+}
+
+static void drop_graphs(sdd_ctx* c)
+{
+    c->graph[0].release();
+    c->graph[1].release();
+    c->graph_ok = false;
+}
+
+sdd_status sdd_set_w(sdd_ctx* c, const float* w)
+{
+    if (!c || !w) return fail(c, SDD_EINVAL, "null argument");
+    CU(c, cudaMemcpyAsync(c->w.p, w, (size_t)c->nx * c->ny * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    c->dirty_w = true;
+    return SDD_OK;
+}
+
+sdd_status sdd_set_w_host(sdd_ctx* c, const float* w)
+{
+    if (!c || !w) return fail(c, SDD_EINVAL, "null argument");
+    CU(c, cudaMemcpyAsync(c->w.p, w, (size_t)c->nx * c->ny * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    c->dirty_w = true;
+    return SDD_OK;
+}
+
+sdd_status sdd_set_fields(sdd_ctx* c, const double* xi, const double* eta)
+{
+    if (!c || !xi || !eta) return fail(c, SDD_EINVAL, "null argument");
+    const size_t bytes = (size_t)c->nx * c->ny * sizeof(double);
+    CU(c, cudaMemcpyAsync(c->fld[c->cur][0].p, xi, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    CU(c, cudaMemcpyAsync(c->fld[c->cur][1].p, eta, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    c->dirty_fields = true;
+    return SDD_OK;
+}
+
+sdd_status sdd_set_boundary(sdd_ctx* c, const double* faces)
+{
+    if (!c) return SDD_EINVAL;
+    if (faces) {
+        CU(c, cudaMemcpyAsync(c->faces64.p, faces, faces_len(c) * sizeof(double), cudaMemcpyDeviceToDevice,
+                              c->stream));
+        CU(c, launch_faces32(c->faces64.p, c->faces32.p, (int)faces_len(c), c->stream));
+        c->user_faces = true;
+    } else {
+        c->user_faces = false;
+        c->dirty_w = true;  // recompute the paper's data from w
+    }
+    drop_graphs(c);
+    return SDD_OK;
+}
+
+sdd_status sdd_get_faces(sdd_ctx* c, double* faces)
+{
+    if (!c || !faces) return fail(c, SDD_EINVAL, "null argument");
+    sdd_status st = prepare(c, c->stream);
+    if (st != SDD_OK) return st;
+    CU(c, cudaMemcpyAsync(faces, c->faces64.p, faces_len(c) * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    return SDD_OK;
+}
+
+sdd_status sdd_get_fields(sdd_ctx* c, double* xi, double* eta)
+{
+    if (!c || !xi || !eta) return fail(c, SDD_EINVAL, "null argument");
+    const size_t bytes = (size_t)c->nx * c->ny * sizeof(double);
+    CU(c, cudaMemcpyAsync(xi, c->fld[c->cur][0].p, bytes, cudaMemcpyDefault, c->stream));
+    CU(c, cudaMemcpyAsync(eta, c->fld[c->cur][1].p, bytes, cudaMemcpyDefault, c->stream));
+    return SDD_OK;
+}
+
+sdd_status sdd_get_fields_host(sdd_ctx* c, double* xi, double* eta)
+{
+    sdd_status st = sdd_get_fields(c, xi, eta);
+    if (st != SDD_OK) return st;
+    CU(c, cudaStreamSynchronize(c->stream));
+    return SDD_OK;
+}
+
+static sdd_status mc_common(sdd_ctx* c, const sdd_nodes* nodes, const sdd_mc_params* p, sdd_node_stats* out,
+                            const sdd_path_records* rec)
+{
+    if (!c || !nodes || !p) return fail(c, SDD_EINVAL, "null argument");
+    if (nodes->count > 0 && (!nodes->x || !nodes->y || !nodes->n_paths)) return fail(c, SDD_EINVAL, "null node array");
+    int K = 0;
+    if (!valid_params(c, p->dt, p->Dt, p->exit_mode, &K))
+        return fail(c, SDD_EINVAL, "dt, Dt or exit_mode rejected (Dt / dt must be an integer in [1, 2^20])");
+    sdd_status st = build_plan(c, c->mc_plan, nodes->x, nodes->y, nodes->n_paths, nodes->count, p->paths_per_task,
+                               p->block_threads, p->exit_mode, rec != nullptr);
+    if (st != SDD_OK) return st;
+    if ((st = prepare(c, c->stream)) != SDD_OK) return st;
+    RecDev rd{};
+    if (rec) {
+        rd.steps = rec->steps;
+        rd.code = rec->code;
+        rd.score_xi = rec->score_xi;
+        rd.score_eta = rec->score_eta;
+        rd.x_end = rec->x_end;
+        rd.y_end = rec->y_end;
+    }
+    return run_plan(c, c->mc_plan, p->dt, K, p->seed, p->step_index, nullptr, p->exit_mode, out_from(out),
+                    rec ? &rd : nullptr, c->stream);
+}
+
+sdd_status sdd_interface_mc(sdd_ctx* c, const sdd_nodes* nodes, const sdd_mc_params* p, sdd_node_stats* out)
+{
+    return mc_common(c, nodes, p, out, nullptr);
+}
+
+sdd_status sdd_interface_mc_record(sdd_ctx* c, const sdd_nodes* nodes, const sdd_mc_params* p, sdd_node_stats* out,
+                                   const sdd_path_records* rec)
+{
+    if (!rec) return fail(c, SDD_EINVAL, "null records");
+    return mc_common(c, nodes, p, out, rec);
+}
+
+sdd_status sdd_interface_nodes(sdd_ctx* c, double* x, double* y, int64_t* count)
+{
+    if (!c || !count) return fail(c, SDD_EINVAL, "null argument");
+    *count = (int64_t)c->iface_x.size();
+    if (x) std::memcpy(x, c->iface_x.data(), c->iface_x.size() * sizeof(double));
+    if (y) std::memcpy(y, c->iface_y.data(), c->iface_y.size() * sizeof(double));
+    return SDD_OK;
+}
+
+sdd_status sdd_subdomain_solve(sdd_ctx* c, double Dt, const double* iface_xi, const double* iface_eta, double rtol,
+                               int32_t max_iter, double* xi_out, double* eta_out, int32_t* iters_out)
+{
+    if (!c || !xi_out || !eta_out) return fail(c, SDD_EINVAL, "null argument");
+    if (!c->iface_idx.empty() && (!iface_xi || !iface_eta)) return fail(c, SDD_EINVAL, "null interface values");
+    if (!(Dt > 0.0) || !(rtol >= 0.0) || max_iter < 0) return fail(c, SDD_EINVAL, "Dt, rtol or max_iter rejected");
+    sdd_status st = prepare(c, c->stream);
+    if (st != SDD_OK) return st;
+    if ((st = enqueue_solve(c, Dt, iface_xi, iface_eta, rtol, max_iter, xi_out, eta_out, c->stream)) != SDD_OK)
+        return st;
+    if (iters_out) {
+        std::vector<int32_t> it(std::max<size_t>(c->systems.size(), 1), 0);
+        CU(c, cudaMemcpyAsync(it.data(), c->d_iters.p, c->systems.size() * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                              c->stream));
+        CU(c, cudaStreamSynchronize(c->stream));
+        int32_t mx = 0;
+        for (size_t k = 0; k < c->systems.size(); ++k) mx = std::max(mx, it[k]);
+        *iters_out = mx;
+        if (mx > max_iter) return fail(c, SDD_ENOCONV, "subdomain solve did not reach rtol in max_iter iterations");
+    }
+    return SDD_OK;
+}
+
+// Record one mesh step into a graph on the capture stream: field tables, the
+// interface estimate, the Dirichlet data, the PCG and the step counter.
+static sdd_status capture_step(sdd_ctx* c, const sdd_step_params* p, int K, int parity)
+{
+    cudaStream_t s = c->cap_stream;
+    cudaGraph_t g = nullptr;
+    CU(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    // the graph always recomputes the tables: w and the fields change every step
+    const bool keep_w = c->dirty_w, keep_f = c->dirty_fields;
+    c->dirty_w = true;
+    c->dirty_fields = true;
+    const int saved = c->cur;
+    c->cur = parity;
+    sdd_status st = SDD_OK;
+    {
+        cudaError_t e0 = cudaEventRecord(c->ev[0], s);
+        if (e0 != cudaSuccess) st = fail(c, SDD_ECUDA, "event: %s", cudaGetErrorString(e0));
+    }
+    if (st == SDD_OK) st = prepare(c, s);
+    OutDev o{};
+    o.mean_xi = c->iface_stats[0].p;
+    o.mean_eta = c->iface_stats[1].p;
+    o.se_xi = c->iface_stats[2].p;
+    o.se_eta = c->iface_stats[3].p;
+    o.n_exit = c->iface_counts[0].p;
+    o.path_steps = c->iface_counts[1].p;
+    if (st == SDD_OK)
+        st = run_plan(c, c->step_plan, p->dt, K, p->seed, 0, c->d_step.p, p->exit_mode, o, nullptr, s, c->ev[1],
+                      c->ev[2]);
+    if (st == SDD_OK) {
+        cudaError_t e = cudaEventRecord(c->ev[3], s);
+        if (e != cudaSuccess) st = fail(c, SDD_ECUDA, "event: %s", cudaGetErrorString(e));
+    }
+    if (st == SDD_OK)
+        st = enqueue_solve(c, p->Dt, o.mean_xi, o.mean_eta, p->rtol, p->max_iter, c->fld[1 - parity][0].p,
+                           c->fld[1 - parity][1].p, s);
+    if (st == SDD_OK) {
+        cudaError_t e = launch_bump_step(c->d_step.p, s);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev[4], s);
+        if (e != cudaSuccess) st = fail(c, SDD_ECUDA, "%s", cudaGetErrorString(e));
+    }
+    c->cur = saved;
+    c->dirty_w = keep_w;
+    c->dirty_fields = keep_f;
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (st != SDD_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return fail(c, SDD_ECUDA, "capture: %s", cudaGetErrorString(e));
+    c->graph[parity].release();
+    {
+        size_t nn = 0;
+        if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+            std::vector<cudaGraphNode_t> nodes(nn);
+            int kernels = 0;
+            if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+                for (size_t k = 0; k < nn; ++k) {
+                    cudaGraphNodeType t;
+                    if (cudaGraphNodeGetType(nodes[k], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+                }
+            c->graph_kernels = kernels;
+        }
+    }
+    e = cudaGraphInstantiate(&c->graph[parity].exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->graph[parity].exec = nullptr;
+        return fail(c, SDD_ECUDA, "instantiate: %s", cudaGetErrorString(e));
+    }
+    return SDD_OK;
+}
+
+sdd_status sdd_step(sdd_ctx* c, const sdd_step_params* p)
+{
+    if (!c || !p) return fail(c, SDD_EINVAL, "null argument");
+    int K = 0;
+    if (!valid_params(c, p->dt, p->Dt, p->exit_mode, &K)) return fail(c, SDD_EINVAL, "dt, Dt or exit_mode rejected");
+    if (p->paths_per_node < 1 || p->paths_per_node > 0x7fffffffLL || p->max_iter < 0 || !(p->rtol >= 0.0))
+        return fail(c, SDD_EINVAL, "paths_per_node, max_iter or rtol rejected");
+    const bool same = c->graph_ok && std::memcmp(&c->graph_params, p, sizeof *p) == 0;
+    if (!same) {
+        drop_graphs(c);
+        std::vector<int64_t> np(c->iface_x.size(), p->paths_per_node);
+        sdd_status st = build_plan(c, c->step_plan, c->iface_x.data(), c->iface_y.data(), np.data(),
+                                   (int64_t)np.size(), 0, 0, p->exit_mode, false);
+        if (st != SDD_OK) return st;
+        CU(c, cudaStreamSynchronize(c->stream));
+        for (int parity = 0; parity < 2; ++parity)
+            if ((st = capture_step(c, p, K, parity)) != SDD_OK) return st;
+        c->graph_params = *p;
+        c->graph_ok = true;
+    }
+    // the step counter lives on the device; make sure it holds n
+    CU(c, cudaMemcpyAsync(c->d_step.p, &c->step_index, sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream));
+    CU(c, cudaGraphLaunch(c->graph[c->cur].exec, c->stream));
+    c->cur = 1 - c->cur;
+    c->step_index += 1;
+    c->dirty_w = false;
+    c->dirty_fields = true;  // the new fields need their tables before a direct estimate
+    return SDD_OK;
+}
+
+sdd_status sdd_last_interface_stats(sdd_ctx* c, sdd_node_stats* out)
+{
+    if (!c || !out) return fail(c, SDD_EINVAL, "null argument");
+    const size_t n = c->iface_idx.size();
+    double* dst[4] = {out->mean_xi, out->mean_eta, out->se_xi, out->se_eta};
+    for (int k = 0; k < 4; ++k)
+        if (dst[k] && n) CU(c, cudaMemcpyAsync(dst[k], c->iface_stats[k].p, n * sizeof(double), cudaMemcpyDefault, c->stream));
+    int64_t* ci[2] = {out->n_exit, out->path_steps};
+    for (int k = 0; k < 2; ++k)
+        if (ci[k] && n) CU(c, cudaMemcpyAsync(ci[k], c->iface_counts[k].p, n * sizeof(int64_t), cudaMemcpyDefault, c->stream));
+    return SDD_OK;
+}
+
+sdd_status sdd_last_step_info(sdd_ctx* c, sdd_step_info* out)
+{
+    if (!c || !out) return fail(c, SDD_EINVAL, "null argument");
+    if (!c->graph_ok) return fail(c, SDD_EINVAL, "no step has run");
+    CU(c, cudaStreamSynchronize(c->stream));
+    out->kernel_nodes = c->graph_kernels;
+    CU(c, cudaEventElapsedTime(&out->paths_ms, c->ev[1], c->ev[2]));
+    CU(c, cudaEventElapsedTime(&out->estimate_ms, c->ev[0], c->ev[3]));
+    CU(c, cudaEventElapsedTime(&out->solve_ms, c->ev[3], c->ev[4]));
+    CU(c, cudaEventElapsedTime(&out->step_ms, c->ev[0], c->ev[4]));
+    return SDD_OK;
+}
+
+sdd_status sdd_set_step_index(sdd_ctx* c, uint32_t n)
+{
+    if (!c) return SDD_EINVAL;
+    c->step_index = n;
+    return SDD_OK;
+}
+
+uint32_t sdd_get_step_index(const sdd_ctx* c) { return c ? c->step_index : 0u; }
+
+sdd_status sdd_sync(sdd_ctx* c)
+{
+    if (!c) return SDD_EINVAL;
+    CU(c, cudaStreamSynchronize(c->stream));
+    int status = 0;
+    CU(c, cudaMemcpy(&status, c->d_status.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status) {
+        CU(c, cudaMemset(c->d_status.p, 0, sizeof(int)));
+        if (status & STATUS_BAD_W) return fail(c, SDD_EDEVICE, "w has a value that is not finite and positive");
+        if (status & STATUS_TIMEOUT) return fail(c, SDD_ETIMEOUT, "a bounded device wait ran out");
+        if (status & STATUS_NOCONV) return fail(c, SDD_ENOCONV, "a subdomain solve stopped at max_iter");
+    }
+    return SDD_OK;
+}
+
+const char* sdd_last_error(const sdd_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void sdd_destroy(sdd_ctx* c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
+    for (int k = 0; k < 5; ++k)
+        if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;  // device buffers are freed by their destructors
+}
+
+sdd_status sdd_rng_draw(uint64_t seed, uint32_t instance, const uint32_t* ctrs, int64_t count, uint32_t* words,
+                        float* normals, void* stream)
+{
+    if (count < 0 || (count > 0 && (!ctrs || !words))) return SDD_EINVAL;
+    cudaError_t e = launch_rng_draw(seed, instance, ctrs, count, words, normals, (cudaStream_t)stream);
+    return e == cudaSuccess ? SDD_OK : SDD_ECUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,151 @@
+// common.cuh -- device-side data layout shared by the kernels of libsdd.
+//
+// One "instance" is one mesh problem (grid, w, xi, eta, face data). A single
+// context is one instance; a batched launch runs many. Work is cut into tasks
+// (a node and a contiguous range of its paths); persistent warps take tasks
+// from a counter in device memory.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sdd {
+
+// Geometry and field tables of one instance, as the path kernel reads them.
+struct InstDev {
+    const float4* bcoef;   // 2 float4 per cell: bilinear coefficients of b_x, then b_y
+    const float4* fcoef;   // 2 float4 per cell: bilinear coefficients of xi, then eta
+    const float* faces32;  // face data, single precision (layout of sdd.h)
+    const double* faces64; // face data, double precision
+    int32_t nx, ny;
+    float sx, sy;          // nx - 1, ny - 1 (inverse spacings)
+    float gxmax, gymax;    // largest floats below nx - 1, ny - 1
+    int32_t pad0, pad1;
+};
+
+// Output arrays of one instance (device pointers; any may be null).
+struct OutDev {
+    double* mean_xi;
+    double* mean_eta;
+    double* se_xi;
+    double* se_eta;
+    long long* n_exit;
+    long long* path_steps;
+};
+
+// One evaluation node.
+struct NodeDev {
+    double x, y;        // as given
+    float xf, yf;       // start point of the paths (single precision)
+    int32_t inst;       // instance index (also xored into the Philox key)
+    uint32_t ctr;       // node word of the Philox counter
+    int32_t n_paths;
+    int32_t task0;      // first task of this node
+    int32_t ntasks;     // 0 for a node on the boundary
+    int32_t local;      // index into the instance's output arrays
+    long long rec0;     // first per-path record of this node
+};
+
+struct Task {
+    int32_t node;
+    int32_t path0;
+    int32_t npaths;
+    int32_t pad;
+};
+
+// Per-task sums, shifted by the node's start coordinates (xi by x, eta by y):
+// s = sum (Y - c), q = sum (Y - c)^2.
+struct Partial {
+    double s_xi, q_xi, s_eta, q_eta;
+    long long exits, steps;
+};
+
+struct RecDev {
+    int32_t* steps;
+    int32_t* code;
+    float* score_xi;
+    float* score_eta;
+    float* x_end;
+    float* y_end;
+};
+
+struct PathArgs {
+    const InstDev* inst;
+    const NodeDev* nodes;
+    const Task* tasks;
+    Partial* partials;
+    int* queue;              // next task (zeroed before the launch)
+    int32_t ntasks;
+    int32_t K;               // sub-steps per mesh step
+    float dt;
+    float bm_scale;          // -4 dt ln 2: r = sqrt(bm_scale * log2(u1)) = sqrt(2 dt) sqrt(-2 ln u1)
+    float bridge_cut;        // skip the bridge test when dmin0 * dmin1 exceeds this
+    uint32_t key0, key1;     // seed halves
+    uint32_t step_index;
+    const uint32_t* step_ptr; // if non-null, read the step index here
+    RecDev rec;
+};
+
+struct FinalArgs {
+    const InstDev* inst;
+    const NodeDev* nodes;
+    const Partial* partials;
+    const OutDev* out_table;  // per instance; if null every node writes to out0
+    OutDev out0;
+    int32_t nnodes;
+};
+
+// Device status word bits.
+enum : int {
+    STATUS_BAD_W = 1,
+    STATUS_NOCONV = 2,
+    STATUS_TIMEOUT = 4,
+};
+
+// Launchers (defined in the .cu files; all asynchronous on `s`).
+cudaError_t launch_paths(const PathArgs& a, int exit_mode, bool record, int grid, int block, cudaStream_t s);
+cudaError_t launch_finalize(const FinalArgs& a, cudaStream_t s);
+int path_kernel_blocks_per_sm(int exit_mode, bool record, int block);
+
+cudaError_t launch_prep_cells(const float* w, const double* xi, const double* eta, int nx, int ny, float4* bcoef,
+                              float4* fcoef, int* status, cudaStream_t s);
+cudaError_t launch_winslow_faces(const float* w, int nx, int ny, double* faces64, cudaStream_t s);
+cudaError_t launch_faces32(const double* faces64, float* faces32, int n, cudaStream_t s);
+
+cudaError_t launch_rng_draw(uint64_t seed, uint32_t instance, const uint32_t* ctrs, long long count,
+                            uint32_t* words, float* normals, cudaStream_t s);
+
+// Subdomain solve.
+struct SolveSys {
+    int32_t i0, i1, j0, j1;   // unknown block [i0, i1) x [j0, j1)
+    int32_t field;            // 0 xi, 1 eta
+    int32_t pad;
+};
+
+struct SolveArgs {
+    int32_t nx, ny;
+    const double* cx;        // face coefficient between (i, j) and (i + 1, j)
+    const double* cy;        // face coefficient between (i, j) and (i, j + 1)
+    const double* dg;        // diagonal
+    const double* rhs0;      // 2 fields: prev / (w Dt)
+    double* x[2];            // solution fields (full grid, Dirichlet entries set)
+    double* r[2];
+    double* p[2];
+    double* q[2];
+    const SolveSys* sys;
+    int32_t nsys;
+    int32_t max_iter;
+    double rtol;
+    int32_t* iters;          // per system
+    int* status;
+};
+
+cudaError_t launch_solve_setup(const float* w, const double* prev_xi, const double* prev_eta, int nx, int ny,
+                               double Dt, double* cx, double* cy, double* dg, double* rhs0, cudaStream_t s);
+cudaError_t launch_dirichlet(const double* faces64, const double* prev_xi, const double* prev_eta,
+                             const double* iface_xi, const double* iface_eta, const int32_t* iface_idx,
+                             int n_iface, int nx, int ny, double* xi_out, double* eta_out, cudaStream_t s);
+cudaError_t launch_pcg(const SolveArgs& a, cudaStream_t s);
+cudaError_t launch_bump_step(uint32_t* step, cudaStream_t s);
+
+}  // namespace sdd

@@ -1,0 +1,163 @@
+// fields.cu -- per-mesh-step field preparation (the path kernel's tables).
+//
+//  * drift b = -grad w / w at the grid nodes by finite differences (Eq. 6;
+//    Sec. 4 "derivatives ... approximated using finite differences"):
+//    second-order central differences inside, second-order one-sided
+//    differences (-3 w0 + 4 w1 - w2) / 2h on the edges, in double precision;
+//  * per cell, the bilinear interpolant of b and of (xi, eta) written as
+//    a0 + a1 s + a2 t + a3 s t over the cell's local coordinates (s, t), with
+//    a0 = f00, a1 = f10 - f00, a2 = f01 - f00, a3 = f11 - f10 - f01 + f00,
+//    formed in double and stored in single precision (Sec. 4: bilinear
+//    interpolation between grid points);
+//  * the boundary data of Sec. 3: xi = 0 / 1 on x = 0 / 1, eta = 0 / 1 on
+//    y = 0 / 1, and on the other faces the 1D Winslow solution
+//    int_0^s w / int_0^1 w (cumulative trapezoid, double precision).
+#include "common.cuh"
+
+namespace sdd {
+
+namespace {
+
+__device__ __forceinline__ double2 node_drift(const float* __restrict__ w, int nx, int ny, int i, int j,
+                                              double rx, double ry)
+{
+    // rx = 1 / (2 hx) = (nx - 1) / 2, ry likewise
+    const float* row = w + (long long)j * nx;
+    double wx, wy;
+    if (i == 0)
+        wx = (-3.0 * (double)row[0] + 4.0 * (double)row[1] - (double)row[2]) * rx;
+    else if (i == nx - 1)
+        wx = (3.0 * (double)row[nx - 1] - 4.0 * (double)row[nx - 2] + (double)row[nx - 3]) * rx;
+    else
+        wx = ((double)row[i + 1] - (double)row[i - 1]) * rx;
+    const float* col = w + i;
+    if (j == 0)
+        wy = (-3.0 * (double)col[0] + 4.0 * (double)col[(long long)nx] - (double)col[2LL * nx]) * ry;
+    else if (j == ny - 1)
+        wy = (3.0 * (double)col[(long long)(ny - 1) * nx] - 4.0 * (double)col[(long long)(ny - 2) * nx] +
+              (double)col[(long long)(ny - 3) * nx]) * ry;
+    else
+        wy = ((double)col[(long long)(j + 1) * nx] - (double)col[(long long)(j - 1) * nx]) * ry;
+    const double wc = (double)row[i];
+    return make_double2(-wx / wc, -wy / wc);
+}
+
+__device__ __forceinline__ float4 bilinear_coefs(double f00, double f10, double f01, double f11)
+{
+    return make_float4((float)f00, (float)(f10 - f00), (float)(f01 - f00), (float)((f11 - f10) - (f01 - f00)));
+}
+
+__device__ __forceinline__ bool bad_w(float v) { return !(v > 0.0f) || !isfinite(v); }
+
+__global__ void k_prep_cells(const float* __restrict__ w, const double* __restrict__ xi,
+                             const double* __restrict__ eta, int nx, int ny, float4* __restrict__ bcoef,
+                             float4* __restrict__ fcoef, int* status)
+{
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int iy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (ix >= nx - 1 || iy >= ny - 1) return;
+    // every node is checked by the cell that has it as lower-left corner,
+    // the last row and column by the cells next to them
+    bool bad = bad_w(w[(long long)iy * nx + ix]);
+    if (ix == nx - 2) bad |= bad_w(w[(long long)iy * nx + ix + 1]);
+    if (iy == ny - 2) bad |= bad_w(w[(long long)(iy + 1) * nx + ix]);
+    if (ix == nx - 2 && iy == ny - 2) bad |= bad_w(w[(long long)(iy + 1) * nx + ix + 1]);
+    if (bad) atomicOr(status, STATUS_BAD_W);
+
+    const double rx = 0.5 * (double)(nx - 1), ry = 0.5 * (double)(ny - 1);
+    const double2 b00 = node_drift(w, nx, ny, ix, iy, rx, ry);
+    const double2 b10 = node_drift(w, nx, ny, ix + 1, iy, rx, ry);
+    const double2 b01 = node_drift(w, nx, ny, ix, iy + 1, rx, ry);
+    const double2 b11 = node_drift(w, nx, ny, ix + 1, iy + 1, rx, ry);
+    const long long cell = (long long)iy * (nx - 1) + ix;
+    bcoef[2 * cell + 0] = bilinear_coefs(b00.x, b10.x, b01.x, b11.x);
+    bcoef[2 * cell + 1] = bilinear_coefs(b00.y, b10.y, b01.y, b11.y);
+    const long long n00 = (long long)iy * nx + ix;
+    const long long n01 = n00 + nx;
+    fcoef[2 * cell + 0] = bilinear_coefs(xi[n00], xi[n00 + 1], xi[n01], xi[n01 + 1]);
+    fcoef[2 * cell + 1] = bilinear_coefs(eta[n00], eta[n00 + 1], eta[n01], eta[n01 + 1]);
+}
+
+// Cumulative trapezoid of one line of w, normalised by its total, by one warp:
+// each lane sums a contiguous run of intervals, the run totals are scanned
+// across the warp, then each lane writes its run.
+__device__ void warp_cumtrapz(const float* __restrict__ v, long long stride, int n, double* __restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int intervals = n - 1;
+    const int run = (intervals + 31) / 32;
+    const int k0 = 1 + lane * run;
+    const int k1 = min(k0 + run, n);
+    double mine = 0.0;
+    for (int k = k0; k < k1; ++k) mine += 0.5 * ((double)v[(k - 1) * stride] + (double)v[k * stride]);
+    double incl = mine;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const double o = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += o;
+    }
+    const double total = __shfl_sync(0xffffffffu, incl, 31);
+    double acc = incl - mine;
+    if (lane == 0) out[0] = 0.0;
+    for (int k = k0; k < k1; ++k) {
+        acc += 0.5 * ((double)v[(k - 1) * stride] + (double)v[k * stride]);
+        out[k] = acc / total;
+    }
+}
+
+__global__ void k_winslow_faces(const float* __restrict__ w, int nx, int ny, double* __restrict__ faces)
+{
+    const long long per_field = 2LL * ny + 2LL * nx;
+    double* xl = faces;
+    double* xr = faces + ny;
+    double* xb = faces + 2LL * ny;
+    double* xt = faces + 2LL * ny + nx;
+    double* el = faces + per_field;
+    double* er = faces + per_field + ny;
+    double* eb = faces + per_field + 2LL * ny;
+    double* et = faces + per_field + 2LL * ny + nx;
+    const int warp = threadIdx.x >> 5;
+    if (warp == 0) warp_cumtrapz(w, 1, nx, xb);                                   // xi on y = 0
+    if (warp == 1) warp_cumtrapz(w + (long long)(ny - 1) * nx, 1, nx, xt);        // xi on y = 1
+    if (warp == 2) warp_cumtrapz(w, nx, ny, el);                                  // eta on x = 0
+    if (warp == 3) warp_cumtrapz(w + (nx - 1), nx, ny, er);                       // eta on x = 1
+    for (int k = threadIdx.x; k < ny; k += blockDim.x) {
+        xl[k] = 0.0;
+        xr[k] = 1.0;
+    }
+    for (int k = threadIdx.x; k < nx; k += blockDim.x) {
+        eb[k] = 0.0;
+        et[k] = 1.0;
+    }
+}
+
+__global__ void k_faces32(const double* __restrict__ f64, float* __restrict__ f32, int n)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) f32[k] = (float)f64[k];
+}
+
+}  // namespace
+
+cudaError_t launch_prep_cells(const float* w, const double* xi, const double* eta, int nx, int ny, float4* bcoef,
+                              float4* fcoef, int* status, cudaStream_t s)
+{
+    const dim3 block(32, 8);
+    const dim3 grid((nx - 1 + 31) / 32, (ny - 1 + 7) / 8);
+    k_prep_cells<<<grid, block, 0, s>>>(w, xi, eta, nx, ny, bcoef, fcoef, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_winslow_faces(const float* w, int nx, int ny, double* faces64, cudaStream_t s)
+{
+    k_winslow_faces<<<1, 128, 0, s>>>(w, nx, ny, faces64);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_faces32(const double* faces64, float* faces32, int n, cudaStream_t s)
+{
+    k_faces32<<<(n + 255) / 256, 256, 0, s>>>(faces64, faces32, n);
+    return cudaGetLastError();
+}
+
+}  // namespace sdd

@@ -1,0 +1,476 @@
+// paths.cu -- the interface Monte Carlo path kernel and the per-node reduction.
+//
+// Each path solves dX = -(1/w) grad w dt + sqrt(2) dW (Eq. 7a with the
+// Winslow coefficients of Eq. 6) from its node by Euler--Maruyama over the K
+// sub-steps of one mesh step (Sec. 4), with dW = sqrt(dt) N(0,1), the drift
+// interpolated bilinearly between the grid nodes, and a boundary test after
+// every sub-step. A path that leaves scores the boundary data f, g at its exit
+// point; a path that stays scores xi, eta of the start of the mesh step at its
+// end point (Eq. 7b). The node's estimate is the mean over its paths (Sec. 4).
+//
+// Execution: a persistent grid; each warp repeatedly takes a task (one node,
+// a contiguous range of its paths) from a counter. Each lane runs one path at
+// a time and, when its path ends, takes the task's next unstarted path, so
+// lanes stay busy when paths leave early. In the paper's (plain) exit mode one
+// Philox block supplies the normals of two consecutive sub-steps, so paths are
+// only started at even sub-step boundaries. Scores are summed per lane with
+// compensation (single precision, shifted by the node's start coordinates),
+// then per warp in double precision; the per-node reduction over tasks runs in
+// a fixed order, so results do not depend on scheduling.
+#include "common.cuh"
+#include "rng.cuh"
+
+namespace sdd {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+struct Cell {
+    const float4* p;
+    float s, t;
+};
+
+// Cell of (x, y) and local coordinates. floor() through a directed add of
+// 2^23: for 0 <= g < 2^23, (g + 2^23) rounded down is 2^23 + floor(g) exactly.
+__device__ __forceinline__ Cell locate(const InstDev& I, const float4* base, float x, float y)
+{
+    const float gx = fminf(x * I.sx, I.gxmax);
+    const float gy = fminf(y * I.sy, I.gymax);
+    const float tx = __fadd_rd(gx, 8388608.0f);
+    const float ty = __fadd_rd(gy, 8388608.0f);
+    const int ix = __float_as_int(tx) - 0x4B000000;
+    const int iy = __float_as_int(ty) - 0x4B000000;
+    Cell c;
+    c.s = gx - (tx - 8388608.0f);
+    c.t = gy - (ty - 8388608.0f);
+    c.p = base + 2 * (iy * (I.nx - 1) + ix);
+    return c;
+}
+
+__device__ __forceinline__ float eval(const float4& a, float s, float t)
+{
+    return fmaf(t, fmaf(s, a.w, a.z), fmaf(s, a.y, a.x));
+}
+
+// Linear interpolation of face `face` of `field` at tangential coordinate s.
+__device__ __forceinline__ float face_value(const InstDev& I, int field, int face, float s)
+{
+    const int n = (face < 2) ? I.ny : I.nx;
+    long long off = (long long)field * (2LL * I.ny + 2LL * I.nx);
+    if (face >= 1) off += I.ny;
+    if (face >= 2) off += I.ny;
+    if (face >= 3) off += I.nx;
+    const float* v = I.faces32 + off;
+    const float g = s * (float)(n - 1);
+    int k = (int)floorf(g);
+    k = max(0, min(k, n - 2));
+    const float f = g - (float)k;
+    return fmaf(f, v[k + 1] - v[k], v[k]);
+}
+
+// Exit through the boundary between X_j = (x, y) and X_{j+1} = (xn, yn):
+// the segment is cut at the smallest crossing fraction over the violated
+// faces, ties to the face listed first (left, right, bottom, top).
+__device__ __noinline__ void plain_exit(const InstDev& I, float x, float y, float xn, float yn, int& face,
+                                        float& yxi, float& yeta, float& xe, float& ye)
+{
+    float best = 2.0f;
+    int f = -1;
+    if (xn <= 0.0f) { const float s = x / (x - xn); if (s < best) { best = s; f = 0; } }
+    if (xn >= 1.0f) { const float s = (1.0f - x) / (xn - x); if (s < best) { best = s; f = 1; } }
+    if (yn <= 0.0f) { const float s = y / (y - yn); if (s < best) { best = s; f = 2; } }
+    if (yn >= 1.0f) { const float s = (1.0f - y) / (yn - y); if (s < best) { best = s; f = 3; } }
+    if (f < 0) { f = 0; best = 0.0f; }  // only for a non-finite position
+    float t = (f < 2) ? fmaf(best, yn - y, y) : fmaf(best, xn - x, x);
+    t = fminf(fmaxf(t, 0.0f), 1.0f);
+    face = f;
+    yxi = face_value(I, 0, f, t);
+    yeta = face_value(I, 1, f, t);
+    xe = (f == 0) ? 0.0f : (f == 1) ? 1.0f : t;
+    ye = (f == 2) ? 0.0f : (f == 3) ? 1.0f : t;
+}
+
+// Brownian-bridge test between two inside points: the half plane behind face
+// k is touched with probability exp(-d0 d1 / dt) (sigma^2 = 2); the faces
+// combine as 1 - prod (1 - p_k). On exit: the face of largest p_k, at the
+// projection of the sub-step midpoint.
+__device__ __noinline__ bool bridge_exit(const InstDev& I, float x, float y, float xn, float yn, float dt, float u,
+                                         int& face, float& yxi, float& yeta, float& xe, float& ye)
+{
+    const float d0[4] = {x, 1.0f - x, y, 1.0f - y};
+    const float d1[4] = {xn, 1.0f - xn, yn, 1.0f - yn};
+    const float inv = 1.0f / dt;
+    float stay = 1.0f, pmax = -1.0f;
+    int f = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float p = __expf(-d0[k] * d1[k] * inv);
+        stay *= (1.0f - p);
+        if (p > pmax) { pmax = p; f = k; }
+    }
+    if (!(u < 1.0f - stay)) return false;
+    float t = (f < 2) ? 0.5f * (y + yn) : 0.5f * (x + xn);
+    t = fminf(fmaxf(t, 0.0f), 1.0f);
+    face = f;
+    yxi = face_value(I, 0, f, t);
+    yeta = face_value(I, 1, f, t);
+    xe = (f == 0) ? 0.0f : (f == 1) ? 1.0f : t;
+    ye = (f == 2) ? 0.0f : (f == 3) ? 1.0f : t;
+    return true;
+}
+
+__device__ __forceinline__ bool inside(float x, float y)
+{
+    return x > 0.0f && x < 1.0f && y > 0.0f && y < 1.0f;
+}
+
+// One Euler--Maruyama sub-step with increment (zx, zy) = sqrt(2 dt) N(0,1)^2.
+__device__ __forceinline__ void em_step(const InstDev& I, float x, float y, float dt, float zx, float zy, float& xn,
+                                        float& yn)
+{
+    const Cell c = locate(I, I.bcoef, x, y);
+    const float4 ax = __ldg(c.p);
+    const float4 ay = __ldg(c.p + 1);
+    xn = fmaf(eval(ax, c.s, c.t), dt, x) + zx;
+    yn = fmaf(eval(ay, c.s, c.t), dt, y) + zy;
+}
+
+struct Acc {
+    float s, cs, q, cq;
+    __device__ __forceinline__ void add(float v)
+    {
+        float y1 = v - cs;
+        float t1 = s + y1;
+        cs = (t1 - s) - y1;
+        s = t1;
+        const float v2 = v * v;
+        float y2 = v2 - cq;
+        float t2 = q + y2;
+        cq = (t2 - q) - y2;
+        q = t2;
+    }
+    __device__ __forceinline__ double sum() const { return (double)s - (double)cs; }
+    __device__ __forceinline__ double sumsq() const { return (double)q - (double)cq; }
+};
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+    return v;
+}
+
+__device__ __forceinline__ long long warp_sum_ll(long long v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+    return v;
+}
+
+template <int MODE, bool RECORD>
+__global__ void __launch_bounds__(256) k_paths(const PathArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    const uint32_t step = a.step_ptr ? *a.step_ptr : a.step_index;
+    const int K = a.K;
+    const float dt = a.dt;
+
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(a.queue, 1);
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= a.ntasks) return;
+
+        const Task task = a.tasks[t];
+        const NodeDev& nd = a.nodes[task.node];
+        const InstDev I = a.inst[nd.inst];
+        const float x0 = nd.xf, y0 = nd.yf;
+        const uint32_t nctr = nd.ctr;
+        const uint32_t k0 = a.key0, k1 = a.key1 ^ (uint32_t)nd.inst;
+        const int end = task.path0 + task.npaths;
+        int next = task.path0 + 32;
+        int path = task.path0 + lane;
+        bool alive = path < end;
+        float x = x0, y = y0;
+        int m = 0;  // plain mode: sub-step pair index; bridge mode: sub-step index
+        Acc ax{0.f, 0.f, 0.f, 0.f}, ae{0.f, 0.f, 0.f, 0.f};
+        int exits = 0, steps = 0;
+
+        while (__any_sync(FULL, alive)) {
+            if (alive) {
+                bool done = false;
+                int code = -1, taken = 0;
+                float yxi = 0.f, yeta = 0.f, xe = 0.f, ye = 0.f;
+                const uint4 r = philox4x32_10(make_uint4((uint32_t)path, nctr, (uint32_t)m, step), k0, k1);
+                if (MODE == 0) {
+                    float zx0, zy0, zx1, zy1;
+                    box_muller(r.x, r.y, a.bm_scale, zx0, zy0);
+                    box_muller(r.z, r.w, a.bm_scale, zx1, zy1);
+                    float xn, yn;
+                    em_step(I, x, y, dt, zx0, zy0, xn, yn);
+                    if (!inside(xn, yn)) {
+                        plain_exit(I, x, y, xn, yn, code, yxi, yeta, xe, ye);
+                        done = true;
+                        taken = 2 * m + 1;
+                    } else {
+                        x = xn;
+                        y = yn;
+                        if (2 * m + 1 < K) {
+                            em_step(I, x, y, dt, zx1, zy1, xn, yn);
+                            if (!inside(xn, yn)) {
+                                plain_exit(I, x, y, xn, yn, code, yxi, yeta, xe, ye);
+                                done = true;
+                                taken = 2 * m + 2;
+                            } else {
+                                x = xn;
+                                y = yn;
+                            }
+                        }
+                    }
+                    ++m;
+                    if (!done && 2 * m >= K) {
+                        done = true;
+                        taken = K;
+                    }
+                } else {
+                    float zx, zy;
+                    box_muller(r.x, r.y, a.bm_scale, zx, zy);
+                    float xn, yn;
+                    em_step(I, x, y, dt, zx, zy, xn, yn);
+                    if (!inside(xn, yn)) {
+                        plain_exit(I, x, y, xn, yn, code, yxi, yeta, xe, ye);
+                        done = true;
+                    } else {
+                        const float dm0 = fminf(fminf(x, 1.0f - x), fminf(y, 1.0f - y));
+                        const float dm1 = fminf(fminf(xn, 1.0f - xn), fminf(yn, 1.0f - yn));
+                        if (dm0 * dm1 < a.bridge_cut &&
+                            bridge_exit(I, x, y, xn, yn, dt, uniform_pos(r.z), code, yxi, yeta, xe, ye)) {
+                            code += 4;
+                            done = true;
+                        } else {
+                            x = xn;
+                            y = yn;
+                        }
+                    }
+                    ++m;
+                    taken = m;
+                    if (!done && m >= K) done = true;
+                }
+                if (done) {
+                    if (code < 0) {
+                        // survived the mesh step: xi, eta of its start at the end point
+                        const Cell c = locate(I, I.fcoef, x, y);
+                        yxi = eval(__ldg(c.p), c.s, c.t);
+                        yeta = eval(__ldg(c.p + 1), c.s, c.t);
+                        xe = x;
+                        ye = y;
+                    } else {
+                        ++exits;
+                    }
+                    ax.add(yxi - x0);
+                    ae.add(yeta - y0);
+                    steps += taken;
+                    if (RECORD) {
+                        const long long ri = nd.rec0 + path;
+                        if (a.rec.steps) a.rec.steps[ri] = taken;
+                        if (a.rec.code) a.rec.code[ri] = code;
+                        if (a.rec.score_xi) a.rec.score_xi[ri] = yxi;
+                        if (a.rec.score_eta) a.rec.score_eta[ri] = yeta;
+                        if (a.rec.x_end) a.rec.x_end[ri] = xe;
+                        if (a.rec.y_end) a.rec.y_end[ri] = ye;
+                    }
+                    alive = false;
+                }
+            }
+            // lanes whose path ended take the task's next paths, in lane order
+            const unsigned need = __ballot_sync(FULL, !alive);
+            if (need != 0u && next < end) {
+                const int cand = next + __popc(need & below);
+                if (!alive && cand < end) {
+                    path = cand;
+                    alive = true;
+                    x = x0;
+                    y = y0;
+                    m = 0;
+                }
+                next += __popc(need);
+            }
+        }
+
+        const double sx = warp_sum(ax.sum()), qx = warp_sum(ax.sumsq());
+        const double se = warp_sum(ae.sum()), qe = warp_sum(ae.sumsq());
+        const long long ex = warp_sum_ll(exits), st = warp_sum_ll(steps);
+        if (lane == 0) {
+            Partial p;
+            p.s_xi = sx;
+            p.q_xi = qx;
+            p.s_eta = se;
+            p.q_eta = qe;
+            p.exits = ex;
+            p.steps = st;
+            a.partials[t] = p;
+        }
+    }
+}
+
+__device__ __forceinline__ double face_value64(const InstDev& I, int field, int face, double s)
+{
+    const int n = (face < 2) ? I.ny : I.nx;
+    long long off = (long long)field * (2LL * I.ny + 2LL * I.nx);
+    if (face >= 1) off += I.ny;
+    if (face >= 2) off += I.ny;
+    if (face >= 3) off += I.nx;
+    const double* v = I.faces64 + off;
+    const double g = s * (double)(n - 1);
+    int k = (int)floor(g);
+    k = max(0, min(k, n - 2));
+    const double f = g - (double)k;
+    return (1.0 - f) * v[k] + f * v[k + 1];
+}
+
+// One warp per node: compensated sums of the node's task partials (each lane a
+// fixed stride of tasks), a fixed butterfly across the warp, then the mean and
+// the standard error s / sqrt(N), s^2 = (Q - S^2 / N) / (N - 1) of the shifted
+// scores.
+__global__ void k_finalize(const FinalArgs a)
+{
+    const int node = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (node >= a.nnodes) return;
+    const NodeDev nd = a.nodes[node];
+    const OutDev o = a.out_table ? a.out_table[nd.inst] : a.out0;
+    const int k = nd.local;
+    if (nd.ntasks == 0) {
+        if (lane == 0) {
+            const InstDev I = a.inst[nd.inst];
+            int face;
+            double tg;
+            if (nd.x <= 0.0) { face = 0; tg = nd.y; }
+            else if (nd.x >= 1.0) { face = 1; tg = nd.y; }
+            else if (nd.y <= 0.0) { face = 2; tg = nd.x; }
+            else { face = 3; tg = nd.x; }
+            if (o.mean_xi) o.mean_xi[k] = face_value64(I, 0, face, tg);
+            if (o.mean_eta) o.mean_eta[k] = face_value64(I, 1, face, tg);
+            if (o.se_xi) o.se_xi[k] = 0.0;
+            if (o.se_eta) o.se_eta[k] = 0.0;
+            if (o.n_exit) o.n_exit[k] = nd.n_paths;
+            if (o.path_steps) o.path_steps[k] = 0;
+        }
+        return;
+    }
+    double v[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0};
+    long long ex = 0, st = 0;
+    for (int t = nd.task0 + lane; t < nd.task0 + nd.ntasks; t += 32) {
+        const Partial p = a.partials[t];
+        const double in[4] = {p.s_xi, p.q_xi, p.s_eta, p.q_eta};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const double y = in[q] - c[q];
+            const double tt = v[q] + y;
+            c[q] = (tt - v[q]) - y;
+            v[q] = tt;
+        }
+        ex += p.exits;
+        st += p.steps;
+    }
+    double tot[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) tot[q] = warp_sum(v[q] - c[q]);
+    ex = warp_sum_ll(ex);
+    st = warp_sum_ll(st);
+    if (lane == 0) {
+        const double N = (double)nd.n_paths;
+        const double mx = tot[0] / N, me = tot[2] / N;
+        double vx = 0.0, ve = 0.0;
+        if (nd.n_paths > 1) {
+            vx = fmax(0.0, (tot[1] - tot[0] * mx) / (N - 1.0));
+            ve = fmax(0.0, (tot[3] - tot[2] * me) / (N - 1.0));
+        }
+        if (o.mean_xi) o.mean_xi[k] = (double)nd.xf + mx;
+        if (o.mean_eta) o.mean_eta[k] = (double)nd.yf + me;
+        if (o.se_xi) o.se_xi[k] = sqrt(vx / N);
+        if (o.se_eta) o.se_eta[k] = sqrt(ve / N);
+        if (o.n_exit) o.n_exit[k] = ex;
+        if (o.path_steps) o.path_steps[k] = st;
+    }
+}
+
+__global__ void k_rng_draw(uint64_t seed, uint32_t instance, const uint32_t* __restrict__ ctrs, long long count,
+                           uint32_t* __restrict__ words, float* __restrict__ normals)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const uint4 c = make_uint4(ctrs[4 * i], ctrs[4 * i + 1], ctrs[4 * i + 2], ctrs[4 * i + 3]);
+    const uint4 r = philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32) ^ instance);
+    words[4 * i + 0] = r.x;
+    words[4 * i + 1] = r.y;
+    words[4 * i + 2] = r.z;
+    words[4 * i + 3] = r.w;
+    if (normals) {
+        const float scale = -1.38629436111989061883f;  // -2 ln 2: unit variance
+        float z0, z1, z2, z3;
+        box_muller(r.x, r.y, scale, z0, z1);
+        box_muller(r.z, r.w, scale, z2, z3);
+        normals[4 * i + 0] = z0;
+        normals[4 * i + 1] = z1;
+        normals[4 * i + 2] = z2;
+        normals[4 * i + 3] = z3;
+    }
+}
+
+template <int MODE, bool RECORD>
+const void* kernel_ptr()
+{
+    return (const void*)k_paths<MODE, RECORD>;
+}
+
+const void* pick(int exit_mode, bool record)
+{
+    if (exit_mode == 0) return record ? kernel_ptr<0, true>() : kernel_ptr<0, false>();
+    return record ? kernel_ptr<1, true>() : kernel_ptr<1, false>();
+}
+
+}  // namespace
+
+int path_kernel_blocks_per_sm(int exit_mode, bool record, int block)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(exit_mode, record), block, 0) != cudaSuccess)
+        return 1;
+    return n > 0 ? n : 1;
+}
+
+cudaError_t launch_paths(const PathArgs& a, int exit_mode, bool record, int grid, int block, cudaStream_t s)
+{
+    if (exit_mode == 0) {
+        if (record) k_paths<0, true><<<grid, block, 0, s>>>(a);
+        else k_paths<0, false><<<grid, block, 0, s>>>(a);
+    } else {
+        if (record) k_paths<1, true><<<grid, block, 0, s>>>(a);
+        else k_paths<1, false><<<grid, block, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const FinalArgs& a, cudaStream_t s)
+{
+    const int block = 256;
+    const long long threads = (long long)a.nnodes * 32;
+    const int grid = (int)((threads + block - 1) / block);
+    if (grid > 0) k_finalize<<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rng_draw(uint64_t seed, uint32_t instance, const uint32_t* ctrs, long long count,
+                            uint32_t* words, float* normals, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    const int block = 256;
+    k_rng_draw<<<(unsigned)((count + block - 1) / block), block, 0, s>>>(seed, instance, ctrs, count, words,
+                                                                         normals);
+    return cudaGetLastError();
+}
+
+}  // namespace sdd

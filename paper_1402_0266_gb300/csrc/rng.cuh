@@ -1,0 +1,61 @@
+// rng.cuh -- the estimator's normal variates on the device.
+//
+// The paper asks for the Brownian increments dW = sqrt(dt) N(0,1) (Sec. 4) and
+// fixes no generator. They come from the counter-based Philox4x32-10 of
+// Salmon, Moraes, Dror and Shaw ("Parallel random numbers: as easy as 1, 2, 3",
+// SC'11): ten rounds, each two 32x32->64 multiplies whose high halves are
+// xored with the other counter words and the round key, the key bumped by the
+// Weyl constants between rounds. A 4-word block feeds two Box--Muller pairs.
+//
+// Uniforms from a word w with m = w & 0x7FFFFF (exact in single precision):
+//   u1 = 1 - m 2^-23 in (0, 1],  u2 = m 2^-23 in [0, 1),  ub = (m + 1) 2^-23 in (0, 1].
+#pragma once
+
+#include <stdint.h>
+
+namespace sdd {
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1,
+                       (uint32_t)p0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ float sqrt_approx(float v)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+// Box--Muller pair scaled by sigma: (sigma R cos 2 pi u2, sigma R sin 2 pi u2),
+// R = sqrt(-2 ln u1). `scale` = -2 sigma^2 ln 2, so that
+// sigma R = sqrt(scale * log2(u1)). The angle is taken as 2 pi (u2 - 1/2),
+// which keeps the argument of the fast sine and cosine in [-pi, pi); then
+// cos(2 pi u2) = -cos(2 pi (u2 - 1/2)) and likewise for the sine.
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float scale, float& z0, float& z1)
+{
+    const float u1 = 2.0f - __uint_as_float(0x3F800000u | (a & 0x7FFFFFu));
+    const float v = __uint_as_float(0x3F800000u | (b & 0x7FFFFFu)) - 1.5f;
+    const float r = sqrt_approx(scale * __log2f(u1));
+    float s, c;
+    __sincosf(6.28318530717958647692f * v, &s, &c);
+    z0 = -r * c;
+    z1 = -r * s;
+}
+
+__device__ __forceinline__ float uniform_pos(uint32_t w)
+{
+    // (1 + m 2^-23) - (1 - 2^-23) = (m + 1) 2^-23, exact
+    return __uint_as_float(0x3F800000u | (w & 0x7FFFFFu)) - 0.99999988079071044921875f;
+}
+
+}  // namespace sdd

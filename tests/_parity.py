@@ -1,0 +1,53 @@
+"""Comparison helpers for the CUDA path against the oracle (same Philox streams)."""
+import numpy as np
+
+# The estimator's own tolerance: per node within 3 standard errors; exit
+# decisions identical for at least 99.9% of paths. Paths whose exit decision
+# agrees carry single-precision rounding only: their scores and end points
+# agree to well below 1e-4.
+EXIT_AGREEMENT = 0.999
+PATH_TOL = 1e-4
+NODE_TOL = 1e-4
+
+
+def compare_records(g, o):
+    """g: GPU records (numpy), o: oracle records. Returns (agree mask, report dict)."""
+    code_g = np.asarray(g["code"])
+    code_o = np.asarray(o["code"])
+    same = (code_g == code_o) & (np.asarray(g["steps"]) == np.asarray(o["steps"]))
+    frac = same.mean() if same.size else 1.0
+    rep = {"paths": int(same.size), "disagree": int((~same).sum()), "agree_frac": float(frac)}
+    if same.any():
+        for k in ("score_xi", "score_eta", "x_end", "y_end"):
+            rep["max_" + k] = float(np.abs(np.asarray(g[k], np.float64)[same] - np.asarray(o[k])[same]).max())
+    return same, rep
+
+
+def assert_records(g, o):
+    same, rep = compare_records(g, o)
+    assert rep["agree_frac"] >= EXIT_AGREEMENT, rep
+    for k in ("score_xi", "score_eta", "x_end", "y_end"):
+        if "max_" + k in rep:
+            assert rep["max_" + k] <= PATH_TOL, rep
+    return same, rep
+
+
+def assert_nodes(g, o, n_paths, same=None, offsets=None):
+    """Per node: |mean_gpu - mean_oracle| <= 3 SE, and <= 1e-4 on every node whose
+    paths all agree; SE, exit and step counts consistent."""
+    for f in ("xi", "eta"):
+        d = np.abs(np.asarray(g["mean_" + f]) - np.asarray(o["mean_" + f]))
+        se = np.asarray(o["se_" + f])
+        assert np.all(d <= 3 * se + 1e-12), (f, d.max(), np.argmax(d - 3 * se))
+        if same is not None and offsets is not None:
+            clean = np.array([same[offsets[k]:offsets[k + 1]].all() for k in range(len(offsets) - 1)])
+            if clean.any():
+                assert d[clean].max() <= NODE_TOL, (f, d[clean].max())
+            gse = np.asarray(g["se_" + f])
+            rel = np.abs(gse[clean] - se[clean]) / np.maximum(se[clean], 1e-12)
+            if clean.any():
+                assert np.all((rel <= 1e-3) | (se[clean] < 1e-9)), (f, rel.max())
+    if same is not None and offsets is not None:
+        clean = np.array([same[offsets[k]:offsets[k + 1]].all() for k in range(len(offsets) - 1)])
+        np.testing.assert_array_equal(np.asarray(g["n_exit"])[clean], np.asarray(o["n_exit"])[clean])
+        np.testing.assert_array_equal(np.asarray(g["path_steps"])[clean], np.asarray(o["path_steps"])[clean])
