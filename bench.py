@@ -220,7 +220,7 @@ def run_ours(args, world, rank, local):
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     steps_dev = torch.zeros(K, dtype=torch.int64, device=dev)
-    paths_ms = []
+    paths_ms, est_ms, solve_ms = [], [], []
     kernel_nodes = 0
     clocks = ClockSampler(local)
     barrier(world)
@@ -236,6 +236,8 @@ def run_ours(args, world, rank, local):
         steps_dev[k] = st["path_steps"].sum()
         info = sdd.sdd_last_step_info(ctx)   # waits: outside the event pair
         paths_ms.append(info["paths_ms"])
+        est_ms.append(info["estimate_ms"])
+        solve_ms.append(info["solve_ms"])
         kernel_nodes = info["kernel_nodes"]
     torch.cuda.synchronize()
     barrier(world)
@@ -314,6 +316,8 @@ def run_ours(args, world, rank, local):
             "interface_nodes_per_s": nodes_per_s,
             "path_steps_per_step": tot_steps / K / world,
             "paths_kernel_ms": mean_paths_ms,
+            "estimate_ms": statistics.mean(est_ms),
+            "solve_ms": statistics.mean(solve_ms),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_paths", "ops_per_path_step": ALG_OPS_PER_PATH_STEP,

@@ -86,7 +86,9 @@ typedef struct {
  * order of sdd_nodes; any may be NULL): sub-steps taken; exit code (-1 survived
  * the mesh step, 0..3 left through face left/right/bottom/top at a sub-step
  * end, 4..7 left through face k-4 by the bridge test); the two scores; the end
- * point (exit point or X at the end of the step). */
+ * point (exit point or X at the end of the step). The paths of a node on the
+ * boundary take 0 steps, the code of its face (first of left, right, bottom,
+ * top that holds), its Dirichlet values and the node as end point. */
 typedef struct {
     int32_t* steps;
     int32_t* code;

@@ -404,6 +404,15 @@ int orc_mc_nodes(const orc_problem* P, const orc_params* Q, int64_t count,
             out[3] = 0.0;
             out[4] = (double)n;
             out[5] = 0.0;
+            /* every path is on the boundary at time 0: no step, the face's value */
+            for (int64_t p = 0; p < n; ++p) {
+                if (rec_steps) rec_steps[rec + p] = 0;
+                if (rec_code) rec_code[rec + p] = face;
+                if (rec_xi) rec_xi[rec + p] = out[0];
+                if (rec_eta) rec_eta[rec + p] = out[1];
+                if (rec_x) rec_x[rec + p] = xs[k];
+                if (rec_y) rec_y[rec + p] = ys[k];
+            }
             rec += n;
             continue;
         }

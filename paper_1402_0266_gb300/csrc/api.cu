@@ -60,14 +60,6 @@ struct Plan {
     DevBuf<Partial> d_partials;
     DevBuf<int> d_queue;
 
-    void release()
-    {
-        d_nodes.release();
-        d_tasks.release();
-        d_partials.release();
-        d_queue.release();
-        valid = false;
-    }
 };
 
 struct GraphSlot {
@@ -323,9 +315,9 @@ sdd_status run_plan(sdd_ctx* c, Plan& P, double dt, int K, uint64_t seed, uint32
         if (rec) a.rec = *rec;
         CU(c, cudaMemsetAsync(P.d_queue.p, 0, sizeof(int), s));
         const int grid = (int)std::min<int64_t>(P.grid, std::max<int64_t>(1, (P.ntasks * 32 + P.block - 1) / P.block));
-        if (ev_a) CU(c, cudaEventRecord(ev_a, s));
+        if (ev_a) CU(c, cudaEventRecordWithFlags(ev_a, s, cudaEventRecordExternal));
         CU(c, launch_paths(a, exit_mode, rec != nullptr, grid, P.block, s));
-        if (ev_b) CU(c, cudaEventRecord(ev_b, s));
+        if (ev_b) CU(c, cudaEventRecordWithFlags(ev_b, s, cudaEventRecordExternal));
     }
     FinalArgs f{};
     f.inst = c->d_inst.p;
@@ -334,6 +326,7 @@ sdd_status run_plan(sdd_ctx* c, Plan& P, double dt, int K, uint64_t seed, uint32
     f.out_table = nullptr;
     f.out0 = out;
     f.nnodes = (int32_t)P.nnodes;
+    if (rec) f.rec = *rec;
     CU(c, launch_finalize(f, s));
     return SDD_OK;
 }
@@ -686,7 +679,7 @@ static sdd_status capture_step(sdd_ctx* c, const sdd_step_params* p, int K, int 
     c->cur = parity;
     sdd_status st = SDD_OK;
     {
-        cudaError_t e0 = cudaEventRecord(c->ev[0], s);
+        cudaError_t e0 = cudaEventRecordWithFlags(c->ev[0], s, cudaEventRecordExternal);
         if (e0 != cudaSuccess) st = fail(c, SDD_ECUDA, "event: %s", cudaGetErrorString(e0));
     }
     if (st == SDD_OK) st = prepare(c, s);
@@ -701,7 +694,7 @@ static sdd_status capture_step(sdd_ctx* c, const sdd_step_params* p, int K, int 
         st = run_plan(c, c->step_plan, p->dt, K, p->seed, 0, c->d_step.p, p->exit_mode, o, nullptr, s, c->ev[1],
                       c->ev[2]);
     if (st == SDD_OK) {
-        cudaError_t e = cudaEventRecord(c->ev[3], s);
+        cudaError_t e = cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal);
         if (e != cudaSuccess) st = fail(c, SDD_ECUDA, "event: %s", cudaGetErrorString(e));
     }
     if (st == SDD_OK)
@@ -709,7 +702,7 @@ static sdd_status capture_step(sdd_ctx* c, const sdd_step_params* p, int K, int 
                            c->fld[1 - parity][1].p, s);
     if (st == SDD_OK) {
         cudaError_t e = launch_bump_step(c->d_step.p, s);
-        if (e == cudaSuccess) e = cudaEventRecord(c->ev[4], s);
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(c->ev[4], s, cudaEventRecordExternal);
         if (e != cudaSuccess) st = fail(c, SDD_ECUDA, "%s", cudaGetErrorString(e));
     }
     c->cur = saved;

@@ -93,6 +93,7 @@ struct FinalArgs {
     const OutDev* out_table;  // per instance; if null every node writes to out0
     OutDev out0;
     int32_t nnodes;
+    RecDev rec;               // per-path records of boundary nodes (may be all null)
 };
 
 // Device status word bits.

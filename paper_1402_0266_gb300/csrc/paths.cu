@@ -169,7 +169,7 @@ __device__ __forceinline__ long long warp_sum_ll(long long v)
 }
 
 template <int MODE, bool RECORD>
-__global__ void __launch_bounds__(256) k_paths(const PathArgs a)
+__global__ void __launch_bounds__(512) k_paths(const PathArgs a)
 {
     const int lane = threadIdx.x & 31;
     const unsigned below = (1u << lane) - 1u;
@@ -343,20 +343,31 @@ __global__ void k_finalize(const FinalArgs a)
     const OutDev o = a.out_table ? a.out_table[nd.inst] : a.out0;
     const int k = nd.local;
     if (nd.ntasks == 0) {
+        // a node on the boundary: its Dirichlet value, every path exits at time 0
+        const InstDev I = a.inst[nd.inst];
+        int face;
+        double tg;
+        if (nd.x <= 0.0) { face = 0; tg = nd.y; }
+        else if (nd.x >= 1.0) { face = 1; tg = nd.y; }
+        else if (nd.y <= 0.0) { face = 2; tg = nd.x; }
+        else { face = 3; tg = nd.x; }
+        const double vx = face_value64(I, 0, face, tg), ve = face_value64(I, 1, face, tg);
         if (lane == 0) {
-            const InstDev I = a.inst[nd.inst];
-            int face;
-            double tg;
-            if (nd.x <= 0.0) { face = 0; tg = nd.y; }
-            else if (nd.x >= 1.0) { face = 1; tg = nd.y; }
-            else if (nd.y <= 0.0) { face = 2; tg = nd.x; }
-            else { face = 3; tg = nd.x; }
-            if (o.mean_xi) o.mean_xi[k] = face_value64(I, 0, face, tg);
-            if (o.mean_eta) o.mean_eta[k] = face_value64(I, 1, face, tg);
+            if (o.mean_xi) o.mean_xi[k] = vx;
+            if (o.mean_eta) o.mean_eta[k] = ve;
             if (o.se_xi) o.se_xi[k] = 0.0;
             if (o.se_eta) o.se_eta[k] = 0.0;
             if (o.n_exit) o.n_exit[k] = nd.n_paths;
             if (o.path_steps) o.path_steps[k] = 0;
+        }
+        for (int p = lane; p < nd.n_paths; p += 32) {
+            const long long ri = nd.rec0 + p;
+            if (a.rec.steps) a.rec.steps[ri] = 0;
+            if (a.rec.code) a.rec.code[ri] = face;
+            if (a.rec.score_xi) a.rec.score_xi[ri] = (float)vx;
+            if (a.rec.score_eta) a.rec.score_eta[ri] = (float)ve;
+            if (a.rec.x_end) a.rec.x_end[ri] = nd.xf;
+            if (a.rec.y_end) a.rec.y_end[ri] = nd.yf;
         }
         return;
     }
