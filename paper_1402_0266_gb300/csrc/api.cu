@@ -101,8 +101,10 @@ struct sdd_ctx {
     DevBuf<long long> iface_counts[2];
 
     // solver
-    DevBuf<double> cx, cy, dg, rhs0, r[2], p[2], q[2];
+    DevBuf<double> cx, cy, dg, rhs0;
+    DevBuf<float> cxf, cyf, dgf, dinvf, r32[2], p32[2], q32[2], d32[2];
     std::vector<SolveSys> systems;
+    int solve_cluster = 1;
     DevBuf<SolveSys> d_systems;
     DevBuf<int32_t> d_iters;
 
@@ -338,13 +340,21 @@ sdd_status setup_solver(sdd_ctx* c)
     CU(c, c->cy.alloc(N));
     CU(c, c->dg.alloc(N));
     CU(c, c->rhs0.alloc(2 * N));
+    CU(c, c->cxf.alloc(N));
+    CU(c, c->cyf.alloc(N));
+    CU(c, c->dgf.alloc(N));
+    CU(c, c->dinvf.alloc(N));
     for (int f = 0; f < 2; ++f) {
-        CU(c, c->r[f].alloc(N));
-        CU(c, c->p[f].alloc(N));
-        CU(c, c->q[f].alloc(N));
+        CU(c, c->r32[f].alloc(N));
+        CU(c, c->p32[f].alloc(N));
+        CU(c, c->q32[f].alloc(N));
+        CU(c, c->d32[f].alloc(N));
+        // the search direction stays zero on the boundary and interface nodes
+        CU(c, cudaMemset(c->p32[f].p, 0, N * sizeof(float)));
     }
     const std::vector<int> xs = block_edges(c->nx, c->sub_x), ys = block_edges(c->ny, c->sub_y);
     c->systems.clear();
+    int min_rows = 1 << 30;
     for (int field = 0; field < 2; ++field)
         for (int b = 0; b < c->sub_y; ++b)
             for (int a = 0; a < c->sub_x; ++a) {
@@ -354,13 +364,17 @@ sdd_status setup_solver(sdd_ctx* c)
                 S.j0 = ys[b] + 1;
                 S.j1 = ys[b + 1];
                 S.field = field;
-                if (S.i1 > S.i0 && S.j1 > S.j0) c->systems.push_back(S);
+                if (S.i1 > S.i0 && S.j1 > S.j0) {
+                    c->systems.push_back(S);
+                    min_rows = std::min(min_rows, S.j1 - S.j0);
+                }
             }
     CU(c, c->d_systems.alloc(std::max<size_t>(c->systems.size(), 1)));
     if (!c->systems.empty())
         CU(c, cudaMemcpy(c->d_systems.p, c->systems.data(), c->systems.size() * sizeof(SolveSys),
                          cudaMemcpyHostToDevice));
     CU(c, c->d_iters.alloc(std::max<size_t>(c->systems.size(), 1)));
+    c->solve_cluster = c->systems.empty() ? 1 : solve_cluster_size((int)c->systems.size(), min_rows, c->sm_count);
     return SDD_OK;
 }
 
@@ -394,7 +408,8 @@ sdd_status enqueue_solve(sdd_ctx* c, double Dt, const double* ix, const double* 
 {
     const double* px = c->fld[c->cur][0].p;
     const double* pe = c->fld[c->cur][1].p;
-    CU(c, launch_solve_setup(c->w.p, px, pe, c->nx, c->ny, Dt, c->cx.p, c->cy.p, c->dg.p, c->rhs0.p, s));
+    CU(c, launch_solve_setup(c->w.p, px, pe, c->nx, c->ny, Dt, c->cx.p, c->cy.p, c->dg.p, c->rhs0.p, c->cxf.p,
+                             c->cyf.p, c->dgf.p, c->dinvf.p, s));
     CU(c, launch_dirichlet(c->faces64.p, px, pe, ix, ie, c->d_iface_idx.p, (int)c->iface_idx.size(), c->nx, c->ny,
                            xo, eo, s));
     SolveArgs a{};
@@ -404,17 +419,25 @@ sdd_status enqueue_solve(sdd_ctx* c, double Dt, const double* ix, const double* 
     a.cy = c->cy.p;
     a.dg = c->dg.p;
     a.rhs0 = c->rhs0.p;
+    a.cxf = c->cxf.p;
+    a.cyf = c->cyf.p;
+    a.dgf = c->dgf.p;
+    a.dinvf = c->dinvf.p;
     a.x[0] = xo;
     a.x[1] = eo;
     for (int f = 0; f < 2; ++f) {
-        a.r[f] = c->r[f].p;
-        a.p[f] = c->p[f].p;
-        a.q[f] = c->q[f].p;
+        a.r[f] = c->r32[f].p;
+        a.p[f] = c->p32[f].p;
+        a.q[f] = c->q32[f].p;
+        a.d[f] = c->d32[f].p;
     }
     a.sys = c->d_systems.p;
     a.nsys = (int32_t)c->systems.size();
+    a.cluster = c->solve_cluster;
     a.max_iter = max_iter;
+    a.max_outer = 12;
     a.rtol = rtol;
+    a.inner_tol = 1e-4f;
     a.iters = c->d_iters.p;
     a.status = c->d_status.p;
     CU(c, launch_pcg(a, s));

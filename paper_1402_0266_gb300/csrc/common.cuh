@@ -129,20 +129,30 @@ struct SolveArgs {
     const double* cy;        // face coefficient between (i, j) and (i, j + 1)
     const double* dg;        // diagonal
     const double* rhs0;      // 2 fields: prev / (w Dt)
+    const float* cxf;        // single-precision copies for the inner iterations
+    const float* cyf;
+    const float* dgf;
+    const float* dinvf;      // 1 / diagonal (Jacobi)
     double* x[2];            // solution fields (full grid, Dirichlet entries set)
-    double* r[2];
-    double* p[2];
-    double* q[2];
+    float* r[2];             // inner residual
+    float* p[2];             // search direction (zero on every node that is not an unknown)
+    float* q[2];             // A p
+    float* d[2];             // inner correction
     const SolveSys* sys;
     int32_t nsys;
-    int32_t max_iter;
-    double rtol;
-    int32_t* iters;          // per system
+    int32_t cluster;         // thread blocks per system
+    int32_t max_iter;        // total inner iterations allowed
+    int32_t max_outer;       // refinement sweeps allowed
+    double rtol;             // on the double-precision residual, relative to ||b||
+    float inner_tol;         // inner reduction of ||r|| per refinement sweep
+    int32_t* iters;          // per system: total inner iterations (max_iter + 1 when not converged)
     int* status;
 };
 
 cudaError_t launch_solve_setup(const float* w, const double* prev_xi, const double* prev_eta, int nx, int ny,
-                               double Dt, double* cx, double* cy, double* dg, double* rhs0, cudaStream_t s);
+                               double Dt, double* cx, double* cy, double* dg, double* rhs0, float* cxf, float* cyf,
+                               float* dgf, float* dinvf, cudaStream_t s);
+int solve_cluster_size(int nsys, int min_rows, int sm_count);
 cudaError_t launch_dirichlet(const double* faces64, const double* prev_xi, const double* prev_eta,
                              const double* iface_xi, const double* iface_eta, const int32_t* iface_idx,
                              int n_iface, int nx, int ny, double* xi_out, double* eta_out, cudaStream_t s);

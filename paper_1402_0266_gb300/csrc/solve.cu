@@ -8,22 +8,39 @@
 //   xi_ij / (w_ij Dt) + sum_nb c_nb (xi_ij - xi_nb) = xi^{n-1}_ij / (w_ij Dt),
 //   c_nb = 1 / (wbar h^2),  wbar = (w_ij + w_nb) / 2,
 //
-// a symmetric positive definite M-matrix, solved here per subdomain and field
-// by Jacobi-preconditioned conjugate gradients in double precision. Each
-// system is one thread block running the whole iteration; the block's
-// unknowns never leave L1/L2. The iteration stops at ||r|| <= rtol ||b|| or
-// after max_iter iterations (then a status bit is set; it never hangs).
+// a symmetric positive definite M-matrix, solved per subdomain and field by
+// Jacobi-preconditioned conjugate gradients.
+//
+// Precision: the solution and its residual are double precision; the
+// conjugate-gradient sweeps run on the residual equation A d = r in single
+// precision (iterative refinement): each sweep reduces ||r|| by inner_tol,
+// then x += d and r = b - A x are formed again in double precision, until
+// ||r|| <= rtol ||b||. On GB300 double-precision arithmetic runs at a small
+// fraction of the single-precision rate; only the residuals use it.
+//
+// Execution: one thread-block cluster per system; each block owns a band of
+// the subdomain's rows. Dot products are reduced inside each block, then
+// across the cluster through distributed shared memory, in a fixed order, so
+// every block takes the same branch. All loops are bounded by max_iter and
+// max_outer; non-convergence sets a status bit.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace sdd {
 
 namespace {
 
-constexpr int SOLVE_THREADS = 1024;
+constexpr int SOLVE_THREADS = 512;
+constexpr int SOLVE_WARPS = SOLVE_THREADS / 32;
 
 __global__ void k_solve_setup(const float* __restrict__ w, const double* __restrict__ pxi,
                               const double* __restrict__ peta, int nx, int ny, double Dt, double* __restrict__ cx,
-                              double* __restrict__ cy, double* __restrict__ dg, double* __restrict__ rhs0)
+                              double* __restrict__ cy, double* __restrict__ dg, double* __restrict__ rhs0,
+                              float* __restrict__ cxf, float* __restrict__ cyf, float* __restrict__ dgf,
+                              float* __restrict__ dinvf)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -36,6 +53,8 @@ __global__ void k_solve_setup(const float* __restrict__ w, const double* __restr
     const double no = (j + 1 < ny) ? ihy2 / (0.5 * (wc + (double)w[n + nx])) : 0.0;
     cx[n] = e;
     cy[n] = no;
+    cxf[n] = (float)e;
+    cyf[n] = (float)no;
     double d = 1.0 / (wc * Dt);
     rhs0[n] = pxi[n] * d;
     rhs0[(long long)nx * ny + n] = peta[n] * d;
@@ -44,6 +63,8 @@ __global__ void k_solve_setup(const float* __restrict__ w, const double* __restr
         d += e + no + ihx2 / (0.5 * (wc + wwest)) + ihy2 / (0.5 * (wc + wsouth));
     }
     dg[n] = d;
+    dgf[n] = (float)d;
+    dinvf[n] = (float)(1.0 / d);
 }
 
 // Dirichlet data of the new fields: the face data on the outer boundary, the
@@ -78,139 +99,176 @@ __global__ void k_scatter_iface(const double* __restrict__ vx, const double* __r
     eo[idx[k]] = ve[k];
 }
 
-__device__ __forceinline__ double block_sum(double v, double* sh)
-{
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    double t = 0.0;
-    const int nw = blockDim.x >> 5;
-    for (int k = 0; k < nw; ++k) t += sh[k];  // same order in every thread
-    return t;
-}
+// Sum of two values over the whole cluster: warps by shuffles, the block's
+// warps by thread 0 in order, the cluster's blocks by lane 0 of warp 0
+// through distributed shared memory, in rank order; every thread of every
+// block gets the same bits. Two slot sets alternate between calls: a block
+// rewrites a slot set only after the next call's cluster barrier, which every
+// block reaches only after it has read the slot set of the call before.
+template <typename T>
+struct ClusterSlots {
+    T warp_part[2][SOLVE_WARPS];
+    T block_part[2];
+    T total[2];
+};
 
-__device__ __forceinline__ void block_sum2(double& a, double& b, double* sh)
+template <typename T>
+__device__ __forceinline__ void cluster_sum2(cg::cluster_group& cl, ClusterSlots<T> (&sh)[2], int& seq, T& v0,
+                                             T& v1)
 {
+    ClusterSlots<T>& S = sh[seq & 1];
+    ++seq;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, off);
-        b += __shfl_xor_sync(0xffffffffu, b, off);
+        v0 += __shfl_xor_sync(0xffffffffu, v0, off);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, off);
     }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
     if (lane == 0) {
-        sh[warp] = a;
-        sh[32 + warp] = b;
+        S.warp_part[0][warp] = v0;
+        S.warp_part[1][warp] = v1;
     }
     __syncthreads();
-    double ta = 0.0, tb = 0.0;
-    const int nw = blockDim.x >> 5;
-    for (int k = 0; k < nw; ++k) {
-        ta += sh[k];
-        tb += sh[32 + k];
+    if (threadIdx.x == 0) {
+        T t0 = 0, t1 = 0;
+        for (int q = 0; q < SOLVE_WARPS; ++q) {
+            t0 += S.warp_part[0][q];
+            t1 += S.warp_part[1][q];
+        }
+        S.block_part[0] = t0;
+        S.block_part[1] = t1;
     }
-    a = ta;
-    b = tb;
+    cl.sync();
+    if (threadIdx.x == 0) {
+        const int C = (int)cl.num_blocks();
+        T t0 = 0, t1 = 0;
+        for (int r = 0; r < C; ++r) {
+            const T* rem = cl.map_shared_rank(&S.block_part[0], r);
+            t0 += rem[0];
+            t1 += rem[1];
+        }
+        S.total[0] = t0;
+        S.total[1] = t1;
+    }
+    __syncthreads();
+    v0 = S.total[0];
+    v1 = S.total[1];
 }
 
-__global__ void __launch_bounds__(SOLVE_THREADS) k_pcg(const SolveArgs a)
+__global__ void __launch_bounds__(SOLVE_THREADS) k_pcg_cluster(const SolveArgs a)
 {
-    __shared__ double sh[64];
-    const SolveSys S = a.sys[blockIdx.x];
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks();
+    const int rank = (int)cl.block_rank();
+    const SolveSys S = a.sys[blockIdx.x / C];
     const int nx = a.nx;
     const int mx = S.i1 - S.i0, my = S.j1 - S.j0;
-    const int m = mx * my;
+    const int row0 = S.j0 + (my * rank) / C, row1 = S.j0 + (my * (rank + 1)) / C;
+    const int m = (row1 - row0) * mx;  // unknowns of this block
     double* __restrict__ x = a.x[S.field];
-    double* __restrict__ r = a.r[S.field];
-    double* __restrict__ p = a.p[S.field];
-    double* __restrict__ q = a.q[S.field];
+    float* __restrict__ r = a.r[S.field];
+    float* __restrict__ p = a.p[S.field];
+    float* __restrict__ q = a.q[S.field];
+    float* __restrict__ d = a.d[S.field];
     const double* __restrict__ rhs = a.rhs0 + (long long)S.field * nx * a.ny;
-    const double* __restrict__ cx = a.cx;
-    const double* __restrict__ cy = a.cy;
-    const double* __restrict__ dg = a.dg;
 
-    // r = b - A x over the block, with x's Dirichlet ring fixed; z = r / diag; p = z
-    double bb = 0.0, rz = 0.0;
-    for (int u = threadIdx.x; u < m; u += blockDim.x) {
-        const int i = S.i0 + u % mx, j = S.j0 + u / mx;
-        const long long n = (long long)j * nx + i;
-        // b: the rhs plus the Dirichlet neighbours
+    __shared__ ClusterSlots<double> red64[2];
+    __shared__ ClusterSlots<float> red32[2];
+    int seq = 0;  // one counter for both slot types: consecutive calls never share a slot set
+
+    auto node = [&](int u) -> long long { return (long long)(row0 + u / mx) * nx + (S.i0 + u % mx); };
+
+    // ||b||^2 with b = rhs + the Dirichlet neighbours' terms
+    double bb = 0.0, unused = 0.0;
+    for (int u = threadIdx.x; u < m; u += SOLVE_THREADS) {
+        const long long n = node(u);
+        const int i = S.i0 + u % mx, j = row0 + u / mx;
         double b = rhs[n];
-        const double ax = dg[n] * x[n] - cx[n - 1] * x[n - 1] - cx[n] * x[n + 1] - cy[n - nx] * x[n - nx] -
-                          cy[n] * x[n + nx];
-        double bd = 0.0;
-        if (i == S.i0) bd += cx[n - 1] * x[n - 1];
-        if (i == S.i1 - 1) bd += cx[n] * x[n + 1];
-        if (j == S.j0) bd += cy[n - nx] * x[n - nx];
-        if (j == S.j1 - 1) bd += cy[n] * x[n + nx];
-        b += bd;
-        const double rr = rhs[n] - ax;
-        const double z = rr / dg[n];
-        r[n] = rr;
-        p[n] = z;
+        if (i == S.i0) b += a.cx[n - 1] * x[n - 1];
+        if (i == S.i1 - 1) b += a.cx[n] * x[n + 1];
+        if (j == S.j0) b += a.cy[n - nx] * x[n - nx];
+        if (j == S.j1 - 1) b += a.cy[n] * x[n + nx];
         bb += b * b;
-        rz += rr * z;
     }
-    block_sum2(bb, rz, sh);
-    const double bnorm = sqrt(bb);
-    double rr_norm2 = 0.0;
-    {
-        double t = 0.0;
-        for (int u = threadIdx.x; u < m; u += blockDim.x) {
-            const int i = S.i0 + u % mx, j = S.j0 + u / mx;
-            const double v = r[(long long)j * nx + i];
-            t += v * v;
+    cluster_sum2(cl, red64, seq, bb, unused);
+    const double stop2 = a.rtol * a.rtol * bb;
+
+    int total = 0;
+    bool converged = false;
+    for (int outer = 0; outer < a.max_outer; ++outer) {
+        // double-precision residual r = b - A x (x complete on every block: cluster-synchronised)
+        double rr64 = 0.0, unused64 = 0.0;
+        for (int u = threadIdx.x; u < m; u += SOLVE_THREADS) {
+            const long long n = node(u);
+            const double ax = a.dg[n] * x[n] - a.cx[n - 1] * x[n - 1] - a.cx[n] * x[n + 1] -
+                              a.cy[n - nx] * x[n - nx] - a.cy[n] * x[n + nx];
+            const double res = rhs[n] - ax;
+            rr64 += res * res;
+            const float rf = (float)res;
+            r[n] = rf;
+            d[n] = 0.0f;
+            p[n] = rf * a.dinvf[n];
         }
-        rr_norm2 = block_sum(t, sh);
-    }
-    int it = 0;
-    if (sqrt(rr_norm2) > a.rtol * bnorm) {
-        for (it = 1; it <= a.max_iter; ++it) {
-            __syncthreads();  // p complete
-            double pq = 0.0;
-            for (int u = threadIdx.x; u < m; u += blockDim.x) {
-                const int i = S.i0 + u % mx, j = S.j0 + u / mx;
-                const long long n = (long long)j * nx + i;
-                // p is zero outside the block (Dirichlet nodes): only block neighbours count
-                double v = dg[n] * p[n];
-                if (i > S.i0) v -= cx[n - 1] * p[n - 1];
-                if (i < S.i1 - 1) v -= cx[n] * p[n + 1];
-                if (j > S.j0) v -= cy[n - nx] * p[n - nx];
-                if (j < S.j1 - 1) v -= cy[n] * p[n + nx];
+        cluster_sum2(cl, red64, seq, rr64, unused64);
+        if (rr64 <= stop2) {
+            converged = true;
+            break;
+        }
+        if (total >= a.max_iter) break;
+        // single-precision PCG on A d = r, from d = 0 with p = z = r / diag
+        float rz = 0.0f, rr = 0.0f;
+        for (int u = threadIdx.x; u < m; u += SOLVE_THREADS) {
+            const long long n = node(u);
+            rz += r[n] * p[n];
+            rr += r[n] * r[n];
+        }
+        cluster_sum2(cl, red32, seq, rz, rr);  // its barrier also publishes p to the neighbouring blocks
+        if (!(rr > 0.0f)) continue;
+        const float stop_in = a.inner_tol * a.inner_tol * rr;
+        while (total < a.max_iter) {
+            ++total;
+            float pq = 0.0f, unused32 = 0.0f;
+            for (int u = threadIdx.x; u < m; u += SOLVE_THREADS) {
+                const long long n = node(u);
+                // p is zero on every node that is not an unknown
+                const float v = a.dgf[n] * p[n] - a.cxf[n - 1] * p[n - 1] - a.cxf[n] * p[n + 1] -
+                                a.cyf[n - nx] * p[n - nx] - a.cyf[n] * p[n + nx];
                 q[n] = v;
                 pq += p[n] * v;
             }
-            pq = block_sum(pq, sh);
-            const double alpha = rz / pq;
-            double rz_new = 0.0, r2 = 0.0;
-            for (int u = threadIdx.x; u < m; u += blockDim.x) {
-                const int i = S.i0 + u % mx, j = S.j0 + u / mx;
-                const long long n = (long long)j * nx + i;
-                x[n] += alpha * p[n];
-                const double rn = r[n] - alpha * q[n];
+            cluster_sum2(cl, red32, seq, pq, unused32);
+            const float alpha = rz / pq;
+            float rz_new = 0.0f, rr_new = 0.0f;
+            for (int u = threadIdx.x; u < m; u += SOLVE_THREADS) {
+                const long long n = node(u);
+                d[n] += alpha * p[n];
+                const float rn = r[n] - alpha * q[n];
                 r[n] = rn;
-                const double z = rn / dg[n];
-                rz_new += rn * z;
-                r2 += rn * rn;
+                rz_new += rn * rn * a.dinvf[n];
+                rr_new += rn * rn;
             }
-            block_sum2(rz_new, r2, sh);
-            if (sqrt(r2) <= a.rtol * bnorm) break;
-            const double beta = rz_new / rz;
+            cluster_sum2(cl, red32, seq, rz_new, rr_new);
+            if (rr_new <= stop_in) break;
+            const float beta = rz_new / rz;
             rz = rz_new;
-            for (int u = threadIdx.x; u < m; u += blockDim.x) {
-                const int i = S.i0 + u % mx, j = S.j0 + u / mx;
-                const long long n = (long long)j * nx + i;
-                p[n] = r[n] / dg[n] + beta * p[n];
+            for (int u = threadIdx.x; u < m; u += SOLVE_THREADS) {
+                const long long n = node(u);
+                p[n] = r[n] * a.dinvf[n] + beta * p[n];
             }
+            cl.sync();  // p complete before the next product
         }
+        // x += d in double precision; the next residual reads the neighbours' x
+        for (int u = threadIdx.x; u < m; u += SOLVE_THREADS) {
+            const long long n = node(u);
+            x[n] += (double)d[n];
+        }
+        cl.sync();
     }
-    if (threadIdx.x == 0) {
-        a.iters[blockIdx.x] = it;
-        if (it > a.max_iter) atomicOr(a.status, STATUS_NOCONV);
+    if (threadIdx.x == 0 && rank == 0) {
+        a.iters[blockIdx.x / C] = converged ? total : a.max_iter + 1;
+        if (!converged) atomicOr(a.status, STATUS_NOCONV);
     }
+    cl.sync();  // no block leaves while others may still read its shared memory
 }
 
 __global__ void k_bump_step(uint32_t* step)
@@ -221,11 +279,12 @@ __global__ void k_bump_step(uint32_t* step)
 }  // namespace
 
 cudaError_t launch_solve_setup(const float* w, const double* prev_xi, const double* prev_eta, int nx, int ny,
-                               double Dt, double* cx, double* cy, double* dg, double* rhs0, cudaStream_t s)
+                               double Dt, double* cx, double* cy, double* dg, double* rhs0, float* cxf, float* cyf,
+                               float* dgf, float* dinvf, cudaStream_t s)
 {
     const dim3 block(32, 8);
     const dim3 grid((nx + 31) / 32, (ny + 7) / 8);
-    k_solve_setup<<<grid, block, 0, s>>>(w, prev_xi, prev_eta, nx, ny, Dt, cx, cy, dg, rhs0);
+    k_solve_setup<<<grid, block, 0, s>>>(w, prev_xi, prev_eta, nx, ny, Dt, cx, cy, dg, rhs0, cxf, cyf, dgf, dinvf);
     return cudaGetLastError();
 }
 
@@ -242,10 +301,50 @@ cudaError_t launch_dirichlet(const double* faces64, const double* prev_xi, const
     return cudaGetLastError();
 }
 
+// Blocks per system: a power of two up to 16, no more than the SMs allow for
+// all systems at once and no more than the smallest system's rows.
+int solve_cluster_size(int nsys, int min_rows, int sm_count)
+{
+    static int max_c = -1;
+    if (max_c < 0) {
+        max_c = 8;
+        if (cudaFuncSetAttribute(k_pcg_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(16);
+            cfg.blockDim = dim3(SOLVE_THREADS);
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = 16;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, k_pcg_cluster, &cfg) == cudaSuccess && n > 0) max_c = 16;
+        }
+        cudaGetLastError();
+    }
+    int c = 1;
+    while (c * 2 <= max_c && (long long)c * 2 * nsys <= sm_count && c * 2 <= min_rows) c *= 2;
+    return c;
+}
+
 cudaError_t launch_pcg(const SolveArgs& a, cudaStream_t s)
 {
-    if (a.nsys > 0) k_pcg<<<a.nsys, SOLVE_THREADS, 0, s>>>(a);
-    return cudaGetLastError();
+    if (a.nsys <= 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(a.nsys * a.cluster));
+    cfg.blockDim = dim3(SOLVE_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)a.cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_pcg_cluster, a);
 }
 
 cudaError_t launch_bump_step(uint32_t* step, cudaStream_t s)

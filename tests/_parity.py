@@ -35,12 +35,17 @@ def assert_records(g, o):
 def assert_nodes(g, o, n_paths, same=None, offsets=None):
     """Per node: |mean_gpu - mean_oracle| <= 3 SE, and <= 1e-4 on every node whose
     paths all agree; SE, exit and step counts consistent."""
+    clean_all = None
+    if same is not None and offsets is not None:
+        clean_all = np.array([same[offsets[k]:offsets[k + 1]].all() for k in range(len(offsets) - 1)])
     for f in ("xi", "eta"):
         d = np.abs(np.asarray(g["mean_" + f]) - np.asarray(o["mean_" + f]))
         se = np.asarray(o["se_" + f])
-        assert np.all(d <= 3 * se + 1e-12), (f, d.max(), np.argmax(d - 3 * se))
+        # nodes whose paths all agree carry only rounding (<= 1e-4); the others <= 3 SE
+        allow = 3 * se + (NODE_TOL * clean_all if clean_all is not None else 1e-12)
+        assert np.all(d <= allow), (f, d.max(), np.argmax(d - allow))
         if same is not None and offsets is not None:
-            clean = np.array([same[offsets[k]:offsets[k + 1]].all() for k in range(len(offsets) - 1)])
+            clean = clean_all
             if clean.any():
                 assert d[clean].max() <= NODE_TOL, (f, d[clean].max())
             gse = np.asarray(g["se_" + f])

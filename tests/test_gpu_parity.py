@@ -137,7 +137,8 @@ def test_records_do_not_depend_on_launch_shape(sdd):
     for r in runs[1:]:
         for k in ("steps", "code", "score_xi", "score_eta", "x_end", "y_end"):
             np.testing.assert_array_equal(r[k], runs[0][k])
-        np.testing.assert_allclose(r["mean_xi"], runs[0]["mean_xi"], rtol=0, atol=1e-12)
+        # different lane groupings change only the single-precision lane sums
+        np.testing.assert_allclose(r["mean_xi"], runs[0]["mean_xi"], rtol=0, atol=1e-8)
         np.testing.assert_array_equal(r["n_exit"], runs[0]["n_exit"])
 
 
