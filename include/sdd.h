@@ -102,7 +102,7 @@ typedef struct {
  *   dt          Euler--Maruyama sub-step, > 0.
  *   Dt          the mesh step; Dt / dt must be an integer K within 1e-9
  *               relative, 1 <= K <= 2^20.
- *   seed        Philox key: key = (seed low 32 bits, high 32 bits ^ instance).
+ *   seed        Philox key: key = (seed low 32 bits, seed high 32 bits).
  *   step_index  mesh step number n, the last word of the Philox counter
  *               (counter = (path, node, draw, n)).
  *   exit_mode   0: the paper's boundary test after every sub-step;
@@ -252,9 +252,9 @@ void sdd_destroy(sdd_ctx* ctx);
  * (path, node, draw, step) in `ctrs` (DEVICE, 4 uint32 per entry), the Philox
  * block (`words`, DEVICE, 4 uint32 per entry) and the four normals of its two
  * Box--Muller pairs, unscaled (`normals`, DEVICE, 4 float per entry; may be
- * NULL). key = (seed low, seed high ^ instance). */
-sdd_status sdd_rng_draw(uint64_t seed, uint32_t instance, const uint32_t* ctrs, int64_t count, uint32_t* words,
-                        float* normals, void* stream);
+ * NULL). key = (seed low 32 bits, seed high 32 bits). */
+sdd_status sdd_rng_draw(uint64_t seed, const uint32_t* ctrs, int64_t count, uint32_t* words, float* normals,
+                        void* stream);
 
 #ifdef __cplusplus
 }

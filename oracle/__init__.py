@@ -59,8 +59,7 @@ class _Problem(ctypes.Structure):
 
 class _Params(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("K", ctypes.c_int32), ("exit_mode", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("instance", ctypes.c_uint32),
-                ("step_index", ctypes.c_uint32)]
+                ("seed", ctypes.c_uint64), ("step_index", ctypes.c_uint32)]
 
 
 def _load():
@@ -83,7 +82,7 @@ def _load():
             lib.orc_mc_nodes.argtypes = [ctypes.POINTER(_Problem), ctypes.POINTER(_Params), ctypes.c_int64,
                                          vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
             lib.orc_mc_nodes.restype = ctypes.c_int
-            lib.orc_draw.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, vp, vp, vp]
+            lib.orc_draw.argtypes = [ctypes.c_uint64, ctypes.c_int64, vp, vp, vp]
             _lib = lib
     return _lib
 
@@ -115,7 +114,7 @@ def box_muller(a: int, b: int):
     return float(z0[0]), float(z1[0])
 
 
-def draw(seed: int, instance: int, counters):
+def draw(seed: int, counters):
     """Philox words and normals for counters (path, node, draw, step), shape (n, 4).
 
     Returns (words (n,4) uint32, normals (n,4) float64): normals[:, 0:2] from
@@ -126,8 +125,7 @@ def draw(seed: int, instance: int, counters):
     n = c.shape[0]
     words = np.zeros((n, 4), np.uint32)
     normals = np.zeros((n, 4), np.float64)
-    lib.orc_draw(ctypes.c_uint64(seed), ctypes.c_uint32(instance), ctypes.c_int64(n), _p(c), _p(words),
-                 _p(normals))
+    lib.orc_draw(ctypes.c_uint64(seed), ctypes.c_int64(n), _p(c), _p(words), _p(normals))
     return words, normals
 
 
@@ -224,13 +222,14 @@ def sub_steps(dt: float, Dt: float) -> int:
 
 
 def interface_mc(problem: Problem, xs, ys, n_paths, *, dt: float, Dt: float, seed: int = 0,
-                 exit_mode: int = 0, step_index: int = 0, instance: int = 0, node_ids=None,
+                 exit_mode: int = 0, step_index: int = 0, node_ids=None,
                  record: bool = False, threads: int | None = None):
     """Estimate xi, eta at the given nodes over one mesh step (Eq. 7b, Sec. 4).
 
     Returns a dict with mean_xi, mean_eta, se_xi, se_eta, n_exit, path_steps
     (one entry per node) and, with record=True, per-path arrays steps, code,
     score_xi, score_eta, x_end, y_end laid out node after node.
+    node_ids: each node's word in the Philox counter (default 0..count-1).
     threads: worker threads over nodes (ctypes releases the GIL), default all cores.
     """
     lib = _load()
@@ -244,7 +243,7 @@ def interface_mc(problem: Problem, xs, ys, n_paths, *, dt: float, Dt: float, see
     K = sub_steps(dt, Dt)
     P = _Problem(problem.nx, problem.ny, problem.bx.ctypes.data, problem.by.ctypes.data,
                  problem.xi0.ctypes.data, problem.eta0.ctypes.data, problem.faces.ctypes.data)
-    Q = _Params(dt, K, exit_mode, seed, instance, step_index)
+    Q = _Params(dt, K, exit_mode, seed, step_index)
     stats = np.zeros((count, 6))
     total = int(n_paths.sum())
     recs = None

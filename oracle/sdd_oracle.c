@@ -73,12 +73,13 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* Stream layout (reading R9): key = (seed_lo, seed_hi ^ instance),
- * counter = (path, node, draw, mesh step). */
-static void draw_words(uint64_t seed, uint32_t instance, uint32_t path, uint32_t node,
-                       uint32_t draw, uint32_t step, uint32_t out[4])
+/* Stream layout (reading R9): key = (seed_lo, seed_hi), counter = (path,
+ * node, draw, mesh step); the node word numbers the nodes of all instances
+ * evaluated together. */
+static void draw_words(uint64_t seed, uint32_t path, uint32_t node, uint32_t draw, uint32_t step,
+                       uint32_t out[4])
 {
-    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32) ^ instance};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
     uint32_t ctr[4] = {path, node, draw, step};
     orc_philox4x32_10(ctr, key, out);
 }
@@ -235,7 +236,6 @@ typedef struct {
     int32_t K;            /* sub-steps per mesh step, Delta t = K dt */
     int32_t exit_mode;    /* 0 plain test, 1 plain test + Brownian-bridge test */
     uint64_t seed;
-    uint32_t instance;
     uint32_t step_index;  /* mesh step n */
 } orc_params;
 
@@ -317,11 +317,11 @@ static int32_t run_path(const orc_problem* P, const orc_params* Q, uint32_t node
         double zx, zy, ub = 1.0;
         if (Q->exit_mode == 0) {
             /* one Philox block serves the sub-step pair (2m, 2m+1) */
-            if ((j & 1) == 0) draw_words(Q->seed, Q->instance, path, node, (uint32_t)(j >> 1), Q->step_index, words);
+            if ((j & 1) == 0) draw_words(Q->seed, path, node, (uint32_t)(j >> 1), Q->step_index, words);
             if ((j & 1) == 0) orc_box_muller(words[0], words[1], &zx, &zy);
             else orc_box_muller(words[2], words[3], &zx, &zy);
         } else {
-            draw_words(Q->seed, Q->instance, path, node, (uint32_t)j, Q->step_index, words);
+            draw_words(Q->seed, path, node, (uint32_t)j, Q->step_index, words);
             orc_box_muller(words[0], words[1], &zx, &zy);
             ub = u_pos(words[2]);
         }
@@ -451,12 +451,11 @@ int orc_mc_nodes(const orc_problem* P, const orc_params* Q, int64_t count,
 /* Raw access to the variates, for the generator's own checks: for each of
  * `count` counters (4 words each) the Philox block and the two normals of
  * its first word pair. */
-void orc_draw(uint64_t seed, uint32_t instance, int64_t count, const uint32_t* ctrs,
-              uint32_t* words_out, double* normals_out)
+void orc_draw(uint64_t seed, int64_t count, const uint32_t* ctrs, uint32_t* words_out, double* normals_out)
 {
     for (int64_t k = 0; k < count; ++k) {
         uint32_t w[4];
-        draw_words(seed, instance, ctrs[4 * k + 0], ctrs[4 * k + 1], ctrs[4 * k + 2], ctrs[4 * k + 3], w);
+        draw_words(seed, ctrs[4 * k + 0], ctrs[4 * k + 1], ctrs[4 * k + 2], ctrs[4 * k + 3], w);
         for (int q = 0; q < 4; ++q) words_out[4 * k + q] = w[q];
         if (normals_out) {
             orc_box_muller(w[0], w[1], &normals_out[4 * k + 0], &normals_out[4 * k + 1]);

@@ -113,7 +113,7 @@ def lib():
                 "sdd_sync": [vp],
                 "sdd_last_error": [vp],
                 "sdd_destroy": [vp],
-                "sdd_rng_draw": [u64, u32, vp, i64, vp, vp, vp],
+                "sdd_rng_draw": [u64, vp, i64, vp, vp, vp],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -368,7 +368,7 @@ def sdd_destroy(ctx: Ctx):
     ctx.handle = ctypes.c_void_p(0)
 
 
-def sdd_rng_draw(seed, instance, counters, stream=None):
+def sdd_rng_draw(seed, counters, stream=None):
     """Philox words and unit normals for counters (n, 4) uint32 (cuda int32 tensor or numpy)."""
     torch = _torch()
     if isinstance(counters, np.ndarray):
@@ -378,7 +378,7 @@ def sdd_rng_draw(seed, instance, counters, stream=None):
     n = c.numel() // 4
     words = torch.empty((n, 4), dtype=torch.int32, device="cuda")
     normals = torch.empty((n, 4), dtype=torch.float32, device="cuda")
-    st = lib().sdd_rng_draw(seed, instance, _ptr(c), n, _ptr(words), _ptr(normals), _stream(stream))
+    st = lib().sdd_rng_draw(seed, _ptr(c), n, _ptr(words), _ptr(normals), _stream(stream))
     if st != SDD_OK:
         raise SddError(st, "sdd_rng_draw failed")
     return words, normals

@@ -1,5 +1,6 @@
 // api.cu -- the C ABI of libsdd (include/sdd.h): contexts, node plans, launches,
 // the subdomain solve and the per-mesh-step CUDA graph.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -251,6 +252,17 @@ sdd_status build_plan(sdd_ctx* c, Plan& P, const double* x, const double* y, con
     P.tasks.clear();
     int64_t rec = 0;
     for (int64_t k = 0; k < count; ++k) {
+        P.nodes[k].rec0 = rec;
+        rec += np[k];
+    }
+    // Tasks go node by node, nodes far from the boundary first: their paths
+    // run the whole mesh step, so the short tasks of nodes near the boundary
+    // fill the end of the launch.
+    std::vector<int64_t> order(count);
+    for (int64_t k = 0; k < count; ++k) order[k] = k;
+    auto dist = [&](int64_t k) { return std::min(std::min(x[k], 1.0 - x[k]), std::min(y[k], 1.0 - y[k])); };
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return dist(a) > dist(b); });
+    for (int64_t k : order) {
         NodeDev& nd = P.nodes[k];
         nd.x = x[k];
         nd.y = y[k];
@@ -260,8 +272,6 @@ sdd_status build_plan(sdd_ctx* c, Plan& P, const double* x, const double* y, con
         nd.ctr = (uint32_t)k;
         nd.n_paths = (int32_t)np[k];
         nd.local = (int32_t)k;
-        nd.rec0 = rec;
-        rec += np[k];
         const bool bnd = x[k] <= 0.0 || x[k] >= 1.0 || y[k] <= 0.0 || y[k] >= 1.0;
         nd.task0 = (int32_t)P.tasks.size();
         if (bnd) {
@@ -316,7 +326,8 @@ sdd_status run_plan(sdd_ctx* c, Plan& P, double dt, int K, uint64_t seed, uint32
         a.step_ptr = step_ptr;
         if (rec) a.rec = *rec;
         CU(c, cudaMemsetAsync(P.d_queue.p, 0, sizeof(int), s));
-        const int grid = (int)std::min<int64_t>(P.grid, std::max<int64_t>(1, (P.ntasks * 32 + P.block - 1) / P.block));
+        const int64_t per_block = P.block / 32;
+        const int grid = (int)std::min<int64_t>(P.grid, std::max<int64_t>(1, (P.ntasks + per_block - 1) / per_block));
         if (ev_a) CU(c, cudaEventRecordWithFlags(ev_a, s, cudaEventRecordExternal));
         CU(c, launch_paths(a, exit_mode, rec != nullptr, grid, P.block, s));
         if (ev_b) CU(c, cudaEventRecordWithFlags(ev_b, s, cudaEventRecordExternal));
@@ -853,11 +864,11 @@ void sdd_destroy(sdd_ctx* c)
     delete c;  // device buffers are freed by their destructors
 }
 
-sdd_status sdd_rng_draw(uint64_t seed, uint32_t instance, const uint32_t* ctrs, int64_t count, uint32_t* words,
-                        float* normals, void* stream)
+sdd_status sdd_rng_draw(uint64_t seed, const uint32_t* ctrs, int64_t count, uint32_t* words, float* normals,
+                        void* stream)
 {
     if (count < 0 || (count > 0 && (!ctrs || !words))) return SDD_EINVAL;
-    cudaError_t e = launch_rng_draw(seed, instance, ctrs, count, words, normals, (cudaStream_t)stream);
+    cudaError_t e = launch_rng_draw(seed, ctrs, count, words, normals, (cudaStream_t)stream);
     return e == cudaSuccess ? SDD_OK : SDD_ECUDA;
 }
 

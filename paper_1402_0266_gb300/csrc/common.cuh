@@ -37,8 +37,8 @@ struct OutDev {
 struct NodeDev {
     double x, y;        // as given
     float xf, yf;       // start point of the paths (single precision)
-    int32_t inst;       // instance index (also xored into the Philox key)
-    uint32_t ctr;       // node word of the Philox counter
+    int32_t inst;       // instance index
+    uint32_t ctr;       // node word of the Philox counter (numbers the nodes of all instances)
     int32_t n_paths;
     int32_t task0;      // first task of this node
     int32_t ntasks;     // 0 for a node on the boundary
@@ -113,8 +113,8 @@ cudaError_t launch_prep_cells(const float* w, const double* xi, const double* et
 cudaError_t launch_winslow_faces(const float* w, int nx, int ny, double* faces64, cudaStream_t s);
 cudaError_t launch_faces32(const double* faces64, float* faces32, int n, cudaStream_t s);
 
-cudaError_t launch_rng_draw(uint64_t seed, uint32_t instance, const uint32_t* ctrs, long long count,
-                            uint32_t* words, float* normals, cudaStream_t s);
+cudaError_t launch_rng_draw(uint64_t seed, const uint32_t* ctrs, long long count, uint32_t* words, float* normals,
+                            cudaStream_t s);
 
 // Subdomain solve.
 struct SolveSys {

@@ -72,7 +72,7 @@ __device__ __forceinline__ float face_value(const InstDev& I, int field, int fac
 // Exit through the boundary between X_j = (x, y) and X_{j+1} = (xn, yn):
 // the segment is cut at the smallest crossing fraction over the violated
 // faces, ties to the face listed first (left, right, bottom, top).
-__device__ __noinline__ void plain_exit(const InstDev& I, float x, float y, float xn, float yn, int& face,
+__device__ __forceinline__ void plain_exit(const InstDev& I, float x, float y, float xn, float yn, int& face,
                                         float& yxi, float& yeta, float& xe, float& ye)
 {
     float best = 2.0f;
@@ -95,7 +95,7 @@ __device__ __noinline__ void plain_exit(const InstDev& I, float x, float y, floa
 // k is touched with probability exp(-d0 d1 / dt) (sigma^2 = 2); the faces
 // combine as 1 - prod (1 - p_k). On exit: the face of largest p_k, at the
 // projection of the sub-step midpoint.
-__device__ __noinline__ bool bridge_exit(const InstDev& I, float x, float y, float xn, float yn, float dt, float u,
+__device__ __forceinline__ bool bridge_exit(const InstDev& I, float x, float y, float xn, float yn, float dt, float u,
                                          int& face, float& yxi, float& yeta, float& xe, float& ye)
 {
     const float d0[4] = {x, 1.0f - x, y, 1.0f - y};
@@ -171,24 +171,32 @@ __device__ __forceinline__ long long warp_sum_ll(long long v)
 template <int MODE, bool RECORD>
 __global__ void __launch_bounds__(512) k_paths(const PathArgs a)
 {
+    __shared__ int s_group;
     const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
     const unsigned below = (1u << lane) - 1u;
     const uint32_t step = a.step_ptr ? *a.step_ptr : a.step_index;
     const int K = a.K;
     const float dt = a.dt;
+    const uint32_t k0 = a.key0, k1 = a.key1;
 
+    // The block takes one task per warp at a time; consecutive tasks belong to
+    // the same node, so the block's gathers share the node's neighbourhood in L1.
     for (;;) {
-        int t = 0;
-        if (lane == 0) t = atomicAdd(a.queue, 1);
-        t = __shfl_sync(FULL, t, 0);
-        if (t >= a.ntasks) return;
+        __syncthreads();  // every warp is done with the previous group
+        if (threadIdx.x == 0) s_group = atomicAdd(a.queue, nwarps);
+        __syncthreads();
+        const int group = s_group;
+        if (group >= a.ntasks) return;
+        const int t = group + warp;
+        if (t >= a.ntasks) continue;
 
         const Task task = a.tasks[t];
         const NodeDev& nd = a.nodes[task.node];
         const InstDev I = a.inst[nd.inst];
         const float x0 = nd.xf, y0 = nd.yf;
         const uint32_t nctr = nd.ctr;
-        const uint32_t k0 = a.key0, k1 = a.key1 ^ (uint32_t)nd.inst;
         const int end = task.path0 + task.npaths;
         int next = task.path0 + 32;
         int path = task.path0 + lane;
@@ -408,13 +416,13 @@ __global__ void k_finalize(const FinalArgs a)
     }
 }
 
-__global__ void k_rng_draw(uint64_t seed, uint32_t instance, const uint32_t* __restrict__ ctrs, long long count,
+__global__ void k_rng_draw(uint64_t seed, const uint32_t* __restrict__ ctrs, long long count,
                            uint32_t* __restrict__ words, float* __restrict__ normals)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= count) return;
     const uint4 c = make_uint4(ctrs[4 * i], ctrs[4 * i + 1], ctrs[4 * i + 2], ctrs[4 * i + 3]);
-    const uint4 r = philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32) ^ instance);
+    const uint4 r = philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
     words[4 * i + 0] = r.x;
     words[4 * i + 1] = r.y;
     words[4 * i + 2] = r.z;
@@ -474,13 +482,12 @@ cudaError_t launch_finalize(const FinalArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_rng_draw(uint64_t seed, uint32_t instance, const uint32_t* ctrs, long long count,
-                            uint32_t* words, float* normals, cudaStream_t s)
+cudaError_t launch_rng_draw(uint64_t seed, const uint32_t* ctrs, long long count, uint32_t* words, float* normals,
+                            cudaStream_t s)
 {
     if (count <= 0) return cudaSuccess;
     const int block = 256;
-    k_rng_draw<<<(unsigned)((count + block - 1) / block), block, 0, s>>>(seed, instance, ctrs, count, words,
-                                                                         normals);
+    k_rng_draw<<<(unsigned)((count + block - 1) / block), block, 0, s>>>(seed, ctrs, count, words, normals);
     return cudaGetLastError();
 }
 

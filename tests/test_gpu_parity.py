@@ -50,9 +50,9 @@ def test_rng_words_bit_exact_and_normals_close(sdd, oracle_mod):
     rng = np.random.default_rng(11)
     ctr = rng.integers(0, 2 ** 32, size=(200000, 4), dtype=np.uint64).astype(np.uint32)
     ctr[:4] = [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [1, 2, 3, 4], [7, 0, 0, 1]]
-    for seed, inst in ((0, 0), (0x0123456789ABCDEF, 3), (2 ** 64 - 1, 0xFFFFFFFF)):
-        wg, zg = sdd.sdd_rng_draw(seed, inst, ctr)
-        wo, zo = oracle_mod.draw(seed, inst, ctr)
+    for seed in (0, 0x0123456789ABCDEF, 2 ** 64 - 1):
+        wg, zg = sdd.sdd_rng_draw(seed, ctr)
+        wo, zo = oracle_mod.draw(seed, ctr)
         np.testing.assert_array_equal(wg.cpu().numpy().view(np.uint32), wo)
         err = np.abs(zg.cpu().numpy().astype(np.float64) - zo)
         assert np.quantile(err, 0.9999) < 1e-5, np.quantile(err, 0.9999)
