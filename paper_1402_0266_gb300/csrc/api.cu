@@ -105,7 +105,7 @@ struct sdd_ctx {
     DevBuf<double> cx, cy, dg, rhs0;
     DevBuf<float> cxf, cyf, dgf, dinvf, r32[2], p32[2], q32[2], d32[2];
     std::vector<SolveSys> systems;
-    int solve_cluster = 1;
+    int solve_cluster = 1, solve_upt = 0, solve_rows_max = 0, solve_mx_max = 0;
     DevBuf<SolveSys> d_systems;
     DevBuf<int32_t> d_iters;
 
@@ -386,6 +386,21 @@ sdd_status setup_solver(sdd_ctx* c)
                          cudaMemcpyHostToDevice));
     CU(c, c->d_iters.alloc(std::max<size_t>(c->systems.size(), 1)));
     c->solve_cluster = c->systems.empty() ? 1 : solve_cluster_size((int)c->systems.size(), min_rows, c->sm_count);
+    // band sizes of the blocks, for the register-resident kernel
+    int band_max = 0, rows_max = 0, mx_max = 0;
+    for (const SolveSys& S : c->systems) {
+        const int my = S.j1 - S.j0, mx = S.i1 - S.i0;
+        for (int rk = 0; rk < c->solve_cluster; ++rk) {
+            const int rows = S.j0 + (my * (rk + 1)) / c->solve_cluster - (S.j0 + (my * rk) / c->solve_cluster);
+            rows_max = std::max(rows_max, rows);
+            band_max = std::max(band_max, rows * mx);
+        }
+        mx_max = std::max(mx_max, mx);
+    }
+    c->solve_upt = solve_reg_upt(band_max);
+    c->solve_rows_max = rows_max;
+    c->solve_mx_max = mx_max;
+    if ((size_t)(rows_max + 2) * (mx_max + 2) * sizeof(float) > 200 * 1024) c->solve_upt = 0;
     return SDD_OK;
 }
 
@@ -451,7 +466,7 @@ sdd_status enqueue_solve(sdd_ctx* c, double Dt, const double* ix, const double* 
     a.inner_tol = 1e-4f;
     a.iters = c->d_iters.p;
     a.status = c->d_status.p;
-    CU(c, launch_pcg(a, s));
+    CU(c, launch_pcg(a, c->solve_upt, c->solve_rows_max, c->solve_mx_max, s));
     return SDD_OK;
 }
 

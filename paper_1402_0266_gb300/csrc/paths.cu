@@ -125,17 +125,6 @@ __device__ __forceinline__ bool inside(float x, float y)
     return x > 0.0f && x < 1.0f && y > 0.0f && y < 1.0f;
 }
 
-// One Euler--Maruyama sub-step with increment (zx, zy) = sqrt(2 dt) N(0,1)^2.
-__device__ __forceinline__ void em_step(const InstDev& I, float x, float y, float dt, float zx, float zy, float& xn,
-                                        float& yn)
-{
-    const Cell c = locate(I, I.bcoef, x, y);
-    const float4 ax = __ldg(c.p);
-    const float4 ay = __ldg(c.p + 1);
-    xn = fmaf(eval(ax, c.s, c.t), dt, x) + zx;
-    yn = fmaf(eval(ay, c.s, c.t), dt, y) + zy;
-}
-
 struct Acc {
     float s, cs, q, cq;
     __device__ __forceinline__ void add(float v)
@@ -202,7 +191,17 @@ __global__ void __launch_bounds__(512) k_paths(const PathArgs a)
         int path = task.path0 + lane;
         bool alive = path < end;
         float x = x0, y = y0;
-        int m = 0;  // plain mode: sub-step pair index; bridge mode: sub-step index
+        int m = 0;  // draw index: the sub-step pair (plain mode) or the sub-step (bridge mode)
+        // normals of draw m, already scaled by sqrt(2 dt): pair (ax_, ay_) for the
+        // first sub-step, (bx_, by_) for the second (plain) or ub (bridge)
+        float zAx = 0.f, zAy = 0.f, zBx = 0.f, zBy = 0.f, ub = 1.f;
+        auto first_draw = [&]() {
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)path, nctr, 0u, step), k0, k1);
+            box_muller(r.x, r.y, a.bm_scale, zAx, zAy);
+            if (MODE == 0) box_muller(r.z, r.w, a.bm_scale, zBx, zBy);
+            else ub = uniform_pos(r.z);
+        };
+        if (alive) first_draw();
         Acc ax{0.f, 0.f, 0.f, 0.f}, ae{0.f, 0.f, 0.f, 0.f};
         int exits = 0, steps = 0;
 
@@ -211,57 +210,73 @@ __global__ void __launch_bounds__(512) k_paths(const PathArgs a)
                 bool done = false;
                 int code = -1, taken = 0;
                 float yxi = 0.f, yeta = 0.f, xe = 0.f, ye = 0.f;
-                const uint4 r = philox4x32_10(make_uint4((uint32_t)path, nctr, (uint32_t)m, step), k0, k1);
+                // sub-step A: gather, then the next draw's first rounds while the gather is in flight
+                const Cell cA = locate(I, I.bcoef, x, y);
+                const float4 gAx = __ldg(cA.p);
+                const float4 gAy = __ldg(cA.p + 1);
+                uint4 r = make_uint4((uint32_t)path, nctr, (uint32_t)(m + 1), step);
+                philox_rounds<0, 5>(r, k0, k1);
+                const float xa = fmaf(eval(gAx, cA.s, cA.t), dt, x) + zAx;
+                const float ya = fmaf(eval(gAy, cA.s, cA.t), dt, y) + zAy;
+                const bool outA = !inside(xa, ya);
                 if (MODE == 0) {
-                    float zx0, zy0, zx1, zy1;
-                    box_muller(r.x, r.y, a.bm_scale, zx0, zy0);
-                    box_muller(r.z, r.w, a.bm_scale, zx1, zy1);
-                    float xn, yn;
-                    em_step(I, x, y, dt, zx0, zy0, xn, yn);
-                    if (!inside(xn, yn)) {
-                        plain_exit(I, x, y, xn, yn, code, yxi, yeta, xe, ye);
+                    // sub-step B from the point A reached (or from X_j when A left: harmless, in bounds)
+                    const float xq = outA ? x : xa, yq = outA ? y : ya;
+                    const Cell cB = locate(I, I.bcoef, xq, yq);
+                    const float4 gBx = __ldg(cB.p);
+                    const float4 gBy = __ldg(cB.p + 1);
+                    philox_rounds<5, 10>(r, k0, k1);
+                    float nAx, nAy, nBx, nBy;
+                    box_muller(r.x, r.y, a.bm_scale, nAx, nAy);
+                    box_muller(r.z, r.w, a.bm_scale, nBx, nBy);
+                    const float xb = fmaf(eval(gBx, cB.s, cB.t), dt, xq) + zBx;
+                    const float yb = fmaf(eval(gBy, cB.s, cB.t), dt, yq) + zBy;
+                    const bool haveB = 2 * m + 1 < K;
+                    const bool outB = haveB && !outA && !inside(xb, yb);
+                    if (outA) {
+                        plain_exit(I, x, y, xa, ya, code, yxi, yeta, xe, ye);
                         done = true;
                         taken = 2 * m + 1;
+                    } else if (outB) {
+                        plain_exit(I, xa, ya, xb, yb, code, yxi, yeta, xe, ye);
+                        done = true;
+                        taken = 2 * m + 2;
                     } else {
-                        x = xn;
-                        y = yn;
-                        if (2 * m + 1 < K) {
-                            em_step(I, x, y, dt, zx1, zy1, xn, yn);
-                            if (!inside(xn, yn)) {
-                                plain_exit(I, x, y, xn, yn, code, yxi, yeta, xe, ye);
-                                done = true;
-                                taken = 2 * m + 2;
-                            } else {
-                                x = xn;
-                                y = yn;
-                            }
-                        }
+                        x = haveB ? xb : xa;
+                        y = haveB ? yb : ya;
                     }
+                    zAx = nAx;
+                    zAy = nAy;
+                    zBx = nBx;
+                    zBy = nBy;
                     ++m;
                     if (!done && 2 * m >= K) {
                         done = true;
                         taken = K;
                     }
                 } else {
-                    float zx, zy;
-                    box_muller(r.x, r.y, a.bm_scale, zx, zy);
-                    float xn, yn;
-                    em_step(I, x, y, dt, zx, zy, xn, yn);
-                    if (!inside(xn, yn)) {
-                        plain_exit(I, x, y, xn, yn, code, yxi, yeta, xe, ye);
+                    philox_rounds<5, 10>(r, k0, k1);
+                    float nAx, nAy;
+                    box_muller(r.x, r.y, a.bm_scale, nAx, nAy);
+                    const float nub = uniform_pos(r.z);
+                    if (outA) {
+                        plain_exit(I, x, y, xa, ya, code, yxi, yeta, xe, ye);
                         done = true;
                     } else {
                         const float dm0 = fminf(fminf(x, 1.0f - x), fminf(y, 1.0f - y));
-                        const float dm1 = fminf(fminf(xn, 1.0f - xn), fminf(yn, 1.0f - yn));
+                        const float dm1 = fminf(fminf(xa, 1.0f - xa), fminf(ya, 1.0f - ya));
                         if (dm0 * dm1 < a.bridge_cut &&
-                            bridge_exit(I, x, y, xn, yn, dt, uniform_pos(r.z), code, yxi, yeta, xe, ye)) {
+                            bridge_exit(I, x, y, xa, ya, dt, ub, code, yxi, yeta, xe, ye)) {
                             code += 4;
                             done = true;
                         } else {
-                            x = xn;
-                            y = yn;
+                            x = xa;
+                            y = ya;
                         }
                     }
+                    zAx = nAx;
+                    zAy = nAy;
+                    ub = nub;
                     ++m;
                     taken = m;
                     if (!done && m >= K) done = true;
@@ -302,6 +317,7 @@ __global__ void __launch_bounds__(512) k_paths(const PathArgs a)
                     x = x0;
                     y = y0;
                     m = 0;
+                    first_draw();
                 }
                 next += __popc(need);
             }

@@ -15,17 +15,26 @@
 
 namespace sdd {
 
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+// Rounds R0 .. R1-1 of Philox4x32-10 on counter state c; round r uses the key
+// (k0 + r W0, k1 + r W1). Splitting the ten rounds lets a caller place them
+// in the shadow of memory loads.
+template <int R0, int R1>
+__device__ __forceinline__ void philox_rounds(uint4& c, uint32_t k0, uint32_t k1)
 {
 #pragma unroll
-    for (int round = 0; round < 10; ++round) {
+    for (int r = R0; r < R1; ++r) {
+        const uint32_t kr0 = k0 + (uint32_t)r * 0x9E3779B9u;
+        const uint32_t kr1 = k1 + (uint32_t)r * 0xBB67AE85u;
         const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
         const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
-        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1,
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ kr0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ kr1,
                        (uint32_t)p0);
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
     }
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+    philox_rounds<0, 10>(c, k0, k1);
     return c;
 }
 

@@ -271,6 +271,241 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_pcg_cluster(const SolveArgs a
     cl.sync();  // no block leaves while others may still read its shared memory
 }
 
+// Register-resident variant for systems whose band fits in the block: each
+// thread keeps UPT unknowns (coefficients, r, p, s, w, d) in registers; the
+// preconditioned residual u lives in shared memory with one halo row above
+// and below, copied from the neighbouring blocks through distributed shared
+// memory. The inner iteration is the Chronopoulos--Gear form of
+// preconditioned CG (one fused reduction per iteration: (r,u), (w,u), (r,r)),
+// so an iteration costs two cluster barriers.
+template <int UPT>
+__global__ void __launch_bounds__(SOLVE_THREADS) k_pcg_reg(const SolveArgs a, int rows_max)
+{
+    extern __shared__ float u_s[];  // (rows_max + 2) x (mx + 2), zero frame
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks();
+    const int rank = (int)cl.block_rank();
+    const SolveSys S = a.sys[blockIdx.x / C];
+    const int nx = a.nx;
+    const int mx = S.i1 - S.i0, my = S.j1 - S.j0;
+    const int row0 = S.j0 + (my * rank) / C, row1 = S.j0 + (my * (rank + 1)) / C;
+    const int rows = row1 - row0;
+    const int m = rows * mx;
+    const int W = mx + 2;  // shared row pitch
+    double* __restrict__ x = a.x[S.field];
+    const double* __restrict__ rhs = a.rhs0 + (long long)S.field * nx * a.ny;
+
+    __shared__ ClusterSlots<double> red64[2];
+    __shared__ ClusterSlots<float> red32[2];
+    __shared__ float red3_part[2][3][SOLVE_WARPS];
+    __shared__ float red3_block[2][3];
+    __shared__ float red3_total[2][3];
+    int seq = 0;
+
+    // zero the frame (halo rows and columns stay zero where they are Dirichlet nodes)
+    for (int k = threadIdx.x; k < (rows_max + 2) * W; k += SOLVE_THREADS) u_s[k] = 0.0f;
+
+    long long n_[UPT];
+    int sidx[UPT];
+    bool own[UPT];
+    float cw[UPT], ce[UPT], cs[UPT], cn[UPT], dgv[UPT], dinv[UPT];
+    float r[UPT], p[UPT], sv[UPT], w[UPT], d[UPT];
+#pragma unroll
+    for (int k = 0; k < UPT; ++k) {
+        const int u = threadIdx.x + k * SOLVE_THREADS;
+        own[k] = u < m;
+        const int uu = own[k] ? u : 0;
+        const int lr = uu / mx, lc = uu % mx;
+        n_[k] = (long long)(row0 + lr) * nx + (S.i0 + lc);
+        sidx[k] = (lr + 1) * W + (lc + 1);
+        if (own[k]) {
+            const long long n = n_[k];
+            cw[k] = a.cxf[n - 1];
+            ce[k] = a.cxf[n];
+            cs[k] = a.cyf[n - nx];
+            cn[k] = a.cyf[n];
+            dgv[k] = a.dgf[n];
+            dinv[k] = a.dinvf[n];
+        } else {
+            cw[k] = ce[k] = cs[k] = cn[k] = dgv[k] = dinv[k] = 0.0f;
+        }
+        r[k] = p[k] = sv[k] = w[k] = d[k] = 0.0f;
+    }
+
+    // three-value cluster sum (two alternating slot sets, as cluster_sum2)
+    auto sum3 = [&](float& v0, float& v1, float& v2) {
+        const int b = seq & 1;
+        ++seq;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            v0 += __shfl_xor_sync(0xffffffffu, v0, off);
+            v1 += __shfl_xor_sync(0xffffffffu, v1, off);
+            v2 += __shfl_xor_sync(0xffffffffu, v2, off);
+        }
+        if (lane == 0) {
+            red3_part[b][0][warp] = v0;
+            red3_part[b][1][warp] = v1;
+            red3_part[b][2][warp] = v2;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+            for (int q = 0; q < SOLVE_WARPS; ++q) {
+                t0 += red3_part[b][0][q];
+                t1 += red3_part[b][1][q];
+                t2 += red3_part[b][2][q];
+            }
+            red3_block[b][0] = t0;
+            red3_block[b][1] = t1;
+            red3_block[b][2] = t2;
+        }
+        cl.sync();
+        if (threadIdx.x == 0) {
+            float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+            for (int q = 0; q < C; ++q) {
+                const float* rem = cl.map_shared_rank(&red3_block[b][0], q);
+                t0 += rem[0];
+                t1 += rem[1];
+                t2 += rem[2];
+            }
+            red3_total[b][0] = t0;
+            red3_total[b][1] = t1;
+            red3_total[b][2] = t2;
+        }
+        __syncthreads();
+        v0 = red3_total[b][0];
+        v1 = red3_total[b][1];
+        v2 = red3_total[b][2];
+    };
+
+    // u is in shared memory: publish, then copy the neighbours' edge rows into the halo rows
+    auto exchange_u = [&]() {
+        cl.sync();
+        if (C > 1) {
+            if (rank > 0) {
+                const float* src = cl.map_shared_rank(u_s, rank - 1);
+                const int rows_below = ((my * rank) / C) - ((my * (rank - 1)) / C);
+                for (int c = threadIdx.x; c < mx; c += SOLVE_THREADS) u_s[c + 1] = src[rows_below * W + c + 1];
+            }
+            if (rank < C - 1) {
+                const float* src = cl.map_shared_rank(u_s, rank + 1);
+                for (int c = threadIdx.x; c < mx; c += SOLVE_THREADS) u_s[(rows + 1) * W + c + 1] = src[1 * W + c + 1];
+            }
+        }
+        __syncthreads();
+    };
+
+    auto apply_A = [&](int k) -> float {
+        const int q = sidx[k];
+        return dgv[k] * u_s[q] - cw[k] * u_s[q - 1] - ce[k] * u_s[q + 1] - cs[k] * u_s[q - W] - cn[k] * u_s[q + W];
+    };
+
+    // ||b||^2
+    double bb = 0.0, unused = 0.0;
+#pragma unroll
+    for (int k = 0; k < UPT; ++k) {
+        if (!own[k]) continue;
+        const long long n = n_[k];
+        const int i = (int)(n % nx), j = (int)(n / nx);
+        double b = rhs[n];
+        if (i == S.i0) b += a.cx[n - 1] * x[n - 1];
+        if (i == S.i1 - 1) b += a.cx[n] * x[n + 1];
+        if (j == S.j0) b += a.cy[n - nx] * x[n - nx];
+        if (j == S.j1 - 1) b += a.cy[n] * x[n + nx];
+        bb += b * b;
+    }
+    cluster_sum2(cl, red64, seq, bb, unused);
+    const double stop2 = a.rtol * a.rtol * bb;
+
+    int total = 0;
+    bool converged = false;
+    for (int outer = 0; outer < a.max_outer; ++outer) {
+        double rr64 = 0.0, unused64 = 0.0;
+#pragma unroll
+        for (int k = 0; k < UPT; ++k) {
+            if (!own[k]) continue;
+            const long long n = n_[k];
+            const double ax = a.dg[n] * x[n] - a.cx[n - 1] * x[n - 1] - a.cx[n] * x[n + 1] -
+                              a.cy[n - nx] * x[n - nx] - a.cy[n] * x[n + nx];
+            const double res = rhs[n] - ax;
+            rr64 += res * res;
+            r[k] = (float)res;
+            d[k] = 0.0f;
+            u_s[sidx[k]] = r[k] * dinv[k];
+        }
+        cluster_sum2(cl, red64, seq, rr64, unused64);
+        if (rr64 <= stop2) {
+            converged = true;
+            break;
+        }
+        if (total >= a.max_iter) break;
+        // Chronopoulos--Gear PCG on A d = r from d = 0
+        exchange_u();
+        float gam = 0.f, del = 0.f, rr = 0.f;
+#pragma unroll
+        for (int k = 0; k < UPT; ++k) {
+            if (!own[k]) continue;
+            w[k] = apply_A(k);
+            const float uk = u_s[sidx[k]];
+            gam += r[k] * uk;
+            del += w[k] * uk;
+            rr += r[k] * r[k];
+            p[k] = 0.f;
+            sv[k] = 0.f;
+        }
+        sum3(gam, del, rr);
+        if (!(rr > 0.0f) || !(del > 0.0f)) continue;
+        const float stop_in = a.inner_tol * a.inner_tol * rr;
+        float alpha = gam / del, beta = 0.0f, gam_old = gam;
+        while (total < a.max_iter) {
+            ++total;
+#pragma unroll
+            for (int k = 0; k < UPT; ++k) {
+                if (!own[k]) continue;
+                const float uk = u_s[sidx[k]];
+                p[k] = uk + beta * p[k];
+                sv[k] = w[k] + beta * sv[k];
+                d[k] += alpha * p[k];
+                r[k] -= alpha * sv[k];
+            }
+            __syncthreads();  // every read of u is done before it is overwritten
+#pragma unroll
+            for (int k = 0; k < UPT; ++k)
+                if (own[k]) u_s[sidx[k]] = r[k] * dinv[k];
+            exchange_u();
+            gam = 0.f;
+            del = 0.f;
+            rr = 0.f;
+#pragma unroll
+            for (int k = 0; k < UPT; ++k) {
+                if (!own[k]) continue;
+                w[k] = apply_A(k);
+                const float uk = u_s[sidx[k]];
+                gam += r[k] * uk;
+                del += w[k] * uk;
+                rr += r[k] * r[k];
+            }
+            sum3(gam, del, rr);
+            if (rr <= stop_in) break;
+            beta = gam / gam_old;
+            alpha = gam / (del - beta * gam / alpha);
+            gam_old = gam;
+        }
+        // x += d in double precision; the next residual reads the neighbours' x
+#pragma unroll
+        for (int k = 0; k < UPT; ++k)
+            if (own[k]) x[n_[k]] += (double)d[k];
+        cl.sync();
+    }
+    if (threadIdx.x == 0 && rank == 0) {
+        a.iters[blockIdx.x / C] = converged ? total : a.max_iter + 1;
+        if (!converged) atomicOr(a.status, STATUS_NOCONV);
+    }
+    (void)red32;
+    cl.sync();  // no block leaves while others may still read its shared memory
+}
+
 __global__ void k_bump_step(uint32_t* step)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) *step += 1u;
@@ -329,22 +564,60 @@ int solve_cluster_size(int nsys, int min_rows, int sm_count)
     return c;
 }
 
-cudaError_t launch_pcg(const SolveArgs& a, cudaStream_t s)
+static cudaLaunchConfig_t cluster_config(const SolveArgs& a, size_t smem, cudaStream_t s, cudaLaunchAttribute* at)
 {
-    if (a.nsys <= 0) return cudaSuccess;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(a.nsys * a.cluster));
     cfg.blockDim = dim3(SOLVE_THREADS);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = (unsigned)a.cluster;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_pcg_cluster, a);
+    return cfg;
+}
+
+template <int UPT>
+static cudaError_t launch_reg(const SolveArgs& a, int rows_max, int max_mx, cudaStream_t s)
+{
+    const size_t smem = (size_t)(rows_max + 2) * (size_t)(max_mx + 2) * sizeof(float);
+    if (a.cluster > 8) cudaFuncSetAttribute(k_pcg_reg<UPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_pcg_reg<UPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchAttribute at[1];
+    cudaLaunchConfig_t cfg = cluster_config(a, smem, s, at);
+    return cudaLaunchKernelEx(&cfg, k_pcg_reg<UPT>, a, rows_max);
+}
+
+// Unknowns per thread of the register-resident kernel for these systems
+// (0: too large, use the general kernel).
+int solve_reg_upt(int max_band_unknowns)
+{
+    const int need = (max_band_unknowns + SOLVE_THREADS - 1) / SOLVE_THREADS;
+    if (need <= 1) return 1;
+    if (need <= 2) return 2;
+    if (need <= 4) return 4;
+    return 0;
+}
+
+cudaError_t launch_pcg(const SolveArgs& a, int upt, int rows_max, int max_mx, cudaStream_t s)
+{
+    if (a.nsys <= 0) return cudaSuccess;
+    switch (upt) {
+    case 1: return launch_reg<1>(a, rows_max, max_mx, s);
+    case 2: return launch_reg<2>(a, rows_max, max_mx, s);
+    case 4: return launch_reg<4>(a, rows_max, max_mx, s);
+    default: {
+        cudaLaunchAttribute at[1];
+        cudaLaunchConfig_t cfg = cluster_config(a, 0, s, at);
+        return cudaLaunchKernelEx(&cfg, k_pcg_cluster, a);
+    }
+    }
 }
 
 cudaError_t launch_bump_step(uint32_t* step, cudaStream_t s)
