@@ -173,6 +173,7 @@ sdd_status upload_inst(sdd_ctx* c)
     I.sy = (float)(c->ny - 1);
     I.gxmax = below((float)(c->nx - 1));
     I.gymax = below((float)(c->ny - 1));
+    I.cell_bias = 0x4B000000u * (uint32_t)c->nx;
     CU(c, c->d_inst.alloc(1));
     CU(c, cudaMemcpy(c->d_inst.p, &I, sizeof I, cudaMemcpyHostToDevice));
     return SDD_OK;

@@ -13,14 +13,15 @@ namespace sdd {
 
 // Geometry and field tables of one instance, as the path kernel reads them.
 struct InstDev {
-    const float4* bcoef;   // 2 float4 per cell: bilinear coefficients of b_x, then b_y
-    const float4* fcoef;   // 2 float4 per cell: bilinear coefficients of xi, then eta
+    const float4* bcoef;   // 2 float4 per cell: (a0x, a0y, a1x, a1y), (a2x, a2y, a3x, a3y) of b = (b_x, b_y)
+    const float4* fcoef;   // 2 float4 per cell: the same for (xi, eta)
     const float* faces32;  // face data, single precision (layout of sdd.h)
     const double* faces64; // face data, double precision
     int32_t nx, ny;
     float sx, sy;          // nx - 1, ny - 1 (inverse spacings)
     float gxmax, gymax;    // largest floats below nx - 1, ny - 1
-    int32_t pad0, pad1;
+    uint32_t cell_bias;    // 0x4B000000 * nx (mod 2^32): cell index from the float bits of 2^23 + floor(g)
+    int32_t pad0;
 };
 
 // Output arrays of one instance (device pointers; any may be null).

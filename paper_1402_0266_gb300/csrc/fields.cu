@@ -7,8 +7,8 @@
 //  * per cell, the bilinear interpolant of b and of (xi, eta) written as
 //    a0 + a1 s + a2 t + a3 s t over the cell's local coordinates (s, t), with
 //    a0 = f00, a1 = f10 - f00, a2 = f01 - f00, a3 = f11 - f10 - f01 + f00,
-//    formed in double and stored in single precision (Sec. 4: bilinear
-//    interpolation between grid points);
+//    formed in double and stored in single precision, the two components
+//    interleaved (Sec. 4: bilinear interpolation between grid points);
 //  * the boundary data of Sec. 3: xi = 0 / 1 on x = 0 / 1, eta = 0 / 1 on
 //    y = 0 / 1, and on the other faces the 1D Winslow solution
 //    int_0^s w / int_0^1 w (cumulative trapezoid, double precision).
@@ -42,9 +42,15 @@ __device__ __forceinline__ double2 node_drift(const float* __restrict__ w, int n
     return make_double2(-wx / wc, -wy / wc);
 }
 
-__device__ __forceinline__ float4 bilinear_coefs(double f00, double f10, double f01, double f11)
+// Bilinear coefficients of two fields u, v on one cell, interleaved so that one
+// paired single-precision FMA evaluates both: (a0u, a0v, a1u, a1v) and
+// (a2u, a2v, a3u, a3v).
+__device__ __forceinline__ void bilinear_coefs2(double u00, double u10, double u01, double u11, double v00,
+                                                double v10, double v01, double v11, float4& lo, float4& hi)
 {
-    return make_float4((float)f00, (float)(f10 - f00), (float)(f01 - f00), (float)((f11 - f10) - (f01 - f00)));
+    lo = make_float4((float)u00, (float)v00, (float)(u10 - u00), (float)(v10 - v00));
+    hi = make_float4((float)(u01 - u00), (float)(v01 - v00), (float)((u11 - u10) - (u01 - u00)),
+                     (float)((v11 - v10) - (v01 - v00)));
 }
 
 __device__ __forceinline__ bool bad_w(float v) { return !(v > 0.0f) || !isfinite(v); }
@@ -70,12 +76,11 @@ __global__ void k_prep_cells(const float* __restrict__ w, const double* __restri
     const double2 b01 = node_drift(w, nx, ny, ix, iy + 1, rx, ry);
     const double2 b11 = node_drift(w, nx, ny, ix + 1, iy + 1, rx, ry);
     const long long cell = (long long)iy * (nx - 1) + ix;
-    bcoef[2 * cell + 0] = bilinear_coefs(b00.x, b10.x, b01.x, b11.x);
-    bcoef[2 * cell + 1] = bilinear_coefs(b00.y, b10.y, b01.y, b11.y);
+    bilinear_coefs2(b00.x, b10.x, b01.x, b11.x, b00.y, b10.y, b01.y, b11.y, bcoef[2 * cell + 0], bcoef[2 * cell + 1]);
     const long long n00 = (long long)iy * nx + ix;
     const long long n01 = n00 + nx;
-    fcoef[2 * cell + 0] = bilinear_coefs(xi[n00], xi[n00 + 1], xi[n01], xi[n01 + 1]);
-    fcoef[2 * cell + 1] = bilinear_coefs(eta[n00], eta[n00 + 1], eta[n01], eta[n01 + 1]);
+    bilinear_coefs2(xi[n00], xi[n00 + 1], xi[n01], xi[n01 + 1], eta[n00], eta[n00 + 1], eta[n01], eta[n01 + 1],
+                    fcoef[2 * cell + 0], fcoef[2 * cell + 1]);
 }
 
 // Cumulative trapezoid of one line of w, normalised by its total, by one warp:

@@ -26,31 +26,58 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// Positions and both components of every bilinear field travel as float2 so
+// that GB300's paired single-precision instructions (FFMA2, FADD2, FMUL2)
+// handle x and y together.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
 struct Cell {
-    const float4* p;
-    float s, t;
+    const float4* p;  // the cell's two coefficient records
+    float2 st;        // local coordinates (s, t) in [0, 1)
 };
 
-// Cell of (x, y) and local coordinates. floor() through a directed add of
-// 2^23: for 0 <= g < 2^23, (g + 2^23) rounded down is 2^23 + floor(g) exactly.
-__device__ __forceinline__ Cell locate(const InstDev& I, const float4* base, float x, float y)
+// Cell of pos and local coordinates. floor() through a directed add of 2^23:
+// for 0 <= g < 2^23, (g + 2^23) rounded down is 2^23 + floor(g) exactly, and
+// its bits are 0x4B000000 + floor(g); cell_bias removes that offset from the
+// row-major cell index in 32-bit wrap-around arithmetic.
+__device__ __forceinline__ Cell locate(const InstDev& I, const float4* base, float2 pos)
 {
-    const float gx = fminf(x * I.sx, I.gxmax);
-    const float gy = fminf(y * I.sy, I.gymax);
-    const float tx = __fadd_rd(gx, 8388608.0f);
-    const float ty = __fadd_rd(gy, 8388608.0f);
-    const int ix = __float_as_int(tx) - 0x4B000000;
-    const int iy = __float_as_int(ty) - 0x4B000000;
+    float2 g = __fmul2_rn(pos, f2(I.sx, I.sy));
+    g.x = fminf(g.x, I.gxmax);
+    g.y = fminf(g.y, I.gymax);
+    const float2 t = __fadd2_rd(g, f2(8388608.0f, 8388608.0f));
+    const uint32_t cell = __float_as_uint(t.y) * (uint32_t)(I.nx - 1) + __float_as_uint(t.x) - I.cell_bias;
+    const float2 fl = __fadd2_rn(t, f2(-8388608.0f, -8388608.0f));    // floor(g), exact
     Cell c;
-    c.s = gx - (tx - 8388608.0f);
-    c.t = gy - (ty - 8388608.0f);
-    c.p = base + 2 * (iy * (I.nx - 1) + ix);
+    c.st = __ffma2_rn(fl, f2(-1.0f, -1.0f), g);                        // g - floor(g), exact
+    c.p = base + 2 * (size_t)cell;
     return c;
 }
 
-__device__ __forceinline__ float eval(const float4& a, float s, float t)
+// Both components of a bilinear field from the cell's records
+// lo = (a0u, a0v, a1u, a1v), hi = (a2u, a2v, a3u, a3v): (a0 + a1 s) + t (a2 + a3 s).
+__device__ __forceinline__ float2 eval2(const float4& lo, const float4& hi, float2 st)
 {
-    return fmaf(t, fmaf(s, a.w, a.z), fmaf(s, a.y, a.x));
+    const float2 ss = f2(st.x, st.x), tt = f2(st.y, st.y);
+    const float2 r = __ffma2_rn(f2(lo.z, lo.w), ss, f2(lo.x, lo.y));
+    const float2 q = __ffma2_rn(f2(hi.z, hi.w), ss, f2(hi.x, hi.y));
+    return __ffma2_rn(q, tt, r);
+}
+
+// One Euler--Maruyama sub-step from pos with increment z = sqrt(2 dt) N(0,1)^2:
+// pos + b(pos) dt + z, b bilinear from the cell's drift records.
+__device__ __forceinline__ float2 em(const float4& lo, const float4& hi, float2 st, float2 pos, float2 dt2, float2 z)
+{
+    return __fadd2_rn(__ffma2_rn(eval2(lo, hi, st), dt2, pos), z);
+}
+
+// Strictly inside the unit square: x - x^2 > 0 and y - y^2 > 0. Each is one
+// rounding of the exact value, whose sign it keeps (barring underflow below
+// 2^-126, which no position of a path reaches).
+__device__ __forceinline__ bool inside2(float2 p)
+{
+    const float2 q = __ffma2_rn(f2(-p.x, -p.y), p, p);
+    return fminf(q.x, q.y) > 0.0f;
 }
 
 // Linear interpolation of face `face` of `field` at tangential coordinate s.
@@ -120,11 +147,6 @@ __device__ __forceinline__ bool bridge_exit(const InstDev& I, float x, float y, 
     return true;
 }
 
-__device__ __forceinline__ bool inside(float x, float y)
-{
-    return x > 0.0f && x < 1.0f && y > 0.0f && y < 1.0f;
-}
-
 struct Acc {
     float s, cs, q, cq;
     __device__ __forceinline__ void add(float v)
@@ -190,16 +212,21 @@ __global__ void __launch_bounds__(512) k_paths(const PathArgs a)
         int next = task.path0 + 32;
         int path = task.path0 + lane;
         bool alive = path < end;
-        float x = x0, y = y0;
+        float2 pos = f2(x0, y0);
         int m = 0;  // draw index: the sub-step pair (plain mode) or the sub-step (bridge mode)
-        // normals of draw m, already scaled by sqrt(2 dt): pair (ax_, ay_) for the
-        // first sub-step, (bx_, by_) for the second (plain) or ub (bridge)
-        float zAx = 0.f, zAy = 0.f, zBx = 0.f, zBy = 0.f, ub = 1.f;
+        // normals of draw m, already scaled by sqrt(2 dt): zA for the first
+        // sub-step, zB for the second (plain mode); ub the bridge uniform
+        float2 zA = f2(0.f, 0.f), zB = f2(0.f, 0.f);
+        float ub = 1.f;
+        const float2 dt2 = f2(dt, dt);
         auto first_draw = [&]() {
             const uint4 r = philox4x32_10(make_uint4((uint32_t)path, nctr, 0u, step), k0, k1);
-            box_muller(r.x, r.y, a.bm_scale, zAx, zAy);
-            if (MODE == 0) box_muller(r.z, r.w, a.bm_scale, zBx, zBy);
-            else ub = uniform_pos(r.z);
+            if (MODE == 0) {
+                box_muller2(r, a.bm_scale, zA, zB);
+            } else {
+                box_muller(r.x, r.y, a.bm_scale, zA.x, zA.y);
+                ub = uniform_pos(r.z);
+            }
         };
         if (alive) first_draw();
         Acc ax{0.f, 0.f, 0.f, 0.f}, ae{0.f, 0.f, 0.f, 0.f};
@@ -211,44 +238,38 @@ __global__ void __launch_bounds__(512) k_paths(const PathArgs a)
                 int code = -1, taken = 0;
                 float yxi = 0.f, yeta = 0.f, xe = 0.f, ye = 0.f;
                 // sub-step A: gather, then the next draw's first rounds while the gather is in flight
-                const Cell cA = locate(I, I.bcoef, x, y);
-                const float4 gAx = __ldg(cA.p);
-                const float4 gAy = __ldg(cA.p + 1);
+                const Cell cA = locate(I, I.bcoef, pos);
+                const float4 gA0 = __ldg(cA.p);
+                const float4 gA1 = __ldg(cA.p + 1);
                 uint4 r = make_uint4((uint32_t)path, nctr, (uint32_t)(m + 1), step);
                 philox_rounds<0, 5>(r, k0, k1);
-                const float xa = fmaf(eval(gAx, cA.s, cA.t), dt, x) + zAx;
-                const float ya = fmaf(eval(gAy, cA.s, cA.t), dt, y) + zAy;
-                const bool outA = !inside(xa, ya);
+                const float2 pa = em(gA0, gA1, cA.st, pos, dt2, zA);
+                const bool outA = !inside2(pa);
                 if (MODE == 0) {
                     // sub-step B from the point A reached (or from X_j when A left: harmless, in bounds)
-                    const float xq = outA ? x : xa, yq = outA ? y : ya;
-                    const Cell cB = locate(I, I.bcoef, xq, yq);
-                    const float4 gBx = __ldg(cB.p);
-                    const float4 gBy = __ldg(cB.p + 1);
+                    const float2 pq = outA ? pos : pa;
+                    const Cell cB = locate(I, I.bcoef, pq);
+                    const float4 gB0 = __ldg(cB.p);
+                    const float4 gB1 = __ldg(cB.p + 1);
                     philox_rounds<5, 10>(r, k0, k1);
-                    float nAx, nAy, nBx, nBy;
-                    box_muller(r.x, r.y, a.bm_scale, nAx, nAy);
-                    box_muller(r.z, r.w, a.bm_scale, nBx, nBy);
-                    const float xb = fmaf(eval(gBx, cB.s, cB.t), dt, xq) + zBx;
-                    const float yb = fmaf(eval(gBy, cB.s, cB.t), dt, yq) + zBy;
+                    float2 nA, nB;
+                    box_muller2(r, a.bm_scale, nA, nB);
+                    const float2 pb = em(gB0, gB1, cB.st, pq, dt2, zB);
                     const bool haveB = 2 * m + 1 < K;
-                    const bool outB = haveB && !outA && !inside(xb, yb);
+                    const bool outB = haveB && !outA && !inside2(pb);
                     if (outA) {
-                        plain_exit(I, x, y, xa, ya, code, yxi, yeta, xe, ye);
+                        plain_exit(I, pos.x, pos.y, pa.x, pa.y, code, yxi, yeta, xe, ye);
                         done = true;
                         taken = 2 * m + 1;
                     } else if (outB) {
-                        plain_exit(I, xa, ya, xb, yb, code, yxi, yeta, xe, ye);
+                        plain_exit(I, pa.x, pa.y, pb.x, pb.y, code, yxi, yeta, xe, ye);
                         done = true;
                         taken = 2 * m + 2;
                     } else {
-                        x = haveB ? xb : xa;
-                        y = haveB ? yb : ya;
+                        pos = haveB ? pb : pa;
                     }
-                    zAx = nAx;
-                    zAy = nAy;
-                    zBx = nBx;
-                    zBy = nBy;
+                    zA = nA;
+                    zB = nB;
                     ++m;
                     if (!done && 2 * m >= K) {
                         done = true;
@@ -256,26 +277,24 @@ __global__ void __launch_bounds__(512) k_paths(const PathArgs a)
                     }
                 } else {
                     philox_rounds<5, 10>(r, k0, k1);
-                    float nAx, nAy;
-                    box_muller(r.x, r.y, a.bm_scale, nAx, nAy);
+                    float2 nA;
+                    box_muller(r.x, r.y, a.bm_scale, nA.x, nA.y);
                     const float nub = uniform_pos(r.z);
                     if (outA) {
-                        plain_exit(I, x, y, xa, ya, code, yxi, yeta, xe, ye);
+                        plain_exit(I, pos.x, pos.y, pa.x, pa.y, code, yxi, yeta, xe, ye);
                         done = true;
                     } else {
-                        const float dm0 = fminf(fminf(x, 1.0f - x), fminf(y, 1.0f - y));
-                        const float dm1 = fminf(fminf(xa, 1.0f - xa), fminf(ya, 1.0f - ya));
+                        const float dm0 = fminf(fminf(pos.x, 1.0f - pos.x), fminf(pos.y, 1.0f - pos.y));
+                        const float dm1 = fminf(fminf(pa.x, 1.0f - pa.x), fminf(pa.y, 1.0f - pa.y));
                         if (dm0 * dm1 < a.bridge_cut &&
-                            bridge_exit(I, x, y, xa, ya, dt, ub, code, yxi, yeta, xe, ye)) {
+                            bridge_exit(I, pos.x, pos.y, pa.x, pa.y, dt, ub, code, yxi, yeta, xe, ye)) {
                             code += 4;
                             done = true;
                         } else {
-                            x = xa;
-                            y = ya;
+                            pos = pa;
                         }
                     }
-                    zAx = nAx;
-                    zAy = nAy;
+                    zA = nA;
                     ub = nub;
                     ++m;
                     taken = m;
@@ -284,11 +303,12 @@ __global__ void __launch_bounds__(512) k_paths(const PathArgs a)
                 if (done) {
                     if (code < 0) {
                         // survived the mesh step: xi, eta of its start at the end point
-                        const Cell c = locate(I, I.fcoef, x, y);
-                        yxi = eval(__ldg(c.p), c.s, c.t);
-                        yeta = eval(__ldg(c.p + 1), c.s, c.t);
-                        xe = x;
-                        ye = y;
+                        const Cell c = locate(I, I.fcoef, pos);
+                        const float2 v = eval2(__ldg(c.p), __ldg(c.p + 1), c.st);
+                        yxi = v.x;
+                        yeta = v.y;
+                        xe = pos.x;
+                        ye = pos.y;
                     } else {
                         ++exits;
                     }
@@ -314,8 +334,7 @@ __global__ void __launch_bounds__(512) k_paths(const PathArgs a)
                 if (!alive && cand < end) {
                     path = cand;
                     alive = true;
-                    x = x0;
-                    y = y0;
+                    pos = f2(x0, y0);
                     m = 0;
                     first_draw();
                 }

@@ -61,6 +61,27 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float scale, 
     z1 = -r * s;
 }
 
+// Both Box--Muller pairs of one Philox block (words 0,1 -> zA, words 2,3 -> zB),
+// the arithmetic of the two pairs done with paired single-precision
+// instructions. Same values as two calls of box_muller.
+__device__ __forceinline__ void box_muller2(uint4 r, float scale, float2& zA, float2& zB)
+{
+    const float2 f1 = make_float2(__uint_as_float(0x3F800000u | (r.x & 0x7FFFFFu)),
+                                  __uint_as_float(0x3F800000u | (r.z & 0x7FFFFFu)));
+    const float2 f2 = make_float2(__uint_as_float(0x3F800000u | (r.y & 0x7FFFFFu)),
+                                  __uint_as_float(0x3F800000u | (r.w & 0x7FFFFFu)));
+    const float2 u1 = __ffma2_rn(f1, make_float2(-1.0f, -1.0f), make_float2(2.0f, 2.0f));   // exact
+    const float2 v = __fadd2_rn(f2, make_float2(-1.5f, -1.5f));                            // exact
+    const float2 l = __fmul2_rn(make_float2(__log2f(u1.x), __log2f(u1.y)), make_float2(scale, scale));
+    const float ra = sqrt_approx(l.x), rb = sqrt_approx(l.y);
+    const float2 ang = __fmul2_rn(v, make_float2(6.28318530717958647692f, 6.28318530717958647692f));
+    float sa, ca, sb, cb;
+    __sincosf(ang.x, &sa, &ca);
+    __sincosf(ang.y, &sb, &cb);
+    zA = __fmul2_rn(make_float2(-ra, -ra), make_float2(ca, sa));
+    zB = __fmul2_rn(make_float2(-rb, -rb), make_float2(cb, sb));
+}
+
 __device__ __forceinline__ float uniform_pos(uint32_t w)
 {
     // (1 + m 2^-23) - (1 - 2^-23) = (m + 1) 2^-23, exact
