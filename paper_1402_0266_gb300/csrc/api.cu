@@ -321,8 +321,7 @@ sdd_status run_plan(sdd_ctx* c, Plan& P, double dt, int K, uint64_t seed, uint32
         a.dt = (float)dt;
         a.bm_scale = (float)(-4.0 * dt * std::log(2.0));
         a.bridge_cut = (float)(18.0 * dt);
-        a.key0 = (uint32_t)(seed & 0xffffffffu);
-        a.key1 = (uint32_t)(seed >> 32);
+        a.keys = philox_keys(seed);
         a.step_index = step_index;
         a.step_ptr = step_ptr;
         if (rec) a.rec = *rec;

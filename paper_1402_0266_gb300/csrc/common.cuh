@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "rng.cuh"
+
 namespace sdd {
 
 // Geometry and field tables of one instance, as the path kernel reads them.
@@ -81,7 +83,7 @@ struct PathArgs {
     float dt;
     float bm_scale;          // -4 dt ln 2: r = sqrt(bm_scale * log2(u1)) = sqrt(2 dt) sqrt(-2 ln u1)
     float bridge_cut;        // skip the bridge test when dmin0 * dmin1 exceeds this
-    uint32_t key0, key1;     // seed halves
+    PhiloxKeys keys;         // round keys of the seed
     uint32_t step_index;
     const uint32_t* step_ptr; // if non-null, read the step index here
     RecDev rec;
@@ -106,6 +108,7 @@ enum : int {
 
 // Launchers (defined in the .cu files; all asynchronous on `s`).
 cudaError_t launch_paths(const PathArgs& a, int exit_mode, bool record, int grid, int block, cudaStream_t s);
+// exit_mode 0 with an even number of sub-steps has its own kernel (no odd last pair)
 cudaError_t launch_finalize(const FinalArgs& a, cudaStream_t s);
 int path_kernel_blocks_per_sm(int exit_mode, bool record, int block);
 

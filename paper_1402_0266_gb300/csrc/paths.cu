@@ -18,7 +18,6 @@
 // then per warp in double precision; the per-node reduction over tasks runs in
 // a fixed order, so results do not depend on scheduling.
 #include "common.cuh"
-#include "rng.cuh"
 
 namespace sdd {
 
@@ -179,8 +178,10 @@ __device__ __forceinline__ long long warp_sum_ll(long long v)
     return v;
 }
 
+// MODE 0: the paper's test, sub-step pairs; MODE 1: with the bridge test;
+// MODE 2: as MODE 0 when K is even (every pair has both sub-steps).
 template <int MODE, bool RECORD>
-__global__ void __launch_bounds__(512) k_paths(const PathArgs a)
+__global__ void __launch_bounds__(512, 2) k_paths(const PathArgs a)
 {
     __shared__ int s_group;
     const int lane = threadIdx.x & 31;
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(512) k_paths(const PathArgs a)
     const uint32_t step = a.step_ptr ? *a.step_ptr : a.step_index;
     const int K = a.K;
     const float dt = a.dt;
-    const uint32_t k0 = a.key0, k1 = a.key1;
+    constexpr bool PAIRS = MODE != 1;
 
     // The block takes one task per warp at a time; consecutive tasks belong to
     // the same node, so the block's gathers share the node's neighbourhood in L1.
@@ -220,8 +221,9 @@ __global__ void __launch_bounds__(512) k_paths(const PathArgs a)
         float ub = 1.f;
         const float2 dt2 = f2(dt, dt);
         auto first_draw = [&]() {
-            const uint4 r = philox4x32_10(make_uint4((uint32_t)path, nctr, 0u, step), k0, k1);
-            if (MODE == 0) {
+            uint4 r = make_uint4((uint32_t)path, nctr, 0u, step);
+            philox_rounds_rk<0, 10>(r, a.keys);
+            if (PAIRS) {
                 box_muller2(r, a.bm_scale, zA, zB);
             } else {
                 box_muller(r.x, r.y, a.bm_scale, zA.x, zA.y);
@@ -242,20 +244,20 @@ __global__ void __launch_bounds__(512) k_paths(const PathArgs a)
                 const float4 gA0 = __ldg(cA.p);
                 const float4 gA1 = __ldg(cA.p + 1);
                 uint4 r = make_uint4((uint32_t)path, nctr, (uint32_t)(m + 1), step);
-                philox_rounds<0, 5>(r, k0, k1);
+                philox_rounds_rk<0, 5>(r, a.keys);
                 const float2 pa = em(gA0, gA1, cA.st, pos, dt2, zA);
                 const bool outA = !inside2(pa);
-                if (MODE == 0) {
+                if (PAIRS) {
                     // sub-step B from the point A reached (or from X_j when A left: harmless, in bounds)
                     const float2 pq = outA ? pos : pa;
                     const Cell cB = locate(I, I.bcoef, pq);
                     const float4 gB0 = __ldg(cB.p);
                     const float4 gB1 = __ldg(cB.p + 1);
-                    philox_rounds<5, 10>(r, k0, k1);
+                    philox_rounds_rk<5, 10>(r, a.keys);
                     float2 nA, nB;
                     box_muller2(r, a.bm_scale, nA, nB);
                     const float2 pb = em(gB0, gB1, cB.st, pq, dt2, zB);
-                    const bool haveB = 2 * m + 1 < K;
+                    const bool haveB = (MODE == 2) || 2 * m + 1 < K;
                     const bool outB = haveB && !outA && !inside2(pb);
                     if (outA) {
                         plain_exit(I, pos.x, pos.y, pa.x, pa.y, code, yxi, yeta, xe, ye);
@@ -276,7 +278,7 @@ __global__ void __launch_bounds__(512) k_paths(const PathArgs a)
                         taken = K;
                     }
                 } else {
-                    philox_rounds<5, 10>(r, k0, k1);
+                    philox_rounds_rk<5, 10>(r, a.keys);
                     float2 nA;
                     box_muller(r.x, r.y, a.bm_scale, nA.x, nA.y);
                     const float nub = uniform_pos(r.z);
@@ -480,9 +482,10 @@ const void* kernel_ptr()
     return (const void*)k_paths<MODE, RECORD>;
 }
 
-const void* pick(int exit_mode, bool record)
+const void* pick(int mode, bool record)
 {
-    if (exit_mode == 0) return record ? kernel_ptr<0, true>() : kernel_ptr<0, false>();
+    if (mode == 0) return record ? kernel_ptr<0, true>() : kernel_ptr<0, false>();
+    if (mode == 2) return record ? kernel_ptr<2, true>() : kernel_ptr<2, false>();
     return record ? kernel_ptr<1, true>() : kernel_ptr<1, false>();
 }
 
@@ -491,17 +494,27 @@ const void* pick(int exit_mode, bool record)
 int path_kernel_blocks_per_sm(int exit_mode, bool record, int block)
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(exit_mode, record), block, 0) != cudaSuccess)
+    // the even-K kernel has the same footprint class; size the grid for the larger of the two
+    const int mode = exit_mode == 1 ? 1 : 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(mode, record), block, 0) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
 }
 
+static int kernel_mode(int exit_mode, int K) { return exit_mode == 1 ? 1 : ((K & 1) == 0 ? 2 : 0); }
+
 cudaError_t launch_paths(const PathArgs& a, int exit_mode, bool record, int grid, int block, cudaStream_t s)
 {
-    if (exit_mode == 0) {
+    switch (kernel_mode(exit_mode, a.K)) {
+    case 0:
         if (record) k_paths<0, true><<<grid, block, 0, s>>>(a);
         else k_paths<0, false><<<grid, block, 0, s>>>(a);
-    } else {
+        break;
+    case 2:
+        if (record) k_paths<2, true><<<grid, block, 0, s>>>(a);
+        else k_paths<2, false><<<grid, block, 0, s>>>(a);
+        break;
+    default:
         if (record) k_paths<1, true><<<grid, block, 0, s>>>(a);
         else k_paths<1, false><<<grid, block, 0, s>>>(a);
     }

@@ -38,6 +38,38 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
+// The same rounds with the round keys precomputed: rk[2r], rk[2r + 1] are
+// (k0 + r W0, k1 + r W1). Passed as kernel parameters, they are read straight
+// from the constant bank by the xor instructions.
+struct PhiloxKeys {
+    uint32_t rk[20];
+};
+
+__host__ __device__ inline PhiloxKeys philox_keys(uint64_t seed)
+{
+    PhiloxKeys k;
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        k.rk[2 * r] = k0;
+        k.rk[2 * r + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return k;
+}
+
+template <int R0, int R1>
+__device__ __forceinline__ void philox_rounds_rk(uint4& c, const PhiloxKeys& K)
+{
+#pragma unroll
+    for (int r = R0; r < R1; ++r) {
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ K.rk[2 * r], (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ K.rk[2 * r + 1], (uint32_t)p0);
+    }
+}
+
 __device__ __forceinline__ float sqrt_approx(float v)
 {
     float r;
