@@ -100,9 +100,9 @@ __global__ void k_scatter_iface(const double* __restrict__ vx, const double* __r
 }
 
 // Sum of two values over the whole cluster: warps by shuffles, the block's
-// warps by thread 0 in order, the cluster's blocks by lane 0 of warp 0
-// through distributed shared memory, in rank order; every thread of every
-// block gets the same bits. Two slot sets alternate between calls: a block
+// warps by thread 0 in order, the cluster's blocks by warp 0 (lane q reads
+// block q through distributed shared memory, then a fixed butterfly); every
+// thread of every block gets the same bits. Two slot sets alternate between calls: a block
 // rewrites a slot set only after the next call's cluster barrier, which every
 // block reaches only after it has read the slot set of the call before.
 template <typename T>
@@ -139,16 +139,24 @@ __device__ __forceinline__ void cluster_sum2(cg::cluster_group& cl, ClusterSlots
         S.block_part[1] = t1;
     }
     cl.sync();
-    if (threadIdx.x == 0) {
+    if (warp == 0) {
+        // lane q reads block q's partials (one round trip), then a fixed butterfly
         const int C = (int)cl.num_blocks();
         T t0 = 0, t1 = 0;
-        for (int r = 0; r < C; ++r) {
-            const T* rem = cl.map_shared_rank(&S.block_part[0], r);
-            t0 += rem[0];
-            t1 += rem[1];
+        if (lane < C) {
+            const T* rem = cl.map_shared_rank(&S.block_part[0], lane);
+            t0 = rem[0];
+            t1 = rem[1];
         }
-        S.total[0] = t0;
-        S.total[1] = t1;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            t0 += __shfl_xor_sync(0xffffffffu, t0, off);
+            t1 += __shfl_xor_sync(0xffffffffu, t1, off);
+        }
+        if (lane == 0) {
+            S.total[0] = t0;
+            S.total[1] = t1;
+        }
     }
     __syncthreads();
     v0 = S.total[0];
@@ -361,17 +369,25 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_pcg_reg(const SolveArgs a, in
             red3_block[b][2] = t2;
         }
         cl.sync();
-        if (threadIdx.x == 0) {
+        if (warp == 0) {
             float t0 = 0.f, t1 = 0.f, t2 = 0.f;
-            for (int q = 0; q < C; ++q) {
-                const float* rem = cl.map_shared_rank(&red3_block[b][0], q);
-                t0 += rem[0];
-                t1 += rem[1];
-                t2 += rem[2];
+            if (lane < C) {
+                const float* rem = cl.map_shared_rank(&red3_block[b][0], lane);
+                t0 = rem[0];
+                t1 = rem[1];
+                t2 = rem[2];
             }
-            red3_total[b][0] = t0;
-            red3_total[b][1] = t1;
-            red3_total[b][2] = t2;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                t0 += __shfl_xor_sync(0xffffffffu, t0, off);
+                t1 += __shfl_xor_sync(0xffffffffu, t1, off);
+                t2 += __shfl_xor_sync(0xffffffffu, t2, off);
+            }
+            if (lane == 0) {
+                red3_total[b][0] = t0;
+                red3_total[b][1] = t1;
+                red3_total[b][2] = t2;
+            }
         }
         __syncthreads();
         v0 = red3_total[b][0];
