@@ -400,7 +400,7 @@ sdd_status setup_solver(sdd_ctx* c)
     c->solve_upt = solve_reg_upt(band_max);
     c->solve_rows_max = rows_max;
     c->solve_mx_max = mx_max;
-    if ((size_t)(rows_max + 2) * (mx_max + 2) * sizeof(float) > 200 * 1024) c->solve_upt = 0;
+    if (2 * (size_t)(rows_max + 2) * (mx_max + 2) * sizeof(float) > 200 * 1024 || c->solve_cluster > 16) c->solve_upt = 0;
     return SDD_OK;
 }
 

@@ -280,16 +280,22 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_pcg_cluster(const SolveArgs a
 }
 
 // Register-resident variant for systems whose band fits in the block: each
-// thread keeps UPT unknowns (coefficients, r, p, s, w, d) in registers; the
-// preconditioned residual u lives in shared memory with one halo row above
-// and below, copied from the neighbouring blocks through distributed shared
-// memory. The inner iteration is the Chronopoulos--Gear form of
-// preconditioned CG (one fused reduction per iteration: (r,u), (w,u), (r,r)),
-// so an iteration costs two cluster barriers.
+// thread keeps UPT unknowns (coefficients and the CG vectors) in registers.
+// The inner iteration is the pipelined form of preconditioned CG (Ghysels &
+// Vanroose, "Hiding global synchronization latency in the preconditioned
+// conjugate gradient algorithm", 2014): per iteration one fused reduction
+// ((r,u), (w,u), (r,r)) and one product n = A m with m = M^-1 w. Blocks push
+// their reduction partials and the edge rows of m straight into the
+// neighbours' shared memory before a single cluster barrier; after it every
+// read is local. Both the partial slots and m are double-buffered by the
+// iteration's parity: a buffer is rewritten only after the next barrier,
+// which no block passes before every block has finished reading it.
 template <int UPT>
-__global__ void __launch_bounds__(SOLVE_THREADS) k_pcg_reg(const SolveArgs a, int rows_max)
+__global__ void __launch_bounds__(SOLVE_THREADS) k_pcg_pipe(const SolveArgs a, int rows_max)
 {
-    extern __shared__ float u_s[];  // (rows_max + 2) x (mx + 2), zero frame
+    extern __shared__ float m_s[];  // 2 x (rows_max + 2) x (mx + 2), zero frame
+    __shared__ float4 slots[2][16];  // [parity][block]: (gamma, delta, rr) partials pushed by every block
+    __shared__ float warp_part[3][SOLVE_WARPS];
     cg::cluster_group cl = cg::this_cluster();
     const int C = (int)cl.num_blocks();
     const int rank = (int)cl.block_rank();
@@ -299,35 +305,39 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_pcg_reg(const SolveArgs a, in
     const int row0 = S.j0 + (my * rank) / C, row1 = S.j0 + (my * (rank + 1)) / C;
     const int rows = row1 - row0;
     const int m = rows * mx;
-    const int W = mx + 2;  // shared row pitch
+    const int W = mx + 2;
+    const int plane = (rows_max + 2) * W;
+    const int rows_below = rank > 0 ? ((my * rank) / C) - ((my * (rank - 1)) / C) : 0;
     double* __restrict__ x = a.x[S.field];
     const double* __restrict__ rhs = a.rhs0 + (long long)S.field * nx * a.ny;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     __shared__ ClusterSlots<double> red64[2];
-    __shared__ ClusterSlots<float> red32[2];
-    __shared__ float red3_part[2][3][SOLVE_WARPS];
-    __shared__ float red3_block[2][3];
-    __shared__ float red3_total[2][3];
     int seq = 0;
 
-    // zero the frame (halo rows and columns stay zero where they are Dirichlet nodes)
-    for (int k = threadIdx.x; k < (rows_max + 2) * W; k += SOLVE_THREADS) u_s[k] = 0.0f;
+    for (int k = threadIdx.x; k < 2 * plane; k += SOLVE_THREADS) m_s[k] = 0.0f;
+    float* nb_lo = (C > 1 && rank > 0) ? cl.map_shared_rank(m_s, rank - 1) : nullptr;     // block below
+    float* nb_hi = (C > 1 && rank < C - 1) ? cl.map_shared_rank(m_s, rank + 1) : nullptr; // block above
 
-    long long n_[UPT];
-    int sidx[UPT];
+    int n_[UPT];      // grid index of the unknown
+    int sidx[UPT];    // its place in a plane of m_s
+    int lc_[UPT];     // its column in the band
+    int edge[UPT];    // 1: first row of the band, 2: last row
     bool own[UPT];
     float cw[UPT], ce[UPT], cs[UPT], cn[UPT], dgv[UPT], dinv[UPT];
-    float r[UPT], p[UPT], sv[UPT], w[UPT], d[UPT];
+    float r[UPT], u[UPT], w[UPT], z[UPT], q[UPT], s[UPT], p[UPT], d[UPT];
 #pragma unroll
     for (int k = 0; k < UPT; ++k) {
-        const int u = threadIdx.x + k * SOLVE_THREADS;
-        own[k] = u < m;
-        const int uu = own[k] ? u : 0;
-        const int lr = uu / mx, lc = uu % mx;
-        n_[k] = (long long)(row0 + lr) * nx + (S.i0 + lc);
-        sidx[k] = (lr + 1) * W + (lc + 1);
+        const int uu0 = threadIdx.x + k * SOLVE_THREADS;
+        own[k] = uu0 < m;
+        const int uu = own[k] ? uu0 : 0;
+        const int lr = uu / mx;
+        lc_[k] = uu % mx;
+        n_[k] = (row0 + lr) * nx + (S.i0 + lc_[k]);
+        sidx[k] = (lr + 1) * W + (lc_[k] + 1);
+        edge[k] = (lr == 0 ? 1 : 0) | (lr == rows - 1 ? 2 : 0);
         if (own[k]) {
-            const long long n = n_[k];
+            const int n = n_[k];
             cw[k] = a.cxf[n - 1];
             ce[k] = a.cxf[n];
             cs[k] = a.cyf[n - nx];
@@ -337,14 +347,27 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_pcg_reg(const SolveArgs a, in
         } else {
             cw[k] = ce[k] = cs[k] = cn[k] = dgv[k] = dinv[k] = 0.0f;
         }
-        r[k] = p[k] = sv[k] = w[k] = d[k] = 0.0f;
+        r[k] = u[k] = w[k] = z[k] = q[k] = s[k] = p[k] = d[k] = 0.0f;
     }
 
-    // three-value cluster sum (two alternating slot sets, as cluster_sum2)
-    auto sum3 = [&](float& v0, float& v1, float& v2) {
-        const int b = seq & 1;
-        ++seq;
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // write a band vector into buffer b of m_s and push its edge rows to the neighbours' halos
+    auto publish = [&](int b, const float (&v)[UPT]) {
+        float* mine = m_s + b * plane;
+#pragma unroll
+        for (int k = 0; k < UPT; ++k) {
+            if (!own[k]) continue;
+            mine[sidx[k]] = v[k];
+            if ((edge[k] & 1) && nb_lo) nb_lo[b * plane + (rows_below + 1) * W + lc_[k] + 1] = v[k];
+            if ((edge[k] & 2) && nb_hi) nb_hi[b * plane + lc_[k] + 1] = v[k];
+        }
+    };
+    auto apply_A = [&](int b, int k) -> float {
+        const float* v = m_s + b * plane;
+        const int c0 = sidx[k];
+        return dgv[k] * v[c0] - cw[k] * v[c0 - 1] - ce[k] * v[c0 + 1] - cs[k] * v[c0 - W] - cn[k] * v[c0 + W];
+    };
+    // block partials of three sums pushed to every block's slot [b][rank]; the barrier follows
+    auto push3 = [&](int b, float v0, float v1, float v2) {
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             v0 += __shfl_xor_sync(0xffffffffu, v0, off);
@@ -352,69 +375,33 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_pcg_reg(const SolveArgs a, in
             v2 += __shfl_xor_sync(0xffffffffu, v2, off);
         }
         if (lane == 0) {
-            red3_part[b][0][warp] = v0;
-            red3_part[b][1][warp] = v1;
-            red3_part[b][2][warp] = v2;
+            warp_part[0][warp] = v0;
+            warp_part[1][warp] = v1;
+            warp_part[2][warp] = v2;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            float t0 = 0.f, t1 = 0.f, t2 = 0.f;
-            for (int q = 0; q < SOLVE_WARPS; ++q) {
-                t0 += red3_part[b][0][q];
-                t1 += red3_part[b][1][q];
-                t2 += red3_part[b][2][q];
-            }
-            red3_block[b][0] = t0;
-            red3_block[b][1] = t1;
-            red3_block[b][2] = t2;
-        }
-        cl.sync();
         if (warp == 0) {
-            float t0 = 0.f, t1 = 0.f, t2 = 0.f;
-            if (lane < C) {
-                const float* rem = cl.map_shared_rank(&red3_block[b][0], lane);
-                t0 = rem[0];
-                t1 = rem[1];
-                t2 = rem[2];
-            }
+            float t0 = lane < SOLVE_WARPS ? warp_part[0][lane] : 0.f;
+            float t1 = lane < SOLVE_WARPS ? warp_part[1][lane] : 0.f;
+            float t2 = lane < SOLVE_WARPS ? warp_part[2][lane] : 0.f;
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
                 t0 += __shfl_xor_sync(0xffffffffu, t0, off);
                 t1 += __shfl_xor_sync(0xffffffffu, t1, off);
                 t2 += __shfl_xor_sync(0xffffffffu, t2, off);
             }
-            if (lane == 0) {
-                red3_total[b][0] = t0;
-                red3_total[b][1] = t1;
-                red3_total[b][2] = t2;
-            }
+            if (lane < C) cl.map_shared_rank(&slots[b][rank], lane)[0] = make_float4(t0, t1, t2, 0.f);
         }
-        __syncthreads();
-        v0 = red3_total[b][0];
-        v1 = red3_total[b][1];
-        v2 = red3_total[b][2];
     };
-
-    // u is in shared memory: publish, then copy the neighbours' edge rows into the halo rows
-    auto exchange_u = [&]() {
-        cl.sync();
-        if (C > 1) {
-            if (rank > 0) {
-                const float* src = cl.map_shared_rank(u_s, rank - 1);
-                const int rows_below = ((my * rank) / C) - ((my * (rank - 1)) / C);
-                for (int c = threadIdx.x; c < mx; c += SOLVE_THREADS) u_s[c + 1] = src[rows_below * W + c + 1];
-            }
-            if (rank < C - 1) {
-                const float* src = cl.map_shared_rank(u_s, rank + 1);
-                for (int c = threadIdx.x; c < mx; c += SOLVE_THREADS) u_s[(rows + 1) * W + c + 1] = src[1 * W + c + 1];
-            }
+    // after the barrier: the cluster sums, in rank order, from the local slots
+    auto read3 = [&](int b, float& v0, float& v1, float& v2) {
+        v0 = v1 = v2 = 0.f;
+        for (int qq = 0; qq < C; ++qq) {
+            const float4 t = slots[b][qq];
+            v0 += t.x;
+            v1 += t.y;
+            v2 += t.z;
         }
-        __syncthreads();
-    };
-
-    auto apply_A = [&](int k) -> float {
-        const int q = sidx[k];
-        return dgv[k] * u_s[q] - cw[k] * u_s[q - 1] - ce[k] * u_s[q + 1] - cs[k] * u_s[q - W] - cn[k] * u_s[q + W];
     };
 
     // ||b||^2
@@ -422,33 +409,34 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_pcg_reg(const SolveArgs a, in
 #pragma unroll
     for (int k = 0; k < UPT; ++k) {
         if (!own[k]) continue;
-        const long long n = n_[k];
-        const int i = (int)(n % nx), j = (int)(n / nx);
-        double b = rhs[n];
-        if (i == S.i0) b += a.cx[n - 1] * x[n - 1];
-        if (i == S.i1 - 1) b += a.cx[n] * x[n + 1];
-        if (j == S.j0) b += a.cy[n - nx] * x[n - nx];
-        if (j == S.j1 - 1) b += a.cy[n] * x[n + nx];
-        bb += b * b;
+        const int n = n_[k];
+        const int i = S.i0 + lc_[k], j = n / nx;
+        double bv = rhs[n];
+        if (i == S.i0) bv += a.cx[n - 1] * x[n - 1];
+        if (i == S.i1 - 1) bv += a.cx[n] * x[n + 1];
+        if (j == S.j0) bv += a.cy[n - nx] * x[n - nx];
+        if (j == S.j1 - 1) bv += a.cy[n] * x[n + nx];
+        bb += bv * bv;
     }
     cluster_sum2(cl, red64, seq, bb, unused);
     const double stop2 = a.rtol * a.rtol * bb;
 
-    int total = 0;
+    int total = 0, it = 0;
     bool converged = false;
     for (int outer = 0; outer < a.max_outer; ++outer) {
         double rr64 = 0.0, unused64 = 0.0;
 #pragma unroll
         for (int k = 0; k < UPT; ++k) {
             if (!own[k]) continue;
-            const long long n = n_[k];
+            const int n = n_[k];
             const double ax = a.dg[n] * x[n] - a.cx[n - 1] * x[n - 1] - a.cx[n] * x[n + 1] -
                               a.cy[n - nx] * x[n - nx] - a.cy[n] * x[n + nx];
             const double res = rhs[n] - ax;
             rr64 += res * res;
             r[k] = (float)res;
             d[k] = 0.0f;
-            u_s[sidx[k]] = r[k] * dinv[k];
+            u[k] = r[k] * dinv[k];
+            z[k] = q[k] = s[k] = p[k] = 0.0f;
         }
         cluster_sum2(cl, red64, seq, rr64, unused64);
         if (rr64 <= stop2) {
@@ -456,57 +444,55 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_pcg_reg(const SolveArgs a, in
             break;
         }
         if (total >= a.max_iter) break;
-        // Chronopoulos--Gear PCG on A d = r from d = 0
-        exchange_u();
-        float gam = 0.f, del = 0.f, rr = 0.f;
+        // w0 = A u0 (u0's halo through buffer `it & 1`)
+        publish(it & 1, u);
+        cl.sync();
 #pragma unroll
-        for (int k = 0; k < UPT; ++k) {
-            if (!own[k]) continue;
-            w[k] = apply_A(k);
-            const float uk = u_s[sidx[k]];
-            gam += r[k] * uk;
-            del += w[k] * uk;
-            rr += r[k] * r[k];
-            p[k] = 0.f;
-            sv[k] = 0.f;
-        }
-        sum3(gam, del, rr);
-        if (!(rr > 0.0f) || !(del > 0.0f)) continue;
-        const float stop_in = a.inner_tol * a.inner_tol * rr;
-        float alpha = gam / del, beta = 0.0f, gam_old = gam;
+        for (int k = 0; k < UPT; ++k) w[k] = own[k] ? apply_A(it & 1, k) : 0.f;
+        ++it;
+        float alpha = 0.f, gam_old = 1.f, rr0 = -1.f;
+        bool first = true;
         while (total < a.max_iter) {
-            ++total;
+            const int b = it & 1;
+            float gam = 0.f, del = 0.f, rr = 0.f;
+            float mv[UPT];
 #pragma unroll
             for (int k = 0; k < UPT; ++k) {
-                if (!own[k]) continue;
-                const float uk = u_s[sidx[k]];
-                p[k] = uk + beta * p[k];
-                sv[k] = w[k] + beta * sv[k];
-                d[k] += alpha * p[k];
-                r[k] -= alpha * sv[k];
-            }
-            __syncthreads();  // every read of u is done before it is overwritten
-#pragma unroll
-            for (int k = 0; k < UPT; ++k)
-                if (own[k]) u_s[sidx[k]] = r[k] * dinv[k];
-            exchange_u();
-            gam = 0.f;
-            del = 0.f;
-            rr = 0.f;
-#pragma unroll
-            for (int k = 0; k < UPT; ++k) {
-                if (!own[k]) continue;
-                w[k] = apply_A(k);
-                const float uk = u_s[sidx[k]];
-                gam += r[k] * uk;
-                del += w[k] * uk;
+                gam += r[k] * u[k];
+                del += w[k] * u[k];
                 rr += r[k] * r[k];
+                mv[k] = w[k] * dinv[k];
             }
-            sum3(gam, del, rr);
-            if (rr <= stop_in) break;
-            beta = gam / gam_old;
-            alpha = gam / (del - beta * gam / alpha);
+            publish(b, mv);
+            push3(b, gam, del, rr);
+            cl.sync();
+            ++it;
+            read3(b, gam, del, rr);
+            if (first) rr0 = rr;
+            if (!(rr > a.inner_tol * a.inner_tol * rr0) || !(rr0 > 0.f)) break;
+            ++total;
+            float beta;
+            if (first) {
+                beta = 0.f;
+                alpha = gam / del;
+            } else {
+                beta = gam / gam_old;
+                alpha = gam / (del - beta * gam / alpha);
+            }
+            first = false;
             gam_old = gam;
+#pragma unroll
+            for (int k = 0; k < UPT; ++k) {
+                const float nk = own[k] ? apply_A(b, k) : 0.f;
+                z[k] = nk + beta * z[k];
+                q[k] = mv[k] + beta * q[k];
+                s[k] = w[k] + beta * s[k];
+                p[k] = u[k] + beta * p[k];
+                d[k] += alpha * p[k];
+                r[k] -= alpha * s[k];
+                u[k] -= alpha * q[k];
+                w[k] -= alpha * z[k];
+            }
         }
         // x += d in double precision; the next residual reads the neighbours' x
 #pragma unroll
@@ -518,8 +504,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_pcg_reg(const SolveArgs a, in
         a.iters[blockIdx.x / C] = converged ? total : a.max_iter + 1;
         if (!converged) atomicOr(a.status, STATUS_NOCONV);
     }
-    (void)red32;
-    cl.sync();  // no block leaves while others may still read its shared memory
+    cl.sync();  // no block leaves while others may still write into its shared memory
 }
 
 __global__ void k_bump_step(uint32_t* step)
@@ -599,15 +584,15 @@ static cudaLaunchConfig_t cluster_config(const SolveArgs& a, size_t smem, cudaSt
 template <int UPT>
 static cudaError_t launch_reg(const SolveArgs& a, int rows_max, int max_mx, cudaStream_t s)
 {
-    const size_t smem = (size_t)(rows_max + 2) * (size_t)(max_mx + 2) * sizeof(float);
-    if (a.cluster > 8) cudaFuncSetAttribute(k_pcg_reg<UPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    const size_t smem = 2 * (size_t)(rows_max + 2) * (size_t)(max_mx + 2) * sizeof(float);
+    if (a.cluster > 8) cudaFuncSetAttribute(k_pcg_pipe<UPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_pcg_reg<UPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_pcg_pipe<UPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     cudaLaunchAttribute at[1];
     cudaLaunchConfig_t cfg = cluster_config(a, smem, s, at);
-    return cudaLaunchKernelEx(&cfg, k_pcg_reg<UPT>, a, rows_max);
+    return cudaLaunchKernelEx(&cfg, k_pcg_pipe<UPT>, a, rows_max);
 }
 
 // Unknowns per thread of the register-resident kernel for these systems
