@@ -280,20 +280,21 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_pcg_cluster(const SolveArgs a
 }
 
 // Register-resident variant for systems whose band fits in the block: each
-// thread keeps UPT unknowns (coefficients and the CG vectors) in registers.
-// The inner iteration is the pipelined form of preconditioned CG (Ghysels &
-// Vanroose, "Hiding global synchronization latency in the preconditioned
-// conjugate gradient algorithm", 2014): per iteration one fused reduction
-// ((r,u), (w,u), (r,r)) and one product n = A m with m = M^-1 w. Blocks push
-// their reduction partials and the edge rows of m straight into the
-// neighbours' shared memory before a single cluster barrier; after it every
-// read is local. Both the partial slots and m are double-buffered by the
-// iteration's parity: a buffer is rewritten only after the next barrier,
-// which no block passes before every block has finished reading it.
+// thread keeps UPT unknowns (coefficients and the CG vectors) in registers;
+// the preconditioned residual u lives in shared memory with a halo row above
+// and below. The inner iteration is the Chronopoulos--Gear form of
+// preconditioned CG (Chronopoulos & Gear, "s-step iterative methods for
+// symmetric linear systems", 1989): one fused reduction per iteration
+// ((r,u), (w,u), (r,r)) after the product w = A u. Blocks push the edge rows
+// of u and their reduction partials straight into the neighbours' shared
+// memory before a cluster barrier, so each iteration is two barriers and no
+// read crosses blocks. Halo rows and partial slots are double-buffered by
+// the iteration's parity; a buffer is rewritten only two barriers after it
+// was read.
 template <int UPT>
-__global__ void __launch_bounds__(SOLVE_THREADS) k_pcg_pipe(const SolveArgs a, int rows_max)
+__global__ void __launch_bounds__(SOLVE_THREADS) k_pcg_cg(const SolveArgs a, int rows_max)
 {
-    extern __shared__ float m_s[];  // 2 x (rows_max + 2) x (mx + 2), zero frame
+    extern __shared__ float m_s[];  // u: 2 x (rows_max + 2) x (mx + 2), zero frame
     __shared__ float4 slots[2][16];  // [parity][block]: (gamma, delta, rr) partials pushed by every block
     __shared__ float warp_part[3][SOLVE_WARPS];
     cg::cluster_group cl = cg::this_cluster();
@@ -325,7 +326,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_pcg_pipe(const SolveArgs a, i
     int edge[UPT];    // 1: first row of the band, 2: last row
     bool own[UPT];
     float cw[UPT], ce[UPT], cs[UPT], cn[UPT], dgv[UPT], dinv[UPT];
-    float r[UPT], u[UPT], w[UPT], z[UPT], q[UPT], s[UPT], p[UPT], d[UPT];
+    float r[UPT], u[UPT], w[UPT], s[UPT], p[UPT], d[UPT];
 #pragma unroll
     for (int k = 0; k < UPT; ++k) {
         const int uu0 = threadIdx.x + k * SOLVE_THREADS;
@@ -347,7 +348,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_pcg_pipe(const SolveArgs a, i
         } else {
             cw[k] = ce[k] = cs[k] = cn[k] = dgv[k] = dinv[k] = 0.0f;
         }
-        r[k] = u[k] = w[k] = z[k] = q[k] = s[k] = p[k] = d[k] = 0.0f;
+        r[k] = u[k] = w[k] = s[k] = p[k] = d[k] = 0.0f;
     }
 
     // write a band vector into buffer b of m_s and push its edge rows to the neighbours' halos
@@ -436,7 +437,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_pcg_pipe(const SolveArgs a, i
             r[k] = (float)res;
             d[k] = 0.0f;
             u[k] = r[k] * dinv[k];
-            z[k] = q[k] = s[k] = p[k] = 0.0f;
+            s[k] = p[k] = 0.0f;
         }
         cluster_sum2(cl, red64, seq, rr64, unused64);
         if (rr64 <= stop2) {
@@ -444,55 +445,49 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_pcg_pipe(const SolveArgs a, i
             break;
         }
         if (total >= a.max_iter) break;
-        // w0 = A u0 (u0's halo through buffer `it & 1`)
-        publish(it & 1, u);
-        cl.sync();
-#pragma unroll
-        for (int k = 0; k < UPT; ++k) w[k] = own[k] ? apply_A(it & 1, k) : 0.f;
-        ++it;
-        float alpha = 0.f, gam_old = 1.f, rr0 = -1.f;
+        // Chronopoulos--Gear iteration on A d = r from d = 0, u = M^-1 r
+        float alpha = 0.f, beta = 0.f, gam_old = 1.f, rr0 = 0.f;
         bool first = true;
-        while (total < a.max_iter) {
+        for (;;) {
+            if (!first) {
+#pragma unroll
+                for (int k = 0; k < UPT; ++k) {
+                    p[k] = u[k] + beta * p[k];
+                    s[k] = w[k] + beta * s[k];
+                    d[k] += alpha * p[k];
+                    r[k] -= alpha * s[k];
+                    u[k] = r[k] * dinv[k];
+                }
+            }
             const int b = it & 1;
+            ++it;
+            publish(b, u);
+            cl.sync();
             float gam = 0.f, del = 0.f, rr = 0.f;
-            float mv[UPT];
 #pragma unroll
             for (int k = 0; k < UPT; ++k) {
+                w[k] = own[k] ? apply_A(b, k) : 0.f;
                 gam += r[k] * u[k];
                 del += w[k] * u[k];
                 rr += r[k] * r[k];
-                mv[k] = w[k] * dinv[k];
             }
-            publish(b, mv);
             push3(b, gam, del, rr);
             cl.sync();
-            ++it;
             read3(b, gam, del, rr);
-            if (first) rr0 = rr;
-            if (!(rr > a.inner_tol * a.inner_tol * rr0) || !(rr0 > 0.f)) break;
-            ++total;
-            float beta;
             if (first) {
-                beta = 0.f;
+                rr0 = rr;
+                if (!(rr0 > 0.f) || !(del > 0.f)) break;
                 alpha = gam / del;
+                beta = 0.f;
+                first = false;
             } else {
+                if (rr <= a.inner_tol * a.inner_tol * rr0) break;
                 beta = gam / gam_old;
                 alpha = gam / (del - beta * gam / alpha);
             }
-            first = false;
             gam_old = gam;
-#pragma unroll
-            for (int k = 0; k < UPT; ++k) {
-                const float nk = own[k] ? apply_A(b, k) : 0.f;
-                z[k] = nk + beta * z[k];
-                q[k] = mv[k] + beta * q[k];
-                s[k] = w[k] + beta * s[k];
-                p[k] = u[k] + beta * p[k];
-                d[k] += alpha * p[k];
-                r[k] -= alpha * s[k];
-                u[k] -= alpha * q[k];
-                w[k] -= alpha * z[k];
-            }
+            if (total >= a.max_iter) break;
+            ++total;
         }
         // x += d in double precision; the next residual reads the neighbours' x
 #pragma unroll
@@ -585,14 +580,14 @@ template <int UPT>
 static cudaError_t launch_reg(const SolveArgs& a, int rows_max, int max_mx, cudaStream_t s)
 {
     const size_t smem = 2 * (size_t)(rows_max + 2) * (size_t)(max_mx + 2) * sizeof(float);
-    if (a.cluster > 8) cudaFuncSetAttribute(k_pcg_pipe<UPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (a.cluster > 8) cudaFuncSetAttribute(k_pcg_cg<UPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_pcg_pipe<UPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_pcg_cg<UPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     cudaLaunchAttribute at[1];
     cudaLaunchConfig_t cfg = cluster_config(a, smem, s, at);
-    return cudaLaunchKernelEx(&cfg, k_pcg_pipe<UPT>, a, rows_max);
+    return cudaLaunchKernelEx(&cfg, k_pcg_cg<UPT>, a, rows_max);
 }
 
 // Unknowns per thread of the register-resident kernel for these systems
