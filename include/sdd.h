@@ -248,6 +248,43 @@ const char* sdd_last_error(const sdd_ctx* ctx);
 /* Release the context and everything it allocated (waits for its stream). */
 void sdd_destroy(sdd_ctx* ctx);
 
+/* The inputs of one mesh step, for entry points that take them directly
+ * (DEVICE arrays of nx*ny entries, row-major): w (float), xi and eta (double);
+ * faces: DEVICE face data in the layout of sdd_set_boundary, or NULL for the
+ * paper's data computed from w. */
+typedef struct {
+    int32_t nx, ny;
+    const float* w;
+    const double* xi;
+    const double* eta;
+    const double* faces;
+} sdd_fields;
+
+/* The interface estimate of sdd_interface_mc without any allocation: no
+ * context, no cudaMalloc or cudaFree, nothing allocated on the host heap.
+ * This entry point has no counterpart in the paper; it exists for callers
+ * that are not allowed to allocate device memory once they are running (a
+ * real-time loop, a host application that hands out only fixed buffers, a
+ * plugin given pointers and a stream). They pass the inputs (`f`, DEVICE;
+ * `nodes`, HOST, as in sdd_interface_mc) and the output arrays (`out`,
+ * DEVICE); all working memory -- the cell tables, the face data, the node
+ * and task lists, the per-task sums and the work counter -- is one static
+ * device array of sdd_static_scratch_bytes() bytes that every GPU loading the
+ * library holds until the process exits.
+ * Limits (else SDD_EINVAL, nothing enqueued): nx, ny <= 257; at most 8192
+ * nodes and 65536 tasks (paths_per_task as requested, else chosen to fit).
+ * The first call on a device looks up the array's device address (so make it
+ * before any stream capture). Every call shares the array: calls whose work
+ * can overlap on the GPU (different streams or host threads) race and must
+ * not be made; one call at a time per process. Results equal those of
+ * sdd_interface_mc for the same inputs, parameters and paths_per_task.
+ * Work is enqueued on `stream`. */
+sdd_status sdd_interface_mc_static(const sdd_fields* f, const sdd_nodes* nodes, const sdd_mc_params* p,
+                                   sdd_node_stats* out, void* stream);
+
+/* Size in bytes of the static array used by sdd_interface_mc_static. */
+int64_t sdd_static_scratch_bytes(void);
+
 /* The variates of the estimator, for checking: for each counter
  * (path, node, draw, step) in `ctrs` (DEVICE, 4 uint32 per entry), the Philox
  * block (`words`, DEVICE, 4 uint32 per entry) and the four normals of its two

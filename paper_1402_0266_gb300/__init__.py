@@ -31,7 +31,8 @@ EXPORTS = [
     "sdd_get_fields", "sdd_get_fields_host", "sdd_interface_mc", "sdd_interface_mc_record", "sdd_interface_nodes",
     "sdd_subdomain_solve", "sdd_step", "sdd_last_interface_stats", "sdd_last_step_info", "sdd_set_step_index",
     "sdd_get_step_index",
-    "sdd_sync", "sdd_last_error", "sdd_destroy", "sdd_rng_draw",
+    "sdd_sync", "sdd_last_error", "sdd_destroy", "sdd_rng_draw", "sdd_interface_mc_static",
+    "sdd_static_scratch_bytes",
 ]
 
 
@@ -63,6 +64,11 @@ class _McParams(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("Dt", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("step_index", ctypes.c_uint32), ("exit_mode", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("paths_per_task", ctypes.c_int32)]
+
+
+class _Fields(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("w", ctypes.c_void_p), ("xi", ctypes.c_void_p),
+                ("eta", ctypes.c_void_p), ("faces", ctypes.c_void_p)]
 
 
 class _StepInfo(ctypes.Structure):
@@ -114,12 +120,16 @@ def lib():
                 "sdd_last_error": [vp],
                 "sdd_destroy": [vp],
                 "sdd_rng_draw": [u64, vp, i64, vp, vp, vp],
+                "sdd_interface_mc_static": [ctypes.POINTER(_Fields), ctypes.POINTER(_Nodes), ctypes.POINTER(_McParams),
+                                            ctypes.POINTER(_Stats), vp],
+                "sdd_static_scratch_bytes": [],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
                 f.argtypes = args
                 f.restype = ctypes.c_int
             L.sdd_get_step_index.restype = ctypes.c_uint32
+            L.sdd_static_scratch_bytes.restype = ctypes.c_int64
             L.sdd_last_error.restype = ctypes.c_char_p
             L.sdd_destroy.restype = None
             _lib = L
@@ -382,3 +392,36 @@ def sdd_rng_draw(seed, counters, stream=None):
     if st != SDD_OK:
         raise SddError(st, "sdd_rng_draw failed")
     return words, normals
+
+
+def sdd_interface_mc_static(w, xi, eta, x, y, n_paths, dt, Dt, seed=0, step_index=0, exit_mode=0, block_threads=0,
+                            paths_per_task=0, faces=None, out=None, stream=None):
+    """The interface estimate without any allocation in the library (see include/sdd.h).
+
+    w (float32), xi, eta (float64): cuda tensors of shape (ny, nx); x, y, n_paths: host arrays.
+    `out`: optional dict of preallocated cuda tensors as returned by sdd_interface_mc.
+    """
+    torch = _torch()
+    ny, nx = w.shape
+    _check_dev(w, torch.float32, (ny, nx), "w")
+    _check_dev(xi, torch.float64, (ny, nx), "xi")
+    _check_dev(eta, torch.float64, (ny, nx), "eta")
+    if faces is not None:
+        _check_dev(faces, torch.float64, (faces_len(nx, ny),), "faces")
+    f = _Fields(nx, ny, w.data_ptr(), xi.data_ptr(), eta.data_ptr(), faces.data_ptr() if faces is not None else None)
+    nodes, keep = _nodes(x, y, n_paths)
+    if out is None:
+        out, s = _alloc_stats(nodes.count)
+    else:
+        s = _Stats(*(out[k].data_ptr() for k in ("mean_xi", "mean_eta", "se_xi", "se_eta", "n_exit", "path_steps")))
+    p = mc_params(dt, Dt, seed, step_index, exit_mode, block_threads, paths_per_task)
+    st = lib().sdd_interface_mc_static(ctypes.byref(f), ctypes.byref(nodes), ctypes.byref(p), ctypes.byref(s),
+                                       _stream(stream))
+    del keep
+    if st != SDD_OK:
+        raise SddError(st, "sdd_interface_mc_static rejected its arguments" if st == SDD_EINVAL else "CUDA error")
+    return out
+
+
+def sdd_static_scratch_bytes() -> int:
+    return int(lib().sdd_static_scratch_bytes())
