@@ -364,43 +364,60 @@ sdd_status setup_solver(sdd_ctx* c)
         CU(c, cudaMemset(c->p32[f].p, 0, N * sizeof(float)));
     }
     const std::vector<int> xs = block_edges(c->nx, c->sub_x), ys = block_edges(c->ny, c->sub_y);
-    c->systems.clear();
+    // subdomains (both fields solved together by the register-resident kernel)
+    std::vector<SolveSys> subs;
     int min_rows = 1 << 30;
-    for (int field = 0; field < 2; ++field)
-        for (int b = 0; b < c->sub_y; ++b)
-            for (int a = 0; a < c->sub_x; ++a) {
-                SolveSys S{};
-                S.i0 = xs[a] + 1;
-                S.i1 = xs[a + 1];
-                S.j0 = ys[b] + 1;
-                S.j1 = ys[b + 1];
-                S.field = field;
-                if (S.i1 > S.i0 && S.j1 > S.j0) {
-                    c->systems.push_back(S);
-                    min_rows = std::min(min_rows, S.j1 - S.j0);
-                }
+    for (int b = 0; b < c->sub_y; ++b)
+        for (int a = 0; a < c->sub_x; ++a) {
+            SolveSys S{};
+            S.i0 = xs[a] + 1;
+            S.i1 = xs[a + 1];
+            S.j0 = ys[b] + 1;
+            S.j1 = ys[b + 1];
+            S.field = -1;
+            if (S.i1 > S.i0 && S.j1 > S.j0) {
+                subs.push_back(S);
+                min_rows = std::min(min_rows, S.j1 - S.j0);
             }
+        }
+    c->solve_upt = 0;
+    if (!subs.empty()) {
+        const int C = solve_cluster_size((int)subs.size(), min_rows, c->sm_count);
+        int band_max = 0, rows_max = 0, mx_max = 0;
+        for (const SolveSys& S : subs) {
+            const int my = S.j1 - S.j0, mx = S.i1 - S.i0;
+            for (int rk = 0; rk < C; ++rk) {
+                const int rows = (my * (rk + 1)) / C - (my * rk) / C;
+                rows_max = std::max(rows_max, rows);
+                band_max = std::max(band_max, rows * mx);
+            }
+            mx_max = std::max(mx_max, mx);
+        }
+        c->solve_upt = solve_reg_upt(band_max);
+        if (4 * (size_t)(rows_max + 2) * (mx_max + 2) * sizeof(float) > 200 * 1024 || C > 16) c->solve_upt = 0;
+        if (c->solve_upt) {
+            c->systems = subs;
+            c->solve_cluster = C;
+            c->solve_rows_max = rows_max;
+            c->solve_mx_max = mx_max;
+        }
+    }
+    if (!c->solve_upt) {
+        // general kernel: one system per subdomain and field
+        c->systems.clear();
+        for (int field = 0; field < 2; ++field)
+            for (const SolveSys& S0 : subs) {
+                SolveSys S = S0;
+                S.field = field;
+                c->systems.push_back(S);
+            }
+        c->solve_cluster = c->systems.empty() ? 1 : solve_cluster_size((int)c->systems.size(), min_rows, c->sm_count);
+    }
     CU(c, c->d_systems.alloc(std::max<size_t>(c->systems.size(), 1)));
     if (!c->systems.empty())
         CU(c, cudaMemcpy(c->d_systems.p, c->systems.data(), c->systems.size() * sizeof(SolveSys),
                          cudaMemcpyHostToDevice));
     CU(c, c->d_iters.alloc(std::max<size_t>(c->systems.size(), 1)));
-    c->solve_cluster = c->systems.empty() ? 1 : solve_cluster_size((int)c->systems.size(), min_rows, c->sm_count);
-    // band sizes of the blocks, for the register-resident kernel
-    int band_max = 0, rows_max = 0, mx_max = 0;
-    for (const SolveSys& S : c->systems) {
-        const int my = S.j1 - S.j0, mx = S.i1 - S.i0;
-        for (int rk = 0; rk < c->solve_cluster; ++rk) {
-            const int rows = S.j0 + (my * (rk + 1)) / c->solve_cluster - (S.j0 + (my * rk) / c->solve_cluster);
-            rows_max = std::max(rows_max, rows);
-            band_max = std::max(band_max, rows * mx);
-        }
-        mx_max = std::max(mx_max, mx);
-    }
-    c->solve_upt = solve_reg_upt(band_max);
-    c->solve_rows_max = rows_max;
-    c->solve_mx_max = mx_max;
-    if (2 * (size_t)(rows_max + 2) * (mx_max + 2) * sizeof(float) > 200 * 1024 || c->solve_cluster > 16) c->solve_upt = 0;
     return SDD_OK;
 }
 

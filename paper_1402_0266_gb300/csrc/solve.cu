@@ -279,24 +279,27 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_pcg_cluster(const SolveArgs a
     cl.sync();  // no block leaves while others may still read its shared memory
 }
 
-// Register-resident variant for systems whose band fits in the block: each
-// thread keeps UPT unknowns (coefficients and the CG vectors) in registers;
-// the preconditioned residual u lives in shared memory with a halo row above
-// and below. The inner iteration is the Chronopoulos--Gear form of
-// preconditioned CG (Chronopoulos & Gear, "s-step iterative methods for
-// symmetric linear systems", 1989): one fused reduction per iteration
-// ((r,u), (w,u), (r,r)) after the product w = A u. Blocks push the edge rows
-// of u and their reduction partials straight into the neighbours' shared
-// memory before a cluster barrier, so each iteration is two barriers and no
-// read crosses blocks. Halo rows and partial slots are double-buffered by
-// the iteration's parity; a buffer is rewritten only two barriers after it
-// was read.
+// Register-resident variant for subdomains whose band fits in the block:
+// one cluster solves both fields of a subdomain (same matrix, two right-hand
+// sides), so the cluster barriers are shared by the two solves. Each thread
+// keeps UPT unknowns (coefficients and, per field, the CG vectors) in
+// registers; the preconditioned residuals u live in shared memory with a
+// halo row above and below. The inner iteration is the Chronopoulos--Gear
+// form of preconditioned CG (Chronopoulos & Gear, "s-step iterative methods
+// for symmetric linear systems", 1989): one fused reduction per iteration
+// ((r,u), (w,u), (r,r) of both fields) after the product w = A u. Blocks push
+// the edge rows of u and their reduction partials straight into the
+// neighbours' shared memory before a cluster barrier, so an iteration is two
+// barriers and no read crosses blocks. Halo rows and partial slots are
+// double-buffered by the iteration's parity; a buffer is rewritten only two
+// barriers after it was read. A field that has converged stops changing
+// while the other one finishes.
 template <int UPT>
-__global__ void __launch_bounds__(SOLVE_THREADS) k_pcg_cg(const SolveArgs a, int rows_max)
+__global__ void __launch_bounds__(SOLVE_THREADS) k_pcg_cg2(const SolveArgs a, int rows_max)
 {
-    extern __shared__ float m_s[];  // u: 2 x (rows_max + 2) x (mx + 2), zero frame
-    __shared__ float4 slots[2][16];  // [parity][block]: (gamma, delta, rr) partials pushed by every block
-    __shared__ float warp_part[3][SOLVE_WARPS];
+    extern __shared__ float m_s[];  // u: [parity][field] planes of (rows_max + 2) x (mx + 2), zero frame
+    __shared__ float4 slots[2][16][2];  // [parity][block]: (gamma, delta, rr) of field 0, then field 1
+    __shared__ float warp_part[6][SOLVE_WARPS];
     cg::cluster_group cl = cg::this_cluster();
     const int C = (int)cl.num_blocks();
     const int rank = (int)cl.block_rank();
@@ -309,14 +312,16 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_pcg_cg(const SolveArgs a, int
     const int W = mx + 2;
     const int plane = (rows_max + 2) * W;
     const int rows_below = rank > 0 ? ((my * rank) / C) - ((my * (rank - 1)) / C) : 0;
-    double* __restrict__ x = a.x[S.field];
-    const double* __restrict__ rhs = a.rhs0 + (long long)S.field * nx * a.ny;
+    double* __restrict__ x0 = a.x[0];
+    double* __restrict__ x1 = a.x[1];
+    const double* __restrict__ rhs0 = a.rhs0;
+    const double* __restrict__ rhs1 = a.rhs0 + (long long)nx * a.ny;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     __shared__ ClusterSlots<double> red64[2];
     int seq = 0;
 
-    for (int k = threadIdx.x; k < 2 * plane; k += SOLVE_THREADS) m_s[k] = 0.0f;
+    for (int k = threadIdx.x; k < 4 * plane; k += SOLVE_THREADS) m_s[k] = 0.0f;
     float* nb_lo = (C > 1 && rank > 0) ? cl.map_shared_rank(m_s, rank - 1) : nullptr;     // block below
     float* nb_hi = (C > 1 && rank < C - 1) ? cl.map_shared_rank(m_s, rank + 1) : nullptr; // block above
 
@@ -326,7 +331,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_pcg_cg(const SolveArgs a, int
     int edge[UPT];    // 1: first row of the band, 2: last row
     bool own[UPT];
     float cw[UPT], ce[UPT], cs[UPT], cn[UPT], dgv[UPT], dinv[UPT];
-    float r[UPT], u[UPT], w[UPT], s[UPT], p[UPT], d[UPT];
+    float r[2][UPT], u[2][UPT], w[2][UPT], s[2][UPT], p[2][UPT], d[2][UPT];
 #pragma unroll
     for (int k = 0; k < UPT; ++k) {
         const int uu0 = threadIdx.x + k * SOLVE_THREADS;
@@ -348,151 +353,192 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_pcg_cg(const SolveArgs a, int
         } else {
             cw[k] = ce[k] = cs[k] = cn[k] = dgv[k] = dinv[k] = 0.0f;
         }
-        r[k] = u[k] = w[k] = s[k] = p[k] = d[k] = 0.0f;
+#pragma unroll
+        for (int f = 0; f < 2; ++f) r[f][k] = u[f][k] = w[f][k] = s[f][k] = p[f][k] = d[f][k] = 0.0f;
     }
 
-    // write a band vector into buffer b of m_s and push its edge rows to the neighbours' halos
-    auto publish = [&](int b, const float (&v)[UPT]) {
-        float* mine = m_s + b * plane;
+    // write both fields' u into buffer b and push their edge rows to the neighbours' halos
+    auto publish = [&](int b) {
 #pragma unroll
-        for (int k = 0; k < UPT; ++k) {
-            if (!own[k]) continue;
-            mine[sidx[k]] = v[k];
-            if ((edge[k] & 1) && nb_lo) nb_lo[b * plane + (rows_below + 1) * W + lc_[k] + 1] = v[k];
-            if ((edge[k] & 2) && nb_hi) nb_hi[b * plane + lc_[k] + 1] = v[k];
+        for (int f = 0; f < 2; ++f) {
+            float* mine = m_s + (2 * b + f) * plane;
+            const int off = (2 * b + f) * plane;
+#pragma unroll
+            for (int k = 0; k < UPT; ++k) {
+                if (!own[k]) continue;
+                mine[sidx[k]] = u[f][k];
+                if ((edge[k] & 1) && nb_lo) nb_lo[off + (rows_below + 1) * W + lc_[k] + 1] = u[f][k];
+                if ((edge[k] & 2) && nb_hi) nb_hi[off + lc_[k] + 1] = u[f][k];
+            }
         }
     };
-    auto apply_A = [&](int b, int k) -> float {
-        const float* v = m_s + b * plane;
+    auto apply_A = [&](int b, int f, int k) -> float {
+        const float* v = m_s + (2 * b + f) * plane;
         const int c0 = sidx[k];
         return dgv[k] * v[c0] - cw[k] * v[c0 - 1] - ce[k] * v[c0 + 1] - cs[k] * v[c0 - W] - cn[k] * v[c0 + W];
     };
-    // block partials of three sums pushed to every block's slot [b][rank]; the barrier follows
-    auto push3 = [&](int b, float v0, float v1, float v2) {
+    // block partials of six sums, pushed to every block's slot [b][rank]; the barrier follows
+    auto push6 = [&](int b, float (&v)[6]) {
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            v0 += __shfl_xor_sync(0xffffffffu, v0, off);
-            v1 += __shfl_xor_sync(0xffffffffu, v1, off);
-            v2 += __shfl_xor_sync(0xffffffffu, v2, off);
-        }
-        if (lane == 0) {
-            warp_part[0][warp] = v0;
-            warp_part[1][warp] = v1;
-            warp_part[2][warp] = v2;
+        for (int q = 0; q < 6; ++q) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
+            if (lane == 0) warp_part[q][warp] = v[q];
         }
         __syncthreads();
         if (warp == 0) {
-            float t0 = lane < SOLVE_WARPS ? warp_part[0][lane] : 0.f;
-            float t1 = lane < SOLVE_WARPS ? warp_part[1][lane] : 0.f;
-            float t2 = lane < SOLVE_WARPS ? warp_part[2][lane] : 0.f;
+            float t[6];
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                t0 += __shfl_xor_sync(0xffffffffu, t0, off);
-                t1 += __shfl_xor_sync(0xffffffffu, t1, off);
-                t2 += __shfl_xor_sync(0xffffffffu, t2, off);
+            for (int q = 0; q < 6; ++q) {
+                t[q] = lane < SOLVE_WARPS ? warp_part[q][lane] : 0.f;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) t[q] += __shfl_xor_sync(0xffffffffu, t[q], off);
             }
-            if (lane < C) cl.map_shared_rank(&slots[b][rank], lane)[0] = make_float4(t0, t1, t2, 0.f);
+            if (lane < C) {
+                float4* dst = cl.map_shared_rank(&slots[b][rank][0], lane);
+                dst[0] = make_float4(t[0], t[1], t[2], 0.f);
+                dst[1] = make_float4(t[3], t[4], t[5], 0.f);
+            }
         }
     };
-    // after the barrier: the cluster sums, in rank order, from the local slots
-    auto read3 = [&](int b, float& v0, float& v1, float& v2) {
-        v0 = v1 = v2 = 0.f;
-        for (int qq = 0; qq < C; ++qq) {
-            const float4 t = slots[b][qq];
-            v0 += t.x;
-            v1 += t.y;
-            v2 += t.z;
+    // after the barrier, in every warp: lane q takes block q's partials, then a fixed butterfly
+    auto read6 = [&](int b, float (&v)[6]) {
+        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+        if (lane < C) {
+            a0 = slots[b][lane][0];
+            a1 = slots[b][lane][1];
+        }
+        v[0] = a0.x; v[1] = a0.y; v[2] = a0.z; v[3] = a1.x; v[4] = a1.y; v[5] = a1.z;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
         }
     };
 
-    // ||b||^2
-    double bb = 0.0, unused = 0.0;
+    // ||b||^2 of both fields
+    double bb[2] = {0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < UPT; ++k) {
         if (!own[k]) continue;
         const int n = n_[k];
         const int i = S.i0 + lc_[k], j = n / nx;
-        double bv = rhs[n];
-        if (i == S.i0) bv += a.cx[n - 1] * x[n - 1];
-        if (i == S.i1 - 1) bv += a.cx[n] * x[n + 1];
-        if (j == S.j0) bv += a.cy[n - nx] * x[n - nx];
-        if (j == S.j1 - 1) bv += a.cy[n] * x[n + nx];
-        bb += bv * bv;
+        double b0 = rhs0[n], b1 = rhs1[n];
+        if (i == S.i0) { b0 += a.cx[n - 1] * x0[n - 1]; b1 += a.cx[n - 1] * x1[n - 1]; }
+        if (i == S.i1 - 1) { b0 += a.cx[n] * x0[n + 1]; b1 += a.cx[n] * x1[n + 1]; }
+        if (j == S.j0) { b0 += a.cy[n - nx] * x0[n - nx]; b1 += a.cy[n - nx] * x1[n - nx]; }
+        if (j == S.j1 - 1) { b0 += a.cy[n] * x0[n + nx]; b1 += a.cy[n] * x1[n + nx]; }
+        bb[0] += b0 * b0;
+        bb[1] += b1 * b1;
     }
-    cluster_sum2(cl, red64, seq, bb, unused);
-    const double stop2 = a.rtol * a.rtol * bb;
+    cluster_sum2(cl, red64, seq, bb[0], bb[1]);
+    const double stop2[2] = {a.rtol * a.rtol * bb[0], a.rtol * a.rtol * bb[1]};
 
     int total = 0, it = 0;
     bool converged = false;
     for (int outer = 0; outer < a.max_outer; ++outer) {
-        double rr64 = 0.0, unused64 = 0.0;
+        double rr64[2] = {0.0, 0.0};
 #pragma unroll
         for (int k = 0; k < UPT; ++k) {
             if (!own[k]) continue;
             const int n = n_[k];
-            const double ax = a.dg[n] * x[n] - a.cx[n - 1] * x[n - 1] - a.cx[n] * x[n + 1] -
-                              a.cy[n - nx] * x[n - nx] - a.cy[n] * x[n + nx];
-            const double res = rhs[n] - ax;
-            rr64 += res * res;
-            r[k] = (float)res;
-            d[k] = 0.0f;
-            u[k] = r[k] * dinv[k];
-            s[k] = p[k] = 0.0f;
+#pragma unroll
+            for (int f = 0; f < 2; ++f) {
+                const double* xf = f ? x1 : x0;
+                const double ax = a.dg[n] * xf[n] - a.cx[n - 1] * xf[n - 1] - a.cx[n] * xf[n + 1] -
+                                  a.cy[n - nx] * xf[n - nx] - a.cy[n] * xf[n + nx];
+                const double res = (f ? rhs1[n] : rhs0[n]) - ax;
+                rr64[f] += res * res;
+                r[f][k] = (float)res;
+                d[f][k] = 0.0f;
+                u[f][k] = r[f][k] * dinv[k];
+                s[f][k] = p[f][k] = 0.0f;
+            }
         }
-        cluster_sum2(cl, red64, seq, rr64, unused64);
-        if (rr64 <= stop2) {
+        cluster_sum2(cl, red64, seq, rr64[0], rr64[1]);
+        bool active[2] = {!(rr64[0] <= stop2[0]), !(rr64[1] <= stop2[1])};
+        if (!active[0] && !active[1]) {
             converged = true;
             break;
         }
         if (total >= a.max_iter) break;
-        // Chronopoulos--Gear iteration on A d = r from d = 0, u = M^-1 r
-        float alpha = 0.f, beta = 0.f, gam_old = 1.f, rr0 = 0.f;
+        // a converged field has d = 0 and a zero residual in this sweep
+#pragma unroll
+        for (int f = 0; f < 2; ++f)
+            if (!active[f]) {
+#pragma unroll
+                for (int k = 0; k < UPT; ++k) r[f][k] = u[f][k] = 0.0f;
+            }
+        // Chronopoulos--Gear iterations on A d = r from d = 0, u = M^-1 r, both fields in step
+        float alpha[2] = {0.f, 0.f}, beta[2] = {0.f, 0.f}, gam_old[2] = {1.f, 1.f}, rr0[2] = {0.f, 0.f};
         bool first = true;
         for (;;) {
             if (!first) {
 #pragma unroll
-                for (int k = 0; k < UPT; ++k) {
-                    p[k] = u[k] + beta * p[k];
-                    s[k] = w[k] + beta * s[k];
-                    d[k] += alpha * p[k];
-                    r[k] -= alpha * s[k];
-                    u[k] = r[k] * dinv[k];
+                for (int f = 0; f < 2; ++f) {
+                    if (!active[f]) continue;
+#pragma unroll
+                    for (int k = 0; k < UPT; ++k) {
+                        p[f][k] = u[f][k] + beta[f] * p[f][k];
+                        s[f][k] = w[f][k] + beta[f] * s[f][k];
+                        d[f][k] += alpha[f] * p[f][k];
+                        r[f][k] -= alpha[f] * s[f][k];
+                        u[f][k] = r[f][k] * dinv[k];
+                    }
                 }
             }
             const int b = it & 1;
             ++it;
-            publish(b, u);
+            publish(b);
             cl.sync();
-            float gam = 0.f, del = 0.f, rr = 0.f;
+            float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int k = 0; k < UPT; ++k) {
-                w[k] = own[k] ? apply_A(b, k) : 0.f;
-                gam += r[k] * u[k];
-                del += w[k] * u[k];
-                rr += r[k] * r[k];
+            for (int f = 0; f < 2; ++f) {
+#pragma unroll
+                for (int k = 0; k < UPT; ++k) {
+                    w[f][k] = own[k] ? apply_A(b, f, k) : 0.f;
+                    v[3 * f + 0] += r[f][k] * u[f][k];
+                    v[3 * f + 1] += w[f][k] * u[f][k];
+                    v[3 * f + 2] += r[f][k] * r[f][k];
+                }
             }
-            push3(b, gam, del, rr);
+            push6(b, v);
             cl.sync();
-            read3(b, gam, del, rr);
-            if (first) {
-                rr0 = rr;
-                if (!(rr0 > 0.f) || !(del > 0.f)) break;
-                alpha = gam / del;
-                beta = 0.f;
-                first = false;
-            } else {
-                if (rr <= a.inner_tol * a.inner_tol * rr0) break;
-                beta = gam / gam_old;
-                alpha = gam / (del - beta * gam / alpha);
+            read6(b, v);
+#pragma unroll
+            for (int f = 0; f < 2; ++f) {
+                if (!active[f]) continue;
+                const float gam = v[3 * f + 0], del = v[3 * f + 1], rr = v[3 * f + 2];
+                if (first) {
+                    rr0[f] = rr;
+                    if (!(rr0[f] > 0.f) || !(del > 0.f)) {
+                        active[f] = false;
+                        continue;
+                    }
+                    alpha[f] = gam / del;
+                    beta[f] = 0.f;
+                } else {
+                    if (rr <= a.inner_tol * a.inner_tol * rr0[f]) {
+                        active[f] = false;
+                        continue;
+                    }
+                    beta[f] = gam / gam_old[f];
+                    alpha[f] = gam / (del - beta[f] * gam / alpha[f]);
+                }
+                gam_old[f] = gam;
             }
-            gam_old = gam;
+            first = false;
+            if (!active[0] && !active[1]) break;
             if (total >= a.max_iter) break;
             ++total;
         }
         // x += d in double precision; the next residual reads the neighbours' x
 #pragma unroll
         for (int k = 0; k < UPT; ++k)
-            if (own[k]) x[n_[k]] += (double)d[k];
+            if (own[k]) {
+                x0[n_[k]] += (double)d[0][k];
+                x1[n_[k]] += (double)d[1][k];
+            }
         cl.sync();
     }
     if (threadIdx.x == 0 && rank == 0) {
@@ -579,15 +625,15 @@ static cudaLaunchConfig_t cluster_config(const SolveArgs& a, size_t smem, cudaSt
 template <int UPT>
 static cudaError_t launch_reg(const SolveArgs& a, int rows_max, int max_mx, cudaStream_t s)
 {
-    const size_t smem = 2 * (size_t)(rows_max + 2) * (size_t)(max_mx + 2) * sizeof(float);
-    if (a.cluster > 8) cudaFuncSetAttribute(k_pcg_cg<UPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    const size_t smem = 4 * (size_t)(rows_max + 2) * (size_t)(max_mx + 2) * sizeof(float);
+    if (a.cluster > 8) cudaFuncSetAttribute(k_pcg_cg2<UPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_pcg_cg<UPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_pcg_cg2<UPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     cudaLaunchAttribute at[1];
     cudaLaunchConfig_t cfg = cluster_config(a, smem, s, at);
-    return cudaLaunchKernelEx(&cfg, k_pcg_cg<UPT>, a, rows_max);
+    return cudaLaunchKernelEx(&cfg, k_pcg_cg2<UPT>, a, rows_max);
 }
 
 // Unknowns per thread of the register-resident kernel for these systems
