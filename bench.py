@@ -186,6 +186,29 @@ def run_reference(args, world, rank):
 
 # ------------------------------------------------------------------ GPU leg
 
+def profiled_traffic(path):
+    """DRAM bytes per launch from a committed ncu summary, or None when the
+    kernel's sources changed since the counters were taken."""
+    import hashlib
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    fields = dict(l.split(": ", 1) for l in lines if ": " in l and l.split(": ", 1)[0] in
+                  ("dram_bytes_per_launch", "source_sha256", "sources"))
+    if not {"dram_bytes_per_launch", "source_sha256", "sources"} <= fields.keys():
+        return None
+    h = hashlib.sha256()
+    for f in fields["sources"].split(", "):
+        try:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        except OSError:
+            return None
+    if h.hexdigest() != fields["source_sha256"]:
+        return None
+    return float(fields["dram_bytes_per_launch"])
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -263,12 +286,7 @@ def run_ours(args, world, rank, local):
     except Exception:
         pass
     peak = props.multi_processor_count * SM_LANES_PER_CLK * sm_max * 1e6 / 1e12
-    traffic = None
-    try:
-        prof = json.load(open(os.path.join(ROOT, "profiles", "paths_front257_traffic.json")))
-        traffic = prof.get("bytes_per_launch")
-    except Exception:
-        pass
+    traffic = profiled_traffic(os.path.join(ROOT, "profiles", "k_paths_front257.md"))
 
     # end to end through the C ABI with host buffers: w in from pinned host memory,
     # the interface statistics back to pinned host memory, every step
@@ -297,7 +315,7 @@ def run_ours(args, world, rank, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        steps_c, el_c, calls, nnc = oracle_sample(10.0, None, 3)
+        steps_c, el_c, calls, nnc = oracle_sample(15.0, None, 40)
         cpu = {"value": steps_c / el_c, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
                "sample": f"{calls} mesh step(s) of the interface estimate, all {nnc} nodes x {WL.paths} paths "
                          f"({steps_c} path-steps, {el_c:.1f} s)"}
