@@ -248,6 +248,43 @@ const char* sdd_last_error(const sdd_ctx* ctx);
 /* Release the context and everything it allocated (waits for its stream). */
 void sdd_destroy(sdd_ctx* ctx);
 
+/* Many mesh instances through one launch (the paper's method applied to
+ * independent problems at once; Sec. 4 "fully parallel"). A batch groups
+ * contexts (each its own grid, w, fields and face data) created on the same
+ * device; the contexts must outlive the batch and must not be destroyed or
+ * re-initialised while it exists. Work is enqueued on the batch's stream;
+ * order it after earlier work on the contexts' streams (e.g. use one stream).
+ * In a batch the node word of the Philox counter numbers the nodes of all
+ * instances in order: instance k's node j is node (sum of the counts of the
+ * instances before k) + j. */
+typedef struct sdd_batch sdd_batch;
+
+sdd_status sdd_batch_create(sdd_batch** out, sdd_ctx* const* ctxs, int32_t count, void* stream);
+
+/* The interface estimate of every instance in one persistent launch: nodes[k]
+ * and out[k] (count entries each, as in sdd_interface_mc) belong to
+ * instance k; dt, Dt, seed and step_index are shared. */
+sdd_status sdd_batch_interface_mc(sdd_batch* b, const sdd_nodes* nodes, const sdd_mc_params* p, sdd_node_stats* out);
+
+/* One mesh step of every instance (as sdd_step, paths_per_node paths at every
+ * interface node of each instance): the field tables of each instance, one
+ * persistent path-kernel launch over all instances' interface nodes, then each
+ * instance's subdomain solves; recorded once into a CUDA graph and replayed.
+ * The batch's step counter (shared by the instances) advances by one. */
+sdd_status sdd_batch_step(sdd_batch* b, const sdd_step_params* p);
+
+/* As sdd_last_step_info, for the last sdd_batch_step (waits for the stream). */
+sdd_status sdd_batch_last_step_info(sdd_batch* b, sdd_step_info* out);
+
+sdd_status sdd_batch_set_step_index(sdd_batch* b, uint32_t n);
+
+/* Wait for the batch stream; then sdd_sync of every instance. */
+sdd_status sdd_batch_sync(sdd_batch* b);
+const char* sdd_batch_last_error(const sdd_batch* b);
+
+/* Release the batch (not its contexts). */
+void sdd_batch_destroy(sdd_batch* b);
+
 /* The inputs of one mesh step, for entry points that take them directly
  * (DEVICE arrays of nx*ny entries, row-major): w (float), xi and eta (double);
  * faces: DEVICE face data in the layout of sdd_set_boundary, or NULL for the

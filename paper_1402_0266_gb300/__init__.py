@@ -32,7 +32,9 @@ EXPORTS = [
     "sdd_subdomain_solve", "sdd_step", "sdd_last_interface_stats", "sdd_last_step_info", "sdd_set_step_index",
     "sdd_get_step_index",
     "sdd_sync", "sdd_last_error", "sdd_destroy", "sdd_rng_draw", "sdd_interface_mc_static",
-    "sdd_static_scratch_bytes",
+    "sdd_static_scratch_bytes", "sdd_batch_create", "sdd_batch_interface_mc", "sdd_batch_step",
+    "sdd_batch_last_step_info", "sdd_batch_set_step_index", "sdd_batch_sync", "sdd_batch_last_error",
+    "sdd_batch_destroy",
 ]
 
 
@@ -123,6 +125,15 @@ def lib():
                 "sdd_interface_mc_static": [ctypes.POINTER(_Fields), ctypes.POINTER(_Nodes), ctypes.POINTER(_McParams),
                                             ctypes.POINTER(_Stats), vp],
                 "sdd_static_scratch_bytes": [],
+                "sdd_batch_create": [ctypes.POINTER(vp), ctypes.POINTER(vp), i32, vp],
+                "sdd_batch_interface_mc": [vp, ctypes.POINTER(_Nodes), ctypes.POINTER(_McParams),
+                                           ctypes.POINTER(_Stats)],
+                "sdd_batch_step": [vp, ctypes.POINTER(_StepParams)],
+                "sdd_batch_last_step_info": [vp, ctypes.POINTER(_StepInfo)],
+                "sdd_batch_set_step_index": [vp, u32],
+                "sdd_batch_sync": [vp],
+                "sdd_batch_last_error": [vp],
+                "sdd_batch_destroy": [vp],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -130,6 +141,8 @@ def lib():
                 f.restype = ctypes.c_int
             L.sdd_get_step_index.restype = ctypes.c_uint32
             L.sdd_static_scratch_bytes.restype = ctypes.c_int64
+            L.sdd_batch_last_error.restype = ctypes.c_char_p
+            L.sdd_batch_destroy.restype = None
             L.sdd_last_error.restype = ctypes.c_char_p
             L.sdd_destroy.restype = None
             _lib = L
@@ -425,3 +438,80 @@ def sdd_interface_mc_static(w, xi, eta, x, y, n_paths, dt, Dt, seed=0, step_inde
 
 def sdd_static_scratch_bytes() -> int:
     return int(lib().sdd_static_scratch_bytes())
+
+
+class Batch:
+    """An sdd_batch handle; keeps its contexts alive."""
+
+    def __init__(self, handle, ctxs):
+        self.handle = handle
+        self.ctxs = list(ctxs)
+
+    def _check(self, st):
+        if st != SDD_OK:
+            msg = lib().sdd_batch_last_error(self.handle)
+            raise SddError(st, msg.decode() if msg else "")
+
+    def __del__(self):
+        try:
+            sdd_batch_destroy(self)
+        except Exception:
+            pass
+
+
+def sdd_batch_create(ctxs, stream=None) -> Batch:
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.handle.value for c in ctxs])
+    h = ctypes.c_void_p()
+    st = lib().sdd_batch_create(ctypes.byref(h), arr, len(ctxs), _stream(stream))
+    if st != SDD_OK:
+        raise SddError(st, "sdd_batch_create failed")
+    return Batch(h, ctxs)
+
+
+def sdd_batch_interface_mc(batch: Batch, node_lists, dt, Dt, seed=0, step_index=0, exit_mode=0, block_threads=0,
+                           paths_per_task=0):
+    """node_lists: one (x, y, n_paths) per instance (host arrays). Returns one result dict per instance."""
+    n = len(batch.ctxs)
+    assert len(node_lists) == n
+    keep, nodes, outs, stats = [], (_Nodes * n)(), [], (_Stats * n)()
+    for k, (x, y, npaths) in enumerate(node_lists):
+        nd, kp = _nodes(x, y, npaths)
+        keep.append(kp)
+        nodes[k] = nd
+        o, s_ = _alloc_stats(nd.count)
+        outs.append(o)
+        stats[k] = s_
+    p = mc_params(dt, Dt, seed, step_index, exit_mode, block_threads, paths_per_task)
+    batch._check(lib().sdd_batch_interface_mc(batch.handle, nodes, ctypes.byref(p), stats))
+    del keep
+    return outs
+
+
+def sdd_batch_step(batch: Batch, dt, Dt, seed=0, paths_per_node=10000, exit_mode=0, max_iter=20000, rtol=1e-12):
+    p = step_params(dt, Dt, seed, paths_per_node, exit_mode, max_iter, rtol)
+    batch._check(lib().sdd_batch_step(batch.handle, ctypes.byref(p)))
+
+
+def sdd_batch_last_step_info(batch: Batch) -> dict:
+    info = _StepInfo()
+    batch._check(lib().sdd_batch_last_step_info(batch.handle, ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in _StepInfo._fields_}
+
+
+def sdd_batch_set_step_index(batch: Batch, n: int):
+    batch._check(lib().sdd_batch_set_step_index(batch.handle, n))
+
+
+def sdd_batch_sync(batch: Batch):
+    batch._check(lib().sdd_batch_sync(batch.handle))
+
+
+def sdd_batch_last_error(batch: Batch) -> str:
+    m = lib().sdd_batch_last_error(batch.handle)
+    return m.decode() if m else ""
+
+
+def sdd_batch_destroy(batch: Batch):
+    if batch.handle is not None and batch.handle.value:
+        lib().sdd_batch_destroy(batch.handle)
+    batch.handle = ctypes.c_void_p(0)

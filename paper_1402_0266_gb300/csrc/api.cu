@@ -49,6 +49,7 @@ struct DevBuf {
 struct Plan {
     std::vector<double> hx, hy;
     std::vector<int64_t> hp;
+    std::vector<int64_t> seg_key;
     int ppt_req = -1, block_req = -1, exit_mode = -1;
     bool valid = false;
 
@@ -122,16 +123,31 @@ struct sdd_ctx {
 
 namespace {
 
+sdd_status vfail(std::string* err, sdd_status s, const char* fmt, va_list ap)
+{
+    if (err) {
+        char buf[512];
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        *err = buf;
+    }
+    return s;
+}
+
+sdd_status fail(std::string* err, sdd_status s, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vfail(err, s, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
 sdd_status fail(sdd_ctx* c, sdd_status s, const char* fmt, ...)
 {
-    if (c) {
-        char buf[512];
-        va_list ap;
-        va_start(ap, fmt);
-        vsnprintf(buf, sizeof buf, fmt, ap);
-        va_end(ap);
-        c->err = buf;
-    }
+    va_list ap;
+    va_start(ap, fmt);
+    vfail(c ? &c->err : nullptr, s, fmt, ap);
+    va_end(ap);
     return s;
 }
 
@@ -159,6 +175,23 @@ std::vector<int> block_edges(int n, int parts)
 }
 
 float below(float v) { return std::nextafter(v, 0.0f); }
+
+InstDev inst_host(const sdd_ctx* c)
+{
+    InstDev I{};
+    I.bcoef = c->bcoef.p;
+    I.fcoef = c->fcoef.p;
+    I.faces32 = c->faces32.p;
+    I.faces64 = c->faces64.p;
+    I.nx = c->nx;
+    I.ny = c->ny;
+    I.sx = (float)(c->nx - 1);
+    I.sy = (float)(c->ny - 1);
+    I.gxmax = std::nextafter((float)(c->nx - 1), 0.0f);
+    I.gymax = std::nextafter((float)(c->ny - 1), 0.0f);
+    I.cell_bias = 0x4B000000u * (uint32_t)c->nx;
+    return I;
+}
 
 sdd_status upload_inst(sdd_ctx* c)
 {
@@ -208,38 +241,75 @@ bool valid_params(sdd_ctx* c, double dt, double Dt, int exit_mode, int* K)
     return true;
 }
 
-// Build (or reuse) the plan of a node set.
-sdd_status build_plan(sdd_ctx* c, Plan& P, const double* x, const double* y, const int64_t* np, int64_t count,
-                      int ppt_req, int block_req, int exit_mode, bool record)
-{
-    if (count < 0 || count > (1LL << 30)) return fail(c, SDD_EINVAL, "node count out of range");
-    for (int64_t k = 0; k < count; ++k) {
-        if (!(x[k] >= 0.0 && x[k] <= 1.0 && y[k] >= 0.0 && y[k] <= 1.0))
-            return fail(c, SDD_EINVAL, "node %lld lies outside the unit square", (long long)k);
-        if (np[k] < 1 || np[k] > 0x7fffffffLL) return fail(c, SDD_EINVAL, "node %lld: n_paths out of range", (long long)k);
-    }
-    if (block_req != 0 && block_req != 64 && block_req != 128 && block_req != 256 && block_req != 512)
-        return fail(c, SDD_EINVAL, "block_threads must be 0, 64, 128, 256 or 512");
-    if (ppt_req < 0 || (ppt_req % 32) != 0) return fail(c, SDD_EINVAL, "paths_per_task must be a multiple of 32");
+// One node list of one instance inside a plan.
+struct NodeSeg {
+    const double* x;
+    const double* y;
+    const int64_t* np;
+    int64_t count;
+    int32_t inst;   // instance index (tables, outputs)
+    uint32_t ctr0;  // node word of the Philox counter of its first node
+};
 
-    const bool same = P.valid && P.ppt_req == ppt_req && P.block_req == block_req && P.exit_mode == exit_mode &&
-                      (int64_t)P.hx.size() == count && std::equal(P.hx.begin(), P.hx.end(), x) &&
-                      std::equal(P.hy.begin(), P.hy.end(), y) && std::equal(P.hp.begin(), P.hp.end(), np);
+// Build (or reuse) the plan of one or more node lists.
+sdd_status build_plan_segs(std::string* err, int sm_count, Plan& P, const std::vector<NodeSeg>& segs, int ppt_req,
+                           int block_req, int exit_mode, bool record)
+{
+    int64_t count = 0;
+    for (const NodeSeg& g : segs) {
+        if (g.count < 0 || g.count > (1LL << 30)) return fail(err, SDD_EINVAL, "node count out of range");
+        for (int64_t k = 0; k < g.count; ++k) {
+            if (!(g.x[k] >= 0.0 && g.x[k] <= 1.0 && g.y[k] >= 0.0 && g.y[k] <= 1.0))
+                return fail(err, SDD_EINVAL, "node %lld of instance %d lies outside the unit square", (long long)k,
+                            g.inst);
+            if (g.np[k] < 1 || g.np[k] > 0x7fffffffLL)
+                return fail(err, SDD_EINVAL, "node %lld of instance %d: n_paths out of range", (long long)k, g.inst);
+        }
+        count += g.count;
+    }
+    if (count > (1LL << 30)) return fail(err, SDD_EINVAL, "node count out of range");
+    if (block_req != 0 && block_req != 64 && block_req != 128 && block_req != 256 && block_req != 512)
+        return fail(err, SDD_EINVAL, "block_threads must be 0, 64, 128, 256 or 512");
+    if (ppt_req < 0 || (ppt_req % 32) != 0) return fail(err, SDD_EINVAL, "paths_per_task must be a multiple of 32");
+
+    std::vector<int64_t> key;
+    key.reserve(3 * segs.size());
+    for (const NodeSeg& g : segs) {
+        key.push_back(g.count);
+        key.push_back(g.inst);
+        key.push_back(g.ctr0);
+    }
+    bool same = P.valid && P.ppt_req == ppt_req && P.block_req == block_req && P.exit_mode == exit_mode &&
+                (int64_t)P.hx.size() == count && P.seg_key == key;
+    if (same) {
+        int64_t o = 0;
+        for (const NodeSeg& g : segs) {
+            same = same && std::equal(g.x, g.x + g.count, P.hx.begin() + o) &&
+                   std::equal(g.y, g.y + g.count, P.hy.begin() + o) && std::equal(g.np, g.np + g.count, P.hp.begin() + o);
+            o += g.count;
+        }
+    }
     if (same) return SDD_OK;
 
-    P.hx.assign(x, x + count);
-    P.hy.assign(y, y + count);
-    P.hp.assign(np, np + count);
+    P.hx.clear();
+    P.hy.clear();
+    P.hp.clear();
+    for (const NodeSeg& g : segs) {
+        P.hx.insert(P.hx.end(), g.x, g.x + g.count);
+        P.hy.insert(P.hy.end(), g.y, g.y + g.count);
+        P.hp.insert(P.hp.end(), g.np, g.np + g.count);
+    }
+    P.seg_key = key;
     P.ppt_req = ppt_req;
     P.block_req = block_req;
     P.exit_mode = exit_mode;
     P.valid = false;
 
     int64_t total = 0;
-    for (int64_t k = 0; k < count; ++k) total += np[k];
+    for (int64_t k = 0; k < count; ++k) total += P.hp[k];
     P.block = block_req ? block_req : 256;
     const int per_sm = path_kernel_blocks_per_sm(exit_mode, record, P.block);
-    P.grid = c->sm_count * per_sm;
+    P.grid = sm_count * per_sm;
     if (ppt_req) {
         P.ppt = ppt_req;
     } else {
@@ -251,11 +321,22 @@ sdd_status build_plan(sdd_ctx* c, Plan& P, const double* x, const double* y, con
     }
     P.nodes.resize(count);
     P.tasks.clear();
-    int64_t rec = 0;
-    for (int64_t k = 0; k < count; ++k) {
-        P.nodes[k].rec0 = rec;
-        rec += np[k];
+    std::vector<int32_t> inst_of(count), local_of(count);
+    std::vector<uint32_t> ctr_of(count);
+    {
+        int64_t o = 0, rec = 0;
+        for (const NodeSeg& g : segs)
+            for (int64_t k = 0; k < g.count; ++k, ++o) {
+                P.nodes[o].rec0 = rec;
+                rec += g.np[k];
+                inst_of[o] = g.inst;
+                local_of[o] = (int32_t)k;
+                ctr_of[o] = g.ctr0 + (uint32_t)k;
+            }
     }
+    const double* x = P.hx.data();
+    const double* y = P.hy.data();
+    const int64_t* np = P.hp.data();
     // Tasks go node by node, nodes far from the boundary first: their paths
     // run the whole mesh step, so the short tasks of nodes near the boundary
     // fill the end of the launch.
@@ -269,10 +350,10 @@ sdd_status build_plan(sdd_ctx* c, Plan& P, const double* x, const double* y, con
         nd.y = y[k];
         nd.xf = (float)x[k];
         nd.yf = (float)y[k];
-        nd.inst = 0;
-        nd.ctr = (uint32_t)k;
+        nd.inst = inst_of[k];
+        nd.ctr = ctr_of[k];
         nd.n_paths = (int32_t)np[k];
-        nd.local = (int32_t)k;
+        nd.local = local_of[k];
         const bool bnd = x[k] <= 0.0 || x[k] >= 1.0 || y[k] <= 0.0 || y[k] >= 1.0;
         nd.task0 = (int32_t)P.tasks.size();
         if (bnd) {
@@ -287,31 +368,40 @@ sdd_status build_plan(sdd_ctx* c, Plan& P, const double* x, const double* y, con
             P.tasks.push_back(t);
         }
         nd.ntasks = (int32_t)(P.tasks.size() - nd.task0);
-        if (P.tasks.size() > 0x7fffffffULL) return fail(c, SDD_EINVAL, "too many tasks");
+        if (P.tasks.size() > 0x7fffffffULL) return fail(err, SDD_EINVAL, "too many tasks");
     }
     P.nnodes = count;
     P.ntasks = (int64_t)P.tasks.size();
     P.total_paths = total;
-    CU(c, P.d_nodes.alloc(std::max<int64_t>(count, 1)));
-    CU(c, P.d_tasks.alloc(std::max<int64_t>(P.ntasks, 1)));
-    CU(c, P.d_partials.alloc(std::max<int64_t>(P.ntasks, 1)));
-    CU(c, P.d_queue.alloc(1));
-    if (count) CU(c, cudaMemcpy(P.d_nodes.p, P.nodes.data(), count * sizeof(NodeDev), cudaMemcpyHostToDevice));
+    CU(err, P.d_nodes.alloc(std::max<int64_t>(count, 1)));
+    CU(err, P.d_tasks.alloc(std::max<int64_t>(P.ntasks, 1)));
+    CU(err, P.d_partials.alloc(std::max<int64_t>(P.ntasks, 1)));
+    CU(err, P.d_queue.alloc(1));
+    if (count) CU(err, cudaMemcpy(P.d_nodes.p, P.nodes.data(), count * sizeof(NodeDev), cudaMemcpyHostToDevice));
     if (P.ntasks)
-        CU(c, cudaMemcpy(P.d_tasks.p, P.tasks.data(), P.ntasks * sizeof(Task), cudaMemcpyHostToDevice));
+        CU(err, cudaMemcpy(P.d_tasks.p, P.tasks.data(), P.ntasks * sizeof(Task), cudaMemcpyHostToDevice));
     P.valid = true;
     return SDD_OK;
 }
 
-// Enqueue the estimate for a built plan.
-sdd_status run_plan(sdd_ctx* c, Plan& P, double dt, int K, uint64_t seed, uint32_t step_index,
-                    const uint32_t* step_ptr, int exit_mode, const OutDev& out, const RecDev* rec, cudaStream_t s,
-                    cudaEvent_t ev_a = nullptr, cudaEvent_t ev_b = nullptr)
+sdd_status build_plan(sdd_ctx* c, Plan& P, const double* x, const double* y, const int64_t* np, int64_t count,
+                      int ppt_req, int block_req, int exit_mode, bool record)
+{
+    std::vector<NodeSeg> segs(1);
+    segs[0] = NodeSeg{x, y, np, count, 0, 0u};
+    return build_plan_segs(&c->err, c->sm_count, P, segs, ppt_req, block_req, exit_mode, record);
+}
+
+// Enqueue the estimate for a built plan. inst: the instance table; outs:
+// per-instance outputs (null: every node writes to out0).
+sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const OutDev* outs, const OutDev& out0, double dt,
+                       int K, uint64_t seed, uint32_t step_index, const uint32_t* step_ptr, int exit_mode,
+                       const RecDev* rec, cudaStream_t s, cudaEvent_t ev_a = nullptr, cudaEvent_t ev_b = nullptr)
 {
     if (P.nnodes == 0) return SDD_OK;
     if (P.ntasks > 0) {
         PathArgs a{};
-        a.inst = c->d_inst.p;
+        a.inst = inst;
         a.nodes = P.d_nodes.p;
         a.tasks = P.d_tasks.p;
         a.partials = P.d_partials.p;
@@ -325,23 +415,31 @@ sdd_status run_plan(sdd_ctx* c, Plan& P, double dt, int K, uint64_t seed, uint32
         a.step_index = step_index;
         a.step_ptr = step_ptr;
         if (rec) a.rec = *rec;
-        CU(c, cudaMemsetAsync(P.d_queue.p, 0, sizeof(int), s));
+        CU(err, cudaMemsetAsync(P.d_queue.p, 0, sizeof(int), s));
         const int64_t per_block = P.block / 32;
         const int grid = (int)std::min<int64_t>(P.grid, std::max<int64_t>(1, (P.ntasks + per_block - 1) / per_block));
-        if (ev_a) CU(c, cudaEventRecordWithFlags(ev_a, s, cudaEventRecordExternal));
-        CU(c, launch_paths(a, exit_mode, rec != nullptr, grid, P.block, s));
-        if (ev_b) CU(c, cudaEventRecordWithFlags(ev_b, s, cudaEventRecordExternal));
+        if (ev_a) CU(err, cudaEventRecordWithFlags(ev_a, s, cudaEventRecordExternal));
+        CU(err, launch_paths(a, exit_mode, rec != nullptr, grid, P.block, s));
+        if (ev_b) CU(err, cudaEventRecordWithFlags(ev_b, s, cudaEventRecordExternal));
     }
     FinalArgs f{};
-    f.inst = c->d_inst.p;
+    f.inst = inst;
     f.nodes = P.d_nodes.p;
     f.partials = P.d_partials.p;
-    f.out_table = nullptr;
-    f.out0 = out;
+    f.out_table = outs;
+    f.out0 = out0;
     f.nnodes = (int32_t)P.nnodes;
     if (rec) f.rec = *rec;
-    CU(c, launch_finalize(f, s));
+    CU(err, launch_finalize(f, s));
     return SDD_OK;
+}
+
+sdd_status run_plan(sdd_ctx* c, Plan& P, double dt, int K, uint64_t seed, uint32_t step_index,
+                    const uint32_t* step_ptr, int exit_mode, const OutDev& out, const RecDev* rec, cudaStream_t s,
+                    cudaEvent_t ev_a = nullptr, cudaEvent_t ev_b = nullptr)
+{
+    return run_plan_on(&c->err, P, c->d_inst.p, nullptr, out, dt, K, seed, step_index, step_ptr, exit_mode, rec, s,
+                       ev_a, ev_b);
 }
 
 sdd_status setup_solver(sdd_ctx* c)
@@ -894,6 +992,288 @@ void sdd_destroy(sdd_ctx* c)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;  // device buffers are freed by their destructors
+}
+
+}  // extern "C"
+
+struct sdd_batch {
+    std::vector<sdd_ctx*> ctxs;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    int device = 0;
+    int sm_count = 0;
+    DevBuf<InstDev> d_inst;
+    DevBuf<OutDev> d_out;       // outputs of sdd_batch_interface_mc
+    DevBuf<OutDev> d_step_out;  // each instance's interface statistics of sdd_batch_step
+    DevBuf<uint32_t> d_step;
+    Plan mc_plan;
+    Plan step_plan;
+    GraphSlot graph[2];
+    std::vector<int> graph_parity[2];
+    sdd_step_params graph_params{};
+    bool graph_ok = false;
+    int graph_kernels = 0;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    uint32_t step_index = 0;
+    std::string err;
+};
+
+namespace {
+
+void drop_batch_graphs(sdd_batch* b)
+{
+    for (int k = 0; k < 2; ++k) {
+        b->graph[k].release();
+        b->graph_parity[k].clear();
+    }
+    b->graph_ok = false;
+}
+
+// the step graph of the batch for the instances' current field buffers
+sdd_status capture_batch_step(sdd_batch* b, const sdd_step_params* p, int K, int slot)
+{
+    cudaStream_t s = b->cap_stream;
+    cudaGraph_t g = nullptr;
+    CU(&b->err, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    sdd_status st = SDD_OK;
+    std::vector<char> keep_w(b->ctxs.size()), keep_f(b->ctxs.size());
+    for (size_t k = 0; k < b->ctxs.size(); ++k) {
+        keep_w[k] = b->ctxs[k]->dirty_w;
+        keep_f[k] = b->ctxs[k]->dirty_fields;
+    }
+    auto rec_ev = [&](int k) {
+        if (st != SDD_OK) return;
+        cudaError_t e = cudaEventRecordWithFlags(b->ev[k], s, cudaEventRecordExternal);
+        if (e != cudaSuccess) st = fail(&b->err, SDD_ECUDA, "event: %s", cudaGetErrorString(e));
+    };
+    rec_ev(0);
+    for (sdd_ctx* c : b->ctxs) {
+        if (st != SDD_OK) break;
+        c->dirty_w = c->dirty_fields = true;
+        st = prepare(c, s);
+        if (st != SDD_OK) b->err = c->err;
+    }
+    if (st == SDD_OK)
+        st = run_plan_on(&b->err, b->step_plan, b->d_inst.p, b->d_step_out.p, OutDev{}, p->dt, K, p->seed, 0,
+                         b->d_step.p, p->exit_mode, nullptr, s, b->ev[1], b->ev[2]);
+    rec_ev(3);
+    for (sdd_ctx* c : b->ctxs) {
+        if (st != SDD_OK) break;
+        st = enqueue_solve(c, p->Dt, c->iface_stats[0].p, c->iface_stats[1].p, p->rtol, p->max_iter,
+                           c->fld[1 - c->cur][0].p, c->fld[1 - c->cur][1].p, s);
+        if (st != SDD_OK) b->err = c->err;
+    }
+    if (st == SDD_OK) {
+        cudaError_t e = launch_bump_step(b->d_step.p, s);
+        if (e != cudaSuccess) st = fail(&b->err, SDD_ECUDA, "%s", cudaGetErrorString(e));
+    }
+    rec_ev(4);
+    for (size_t k = 0; k < b->ctxs.size(); ++k) {
+        b->ctxs[k]->dirty_w = keep_w[k];
+        b->ctxs[k]->dirty_fields = keep_f[k];
+    }
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (st != SDD_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return fail(&b->err, SDD_ECUDA, "capture: %s", cudaGetErrorString(e));
+    b->graph[slot].release();
+    size_t nn = 0;
+    if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+        std::vector<cudaGraphNode_t> nodes(nn);
+        int kernels = 0;
+        if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+            for (size_t k = 0; k < nn; ++k) {
+                cudaGraphNodeType t;
+                if (cudaGraphNodeGetType(nodes[k], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+            }
+        b->graph_kernels = kernels;
+    }
+    e = cudaGraphInstantiate(&b->graph[slot].exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->graph[slot].exec = nullptr;
+        return fail(&b->err, SDD_ECUDA, "instantiate: %s", cudaGetErrorString(e));
+    }
+    b->graph_parity[slot].clear();
+    for (sdd_ctx* c : b->ctxs) b->graph_parity[slot].push_back(c->cur);
+    return SDD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sdd_status sdd_batch_create(sdd_batch** out, sdd_ctx* const* ctxs, int32_t count, void* stream)
+{
+    if (!out || !ctxs || count < 1) return SDD_EINVAL;
+    *out = nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SDD_ECUDA;
+    for (int32_t k = 0; k < count; ++k)
+        if (!ctxs[k] || ctxs[k]->device != dev) return SDD_EINVAL;
+    for (int32_t a = 0; a < count; ++a)
+        for (int32_t c = a + 1; c < count; ++c)
+            if (ctxs[a] == ctxs[c]) return SDD_EINVAL;
+    sdd_batch* b = new (std::nothrow) sdd_batch();
+    if (!b) return SDD_ENOMEM;
+    b->ctxs.assign(ctxs, ctxs + count);
+    b->stream = (cudaStream_t)stream;
+    b->device = dev;
+    b->sm_count = ctxs[0]->sm_count;
+    auto bail = [&](sdd_status st) {
+        sdd_batch_destroy(b);
+        return st;
+    };
+    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(SDD_ECUDA);
+    for (int k = 0; k < 5; ++k)
+        if (cudaEventCreate(&b->ev[k]) != cudaSuccess) return bail(SDD_ECUDA);
+    std::vector<InstDev> inst(count);
+    std::vector<OutDev> outs(count);
+    for (int32_t k = 0; k < count; ++k) {
+        inst[k] = inst_host(ctxs[k]);
+        sdd_ctx* c = ctxs[k];
+        outs[k].mean_xi = c->iface_stats[0].p;
+        outs[k].mean_eta = c->iface_stats[1].p;
+        outs[k].se_xi = c->iface_stats[2].p;
+        outs[k].se_eta = c->iface_stats[3].p;
+        outs[k].n_exit = c->iface_counts[0].p;
+        outs[k].path_steps = c->iface_counts[1].p;
+    }
+    if (b->d_inst.alloc(count) != cudaSuccess || b->d_out.alloc(count) != cudaSuccess ||
+        b->d_step_out.alloc(count) != cudaSuccess || b->d_step.alloc(1) != cudaSuccess)
+        return bail(SDD_ENOMEM);
+    if (cudaMemcpy(b->d_inst.p, inst.data(), count * sizeof(InstDev), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_step_out.p, outs.data(), count * sizeof(OutDev), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(b->d_step.p, 0, sizeof(uint32_t)) != cudaSuccess)
+        return bail(SDD_ECUDA);
+    *out = b;
+    return SDD_OK;
+}
+
+sdd_status sdd_batch_interface_mc(sdd_batch* b, const sdd_nodes* nodes, const sdd_mc_params* p, sdd_node_stats* out)
+{
+    if (!b || !nodes || !p || !out) return b ? fail(&b->err, SDD_EINVAL, "null argument") : SDD_EINVAL;
+    int K = 0;
+    if (!valid_params(nullptr, p->dt, p->Dt, p->exit_mode, &K))
+        return fail(&b->err, SDD_EINVAL, "dt, Dt or exit_mode rejected (Dt / dt must be an integer in [1, 2^20])");
+    const int32_t n = (int32_t)b->ctxs.size();
+    std::vector<NodeSeg> segs(n);
+    uint32_t ctr = 0;
+    for (int32_t k = 0; k < n; ++k) {
+        if (nodes[k].count > 0 && (!nodes[k].x || !nodes[k].y || !nodes[k].n_paths))
+            return fail(&b->err, SDD_EINVAL, "null node array for instance %d", k);
+        segs[k] = NodeSeg{nodes[k].x, nodes[k].y, nodes[k].n_paths, nodes[k].count, k, ctr};
+        ctr += (uint32_t)nodes[k].count;
+    }
+    sdd_status st = build_plan_segs(&b->err, b->sm_count, b->mc_plan, segs, p->paths_per_task, p->block_threads,
+                                    p->exit_mode, false);
+    if (st != SDD_OK) return st;
+    for (sdd_ctx* c : b->ctxs)
+        if ((st = prepare(c, b->stream)) != SDD_OK) return fail(&b->err, st, "%s", c->err.c_str());
+    std::vector<OutDev> outs(n);
+    for (int32_t k = 0; k < n; ++k) outs[k] = out_from(&out[k]);
+    CU(&b->err, cudaMemcpyAsync(b->d_out.p, outs.data(), n * sizeof(OutDev), cudaMemcpyHostToDevice, b->stream));
+    return run_plan_on(&b->err, b->mc_plan, b->d_inst.p, b->d_out.p, OutDev{}, p->dt, K, p->seed, p->step_index,
+                       nullptr, p->exit_mode, nullptr, b->stream);
+}
+
+sdd_status sdd_batch_step(sdd_batch* b, const sdd_step_params* p)
+{
+    if (!b || !p) return b ? fail(&b->err, SDD_EINVAL, "null argument") : SDD_EINVAL;
+    int K = 0;
+    if (!valid_params(nullptr, p->dt, p->Dt, p->exit_mode, &K)) return fail(&b->err, SDD_EINVAL, "dt, Dt or exit_mode rejected");
+    if (p->paths_per_node < 1 || p->paths_per_node > 0x7fffffffLL || p->max_iter < 0 || !(p->rtol >= 0.0))
+        return fail(&b->err, SDD_EINVAL, "paths_per_node, max_iter or rtol rejected");
+    const bool same = b->graph_ok && std::memcmp(&b->graph_params, p, sizeof *p) == 0;
+    if (!same) {
+        drop_batch_graphs(b);
+        const int32_t n = (int32_t)b->ctxs.size();
+        std::vector<std::vector<int64_t>> np(n);
+        std::vector<NodeSeg> segs(n);
+        uint32_t ctr = 0;
+        for (int32_t k = 0; k < n; ++k) {
+            sdd_ctx* c = b->ctxs[k];
+            np[k].assign(c->iface_x.size(), p->paths_per_node);
+            segs[k] = NodeSeg{c->iface_x.data(), c->iface_y.data(), np[k].data(), (int64_t)np[k].size(), k, ctr};
+            ctr += (uint32_t)np[k].size();
+        }
+        sdd_status st = build_plan_segs(&b->err, b->sm_count, b->step_plan, segs, 0, 0, p->exit_mode, false);
+        if (st != SDD_OK) return st;
+        b->graph_params = *p;
+        b->graph_ok = true;
+    }
+    // the graph whose field buffers match the instances' current ones
+    int slot = -1;
+    for (int k = 0; k < 2 && slot < 0; ++k) {
+        if (!b->graph[k].exec || b->graph_parity[k].size() != b->ctxs.size()) continue;
+        bool match = true;
+        for (size_t i = 0; i < b->ctxs.size(); ++i) match = match && b->graph_parity[k][i] == b->ctxs[i]->cur;
+        if (match) slot = k;
+    }
+    if (slot < 0) {
+        slot = b->graph[0].exec ? 1 : 0;
+        if (b->graph[0].exec && b->graph[1].exec) slot = 0;
+        CU(&b->err, cudaStreamSynchronize(b->stream));
+        sdd_status st = capture_batch_step(b, p, K, slot);
+        if (st != SDD_OK) return st;
+    }
+    CU(&b->err, cudaMemcpyAsync(b->d_step.p, &b->step_index, sizeof(uint32_t), cudaMemcpyHostToDevice, b->stream));
+    CU(&b->err, cudaGraphLaunch(b->graph[slot].exec, b->stream));
+    for (sdd_ctx* c : b->ctxs) {
+        c->cur = 1 - c->cur;
+        c->step_index = b->step_index + 1;
+        c->dirty_w = false;
+        c->dirty_fields = true;
+    }
+    b->step_index += 1;
+    return SDD_OK;
+}
+
+sdd_status sdd_batch_last_step_info(sdd_batch* b, sdd_step_info* out)
+{
+    if (!b || !out) return SDD_EINVAL;
+    if (!b->graph_ok) return fail(&b->err, SDD_EINVAL, "no step has run");
+    CU(&b->err, cudaStreamSynchronize(b->stream));
+    out->kernel_nodes = b->graph_kernels;
+    CU(&b->err, cudaEventElapsedTime(&out->paths_ms, b->ev[1], b->ev[2]));
+    CU(&b->err, cudaEventElapsedTime(&out->estimate_ms, b->ev[0], b->ev[3]));
+    CU(&b->err, cudaEventElapsedTime(&out->solve_ms, b->ev[3], b->ev[4]));
+    CU(&b->err, cudaEventElapsedTime(&out->step_ms, b->ev[0], b->ev[4]));
+    return SDD_OK;
+}
+
+sdd_status sdd_batch_set_step_index(sdd_batch* b, uint32_t n)
+{
+    if (!b) return SDD_EINVAL;
+    b->step_index = n;
+    for (sdd_ctx* c : b->ctxs) c->step_index = n;
+    return SDD_OK;
+}
+
+sdd_status sdd_batch_sync(sdd_batch* b)
+{
+    if (!b) return SDD_EINVAL;
+    CU(&b->err, cudaStreamSynchronize(b->stream));
+    for (sdd_ctx* c : b->ctxs) {
+        sdd_status st = sdd_sync(c);
+        if (st != SDD_OK) return fail(&b->err, st, "%s", c->err.c_str());
+    }
+    return SDD_OK;
+}
+
+const char* sdd_batch_last_error(const sdd_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+void sdd_batch_destroy(sdd_batch* b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    drop_batch_graphs(b);
+    for (int k = 0; k < 5; ++k)
+        if (b->ev[k]) cudaEventDestroy(b->ev[k]);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    delete b;
 }
 
 sdd_status sdd_rng_draw(uint64_t seed, const uint32_t* ctrs, int64_t count, uint32_t* words, float* normals,
