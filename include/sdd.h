@@ -175,6 +175,22 @@ sdd_status sdd_interface_mc(sdd_ctx* ctx, const sdd_nodes* nodes, const sdd_mc_p
 sdd_status sdd_interface_mc_record(sdd_ctx* ctx, const sdd_nodes* nodes, const sdd_mc_params* p,
                                    sdd_node_stats* out, const sdd_path_records* rec);
 
+/* Launch shape of the path kernel: threads per block and paths per task (a
+ * task is a node and a run of its paths that one warp computes). */
+typedef struct {
+    int32_t block_threads;
+    int32_t paths_per_task;
+    float ms;   /* measured time of one estimate with this shape */
+} sdd_launch_shape;
+
+/* Autotuner: time the interface estimate of this node set and these
+ * parameters with every candidate launch shape (128, 256, 512 threads x 32 ..
+ * 1024 paths per task; outputs discarded; uses the context's current tables),
+ * keep the fastest, and use it for later calls on the same node set, K and
+ * exit mode that leave block_threads and paths_per_task at 0. Waits for the
+ * stream. `out` (HOST, may be NULL) receives the chosen shape. */
+sdd_status sdd_autotune(sdd_ctx* ctx, const sdd_nodes* nodes, const sdd_mc_params* p, sdd_launch_shape* out);
+
 /* The interface nodes of the context's decomposition (each once): first the
  * vertical lines left to right, each bottom to top (j = 1 .. ny-2), then the
  * horizontal lines bottom to top, each left to right (i = 1 .. nx-2), skipping
@@ -213,6 +229,8 @@ typedef struct {
     int32_t exit_mode;
     int32_t max_iter;
     double rtol;
+    int32_t tune;   /* nonzero: autotune the path kernel's launch shape for this step (see sdd_autotune) */
+    int32_t pad;
 } sdd_step_params;
 
 sdd_status sdd_step(sdd_ctx* ctx, const sdd_step_params* p);
@@ -272,6 +290,9 @@ sdd_status sdd_batch_interface_mc(sdd_batch* b, const sdd_nodes* nodes, const sd
  * instance's subdomain solves; recorded once into a CUDA graph and replayed.
  * The batch's step counter (shared by the instances) advances by one. */
 sdd_status sdd_batch_step(sdd_batch* b, const sdd_step_params* p);
+
+/* As sdd_autotune for the batched estimate (nodes: one list per instance). */
+sdd_status sdd_batch_autotune(sdd_batch* b, const sdd_nodes* nodes, const sdd_mc_params* p, sdd_launch_shape* out);
 
 /* As sdd_last_step_info, for the last sdd_batch_step (waits for the stream). */
 sdd_status sdd_batch_last_step_info(sdd_batch* b, sdd_step_info* out);

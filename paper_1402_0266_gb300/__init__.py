@@ -34,7 +34,7 @@ EXPORTS = [
     "sdd_sync", "sdd_last_error", "sdd_destroy", "sdd_rng_draw", "sdd_interface_mc_static",
     "sdd_static_scratch_bytes", "sdd_batch_create", "sdd_batch_interface_mc", "sdd_batch_step",
     "sdd_batch_last_step_info", "sdd_batch_set_step_index", "sdd_batch_sync", "sdd_batch_last_error",
-    "sdd_batch_destroy",
+    "sdd_batch_destroy", "sdd_autotune", "sdd_batch_autotune",
 ]
 
 
@@ -81,7 +81,11 @@ class _StepInfo(ctypes.Structure):
 class _StepParams(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("Dt", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("paths_per_node", ctypes.c_int64), ("exit_mode", ctypes.c_int32), ("max_iter", ctypes.c_int32),
-                ("rtol", ctypes.c_double)]
+                ("rtol", ctypes.c_double), ("tune", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class _Shape(ctypes.Structure):
+    _fields_ = [("block_threads", ctypes.c_int32), ("paths_per_task", ctypes.c_int32), ("ms", ctypes.c_float)]
 
 
 _lib = None
@@ -134,6 +138,8 @@ def lib():
                 "sdd_batch_sync": [vp],
                 "sdd_batch_last_error": [vp],
                 "sdd_batch_destroy": [vp],
+                "sdd_autotune": [vp, ctypes.POINTER(_Nodes), ctypes.POINTER(_McParams), ctypes.POINTER(_Shape)],
+                "sdd_batch_autotune": [vp, ctypes.POINTER(_Nodes), ctypes.POINTER(_McParams), ctypes.POINTER(_Shape)],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -340,12 +346,12 @@ def sdd_subdomain_solve(ctx: Ctx, Dt, iface_xi, iface_eta, rtol=1e-12, max_iter=
     return xi, eta, it.value
 
 
-def step_params(dt, Dt, seed=0, paths_per_node=10000, exit_mode=0, max_iter=20000, rtol=1e-12):
-    return _StepParams(dt, Dt, seed, paths_per_node, exit_mode, max_iter, rtol)
+def step_params(dt, Dt, seed=0, paths_per_node=10000, exit_mode=0, max_iter=20000, rtol=1e-12, tune=0):
+    return _StepParams(dt, Dt, seed, paths_per_node, exit_mode, max_iter, rtol, tune, 0)
 
 
-def sdd_step(ctx: Ctx, dt, Dt, seed=0, paths_per_node=10000, exit_mode=0, max_iter=20000, rtol=1e-12):
-    p = step_params(dt, Dt, seed, paths_per_node, exit_mode, max_iter, rtol)
+def sdd_step(ctx: Ctx, dt, Dt, seed=0, paths_per_node=10000, exit_mode=0, max_iter=20000, rtol=1e-12, tune=0):
+    p = step_params(dt, Dt, seed, paths_per_node, exit_mode, max_iter, rtol, tune)
     ctx._check(lib().sdd_step(ctx.handle, ctypes.byref(p)))
 
 
@@ -487,8 +493,9 @@ def sdd_batch_interface_mc(batch: Batch, node_lists, dt, Dt, seed=0, step_index=
     return outs
 
 
-def sdd_batch_step(batch: Batch, dt, Dt, seed=0, paths_per_node=10000, exit_mode=0, max_iter=20000, rtol=1e-12):
-    p = step_params(dt, Dt, seed, paths_per_node, exit_mode, max_iter, rtol)
+def sdd_batch_step(batch: Batch, dt, Dt, seed=0, paths_per_node=10000, exit_mode=0, max_iter=20000, rtol=1e-12,
+                   tune=0):
+    p = step_params(dt, Dt, seed, paths_per_node, exit_mode, max_iter, rtol, tune)
     batch._check(lib().sdd_batch_step(batch.handle, ctypes.byref(p)))
 
 
@@ -515,3 +522,27 @@ def sdd_batch_destroy(batch: Batch):
     if batch.handle is not None and batch.handle.value:
         lib().sdd_batch_destroy(batch.handle)
     batch.handle = ctypes.c_void_p(0)
+
+
+def sdd_autotune(ctx: Ctx, x, y, n_paths, dt, Dt, exit_mode=0) -> dict:
+    """Pick the fastest launch shape for this node set (see include/sdd.h)."""
+    nodes, keep = _nodes(x, y, n_paths)
+    p = mc_params(dt, Dt, 0, 0, exit_mode, 0, 0)
+    out = _Shape()
+    ctx._check(lib().sdd_autotune(ctx.handle, ctypes.byref(nodes), ctypes.byref(p), ctypes.byref(out)))
+    del keep
+    return {"block_threads": out.block_threads, "paths_per_task": out.paths_per_task, "ms": out.ms}
+
+
+def sdd_batch_autotune(batch: Batch, node_lists, dt, Dt, exit_mode=0) -> dict:
+    n = len(batch.ctxs)
+    keep, nodes = [], (_Nodes * n)()
+    for k, (x, y, npaths) in enumerate(node_lists):
+        nd, kp = _nodes(x, y, npaths)
+        keep.append(kp)
+        nodes[k] = nd
+    p = mc_params(dt, Dt, 0, 0, exit_mode, 0, 0)
+    out = _Shape()
+    batch._check(lib().sdd_batch_autotune(batch.handle, nodes, ctypes.byref(p), ctypes.byref(out)))
+    del keep
+    return {"block_threads": out.block_threads, "paths_per_task": out.paths_per_task, "ms": out.ms}

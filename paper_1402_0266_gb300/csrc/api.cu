@@ -64,6 +64,14 @@ struct Plan {
 
 };
 
+// Launch shapes chosen by the autotuner, keyed by a hash of the node set and
+// the parameters that change the work (K, exit mode).
+struct TunedShape {
+    uint64_t key;
+    int block, ppt;
+    float ms;
+};
+
 struct GraphSlot {
     cudaGraphExec_t exec = nullptr;
     void release()
@@ -96,6 +104,7 @@ struct sdd_ctx {
 
     Plan mc_plan;     // sdd_interface_mc
     Plan step_plan;   // the interface nodes of sdd_step
+    std::vector<TunedShape> tuned;
     std::vector<double> iface_x, iface_y;
     std::vector<int32_t> iface_idx;
     DevBuf<int32_t> d_iface_idx;
@@ -384,6 +393,103 @@ sdd_status build_plan_segs(std::string* err, int sm_count, Plan& P, const std::v
     return SDD_OK;
 }
 
+uint64_t shape_key(const std::vector<NodeSeg>& segs, int K, int exit_mode)
+{
+    uint64_t h = 1469598103934665603ULL;
+    auto mix = [&](const void* p, size_t n) {
+        const unsigned char* b = (const unsigned char*)p;
+        for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ULL;
+    };
+    for (const NodeSeg& g : segs) {
+        mix(&g.count, sizeof g.count);
+        mix(&g.inst, sizeof g.inst);
+        mix(g.x, g.count * sizeof(double));
+        mix(g.y, g.count * sizeof(double));
+        mix(g.np, g.count * sizeof(int64_t));
+    }
+    mix(&K, sizeof K);
+    mix(&exit_mode, sizeof exit_mode);
+    return h;
+}
+
+sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const OutDev* outs, const OutDev& out0, double dt,
+                       int K, uint64_t seed, uint32_t step_index, const uint32_t* step_ptr, int exit_mode,
+                       const RecDev* rec, cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_b);
+
+const TunedShape* find_tuned(const std::vector<TunedShape>& t, uint64_t key)
+{
+    for (const TunedShape& s : t)
+        if (s.key == key) return &s;
+    return nullptr;
+}
+
+// Time every candidate launch shape on this node set (outputs discarded) and
+// keep the fastest: block sizes 128 / 256 / 512 x paths per task 32 .. 1024.
+sdd_status autotune_plan(std::string* err, int sm_count, const std::vector<NodeSeg>& segs, const InstDev* inst,
+                         int ninst, int K, double dt, int exit_mode, cudaStream_t s, std::vector<TunedShape>& cache,
+                         TunedShape* best_out)
+{
+    int64_t count = 0;
+    for (const NodeSeg& g : segs) count += g.count;
+    DevBuf<double> dmean;
+    DevBuf<OutDev> dout;
+    CU(err, dmean.alloc(std::max<int64_t>(count, 1)));
+    std::vector<OutDev> outs(ninst);
+    {
+        int64_t o = 0;
+        for (int k = 0; k < ninst; ++k) {
+            outs[k] = OutDev{};
+            outs[k].mean_xi = dmean.p + o;  // only the means are written, each instance its own slice
+            o += segs[k].count;
+        }
+    }
+    CU(err, dout.alloc(ninst));
+    CU(err, cudaMemcpy(dout.p, outs.data(), ninst * sizeof(OutDev), cudaMemcpyHostToDevice));
+    cudaEvent_t e0, e1;
+    CU(err, cudaEventCreate(&e0));
+    CU(err, cudaEventCreate(&e1));
+    TunedShape best{shape_key(segs, K, exit_mode), 256, 0, 1e30f};
+    sdd_status st = SDD_OK;
+    for (int block : {128, 256, 512}) {
+        for (int ppt : {32, 64, 128, 256, 512, 1024}) {
+            Plan P;
+            st = build_plan_segs(err, sm_count, P, segs, ppt, block, exit_mode, false);
+            if (st != SDD_OK) break;
+            // one untimed run, then the mean of two timed runs
+            st = run_plan_on(err, P, inst, dout.p, OutDev{}, dt, K, 0x5EEDULL, 0, nullptr, exit_mode, nullptr, s,
+                             nullptr, nullptr);
+            if (st == SDD_OK && cudaEventRecord(e0, s) != cudaSuccess) st = fail(err, SDD_ECUDA, "event record");
+            for (int r = 0; r < 2 && st == SDD_OK; ++r)
+                st = run_plan_on(err, P, inst, dout.p, OutDev{}, dt, K, 0x5EEDULL + r, 0, nullptr, exit_mode, nullptr, s,
+                                 nullptr, nullptr);
+            if (st == SDD_OK && cudaEventRecord(e1, s) != cudaSuccess) st = fail(err, SDD_ECUDA, "event record");
+            if (st == SDD_OK && cudaEventSynchronize(e1) != cudaSuccess) st = fail(err, SDD_ECUDA, "event sync");
+            if (st != SDD_OK) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms *= 0.5f;
+            if (ms < best.ms) {
+                best.block = block;
+                best.ppt = ppt;
+                best.ms = ms;
+            }
+        }
+        if (st != SDD_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != SDD_OK) return st;
+    for (TunedShape& t : cache)
+        if (t.key == best.key) {
+            t = best;
+            *best_out = best;
+            return SDD_OK;
+        }
+    cache.push_back(best);
+    *best_out = best;
+    return SDD_OK;
+}
+
 sdd_status build_plan(sdd_ctx* c, Plan& P, const double* x, const double* y, const int64_t* np, int64_t count,
                       int ppt_req, int block_req, int exit_mode, bool record)
 {
@@ -396,7 +502,7 @@ sdd_status build_plan(sdd_ctx* c, Plan& P, const double* x, const double* y, con
 // per-instance outputs (null: every node writes to out0).
 sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const OutDev* outs, const OutDev& out0, double dt,
                        int K, uint64_t seed, uint32_t step_index, const uint32_t* step_ptr, int exit_mode,
-                       const RecDev* rec, cudaStream_t s, cudaEvent_t ev_a = nullptr, cudaEvent_t ev_b = nullptr)
+                       const RecDev* rec, cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_b)
 {
     if (P.nnodes == 0) return SDD_OK;
     if (P.ntasks > 0) {
@@ -440,6 +546,18 @@ sdd_status run_plan(sdd_ctx* c, Plan& P, double dt, int K, uint64_t seed, uint32
 {
     return run_plan_on(&c->err, P, c->d_inst.p, nullptr, out, dt, K, seed, step_index, step_ptr, exit_mode, rec, s,
                        ev_a, ev_b);
+}
+
+// Launch shape for a plan: explicit requests win, else a tuned shape for this node set, else the heuristic.
+void pick_shape(const std::vector<TunedShape>& cache, const std::vector<NodeSeg>& segs, int K, int exit_mode,
+                int* ppt, int* block)
+{
+    if (*ppt || *block) return;
+    const TunedShape* t = find_tuned(cache, shape_key(segs, K, exit_mode));
+    if (t) {
+        *ppt = t->ppt;
+        *block = t->block;
+    }
 }
 
 sdd_status setup_solver(sdd_ctx* c)
@@ -767,8 +885,14 @@ static sdd_status mc_common(sdd_ctx* c, const sdd_nodes* nodes, const sdd_mc_par
     int K = 0;
     if (!valid_params(c, p->dt, p->Dt, p->exit_mode, &K))
         return fail(c, SDD_EINVAL, "dt, Dt or exit_mode rejected (Dt / dt must be an integer in [1, 2^20])");
-    sdd_status st = build_plan(c, c->mc_plan, nodes->x, nodes->y, nodes->n_paths, nodes->count, p->paths_per_task,
-                               p->block_threads, p->exit_mode, rec != nullptr);
+    int ppt = p->paths_per_task, block = p->block_threads;
+    {
+        std::vector<NodeSeg> segs(1);
+        segs[0] = NodeSeg{nodes->x, nodes->y, nodes->n_paths, nodes->count, 0, 0u};
+        pick_shape(c->tuned, segs, K, p->exit_mode, &ppt, &block);
+    }
+    sdd_status st = build_plan(c, c->mc_plan, nodes->x, nodes->y, nodes->n_paths, nodes->count, ppt, block,
+                               p->exit_mode, rec != nullptr);
     if (st != SDD_OK) return st;
     if ((st = prepare(c, c->stream)) != SDD_OK) return st;
     RecDev rd{};
@@ -794,6 +918,27 @@ sdd_status sdd_interface_mc_record(sdd_ctx* c, const sdd_nodes* nodes, const sdd
 {
     if (!rec) return fail(c, SDD_EINVAL, "null records");
     return mc_common(c, nodes, p, out, rec);
+}
+
+sdd_status sdd_autotune(sdd_ctx* c, const sdd_nodes* nodes, const sdd_mc_params* p, sdd_launch_shape* out)
+{
+    if (!c || !nodes || !p) return fail(c, SDD_EINVAL, "null argument");
+    if (nodes->count > 0 && (!nodes->x || !nodes->y || !nodes->n_paths)) return fail(c, SDD_EINVAL, "null node array");
+    int K = 0;
+    if (!valid_params(c, p->dt, p->Dt, p->exit_mode, &K)) return fail(c, SDD_EINVAL, "dt, Dt or exit_mode rejected");
+    sdd_status st = prepare(c, c->stream);
+    if (st != SDD_OK) return st;
+    std::vector<NodeSeg> segs(1);
+    segs[0] = NodeSeg{nodes->x, nodes->y, nodes->n_paths, nodes->count, 0, 0u};
+    TunedShape best{};
+    st = autotune_plan(&c->err, c->sm_count, segs, c->d_inst.p, 1, K, p->dt, p->exit_mode, c->stream, c->tuned, &best);
+    if (st != SDD_OK) return st;
+    if (out) {
+        out->block_threads = best.block;
+        out->paths_per_task = best.ppt;
+        out->ms = best.ms;
+    }
+    return SDD_OK;
 }
 
 sdd_status sdd_interface_nodes(sdd_ctx* c, double* x, double* y, int64_t* count)
@@ -912,8 +1057,20 @@ sdd_status sdd_step(sdd_ctx* c, const sdd_step_params* p)
     if (!same) {
         drop_graphs(c);
         std::vector<int64_t> np(c->iface_x.size(), p->paths_per_node);
+        std::vector<NodeSeg> segs(1);
+        segs[0] = NodeSeg{c->iface_x.data(), c->iface_y.data(), np.data(), (int64_t)np.size(), 0, 0u};
+        if (p->tune && !find_tuned(c->tuned, shape_key(segs, K, p->exit_mode))) {
+            sdd_status st0 = prepare(c, c->stream);
+            if (st0 != SDD_OK) return st0;
+            TunedShape best{};
+            st0 = autotune_plan(&c->err, c->sm_count, segs, c->d_inst.p, 1, K, p->dt, p->exit_mode, c->stream, c->tuned,
+                                &best);
+            if (st0 != SDD_OK) return st0;
+        }
+        int ppt = 0, block = 0;
+        pick_shape(c->tuned, segs, K, p->exit_mode, &ppt, &block);
         sdd_status st = build_plan(c, c->step_plan, c->iface_x.data(), c->iface_y.data(), np.data(),
-                                   (int64_t)np.size(), 0, 0, p->exit_mode, false);
+                                   (int64_t)np.size(), ppt, block, p->exit_mode, false);
         if (st != SDD_OK) return st;
         CU(c, cudaStreamSynchronize(c->stream));
         for (int parity = 0; parity < 2; ++parity)
@@ -1008,6 +1165,7 @@ struct sdd_batch {
     DevBuf<uint32_t> d_step;
     Plan mc_plan;
     Plan step_plan;
+    std::vector<TunedShape> tuned;
     GraphSlot graph[2];
     std::vector<int> graph_parity[2];
     sdd_step_params graph_params{};
@@ -1167,8 +1325,9 @@ sdd_status sdd_batch_interface_mc(sdd_batch* b, const sdd_nodes* nodes, const sd
         segs[k] = NodeSeg{nodes[k].x, nodes[k].y, nodes[k].n_paths, nodes[k].count, k, ctr};
         ctr += (uint32_t)nodes[k].count;
     }
-    sdd_status st = build_plan_segs(&b->err, b->sm_count, b->mc_plan, segs, p->paths_per_task, p->block_threads,
-                                    p->exit_mode, false);
+    int ppt = p->paths_per_task, block = p->block_threads;
+    pick_shape(b->tuned, segs, K, p->exit_mode, &ppt, &block);
+    sdd_status st = build_plan_segs(&b->err, b->sm_count, b->mc_plan, segs, ppt, block, p->exit_mode, false);
     if (st != SDD_OK) return st;
     for (sdd_ctx* c : b->ctxs)
         if ((st = prepare(c, b->stream)) != SDD_OK) return fail(&b->err, st, "%s", c->err.c_str());
@@ -1176,7 +1335,7 @@ sdd_status sdd_batch_interface_mc(sdd_batch* b, const sdd_nodes* nodes, const sd
     for (int32_t k = 0; k < n; ++k) outs[k] = out_from(&out[k]);
     CU(&b->err, cudaMemcpyAsync(b->d_out.p, outs.data(), n * sizeof(OutDev), cudaMemcpyHostToDevice, b->stream));
     return run_plan_on(&b->err, b->mc_plan, b->d_inst.p, b->d_out.p, OutDev{}, p->dt, K, p->seed, p->step_index,
-                       nullptr, p->exit_mode, nullptr, b->stream);
+                       nullptr, p->exit_mode, nullptr, b->stream, nullptr, nullptr);
 }
 
 sdd_status sdd_batch_step(sdd_batch* b, const sdd_step_params* p)
@@ -1199,7 +1358,19 @@ sdd_status sdd_batch_step(sdd_batch* b, const sdd_step_params* p)
             segs[k] = NodeSeg{c->iface_x.data(), c->iface_y.data(), np[k].data(), (int64_t)np[k].size(), k, ctr};
             ctr += (uint32_t)np[k].size();
         }
-        sdd_status st = build_plan_segs(&b->err, b->sm_count, b->step_plan, segs, 0, 0, p->exit_mode, false);
+        if (p->tune && !find_tuned(b->tuned, shape_key(segs, K, p->exit_mode))) {
+            for (sdd_ctx* c : b->ctxs) {
+                sdd_status st0 = prepare(c, b->stream);
+                if (st0 != SDD_OK) return fail(&b->err, st0, "%s", c->err.c_str());
+            }
+            TunedShape best{};
+            sdd_status st0 = autotune_plan(&b->err, b->sm_count, segs, b->d_inst.p, n, K, p->dt, p->exit_mode,
+                                           b->stream, b->tuned, &best);
+            if (st0 != SDD_OK) return st0;
+        }
+        int ppt = 0, block = 0;
+        pick_shape(b->tuned, segs, K, p->exit_mode, &ppt, &block);
+        sdd_status st = build_plan_segs(&b->err, b->sm_count, b->step_plan, segs, ppt, block, p->exit_mode, false);
         if (st != SDD_OK) return st;
         b->graph_params = *p;
         b->graph_ok = true;
@@ -1228,6 +1399,36 @@ sdd_status sdd_batch_step(sdd_batch* b, const sdd_step_params* p)
         c->dirty_fields = true;
     }
     b->step_index += 1;
+    return SDD_OK;
+}
+
+sdd_status sdd_batch_autotune(sdd_batch* b, const sdd_nodes* nodes, const sdd_mc_params* p, sdd_launch_shape* out)
+{
+    if (!b || !nodes || !p) return b ? fail(&b->err, SDD_EINVAL, "null argument") : SDD_EINVAL;
+    int K = 0;
+    if (!valid_params(nullptr, p->dt, p->Dt, p->exit_mode, &K)) return fail(&b->err, SDD_EINVAL, "dt, Dt or exit_mode rejected");
+    const int32_t n = (int32_t)b->ctxs.size();
+    std::vector<NodeSeg> segs(n);
+    uint32_t ctr = 0;
+    for (int32_t k = 0; k < n; ++k) {
+        if (nodes[k].count > 0 && (!nodes[k].x || !nodes[k].y || !nodes[k].n_paths))
+            return fail(&b->err, SDD_EINVAL, "null node array for instance %d", k);
+        segs[k] = NodeSeg{nodes[k].x, nodes[k].y, nodes[k].n_paths, nodes[k].count, k, ctr};
+        ctr += (uint32_t)nodes[k].count;
+    }
+    for (sdd_ctx* c : b->ctxs) {
+        sdd_status st = prepare(c, b->stream);
+        if (st != SDD_OK) return fail(&b->err, st, "%s", c->err.c_str());
+    }
+    TunedShape best{};
+    sdd_status st = autotune_plan(&b->err, b->sm_count, segs, b->d_inst.p, n, K, p->dt, p->exit_mode, b->stream,
+                                  b->tuned, &best);
+    if (st != SDD_OK) return st;
+    if (out) {
+        out->block_threads = best.block;
+        out->paths_per_task = best.ppt;
+        out->ms = best.ms;
+    }
     return SDD_OK;
 }
 

@@ -284,3 +284,22 @@ def test_mesh_steps_match_oracle(sdd, oracle_mod):
         assert gap <= max(iface_gap, prev_gap) + 1e-9, (step, gap, iface_gap)
         prev_gap = gap
     assert sdd.sdd_get_step_index(ctx) == 3
+
+
+def test_autotune_chooses_a_candidate_and_keeps_results(sdd):
+    n = 129
+    ctx = _ctx(sdd, W.w_front(n, 0.15), *W.identity_fields(n))
+    xs, ys = W.interface_node_coords(n, n, 2, 2)
+    kw = dict(dt=1e-4, Dt=1e-2)
+    before = _np(sdd.sdd_interface_mc_record(ctx, xs, ys, 2000, seed=21, **kw))
+    shape = sdd.sdd_autotune(ctx, xs, ys, 2000, **kw)
+    assert shape["block_threads"] in (128, 256, 512)
+    assert shape["paths_per_task"] in (32, 64, 128, 256, 512, 1024) and shape["ms"] > 0
+    after = _np(sdd.sdd_interface_mc_record(ctx, xs, ys, 2000, seed=21, **kw))
+    for k in ("steps", "code", "score_xi", "x_end"):
+        np.testing.assert_array_equal(after[k], before[k])
+    np.testing.assert_allclose(after["mean_xi"], before["mean_xi"], rtol=0, atol=1e-8)
+    # a tuned mesh step runs and advances the counter
+    sdd.sdd_step(ctx, dt=1e-4, Dt=1e-2, seed=1, paths_per_node=500, tune=1)
+    sdd.sdd_sync(ctx)
+    assert sdd.sdd_get_step_index(ctx) == 1
