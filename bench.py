@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--paths", type=int, default=WL.paths)
+    ap.add_argument("--paths", type=int, default=None)
+    ap.add_argument("--workload", choices=["front257", "batch64", "ring2049", "heat65"], default="front257")
     return ap.parse_args()
 
 
@@ -227,7 +228,8 @@ def run_ours(args, world, rank, local):
     nsteps = max(K, Wm)
     w_all = torch.from_numpy(np.stack([W.w_front(n, k * WL.Dt) for k in range(nsteps)])).to(dev)
     ctx = sdd.sdd_init(n, n, WL.sub, WL.sub, w=w_all[0], xi0=xi0_d, eta0=eta0_d)
-    sp = dict(dt=WL.dt, Dt=WL.Dt, seed=seed, paths_per_node=args.paths, exit_mode=0, rtol=1e-12, max_iter=20000)
+    sp = dict(dt=WL.dt, Dt=WL.Dt, seed=seed, paths_per_node=args.paths, exit_mode=0, rtol=1e-12, max_iter=20000,
+              tune=1)
 
     def reset():
         sdd.sdd_set_fields(ctx, xi0_d, eta0_d)
@@ -348,8 +350,116 @@ def run_ours(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_batch64(args, world, rank, local):
+    """The 64-instance workload: one batched interface estimate (one persistent launch) per step."""
+    import torch
+
+    import paper_1402_0266_gb300 as sdd
+    from paper_1402_0266_gb300 import build as b
+    b.build()
+    torch.cuda.set_device(local)
+    insts = W.batch64_instances(seed=0)
+    ctxs, lists = [], []
+    for I in insts:
+        w = torch.from_numpy(W.w_bump(I.n, I.cx, I.cy, I.width, I.alpha)).cuda()
+        ctxs.append(sdd.sdd_init(I.n, I.n, 2, 2, w=w))
+        lists.append((I.nodes_i / (I.n - 1), I.nodes_j / (I.n - 1), I.paths))
+    batch = sdd.sdd_batch_create(ctxs)
+    dt, Dt = 1e-4, 1e-2
+    shape = sdd.sdd_batch_autotune(batch, lists, dt, Dt)
+    for k in range(args.warmup):
+        sdd.sdd_batch_interface_mc(batch, lists, dt, Dt, seed=rank, step_index=k)
+    torch.cuda.synchronize()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    times, steps = [], 0
+    for k in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        outs = sdd.sdd_batch_interface_mc(batch, lists, dt, Dt, seed=rank, step_index=k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        steps += sum(int(o["path_steps"].sum()) for o in outs)
+    ms = sum(times)
+    nodes = sum(l[0].size for l in lists)
+    if rank == 0:
+        print(json.dumps({"metric": METRIC.replace("whole mesh steps", "batched estimate"), "value": steps / (ms / 1e3),
+                          "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                          "config": {"workload": f"batch64: 64 instances, grids 65..513, {nodes} nodes, paths 1e3..1e5 "
+                                                 f"log-uniform, dt={dt}, Dt={Dt}, one persistent launch per step",
+                                     "tuned_shape": shape},
+                          "interface_nodes_per_s": nodes * args.steps / (ms / 1e3),
+                          "path_steps_per_step": steps / args.steps}), flush=True)
+
+
+def run_ring2049(args, world, rank, local):
+    """The large ring workload: mesh steps on 2049 x 2049 with 8 x 8 subdomains."""
+    import torch
+
+    import paper_1402_0266_gb300 as sdd
+    from paper_1402_0266_gb300 import build as b
+    b.build()
+    torch.cuda.set_device(local)
+    wl = W.RING2049
+    n = wl.n
+    paths = args.paths or wl.paths
+    ctx = sdd.sdd_init(n, n, wl.sub, wl.sub, w=torch.from_numpy(W.w_ring(n, 0.0)).cuda())
+    sp = dict(dt=wl.dt, Dt=wl.Dt, seed=rank, paths_per_node=paths, exit_mode=0, rtol=1e-12, max_iter=40000, tune=1)
+    for k in range(args.warmup):
+        sdd.sdd_set_w(ctx, torch.from_numpy(W.w_ring(n, k * wl.Dt)).cuda())
+        sdd.sdd_step(ctx, **sp)
+    sdd.sdd_sync(ctx)
+    times, steps, pk, sv = [], 0, [], []
+    for k in range(args.steps):
+        w = torch.from_numpy(W.w_ring(n, (args.warmup + k) * wl.Dt)).cuda()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sdd.sdd_set_w(ctx, w)
+        sdd.sdd_step(ctx, **sp)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        st = sdd.sdd_last_interface_stats(ctx)
+        steps += int(st["path_steps"].sum())
+        info = sdd.sdd_last_step_info(ctx)
+        pk.append(info["paths_ms"])
+        sv.append(info["solve_ms"])
+    sdd.sdd_sync(ctx)
+    ms = sum(times)
+    nodes = len(sdd.sdd_interface_nodes(ctx)[0])
+    if rank == 0:
+        print(json.dumps({"metric": METRIC, "value": steps / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                          "data": "synthetic",
+                          "config": {"workload": f"ring2049: {n}x{n}, 8x8 subdomains, {nodes} nodes x {paths} paths, "
+                                                 f"dt={wl.dt}, Dt={wl.Dt}"},
+                          "interface_nodes_per_s": nodes * args.steps / (ms / 1e3),
+                          "path_steps_per_step": steps / args.steps, "paths_kernel_ms": statistics.mean(pk),
+                          "solve_ms": statistics.mean(sv),
+                          "roofline_frac_paths": ALG_OPS_PER_PATH_STEP * steps / args.steps / (statistics.mean(pk) / 1e3)
+                          / 1e12 / (152 * SM_LANES_PER_CLK * 2070e6 / 1e12)}), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "batch64" and args.impl == "ours":
+        world, rank, local = dist_init()
+        run_batch64(args, world, rank, local)
+        return
+    if args.workload == "ring2049" and args.impl == "ours":
+        world, rank, local = dist_init()
+        run_ring2049(args, world, rank, local)
+        return
+    if args.paths is None:
+        args.paths = WL.paths
     if args.impl == "reference":
         # the CPU oracle: rank 0 alone runs; other ranks exit without work
         run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")))
