@@ -54,7 +54,7 @@ class _Problem(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("bx", ctypes.c_void_p), ("by", ctypes.c_void_p),
                 ("xi0", ctypes.c_void_p), ("eta0", ctypes.c_void_p),
-                ("faces", ctypes.c_void_p)]
+                ("faces", ctypes.c_void_p), ("cv", ctypes.c_void_p), ("cv_slices", ctypes.c_int)]
 
 
 class _Params(ctypes.Structure):
@@ -223,7 +223,7 @@ def sub_steps(dt: float, Dt: float) -> int:
 
 def interface_mc(problem: Problem, xs, ys, n_paths, *, dt: float, Dt: float, seed: int = 0,
                  exit_mode: int = 0, step_index: int = 0, node_ids=None,
-                 record: bool = False, threads: int | None = None):
+                 record: bool = False, threads: int | None = None, cv_table=None):
     """Estimate xi, eta at the given nodes over one mesh step (Eq. 7b, Sec. 4).
 
     Returns a dict with mean_xi, mean_eta, se_xi, se_eta, n_exit, path_steps
@@ -231,6 +231,9 @@ def interface_mc(problem: Problem, xs, ys, n_paths, *, dt: float, Dt: float, see
     score_xi, score_eta, x_end, y_end laid out node after node.
     node_ids: each node's word in the Philox counter (default 0..count-1).
     threads: worker threads over nodes (ctypes releases the GIL), default all cores.
+    cv_table: optional control-variate model gradients, shape (S, ny, nx, 4):
+    slice q serves the sub-steps j with floor(j S / K) = q; components are
+    d/dx, d/dy of the xi model and of the eta model at the nodes.
     """
     lib = _load()
     xs = np.ascontiguousarray(xs, dtype=np.float64)
@@ -241,8 +244,13 @@ def interface_mc(problem: Problem, xs, ys, n_paths, *, dt: float, Dt: float, see
         node_ids = np.arange(count, dtype=np.uint32)
     node_ids = np.ascontiguousarray(node_ids, dtype=np.uint32)
     K = sub_steps(dt, Dt)
+    cv = None
+    if cv_table is not None:
+        cv = np.ascontiguousarray(cv_table, dtype=np.float64)
+        assert cv.ndim == 4 and cv.shape[1:] == (problem.ny, problem.nx, 4)
     P = _Problem(problem.nx, problem.ny, problem.bx.ctypes.data, problem.by.ctypes.data,
-                 problem.xi0.ctypes.data, problem.eta0.ctypes.data, problem.faces.ctypes.data)
+                 problem.xi0.ctypes.data, problem.eta0.ctypes.data, problem.faces.ctypes.data,
+                 cv.ctypes.data if cv is not None else None, cv.shape[0] if cv is not None else 0)
     Q = _Params(dt, K, exit_mode, seed, step_index)
     stats = np.zeros((count, 6))
     total = int(n_paths.sum())

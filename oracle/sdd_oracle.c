@@ -153,6 +153,22 @@ double orc_bilinear(int nx, int ny, const double* f, double x, double y)
     return (1.0 - s) * (1.0 - t) * f00 + s * (1.0 - t) * f10 + (1.0 - s) * t * f01 + s * t * f11;
 }
 
+/* Bilinear interpolation of a node table whose values are strided by 4
+ * (one of the four components of a control-variate slice). */
+static double cv_bilinear(int nx, int ny, const double* f, double x, double y)
+{
+    double gx = x * (double)(nx - 1), gy = y * (double)(ny - 1);
+    int i = (int)floor(gx), j = (int)floor(gy);
+    if (i < 0) i = 0;
+    if (i > nx - 2) i = nx - 2;
+    if (j < 0) j = 0;
+    if (j > ny - 2) j = ny - 2;
+    double s = gx - (double)i, t = gy - (double)j;
+    double f00 = f[4 * (j * nx + i)], f10 = f[4 * (j * nx + i + 1)];
+    double f01 = f[4 * ((j + 1) * nx + i)], f11 = f[4 * ((j + 1) * nx + i + 1)];
+    return (1.0 - s) * (1.0 - t) * f00 + s * (1.0 - t) * f10 + (1.0 - s) * t * f01 + s * t * f11;
+}
+
 /* Face tables. Layout (8 segments, back to back):
  *   xi_left[ny] xi_right[ny] xi_bottom[nx] xi_top[nx]
  *   eta_left[ny] eta_right[ny] eta_bottom[nx] eta_top[nx]
@@ -229,6 +245,11 @@ typedef struct {
     const double* xi0;    /* xi at the start of the mesh step, nx*ny */
     const double* eta0;
     const double* faces;  /* face tables, orc_faces_len(nx, ny) */
+    /* optional control variate: cv_slices tables of node values, each
+     * nx*ny*4 doubles (d/dx, d/dy of the xi model, then of the eta model);
+     * NULL or cv_slices = 0 for the plain estimator */
+    const double* cv;
+    int cv_slices;
 } orc_problem;
 
 typedef struct {
@@ -300,7 +321,9 @@ static int boundary_face(double x, double y, double* tang)
     return 3;
 }
 
-/* One path of the estimator (Eq. 7b under Euler--Maruyama, Sec. 4).
+/* One path of the estimator (Eq. 7b under Euler--Maruyama, Sec. 4). With a
+ * control-variate table the scores are Y - sum_j G(j, X_j) . sqrt(2) dW_j,
+ * G the table's slice q = floor(j S / K) interpolated bilinearly at X_j. 
  * Returns the number of sub-steps taken; writes the two scores, the end point
  * and the exit code (-1 survived, 0..3 plain exit through face k, 4..7 bridge
  * exit through face k-4). */
@@ -313,6 +336,8 @@ static int32_t run_path(const orc_problem* P, const orc_params* Q, uint32_t node
     const double sq = sqrt(2.0 * dt); /* sigma = sqrt(2), dW = sqrt(dt) N(0,1) */
     double x = x0, y = y0;
     uint32_t words[4];
+    const int cv_on = P->cv && P->cv_slices > 0;
+    double cv_sum[2] = {0.0, 0.0};
     for (int32_t j = 0; j < Q->K; ++j) {
         double zx, zy, ub = 1.0;
         if (Q->exit_mode == 0) {
@@ -331,6 +356,19 @@ static int32_t run_path(const orc_problem* P, const orc_params* Q, uint32_t node
         /* Euler--Maruyama step */
         double xn = x + bx * dt + sq * zx;
         double yn = y + by * dt + sq * zy;
+        /* control variate: the model gradient at X_j (before the increment)
+         * times the increment's noise sqrt(2) dW_j, summed over the sub-steps
+         * the path takes; its expectation is zero for any model */
+        if (cv_on) {
+            int q = (int)(((int64_t)j * P->cv_slices) / Q->K);
+            if (q > P->cv_slices - 1) q = P->cv_slices - 1;
+            const double* T = P->cv + (int64_t)q * 4 * nx * ny;
+            for (int c = 0; c < 4; ++c) {
+                /* component c of slice q, node values strided by 4 */
+                double g = cv_bilinear(nx, ny, T + c, x, y);
+                cv_sum[c >> 1] += g * sq * ((c & 1) ? zy : zx);
+            }
+        }
         /* boundary test after every sub-step; the closed boundary counts */
         if (on_boundary(xn, yn)) {
             double t;
@@ -340,6 +378,8 @@ static int32_t run_path(const orc_problem* P, const orc_params* Q, uint32_t node
             *xe = (face == 0) ? 0.0 : (face == 1) ? 1.0 : t;
             *ye = (face == 2) ? 0.0 : (face == 3) ? 1.0 : t;
             *code = face;
+            *score_xi -= cv_sum[0];
+            *score_eta -= cv_sum[1];
             return j + 1;
         }
         if (Q->exit_mode == 1) {
@@ -351,6 +391,8 @@ static int32_t run_path(const orc_problem* P, const orc_params* Q, uint32_t node
                 *xe = (face == 0) ? 0.0 : (face == 1) ? 1.0 : t;
                 *ye = (face == 2) ? 0.0 : (face == 3) ? 1.0 : t;
                 *code = 4 + face;
+                *score_xi -= cv_sum[0];
+                *score_eta -= cv_sum[1];
                 return j + 1;
             }
         }
@@ -363,6 +405,8 @@ static int32_t run_path(const orc_problem* P, const orc_params* Q, uint32_t node
     *xe = x;
     *ye = y;
     *code = -1;
+    *score_xi -= cv_sum[0];
+    *score_eta -= cv_sum[1];
     return Q->K;
 }
 

@@ -1,0 +1,90 @@
+"""Pins of the oracle's control-variate estimator.
+
+Y_cv = Y - sum_{j < kappa} G(s_j, X_j) . sqrt(2) dW_j with G any model of the
+solution's gradient, evaluated at the start of each sub-step. The sum is a
+martingale stopped at a bounded time, so E[Y_cv] = E[Y] for every model; with
+the exact gradient of the heat problem the per-path variance collapses down
+to the sub-step discretisation's share.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+
+def _heat_problem(oracle_mod):
+    xi0, eta0 = W.heat65_fields()
+    faces = np.zeros(oracle_mod.faces_len(65, 65))
+    return oracle_mod.Problem(W.w_const(65), xi0, eta0, faces)
+
+
+def test_zero_model_is_the_plain_estimator(oracle_mod):
+    n = 33
+    P = oracle_mod.Problem(W.w_smooth_random(n, 3), *W.identity_fields(n))
+    xs, ys = np.array([0.5, 0.1]), np.array([0.5, 0.7])
+    kw = dict(dt=1e-3, Dt=0.02, seed=4, record=True)
+    a = oracle_mod.interface_mc(P, xs, ys, 300, **kw)
+    b = oracle_mod.interface_mc(P, xs, ys, 300, cv_table=np.zeros((3, n, n, 4)), **kw)
+    for k in ("score_xi", "score_eta", "steps", "code", "mean_xi", "se_xi"):
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_any_model_leaves_the_mean_unbiased(oracle_mod):
+    # a smooth model unrelated to the solution: E[sum G . sqrt(2) dW] = 0
+    n = 65
+    P = oracle_mod.Problem(W.w_front(n, 0.1), *W.identity_fields(n))
+    X, Y = W.grid(n)
+    S = 4
+    T = np.zeros((S, n, n, 4))
+    for q in range(S):
+        T[q, ..., 0] = 2.0 * np.sin(3 * X + q) * np.cos(2 * Y)
+        T[q, ..., 1] = 1.5 + np.cos(5 * X * Y)
+        T[q, ..., 2] = -3.0 * X * Y + q
+        T[q, ..., 3] = np.sin(4 * Y - X)
+    xs, ys = np.array([0.5, 0.3, 0.08]), np.array([0.5, 0.62, 0.4])
+    kw = dict(dt=2e-4, Dt=1e-2, seed=8, record=True)
+    N = 20000
+    a = oracle_mod.interface_mc(P, xs, ys, N, **kw)
+    b = oracle_mod.interface_mc(P, xs, ys, N, cv_table=T, **kw)
+    np.testing.assert_array_equal(a["code"], b["code"])     # the model never moves a path
+    for f in ("xi", "eta"):
+        D = (b["score_" + f] - a["score_" + f]).reshape(3, N)
+        assert np.all(D.std(axis=1) > 1e-3)                 # the term is really there
+        z = D.mean(axis=1) / (D.std(axis=1, ddof=1) / math.sqrt(N))
+        assert np.all(np.abs(z) < 4.0), z
+
+
+def test_exact_gradient_collapses_the_variance(oracle_mod):
+    # heat problem: v(s, x) = exp(-2 pi^2 s) sin(pi x) sin(pi y) (xi) and
+    # exp(-5 pi^2 s) sin(pi x) sin(2 pi y) (eta), s the time left in the step;
+    # one slice per sub-step holds grad v at s_j = Dt - j dt
+    P = _heat_problem(oracle_mod)
+    n, dt, Dt = 65, 5e-4, 0.05
+    K = int(round(Dt / dt))
+    X, Y = W.grid(n)
+    T = np.zeros((K, n, n, 4))
+    for j in range(K):
+        s = Dt - j * dt
+        ex, ee = math.exp(-2 * math.pi ** 2 * s), math.exp(-5 * math.pi ** 2 * s)
+        T[j, ..., 0] = ex * math.pi * np.cos(np.pi * X) * np.sin(np.pi * Y)
+        T[j, ..., 1] = ex * math.pi * np.sin(np.pi * X) * np.cos(np.pi * Y)
+        T[j, ..., 2] = ee * math.pi * np.cos(np.pi * X) * np.sin(2 * np.pi * Y)
+        T[j, ..., 3] = ee * 2 * math.pi * np.sin(np.pi * X) * np.cos(2 * np.pi * Y)
+    xs, ys = np.full(3, 0.5), np.array([0.375, 0.5, 0.625])
+    kw = dict(dt=dt, Dt=Dt, seed=0, exit_mode=1)
+    plain = oracle_mod.interface_mc(P, xs, ys, 4000, **kw)
+    exact = oracle_mod.interface_mc(P, xs, ys, 4000, cv_table=T, **kw)
+    # what is left is the sub-step discretisation (exits between sub-steps, second-order terms),
+    # which shrinks like sqrt(dt): about 7x (xi) and 6x (eta) fewer standard errors at dt = 5e-4
+    assert np.all(exact["se_xi"] < plain["se_xi"] / 5), (plain["se_xi"], exact["se_xi"])
+    assert np.all(exact["se_eta"] < plain["se_eta"] / 4.5), (plain["se_eta"], exact["se_eta"])
+    # the sign and the sqrt(2) scale are pinned: a flipped or a rescaled model does worse
+    flipped = oracle_mod.interface_mc(P, xs, ys, 4000, cv_table=-T, **kw)
+    assert np.all(flipped["se_xi"] > plain["se_xi"])
+    scaled = oracle_mod.interface_mc(P, xs, ys, 4000, cv_table=T / math.sqrt(2), **kw)
+    assert np.all(scaled["se_xi"] > 1.5 * exact["se_xi"])
+    # and the corrected mean is the closed form up to the method's own bias
+    ex, ee = W.heat_exact(xs, ys, Dt)
+    assert np.all(np.abs(exact["mean_xi"] - ex) < 2e-3), exact["mean_xi"] - ex
