@@ -175,6 +175,25 @@ sdd_status sdd_interface_mc(sdd_ctx* ctx, const sdd_nodes* nodes, const sdd_mc_p
 sdd_status sdd_interface_mc_record(sdd_ctx* ctx, const sdd_nodes* nodes, const sdd_mc_params* p,
                                    sdd_node_stats* out, const sdd_path_records* rec);
 
+/* Control variate (a learned or given model of the solution's gradient; the
+ * paper notes that Monte Carlo converges slowly, Sec. 4). With it enabled,
+ * every path's scores become Y - sum_{j < kappa} G(s_j, X_j) . sqrt(2) dW_j:
+ * the model gradient at the start of each sub-step the path takes times the
+ * sub-step's Brownian increment. The sum has zero mean for any model (a
+ * martingale stopped at a bounded time), so the estimate stays unbiased; a
+ * good model shrinks the variance.
+ *   grad    DEVICE doubles, shape (slices, ny, nx, 4): at every node the
+ *           d/dx, d/dy of the xi model and of the eta model; slice q serves
+ *           the sub-steps j with floor(j * slices / K) = q and is interpolated
+ *           bilinearly in space. 1 <= slices <= 128, and an estimate with
+ *           more slices than sub-steps K fails with SDD_EINVAL. Copied into a
+ *           table of the context (the call waits for it).
+ * sdd_cv_enable turns the control variate on (nonzero) or off for every later
+ * estimate and mesh step of the context (not for batched calls, which run
+ * without it); turning it on needs a table. */
+sdd_status sdd_cv_set_table(sdd_ctx* ctx, const double* grad, int32_t slices);
+sdd_status sdd_cv_enable(sdd_ctx* ctx, int32_t on);
+
 /* Launch shape of the path kernel: threads per block and paths per task (a
  * task is a node and a run of its paths that one warp computes). */
 typedef struct {

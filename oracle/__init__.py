@@ -313,20 +313,23 @@ def boundary_grid(faces, nx: int, ny: int, field: int, inner):
 
 
 def dd_step(w, xi, eta, *, sub_x: int, sub_y: int, dt: float, Dt: float, n_paths: int, seed: int,
-            step_index: int, nodes_ij, exit_mode: int = 0, faces=None, threads=None, node_word0: int = 0):
+            step_index: int, nodes_ij, exit_mode: int = 0, faces=None, threads=None, node_word0: int = 0,
+            cv_table=None):
     """One mesh step t_{n-1} -> t_n of the method (Sec. 4): the interface
     estimate at the nodes nodes_ij = (i, j) (their position is their node index
     in the random stream), then the implicit subdomain solves by LU with those
     values and the face data as Dirichlet data. node_word0 offsets the node
     word of the random stream (instances evaluated together number their nodes
-    in sequence). Returns ([xi_n, eta_n], stats)."""
+    in sequence); cv_table, if given, is the control-variate model of
+    interface_mc. Returns ([xi_n, eta_n], stats)."""
     from . import solver
     P = Problem(w, xi, eta, faces)
     ii, jj = (np.asarray(a) for a in nodes_ij)
     xs = ii / (P.nx - 1)
     ys = jj / (P.ny - 1)
     r = interface_mc(P, xs, ys, n_paths, dt=dt, Dt=Dt, seed=seed, exit_mode=exit_mode, step_index=step_index,
-                     threads=threads, node_ids=np.arange(xs.size, dtype=np.uint32) + np.uint32(node_word0))
+                     threads=threads, node_ids=np.arange(xs.size, dtype=np.uint32) + np.uint32(node_word0),
+                     cv_table=cv_table)
     bx = boundary_grid(P.faces, P.nx, P.ny, 0, P.xi0)
     be = boundary_grid(P.faces, P.nx, P.ny, 1, P.eta0)
     bx[jj, ii] = r["mean_xi"]

@@ -34,7 +34,7 @@ EXPORTS = [
     "sdd_sync", "sdd_last_error", "sdd_destroy", "sdd_rng_draw", "sdd_interface_mc_static",
     "sdd_static_scratch_bytes", "sdd_batch_create", "sdd_batch_interface_mc", "sdd_batch_step",
     "sdd_batch_last_step_info", "sdd_batch_set_step_index", "sdd_batch_sync", "sdd_batch_last_error",
-    "sdd_batch_destroy", "sdd_autotune", "sdd_batch_autotune",
+    "sdd_batch_destroy", "sdd_autotune", "sdd_batch_autotune", "sdd_cv_set_table", "sdd_cv_enable",
 ]
 
 
@@ -139,6 +139,8 @@ def lib():
                 "sdd_batch_last_error": [vp],
                 "sdd_batch_destroy": [vp],
                 "sdd_autotune": [vp, ctypes.POINTER(_Nodes), ctypes.POINTER(_McParams), ctypes.POINTER(_Shape)],
+                "sdd_cv_set_table": [vp, vp, i32],
+                "sdd_cv_enable": [vp, i32],
                 "sdd_batch_autotune": [vp, ctypes.POINTER(_Nodes), ctypes.POINTER(_McParams), ctypes.POINTER(_Shape)],
             }
             for name, args in sig.items():
@@ -546,3 +548,16 @@ def sdd_batch_autotune(batch: Batch, node_lists, dt, Dt, exit_mode=0) -> dict:
     batch._check(lib().sdd_batch_autotune(batch.handle, nodes, ctypes.byref(p), ctypes.byref(out)))
     del keep
     return {"block_threads": out.block_threads, "paths_per_task": out.paths_per_task, "ms": out.ms}
+
+
+def sdd_cv_set_table(ctx: Ctx, grad):
+    """grad: cuda float64 tensor of shape (slices, ny, nx, 4) (see include/sdd.h)."""
+    torch = _torch()
+    if not (grad.is_cuda and grad.dtype == torch.float64 and grad.is_contiguous() and grad.dim() == 4
+            and tuple(grad.shape[1:]) == (ctx.ny, ctx.nx, 4)):
+        raise ValueError("grad: expected a contiguous cuda float64 tensor of shape (slices, ny, nx, 4)")
+    ctx._check(lib().sdd_cv_set_table(ctx.handle, _ptr(grad), grad.shape[0]))
+
+
+def sdd_cv_enable(ctx: Ctx, on=True):
+    ctx._check(lib().sdd_cv_enable(ctx.handle, 1 if on else 0))

@@ -96,6 +96,9 @@ struct sdd_ctx {
     DevBuf<double> faces64;
     DevBuf<float> faces32;
     DevBuf<float4> bcoef, fcoef;
+    DevBuf<float4> cvcoef;     // control-variate table (per slice and cell)
+    int cv_slices = 0;
+    bool cv_on = false;
     DevBuf<InstDev> d_inst;
     DevBuf<int> d_status;
     DevBuf<uint32_t> d_step;
@@ -199,23 +202,14 @@ InstDev inst_host(const sdd_ctx* c)
     I.gxmax = std::nextafter((float)(c->nx - 1), 0.0f);
     I.gymax = std::nextafter((float)(c->ny - 1), 0.0f);
     I.cell_bias = 0x4B000000u * (uint32_t)c->nx;
+    I.cv_slices = c->cv_slices;
+    I.cvcoef = c->cvcoef.p;
     return I;
 }
 
 sdd_status upload_inst(sdd_ctx* c)
 {
-    InstDev I{};
-    I.bcoef = c->bcoef.p;
-    I.fcoef = c->fcoef.p;
-    I.faces32 = c->faces32.p;
-    I.faces64 = c->faces64.p;
-    I.nx = c->nx;
-    I.ny = c->ny;
-    I.sx = (float)(c->nx - 1);
-    I.sy = (float)(c->ny - 1);
-    I.gxmax = below((float)(c->nx - 1));
-    I.gymax = below((float)(c->ny - 1));
-    I.cell_bias = 0x4B000000u * (uint32_t)c->nx;
+    const InstDev I = inst_host(c);
     CU(c, c->d_inst.alloc(1));
     CU(c, cudaMemcpy(c->d_inst.p, &I, sizeof I, cudaMemcpyHostToDevice));
     return SDD_OK;
@@ -414,7 +408,7 @@ uint64_t shape_key(const std::vector<NodeSeg>& segs, int K, int exit_mode)
 
 sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const OutDev* outs, const OutDev& out0, double dt,
                        int K, uint64_t seed, uint32_t step_index, const uint32_t* step_ptr, int exit_mode,
-                       const RecDev* rec, cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_b);
+                       const RecDev* rec, cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_b, int cv_slices = 0);
 
 const TunedShape* find_tuned(const std::vector<TunedShape>& t, uint64_t key)
 {
@@ -502,7 +496,7 @@ sdd_status build_plan(sdd_ctx* c, Plan& P, const double* x, const double* y, con
 // per-instance outputs (null: every node writes to out0).
 sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const OutDev* outs, const OutDev& out0, double dt,
                        int K, uint64_t seed, uint32_t step_index, const uint32_t* step_ptr, int exit_mode,
-                       const RecDev* rec, cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_b)
+                       const RecDev* rec, cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_b, int cv_slices)
 {
     if (P.nnodes == 0) return SDD_OK;
     if (P.ntasks > 0) {
@@ -521,11 +515,22 @@ sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const Out
         a.step_index = step_index;
         a.step_ptr = step_ptr;
         if (rec) a.rec = *rec;
+        const bool cv = cv_slices > 0;
+        if (cv && cv_slices > K) return fail(err, SDD_EINVAL, "more control-variate slices than sub-steps per step");
+        for (int q = 0; q <= kMaxCvSlices; ++q)
+            a.cv_bound[q] = cv && q <= cv_slices ? (int32_t)(((int64_t)q * K + cv_slices - 1) / cv_slices) : K + 1;
         CU(err, cudaMemsetAsync(P.d_queue.p, 0, sizeof(int), s));
         const int64_t per_block = P.block / 32;
-        const int grid = (int)std::min<int64_t>(P.grid, std::max<int64_t>(1, (P.ntasks + per_block - 1) / per_block));
+        int grid_max = P.grid;
+        if (cv) {
+            int dev = 0, sms = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            grid_max = sms * path_kernel_blocks_per_sm(exit_mode, rec != nullptr, P.block, true);
+        }
+        const int grid = (int)std::min<int64_t>(grid_max, std::max<int64_t>(1, (P.ntasks + per_block - 1) / per_block));
         if (ev_a) CU(err, cudaEventRecordWithFlags(ev_a, s, cudaEventRecordExternal));
-        CU(err, launch_paths(a, exit_mode, rec != nullptr, grid, P.block, s));
+        CU(err, launch_paths(a, exit_mode, rec != nullptr, grid, P.block, s, cv));
         if (ev_b) CU(err, cudaEventRecordWithFlags(ev_b, s, cudaEventRecordExternal));
     }
     FinalArgs f{};
@@ -545,7 +550,7 @@ sdd_status run_plan(sdd_ctx* c, Plan& P, double dt, int K, uint64_t seed, uint32
                     cudaEvent_t ev_a = nullptr, cudaEvent_t ev_b = nullptr)
 {
     return run_plan_on(&c->err, P, c->d_inst.p, nullptr, out, dt, K, seed, step_index, step_ptr, exit_mode, rec, s,
-                       ev_a, ev_b);
+                       ev_a, ev_b, c->cv_on ? c->cv_slices : 0);
 }
 
 // Launch shape for a plan: explicit requests win, else a tuned shape for this node set, else the heuristic.
@@ -918,6 +923,30 @@ sdd_status sdd_interface_mc_record(sdd_ctx* c, const sdd_nodes* nodes, const sdd
 {
     if (!rec) return fail(c, SDD_EINVAL, "null records");
     return mc_common(c, nodes, p, out, rec);
+}
+
+sdd_status sdd_cv_set_table(sdd_ctx* c, const double* grad, int32_t slices)
+{
+    if (!c || !grad) return fail(c, SDD_EINVAL, "null argument");
+    if (slices < 1 || slices > kMaxCvSlices) return fail(c, SDD_EINVAL, "slices must be in [1, %d]", kMaxCvSlices);
+    const size_t cells = (size_t)(c->nx - 1) * (c->ny - 1);
+    CU(c, c->cvcoef.alloc(4 * cells * (size_t)slices));
+    CU(c, launch_cv_cells(grad, slices, c->nx, c->ny, c->cvcoef.p, c->stream));
+    c->cv_slices = slices;
+    CU(c, cudaStreamSynchronize(c->stream));
+    sdd_status st = upload_inst(c);
+    if (st != SDD_OK) return st;
+    drop_graphs(c);
+    return SDD_OK;
+}
+
+sdd_status sdd_cv_enable(sdd_ctx* c, int32_t on)
+{
+    if (!c) return SDD_EINVAL;
+    if (on && c->cv_slices < 1) return fail(c, SDD_EINVAL, "no control-variate table has been set");
+    if ((on != 0) != c->cv_on) drop_graphs(c);
+    c->cv_on = on != 0;
+    return SDD_OK;
 }
 
 sdd_status sdd_autotune(sdd_ctx* c, const sdd_nodes* nodes, const sdd_mc_params* p, sdd_launch_shape* out)

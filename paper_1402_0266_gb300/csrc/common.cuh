@@ -13,6 +13,8 @@
 
 namespace sdd {
 
+constexpr int kMaxCvSlices = 128;  // time slices of a control-variate table
+
 // Geometry and field tables of one instance, as the path kernel reads them.
 struct InstDev {
     const float4* bcoef;   // 2 float4 per cell: (a0x, a0y, a1x, a1y), (a2x, a2y, a3x, a3y) of b = (b_x, b_y)
@@ -23,7 +25,8 @@ struct InstDev {
     float sx, sy;          // nx - 1, ny - 1 (inverse spacings)
     float gxmax, gymax;    // largest floats below nx - 1, ny - 1
     uint32_t cell_bias;    // 0x4B000000 * nx (mod 2^32): cell index from the float bits of 2^23 + floor(g)
-    int32_t pad0;
+    int32_t cv_slices;     // slices of the control-variate table (0: none)
+    const float4* cvcoef;  // per slice and cell 4 float4: the xi model's gradient record, then the eta model's
 };
 
 // Output arrays of one instance (device pointers; any may be null).
@@ -84,6 +87,7 @@ struct PathArgs {
     float bm_scale;          // -4 dt ln 2: r = sqrt(bm_scale * log2(u1)) = sqrt(2 dt) sqrt(-2 ln u1)
     float bridge_cut;        // skip the bridge test when dmin0 * dmin1 exceeds this
     PhiloxKeys keys;         // round keys of the seed
+    int32_t cv_bound[kMaxCvSlices + 1];  // control variate: slice q serves sub-steps cv_bound[q] <= j < cv_bound[q + 1]
     uint32_t step_index;
     const uint32_t* step_ptr; // if non-null, read the step index here
     RecDev rec;
@@ -107,14 +111,16 @@ enum : int {
 };
 
 // Launchers (defined in the .cu files; all asynchronous on `s`).
-cudaError_t launch_paths(const PathArgs& a, int exit_mode, bool record, int grid, int block, cudaStream_t s);
+cudaError_t launch_paths(const PathArgs& a, int exit_mode, bool record, int grid, int block, cudaStream_t s,
+                         bool cv = false);
 // exit_mode 0 with an even number of sub-steps has its own kernel (no odd last pair)
 cudaError_t launch_finalize(const FinalArgs& a, cudaStream_t s);
-int path_kernel_blocks_per_sm(int exit_mode, bool record, int block);
+int path_kernel_blocks_per_sm(int exit_mode, bool record, int block, bool cv = false);
 
 cudaError_t launch_prep_cells(const float* w, const double* xi, const double* eta, int nx, int ny, float4* bcoef,
                               float4* fcoef, int* status, cudaStream_t s);
 cudaError_t launch_winslow_faces(const float* w, int nx, int ny, double* faces64, cudaStream_t s);
+cudaError_t launch_cv_cells(const double* grad, int slices, int nx, int ny, float4* cvcoef, cudaStream_t s);
 cudaError_t launch_faces32(const double* faces64, float* faces32, int n, cudaStream_t s);
 
 cudaError_t launch_rng_draw(uint64_t seed, const uint32_t* ctrs, long long count, uint32_t* words, float* normals,

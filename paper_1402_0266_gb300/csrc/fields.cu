@@ -83,6 +83,25 @@ __global__ void k_prep_cells(const float* __restrict__ w, const double* __restri
                     fcoef[2 * cell + 0], fcoef[2 * cell + 1]);
 }
 
+// Control-variate table: node values (slice, j, i, 4) of the two models'
+// gradients -> per slice and cell the interleaved bilinear records of
+// (d/dx, d/dy) of the xi model and of the eta model.
+__global__ void k_cv_cells(const double* __restrict__ g, int slices, int nx, int ny, float4* __restrict__ cv)
+{
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int iy = blockIdx.y * blockDim.y + threadIdx.y;
+    const int q = blockIdx.z;
+    if (ix >= nx - 1 || iy >= ny - 1 || q >= slices) return;
+    const double* T = g + (long long)q * nx * ny * 4;
+    const long long n00 = (long long)iy * nx + ix, n10 = n00 + 1, n01 = n00 + nx, n11 = n01 + 1;
+    const long long cell = (long long)q * (nx - 1) * (ny - 1) + (long long)iy * (nx - 1) + ix;
+    float4* out = cv + 4 * cell;
+    bilinear_coefs2(T[4 * n00 + 0], T[4 * n10 + 0], T[4 * n01 + 0], T[4 * n11 + 0], T[4 * n00 + 1], T[4 * n10 + 1],
+                    T[4 * n01 + 1], T[4 * n11 + 1], out[0], out[1]);
+    bilinear_coefs2(T[4 * n00 + 2], T[4 * n10 + 2], T[4 * n01 + 2], T[4 * n11 + 2], T[4 * n00 + 3], T[4 * n10 + 3],
+                    T[4 * n01 + 3], T[4 * n11 + 3], out[2], out[3]);
+}
+
 // Cumulative trapezoid of one line of w, normalised by its total, by one warp:
 // each lane sums a contiguous run of intervals, the run totals are scanned
 // across the warp, then each lane writes its run.
@@ -150,6 +169,14 @@ cudaError_t launch_prep_cells(const float* w, const double* xi, const double* et
     const dim3 block(32, 8);
     const dim3 grid((nx - 1 + 31) / 32, (ny - 1 + 7) / 8);
     k_prep_cells<<<grid, block, 0, s>>>(w, xi, eta, nx, ny, bcoef, fcoef, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cv_cells(const double* grad, int slices, int nx, int ny, float4* cvcoef, cudaStream_t s)
+{
+    const dim3 block(32, 8);
+    const dim3 grid((nx - 1 + 31) / 32, (ny - 1 + 7) / 8, slices);
+    k_cv_cells<<<grid, block, 0, s>>>(grad, slices, nx, ny, cvcoef);
     return cudaGetLastError();
 }
 

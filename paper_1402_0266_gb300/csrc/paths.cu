@@ -33,6 +33,7 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 struct Cell {
     const float4* p;  // the cell's two coefficient records
     float2 st;        // local coordinates (s, t) in [0, 1)
+    uint32_t idx;     // row-major cell index
 };
 
 // Cell of pos and local coordinates. floor() through a directed add of 2^23:
@@ -50,6 +51,7 @@ __device__ __forceinline__ Cell locate(const InstDev& I, const float4* base, flo
     Cell c;
     c.st = __ffma2_rn(fl, f2(-1.0f, -1.0f), g);                        // g - floor(g), exact
     c.p = base + 2 * (size_t)cell;
+    c.idx = cell;
     return c;
 }
 
@@ -155,6 +157,20 @@ __device__ __forceinline__ bool bridge_exit(const InstDev& I, float x, float y, 
     return true;
 }
 
+// Control variate: the two models' gradients at the cell of X_j for slice q,
+// times the sub-step's increment z = sqrt(2 dt) N(0,1)^2, added to the running
+// sums (acc_xi, acc_eta hold the x and y parts separately).
+__device__ __forceinline__ void cv_add(const InstDev& I, const Cell& c, int q, float2 z, float2& acc_xi,
+                                       float2& acc_eta)
+{
+    const float4* r = I.cvcoef + 4 * ((size_t)q * (size_t)(I.nx - 1) * (size_t)(I.ny - 1) + c.idx);
+    float4 a0, a1, b0, b1;
+    load_cell(r, a0, a1);
+    load_cell(r + 2, b0, b1);
+    acc_xi = __ffma2_rn(eval2(a0, a1, c.st), z, acc_xi);
+    acc_eta = __ffma2_rn(eval2(b0, b1, c.st), z, acc_eta);
+}
+
 struct Acc {
     float s, cs, q, cq;
     __device__ __forceinline__ void add(float v)
@@ -189,8 +205,9 @@ __device__ __forceinline__ long long warp_sum_ll(long long v)
 
 // MODE 0: the paper's test, sub-step pairs; MODE 1: with the bridge test;
 // MODE 2: as MODE 0 when K is even (every pair has both sub-steps).
-template <int MODE, bool RECORD>
-__global__ void __launch_bounds__(512, 2) k_paths(const PathArgs a)
+// CV: subtract the control variate sum_j G(s_j, X_j) . sqrt(2) dW_j from both scores.
+template <int MODE, bool RECORD, bool CV>
+__global__ void __launch_bounds__(512, CV ? 1 : 2) k_paths(const PathArgs a)
 {
     __shared__ int s_group;
     const int lane = threadIdx.x & 31;
@@ -228,6 +245,8 @@ __global__ void __launch_bounds__(512, 2) k_paths(const PathArgs a)
         // sub-step, zB for the second (plain mode); ub the bridge uniform
         float2 zA = f2(0.f, 0.f), zB = f2(0.f, 0.f);
         float ub = 1.f;
+        float2 cvx = f2(0.f, 0.f), cve = f2(0.f, 0.f);  // control-variate sums of the path
+        int cvq = 0, cvn = CV ? a.cv_bound[1] : 0;       // slice of the current sub-step, start of the next
         const float2 dt2 = f2(dt, dt);
         auto first_draw = [&]() {
             uint4 r = make_uint4((uint32_t)path, nctr, 0u, step);
@@ -252,6 +271,11 @@ __global__ void __launch_bounds__(512, 2) k_paths(const PathArgs a)
                 const Cell cA = locate(I, I.bcoef, pos);
                 float4 gA0, gA1;
                 load_cell(cA.p, gA0, gA1);
+                if (CV) {
+                    const int j = PAIRS ? 2 * m : m;
+                    if (j >= cvn) cvn = a.cv_bound[++cvq + 1];
+                    cv_add(I, cA, cvq, zA, cvx, cve);
+                }
                 uint4 r = make_uint4((uint32_t)path, nctr, (uint32_t)(m + 1), step);
                 philox_rounds_rk<0, 5>(r, a.keys);
                 const float2 pa = em(gA0, gA1, cA.st, pos, dt2, zA);
@@ -268,6 +292,12 @@ __global__ void __launch_bounds__(512, 2) k_paths(const PathArgs a)
                     const float2 pb = em(gB0, gB1, cB.st, pq, dt2, zB);
                     const bool haveB = (MODE == 2) || 2 * m + 1 < K;
                     const bool outB = haveB && !outA && !inside2(pb);
+                    if (CV) {
+                        // the second sub-step counts only when the path takes it
+                        if (haveB && 2 * m + 1 >= cvn) cvn = a.cv_bound[++cvq + 1];
+                        const float2 zt = (haveB && !outA) ? zB : f2(0.f, 0.f);
+                        cv_add(I, cB, cvq, zt, cvx, cve);
+                    }
                     if (outA) {
                         plain_exit(I, pos.x, pos.y, pa.x, pa.y, code, yxi, yeta, xe, ye);
                         done = true;
@@ -325,6 +355,10 @@ __global__ void __launch_bounds__(512, 2) k_paths(const PathArgs a)
                     } else {
                         ++exits;
                     }
+                    if (CV) {
+                        yxi -= cvx.x + cvx.y;
+                        yeta -= cve.x + cve.y;
+                    }
                     ax.add(yxi - x0);
                     ae.add(yeta - y0);
                     steps += taken;
@@ -349,6 +383,11 @@ __global__ void __launch_bounds__(512, 2) k_paths(const PathArgs a)
                     alive = true;
                     pos = f2(x0, y0);
                     m = 0;
+                    if (CV) {
+                        cvx = cve = f2(0.f, 0.f);
+                        cvq = 0;
+                        cvn = a.cv_bound[1];
+                    }
                     first_draw();
                 }
                 next += __popc(need);
@@ -487,27 +526,30 @@ __global__ void k_rng_draw(uint64_t seed, const uint32_t* __restrict__ ctrs, lon
     }
 }
 
-template <int MODE, bool RECORD>
+template <int MODE, bool RECORD, bool CV>
 const void* kernel_ptr()
 {
-    return (const void*)k_paths<MODE, RECORD>;
+    return (const void*)k_paths<MODE, RECORD, CV>;
 }
 
-const void* pick(int mode, bool record)
+template <bool CV>
+const void* pick_cv(int mode, bool record)
 {
-    if (mode == 0) return record ? kernel_ptr<0, true>() : kernel_ptr<0, false>();
-    if (mode == 2) return record ? kernel_ptr<2, true>() : kernel_ptr<2, false>();
-    return record ? kernel_ptr<1, true>() : kernel_ptr<1, false>();
+    if (mode == 0) return record ? kernel_ptr<0, true, CV>() : kernel_ptr<0, false, CV>();
+    if (mode == 2) return record ? kernel_ptr<2, true, CV>() : kernel_ptr<2, false, CV>();
+    return record ? kernel_ptr<1, true, CV>() : kernel_ptr<1, false, CV>();
 }
+
+const void* pick(int mode, bool record, bool cv = false) { return cv ? pick_cv<true>(mode, record) : pick_cv<false>(mode, record); }
 
 }  // namespace
 
-int path_kernel_blocks_per_sm(int exit_mode, bool record, int block)
+int path_kernel_blocks_per_sm(int exit_mode, bool record, int block, bool cv)
 {
     int n = 0;
     // the even-K kernel has the same footprint class; size the grid for the larger of the two
     const int mode = exit_mode == 1 ? 1 : 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(mode, record), block, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(mode, record, cv), block, 0) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
 }
@@ -522,26 +564,36 @@ static void prefer_l1()
     done = true;
     for (int mode : {0, 1, 2})
         for (bool rec : {false, true})
-            cudaFuncSetAttribute(pick(mode, rec), cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+            for (bool cv : {false, true})
+                cudaFuncSetAttribute(pick(mode, rec, cv), cudaFuncAttributePreferredSharedMemoryCarveout, 0);
     cudaGetLastError();
 }
 
-cudaError_t launch_paths(const PathArgs& a, int exit_mode, bool record, int grid, int block, cudaStream_t s)
+template <bool CV>
+static void launch_mode(const PathArgs& a, int mode, bool record, int grid, int block, cudaStream_t s)
 {
-    prefer_l1();
-    switch (kernel_mode(exit_mode, a.K)) {
+    switch (mode) {
     case 0:
-        if (record) k_paths<0, true><<<grid, block, 0, s>>>(a);
-        else k_paths<0, false><<<grid, block, 0, s>>>(a);
+        if (record) k_paths<0, true, CV><<<grid, block, 0, s>>>(a);
+        else k_paths<0, false, CV><<<grid, block, 0, s>>>(a);
         break;
     case 2:
-        if (record) k_paths<2, true><<<grid, block, 0, s>>>(a);
-        else k_paths<2, false><<<grid, block, 0, s>>>(a);
+        if (record) k_paths<2, true, CV><<<grid, block, 0, s>>>(a);
+        else k_paths<2, false, CV><<<grid, block, 0, s>>>(a);
         break;
     default:
-        if (record) k_paths<1, true><<<grid, block, 0, s>>>(a);
-        else k_paths<1, false><<<grid, block, 0, s>>>(a);
+        if (record) k_paths<1, true, CV><<<grid, block, 0, s>>>(a);
+        else k_paths<1, false, CV><<<grid, block, 0, s>>>(a);
     }
+}
+
+
+cudaError_t launch_paths(const PathArgs& a, int exit_mode, bool record, int grid, int block, cudaStream_t s, bool cv)
+{
+    prefer_l1();
+    const int mode = kernel_mode(exit_mode, a.K);
+    if (cv) launch_mode<true>(a, mode, record, grid, block, s);
+    else launch_mode<false>(a, mode, record, grid, block, s);
     return cudaGetLastError();
 }
 

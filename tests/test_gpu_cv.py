@@ -1,0 +1,198 @@
+"""The control-variate path on the GPU against the oracle's control-variate estimator.
+
+Y_cv = Y - sum_{j < kappa} G(s_j, X_j) . sqrt(2) dW_j, the model G given as a
+node table in space and piecewise constant in time. The same Philox streams
+drive both sides, so the records must agree path by path (the paths are not
+moved by the model; only the score changes).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from tests import _parity as PT
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sdd():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1402_0266_gb300 import build
+    build.build()
+    import paper_1402_0266_gb300 as m
+    return m
+
+
+def _np(d):
+    return {k: v.cpu().numpy() for k, v in d.items()}
+
+
+def _ctx(sdd, w, xi0, eta0, sub=2, faces=None):
+    import torch
+    ny, nx = w.shape
+    ctx = sdd.sdd_init(nx, ny, sub, sub, w=torch.from_numpy(np.ascontiguousarray(w, np.float32)).cuda(),
+                       xi0=torch.from_numpy(np.ascontiguousarray(xi0)).cuda(),
+                       eta0=torch.from_numpy(np.ascontiguousarray(eta0)).cuda())
+    if faces is not None:
+        sdd.sdd_set_boundary(ctx, torch.from_numpy(np.ascontiguousarray(faces, np.float64)).cuda())
+    return ctx
+
+
+def _set_table(sdd, ctx, T):
+    import torch
+    sdd.sdd_cv_set_table(ctx, torch.from_numpy(np.ascontiguousarray(T, np.float64)).cuda())
+
+
+def _smooth_table(n, S):
+    X, Y = W.grid(n)
+    T = np.zeros((S, n, n, 4))
+    for q in range(S):
+        T[q, ..., 0] = 2.0 * np.sin(3 * X + q) * np.cos(2 * Y)
+        T[q, ..., 1] = 1.5 + np.cos(5 * X * Y)
+        T[q, ..., 2] = -3.0 * X * Y + 0.3 * q
+        T[q, ..., 3] = np.sin(4 * Y - X)
+    return T
+
+
+def _heat_table(n, dt, Dt):
+    # grad of exp(-2 pi^2 s) sin(pi x) sin(pi y) and exp(-5 pi^2 s) sin(pi x) sin(2 pi y),
+    # s = Dt - j dt the time left at sub-step j; one slice per sub-step
+    K = int(round(Dt / dt))
+    X, Y = W.grid(n)
+    T = np.zeros((K, n, n, 4))
+    for j in range(K):
+        s = Dt - j * dt
+        ex, ee = math.exp(-2 * math.pi ** 2 * s), math.exp(-5 * math.pi ** 2 * s)
+        T[j, ..., 0] = ex * math.pi * np.cos(np.pi * X) * np.sin(np.pi * Y)
+        T[j, ..., 1] = ex * math.pi * np.sin(np.pi * X) * np.cos(np.pi * Y)
+        T[j, ..., 2] = ee * math.pi * np.cos(np.pi * X) * np.sin(2 * np.pi * Y)
+        T[j, ..., 3] = ee * 2 * math.pi * np.sin(np.pi * X) * np.cos(2 * np.pi * Y)
+    return T
+
+
+# odd K in the paired kernel (the last pair takes one sub-step), even K, the bridge kernel;
+# slice counts that split K unevenly, and one slice per sub-step
+CASES = [(0, 1e-3, 0.049, 5), (0, 1e-3, 0.05, 50), (1, 1e-3, 0.05, 7), (0, 5e-4, 0.02, 3)]
+
+
+@pytest.mark.parametrize("exit_mode,dt,Dt,S", CASES)
+def test_cv_records_match_oracle(sdd, oracle_mod, exit_mode, dt, Dt, S):
+    n = 65
+    w = W.w_front(n, 0.1)
+    xi0, eta0 = W.identity_fields(n)
+    ctx = _ctx(sdd, w, xi0, eta0)
+    T = _smooth_table(n, S)
+    _set_table(sdd, ctx, T)
+    sdd.sdd_cv_enable(ctx, True)
+    xs, ys = W.interface_node_coords(n, n, 2, 2)
+    pick = np.arange(0, xs.size, 9)
+    xs = np.concatenate([xs[pick], [0.0, 0.013]])
+    ys = np.concatenate([ys[pick], [0.4, 0.77]])
+    npaths = np.full(xs.size, 700)
+    npaths[::3] = 41
+    kw = dict(dt=dt, Dt=Dt, seed=5, step_index=2, exit_mode=exit_mode)
+    g = _np(sdd.sdd_interface_mc_record(ctx, xs, ys, npaths, **kw))
+    P = oracle_mod.Problem(w, xi0, eta0)
+    o = oracle_mod.interface_mc(P, xs, ys, npaths, record=True, cv_table=T, **kw)
+    plain = oracle_mod.interface_mc(P, xs, ys, npaths, record=True, **kw)
+    # the table really enters the scores
+    assert np.abs(o["score_xi"] - plain["score_xi"]).max() > 1e-2
+    same, rep = PT.assert_records(g, o)
+    offsets = np.concatenate([[0], np.cumsum(npaths)])
+    PT.assert_nodes(g, o, npaths, same, offsets)
+
+
+def test_cv_zero_table_gives_the_plain_estimate(sdd):
+    n = 65
+    w = W.w_ring(n, 0.1)
+    xi0, eta0 = W.identity_fields(n)
+    ctx = _ctx(sdd, w, xi0, eta0)
+    xs, ys = W.interface_node_coords(n, n, 2, 2)
+    npaths = np.full(xs.size, 500)
+    kw = dict(dt=1e-3, Dt=0.03, seed=3)
+    plain = _np(sdd.sdd_interface_mc(ctx, xs, ys, npaths, **kw))
+    _set_table(sdd, ctx, np.zeros((4, n, n, 4)))
+    sdd.sdd_cv_enable(ctx, True)
+    cv = _np(sdd.sdd_interface_mc(ctx, xs, ys, npaths, **kw))
+    for k in ("mean_xi", "mean_eta", "se_xi", "se_eta"):
+        np.testing.assert_allclose(cv[k], plain[k], rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(cv["n_exit"], plain["n_exit"])
+    np.testing.assert_array_equal(cv["path_steps"], plain["path_steps"])
+    sdd.sdd_cv_enable(ctx, False)
+    again = _np(sdd.sdd_interface_mc(ctx, xs, ys, npaths, **kw))
+    np.testing.assert_array_equal(again["mean_xi"], plain["mean_xi"])
+
+
+def test_cv_exact_gradient_shrinks_the_error_on_gpu(sdd, oracle_mod):
+    n, dt, Dt = 65, 5e-4, 0.05
+    xi0, eta0 = W.heat65_fields()
+    faces = np.zeros(oracle_mod.faces_len(n, n))
+    ctx = _ctx(sdd, W.w_const(n), xi0, eta0, faces=faces)
+    xs, ys = W.heat65_nodes()
+    npaths = np.full(xs.size, 4000)
+    kw = dict(dt=dt, Dt=Dt, seed=0, exit_mode=1)
+    plain = _np(sdd.sdd_interface_mc(ctx, xs, ys, npaths, **kw))
+    T = _heat_table(n, dt, Dt)
+    _set_table(sdd, ctx, T)
+    sdd.sdd_cv_enable(ctx, True)
+    cv = _np(sdd.sdd_interface_mc(ctx, xs, ys, npaths, **kw))
+    inner = (xs > 0) & (xs < 1) & (ys > 0) & (ys < 1)
+    assert np.all(cv["se_xi"][inner] < plain["se_xi"][inner] / 5)
+    assert np.all(cv["se_eta"][inner] < plain["se_eta"][inner] / 4.5)
+    ex, ee = W.heat_exact(xs, ys, Dt)
+    assert np.all(np.abs(cv["mean_xi"] - ex)[inner] < 2e-3)
+    assert np.all(np.abs(cv["mean_eta"] - ee)[inner] < 2e-3)
+    # and the same numbers as the oracle's control-variate estimator on a few nodes
+    sel = np.flatnonzero(inner)[::8]
+    P = oracle_mod.Problem(W.w_const(n), xi0, eta0, faces)
+    o = oracle_mod.interface_mc(P, xs[sel], ys[sel], npaths[sel], cv_table=T, node_ids=sel.astype(np.uint32), **kw)
+    for f in ("xi", "eta"):
+        d = np.abs(cv["mean_" + f][sel] - o["mean_" + f])
+        assert np.all(d <= 3 * o["se_" + f] + 1e-4), (f, d)
+
+
+def test_cv_mesh_step_matches_oracle(sdd, oracle_mod):
+    n, sub, dt, Dt, paths = 33, 2, 1e-4, 1e-2, 1500
+    w = W.w_front(n, 0.0)
+    xi0, eta0 = W.identity_fields(n)
+    ctx = _ctx(sdd, w, xi0, eta0, sub)
+    T = _smooth_table(n, 10)
+    _set_table(sdd, ctx, T)
+    sdd.sdd_cv_enable(ctx, True)
+    sdd.sdd_step(ctx, dt=dt, Dt=Dt, seed=9, paths_per_node=paths, rtol=1e-13, max_iter=50000)
+    sdd.sdd_sync(ctx)
+    g = _np(sdd.sdd_last_interface_stats(ctx))
+    ii, jj = W.interface_nodes(n, n, sub, sub)
+    new, o = oracle_mod.dd_step(w, xi0, eta0, sub_x=sub, sub_y=sub, dt=dt, Dt=Dt, n_paths=paths, seed=9,
+                                step_index=0, nodes_ij=(ii, jj), cv_table=T)
+    for f in ("xi", "eta"):
+        d = np.abs(g["mean_" + f] - o["mean_" + f])
+        assert np.all(d <= 3 * o["se_" + f] + 1e-4), (f, d.max())
+        assert np.median(d) <= 1e-5
+    gx, ge = (a.cpu().numpy() for a in sdd.sdd_get_fields(ctx))
+    iface_gap = max(np.abs(g["mean_xi"] - o["mean_xi"]).max(), np.abs(g["mean_eta"] - o["mean_eta"]).max())
+    assert max(np.abs(gx - new[0]).max(), np.abs(ge - new[1]).max()) <= iface_gap + 1e-9
+
+
+def test_cv_rejections(sdd):
+    import torch
+    n = 17
+    w = np.ones((n, n))
+    xi0, eta0 = W.identity_fields(n)
+    ctx = _ctx(sdd, w, xi0, eta0)
+    with pytest.raises(sdd.SddError) as e:
+        sdd.sdd_cv_enable(ctx, True)              # no table yet
+    assert e.value.status == sdd.SDD_EINVAL
+    for S in (0, 129):
+        with pytest.raises((sdd.SddError, ValueError)):
+            sdd.sdd_cv_set_table(ctx, torch.zeros((S, n, n, 4), dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError):
+        sdd.sdd_cv_set_table(ctx, torch.zeros((2, n, n, 3), dtype=torch.float64, device="cuda"))
+    _set_table(sdd, ctx, np.zeros((20, n, n, 4)))
+    sdd.sdd_cv_enable(ctx, True)
+    with pytest.raises(sdd.SddError) as e:        # 20 slices, 10 sub-steps
+        sdd.sdd_interface_mc(ctx, [0.5], [0.5], [10], dt=1e-3, Dt=1e-2)
+    assert e.value.status == sdd.SDD_EINVAL
