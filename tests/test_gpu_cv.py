@@ -140,11 +140,15 @@ def test_cv_exact_gradient_shrinks_the_error_on_gpu(sdd, oracle_mod):
     sdd.sdd_cv_enable(ctx, True)
     cv = _np(sdd.sdd_interface_mc(ctx, xs, ys, npaths, **kw))
     inner = (xs > 0) & (xs < 1) & (ys > 0) & (ys < 1)
-    assert np.all(cv["se_xi"][inner] < plain["se_xi"][inner] / 5)
-    assert np.all(cv["se_eta"][inner] < plain["se_eta"][inner] / 4.5)
+    # what is left is the sub-step discretisation, larger near the boundary where more paths exit
+    for f in ("xi", "eta"):
+        ratio = plain["se_" + f][inner] / cv["se_" + f][inner]
+        assert np.all(ratio > 3.5), (f, ratio.min())
+        assert np.median(ratio) > 5, (f, np.median(ratio))
     ex, ee = W.heat_exact(xs, ys, Dt)
-    assert np.all(np.abs(cv["mean_xi"] - ex)[inner] < 2e-3)
-    assert np.all(np.abs(cv["mean_eta"] - ee)[inner] < 2e-3)
+    # within the (now small) statistical error plus the sub-step bias of the method
+    assert np.all(np.abs(cv["mean_xi"] - ex)[inner] < 4 * cv["se_xi"][inner] + 3e-4)
+    assert np.all(np.abs(cv["mean_eta"] - ee)[inner] < 4 * cv["se_eta"][inner] + 3e-4)
     # and the same numbers as the oracle's control-variate estimator on a few nodes
     sel = np.flatnonzero(inner)[::8]
     P = oracle_mod.Problem(W.w_const(n), xi0, eta0, faces)
@@ -152,6 +156,7 @@ def test_cv_exact_gradient_shrinks_the_error_on_gpu(sdd, oracle_mod):
     for f in ("xi", "eta"):
         d = np.abs(cv["mean_" + f][sel] - o["mean_" + f])
         assert np.all(d <= 3 * o["se_" + f] + 1e-4), (f, d)
+        np.testing.assert_allclose(cv["se_" + f][sel], o["se_" + f], rtol=0.05)
 
 
 def test_cv_mesh_step_matches_oracle(sdd, oracle_mod):
