@@ -194,6 +194,137 @@ sdd_status sdd_interface_mc_record(sdd_ctx* ctx, const sdd_nodes* nodes, const s
 sdd_status sdd_cv_set_table(sdd_ctx* ctx, const double* grad, int32_t slices);
 sdd_status sdd_cv_enable(sdd_ctx* ctx, int32_t on);
 
+/* A copy of the context's current table in the layout of sdd_cv_set_table
+ * (DEVICE, slices * ny * nx * 4 doubles; slices as last set or tabulated). */
+sdd_status sdd_cv_get_table(sdd_ctx* ctx, double* grad);
+
+/* ------------------------------------------------------------------------
+ * Learned control variate.
+ *
+ * The model G of the control variate above is the spatial gradient of a
+ * network g, fitted to the method's own paths (the paper's estimator is the
+ * plain mean of Sec. 4; the network and its training have no counterpart in
+ * the paper). One network per field:
+ *   features  f = (x, y, t / Dt, w(x, y), r(x, y)) with t the time left in
+ *             the mesh step and r = |grad w| / w; w and r are node fields
+ *             (finite differences of the drift, Sec. 4) interpolated
+ *             bilinearly;
+ *   input     z = (f - mu) * s, the standardisation of the training set
+ *             (mu the mean, s the inverse population standard deviation, 0
+ *             for a feature whose deviation is below 1e-6 max(1, |mu|));
+ *   network   g(z) = w3 . tanh(W2 tanh(W1 z + b1) + b2) + b3, widths
+ *             5 -> 64 -> 64 -> 1, FP32;
+ *   loss      the mean of (g - Y)^2 over a batch of single-path scores Y;
+ *   optimiser Adam (beta1 0.9, beta2 0.999, eps 1e-8) with the step decayed
+ *             as lr (1 + cos(pi t / T)) / 2 over the T planned updates.
+ * A parameter block (DEVICE float) holds the xi network at offset 0 and the
+ * eta network at offset SDD_MLP_STRIDE; each is W1 (64 x 5, row-major,
+ * [unit][input]), b1 (64), W2 (64 x 64, [unit][input]), b2 (64), w3 (64),
+ * b3 (1). A normalisation (DEVICE float) is mu[5] then s[5].
+ * All calls below run on the context's stream; those that return values on
+ * the host, or that refill context buffers, wait for it. */
+#define SDD_MLP_INPUTS 5
+#define SDD_MLP_HIDDEN 64
+#define SDD_MLP_PARAMS 4609
+#define SDD_MLP_STRIDE 4616
+
+/* Initial weights: Glorot-uniform, limit sqrt(6 / (fan_in + fan_out)), and
+ * zero biases. Weight p of network f (0 xi, 1 eta) is (2u - 1) limit rounded
+ * to float, u = ((word >> 8) + 0.5) 2^-24 with `word` word 0 of the Philox
+ * block of key `seed` and counter (p, f, 0x494E4954, 0). theta: DEVICE block
+ * of 2 * SDD_MLP_STRIDE floats (the padding is zeroed). */
+sdd_status sdd_mlp_init(sdd_ctx* ctx, uint64_t seed, float* theta);
+
+/* Training data generated by the method itself on the context's current w,
+ * fields and face data: for every horizon k = 1..K (K = Dt / dt) and
+ * m = 0..per_horizon-1, one path of the plain estimator (no control variate)
+ * run k sub-steps from a start point uniform in the unit square. Its node
+ * word is (k - 1) per_horizon + m, its step word 0xFFFFFFFF; the start point
+ * is (u(word 0), u(word 1)) of the Philox block with counter (1, node word,
+ * 0, 0xFFFFFFFF), u as for sdd_mlp_init. Row m K + k - 1 of
+ * feats (DEVICE float, 5 per row) holds its raw features, with t / Dt = k / K,
+ * and of targets (DEVICE float, 2 per row) its two scores.
+ * per_horizon * K <= 2^28 rows. */
+typedef struct {
+    int32_t per_horizon;
+    int32_t exit_mode;
+    double dt;
+    double Dt;
+    uint64_t seed;
+} sdd_sample_params;
+
+sdd_status sdd_cv_samples(sdd_ctx* ctx, const sdd_sample_params* p, float* feats, float* targets);
+
+/* The standardisation of n feature rows (DEVICE, 5 floats each) into norm
+ * (DEVICE, 10 floats): two passes, sums in double. */
+sdd_status sdd_mlp_norm(sdd_ctx* ctx, const float* feats, int64_t n, float* norm);
+
+/* Gradient of the mean squared error over rows 0..rows-1 (a positive multiple
+ * of 64) for both networks: grad (DEVICE, 2 * SDD_MLP_STRIDE floats, same
+ * layout as theta; the padding is not written) and loss (DEVICE, 2 floats, or
+ * NULL). targets: DEVICE, 2 floats per row (xi score, eta score). */
+sdd_status sdd_mlp_grad(sdd_ctx* ctx, const float* theta, const float* norm, const float* feats,
+                        const float* targets, int64_t rows, float* grad, float* loss);
+
+/* Minibatch Adam over the rows in their stored order: epoch after epoch, update
+ * t uses rows [(t mod B) batch, (t mod B + 1) batch), B = floor(n / batch);
+ * batch a positive multiple of 64. max_steps > 0 stops early (the schedule
+ * still spans epochs * B updates). theta (DEVICE) is updated in place;
+ * losses (DEVICE, 2 x updates floats, xi then eta, or NULL) receives each
+ * update's batch loss before the update. */
+typedef struct {
+    int32_t epochs;
+    int32_t batch;
+    double lr;
+    int64_t max_steps;
+} sdd_train_params;
+
+sdd_status sdd_mlp_train(sdd_ctx* ctx, float* theta, const float* norm, const float* feats, const float* targets,
+                         int64_t n, const sdd_train_params* p, float* losses);
+
+/* Tabulate the model of the control variate from a parameter block and
+ * normalisation on the context's current w: at every node and every time
+ * slice q (1 <= slices <= min(K, 128), slice q serving the sub-steps j with
+ * floor(j slices / K) = q, evaluated at the time left at its middle sub-step)
+ * the total derivatives d g / dx, d g / dy of both networks, by forward-mode
+ * differentiation through the features. The 64 x 64 layer runs on the tensor
+ * cores with BF16 operands and FP32 sums. The result replaces the context's
+ * table (as sdd_cv_set_table); sdd_cv_enable still decides whether it is used. */
+sdd_status sdd_cv_tabulate(sdd_ctx* ctx, const float* theta, const float* norm, int32_t slices, double dt, double Dt);
+
+/* All of the above in one call, into buffers the context owns: samples,
+ * standardisation and initial weights (init_seed) -- or, with warm_start and
+ * a model already trained, the previous weights and standardisation --
+ * training, tabulation (slices 0: one per sub-step up to 128). The control
+ * variate is not switched on. info (HOST, may be NULL) receives the times of
+ * the three phases, the rows, the updates, the slices and the last batch
+ * losses. */
+typedef struct {
+    sdd_sample_params samples;
+    sdd_train_params train;
+    int32_t slices;
+    int32_t warm_start;
+    uint64_t init_seed;
+} sdd_cv_train_params;
+
+typedef struct {
+    float samples_ms;
+    float train_ms;
+    float tabulate_ms;
+    float loss_xi;
+    float loss_eta;
+    int32_t slices;
+    int64_t rows;
+    int64_t steps;
+} sdd_cv_train_info;
+
+sdd_status sdd_cv_train(sdd_ctx* ctx, const sdd_cv_train_params* p, sdd_cv_train_info* info);
+
+/* Copies of the model trained by sdd_cv_train (DEVICE; either may be NULL)
+ * and of its first `count` batch losses per network (DEVICE, xi then eta). */
+sdd_status sdd_cv_get_model(sdd_ctx* ctx, float* theta, float* norm);
+sdd_status sdd_cv_losses(sdd_ctx* ctx, float* losses, int64_t count);
+
 /* Launch shape of the path kernel: threads per block and paths per task (a
  * task is a node and a run of its paths that one warp computes). */
 typedef struct {

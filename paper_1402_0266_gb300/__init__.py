@@ -35,7 +35,11 @@ EXPORTS = [
     "sdd_static_scratch_bytes", "sdd_batch_create", "sdd_batch_interface_mc", "sdd_batch_step",
     "sdd_batch_last_step_info", "sdd_batch_set_step_index", "sdd_batch_sync", "sdd_batch_last_error",
     "sdd_batch_destroy", "sdd_autotune", "sdd_batch_autotune", "sdd_cv_set_table", "sdd_cv_enable",
+    "sdd_mlp_init", "sdd_cv_samples", "sdd_mlp_norm", "sdd_mlp_grad", "sdd_mlp_train", "sdd_cv_tabulate",
+    "sdd_cv_train", "sdd_cv_get_model", "sdd_cv_losses", "sdd_cv_get_table",
 ]
+
+MLP_INPUTS, MLP_HIDDEN, MLP_PARAMS, MLP_STRIDE = 5, 64, 4609, 4616
 
 
 class SddError(RuntimeError):
@@ -86,6 +90,27 @@ class _StepParams(ctypes.Structure):
 
 class _Shape(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int32), ("paths_per_task", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+
+class _SampleParams(ctypes.Structure):
+    _fields_ = [("per_horizon", ctypes.c_int32), ("exit_mode", ctypes.c_int32), ("dt", ctypes.c_double),
+                ("Dt", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class _TrainParams(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_double),
+                ("max_steps", ctypes.c_int64)]
+
+
+class _CvTrainParams(ctypes.Structure):
+    _fields_ = [("samples", _SampleParams), ("train", _TrainParams), ("slices", ctypes.c_int32),
+                ("warm_start", ctypes.c_int32), ("init_seed", ctypes.c_uint64)]
+
+
+class _CvTrainInfo(ctypes.Structure):
+    _fields_ = [("samples_ms", ctypes.c_float), ("train_ms", ctypes.c_float), ("tabulate_ms", ctypes.c_float),
+                ("loss_xi", ctypes.c_float), ("loss_eta", ctypes.c_float), ("slices", ctypes.c_int32),
+                ("rows", ctypes.c_int64), ("steps", ctypes.c_int64)]
 
 
 _lib = None
@@ -141,6 +166,16 @@ def lib():
                 "sdd_autotune": [vp, ctypes.POINTER(_Nodes), ctypes.POINTER(_McParams), ctypes.POINTER(_Shape)],
                 "sdd_cv_set_table": [vp, vp, i32],
                 "sdd_cv_enable": [vp, i32],
+                "sdd_mlp_init": [vp, u64, vp],
+                "sdd_cv_samples": [vp, ctypes.POINTER(_SampleParams), vp, vp],
+                "sdd_mlp_norm": [vp, vp, i64, vp],
+                "sdd_mlp_grad": [vp, vp, vp, vp, vp, i64, vp, vp],
+                "sdd_mlp_train": [vp, vp, vp, vp, vp, i64, ctypes.POINTER(_TrainParams), vp],
+                "sdd_cv_tabulate": [vp, vp, vp, i32, dbl, dbl],
+                "sdd_cv_train": [vp, ctypes.POINTER(_CvTrainParams), ctypes.POINTER(_CvTrainInfo)],
+                "sdd_cv_get_model": [vp, vp, vp],
+                "sdd_cv_losses": [vp, vp, i64],
+                "sdd_cv_get_table": [vp, vp],
                 "sdd_batch_autotune": [vp, ctypes.POINTER(_Nodes), ctypes.POINTER(_McParams), ctypes.POINTER(_Shape)],
             }
             for name, args in sig.items():
@@ -561,3 +596,113 @@ def sdd_cv_set_table(ctx: Ctx, grad):
 
 def sdd_cv_enable(ctx: Ctx, on=True):
     ctx._check(lib().sdd_cv_enable(ctx.handle, 1 if on else 0))
+
+
+# ---------------------------------------------------------------- learned control variate
+
+def _f32(t, n, name):
+    torch = _torch()
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.numel() >= n):
+        raise ValueError(f"{name}: expected a contiguous cuda float32 tensor of at least {n} elements")
+    return _ptr(t)
+
+
+def sdd_mlp_init(ctx: Ctx, seed: int):
+    """Initial parameter block (cuda float32, 2 * MLP_STRIDE)."""
+    torch = _torch()
+    th = torch.zeros(2 * MLP_STRIDE, dtype=torch.float32, device="cuda")
+    ctx._check(lib().sdd_mlp_init(ctx.handle, seed, _ptr(th)))
+    return th
+
+
+def sdd_cv_samples(ctx: Ctx, per_horizon: int, *, dt: float, Dt: float, seed: int = 0, exit_mode: int = 0):
+    """(feats (n, 5), targets (n, 2)) cuda float32 tensors, n = per_horizon * K."""
+    torch = _torch()
+    K = int(round(Dt / dt))
+    n = per_horizon * K
+    feats = torch.empty((n, MLP_INPUTS), dtype=torch.float32, device="cuda")
+    targets = torch.empty((n, 2), dtype=torch.float32, device="cuda")
+    p = _SampleParams(per_horizon, exit_mode, dt, Dt, seed)
+    ctx._check(lib().sdd_cv_samples(ctx.handle, ctypes.byref(p), _ptr(feats), _ptr(targets)))
+    return feats, targets
+
+
+def sdd_mlp_norm(ctx: Ctx, feats):
+    torch = _torch()
+    n = feats.shape[0]
+    _f32(feats, n * MLP_INPUTS, "feats")
+    norm = torch.zeros(2 * MLP_INPUTS, dtype=torch.float32, device="cuda")
+    ctx._check(lib().sdd_mlp_norm(ctx.handle, _ptr(feats), n, _ptr(norm)))
+    return norm
+
+
+def sdd_mlp_grad(ctx: Ctx, theta, norm, feats, targets, rows=None):
+    """(grad (2 * MLP_STRIDE), loss (2,)) of the mean squared error over the first rows."""
+    torch = _torch()
+    rows = feats.shape[0] if rows is None else rows
+    _f32(theta, 2 * MLP_STRIDE, "theta")
+    _f32(norm, 2 * MLP_INPUTS, "norm")
+    _f32(feats, rows * MLP_INPUTS, "feats")
+    _f32(targets, rows * 2, "targets")
+    grad = torch.zeros(2 * MLP_STRIDE, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(2, dtype=torch.float32, device="cuda")
+    ctx._check(lib().sdd_mlp_grad(ctx.handle, _ptr(theta), _ptr(norm), _ptr(feats), _ptr(targets), rows,
+                                  _ptr(grad), _ptr(loss)))
+    return grad, loss
+
+
+def sdd_mlp_train(ctx: Ctx, theta, norm, feats, targets, *, epochs: int, batch: int, lr: float, max_steps: int = 0):
+    """Adam in place on theta; returns the batch losses, shape (2, updates)."""
+    torch = _torch()
+    n = feats.shape[0]
+    _f32(theta, 2 * MLP_STRIDE, "theta")
+    _f32(norm, 2 * MLP_INPUTS, "norm")
+    _f32(feats, n * MLP_INPUTS, "feats")
+    _f32(targets, n * 2, "targets")
+    total = epochs * (n // batch)
+    steps = min(total, max_steps) if max_steps > 0 else total
+    losses = torch.zeros((2, max(steps, 1)), dtype=torch.float32, device="cuda")
+    p = _TrainParams(epochs, batch, lr, max_steps)
+    ctx._check(lib().sdd_mlp_train(ctx.handle, _ptr(theta), _ptr(norm), _ptr(feats), _ptr(targets), n,
+                                   ctypes.byref(p), _ptr(losses)))
+    return losses[:, :steps]
+
+
+def sdd_cv_tabulate(ctx: Ctx, theta, norm, slices: int, *, dt: float, Dt: float):
+    _f32(theta, 2 * MLP_STRIDE, "theta")
+    _f32(norm, 2 * MLP_INPUTS, "norm")
+    ctx._check(lib().sdd_cv_tabulate(ctx.handle, _ptr(theta), _ptr(norm), slices, dt, Dt))
+
+
+def sdd_cv_train(ctx: Ctx, *, per_horizon: int, dt: float, Dt: float, seed: int = 0, exit_mode: int = 0,
+                 epochs: int = 20, batch: int = 4096, lr: float = 3e-3, max_steps: int = 0, slices: int = 0,
+                 warm_start: bool = False, init_seed: int = 0):
+    """Samples, training and tabulation in one call; returns the phase times and last losses."""
+    p = _CvTrainParams(_SampleParams(per_horizon, exit_mode, dt, Dt, seed), _TrainParams(epochs, batch, lr, max_steps),
+                       slices, 1 if warm_start else 0, init_seed)
+    info = _CvTrainInfo()
+    ctx._check(lib().sdd_cv_train(ctx.handle, ctypes.byref(p), ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in _CvTrainInfo._fields_}
+
+
+def sdd_cv_get_model(ctx: Ctx):
+    torch = _torch()
+    th = torch.zeros(2 * MLP_STRIDE, dtype=torch.float32, device="cuda")
+    norm = torch.zeros(2 * MLP_INPUTS, dtype=torch.float32, device="cuda")
+    ctx._check(lib().sdd_cv_get_model(ctx.handle, _ptr(th), _ptr(norm)))
+    return th, norm
+
+
+def sdd_cv_losses(ctx: Ctx, count: int):
+    torch = _torch()
+    out = torch.zeros((2, max(count, 1)), dtype=torch.float32, device="cuda")
+    ctx._check(lib().sdd_cv_losses(ctx.handle, _ptr(out), count))
+    return out[:, :count]
+
+
+def sdd_cv_get_table(ctx: Ctx, slices: int):
+    """The context's current table, cuda float64 (slices, ny, nx, 4)."""
+    torch = _torch()
+    out = torch.zeros((slices, ctx.ny, ctx.nx, 4), dtype=torch.float64, device="cuda")
+    ctx._check(lib().sdd_cv_get_table(ctx.handle, _ptr(out)))
+    return out

@@ -99,6 +99,17 @@ struct sdd_ctx {
     DevBuf<float4> cvcoef;     // control-variate table (per slice and cell)
     int cv_slices = 0;
     bool cv_on = false;
+
+    // learned control variate: node features, training data, model, scratch
+    DevBuf<double> cv_w64, cv_r64, cv_table64, cv_norm_scratch, cv_sxy, cv_smean[2];
+    DevBuf<double2> cv_gw;
+    DevBuf<float4> cv_nfa;
+    DevBuf<float2> cv_nfb;
+    DevBuf<float> cv_feats, cv_targets, cv_theta, cv_norm, cv_m, cv_v, cv_part, cv_losses, cv_grad_part;
+    int64_t cv_rows = 0;
+    int64_t cv_loss_steps = 0;
+    bool cv_model = false;
+    Plan sample_plan;
     DevBuf<InstDev> d_inst;
     DevBuf<int> d_status;
     DevBuf<uint32_t> d_step;
@@ -186,7 +197,6 @@ std::vector<int> block_edges(int n, int parts)
     return v;
 }
 
-float below(float v) { return std::nextafter(v, 0.0f); }
 
 InstDev inst_host(const sdd_ctx* c)
 {
@@ -376,6 +386,9 @@ sdd_status build_plan_segs(std::string* err, int sm_count, Plan& P, const std::v
     P.nnodes = count;
     P.ntasks = (int64_t)P.tasks.size();
     P.total_paths = total;
+    // an earlier launch of this plan may still read its buffers on a stream
+    // that does not wait for the synchronous copies below
+    CU(err, cudaDeviceSynchronize());
     CU(err, P.d_nodes.alloc(std::max<int64_t>(count, 1)));
     CU(err, P.d_tasks.alloc(std::max<int64_t>(P.ntasks, 1)));
     CU(err, P.d_partials.alloc(std::max<int64_t>(P.ntasks, 1)));
@@ -708,6 +721,167 @@ sdd_status enqueue_solve(sdd_ctx* c, double Dt, const double* ix, const double* 
     return SDD_OK;
 }
 
+
+void drop_graphs_fn(sdd_ctx* c)
+{
+    c->graph[0].release();
+    c->graph[1].release();
+    c->graph_ok = false;
+}
+
+// ---------------------------------------------------------------- learned control variate (host side)
+
+constexpr uint32_t kInitWord = 0x494E4954u;        // counter word of the initial weights
+constexpr uint32_t kSampleStepWord = 0xFFFFFFFFu;  // step word of the training paths
+
+// u = ((bits >> 8) + 0.5) 2^-24: a uniform in (0, 1) with 24 significant bits
+double unit_open(uint32_t bits) { return ((double)(bits >> 8) + 0.5) * (1.0 / 16777216.0); }
+
+// Glorot-uniform weights, zero biases; weight p of network f from word 0 of
+// the Philox block with counter (p, f, kInitWord, 0).
+void init_params_host(uint64_t seed, std::vector<float>& th)
+{
+    th.assign(2 * (size_t)kMlpStride, 0.f);
+    const int H = kMlpHidden, D = kMlpInputs;
+    struct Seg { int a, b, fan_in, fan_out; };
+    const Seg segs[3] = {{0, H * D, D, H}, {H * D + H, H * D + H + H * H, H, H},
+                         {H * D + 2 * H + H * H, H * D + 3 * H + H * H, H, 1}};
+    for (int f = 0; f < 2; ++f)
+        for (const Seg& g : segs) {
+            const double limit = std::sqrt(6.0 / (double)(g.fan_in + g.fan_out));
+            for (int p = g.a; p < g.b; ++p) {
+                const uint4 r = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)f, kInitWord, 0u), (uint32_t)seed,
+                                              (uint32_t)(seed >> 32));
+                th[(size_t)f * kMlpStride + p] = (float)((2.0 * unit_open(r.x) - 1.0) * limit);
+            }
+        }
+}
+
+sdd_status ensure_node_features(sdd_ctx* c)
+{
+    const size_t n = (size_t)c->nx * c->ny;
+    CU(c, c->cv_w64.alloc(n));
+    CU(c, c->cv_r64.alloc(n));
+    CU(c, c->cv_gw.alloc(n));
+    CU(c, c->cv_nfa.alloc(n));
+    CU(c, c->cv_nfb.alloc(n));
+    CU(c, launch_node_features(c->w.p, c->nx, c->ny, c->cv_w64.p, c->cv_r64.p, c->cv_gw.p, c->cv_nfa.p, c->cv_nfb.p,
+                               c->stream));
+    return SDD_OK;
+}
+
+// Time left, as a fraction of Dt, at the middle sub-step of each slice.
+void slice_fracs(int K, int S, float* out)
+{
+    for (int q = 0; q < S; ++q) {
+        const int64_t b0 = ((int64_t)q * K + S - 1) / S, b1 = ((int64_t)(q + 1) * K + S - 1) / S;
+        out[q] = (float)(((double)K - 0.5 * (double)(b0 + b1 - 1)) / (double)K);
+    }
+}
+
+sdd_status set_table_from64(sdd_ctx* c, int slices)
+{
+    const size_t cells = (size_t)(c->nx - 1) * (c->ny - 1);
+    CU(c, c->cvcoef.alloc(4 * cells * (size_t)slices));
+    CU(c, launch_cv_cells(c->cv_table64.p, slices, c->nx, c->ny, c->cvcoef.p, c->stream));
+    c->cv_slices = slices;
+    CU(c, cudaStreamSynchronize(c->stream));
+    return upload_inst(c);
+}
+
+sdd_status train_loop(sdd_ctx* c, float* theta, const float* norm, const float* feats, const float* targets,
+                      int64_t n, const sdd_train_params* p, float* losses, int64_t* steps_out)
+{
+    const int tile = mlp_tile_rows();
+    if (p->epochs < 1 || p->batch < tile || p->batch % tile != 0 || p->batch > (1 << 24))
+        return fail(c, SDD_EINVAL, "epochs must be >= 1 and batch a positive multiple of %d", tile);
+    if (!(p->lr > 0.0) || !std::isfinite(p->lr)) return fail(c, SDD_EINVAL, "lr must be positive");
+    const int64_t nb = n / p->batch;
+    if (nb < 1) return fail(c, SDD_EINVAL, "fewer rows than one batch");
+    int64_t total = (int64_t)p->epochs * nb;
+    const int64_t run = p->max_steps > 0 ? std::min<int64_t>(p->max_steps, total) : total;
+    const int nblk = p->batch / tile;
+    CU(c, c->cv_m.alloc(2 * (size_t)kMlpStride));
+    CU(c, c->cv_v.alloc(2 * (size_t)kMlpStride));
+    CU(c, c->cv_part.alloc(2 * (size_t)nblk * kMlpStride));
+    CU(c, cudaMemsetAsync(c->cv_m.p, 0, 2 * (size_t)kMlpStride * sizeof(float), c->stream));
+    CU(c, cudaMemsetAsync(c->cv_v.p, 0, 2 * (size_t)kMlpStride * sizeof(float), c->stream));
+    const float inv = 1.0f / (float)p->batch;
+    for (int64_t t = 0; t < run; ++t) {
+        const int64_t b = t % nb;
+        const double lr = p->lr * 0.5 * (1.0 + std::cos(M_PI * (double)t / (double)total));
+        CU(c, launch_mlp_grad(theta, norm, feats, targets, b * p->batch, p->batch, inv, c->cv_part.p, c->stream));
+        CU(c, launch_mlp_adam(theta, c->cv_m.p, c->cv_v.p, c->cv_part.p, nblk, lr, t + 1, inv, losses, run, t,
+                              c->stream));
+    }
+    if (steps_out) *steps_out = run;
+    return SDD_OK;
+}
+
+sdd_status samples_into(sdd_ctx* c, const sdd_sample_params* p, float* feats, float* targets)
+{
+    int K = 0;
+    if (!valid_params(c, p->dt, p->Dt, p->exit_mode, &K))
+        return fail(c, SDD_EINVAL, "dt, Dt or exit_mode rejected (Dt / dt must be an integer in [1, 2^20])");
+    const int64_t M = p->per_horizon;
+    if (M < 1 || M * (int64_t)K > (int64_t)1 << 28)
+        return fail(c, SDD_EINVAL, "per_horizon must be >= 1 and per_horizon * K <= 2^28");
+    sdd_status st = prepare(c, c->stream);
+    if (st != SDD_OK) return st;
+    if ((st = ensure_node_features(c)) != SDD_OK) return st;
+    CU(c, c->cv_sxy.alloc(2 * (size_t)M));
+    CU(c, c->cv_smean[0].alloc((size_t)M));
+    CU(c, c->cv_smean[1].alloc((size_t)M));
+    std::vector<double> xs(M), ys(M);
+    std::vector<int64_t> np(M, 1);
+    OutDev out{};
+    out.mean_xi = c->cv_smean[0].p;
+    out.mean_eta = c->cv_smean[1].p;
+    for (int k = 1; k <= K; ++k) {
+        const uint32_t word0 = (uint32_t)((int64_t)(k - 1) * M);
+        for (int64_t m = 0; m < M; ++m) {
+            const uint4 r = philox4x32_10(make_uint4(1u, word0 + (uint32_t)m, 0u, kSampleStepWord), (uint32_t)p->seed,
+                                          (uint32_t)(p->seed >> 32));
+            xs[m] = unit_open(r.x);
+            ys[m] = unit_open(r.y);
+        }
+        // the previous horizon's launch and scatter read the buffers refilled here
+        CU(c, cudaStreamSynchronize(c->stream));
+        std::vector<NodeSeg> segs(1);
+        segs[0] = NodeSeg{xs.data(), ys.data(), np.data(), M, 0, word0};
+        if ((st = build_plan_segs(&c->err, c->sm_count, c->sample_plan, segs, 0, 0, p->exit_mode, false)) != SDD_OK)
+            return st;
+        CU(c, cudaMemcpyAsync(c->cv_sxy.p, xs.data(), M * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        CU(c, cudaMemcpyAsync(c->cv_sxy.p + M, ys.data(), M * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        if ((st = run_plan_on(&c->err, c->sample_plan, c->d_inst.p, nullptr, out, p->dt, k, p->seed, kSampleStepWord,
+                              nullptr, p->exit_mode, nullptr, c->stream, nullptr, nullptr, 0)) != SDD_OK)
+            return st;
+        CU(c, launch_cv_scatter(c->cv_sxy.p, c->cv_sxy.p + M, out.mean_xi, out.mean_eta, c->cv_nfa.p, c->nx, c->ny, k,
+                                K, (int)M, feats, targets, c->stream));
+    }
+    CU(c, cudaStreamSynchronize(c->stream));
+    return SDD_OK;
+}
+
+sdd_status tabulate_into_ctx(sdd_ctx* c, const float* theta, const float* norm, int slices, double dt, double Dt)
+{
+    int K = 0;
+    if (!valid_params(c, dt, Dt, 0, &K)) return fail(c, SDD_EINVAL, "dt, Dt rejected");
+    if (slices < 1 || slices > kMaxCvSlices || slices > K)
+        return fail(c, SDD_EINVAL, "slices must be in [1, min(K, %d)]", kMaxCvSlices);
+    sdd_status st = ensure_node_features(c);
+    if (st != SDD_OK) return st;
+    const size_t nn = (size_t)c->nx * c->ny;
+    CU(c, c->cv_table64.alloc(4 * nn * (size_t)slices));
+    float tf[kMaxCvSlices];
+    slice_fracs(K, slices, tf);
+    CU(c, launch_cv_tabulate(theta, norm, c->cv_nfa.p, c->cv_nfb.p, c->nx, c->ny, slices, tf, c->cv_table64.p,
+                             c->sm_count, c->stream));
+    if ((st = set_table_from64(c, slices)) != SDD_OK) return st;
+    drop_graphs_fn(c);
+    return SDD_OK;
+}
+
 OutDev out_from(const sdd_node_stats* o)
 {
     OutDev d{};
@@ -807,12 +981,7 @@ sdd_status sdd_init(sdd_ctx** out, const sdd_grid* g, const float* w, const doub
     return SDD_OK;
 }
 
-static void drop_graphs(sdd_ctx* c)
-{
-    c->graph[0].release();
-    c->graph[1].release();
-    c->graph_ok = false;
-}
+static void drop_graphs(sdd_ctx* c) { drop_graphs_fn(c); }
 
 sdd_status sdd_set_w(sdd_ctx* c, const float* w)
 {
@@ -929,14 +1098,21 @@ sdd_status sdd_cv_set_table(sdd_ctx* c, const double* grad, int32_t slices)
 {
     if (!c || !grad) return fail(c, SDD_EINVAL, "null argument");
     if (slices < 1 || slices > kMaxCvSlices) return fail(c, SDD_EINVAL, "slices must be in [1, %d]", kMaxCvSlices);
-    const size_t cells = (size_t)(c->nx - 1) * (c->ny - 1);
-    CU(c, c->cvcoef.alloc(4 * cells * (size_t)slices));
-    CU(c, launch_cv_cells(grad, slices, c->nx, c->ny, c->cvcoef.p, c->stream));
-    c->cv_slices = slices;
-    CU(c, cudaStreamSynchronize(c->stream));
-    sdd_status st = upload_inst(c);
+    const size_t n = 4 * (size_t)c->nx * c->ny * (size_t)slices;
+    CU(c, c->cv_table64.alloc(n));
+    CU(c, cudaMemcpyAsync(c->cv_table64.p, grad, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    sdd_status st = set_table_from64(c, slices);
     if (st != SDD_OK) return st;
     drop_graphs(c);
+    return SDD_OK;
+}
+
+sdd_status sdd_cv_get_table(sdd_ctx* c, double* grad)
+{
+    if (!c || !grad) return fail(c, SDD_EINVAL, "null argument");
+    if (c->cv_slices < 1) return fail(c, SDD_EINVAL, "no control-variate table has been set");
+    const size_t n = 4 * (size_t)c->nx * c->ny * (size_t)c->cv_slices;
+    CU(c, cudaMemcpyAsync(grad, c->cv_table64.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     return SDD_OK;
 }
 
@@ -946,6 +1122,151 @@ sdd_status sdd_cv_enable(sdd_ctx* c, int32_t on)
     if (on && c->cv_slices < 1) return fail(c, SDD_EINVAL, "no control-variate table has been set");
     if ((on != 0) != c->cv_on) drop_graphs(c);
     c->cv_on = on != 0;
+    return SDD_OK;
+}
+
+sdd_status sdd_mlp_init(sdd_ctx* c, uint64_t seed, float* theta)
+{
+    if (!c || !theta) return fail(c, SDD_EINVAL, "null argument");
+    std::vector<float> th;
+    init_params_host(seed, th);
+    CU(c, cudaMemcpyAsync(theta, th.data(), th.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    CU(c, cudaStreamSynchronize(c->stream));
+    return SDD_OK;
+}
+
+sdd_status sdd_cv_samples(sdd_ctx* c, const sdd_sample_params* p, float* feats, float* targets)
+{
+    if (!c || !p || !feats || !targets) return fail(c, SDD_EINVAL, "null argument");
+    return samples_into(c, p, feats, targets);
+}
+
+sdd_status sdd_mlp_norm(sdd_ctx* c, const float* feats, int64_t n, float* norm)
+{
+    if (!c || !feats || !norm) return fail(c, SDD_EINVAL, "null argument");
+    if (n < 1) return fail(c, SDD_EINVAL, "no rows");
+    CU(c, c->cv_norm_scratch.alloc(mlp_norm_scratch_doubles()));
+    CU(c, launch_mlp_norm(feats, n, c->cv_norm_scratch.p, norm, c->stream));
+    return SDD_OK;
+}
+
+sdd_status sdd_mlp_grad(sdd_ctx* c, const float* theta, const float* norm, const float* feats, const float* targets,
+                        int64_t rows, float* grad, float* loss)
+{
+    if (!c || !theta || !norm || !feats || !targets || !grad) return fail(c, SDD_EINVAL, "null argument");
+    const int tile = mlp_tile_rows();
+    if (rows < tile || rows % tile != 0 || rows > (1LL << 28))
+        return fail(c, SDD_EINVAL, "rows must be a positive multiple of %d", tile);
+    const int nblk = (int)(rows / tile);
+    CU(c, c->cv_grad_part.alloc(2 * (size_t)nblk * kMlpStride));
+    const float inv = (float)(1.0 / (double)rows);
+    CU(c, launch_mlp_grad(theta, norm, feats, targets, 0, rows, inv, c->cv_grad_part.p, c->stream));
+    CU(c, launch_mlp_reduce(c->cv_grad_part.p, nblk, inv, grad, loss, c->stream));
+    return SDD_OK;
+}
+
+sdd_status sdd_mlp_train(sdd_ctx* c, float* theta, const float* norm, const float* feats, const float* targets,
+                         int64_t n, const sdd_train_params* p, float* losses)
+{
+    if (!c || !theta || !norm || !feats || !targets || !p) return fail(c, SDD_EINVAL, "null argument");
+    return train_loop(c, theta, norm, feats, targets, n, p, losses, nullptr);
+}
+
+sdd_status sdd_cv_tabulate(sdd_ctx* c, const float* theta, const float* norm, int32_t slices, double dt, double Dt)
+{
+    if (!c || !theta || !norm) return fail(c, SDD_EINVAL, "null argument");
+    return tabulate_into_ctx(c, theta, norm, slices, dt, Dt);
+}
+
+sdd_status sdd_cv_train(sdd_ctx* c, const sdd_cv_train_params* p, sdd_cv_train_info* info)
+{
+    if (!c || !p) return fail(c, SDD_EINVAL, "null argument");
+    int K = 0;
+    if (!valid_params(c, p->samples.dt, p->samples.Dt, p->samples.exit_mode, &K))
+        return fail(c, SDD_EINVAL, "dt, Dt or exit_mode rejected");
+    const int slices = p->slices > 0 ? p->slices : std::min(K, kMaxCvSlices);
+    if (slices > K || slices > kMaxCvSlices) return fail(c, SDD_EINVAL, "slices must be in [1, min(K, %d)]", kMaxCvSlices);
+    const int64_t n = (int64_t)p->samples.per_horizon * K;
+    if (p->samples.per_horizon < 1 || n > (1LL << 28)) return fail(c, SDD_EINVAL, "per_horizon out of range");
+    if (n < p->train.batch) return fail(c, SDD_EINVAL, "fewer training rows than one batch");
+    cudaEvent_t ev[4] = {};
+    for (auto& e : ev) CU(c, cudaEventCreate(&e));
+    struct Guard {
+        cudaEvent_t* e;
+        ~Guard() { for (int k = 0; k < 4; ++k) if (e[k]) cudaEventDestroy(e[k]); }
+    } guard{ev};
+    CU(c, c->cv_feats.alloc((size_t)n * kMlpInputs));
+    CU(c, c->cv_targets.alloc((size_t)n * 2));
+    CU(c, c->cv_theta.alloc(2 * (size_t)kMlpStride));
+    CU(c, c->cv_norm.alloc(16));
+    CU(c, cudaEventRecord(ev[0], c->stream));
+    sdd_status st = samples_into(c, &p->samples, c->cv_feats.p, c->cv_targets.p);
+    if (st != SDD_OK) return st;
+    CU(c, cudaEventRecord(ev[1], c->stream));
+    if (!(p->warm_start && c->cv_model)) {
+        std::vector<float> th;
+        init_params_host(p->init_seed, th);
+        CU(c, cudaMemcpyAsync(c->cv_theta.p, th.data(), th.size() * sizeof(float), cudaMemcpyHostToDevice,
+                              c->stream));
+        CU(c, cudaStreamSynchronize(c->stream));
+        CU(c, c->cv_norm_scratch.alloc(mlp_norm_scratch_doubles()));
+        CU(c, launch_mlp_norm(c->cv_feats.p, n, c->cv_norm_scratch.p, c->cv_norm.p, c->stream));
+    }
+    int64_t steps = 0;
+    const int64_t nb = n / p->train.batch;
+    const int64_t planned = (int64_t)p->train.epochs * nb;
+    const int64_t run = p->train.max_steps > 0 ? std::min<int64_t>(p->train.max_steps, planned) : planned;
+    CU(c, c->cv_losses.alloc(2 * (size_t)std::max<int64_t>(run, 1)));
+    if ((st = train_loop(c, c->cv_theta.p, c->cv_norm.p, c->cv_feats.p, c->cv_targets.p, n, &p->train,
+                         c->cv_losses.p, &steps)) != SDD_OK)
+        return st;
+    CU(c, cudaEventRecord(ev[2], c->stream));
+    c->cv_model = true;
+    c->cv_rows = n;
+    c->cv_loss_steps = steps;
+    if ((st = tabulate_into_ctx(c, c->cv_theta.p, c->cv_norm.p, slices, p->samples.dt, p->samples.Dt)) != SDD_OK)
+        return st;
+    CU(c, cudaEventRecord(ev[3], c->stream));
+    CU(c, cudaEventSynchronize(ev[3]));
+    if (info) {
+        std::memset(info, 0, sizeof *info);
+        CU(c, cudaEventElapsedTime(&info->samples_ms, ev[0], ev[1]));
+        CU(c, cudaEventElapsedTime(&info->train_ms, ev[1], ev[2]));
+        CU(c, cudaEventElapsedTime(&info->tabulate_ms, ev[2], ev[3]));
+        info->rows = n;
+        info->steps = steps;
+        info->slices = slices;
+        if (steps > 0) {
+            float l[2];
+            CU(c, cudaMemcpy(&l[0], c->cv_losses.p + (steps - 1), sizeof(float), cudaMemcpyDeviceToHost));
+            CU(c, cudaMemcpy(&l[1], c->cv_losses.p + steps + (steps - 1), sizeof(float), cudaMemcpyDeviceToHost));
+            info->loss_xi = l[0];
+            info->loss_eta = l[1];
+        }
+    }
+    return SDD_OK;
+}
+
+sdd_status sdd_cv_get_model(sdd_ctx* c, float* theta, float* norm)
+{
+    if (!c) return SDD_EINVAL;
+    if (!c->cv_model) return fail(c, SDD_EINVAL, "no trained model");
+    if (theta)
+        CU(c, cudaMemcpyAsync(theta, c->cv_theta.p, 2 * (size_t)kMlpStride * sizeof(float), cudaMemcpyDeviceToDevice,
+                              c->stream));
+    if (norm) CU(c, cudaMemcpyAsync(norm, c->cv_norm.p, 2 * kMlpInputs * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    return SDD_OK;
+}
+
+sdd_status sdd_cv_losses(sdd_ctx* c, float* losses, int64_t count)
+{
+    if (!c || !losses) return fail(c, SDD_EINVAL, "null argument");
+    if (!c->cv_model) return fail(c, SDD_EINVAL, "no trained model");
+    const int64_t have = c->cv_loss_steps;
+    if (count < 0 || count > have) return fail(c, SDD_EINVAL, "count exceeds the recorded steps");
+    CU(c, cudaMemcpyAsync(losses, c->cv_losses.p, (size_t)count * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    CU(c, cudaMemcpyAsync(losses + count, c->cv_losses.p + have, (size_t)count * sizeof(float),
+                          cudaMemcpyDeviceToDevice, c->stream));
     return SDD_OK;
 }
 

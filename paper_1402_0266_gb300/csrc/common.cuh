@@ -15,6 +15,13 @@ namespace sdd {
 
 constexpr int kMaxCvSlices = 128;  // time slices of a control-variate table
 
+// The control variate's network: 5 inputs, two tanh layers of 64, one output;
+// parameters W1 (64 x 5), b1, W2 (64 x 64, [out][in]), b2, w3, b3 in this order.
+constexpr int kMlpInputs = 5;
+constexpr int kMlpHidden = 64;
+constexpr int kMlpParams = 4609;
+constexpr int kMlpStride = 4616;   // floats between the two networks (xi, eta) of a parameter block
+
 // Geometry and field tables of one instance, as the path kernel reads them.
 struct InstDev {
     const float4* bcoef;   // 2 float4 per cell: (a0x, a0y, a1x, a1y), (a2x, a2y, a3x, a3y) of b = (b_x, b_y)
@@ -122,6 +129,23 @@ cudaError_t launch_prep_cells(const float* w, const double* xi, const double* et
 cudaError_t launch_winslow_faces(const float* w, int nx, int ny, double* faces64, cudaStream_t s);
 cudaError_t launch_cv_cells(const double* grad, int slices, int nx, int ny, float4* cvcoef, cudaStream_t s);
 cudaError_t launch_faces32(const double* faces64, float* faces32, int n, cudaStream_t s);
+
+// Learned control variate (mlp.cu).
+cudaError_t launch_node_features(const float* w, int nx, int ny, double* w64, double* r64, double2* gw, float4* nfa,
+                                 float2* nfb, cudaStream_t s);
+cudaError_t launch_cv_scatter(const double* xs, const double* ys, const double* yxi, const double* yeta,
+                              const float4* nfa, int nx, int ny, int k, int K, int M, float* feats, float* targets,
+                              cudaStream_t s);
+size_t mlp_norm_scratch_doubles();
+cudaError_t launch_mlp_norm(const float* feats, long long n, double* scratch, float* norm, cudaStream_t s);
+int mlp_tile_rows();
+cudaError_t launch_mlp_grad(const float* theta, const float* norm, const float* feats, const float* targets,
+                            long long row0, long long rows, float inv_batch, float* part, cudaStream_t s);
+cudaError_t launch_mlp_reduce(const float* part, int nblk, float inv_rows, float* grad, float* loss, cudaStream_t s);
+cudaError_t launch_mlp_adam(float* theta, float* m, float* v, const float* part, int nblk, double lr, long long t,
+                            float inv_rows, float* losses, long long steps, long long step, cudaStream_t s);
+cudaError_t launch_cv_tabulate(const float* theta, const float* norm, const float4* nfa, const float2* nfb, int nx,
+                               int ny, int slices, const float* tfrac, double* table, int sm_count, cudaStream_t s);
 
 cudaError_t launch_rng_draw(uint64_t seed, const uint32_t* ctrs, long long count, uint32_t* words, float* normals,
                             cudaStream_t s);

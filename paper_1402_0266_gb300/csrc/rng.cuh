@@ -19,7 +19,7 @@ namespace sdd {
 // (k0 + r W0, k1 + r W1). Splitting the ten rounds lets a caller place them
 // in the shadow of memory loads.
 template <int R0, int R1>
-__device__ __forceinline__ void philox_rounds(uint4& c, uint32_t k0, uint32_t k1)
+__host__ __device__ __forceinline__ void philox_rounds(uint4& c, uint32_t k0, uint32_t k1)
 {
 #pragma unroll
     for (int r = R0; r < R1; ++r) {
@@ -32,7 +32,7 @@ __device__ __forceinline__ void philox_rounds(uint4& c, uint32_t k0, uint32_t k1
     }
 }
 
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+__host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
 {
     philox_rounds<0, 10>(c, k0, k1);
     return c;
