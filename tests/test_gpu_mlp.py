@@ -144,7 +144,9 @@ def test_adam_updates_match_oracle(sdd, mlp, oracle_mod):
     got = _split(theta)
     for f in range(2):
         want, wl = mlp.train(th0[f], Z, Y[:, f], epochs=3, batch=1024, lr0=lr, steps=steps)
-        np.testing.assert_allclose(losses.cpu().numpy()[f], wl, rtol=1e-5)
+        # the first loss is FP32 rounding only; later ones also carry the earlier updates' differences
+        np.testing.assert_allclose(losses.cpu().numpy()[f][0], wl[0], rtol=1e-5)
+        np.testing.assert_allclose(losses.cpu().numpy()[f], wl, rtol=1e-4)
         d = np.abs(got[f] - want)
         moved = np.abs(want - th0[f]).max()
         assert moved > 0.5 * lr
