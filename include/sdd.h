@@ -175,24 +175,36 @@ sdd_status sdd_interface_mc(sdd_ctx* ctx, const sdd_nodes* nodes, const sdd_mc_p
 sdd_status sdd_interface_mc_record(sdd_ctx* ctx, const sdd_nodes* nodes, const sdd_mc_params* p,
                                    sdd_node_stats* out, const sdd_path_records* rec);
 
-/* Control variate (a learned or given model of the solution's gradient; the
- * paper notes that Monte Carlo converges slowly, Sec. 4). With it enabled,
- * every path's scores become Y - sum_{j < kappa} G(s_j, X_j) . sqrt(2) dW_j:
- * the model gradient at the start of each sub-step the path takes times the
- * sub-step's Brownian increment. The sum has zero mean for any model (a
- * martingale stopped at a bounded time), so the estimate stays unbiased; a
- * good model shrinks the variance.
+/* Control variate (a model of the solution's gradient; the paper notes that
+ * Monte Carlo converges slowly, Sec. 4). With it enabled, every path's scores
+ * become Y - sum_{j < kappa} G(s_j, X_j) . sqrt(2) dW_j: the model gradient at
+ * the start of each sub-step the path takes times the sub-step's Brownian
+ * increment. The sum has zero mean for any model (a martingale stopped at a
+ * bounded time), so the estimate stays unbiased; a good model shrinks the
+ * variance.
+ * sdd_cv_set_table gives the model as a table:
  *   grad    DEVICE doubles, shape (slices, ny, nx, 4): at every node the
  *           d/dx, d/dy of the xi model and of the eta model; slice q serves
  *           the sub-steps j with floor(j * slices / K) = q and is interpolated
  *           bilinearly in space. 1 <= slices <= 128, and an estimate with
- *           more slices than sub-steps K fails with SDD_EINVAL. Copied into a
- *           table of the context (the call waits for it).
- * sdd_cv_enable turns the control variate on (nonzero) or off for every later
- * estimate and mesh step of the context (not for batched calls, which run
- * without it); turning it on needs a table. */
+ *           more slices than sub-steps K fails with SDD_EINVAL. Copied into
+ *           the context (the call waits for it).
+ * sdd_cv_enable chooses the model of every later estimate and mesh step of
+ * the context (batched calls run without one):
+ *   SDD_CV_OFF     the plain estimator;
+ *   SDD_CV_TABLE   the table last set or tabulated;
+ *   SDD_CV_MODEL   the trained network (sdd_cv_train or sdd_cv_set_model),
+ *                  tabulated again from the context's w before every
+ *                  estimate (inside the mesh step's graph);
+ *   SDD_CV_FIELDS  one slice from the fields at t_{n-1}: the finite-difference
+ *                  gradients of xi and eta (no training; over a short mesh
+ *                  step the solution's gradient stays close to it). */
+#define SDD_CV_OFF 0
+#define SDD_CV_TABLE 1
+#define SDD_CV_MODEL 2
+#define SDD_CV_FIELDS 3
 sdd_status sdd_cv_set_table(sdd_ctx* ctx, const double* grad, int32_t slices);
-sdd_status sdd_cv_enable(sdd_ctx* ctx, int32_t on);
+sdd_status sdd_cv_enable(sdd_ctx* ctx, int32_t mode);
 
 /* A copy of the context's current table in the layout of sdd_cv_set_table
  * (DEVICE, slices * ny * nx * 4 doubles; slices as last set or tabulated). */
@@ -321,7 +333,10 @@ typedef struct {
 sdd_status sdd_cv_train(sdd_ctx* ctx, const sdd_cv_train_params* p, sdd_cv_train_info* info);
 
 /* Copies of the model trained by sdd_cv_train (DEVICE; either may be NULL)
- * and of its first `count` batch losses per network (DEVICE, xi then eta). */
+ * and of its first `count` batch losses per network (DEVICE, xi then eta).
+ * sdd_cv_set_model makes a parameter block and normalisation (DEVICE, copied)
+ * the context's model, tabulated at `slices` time slices in SDD_CV_MODEL. */
+sdd_status sdd_cv_set_model(sdd_ctx* ctx, const float* theta, const float* norm, int32_t slices);
 sdd_status sdd_cv_get_model(sdd_ctx* ctx, float* theta, float* norm);
 sdd_status sdd_cv_losses(sdd_ctx* ctx, float* losses, int64_t count);
 

@@ -294,6 +294,15 @@ def tabulate(thetas, mu, s, w, K: int, S: int):
     return T
 
 
+def field_gradient_table(xi, eta):
+    """The control variate without training: one slice holding the finite-
+    difference gradients of the fields at t_{n-1} (Sec. 4's differences). Over
+    a short mesh step the solution's gradient stays close to it."""
+    gx, gy = fd_grad(xi)
+    hx, hy = fd_grad(eta)
+    return np.stack([gx, gy, hx, hy], axis=-1)[None]
+
+
 # ---------------------------------------------------------------- training data
 
 def sample_starts(seed: int, words):

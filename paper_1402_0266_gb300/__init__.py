@@ -36,8 +36,10 @@ EXPORTS = [
     "sdd_batch_last_step_info", "sdd_batch_set_step_index", "sdd_batch_sync", "sdd_batch_last_error",
     "sdd_batch_destroy", "sdd_autotune", "sdd_batch_autotune", "sdd_cv_set_table", "sdd_cv_enable",
     "sdd_mlp_init", "sdd_cv_samples", "sdd_mlp_norm", "sdd_mlp_grad", "sdd_mlp_train", "sdd_cv_tabulate",
-    "sdd_cv_train", "sdd_cv_get_model", "sdd_cv_losses", "sdd_cv_get_table",
+    "sdd_cv_train", "sdd_cv_get_model", "sdd_cv_losses", "sdd_cv_get_table", "sdd_cv_set_model",
 ]
+
+SDD_CV_OFF, SDD_CV_TABLE, SDD_CV_MODEL, SDD_CV_FIELDS = range(4)
 
 MLP_INPUTS, MLP_HIDDEN, MLP_PARAMS, MLP_STRIDE = 5, 64, 4609, 4616
 
@@ -176,6 +178,7 @@ def lib():
                 "sdd_cv_get_model": [vp, vp, vp],
                 "sdd_cv_losses": [vp, vp, i64],
                 "sdd_cv_get_table": [vp, vp],
+                "sdd_cv_set_model": [vp, vp, vp, i32],
                 "sdd_batch_autotune": [vp, ctypes.POINTER(_Nodes), ctypes.POINTER(_McParams), ctypes.POINTER(_Shape)],
             }
             for name, args in sig.items():
@@ -594,8 +597,13 @@ def sdd_cv_set_table(ctx: Ctx, grad):
     ctx._check(lib().sdd_cv_set_table(ctx.handle, _ptr(grad), grad.shape[0]))
 
 
-def sdd_cv_enable(ctx: Ctx, on=True):
-    ctx._check(lib().sdd_cv_enable(ctx.handle, 1 if on else 0))
+def sdd_cv_enable(ctx: Ctx, mode=SDD_CV_TABLE):
+    """mode: SDD_CV_OFF / SDD_CV_TABLE / SDD_CV_MODEL / SDD_CV_FIELDS (True means SDD_CV_TABLE, False off)."""
+    if mode is True:
+        mode = SDD_CV_TABLE
+    elif mode is False or mode is None:
+        mode = SDD_CV_OFF
+    ctx._check(lib().sdd_cv_enable(ctx.handle, int(mode)))
 
 
 # ---------------------------------------------------------------- learned control variate
@@ -706,3 +714,9 @@ def sdd_cv_get_table(ctx: Ctx, slices: int):
     out = torch.zeros((slices, ctx.ny, ctx.nx, 4), dtype=torch.float64, device="cuda")
     ctx._check(lib().sdd_cv_get_table(ctx.handle, _ptr(out)))
     return out
+
+
+def sdd_cv_set_model(ctx: Ctx, theta, norm, slices: int):
+    _f32(theta, 2 * MLP_STRIDE, "theta")
+    _f32(norm, 2 * MLP_INPUTS, "norm")
+    ctx._check(lib().sdd_cv_set_model(ctx.handle, _ptr(theta), _ptr(norm), slices))

@@ -98,7 +98,8 @@ struct sdd_ctx {
     DevBuf<float4> bcoef, fcoef;
     DevBuf<float4> cvcoef;     // control-variate table (per slice and cell)
     int cv_slices = 0;
-    bool cv_on = false;
+    int cv_mode = 0;           // 0 off, 1 the table as set, 2 the model re-tabulated per estimate, 3 field gradient
+    int cv_model_slices = 0;   // time slices of the model's table
 
     // learned control variate: node features, training data, model, scratch
     DevBuf<double> cv_w64, cv_r64, cv_table64, cv_norm_scratch, cv_sxy, cv_smean[2];
@@ -563,7 +564,7 @@ sdd_status run_plan(sdd_ctx* c, Plan& P, double dt, int K, uint64_t seed, uint32
                     cudaEvent_t ev_a = nullptr, cudaEvent_t ev_b = nullptr)
 {
     return run_plan_on(&c->err, P, c->d_inst.p, nullptr, out, dt, K, seed, step_index, step_ptr, exit_mode, rec, s,
-                       ev_a, ev_b, c->cv_on ? c->cv_slices : 0);
+                       ev_a, ev_b, c->cv_mode ? c->cv_slices : 0);
 }
 
 // Launch shape for a plan: explicit requests win, else a tuned shape for this node set, else the heuristic.
@@ -779,6 +780,8 @@ void slice_fracs(int K, int S, float* out)
     }
 }
 
+sdd_status cv_mode_buffers(sdd_ctx* c, int mode);
+
 sdd_status set_table_from64(sdd_ctx* c, int slices)
 {
     const size_t cells = (size_t)(c->nx - 1) * (c->ny - 1);
@@ -786,6 +789,8 @@ sdd_status set_table_from64(sdd_ctx* c, int slices)
     CU(c, launch_cv_cells(c->cv_table64.p, slices, c->nx, c->ny, c->cvcoef.p, c->stream));
     c->cv_slices = slices;
     CU(c, cudaStreamSynchronize(c->stream));
+    // a mode that rebuilds its table per estimate keeps its own slice count
+    if (c->cv_mode >= 2) return cv_mode_buffers(c, c->cv_mode);
     return upload_inst(c);
 }
 
@@ -879,6 +884,46 @@ sdd_status tabulate_into_ctx(sdd_ctx* c, const float* theta, const float* norm, 
                              c->sm_count, c->stream));
     if ((st = set_table_from64(c, slices)) != SDD_OK) return st;
     drop_graphs_fn(c);
+    return SDD_OK;
+}
+
+// Buffers of a control-variate mode, allocated before any capture.
+sdd_status cv_mode_buffers(sdd_ctx* c, int mode)
+{
+    const size_t nn = (size_t)c->nx * c->ny, cells = (size_t)(c->nx - 1) * (c->ny - 1);
+    const int slices = mode == 2 ? c->cv_model_slices : mode == 3 ? 1 : c->cv_slices;
+    if (mode == 2 || mode == 3) {
+        const size_t n = (size_t)c->nx * c->ny;
+        CU(c, c->cv_w64.alloc(n));
+        CU(c, c->cv_r64.alloc(n));
+        CU(c, c->cv_gw.alloc(n));
+        CU(c, c->cv_nfa.alloc(n));
+        CU(c, c->cv_nfb.alloc(n));
+        CU(c, c->cv_table64.alloc(4 * nn * (size_t)slices));
+        CU(c, c->cvcoef.alloc(4 * cells * (size_t)slices));
+        c->cv_slices = slices;
+        return upload_inst(c);
+    }
+    return SDD_OK;
+}
+
+// The per-estimate part of modes 2 and 3: the table from the current w (model)
+// or the current fields (field gradient), then its cell records.
+sdd_status enqueue_cv_refresh(sdd_ctx* c, int K, cudaStream_t s)
+{
+    if (c->cv_mode == 2) {
+        if (c->cv_slices > K) return fail(c, SDD_EINVAL, "more control-variate slices than sub-steps per step");
+        float tf[kMaxCvSlices];
+        slice_fracs(K, c->cv_slices, tf);
+        CU(c, launch_node_features(c->w.p, c->nx, c->ny, c->cv_w64.p, c->cv_r64.p, c->cv_gw.p, c->cv_nfa.p,
+                                   c->cv_nfb.p, s));
+        CU(c, launch_cv_tabulate(c->cv_theta.p, c->cv_norm.p, c->cv_nfa.p, c->cv_nfb.p, c->nx, c->ny, c->cv_slices,
+                                 tf, c->cv_table64.p, c->sm_count, s));
+        CU(c, launch_cv_cells(c->cv_table64.p, c->cv_slices, c->nx, c->ny, c->cvcoef.p, s));
+    } else if (c->cv_mode == 3) {
+        CU(c, launch_field_grad(c->fld[c->cur][0].p, c->fld[c->cur][1].p, c->nx, c->ny, c->cv_table64.p, s));
+        CU(c, launch_cv_cells(c->cv_table64.p, 1, c->nx, c->ny, c->cvcoef.p, s));
+    }
     return SDD_OK;
 }
 
@@ -1069,6 +1114,7 @@ static sdd_status mc_common(sdd_ctx* c, const sdd_nodes* nodes, const sdd_mc_par
                                p->exit_mode, rec != nullptr);
     if (st != SDD_OK) return st;
     if ((st = prepare(c, c->stream)) != SDD_OK) return st;
+    if ((st = enqueue_cv_refresh(c, K, c->stream)) != SDD_OK) return st;
     RecDev rd{};
     if (rec) {
         rd.steps = rec->steps;
@@ -1116,12 +1162,16 @@ sdd_status sdd_cv_get_table(sdd_ctx* c, double* grad)
     return SDD_OK;
 }
 
-sdd_status sdd_cv_enable(sdd_ctx* c, int32_t on)
+sdd_status sdd_cv_enable(sdd_ctx* c, int32_t mode)
 {
     if (!c) return SDD_EINVAL;
-    if (on && c->cv_slices < 1) return fail(c, SDD_EINVAL, "no control-variate table has been set");
-    if ((on != 0) != c->cv_on) drop_graphs(c);
-    c->cv_on = on != 0;
+    if (mode < 0 || mode > 3) return fail(c, SDD_EINVAL, "control-variate mode must be 0..3");
+    if (mode == 1 && c->cv_slices < 1) return fail(c, SDD_EINVAL, "no control-variate table has been set");
+    if (mode == 2 && !c->cv_model) return fail(c, SDD_EINVAL, "no control-variate model has been trained or set");
+    sdd_status st = cv_mode_buffers(c, mode);
+    if (st != SDD_OK) return st;
+    if (mode != c->cv_mode) drop_graphs(c);
+    c->cv_mode = mode;
     return SDD_OK;
 }
 
@@ -1222,6 +1272,7 @@ sdd_status sdd_cv_train(sdd_ctx* c, const sdd_cv_train_params* p, sdd_cv_train_i
         return st;
     CU(c, cudaEventRecord(ev[2], c->stream));
     c->cv_model = true;
+    c->cv_model_slices = slices;
     c->cv_rows = n;
     c->cv_loss_steps = steps;
     if ((st = tabulate_into_ctx(c, c->cv_theta.p, c->cv_norm.p, slices, p->samples.dt, p->samples.Dt)) != SDD_OK)
@@ -1243,6 +1294,25 @@ sdd_status sdd_cv_train(sdd_ctx* c, const sdd_cv_train_params* p, sdd_cv_train_i
             info->loss_xi = l[0];
             info->loss_eta = l[1];
         }
+    }
+    return SDD_OK;
+}
+
+sdd_status sdd_cv_set_model(sdd_ctx* c, const float* theta, const float* norm, int32_t slices)
+{
+    if (!c || !theta || !norm) return fail(c, SDD_EINVAL, "null argument");
+    if (slices < 1 || slices > kMaxCvSlices) return fail(c, SDD_EINVAL, "slices must be in [1, %d]", kMaxCvSlices);
+    CU(c, c->cv_theta.alloc(2 * (size_t)kMlpStride));
+    CU(c, c->cv_norm.alloc(16));
+    CU(c, cudaMemcpyAsync(c->cv_theta.p, theta, 2 * (size_t)kMlpStride * sizeof(float), cudaMemcpyDeviceToDevice,
+                          c->stream));
+    CU(c, cudaMemcpyAsync(c->cv_norm.p, norm, 2 * kMlpInputs * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    c->cv_model = true;
+    c->cv_model_slices = slices;
+    if (c->cv_mode == 2) {
+        sdd_status st = cv_mode_buffers(c, 2);
+        if (st != SDD_OK) return st;
+        drop_graphs(c);
     }
     return SDD_OK;
 }
@@ -1342,6 +1412,7 @@ static sdd_status capture_step(sdd_ctx* c, const sdd_step_params* p, int K, int 
         if (e0 != cudaSuccess) st = fail(c, SDD_ECUDA, "event: %s", cudaGetErrorString(e0));
     }
     if (st == SDD_OK) st = prepare(c, s);
+    if (st == SDD_OK) st = enqueue_cv_refresh(c, K, s);
     OutDev o{};
     o.mean_xi = c->iface_stats[0].p;
     o.mean_eta = c->iface_stats[1].p;

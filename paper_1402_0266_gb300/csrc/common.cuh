@@ -133,6 +133,7 @@ cudaError_t launch_faces32(const double* faces64, float* faces32, int n, cudaStr
 // Learned control variate (mlp.cu).
 cudaError_t launch_node_features(const float* w, int nx, int ny, double* w64, double* r64, double2* gw, float4* nfa,
                                  float2* nfb, cudaStream_t s);
+cudaError_t launch_field_grad(const double* xi, const double* eta, int nx, int ny, double* table, cudaStream_t s);
 cudaError_t launch_cv_scatter(const double* xs, const double* ys, const double* yxi, const double* yeta,
                               const float4* nfa, int nx, int ny, int k, int K, int M, float* feats, float* targets,
                               cudaStream_t s);

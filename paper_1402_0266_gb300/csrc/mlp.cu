@@ -94,6 +94,25 @@ __global__ void k_node_features(const double* __restrict__ w64, const double* __
     }
 }
 
+// The control variate's model from the fields at t_{n-1} themselves: one
+// slice, (d xi/dx, d xi/dy, d eta/dx, d eta/dy) at every node by the same
+// finite differences. Over a short mesh step the solution's gradient stays
+// close to the previous field's.
+__global__ void k_field_grad(const double* __restrict__ xi, const double* __restrict__ eta, int nx, int ny,
+                             double* __restrict__ table)
+{
+    const long long n = (long long)nx * ny;
+    const double rx = 0.5 * (nx - 1), ry = 0.5 * (ny - 1);
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(k % nx), j = (int)(k / nx);
+        double* o = table + 4 * k;
+        o[0] = fd_x(xi, nx, i, j, rx);
+        o[1] = fd_y(xi, nx, ny, i, j, ry);
+        o[2] = fd_x(eta, nx, i, j, rx);
+        o[3] = fd_y(eta, nx, ny, i, j, ry);
+    }
+}
+
 // ---------------------------------------------------------------- training rows
 
 __device__ __forceinline__ float bilin(const float4* __restrict__ nfa, int nx, int ny, double x, double y, int comp)
@@ -613,6 +632,13 @@ cudaError_t launch_node_features(const float* w, int nx, int ny, double* w64, do
     k_node_w64<<<grid_for(n, 256), 256, 0, s>>>(w, n, w64);
     k_node_r<<<grid_for(n, 256), 256, 0, s>>>(w64, nx, ny, r64, gw);
     k_node_features<<<grid_for(n, 256), 256, 0, s>>>(w64, r64, gw, nx, ny, nfa, nfb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_grad(const double* xi, const double* eta, int nx, int ny, double* table, cudaStream_t s)
+{
+    const long long n = (long long)nx * ny;
+    k_field_grad<<<grid_for(n, 256), 256, 0, s>>>(xi, eta, nx, ny, table);
     return cudaGetLastError();
 }
 

@@ -201,3 +201,84 @@ def test_cv_rejections(sdd):
     with pytest.raises(sdd.SddError) as e:        # 20 slices, 10 sub-steps
         sdd.sdd_interface_mc(ctx, [0.5], [0.5], [10], dt=1e-3, Dt=1e-2)
     assert e.value.status == sdd.SDD_EINVAL
+
+
+def test_field_gradient_mode_matches_oracle(sdd, oracle_mod):
+    from oracle import mlp
+    n = 65
+    w = W.w_front(n, 0.1)
+    X, Y = W.grid(n)
+    xi0 = X + 0.02 * np.sin(np.pi * X) * np.sin(np.pi * Y)
+    eta0 = Y.copy()
+    ctx = _ctx(sdd, w, xi0, eta0)
+    sdd.sdd_cv_enable(ctx, sdd.SDD_CV_FIELDS)
+    xs, ys = W.interface_node_coords(n, n, 2, 2)
+    pick = np.arange(0, xs.size, 5)
+    xs, ys = xs[pick], ys[pick]
+    npaths = np.full(xs.size, 600)
+    kw = dict(dt=1e-4, Dt=1e-2, seed=6, exit_mode=0)
+    g = _np(sdd.sdd_interface_mc_record(ctx, xs, ys, npaths, **kw))
+    T = mlp.field_gradient_table(xi0, eta0)
+    np.testing.assert_allclose(sdd.sdd_cv_get_table(ctx, 1).cpu().numpy(), T, rtol=1e-12, atol=1e-9)
+    o = oracle_mod.interface_mc(oracle_mod.Problem(w, xi0, eta0), xs, ys, npaths, record=True, cv_table=T, **kw)
+    same, rep = PT.assert_records(g, o)
+    PT.assert_nodes(g, o, npaths, same, np.concatenate([[0], np.cumsum(npaths)]))
+
+
+def test_model_mode_tabulates_before_every_estimate(sdd, oracle_mod):
+    # SDD_CV_MODEL rebuilds the table from the context's current w: the same numbers as
+    # tabulating by hand and using the table, before and after w changes
+    n = 65
+    xi0, eta0 = W.identity_fields(n)
+    ctx = _ctx(sdd, W.w_front(n, 0.0), xi0, eta0)
+    info = sdd.sdd_cv_train(ctx, per_horizon=400, dt=1e-3, Dt=1e-2, seed=2, epochs=2, batch=1024, slices=4)
+    theta, norm = sdd.sdd_cv_get_model(ctx)
+    xs, ys = W.interface_node_coords(n, n, 2, 2)
+    npaths = np.full(xs.size, 300)
+    kw = dict(dt=1e-3, Dt=1e-2, seed=8)
+    import torch
+    for t in (0.0, 0.3):
+        sdd.sdd_set_w(ctx, torch.from_numpy(W.w_front(n, t)).cuda())
+        sdd.sdd_cv_enable(ctx, sdd.SDD_CV_MODEL)
+        a = _np(sdd.sdd_interface_mc(ctx, xs, ys, npaths, **kw))
+        sdd.sdd_cv_tabulate(ctx, theta, norm, 4, dt=1e-3, Dt=1e-2)
+        sdd.sdd_cv_enable(ctx, sdd.SDD_CV_TABLE)
+        b = _np(sdd.sdd_interface_mc(ctx, xs, ys, npaths, **kw))
+        for k in ("mean_xi", "mean_eta", "se_xi", "se_eta"):
+            np.testing.assert_array_equal(a[k], b[k])
+
+
+@pytest.mark.parametrize("mode", ["fields", "model"])
+def test_mesh_steps_with_control_variate_match_oracle(sdd, oracle_mod, mode):
+    from oracle import mlp
+    import torch
+    n, sub, dt, Dt, paths = 33, 2, 1e-4, 1e-2, 1500
+    xi0, eta0 = W.identity_fields(n)
+    ctx = _ctx(sdd, W.w_front(n, 0.0), xi0, eta0, sub)
+    if mode == "model":
+        sdd.sdd_cv_train(ctx, per_horizon=100, dt=dt, Dt=Dt, seed=2, epochs=2, batch=1024, slices=4)
+        sdd.sdd_cv_enable(ctx, sdd.SDD_CV_MODEL)
+    else:
+        sdd.sdd_cv_enable(ctx, sdd.SDD_CV_FIELDS)
+    ii, jj = W.interface_nodes(n, n, sub, sub)
+    state = [xi0, eta0]
+    for step in range(3):
+        w = W.w_front(n, step * Dt)
+        sdd.sdd_set_w(ctx, torch.from_numpy(w).cuda())
+        sdd.sdd_step(ctx, dt=dt, Dt=Dt, seed=9, paths_per_node=paths, rtol=1e-13, max_iter=50000)
+        sdd.sdd_sync(ctx)
+        g = _np(sdd.sdd_last_interface_stats(ctx))
+        if mode == "model":
+            T = sdd.sdd_cv_get_table(ctx, 4).cpu().numpy()
+        else:
+            T = mlp.field_gradient_table(*state)
+        new, o = oracle_mod.dd_step(w, state[0], state[1], sub_x=sub, sub_y=sub, dt=dt, Dt=Dt, n_paths=paths, seed=9,
+                                    step_index=step, nodes_ij=(ii, jj), cv_table=T)
+        for f in ("xi", "eta"):
+            d = np.abs(g["mean_" + f] - o["mean_" + f])
+            assert np.all(d <= 3 * o["se_" + f] + 1e-4), (step, f, d.max())
+            assert np.median(d) <= 1e-5, (step, f, np.median(d))
+        gx, ge = (a.cpu().numpy() for a in sdd.sdd_get_fields(ctx))
+        iface_gap = max(np.abs(g["mean_xi"] - o["mean_xi"]).max(), np.abs(g["mean_eta"] - o["mean_eta"]).max())
+        assert max(np.abs(gx - new[0]).max(), np.abs(ge - new[1]).max()) <= iface_gap + 1e-9
+        state = [gx, ge]    # continue from the GPU's fields (the oracle's differ by the MC rounding)

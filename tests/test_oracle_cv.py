@@ -88,3 +88,26 @@ def test_exact_gradient_collapses_the_variance(oracle_mod):
     # and the corrected mean is the closed form up to the method's own bias
     ex, ee = W.heat_exact(xs, ys, Dt)
     assert np.all(np.abs(exact["mean_xi"] - ex) < 2e-3), exact["mean_xi"] - ex
+
+
+def test_field_gradient_model(oracle_mod):
+    # the untrained model: finite-difference gradients of the fields at t_{n-1}
+    from oracle import mlp
+    n = 65
+    X, Y = W.grid(n)
+    xi0 = X + 0.02 * np.sin(np.pi * X) * np.sin(np.pi * Y)
+    eta0 = Y.copy()
+    T = mlp.field_gradient_table(xi0, eta0)
+    assert T.shape == (1, n, n, 4)
+    np.testing.assert_allclose(T[0, ..., 3], 1.0, atol=1e-12)        # d eta / dy of eta = y
+    np.testing.assert_allclose(T[0, ..., 2], 0.0, atol=1e-12)
+    P = oracle_mod.Problem(W.w_front(n, 0.1), xi0, eta0)
+    xs, ys = W.interface_node_coords(n, n, 2, 2)
+    pick = np.arange(0, xs.size, 8)
+    kw = dict(dt=1e-4, Dt=1e-2, seed=3)
+    a = oracle_mod.interface_mc(P, xs[pick], ys[pick], 2000, **kw)
+    b = oracle_mod.interface_mc(P, xs[pick], ys[pick], 2000, cv_table=T, **kw)
+    for f, want in (("xi", 3.0), ("eta", 50.0)):
+        r = (a["se_" + f] / b["se_" + f]) ** 2
+        assert np.median(r) > want, (f, np.median(r))
+        assert np.all(np.abs(a["mean_" + f] - b["mean_" + f]) < 4 * np.hypot(a["se_" + f], b["se_" + f]))
