@@ -52,7 +52,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--paths", type=int, default=None)
-    ap.add_argument("--workload", choices=["front257", "batch64", "ring2049", "heat65"], default="front257")
+    ap.add_argument("--workload", choices=["front257", "batch64", "ring2049", "heat65", "cv65"], default="front257")
+    ap.add_argument("--cv", choices=["off", "fields", "model"], default="off",
+                    help="ring2049: control variate of the timed mesh steps")
     return ap.parse_args()
 
 
@@ -397,6 +399,76 @@ def run_batch64(args, world, rank, local):
                           "path_steps_per_step": steps / args.steps}), flush=True)
 
 
+def run_cv65(args, world, rank, local):
+    """The learned control variate on the w = 1 heat problem (65 x 65, 33 nodes on
+    x = 1/2, dt = 1e-3, Dt = 0.05): train on 1e6 single-path samples of the method,
+    then compare the plain estimator at 1e4 paths per node with the control variate
+    at 2e3 paths per node against a 1e6-path estimate. Value: path-steps per second
+    of plain-estimator work matched at the control variate's error."""
+    import torch
+
+    import paper_1402_0266_gb300 as sdd
+    from paper_1402_0266_gb300 import build as b
+    b.build()
+    torch.cuda.set_device(local)
+    n, dt, Dt = 65, 1e-3, 0.05
+    xi0, eta0 = W.heat65_fields()
+    ctx = sdd.sdd_init(n, n, 2, 1, w=torch.from_numpy(W.w_const(n)).cuda(), xi0=torch.from_numpy(xi0).cuda(),
+                       eta0=torch.from_numpy(eta0).cuda())
+    sdd.sdd_set_boundary(ctx, torch.zeros(4 * n + 4 * n, dtype=torch.float64, device="cuda"))
+    info = sdd.sdd_cv_train(ctx, per_horizon=20000, dt=dt, Dt=Dt, seed=1, epochs=20, batch=4096, lr=3e-3, init_seed=7)
+    xs, ys = W.heat65_nodes()
+    xs, ys = xs[1:32], ys[1:32]
+
+    def run(paths, seed, mode, timed=False):
+        sdd.sdd_cv_enable(ctx, mode)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        o = sdd.sdd_interface_mc(ctx, xs, ys, np.full(xs.size, paths), dt=dt, Dt=Dt, seed=seed)
+        e1.record()
+        torch.cuda.synchronize()
+        return {k: v.cpu().numpy() for k, v in o.items()}, e0.elapsed_time(e1)
+
+    ref, _ = run(10 ** 6, 1000, sdd.SDD_CV_OFF)
+    for k in range(args.warmup):
+        run(10000, 10 + k, sdd.SDD_CV_OFF)
+        run(2000, 20 + k, sdd.SDD_CV_TABLE)
+    ep, ec, tp, tc, sp_, sc = [], [], 0.0, 0.0, 0, 0
+    for r in range(args.steps):
+        a, ta = run(10000, 2000 + r, sdd.SDD_CV_OFF)
+        c, tcv = run(2000, 3000 + r, sdd.SDD_CV_TABLE)
+        ep.append(np.concatenate([a["mean_xi"] - ref["mean_xi"], a["mean_eta"] - ref["mean_eta"]]))
+        ec.append(np.concatenate([c["mean_xi"] - ref["mean_xi"], c["mean_eta"] - ref["mean_eta"]]))
+        tp += ta
+        tc += tcv
+        sp_ += int(a["path_steps"].sum())
+        sc += int(c["path_steps"].sum())
+    rms_p = math.sqrt(np.mean(np.square(ep)))
+    rms_c = math.sqrt(np.mean(np.square(ec)))
+    # plain path-steps needed for the control variate's error, per second of control-variate run
+    equiv = sp_ * (rms_p / rms_c) ** 2
+    if rank == 0:
+        print(json.dumps({
+            "metric": "path-steps/s at equal MC error (plain-estimator work matched by the learned control variate)",
+            "value": equiv / (tc / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tc / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "cv65: w=1 heat problem on 65x65, 31 interior nodes on x=1/2, dt=1e-3, Dt=0.05; "
+                                   "network 5-64-64-1 trained on 1e6 samples (20 epochs, batch 4096); "
+                                   "plain at 1e4 paths vs control variate at 2e3 paths, both against a 1e6-path "
+                                   "estimate; one step = one estimate of each"},
+            "rms_plain_1e4": rms_p, "rms_cv_2e3": rms_c,
+            "path_steps_plain": sp_ / args.steps, "path_steps_cv": sc / args.steps,
+            "path_step_ratio": sp_ / sc, "error_ratio": rms_c / rms_p,
+            "ms_plain_1e4": tp / args.steps, "ms_cv_2e3": tc / args.steps,
+            "speedup_at_equal_error": (tp * (rms_p / rms_c) ** 2) / tc,
+            "training": {k: info[k] for k in ("samples_ms", "train_ms", "tabulate_ms", "rows", "steps", "slices",
+                                              "loss_xi", "loss_eta")},
+        }), flush=True)
+
+
 def run_ring2049(args, world, rank, local):
     """The large ring workload: mesh steps on 2049 x 2049 with 8 x 8 subdomains."""
     import torch
@@ -410,6 +482,12 @@ def run_ring2049(args, world, rank, local):
     paths = args.paths or wl.paths
     ctx = sdd.sdd_init(n, n, wl.sub, wl.sub, w=torch.from_numpy(W.w_ring(n, 0.0)).cuda())
     sp = dict(dt=wl.dt, Dt=wl.Dt, seed=rank, paths_per_node=paths, exit_mode=0, rtol=1e-12, max_iter=40000, tune=1)
+    train = None
+    mode = {"off": sdd.SDD_CV_OFF, "fields": sdd.SDD_CV_FIELDS, "model": sdd.SDD_CV_MODEL}[args.cv]
+    if args.cv == "model":
+        train = sdd.sdd_cv_train(ctx, per_horizon=10000, dt=wl.dt, Dt=wl.Dt, seed=100 + rank, epochs=10,
+                                 batch=4096, lr=3e-3, slices=4, init_seed=7)
+    sdd.sdd_cv_enable(ctx, mode)
     for k in range(args.warmup):
         sdd.sdd_set_w(ctx, torch.from_numpy(W.w_ring(n, k * wl.Dt)).cuda())
         sdd.sdd_step(ctx, **sp)
@@ -434,13 +512,33 @@ def run_ring2049(args, world, rank, local):
     sdd.sdd_sync(ctx)
     ms = sum(times)
     nodes = len(sdd.sdd_interface_nodes(ctx)[0])
+    # variance against the plain estimator on the same state: one estimate each on a sample of the nodes
+    ix, iy = sdd.sdd_interface_nodes(ctx)
+    pick = np.arange(0, len(ix), 16)
+    xs_, ys_ = np.asarray(ix)[pick], np.asarray(iy)[pick]
+    var_ratio = None
+    if mode != sdd.SDD_CV_OFF:
+        sdd.sdd_cv_enable(ctx, sdd.SDD_CV_OFF)
+        a = sdd.sdd_interface_mc(ctx, xs_, ys_, np.full(xs_.size, paths), dt=wl.dt, Dt=wl.Dt, seed=77)
+        sdd.sdd_cv_enable(ctx, mode)
+        c = sdd.sdd_interface_mc(ctx, xs_, ys_, np.full(xs_.size, paths), dt=wl.dt, Dt=wl.Dt, seed=77)
+        r = []
+        for f in ("se_xi", "se_eta"):
+            sa, sc = a[f].cpu().numpy(), c[f].cpu().numpy()
+            ok = sc > 0
+            r.append(float(np.median((sa[ok] / sc[ok]) ** 2)))
+        var_ratio = {"xi": r[0], "eta": r[1]}
     if rank == 0:
         print(json.dumps({"metric": METRIC, "value": steps / (ms / 1e3), "unit": UNIT, "n_gpus": world,
                           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                           "data": "synthetic",
                           "config": {"workload": f"ring2049: {n}x{n}, 8x8 subdomains, {nodes} nodes x {paths} paths, "
-                                                 f"dt={wl.dt}, Dt={wl.Dt}"},
+                                                 f"dt={wl.dt}, Dt={wl.Dt}, control variate {args.cv}"},
+                          "control_variate": args.cv, "variance_ratio_vs_plain": var_ratio,
+                          "equal_error_path_steps_per_s": (None if var_ratio is None else
+                                                           steps / (ms / 1e3) * min(var_ratio.values())),
+                          "training": train,
                           "interface_nodes_per_s": nodes * args.steps / (ms / 1e3),
                           "path_steps_per_step": steps / args.steps, "paths_kernel_ms": statistics.mean(pk),
                           "solve_ms": statistics.mean(sv),
@@ -457,6 +555,12 @@ def main():
     if args.workload == "ring2049" and args.impl == "ours":
         world, rank, local = dist_init()
         run_ring2049(args, world, rank, local)
+        return
+    if args.workload == "cv65" and args.impl == "ours":
+        world, rank, local = dist_init()
+        if args.steps == WL.steps:
+            args.steps = 12
+        run_cv65(args, world, rank, local)
         return
     if args.paths is None:
         args.paths = WL.paths

@@ -188,7 +188,10 @@ sdd_status sdd_interface_mc_record(sdd_ctx* ctx, const sdd_nodes* nodes, const s
  *           the sub-steps j with floor(j * slices / K) = q and is interpolated
  *           bilinearly in space. 1 <= slices <= 128, and an estimate with
  *           more slices than sub-steps K fails with SDD_EINVAL. Copied into
- *           the context (the call waits for it).
+ *           the context (the call waits for it). The estimator reads the node
+ *           values rounded to half precision (nearest even): the model is the
+ *           bilinear interpolation of the rounded values, so one 32-byte
+ *           record per cell and slice serves a sub-step.
  * sdd_cv_enable chooses the model of every later estimate and mesh step of
  * the context (batched calls run without one):
  *   SDD_CV_OFF     the plain estimator;

@@ -96,7 +96,7 @@ struct sdd_ctx {
     DevBuf<double> faces64;
     DevBuf<float> faces32;
     DevBuf<float4> bcoef, fcoef;
-    DevBuf<float4> cvcoef;     // control-variate table (per slice and cell)
+    DevBuf<uint4> cvcoef;      // control-variate table (per slice and cell, half-precision corners)
     int cv_slices = 0;
     int cv_mode = 0;           // 0 off, 1 the table as set, 2 the model re-tabulated per estimate, 3 field gradient
     int cv_model_slices = 0;   // time slices of the model's table
@@ -534,17 +534,19 @@ sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const Out
         for (int q = 0; q <= kMaxCvSlices; ++q)
             a.cv_bound[q] = cv && q <= cv_slices ? (int32_t)(((int64_t)q * K + cv_slices - 1) / cv_slices) : K + 1;
         CU(err, cudaMemsetAsync(P.d_queue.p, 0, sizeof(int), s));
-        const int64_t per_block = P.block / 32;
+        // the control-variate kernel is compiled for at most kCvMaxBlock threads per block
+        const int block = cv ? std::min(P.block, kCvMaxBlock) : P.block;
+        const int64_t per_block = block / 32;
         int grid_max = P.grid;
         if (cv) {
             int dev = 0, sms = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            grid_max = sms * path_kernel_blocks_per_sm(exit_mode, rec != nullptr, P.block, true);
+            grid_max = sms * path_kernel_blocks_per_sm(exit_mode, rec != nullptr, block, true);
         }
         const int grid = (int)std::min<int64_t>(grid_max, std::max<int64_t>(1, (P.ntasks + per_block - 1) / per_block));
         if (ev_a) CU(err, cudaEventRecordWithFlags(ev_a, s, cudaEventRecordExternal));
-        CU(err, launch_paths(a, exit_mode, rec != nullptr, grid, P.block, s, cv));
+        CU(err, launch_paths(a, exit_mode, rec != nullptr, grid, block, s, cv));
         if (ev_b) CU(err, cudaEventRecordWithFlags(ev_b, s, cudaEventRecordExternal));
     }
     FinalArgs f{};
@@ -785,7 +787,7 @@ sdd_status cv_mode_buffers(sdd_ctx* c, int mode);
 sdd_status set_table_from64(sdd_ctx* c, int slices)
 {
     const size_t cells = (size_t)(c->nx - 1) * (c->ny - 1);
-    CU(c, c->cvcoef.alloc(4 * cells * (size_t)slices));
+    CU(c, c->cvcoef.alloc(2 * cells * (size_t)slices));
     CU(c, launch_cv_cells(c->cv_table64.p, slices, c->nx, c->ny, c->cvcoef.p, c->stream));
     c->cv_slices = slices;
     CU(c, cudaStreamSynchronize(c->stream));
@@ -900,7 +902,7 @@ sdd_status cv_mode_buffers(sdd_ctx* c, int mode)
         CU(c, c->cv_nfa.alloc(n));
         CU(c, c->cv_nfb.alloc(n));
         CU(c, c->cv_table64.alloc(4 * nn * (size_t)slices));
-        CU(c, c->cvcoef.alloc(4 * cells * (size_t)slices));
+        CU(c, c->cvcoef.alloc(2 * cells * (size_t)slices));
         c->cv_slices = slices;
         return upload_inst(c);
     }

@@ -14,6 +14,7 @@
 namespace sdd {
 
 constexpr int kMaxCvSlices = 128;  // time slices of a control-variate table
+constexpr int kCvMaxBlock = 256;   // threads per block of the path kernel with a control variate (3 blocks per SM)
 
 // The control variate's network: 5 inputs, two tanh layers of 64, one output;
 // parameters W1 (64 x 5), b1, W2 (64 x 64, [out][in]), b2, w3, b3 in this order.
@@ -33,7 +34,7 @@ struct InstDev {
     float gxmax, gymax;    // largest floats below nx - 1, ny - 1
     uint32_t cell_bias;    // 0x4B000000 * nx (mod 2^32): cell index from the float bits of 2^23 + floor(g)
     int32_t cv_slices;     // slices of the control-variate table (0: none)
-    const float4* cvcoef;  // per slice and cell 4 float4: the xi model's gradient record, then the eta model's
+    const uint4* cvcoef;   // per slice and cell 2 uint4: corner values (half precision) of the xi model's gradient, then the eta model's
 };
 
 // Output arrays of one instance (device pointers; any may be null).
@@ -127,7 +128,7 @@ int path_kernel_blocks_per_sm(int exit_mode, bool record, int block, bool cv = f
 cudaError_t launch_prep_cells(const float* w, const double* xi, const double* eta, int nx, int ny, float4* bcoef,
                               float4* fcoef, int* status, cudaStream_t s);
 cudaError_t launch_winslow_faces(const float* w, int nx, int ny, double* faces64, cudaStream_t s);
-cudaError_t launch_cv_cells(const double* grad, int slices, int nx, int ny, float4* cvcoef, cudaStream_t s);
+cudaError_t launch_cv_cells(const double* grad, int slices, int nx, int ny, uint4* cvcoef, cudaStream_t s);
 cudaError_t launch_faces32(const double* faces64, float* faces32, int n, cudaStream_t s);
 
 // Learned control variate (mlp.cu).

@@ -12,6 +12,8 @@
 //  * the boundary data of Sec. 3: xi = 0 / 1 on x = 0 / 1, eta = 0 / 1 on
 //    y = 0 / 1, and on the other faces the 1D Winslow solution
 //    int_0^s w / int_0^1 w (cumulative trapezoid, double precision).
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 
 namespace sdd {
@@ -84,22 +86,30 @@ __global__ void k_prep_cells(const float* __restrict__ w, const double* __restri
 }
 
 // Control-variate table: node values (slice, j, i, 4) of the two models'
-// gradients -> per slice and cell the interleaved bilinear records of
-// (d/dx, d/dy) of the xi model and of the eta model.
-__global__ void k_cv_cells(const double* __restrict__ g, int slices, int nx, int ny, float4* __restrict__ cv)
+// gradients -> one 32-byte record per slice and cell holding the cell's four
+// corner values in half precision (round to nearest even): the xi model's
+// (d/dx, d/dy) at corners 00, 10, 01, 11, then the eta model's. The model the
+// estimator uses is the bilinear interpolation of these rounded node values
+// (continuous across cells: neighbouring cells hold the same rounded values).
+__global__ void k_cv_cells(const double* __restrict__ g, int slices, int nx, int ny, uint4* __restrict__ cv)
 {
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;
     const int iy = blockIdx.y * blockDim.y + threadIdx.y;
     const int q = blockIdx.z;
     if (ix >= nx - 1 || iy >= ny - 1 || q >= slices) return;
     const double* T = g + (long long)q * nx * ny * 4;
-    const long long n00 = (long long)iy * nx + ix, n10 = n00 + 1, n01 = n00 + nx, n11 = n01 + 1;
+    const long long n00 = (long long)iy * nx + ix;
+    const long long corner[4] = {n00, n00 + 1, n00 + nx, n00 + nx + 1};
     const long long cell = (long long)q * (nx - 1) * (ny - 1) + (long long)iy * (nx - 1) + ix;
-    float4* out = cv + 4 * cell;
-    bilinear_coefs2(T[4 * n00 + 0], T[4 * n10 + 0], T[4 * n01 + 0], T[4 * n11 + 0], T[4 * n00 + 1], T[4 * n10 + 1],
-                    T[4 * n01 + 1], T[4 * n11 + 1], out[0], out[1]);
-    bilinear_coefs2(T[4 * n00 + 2], T[4 * n10 + 2], T[4 * n01 + 2], T[4 * n11 + 2], T[4 * n00 + 3], T[4 * n10 + 3],
-                    T[4 * n01 + 3], T[4 * n11 + 3], out[2], out[3]);
+    uint32_t w[8];
+    for (int f = 0; f < 2; ++f)
+        for (int k = 0; k < 4; ++k) {
+            const double* v = T + 4 * corner[k] + 2 * f;
+            const __half hx = __double2half(v[0]), hy = __double2half(v[1]);
+            w[4 * f + k] = (uint32_t)__half_as_ushort(hx) | ((uint32_t)__half_as_ushort(hy) << 16);
+        }
+    cv[2 * cell + 0] = make_uint4(w[0], w[1], w[2], w[3]);
+    cv[2 * cell + 1] = make_uint4(w[4], w[5], w[6], w[7]);
 }
 
 // Cumulative trapezoid of one line of w, normalised by its total, by one warp:
@@ -172,7 +182,7 @@ cudaError_t launch_prep_cells(const float* w, const double* xi, const double* et
     return cudaGetLastError();
 }
 
-cudaError_t launch_cv_cells(const double* grad, int slices, int nx, int ny, float4* cvcoef, cudaStream_t s)
+cudaError_t launch_cv_cells(const double* grad, int slices, int nx, int ny, uint4* cvcoef, cudaStream_t s)
 {
     const dim3 block(32, 8);
     const dim3 grid((nx - 1 + 31) / 32, (ny - 1 + 7) / 8, slices);

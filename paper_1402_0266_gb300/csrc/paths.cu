@@ -17,6 +17,10 @@
 // compensation (single precision, shifted by the node's start coordinates),
 // then per warp in double precision; the per-node reduction over tasks runs in
 // a fixed order, so results do not depend on scheduling.
+#include <cuda_fp16.h>
+
+#include <cstring>
+
 #include "common.cuh"
 
 namespace sdd {
@@ -157,18 +161,43 @@ __device__ __forceinline__ bool bridge_exit(const InstDev& I, float x, float y, 
     return true;
 }
 
-// Control variate: the two models' gradients at the cell of X_j for slice q,
-// times the sub-step's increment z = sqrt(2 dt) N(0,1)^2, added to the running
-// sums (acc_xi, acc_eta hold the x and y parts separately).
+// 32 bytes through the non-coherent path as eight words.
+__device__ __forceinline__ void load_words(const uint4* p, uint4& lo, uint4& hi)
+{
+    asm("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(lo.x), "=r"(lo.y), "=r"(lo.z), "=r"(lo.w), "=r"(hi.x), "=r"(hi.y), "=r"(hi.z), "=r"(hi.w)
+        : "l"(p));
+}
+
+__device__ __forceinline__ float2 half2_to_float2(uint32_t u)
+{
+    __half2 h;
+    memcpy(&h, &u, sizeof h);
+    return __half22float2(h);
+}
+
+// Bilinear interpolation of four corner values (00, 10, 01, 11) at (s, t):
+// ((1 - s) f00 + s f10) (1 - t) + ((1 - s) f01 + s f11) t, both components.
+__device__ __forceinline__ float2 corners2(const uint4& r, float2 ss, float2 oms, float2 tt, float2 omt)
+{
+    const float2 r0 = __ffma2_rn(ss, half2_to_float2(r.y), __fmul2_rn(oms, half2_to_float2(r.x)));
+    const float2 r1 = __ffma2_rn(ss, half2_to_float2(r.w), __fmul2_rn(oms, half2_to_float2(r.z)));
+    return __ffma2_rn(tt, r1, __fmul2_rn(omt, r0));
+}
+
+// Control variate: the model gradients (xi, eta) at the cell's point, times
+// the sub-step's increment z = sqrt(2 dt) N(0,1)^2, added to the running sums
+// (acc_xi, acc_eta hold the x and y parts separately).
 __device__ __forceinline__ void cv_add(const InstDev& I, const Cell& c, int q, float2 z, float2& acc_xi,
                                        float2& acc_eta)
 {
-    const float4* r = I.cvcoef + 4 * ((size_t)q * (size_t)(I.nx - 1) * (size_t)(I.ny - 1) + c.idx);
-    float4 a0, a1, b0, b1;
-    load_cell(r, a0, a1);
-    load_cell(r + 2, b0, b1);
-    acc_xi = __ffma2_rn(eval2(a0, a1, c.st), z, acc_xi);
-    acc_eta = __ffma2_rn(eval2(b0, b1, c.st), z, acc_eta);
+    const uint4* r = I.cvcoef + 2 * ((size_t)q * (size_t)(I.nx - 1) * (size_t)(I.ny - 1) + c.idx);
+    uint4 gx, ge;
+    load_words(r, gx, ge);
+    const float2 ss = f2(c.st.x, c.st.x), tt = f2(c.st.y, c.st.y);
+    const float2 oms = f2(1.f - c.st.x, 1.f - c.st.x), omt = f2(1.f - c.st.y, 1.f - c.st.y);
+    acc_xi = __ffma2_rn(corners2(gx, ss, oms, tt, omt), z, acc_xi);
+    acc_eta = __ffma2_rn(corners2(ge, ss, oms, tt, omt), z, acc_eta);
 }
 
 struct Acc {
@@ -207,7 +236,7 @@ __device__ __forceinline__ long long warp_sum_ll(long long v)
 // MODE 2: as MODE 0 when K is even (every pair has both sub-steps).
 // CV: subtract the control variate sum_j G(s_j, X_j) . sqrt(2) dW_j from both scores.
 template <int MODE, bool RECORD, bool CV>
-__global__ void __launch_bounds__(512, CV ? 1 : 2) k_paths(const PathArgs a)
+__global__ void __launch_bounds__(CV ? kCvMaxBlock : 512, CV ? 3 : 2) k_paths(const PathArgs a)
 {
     __shared__ int s_group;
     const int lane = threadIdx.x & 31;

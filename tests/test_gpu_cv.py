@@ -41,6 +41,11 @@ def _ctx(sdd, w, xi0, eta0, sub=2, faces=None):
     return ctx
 
 
+def _h(T):
+    """The model the GPU uses: the table's node values rounded to half precision."""
+    return np.asarray(T, dtype=np.float16).astype(np.float64)
+
+
 def _set_table(sdd, ctx, T):
     import torch
     sdd.sdd_cv_set_table(ctx, torch.from_numpy(np.ascontiguousarray(T, np.float64)).cuda())
@@ -96,7 +101,7 @@ def test_cv_records_match_oracle(sdd, oracle_mod, exit_mode, dt, Dt, S):
     kw = dict(dt=dt, Dt=Dt, seed=5, step_index=2, exit_mode=exit_mode)
     g = _np(sdd.sdd_interface_mc_record(ctx, xs, ys, npaths, **kw))
     P = oracle_mod.Problem(w, xi0, eta0)
-    o = oracle_mod.interface_mc(P, xs, ys, npaths, record=True, cv_table=T, **kw)
+    o = oracle_mod.interface_mc(P, xs, ys, npaths, record=True, cv_table=_h(T), **kw)
     plain = oracle_mod.interface_mc(P, xs, ys, npaths, record=True, **kw)
     # the table really enters the scores
     assert np.abs(o["score_xi"] - plain["score_xi"]).max() > 1e-2
@@ -152,7 +157,8 @@ def test_cv_exact_gradient_shrinks_the_error_on_gpu(sdd, oracle_mod):
     # and the same numbers as the oracle's control-variate estimator on a few nodes
     sel = np.flatnonzero(inner)[::8]
     P = oracle_mod.Problem(W.w_const(n), xi0, eta0, faces)
-    o = oracle_mod.interface_mc(P, xs[sel], ys[sel], npaths[sel], cv_table=T, node_ids=sel.astype(np.uint32), **kw)
+    o = oracle_mod.interface_mc(P, xs[sel], ys[sel], npaths[sel], cv_table=_h(T), node_ids=sel.astype(np.uint32),
+                                **kw)
     for f in ("xi", "eta"):
         d = np.abs(cv["mean_" + f][sel] - o["mean_" + f])
         assert np.all(d <= 3 * o["se_" + f] + 1e-4), (f, d)
@@ -172,7 +178,7 @@ def test_cv_mesh_step_matches_oracle(sdd, oracle_mod):
     g = _np(sdd.sdd_last_interface_stats(ctx))
     ii, jj = W.interface_nodes(n, n, sub, sub)
     new, o = oracle_mod.dd_step(w, xi0, eta0, sub_x=sub, sub_y=sub, dt=dt, Dt=Dt, n_paths=paths, seed=9,
-                                step_index=0, nodes_ij=(ii, jj), cv_table=T)
+                                step_index=0, nodes_ij=(ii, jj), cv_table=_h(T))
     for f in ("xi", "eta"):
         d = np.abs(g["mean_" + f] - o["mean_" + f])
         assert np.all(d <= 3 * o["se_" + f] + 1e-4), (f, d.max())
@@ -220,7 +226,7 @@ def test_field_gradient_mode_matches_oracle(sdd, oracle_mod):
     g = _np(sdd.sdd_interface_mc_record(ctx, xs, ys, npaths, **kw))
     T = mlp.field_gradient_table(xi0, eta0)
     np.testing.assert_allclose(sdd.sdd_cv_get_table(ctx, 1).cpu().numpy(), T, rtol=1e-12, atol=1e-9)
-    o = oracle_mod.interface_mc(oracle_mod.Problem(w, xi0, eta0), xs, ys, npaths, record=True, cv_table=T, **kw)
+    o = oracle_mod.interface_mc(oracle_mod.Problem(w, xi0, eta0), xs, ys, npaths, record=True, cv_table=_h(T), **kw)
     same, rep = PT.assert_records(g, o)
     PT.assert_nodes(g, o, npaths, same, np.concatenate([[0], np.cumsum(npaths)]))
 
@@ -273,7 +279,7 @@ def test_mesh_steps_with_control_variate_match_oracle(sdd, oracle_mod, mode):
         else:
             T = mlp.field_gradient_table(*state)
         new, o = oracle_mod.dd_step(w, state[0], state[1], sub_x=sub, sub_y=sub, dt=dt, Dt=Dt, n_paths=paths, seed=9,
-                                    step_index=step, nodes_ij=(ii, jj), cv_table=T)
+                                    step_index=step, nodes_ij=(ii, jj), cv_table=_h(T))
         for f in ("xi", "eta"):
             d = np.abs(g["mean_" + f] - o["mean_" + f])
             assert np.all(d <= 3 * o["se_" + f] + 1e-4), (step, f, d.max())
