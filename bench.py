@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cv", action="store_true", help="skip the control-variate measurement of the default workload")
     ap.add_argument("--paths", type=int, default=None)
     ap.add_argument("--workload", choices=["front257", "batch64", "ring2049", "heat65", "cv65"], default="front257")
     ap.add_argument("--cv", choices=["off", "fields", "model"], default="off",
@@ -317,6 +318,45 @@ def run_ours(args, world, rank, local):
         e2e = {"value": e2e_tot / e2e_max, "unit": UNIT, "h2d_bytes_per_step": n * n * 4,
                "d2h_bytes_per_step": nn * 48}
 
+    # the same mesh steps with the control variate of the previous fields' gradient:
+    # throughput, and the variance against the plain estimator on the same state
+    equal_error = None
+    if not args.no_cv:
+        reset()
+        sdd.sdd_cv_enable(ctx, sdd.SDD_CV_FIELDS)
+        kc = min(K, 10)
+        cv_ms, cv_steps, cv_pk = 0.0, 0, []
+        for k in range(kc):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sdd.sdd_set_w(ctx, w_all[k])
+            sdd.sdd_step(ctx, **sp)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            cv_ms += e0.elapsed_time(e1)
+            cv_steps += int(sdd.sdd_last_interface_stats(ctx)["path_steps"].sum())
+            cv_pk.append(sdd.sdd_last_step_info(ctx)["paths_ms"])
+        ix, iy = sdd.sdd_interface_nodes(ctx)
+        est = {}
+        for name, mode in (("plain", sdd.SDD_CV_OFF), ("cv", sdd.SDD_CV_FIELDS)):
+            sdd.sdd_cv_enable(ctx, mode)
+            o = sdd.sdd_interface_mc(ctx, ix, iy, np.full(len(ix), args.paths), dt=WL.dt, Dt=WL.Dt, seed=seed + 99)
+            est[name] = {k2: v.cpu().numpy() for k2, v in o.items()}
+        sdd.sdd_cv_enable(ctx, sdd.SDD_CV_OFF)
+        ratio = {}
+        for f in ("xi", "eta"):
+            a, c = est["plain"]["se_" + f], est["cv"]["se_" + f]
+            ok = c > 0
+            ratio[f] = float(np.median((a[ok] / c[ok]) ** 2))
+        cv_value = cv_steps / (cv_ms / 1e3)
+        equal_error = {"control_variate": "gradient of the fields at t_{n-1} (no training)", "steps": kc,
+                       "path_steps_per_s": cv_value, "paths_kernel_ms": statistics.mean(cv_pk),
+                       "variance_ratio_vs_plain": ratio,
+                       "path_steps_per_s_at_equal_error": cv_value * min(ratio.values()),
+                       "interface_nodes_per_s_at_equal_error": nodes * kc / (cv_ms / 1e3) * min(ratio.values())}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         steps_c, el_c, calls, nnc = oracle_sample(15.0, None, 40)
@@ -344,6 +384,7 @@ def run_ours(args, world, rank, local):
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_paths", "ops_per_path_step": ALG_OPS_PER_PATH_STEP,
                          "peak_basis": f"{props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz"},
+            "equal_error": equal_error,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": kernel_nodes * K,
