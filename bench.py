@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-cv", action="store_true", help="skip the control-variate measurement of the default workload")
     ap.add_argument("--paths", type=int, default=None)
-    ap.add_argument("--workload", choices=["front257", "batch64", "ring2049", "heat65", "cv65"], default="front257")
+    ap.add_argument("--workload", choices=["front257", "batch64", "ring2049", "heat65", "cv65", "ring41"],
+                    default="front257")
     ap.add_argument("--cv", choices=["off", "fields", "model"], default="off",
                     help="ring2049: control variate of the timed mesh steps")
     return ap.parse_args()
@@ -510,6 +511,63 @@ def run_cv65(args, world, rank, local):
         }), flush=True)
 
 
+def run_ring41(args, world, rank, local):
+    """The paper's Sec. 5 experiment: w = 1 / rho (moving ring), 41 x 41, four subdomains, Dt = 1e-3 up to
+    t = 0.75 (750 mesh steps) with 20 sub-steps and 1e4 paths per interface node, from the uniform mesh.
+    One step = one mesh step (w of the step uploaded from the host, then the graph of the step)."""
+    import torch
+
+    import paper_1402_0266_gb300 as sdd
+    from paper_1402_0266_gb300 import build as b
+    b.build()
+    torch.cuda.set_device(local)
+    wl = W.RING41
+    n, Dt = wl.n, wl.Dt
+    steps = args.steps if args.steps != WL.steps else wl.steps
+    xi0, eta0 = W.identity_fields(n)
+    w_all = torch.from_numpy(np.stack([W.w_paper_ring(n, k * Dt) for k in range(steps)])).cuda()
+    ctx = sdd.sdd_init(n, n, wl.sub, wl.sub, w=w_all[0], xi0=torch.from_numpy(xi0).cuda(),
+                       eta0=torch.from_numpy(eta0).cuda())
+    sp = dict(dt=wl.dt, Dt=Dt, seed=rank, paths_per_node=wl.paths, rtol=1e-12, max_iter=20000)
+    for k in range(args.warmup):
+        sdd.sdd_set_w(ctx, w_all[k % steps])
+        sdd.sdd_step(ctx, **sp)
+    sdd.sdd_set_fields(ctx, torch.from_numpy(xi0).cuda(), torch.from_numpy(eta0).cuda())
+    sdd.sdd_set_step_index(ctx, 0)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    counts = torch.zeros(steps, dtype=torch.int64, device="cuda")
+    e0.record()
+    for k in range(steps):
+        sdd.sdd_set_w(ctx, w_all[k])
+        sdd.sdd_step(ctx, **sp)
+        counts[k] = sdd.sdd_last_interface_stats(ctx)["path_steps"].sum()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    xi, eta = (a.cpu().numpy() for a in sdd.sdd_get_fields(ctx))
+    p = np.stack([xi, eta], axis=-1)
+    quad = [p[:-1, :-1], p[:-1, 1:], p[1:, 1:], p[1:, :-1]]
+    folded = np.zeros(xi[:-1, :-1].shape, dtype=bool)
+    for k in range(4):
+        e1_, e2_ = quad[k] - quad[k - 1], quad[(k + 1) % 4] - quad[k]
+        folded |= (e1_[..., 0] * e2_[..., 1] - e1_[..., 1] * e2_[..., 0]) <= 0
+    tot = int(counts.sum().item())
+    nodes = len(sdd.sdd_interface_nodes(ctx)[0])
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": tot / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"ring41 (Sec. 5): w = 1/rho, {n}x{n}, 2x2 subdomains, {nodes} interface nodes x "
+                                   f"{wl.paths} paths, dt={wl.dt}, Dt={Dt}, {steps} mesh steps from the uniform mesh"},
+            "interface_nodes_per_s": nodes * steps / (ms / 1e3), "path_steps_per_step": tot / steps,
+            "folded_cells_at_end": int(folded.sum()),
+            "max_mesh_displacement": float(max(np.abs(xi - W.grid(n)[0]).max(), np.abs(eta - W.grid(n)[1]).max())),
+        }), flush=True)
+
+
 def run_ring2049(args, world, rank, local):
     """The large ring workload: mesh steps on 2049 x 2049 with 8 x 8 subdomains."""
     import torch
@@ -596,6 +654,10 @@ def main():
     if args.workload == "ring2049" and args.impl == "ours":
         world, rank, local = dist_init()
         run_ring2049(args, world, rank, local)
+        return
+    if args.workload == "ring41" and args.impl == "ours":
+        world, rank, local = dist_init()
+        run_ring41(args, world, rank, local)
         return
     if args.workload == "cv65" and args.impl == "ours":
         world, rank, local = dist_init()
