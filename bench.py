@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--paths", type=int, default=None)
     ap.add_argument("--workload", choices=["front257", "batch64", "ring2049", "heat65", "cv65", "ring41"],
                     default="front257")
+    ap.add_argument("--solver", choices=["auto", "jacobi", "mg"], default="auto",
+                    help="subdomain solver of the mesh steps")
     ap.add_argument("--cv", choices=["off", "fields", "model"], default="off",
                     help="ring2049: control variate of the timed mesh steps")
     return ap.parse_args()
@@ -232,6 +234,7 @@ def run_ours(args, world, rank, local):
     nsteps = max(K, Wm)
     w_all = torch.from_numpy(np.stack([W.w_front(n, k * WL.Dt) for k in range(nsteps)])).to(dev)
     ctx = sdd.sdd_init(n, n, WL.sub, WL.sub, w=w_all[0], xi0=xi0_d, eta0=eta0_d)
+    sdd.sdd_set_solver(ctx, {"auto": 0, "jacobi": 1, "mg": 2}[args.solver])
     sp = dict(dt=WL.dt, Dt=WL.Dt, seed=seed, paths_per_node=args.paths, exit_mode=0, rtol=1e-12, max_iter=20000,
               tune=1)
 
@@ -580,6 +583,7 @@ def run_ring2049(args, world, rank, local):
     n = wl.n
     paths = args.paths or wl.paths
     ctx = sdd.sdd_init(n, n, wl.sub, wl.sub, w=torch.from_numpy(W.w_ring(n, 0.0)).cuda())
+    sdd.sdd_set_solver(ctx, {"auto": 0, "jacobi": 1, "mg": 2}[args.solver])
     sp = dict(dt=wl.dt, Dt=wl.Dt, seed=rank, paths_per_node=paths, exit_mode=0, rtol=1e-12, max_iter=40000, tune=1)
     train = None
     mode = {"off": sdd.SDD_CV_OFF, "fields": sdd.SDD_CV_FIELDS, "model": sdd.SDD_CV_MODEL}[args.cv]

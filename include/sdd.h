@@ -383,6 +383,26 @@ sdd_status sdd_subdomain_solve(sdd_ctx* ctx, double Dt, const double* iface_xi, 
                                double rtol, int32_t max_iter, double* xi_out, double* eta_out,
                                int32_t* iters_out);
 
+/* The solver of the subdomain systems (sdd_subdomain_solve and sdd_step).
+ * The paper uses LU (Sec. 4); both GPU solvers are conjugate gradients on the
+ * same symmetric system, refined in double precision to rtol:
+ *   SDD_SOLVER_JACOBI  Jacobi preconditioner; one thread-block cluster per
+ *                      subdomain, register-resident when the subdomain fits;
+ *   SDD_SOLVER_MG      a geometric multigrid V-cycle as preconditioner
+ *                      (available when every subdomain has the same odd
+ *                      sizes that halve, (m - 1) / 2, down to a box of at
+ *                      most 64 unknowns; else SDD_EINVAL);
+ *   SDD_SOLVER_AUTO    multigrid where it is available and the subdomains are
+ *                      too large for the register-resident Jacobi kernel.
+ * With multigrid, max_iter caps the inner iterations (at most 5 per
+ * refinement sweep, at most 6 sweeps). sdd_solver_in_use returns the solver
+ * the next solve will use (1 Jacobi, 2 multigrid). */
+#define SDD_SOLVER_AUTO 0
+#define SDD_SOLVER_JACOBI 1
+#define SDD_SOLVER_MG 2
+sdd_status sdd_set_solver(sdd_ctx* ctx, int32_t solver);
+int32_t sdd_solver_in_use(const sdd_ctx* ctx);
+
 /* One mesh step t_{n-1} -> t_n (Sec. 4): the interface estimate at every
  * interface node with paths_per_node paths, the subdomain solves with those
  * values, then xi, eta advance and the step counter n (the Philox counter's

@@ -37,7 +37,10 @@ EXPORTS = [
     "sdd_batch_destroy", "sdd_autotune", "sdd_batch_autotune", "sdd_cv_set_table", "sdd_cv_enable",
     "sdd_mlp_init", "sdd_cv_samples", "sdd_mlp_norm", "sdd_mlp_grad", "sdd_mlp_train", "sdd_cv_tabulate",
     "sdd_cv_train", "sdd_cv_get_model", "sdd_cv_losses", "sdd_cv_get_table", "sdd_cv_set_model",
+    "sdd_set_solver", "sdd_solver_in_use",
 ]
+
+SDD_SOLVER_AUTO, SDD_SOLVER_JACOBI, SDD_SOLVER_MG = range(3)
 
 SDD_CV_OFF, SDD_CV_TABLE, SDD_CV_MODEL, SDD_CV_FIELDS = range(4)
 
@@ -179,6 +182,8 @@ def lib():
                 "sdd_cv_losses": [vp, vp, i64],
                 "sdd_cv_get_table": [vp, vp],
                 "sdd_cv_set_model": [vp, vp, vp, i32],
+                "sdd_set_solver": [vp, i32],
+                "sdd_solver_in_use": [vp],
                 "sdd_batch_autotune": [vp, ctypes.POINTER(_Nodes), ctypes.POINTER(_McParams), ctypes.POINTER(_Shape)],
             }
             for name, args in sig.items():
@@ -720,3 +725,11 @@ def sdd_cv_set_model(ctx: Ctx, theta, norm, slices: int):
     _f32(theta, 2 * MLP_STRIDE, "theta")
     _f32(norm, 2 * MLP_INPUTS, "norm")
     ctx._check(lib().sdd_cv_set_model(ctx.handle, _ptr(theta), _ptr(norm), slices))
+
+
+def sdd_set_solver(ctx: Ctx, solver: int):
+    ctx._check(lib().sdd_set_solver(ctx.handle, int(solver)))
+
+
+def sdd_solver_in_use(ctx: Ctx) -> int:
+    return int(lib().sdd_solver_in_use(ctx.handle))

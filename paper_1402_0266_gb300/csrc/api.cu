@@ -133,6 +133,15 @@ struct sdd_ctx {
     int solve_cluster = 1, solve_upt = 0, solve_rows_max = 0, solve_mx_max = 0;
     DevBuf<SolveSys> d_systems;
     DevBuf<int32_t> d_iters;
+    // multigrid-preconditioned solver (every subdomain the same size)
+    bool mg_ok = false;
+    MgArgs mg{};
+    int solver = 0;                 // 0 automatic, 1 Jacobi-PCG, 2 multigrid-PCG
+    size_t solve_nsys_used = 0;     // systems of the last enqueued solve (entries of d_iters)
+    DevBuf<SolveSys> mg_sys;
+    DevBuf<float> mg_lv[8], mg_kv[6], mg_part, mg_rz, mg_rr0;
+    DevBuf<double> mg_part64, mg_stop2;
+    DevBuf<int32_t> mg_flags;
 
     // step graph (one per parity of the current field buffer)
     GraphSlot graph[2];
@@ -654,7 +663,33 @@ sdd_status setup_solver(sdd_ctx* c)
     if (!c->systems.empty())
         CU(c, cudaMemcpy(c->d_systems.p, c->systems.data(), c->systems.size() * sizeof(SolveSys),
                          cudaMemcpyHostToDevice));
-    CU(c, c->d_iters.alloc(std::max<size_t>(c->systems.size(), 1)));
+    CU(c, c->d_iters.alloc(std::max<size_t>(std::max(c->systems.size(), subs.size()), 1)));
+
+    // multigrid: every subdomain the same odd sizes, coarsening down to a small box
+    c->mg_ok = false;
+    bool same = !subs.empty();
+    for (const SolveSys& S : subs)
+        same = same && (S.i1 - S.i0) == (subs[0].i1 - subs[0].i0) && (S.j1 - S.j0) == (subs[0].j1 - subs[0].j0);
+    MgArgs m{};
+    if (same && mg_levels(subs[0].i1 - subs[0].i0, subs[0].j1 - subs[0].j0, m)) {
+        const long long total = mg_layout(m, (int)subs.size());
+        const long long P0 = (long long)(m.mx[0] + 2) * (m.my[0] + 2) * (long long)subs.size();
+        for (auto& b : c->mg_lv) CU(c, b.alloc((size_t)total));
+        for (auto& b : c->mg_kv) CU(c, b.alloc((size_t)P0));
+        const size_t ns = subs.size();
+        CU(c, c->mg_part.alloc(ns * m.B0 * 4));
+        CU(c, c->mg_part64.alloc(ns * m.B0 * 4));
+        CU(c, c->mg_stop2.alloc(2 * ns));
+        CU(c, c->mg_rz.alloc(4 * ns));
+        CU(c, c->mg_rr0.alloc(2 * ns));
+        CU(c, c->mg_flags.alloc(6 * ns));
+        CU(c, cudaMemset(c->mg_rz.p, 0, 4 * ns * sizeof(float)));
+        CU(c, cudaMemset(c->mg_flags.p, 0, 6 * ns * sizeof(int32_t)));
+        CU(c, c->mg_sys.alloc(ns));
+        CU(c, cudaMemcpy(c->mg_sys.p, subs.data(), ns * sizeof(SolveSys), cudaMemcpyHostToDevice));
+        c->mg = m;
+        c->mg_ok = true;
+    }
     return SDD_OK;
 }
 
@@ -720,7 +755,62 @@ sdd_status enqueue_solve(sdd_ctx* c, double Dt, const double* ix, const double* 
     a.inner_tol = 1e-4f;
     a.iters = c->d_iters.p;
     a.status = c->d_status.p;
+    const bool use_mg = c->mg_ok && (c->solver == 2 || (c->solver == 0 && c->solve_upt == 0));
+    if (use_mg) {
+        MgArgs m = c->mg;
+        m.nx = c->nx;
+        m.ny = c->ny;
+        m.cx = c->cx.p;
+        m.cy = c->cy.p;
+        m.dg = c->dg.p;
+        m.rhs0 = c->rhs0.p;
+        m.cxf = c->cxf.p;
+        m.cyf = c->cyf.p;
+        m.dgf = c->dgf.p;
+        m.w = c->w.p;
+        m.Dt = Dt;
+        m.x[0] = xo;
+        m.x[1] = eo;
+        m.sys = c->mg_sys.p;
+        m.D = c->mg_lv[0].p;
+        m.CX = c->mg_lv[1].p;
+        m.CY = c->mg_lv[2].p;
+        m.MS = c->mg_lv[3].p;
+        m.U[0] = c->mg_lv[4].p;
+        m.U[1] = c->mg_lv[5].p;
+        m.F[0] = c->mg_lv[6].p;
+        m.F[1] = c->mg_lv[7].p;
+        for (int f = 0; f < 2; ++f) {
+            m.Pv[f] = c->mg_kv[f].p;
+            m.Qv[f] = c->mg_kv[2 + f].p;
+            m.Cv[f] = c->mg_kv[4 + f].p;
+        }
+        const size_t ns = (size_t)m.nsys;
+        m.part = c->mg_part.p;
+        m.part64 = c->mg_part64.p;
+        m.stop2 = c->mg_stop2.p;
+        m.rz = c->mg_rz.p;
+        m.rr0 = c->mg_rr0.p;
+        m.act_o = c->mg_flags.p;
+        m.act_i = c->mg_flags.p + 2 * ns;
+        m.iters = c->mg_flags.p + 4 * ns;
+        m.sys_iters = c->d_iters.p;
+        m.status = c->d_status.p;
+        // inner iterations per refinement sweep and sweeps: 5 x 6 at most, within max_iter
+        m.inner = std::max(1, std::min(5, max_iter));
+        m.outer = std::max(1, std::min(6, max_iter / m.inner));
+        m.nu = 2;
+        m.coarse_sweeps = 20;
+        m.max_iter = max_iter;
+        m.rtol = rtol;
+        m.inner_tol = 1e-5f;
+        CU(c, launch_mg_setup(m, s));
+        CU(c, launch_mg_solve(m, s));
+        c->solve_nsys_used = ns;
+        return SDD_OK;
+    }
     CU(c, launch_pcg(a, c->solve_upt, c->solve_rows_max, c->solve_mx_max, s));
+    c->solve_nsys_used = c->systems.size();
     return SDD_OK;
 }
 
@@ -1142,6 +1232,23 @@ sdd_status sdd_interface_mc_record(sdd_ctx* c, const sdd_nodes* nodes, const sdd
     return mc_common(c, nodes, p, out, rec);
 }
 
+sdd_status sdd_set_solver(sdd_ctx* c, int32_t solver)
+{
+    if (!c) return SDD_EINVAL;
+    if (solver < 0 || solver > 2) return fail(c, SDD_EINVAL, "solver must be 0, 1 or 2");
+    if (solver == 2 && !c->mg_ok)
+        return fail(c, SDD_EINVAL, "multigrid needs subdomains of one size, odd, coarsening to at most 64 unknowns");
+    if (solver != c->solver) drop_graphs(c);
+    c->solver = solver;
+    return SDD_OK;
+}
+
+int32_t sdd_solver_in_use(const sdd_ctx* c)
+{
+    if (!c) return -1;
+    return (c->mg_ok && (c->solver == 2 || (c->solver == 0 && c->solve_upt == 0))) ? 2 : 1;
+}
+
 sdd_status sdd_cv_set_table(sdd_ctx* c, const double* grad, int32_t slices)
 {
     if (!c || !grad) return fail(c, SDD_EINVAL, "null argument");
@@ -1383,12 +1490,12 @@ sdd_status sdd_subdomain_solve(sdd_ctx* c, double Dt, const double* iface_xi, co
     if ((st = enqueue_solve(c, Dt, iface_xi, iface_eta, rtol, max_iter, xi_out, eta_out, c->stream)) != SDD_OK)
         return st;
     if (iters_out) {
-        std::vector<int32_t> it(std::max<size_t>(c->systems.size(), 1), 0);
-        CU(c, cudaMemcpyAsync(it.data(), c->d_iters.p, c->systems.size() * sizeof(int32_t), cudaMemcpyDeviceToHost,
-                              c->stream));
+        const size_t ns = c->solve_nsys_used;
+        std::vector<int32_t> it(std::max<size_t>(ns, 1), 0);
+        CU(c, cudaMemcpyAsync(it.data(), c->d_iters.p, ns * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
         CU(c, cudaStreamSynchronize(c->stream));
         int32_t mx = 0;
-        for (size_t k = 0; k < c->systems.size(); ++k) mx = std::max(mx, it[k]);
+        for (size_t k = 0; k < ns; ++k) mx = std::max(mx, it[k]);
         *iters_out = mx;
         if (mx > max_iter) return fail(c, SDD_ENOCONV, "subdomain solve did not reach rtol in max_iter iterations");
     }

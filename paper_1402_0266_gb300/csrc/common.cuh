@@ -185,6 +185,59 @@ struct SolveArgs {
     int* status;
 };
 
+// Multigrid-preconditioned solves (mg.cu): every subdomain a system of the same
+// mx x my unknowns, both fields together.
+constexpr int kMgMaxLevels = 10;
+struct MgArgs {
+    // grid data (as SolveArgs)
+    int32_t nx, ny;
+    const double* cx;
+    const double* cy;
+    const double* dg;
+    const double* rhs0;
+    const float* cxf;
+    const float* cyf;
+    const float* dgf;
+    const float* w;
+    double Dt;
+    double* x[2];
+    const SolveSys* sys;     // subdomain boxes
+    int32_t nsys;
+    // levels: interior sizes, first element of each level in the level arrays
+    int32_t levels, tail;    // number of levels; first level handled inside one block per system
+    int32_t mx[kMgMaxLevels], my[kMgMaxLevels];
+    long long off[kMgMaxLevels];
+    int32_t B0;              // blocks per system for level-0 vectors (partial sums)
+    // level arrays (all levels, padded boxes with a zero frame)
+    float* D;
+    float* CX;               // coefficient between a node and its east neighbour
+    float* CY;               // ... and its north neighbour
+    float* MS;               // mass term 1 / (w Dt)
+    float* U[2];             // V-cycle iterate (level 0: the preconditioned residual z)
+    float* F[2];             // V-cycle right-hand side (level 0: the residual r)
+    // level-0 Krylov vectors: search direction, product, correction
+    float* Pv[2];
+    float* Qv[2];
+    float* Cv[2];
+    float* part;             // [nsys][B0][4] single-precision partial sums
+    double* part64;          // [nsys][B0][4] double-precision partial sums
+    double* stop2;           // [nsys][2]
+    float* rz;               // [nsys][2][2] (r, z) by parity
+    float* rr0;              // [nsys][2]
+    int32_t* act_o;          // [nsys][2] field still short of rtol
+    int32_t* act_i;          // [nsys][2] inner iteration still running
+    int32_t* iters;          // [nsys][2]
+    int32_t* sys_iters;      // [nsys] inner iterations of the system (max_iter + 1: not converged)
+    int* status;
+    int32_t outer, inner, nu, coarse_sweeps, max_iter;
+    double rtol;
+    float inner_tol;
+};
+bool mg_levels(int mx, int my, MgArgs& a);
+long long mg_layout(MgArgs& a, int nsys);
+cudaError_t launch_mg_setup(const MgArgs& a, cudaStream_t s);
+cudaError_t launch_mg_solve(const MgArgs& a, cudaStream_t s);
+
 cudaError_t launch_solve_setup(const float* w, const double* prev_xi, const double* prev_eta, int nx, int ny,
                                double Dt, double* cx, double* cy, double* dg, double* rhs0, float* cxf, float* cyf,
                                float* dgf, float* dinvf, cudaStream_t s);
