@@ -314,22 +314,37 @@ def boundary_grid(faces, nx: int, ny: int, field: int, inner):
 
 def dd_step(w, xi, eta, *, sub_x: int, sub_y: int, dt: float, Dt: float, n_paths: int, seed: int,
             step_index: int, nodes_ij, exit_mode: int = 0, faces=None, threads=None, node_word0: int = 0,
-            cv_table=None):
+            cv_table=None, keypoints: bool = False):
     """One mesh step t_{n-1} -> t_n of the method (Sec. 4): the interface
     estimate at the nodes nodes_ij = (i, j) (their position is their node index
     in the random stream), then the implicit subdomain solves by LU with those
     values and the face data as Dirichlet data. node_word0 offsets the node
     word of the random stream (instances evaluated together number their nodes
     in sequence); cv_table, if given, is the control-variate model of
-    interface_mc. Returns ([xi_n, eta_n], stats)."""
+    interface_mc. keypoints: estimate only at the key points of Sec. 4 and fill
+    the rest of each interface line by PCHIP (oracle.keypoints; nodes_ij must
+    then be the whole interface list). Returns ([xi_n, eta_n], stats)."""
     from . import solver
     P = Problem(w, xi, eta, faces)
     ii, jj = (np.asarray(a) for a in nodes_ij)
     xs = ii / (P.nx - 1)
     ys = jj / (P.ny - 1)
-    r = interface_mc(P, xs, ys, n_paths, dt=dt, Dt=Dt, seed=seed, exit_mode=exit_mode, step_index=step_index,
-                     threads=threads, node_ids=np.arange(xs.size, dtype=np.uint32) + np.uint32(node_word0),
-                     cv_table=cv_table)
+    ids = np.arange(xs.size, dtype=np.uint32) + np.uint32(node_word0)
+    if keypoints:
+        from . import keypoints as kp
+        mask = kp.key_mask(P.w, sub_x, sub_y)
+        assert mask.size == xs.size
+        rk = interface_mc(P, xs[mask], ys[mask], n_paths, dt=dt, Dt=Dt, seed=seed, exit_mode=exit_mode,
+                          step_index=step_index, threads=threads, node_ids=ids[mask], cv_table=cv_table)
+        r = {k: np.zeros(xs.size, dtype=v.dtype) for k, v in rk.items() if np.ndim(v) == 1 and len(v) == mask.sum()}
+        for k in r:
+            r[k][mask] = rk[k]
+        r["mean_xi"], r["mean_eta"] = kp.pchip_fill(r["mean_xi"], r["mean_eta"], mask, P.faces, P.nx, P.ny, sub_x,
+                                                    sub_y)
+        r["key"] = mask
+    else:
+        r = interface_mc(P, xs, ys, n_paths, dt=dt, Dt=Dt, seed=seed, exit_mode=exit_mode, step_index=step_index,
+                         threads=threads, node_ids=ids, cv_table=cv_table)
     bx = boundary_grid(P.faces, P.nx, P.ny, 0, P.xi0)
     be = boundary_grid(P.faces, P.nx, P.ny, 1, P.eta0)
     bx[jj, ii] = r["mean_xi"]

@@ -97,7 +97,8 @@ def w_smooth_random(n: int, seed: int, modes: int = 3, amp: float = 0.4):
 
 def interface_lines(n_nodes: int, n_sub: int):
     """Grid indices of the interface lines splitting n_nodes nodes into n_sub parts."""
-    return [int(round(k * (n_nodes - 1) / n_sub)) for k in range(1, n_sub)]
+    # nearest index, halves rounded up
+    return [int(math.floor(k * (n_nodes - 1) / n_sub + 0.5)) for k in range(1, n_sub)]
 
 
 def interface_nodes(nx: int, ny: int, sub_x: int, sub_y: int):
