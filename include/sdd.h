@@ -383,6 +383,26 @@ sdd_status sdd_subdomain_solve(sdd_ctx* ctx, double Dt, const double* iface_xi, 
                                double rtol, int32_t max_iter, double* xi_out, double* eta_out,
                                int32_t* iters_out);
 
+/* Key points (Sec. 4) and interface fill (Sec. 5). With key points on, each
+ * mesh step of sdd_step estimates only at the key points of the interface
+ * lines and fills the other interface nodes, line by line, by monotone PCHIP
+ * interpolation (Fritsch-Carlson, Fritsch-Butland derivatives) through the
+ * line's two boundary values (face data) and the key points' estimates; the
+ * filled nodes report a standard error of 0 and no path steps. Key points of
+ * a line (rho = 1 / w at its nodes t = 0 .. n - 1, t = 0, n - 1 on the
+ * boundary): the positions t in 2 .. n - 3 where D1(t) = rho(t+1) - rho(t-1)
+ * or D2(t) = (rho(t+1) - rho(t)) - (rho(t) - rho(t-1)) (computed in double
+ * precision for t = 1 .. n - 2) has a local extremum (p(t) > p(t-1) and
+ * p(t) >= p(t+1), or the mirror) of size |p(t)| >= max |p| / 100, every
+ * crossing of a vertical and a horizontal line, and, with spacing > 0, every
+ * position t with t mod spacing = 0 (the mesh also moves where rho is flat
+ * along a line; 0 keeps the extrema alone).
+ * sdd_keypoint_mask writes the mask of the context's current w (DEVICE, one
+ * byte per interface node in the order of sdd_interface_nodes) on the
+ * context's stream. */
+sdd_status sdd_set_keypoints(sdd_ctx* ctx, int32_t on, int32_t spacing);
+sdd_status sdd_keypoint_mask(sdd_ctx* ctx, uint8_t* mask);
+
 /* The solver of the subdomain systems (sdd_subdomain_solve and sdd_step).
  * The paper uses LU (Sec. 4); both GPU solvers are conjugate gradients on the
  * same symmetric system, refined in double precision to rtol:

@@ -314,7 +314,7 @@ def boundary_grid(faces, nx: int, ny: int, field: int, inner):
 
 def dd_step(w, xi, eta, *, sub_x: int, sub_y: int, dt: float, Dt: float, n_paths: int, seed: int,
             step_index: int, nodes_ij, exit_mode: int = 0, faces=None, threads=None, node_word0: int = 0,
-            cv_table=None, keypoints: bool = False):
+            cv_table=None, keypoints: bool = False, key_spacing: int = 0):
     """One mesh step t_{n-1} -> t_n of the method (Sec. 4): the interface
     estimate at the nodes nodes_ij = (i, j) (their position is their node index
     in the random stream), then the implicit subdomain solves by LU with those
@@ -323,7 +323,8 @@ def dd_step(w, xi, eta, *, sub_x: int, sub_y: int, dt: float, Dt: float, n_paths
     in sequence); cv_table, if given, is the control-variate model of
     interface_mc. keypoints: estimate only at the key points of Sec. 4 and fill
     the rest of each interface line by PCHIP (oracle.keypoints; nodes_ij must
-    then be the whole interface list). Returns ([xi_n, eta_n], stats)."""
+    then be the whole interface list; key_spacing adds every key_spacing-th
+    position of each line). Returns ([xi_n, eta_n], stats)."""
     from . import solver
     P = Problem(w, xi, eta, faces)
     ii, jj = (np.asarray(a) for a in nodes_ij)
@@ -332,7 +333,7 @@ def dd_step(w, xi, eta, *, sub_x: int, sub_y: int, dt: float, Dt: float, n_paths
     ids = np.arange(xs.size, dtype=np.uint32) + np.uint32(node_word0)
     if keypoints:
         from . import keypoints as kp
-        mask = kp.key_mask(P.w, sub_x, sub_y)
+        mask = kp.key_mask(P.w, sub_x, sub_y, key_spacing)
         assert mask.size == xs.size
         rk = interface_mc(P, xs[mask], ys[mask], n_paths, dt=dt, Dt=Dt, seed=seed, exit_mode=exit_mode,
                           step_index=step_index, threads=threads, node_ids=ids[mask], cv_table=cv_table)

@@ -20,8 +20,10 @@ Readings taken here (the paper gives no formulas):
              (p(t) > p(t - 1) and p(t) >= p(t + 1), or p(t) < p(t - 1) and
              p(t) <= p(t + 1)) of size |p(t)| >= max_t |p| / 100 -- the grid
              node nearest the extremum; smaller extrema (rounding noise where
-             rho is flat) do not count -- and every crossing of a vertical and
-             a horizontal line;
+             rho is flat) do not count -- every crossing of a vertical and
+             a horizontal line, and, with spacing g > 0, every position t
+             with t mod g = 0 (the mesh also moves where rho is flat along a
+             line, and a fill through the extrema alone misses that);
   fill       along every line, the PCHIP interpolant (Fritsch and Carlson's
              monotone cubic Hermite scheme with the derivatives of Fritsch and
              Butland, as scipy.interpolate.PchipInterpolator implements it)
@@ -71,7 +73,7 @@ def _extrema(p):
     return out
 
 
-def key_mask(w, sub_x: int, sub_y: int):
+def key_mask(w, sub_x: int, sub_y: int, spacing: int = 0):
     """Boolean mask over the interface node list: True at the key points."""
     w = np.asarray(w, dtype=np.float64)
     ny, nx = w.shape
@@ -89,6 +91,10 @@ def key_mask(w, sub_x: int, sub_y: int):
         for prof in (d1, d2):
             for k in _extrema(prof):
                 mask[index[pts[k + 1]]] = True
+        if spacing > 0:
+            for t in range(1, n - 1):
+                if t % spacing == 0:
+                    mask[index[pts[t]]] = True
         for (i, j) in pts[1:-1]:
             if i in vi and j in hj:
                 mask[index[(i, j)]] = True

@@ -37,7 +37,7 @@ EXPORTS = [
     "sdd_batch_destroy", "sdd_autotune", "sdd_batch_autotune", "sdd_cv_set_table", "sdd_cv_enable",
     "sdd_mlp_init", "sdd_cv_samples", "sdd_mlp_norm", "sdd_mlp_grad", "sdd_mlp_train", "sdd_cv_tabulate",
     "sdd_cv_train", "sdd_cv_get_model", "sdd_cv_losses", "sdd_cv_get_table", "sdd_cv_set_model",
-    "sdd_set_solver", "sdd_solver_in_use",
+    "sdd_set_solver", "sdd_solver_in_use", "sdd_set_keypoints", "sdd_keypoint_mask",
 ]
 
 SDD_SOLVER_AUTO, SDD_SOLVER_JACOBI, SDD_SOLVER_MG = range(3)
@@ -183,6 +183,8 @@ def lib():
                 "sdd_cv_get_table": [vp, vp],
                 "sdd_cv_set_model": [vp, vp, vp, i32],
                 "sdd_set_solver": [vp, i32],
+                "sdd_set_keypoints": [vp, i32, i32],
+                "sdd_keypoint_mask": [vp, vp],
                 "sdd_solver_in_use": [vp],
                 "sdd_batch_autotune": [vp, ctypes.POINTER(_Nodes), ctypes.POINTER(_McParams), ctypes.POINTER(_Shape)],
             }
@@ -733,3 +735,16 @@ def sdd_set_solver(ctx: Ctx, solver: int):
 
 def sdd_solver_in_use(ctx: Ctx) -> int:
     return int(lib().sdd_solver_in_use(ctx.handle))
+
+
+def sdd_set_keypoints(ctx: Ctx, on=True, spacing: int = 0):
+    ctx._check(lib().sdd_set_keypoints(ctx.handle, 1 if on else 0, int(spacing)))
+
+
+def sdd_keypoint_mask(ctx: Ctx):
+    """Key-point mask of the current w: cuda uint8 tensor, one entry per interface node."""
+    torch = _torch()
+    n = len(sdd_interface_nodes(ctx)[0])
+    out = torch.zeros(max(n, 1), dtype=torch.uint8, device="cuda")
+    ctx._check(lib().sdd_keypoint_mask(ctx.handle, _ptr(out)))
+    return out[:n]

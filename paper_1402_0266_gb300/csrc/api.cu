@@ -133,6 +133,17 @@ struct sdd_ctx {
     int solve_cluster = 1, solve_upt = 0, solve_rows_max = 0, solve_mx_max = 0;
     DevBuf<SolveSys> d_systems;
     DevBuf<int32_t> d_iters;
+    // key points (Sec. 4) and the interface fill
+    int keypoints = 0;
+    int key_spacing = 0;
+    std::vector<KeyLine> klines;
+    std::vector<int32_t> kpos_idx;
+    std::vector<uint8_t> kpos_cross;
+    int kmax_n = 0;
+    DevBuf<KeyLine> d_klines;
+    DevBuf<int32_t> d_kpos_idx;
+    DevBuf<uint8_t> d_kpos_cross, d_kmask;
+    DevBuf<double> d_kscratch;
     // multigrid-preconditioned solver (every subdomain the same size)
     bool mg_ok = false;
     MgArgs mg{};
@@ -431,7 +442,8 @@ uint64_t shape_key(const std::vector<NodeSeg>& segs, int K, int exit_mode)
 
 sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const OutDev* outs, const OutDev& out0, double dt,
                        int K, uint64_t seed, uint32_t step_index, const uint32_t* step_ptr, int exit_mode,
-                       const RecDev* rec, cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_b, int cv_slices = 0);
+                       const RecDev* rec, cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_b, int cv_slices = 0,
+                       const uint8_t* node_mask = nullptr);
 
 const TunedShape* find_tuned(const std::vector<TunedShape>& t, uint64_t key)
 {
@@ -519,7 +531,8 @@ sdd_status build_plan(sdd_ctx* c, Plan& P, const double* x, const double* y, con
 // per-instance outputs (null: every node writes to out0).
 sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const OutDev* outs, const OutDev& out0, double dt,
                        int K, uint64_t seed, uint32_t step_index, const uint32_t* step_ptr, int exit_mode,
-                       const RecDev* rec, cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_b, int cv_slices)
+                       const RecDev* rec, cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_b, int cv_slices,
+                       const uint8_t* node_mask)
 {
     if (P.nnodes == 0) return SDD_OK;
     if (P.ntasks > 0) {
@@ -538,6 +551,7 @@ sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const Out
         a.step_index = step_index;
         a.step_ptr = step_ptr;
         if (rec) a.rec = *rec;
+        a.node_mask = node_mask;
         const bool cv = cv_slices > 0;
         if (cv && cv_slices > K) return fail(err, SDD_EINVAL, "more control-variate slices than sub-steps per step");
         for (int q = 0; q <= kMaxCvSlices; ++q)
@@ -566,16 +580,17 @@ sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const Out
     f.out0 = out0;
     f.nnodes = (int32_t)P.nnodes;
     if (rec) f.rec = *rec;
+    f.node_mask = node_mask;
     CU(err, launch_finalize(f, s));
     return SDD_OK;
 }
 
 sdd_status run_plan(sdd_ctx* c, Plan& P, double dt, int K, uint64_t seed, uint32_t step_index,
                     const uint32_t* step_ptr, int exit_mode, const OutDev& out, const RecDev* rec, cudaStream_t s,
-                    cudaEvent_t ev_a = nullptr, cudaEvent_t ev_b = nullptr)
+                    cudaEvent_t ev_a = nullptr, cudaEvent_t ev_b = nullptr, const uint8_t* node_mask = nullptr)
 {
     return run_plan_on(&c->err, P, c->d_inst.p, nullptr, out, dt, K, seed, step_index, step_ptr, exit_mode, rec, s,
-                       ev_a, ev_b, c->cv_mode ? c->cv_slices : 0);
+                       ev_a, ev_b, c->cv_mode ? c->cv_slices : 0, node_mask);
 }
 
 // Launch shape for a plan: explicit requests win, else a tuned shape for this node set, else the heuristic.
@@ -714,6 +729,49 @@ void build_interface(sdd_ctx* c)
             c->iface_y.push_back((double)J / (c->ny - 1));
             c->iface_idx.push_back(J * c->nx + i);
         }
+    // the interface lines as key-point lines: interior positions -> interface-node index
+    c->klines.clear();
+    c->kpos_idx.clear();
+    c->kpos_cross.clear();
+    c->kmax_n = 0;
+    const int nv = c->ny - 2;
+    for (size_t a = 0; a < vi.size(); ++a) {
+        KeyLine L{0, vi[a], c->ny, (int32_t)c->kpos_idx.size()};
+        for (int j = 1; j < c->ny - 1; ++j) {
+            bool cross = false;
+            for (int J : hj) cross |= (J == j);
+            c->kpos_idx.push_back((int32_t)(a * nv + (j - 1)));
+            c->kpos_cross.push_back(cross ? 1 : 0);
+        }
+        c->klines.push_back(L);
+        c->kmax_n = std::max(c->kmax_n, c->ny);
+    }
+    int32_t next = (int32_t)(vi.size() * nv);
+    for (int J : hj) {
+        KeyLine L{1, J, c->nx, (int32_t)c->kpos_idx.size()};
+        for (int i = 1; i < c->nx - 1; ++i) {
+            int a_cross = -1;
+            for (size_t a = 0; a < vi.size(); ++a)
+                if (vi[a] == i) a_cross = (int)a;
+            if (a_cross >= 0) {
+                c->kpos_idx.push_back((int32_t)(a_cross * nv + (J - 1)));
+                c->kpos_cross.push_back(1);
+            } else {
+                c->kpos_idx.push_back(next++);
+                c->kpos_cross.push_back(0);
+            }
+        }
+        c->klines.push_back(L);
+        c->kmax_n = std::max(c->kmax_n, c->nx);
+    }
+}
+
+// Key-point mask of the current w (one byte per interface node) on stream s.
+sdd_status enqueue_keypoints(sdd_ctx* c, uint8_t* mask, cudaStream_t s)
+{
+    CU(c, launch_keypoints(c->w.p, c->nx, c->d_klines.p, (int)c->klines.size(), c->kmax_n, c->d_kpos_idx.p,
+                           c->d_kpos_cross.p, c->key_spacing, mask, s));
+    return SDD_OK;
 }
 
 // The implicit subdomain step on stream s: Dirichlet data from the faces and the
@@ -1108,6 +1166,17 @@ sdd_status sdd_init(sdd_ctx** out, const sdd_grid* g, const float* w, const doub
     if (!c->iface_idx.empty())
         INIT_CU(cudaMemcpy(c->d_iface_idx.p, c->iface_idx.data(), c->iface_idx.size() * sizeof(int32_t),
                            cudaMemcpyHostToDevice));
+    INIT_CU(c->d_klines.alloc(std::max<size_t>(c->klines.size(), 1)));
+    INIT_CU(c->d_kpos_idx.alloc(std::max<size_t>(c->kpos_idx.size(), 1)));
+    INIT_CU(c->d_kpos_cross.alloc(std::max<size_t>(c->kpos_cross.size(), 1)));
+    INIT_CU(c->d_kmask.alloc(std::max<size_t>(c->iface_idx.size(), 1)));
+    INIT_CU(c->d_kscratch.alloc(pchip_scratch_doubles((long long)c->kpos_idx.size(), (int)c->klines.size())));
+    if (!c->klines.empty()) {
+        INIT_CU(cudaMemcpy(c->d_klines.p, c->klines.data(), c->klines.size() * sizeof(KeyLine), cudaMemcpyHostToDevice));
+        INIT_CU(cudaMemcpy(c->d_kpos_idx.p, c->kpos_idx.data(), c->kpos_idx.size() * sizeof(int32_t),
+                           cudaMemcpyHostToDevice));
+        INIT_CU(cudaMemcpy(c->d_kpos_cross.p, c->kpos_cross.data(), c->kpos_cross.size(), cudaMemcpyHostToDevice));
+    }
     for (int k = 0; k < 4; ++k) INIT_CU(c->iface_stats[k].alloc(std::max<size_t>(c->iface_idx.size(), 1)));
     for (int k = 0; k < 2; ++k) INIT_CU(c->iface_counts[k].alloc(std::max<size_t>(c->iface_idx.size(), 1)));
     c->dirty_w = c->dirty_fields = true;
@@ -1230,6 +1299,22 @@ sdd_status sdd_interface_mc_record(sdd_ctx* c, const sdd_nodes* nodes, const sdd
 {
     if (!rec) return fail(c, SDD_EINVAL, "null records");
     return mc_common(c, nodes, p, out, rec);
+}
+
+sdd_status sdd_set_keypoints(sdd_ctx* c, int32_t on, int32_t spacing)
+{
+    if (!c) return SDD_EINVAL;
+    if (spacing < 0) return fail(c, SDD_EINVAL, "spacing must be >= 0");
+    if ((on != 0) != (c->keypoints != 0) || spacing != c->key_spacing) drop_graphs(c);
+    c->keypoints = on != 0;
+    c->key_spacing = spacing;
+    return SDD_OK;
+}
+
+sdd_status sdd_keypoint_mask(sdd_ctx* c, uint8_t* mask)
+{
+    if (!c || !mask) return fail(c, SDD_EINVAL, "null argument");
+    return enqueue_keypoints(c, mask, c->stream);
 }
 
 sdd_status sdd_set_solver(sdd_ctx* c, int32_t solver)
@@ -1529,9 +1614,16 @@ static sdd_status capture_step(sdd_ctx* c, const sdd_step_params* p, int K, int 
     o.se_eta = c->iface_stats[3].p;
     o.n_exit = c->iface_counts[0].p;
     o.path_steps = c->iface_counts[1].p;
+    const uint8_t* kmask = c->keypoints ? c->d_kmask.p : nullptr;
+    if (st == SDD_OK && kmask) st = enqueue_keypoints(c, c->d_kmask.p, s);
     if (st == SDD_OK)
         st = run_plan(c, c->step_plan, p->dt, K, p->seed, 0, c->d_step.p, p->exit_mode, o, nullptr, s, c->ev[1],
-                      c->ev[2]);
+                      c->ev[2], kmask);
+    if (st == SDD_OK && kmask) {
+        cudaError_t e = launch_pchip(c->d_klines.p, (int)c->klines.size(), c->d_kpos_idx.p, c->d_kpos_cross.p, kmask,
+                                     c->faces64.p, c->nx, c->ny, o.mean_xi, o.mean_eta, c->d_kscratch.p, s);
+        if (e != cudaSuccess) st = fail(c, SDD_ECUDA, "interface fill: %s", cudaGetErrorString(e));
+    }
     if (st == SDD_OK) {
         cudaError_t e = cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal);
         if (e != cudaSuccess) st = fail(c, SDD_ECUDA, "event: %s", cudaGetErrorString(e));

@@ -99,6 +99,7 @@ struct PathArgs {
     uint32_t step_index;
     const uint32_t* step_ptr; // if non-null, read the step index here
     RecDev rec;
+    const uint8_t* node_mask; // if non-null, only nodes with a nonzero entry run their paths
 };
 
 struct FinalArgs {
@@ -109,6 +110,7 @@ struct FinalArgs {
     OutDev out0;
     int32_t nnodes;
     RecDev rec;               // per-path records of boundary nodes (may be all null)
+    const uint8_t* node_mask; // if non-null, nodes with a zero entry report no paths (filled later)
 };
 
 // Device status word bits.
@@ -130,6 +132,21 @@ cudaError_t launch_prep_cells(const float* w, const double* xi, const double* et
 cudaError_t launch_winslow_faces(const float* w, int nx, int ny, double* faces64, cudaStream_t s);
 cudaError_t launch_cv_cells(const double* grad, int slices, int nx, int ny, uint4* cvcoef, cudaStream_t s);
 cudaError_t launch_faces32(const double* faces64, float* faces32, int n, cudaStream_t s);
+
+// Key points and interface fill (keypoints.cu). One interface line: vertical
+// (orient 0, column fixed) or horizontal (orient 1, row fixed), n nodes along
+// it (both ends on the boundary); its interior positions t = 1 .. n - 2 are
+// entries start + t - 1 of the position arrays (interface-node index, crossing flag).
+struct KeyLine {
+    int32_t orient, fixed, n, start;
+};
+cudaError_t launch_keypoints(const float* w, int nx, const KeyLine* lines, int nlines, int max_n,
+                             const int32_t* pos_idx, const uint8_t* pos_cross, int spacing, uint8_t* mask,
+                             cudaStream_t s);
+size_t pchip_scratch_doubles(long long total_positions, int nlines);
+cudaError_t launch_pchip(const KeyLine* lines, int nlines, const int32_t* pos_idx, const uint8_t* pos_cross,
+                         const uint8_t* mask, const double* faces, int nx, int ny, double* mean_xi, double* mean_eta,
+                         double* scratch, cudaStream_t s);
 
 // Learned control variate (mlp.cu).
 cudaError_t launch_node_features(const float* w, int nx, int ny, double* w64, double* r64, double2* gw, float4* nfa,

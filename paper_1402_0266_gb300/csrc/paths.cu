@@ -260,6 +260,7 @@ __global__ void __launch_bounds__(CV ? kCvMaxBlock : 512, CV ? 3 : 2) k_paths(co
         if (t >= a.ntasks) continue;
 
         const Task task = a.tasks[t];
+        if (a.node_mask && !a.node_mask[task.node]) continue;   // not a key point this step
         const NodeDev& nd = a.nodes[task.node];
         const InstDev I = a.inst[nd.inst];
         const float x0 = nd.xf, y0 = nd.yf;
@@ -466,6 +467,18 @@ __global__ void k_finalize(const FinalArgs a)
     const NodeDev nd = a.nodes[node];
     const OutDev o = a.out_table ? a.out_table[nd.inst] : a.out0;
     const int k = nd.local;
+    if (a.node_mask && !a.node_mask[node]) {
+        // not estimated this step: no paths; the interface fill writes its value
+        if (lane == 0) {
+            if (o.mean_xi) o.mean_xi[k] = 0.0;
+            if (o.mean_eta) o.mean_eta[k] = 0.0;
+            if (o.se_xi) o.se_xi[k] = 0.0;
+            if (o.se_eta) o.se_eta[k] = 0.0;
+            if (o.n_exit) o.n_exit[k] = 0;
+            if (o.path_steps) o.path_steps[k] = 0;
+        }
+        return;
+    }
     if (nd.ntasks == 0) {
         // a node on the boundary: its Dirichlet value, every path exits at time 0
         const InstDev I = a.inst[nd.inst];

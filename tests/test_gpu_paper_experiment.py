@@ -39,13 +39,17 @@ def folded_cells(xi, eta):
     return int(bad.sum())
 
 
-def test_sec5_moving_ring_mesh(sdd, oracle_mod):
+@pytest.mark.parametrize("keypoints", [True, False])
+def test_sec5_moving_ring_mesh(sdd, oracle_mod, keypoints):
+    # keypoints=True is the paper's setup (estimates at the key points, PCHIP elsewhere), with a key
+    # point also at every 8th node of each line
     import torch
     from oracle import solver
     n, Dt, K, paths, steps = 41, 1e-3, 20, 10000, 750
     xi0, eta0 = W.identity_fields(n)
     ctx = sdd.sdd_init(n, n, 2, 2, w=torch.from_numpy(W.w_paper_ring(n, 0.0)).cuda(),
                        xi0=torch.from_numpy(xi0).cuda(), eta0=torch.from_numpy(eta0).cuda())
+    sdd.sdd_set_keypoints(ctx, keypoints, 8)
     ref = [xi0.copy(), eta0.copy()]
     snaps = {}
     for k in range(steps):
@@ -66,10 +70,11 @@ def test_sec5_moving_ring_mesh(sdd, oracle_mod):
         dev = max(np.abs(gx - rx).max(), np.abs(ge - re).max())
         moved = max(np.abs(gx - X).max(), np.abs(ge - Y).max())
         report[k] = (folded_cells(gx, ge), folded_cells(rx, re), dev, moved)
-    print(report)
+    print(keypoints, report)
     for k, (fg, fr, dev, moved) in report.items():
         assert fg == 0 and fr == 0, (k, fg, fr)
         # the interface values carry the Monte Carlo error and the plain exit test's sqrt(dt) bias
-        # (Sec. 4): the mesh stays within half a cell (h / 2 = 0.0125) of the deterministic scheme
-        assert dev < 0.0125, (k, dev)
+        # (Sec. 4), and with key points the fill's interpolation error: the mesh stays within half a
+        # cell (h / 2 = 0.0125) of the deterministic scheme, one cell with key points
+        assert dev < (0.025 if keypoints else 0.0125), (k, dev)
         assert moved > 0.1, (k, moved)      # while it moves by several cells towards the ring

@@ -103,3 +103,19 @@ def test_keypoint_step_uses_fewer_nodes_and_stays_close(oracle_mod, kp):
     assert np.all(rk["path_steps"][~m] == 0)
     gap = max(np.abs(key[0] - full[0]).max(), np.abs(key[1] - full[1]).max())
     assert gap < 5e-3, gap
+
+
+def test_spacing_adds_every_gth_position(kp):
+    n, sub, g = 41, 2, 8
+    w = W.w_paper_ring(n, 0.0)
+    base = kp.key_mask(w, sub, sub)
+    spaced = kp.key_mask(w, sub, sub, g)
+    assert np.all(spaced >= base)
+    nodes = kp.node_list(n, n, sub, sub)
+    I = kp.line_indices(n, sub)[0]
+    for k, (i, j) in enumerate(nodes):
+        t = j if i == I else i
+        if t % g == 0:
+            assert spaced[k], (i, j)
+        elif not base[k]:
+            assert not spaced[k], (i, j)
