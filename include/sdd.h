@@ -413,10 +413,14 @@ sdd_status sdd_keypoint_mask(sdd_ctx* ctx, uint8_t* mask);
  *                      sizes that halve, (m - 1) / 2, down to a box of at
  *                      most 64 unknowns; else SDD_EINVAL);
  *   SDD_SOLVER_AUTO    multigrid where it is available and the subdomains are
- *                      too large for the register-resident Jacobi kernel.
- * With multigrid, max_iter caps the inner iterations (at most 5 per
- * refinement sweep, at most 6 sweeps). sdd_solver_in_use returns the solver
- * the next solve will use (1 Jacobi, 2 multigrid). */
+ *                      too large for the register-resident Jacobi kernel or
+ *                      hold at least 10,000 unknowns.
+ * With multigrid, max_iter caps the inner iterations: inside sdd_step's graph
+ * the refinement sweeps and inner iterations are graph while-loops that stop
+ * once every field has converged (at most 30 inner iterations per sweep and
+ * 8 sweeps, within max_iter); a direct sdd_subdomain_solve runs a fixed 5 x 6.
+ * sdd_solver_in_use returns the solver the next solve will use (1 Jacobi,
+ * 2 multigrid). */
 #define SDD_SOLVER_AUTO 0
 #define SDD_SOLVER_JACOBI 1
 #define SDD_SOLVER_MG 2
@@ -451,7 +455,8 @@ sdd_status sdd_last_interface_stats(sdd_ctx* ctx, sdd_node_stats* out);
  * the number of kernel launches in the step graph and the device time of the
  * step's parts, taken with events recorded inside the graph. */
 typedef struct {
-    int32_t kernel_nodes;  /* kernels launched per step                          */
+    int32_t kernel_nodes;  /* kernels the last step launched (the graph's kernel nodes
+                              and the kernels its solver loops ran)                */
     float paths_ms;        /* the path kernel                                    */
     float estimate_ms;     /* the whole interface estimate (tables, paths, means) */
     float solve_ms;        /* the subdomain solves                               */

@@ -245,6 +245,8 @@ struct MgArgs {
     int32_t* act_i;          // [nsys][2] inner iteration still running
     int32_t* iters;          // [nsys][2]
     int32_t* sys_iters;      // [nsys] inner iterations of the system (max_iter + 1: not converged)
+    int32_t* loop;           // [2] pass counters of the graph loops (refinement sweeps, inner iterations)
+    int32_t* launches;       // kernels the graph loops' bodies launched in this solve (or null)
     int* status;
     int32_t outer, inner, nu, coarse_sweeps, max_iter;
     double rtol;
@@ -254,6 +256,7 @@ bool mg_levels(int mx, int my, MgArgs& a);
 long long mg_layout(MgArgs& a, int nsys);
 cudaError_t launch_mg_setup(const MgArgs& a, cudaStream_t s);
 cudaError_t launch_mg_solve(const MgArgs& a, cudaStream_t s);
+cudaError_t launch_mg_solve_graph(const MgArgs& a, cudaStream_t s, cudaStream_t s2, cudaStream_t s3);
 
 cudaError_t launch_solve_setup(const float* w, const double* prev_xi, const double* prev_eta, int nx, int ny,
                                double Dt, double* cx, double* cy, double* dg, double* rhs0, float* cxf, float* cyf,

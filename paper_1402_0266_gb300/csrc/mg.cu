@@ -210,11 +210,10 @@ __global__ void __launch_bounds__(MG_THREADS) k_mg_prolong(const MgArgs a, int l
     }
 }
 
-// The levels from lt down to the coarsest and back, one block per system.
-__global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(const MgArgs a, int lt)
+// The levels from lt down to the coarsest and back, by the calling block
+// (system s); U_lt starts at zero.
+__device__ void vcycle_block(const MgArgs& a, int s, int lt)
 {
-    const int s = blockIdx.x;
-    if (!any_active(a, s)) return;
     auto sweep = [&](int l, int color) {
         const Lv v = level(a, l, s);
         const int per_row = (v.mx + 1) / 2;
@@ -289,6 +288,13 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(const MgArgs a, int lt
             sweep(l, 0);
         }
     }
+}
+
+__global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(const MgArgs a, int lt)
+{
+    const int s = blockIdx.x;
+    if (!any_active(a, s)) return;
+    vcycle_block(a, s, lt);
 }
 
 // ---------------------------------------------------------------- Krylov pieces (level-0 vectors)
@@ -450,6 +456,7 @@ __global__ void __launch_bounds__(MG_THREADS) k_mg_pupdate(const MgArgs a, int f
 {
     const int s = blockIdx.y;
     if (!any_active(a, s)) return;
+    if (parity < 0) parity = a.loop[1] & 1;   // inside a graph loop: the inner iteration counter
     const V0 v = v0(a, s);
     const int n = v.mx * v.my;
     float beta[2];
@@ -494,6 +501,7 @@ __global__ void __launch_bounds__(MG_THREADS) k_mg_spmv(const MgArgs a)
 __global__ void __launch_bounds__(MG_THREADS) k_mg_update(const MgArgs a, int parity)
 {
     const int s = blockIdx.y;
+    if (parity < 0) parity = a.loop[1] & 1;
     const V0 v = v0(a, s);
     const int n = v.mx * v.my;
     float t[2] = {0.f, 0.f};
@@ -529,6 +537,33 @@ __global__ void k_mg_inner(const MgArgs a)
     const float rr = sum_part(a, t >> 1, t & 1);
     a.iters[t] += 1;
     if (!(rr > a.inner_tol * a.inner_tol * a.rr0[t])) a.act_i[t] = 0;
+}
+
+// Loop control inside a graph: counter `which` (0 refinement sweeps, 1 inner
+// iterations) counts this pass, and the while-node's condition becomes "some
+// field still active (act_o for 0, act_i for 1) and fewer than cap passes".
+__global__ void k_mg_cond(const MgArgs a, cudaGraphConditionalHandle h, int which, int cap, int body_kernels)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (a.launches) *a.launches += body_kernels;   // the pass of the loop body that ends here
+    const int32_t* act = which == 0 ? a.act_o : a.act_i;
+    int any = 0;
+    for (int t = 0; t < 2 * a.nsys; ++t) any |= act[t];
+    const int c = a.loop[which] + 1;
+    a.loop[which] = c;
+    cudaGraphSetConditional(h, (any && c < cap) ? 1u : 0u);
+}
+
+// Start a loop: counter `which` to zero and the loop's condition to "some field active".
+__global__ void k_mg_loop_reset(const MgArgs a, cudaGraphConditionalHandle h, int which)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (which == 0 && a.launches) *a.launches = 0;
+    const int32_t* act = which == 0 ? a.act_o : a.act_i;
+    int any = 0;
+    for (int t = 0; t < 2 * a.nsys; ++t) any |= act[t];
+    a.loop[which] = 0;
+    cudaGraphSetConditional(h, any ? 1u : 0u);
 }
 
 // x += d (double precision) on every unknown of the fields still iterating
@@ -602,6 +637,9 @@ cudaError_t launch_mg_setup(const MgArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// kernels one V-cycle launches
+static int vcycle_kernels(const MgArgs& a) { return a.tail * (4 * a.nu + 2) + 1; }
+
 static void vcycle(const MgArgs& a, cudaStream_t s)
 {
     for (int l = 0; l < a.tail; ++l) {
@@ -650,6 +688,108 @@ cudaError_t launch_mg_solve(const MgArgs& a, cudaStream_t s)
     k_mg_res64<<<g0, MG_THREADS, 0, s>>>(a);
     k_mg_outer<<<sc, 128, 0, s>>>(a, 0, 1);
     return cudaGetLastError();
+}
+
+// A condition handle of the graph that stream s is capturing into. The
+// handle's default (1) applies only when the whole graph is launched, so a
+// loop entered more than once per launch has its handle set by a kernel first.
+static cudaError_t make_handle(cudaStream_t s, cudaGraphConditionalHandle* h)
+{
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr);
+    if (e != cudaSuccess) return e;
+    if (st != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureImplicit;
+    return cudaGraphConditionalHandleCreate(h, g, 1, cudaGraphCondAssignDefault);
+}
+
+// Add a while-node on handle h after the capture's current dependencies on
+// stream s and start capturing its body on stream b.
+static cudaError_t begin_while(cudaStream_t s, cudaStream_t b, cudaGraphConditionalHandle h, cudaGraphNode_t* node)
+{
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd);
+    if (e != cudaSuccess) return e;
+    if (st != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureImplicit;
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    if ((e = cudaGraphAddNode(node, g, deps, nullptr, nd, &p)) != cudaSuccess) return e;
+    return cudaStreamBeginCaptureToGraph(b, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeRelaxed);
+}
+
+// Close the body captured on b; s continues after the while-node.
+static cudaError_t end_while(cudaStream_t s, cudaStream_t b, cudaGraphNode_t node)
+{
+    cudaGraph_t body = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b, &body);
+    if (e != cudaSuccess) return e;
+    return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+static cudaError_t mg_graph_body(const MgArgs& a, cudaStream_t s, cudaStream_t s2, cudaStream_t s3)
+{
+    const dim3 g0(a.B0, a.nsys);
+    const int sc = (2 * a.nsys + 127) / 128;
+    cudaError_t e;
+    cudaGraphConditionalHandle ho, hi;
+    cudaGraphNode_t no, ni;
+    k_mg_res64<<<g0, MG_THREADS, 0, s>>>(a);
+    k_mg_outer<<<sc, 128, 0, s>>>(a, 1, 0);
+    if ((e = make_handle(s, &ho)) != cudaSuccess) return e;
+    k_mg_loop_reset<<<1, 32, 0, s>>>(a, ho, 0);
+    if ((e = begin_while(s, s2, ho, &no)) != cudaSuccess) return e;
+    // one refinement sweep: the inner PCG on A d = r, then x += d and the new residual
+    vcycle(a, s2);
+    k_mg_rz<<<g0, MG_THREADS, 0, s2>>>(a);
+    if ((e = make_handle(s2, &hi)) != cudaSuccess) return e;
+    k_mg_loop_reset<<<1, 32, 0, s2>>>(a, hi, 1);
+    k_mg_pupdate<<<g0, MG_THREADS, 0, s2>>>(a, 1, -1);
+    if ((e = begin_while(s2, s3, hi, &ni)) != cudaSuccess) return e;
+    k_mg_spmv<<<g0, MG_THREADS, 0, s3>>>(a);
+    k_mg_update<<<g0, MG_THREADS, 0, s3>>>(a, -1);
+    k_mg_inner<<<sc, 128, 0, s3>>>(a);
+    k_mg_cond<<<1, 32, 0, s3>>>(a, hi, 1, a.inner, 6 + vcycle_kernels(a));
+    vcycle(a, s3);
+    k_mg_rz<<<g0, MG_THREADS, 0, s3>>>(a);
+    k_mg_pupdate<<<g0, MG_THREADS, 0, s3>>>(a, 0, -1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = end_while(s2, s3, ni)) != cudaSuccess) return e;
+    k_mg_xupdate<<<g0, MG_THREADS, 0, s2>>>(a);
+    k_mg_res64<<<g0, MG_THREADS, 0, s2>>>(a);
+    k_mg_outer<<<sc, 128, 0, s2>>>(a, 0, 0);
+    k_mg_cond<<<1, 32, 0, s2>>>(a, ho, 0, a.outer, 8 + vcycle_kernels(a));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = end_while(s, s2, no)) != cudaSuccess) return e;
+    k_mg_outer<<<sc, 128, 0, s>>>(a, 0, 1);
+    return cudaGetLastError();
+}
+
+// The same solve for a stream that is being captured: the refinement sweeps
+// and the inner iterations are while-nodes whose condition kernels stop them
+// once every field has converged (at most outer x inner passes), so a graph
+// replay runs only the iterations the systems need.
+cudaError_t launch_mg_solve_graph(const MgArgs& a, cudaStream_t s, cudaStream_t s2, cudaStream_t s3)
+{
+    const cudaError_t e = mg_graph_body(a, s, s2, s3);
+    if (e != cudaSuccess) {
+        // leave no body capture open: the caller ends (and discards) the main capture
+        for (cudaStream_t b : {s3, s2}) {
+            cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(b, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+                cudaGraph_t g = nullptr;
+                cudaStreamEndCapture(b, &g);
+                if (g) cudaGraphDestroy(g);
+            }
+        }
+    }
+    return e;
 }
 
 }  // namespace sdd

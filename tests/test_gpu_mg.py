@@ -112,6 +112,8 @@ def test_multigrid_availability(sdd):
     assert sdd.sdd_solver_in_use(ctx) == 2
     ctx = _ctx(sdd, np.ones((65, 65)), *W.identity_fields(65), 2)
     assert sdd.sdd_solver_in_use(ctx) == 1
+    ctx = _ctx(sdd, np.ones((257, 257)), *W.identity_fields(257), 2)    # 127^2 unknowns per subdomain
+    assert sdd.sdd_solver_in_use(ctx) == 2
 
 
 def test_multigrid_nonconvergence_is_a_status(sdd):
