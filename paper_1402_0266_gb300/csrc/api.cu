@@ -304,8 +304,9 @@ sdd_status build_plan_segs(std::string* err, int sm_count, Plan& P, const std::v
         count += g.count;
     }
     if (count > (1LL << 30)) return fail(err, SDD_EINVAL, "node count out of range");
-    if (block_req != 0 && block_req != 64 && block_req != 128 && block_req != 256 && block_req != 512)
-        return fail(err, SDD_EINVAL, "block_threads must be 0, 64, 128, 256 or 512");
+    if (block_req != 0 && block_req != 64 && block_req != 128 && block_req != 256 && block_req != 512 &&
+        block_req != 1024)
+        return fail(err, SDD_EINVAL, "block_threads must be 0, 64, 128, 256, 512 or 1024");
     if (ppt_req < 0 || (ppt_req % 32) != 0) return fail(err, SDD_EINVAL, "paths_per_task must be a multiple of 32");
 
     std::vector<int64_t> key;
@@ -481,7 +482,7 @@ sdd_status autotune_plan(std::string* err, int sm_count, const std::vector<NodeS
     CU(err, cudaEventCreate(&e1));
     TunedShape best{shape_key(segs, K, exit_mode), 256, 0, 1e30f};
     sdd_status st = SDD_OK;
-    for (int block : {128, 256, 512}) {
+    for (int block : {128, 256, 512, 1024}) {
         for (int ppt : {32, 64, 128, 256, 512, 1024}) {
             Plan P;
             st = build_plan_segs(err, sm_count, P, segs, ppt, block, exit_mode, false);
@@ -878,7 +879,14 @@ sdd_status enqueue_solve(sdd_ctx* c, double Dt, const double* ix, const double* 
         CU(c, launch_mg_setup(m, s));
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         CU(c, cudaStreamIsCapturing(s, &cs));
-        if (cs == cudaStreamCaptureStatusActive) {
+        int C = 0, rows_max = 0;
+        size_t smem = 0;
+        const int upt = mgc_config(m, &C, &rows_max, &smem);
+        if (upt > 0) {
+            // subdomains that fit one cluster: the whole solve in one launch
+            m.outer = 8;
+            CU(c, launch_mgc(m, upt, C, rows_max, smem, s));
+        } else if (cs == cudaStreamCaptureStatusActive) {
             // inside the step's graph: while-loops that stop once every field has converged
             m.inner = std::max(1, std::min(30, max_iter));
             m.outer = std::max(1, std::min(8, max_iter / m.inner));
