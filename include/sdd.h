@@ -108,7 +108,7 @@ typedef struct {
  *   exit_mode   0: the paper's boundary test after every sub-step;
  *               1: that test plus a Brownian-bridge test between sub-steps.
  *   block_threads, paths_per_task: launch shape; 0 picks the tuned default.
- *               block_threads in {64, 128, 256, 512, 1024}; paths_per_task a
+ *               block_threads in {64, 128, 256, 512}; paths_per_task a
  *               multiple of 32. */
 typedef struct {
     double dt;
@@ -352,7 +352,7 @@ typedef struct {
 } sdd_launch_shape;
 
 /* Autotuner: time the interface estimate of this node set and these
- * parameters with every candidate launch shape (128, 256, 512, 1024 threads x 32 ..
+ * parameters with every candidate launch shape (128, 256, 512 threads x 32 ..
  * 1024 paths per task; outputs discarded; uses the context's current tables),
  * keep the fastest, and use it for later calls on the same node set, K and
  * exit mode that leave block_threads and paths_per_task at 0. Waits for the

@@ -304,9 +304,8 @@ sdd_status build_plan_segs(std::string* err, int sm_count, Plan& P, const std::v
         count += g.count;
     }
     if (count > (1LL << 30)) return fail(err, SDD_EINVAL, "node count out of range");
-    if (block_req != 0 && block_req != 64 && block_req != 128 && block_req != 256 && block_req != 512 &&
-        block_req != 1024)
-        return fail(err, SDD_EINVAL, "block_threads must be 0, 64, 128, 256, 512 or 1024");
+    if (block_req != 0 && block_req != 64 && block_req != 128 && block_req != 256 && block_req != 512)
+        return fail(err, SDD_EINVAL, "block_threads must be 0, 64, 128, 256 or 512");
     if (ppt_req < 0 || (ppt_req % 32) != 0) return fail(err, SDD_EINVAL, "paths_per_task must be a multiple of 32");
 
     std::vector<int64_t> key;
@@ -482,7 +481,7 @@ sdd_status autotune_plan(std::string* err, int sm_count, const std::vector<NodeS
     CU(err, cudaEventCreate(&e1));
     TunedShape best{shape_key(segs, K, exit_mode), 256, 0, 1e30f};
     sdd_status st = SDD_OK;
-    for (int block : {128, 256, 512, 1024}) {
+    for (int block : {128, 256, 512}) {
         for (int ppt : {32, 64, 128, 256, 512, 1024}) {
             Plan P;
             st = build_plan_segs(err, sm_count, P, segs, ppt, block, exit_mode, false);

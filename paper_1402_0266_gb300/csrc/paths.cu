@@ -236,7 +236,7 @@ __device__ __forceinline__ long long warp_sum_ll(long long v)
 // MODE 2: as MODE 0 when K is even (every pair has both sub-steps).
 // CV: subtract the control variate sum_j G(s_j, X_j) . sqrt(2) dW_j from both scores.
 template <int MODE, bool RECORD, bool CV>
-__global__ void __launch_bounds__(CV ? kCvMaxBlock : 1024, CV ? 3 : 1) k_paths(const PathArgs a)
+__global__ void __launch_bounds__(CV ? kCvMaxBlock : 512, CV ? 3 : 2) k_paths(const PathArgs a)
 {
     __shared__ int s_group;
     const int lane = threadIdx.x & 31;
