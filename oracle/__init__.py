@@ -226,6 +226,10 @@ def interface_mc(problem: Problem, xs, ys, n_paths, *, dt: float, Dt: float, see
                  record: bool = False, threads: int | None = None, cv_table=None):
     """Estimate xi, eta at the given nodes over one mesh step (Eq. 7b, Sec. 4).
 
+    exit_mode: 0 fixed sub-steps with the plain exit test, 1 fixed sub-steps
+    with the plain and the Brownian-bridge tests, 2 exponential time-stepping
+    (sub-step lengths exponential with mean dt, both tests over each).
+
     Returns a dict with mean_xi, mean_eta, se_xi, se_eta, n_exit, path_steps
     (one entry per node) and, with record=True, per-path arrays steps, code,
     score_xi, score_eta, x_end, y_end laid out node after node.
@@ -246,6 +250,8 @@ def interface_mc(problem: Problem, xs, ys, n_paths, *, dt: float, Dt: float, see
     K = sub_steps(dt, Dt)
     cv = None
     if cv_table is not None:
+        if exit_mode == 2:
+            raise ValueError("the control variate needs fixed sub-steps (exit_mode 0 or 1)")
         cv = np.ascontiguousarray(cv_table, dtype=np.float64)
         assert cv.ndim == 4 and cv.shape[1:] == (problem.ny, problem.nx, 4)
     P = _Problem(problem.nx, problem.ny, problem.bx.ctypes.data, problem.by.ctypes.data,

@@ -255,7 +255,7 @@ typedef struct {
 typedef struct {
     double dt;            /* sub-step */
     int32_t K;            /* sub-steps per mesh step, Delta t = K dt */
-    int32_t exit_mode;    /* 0 plain test, 1 plain test + Brownian-bridge test */
+    int32_t exit_mode;    /* 0 plain test, 1 plain test + Brownian-bridge test, 2 exponential time-stepping */
     uint64_t seed;
     uint32_t step_index;  /* mesh step n */
 } orc_params;
@@ -319,6 +319,73 @@ static int boundary_face(double x, double y, double* tang)
     if (y <= 0.0) { *tang = x; return 2; }
     *tang = x;
     return 3;
+}
+
+/* Exponential time-stepping, the alternative to fixed Euler--Maruyama steps
+ * that Sec. 4 names (after Jansons and Lythe): the sub-step lengths are
+ * independent exponential times of mean dt, tau_j = -dt ln u with u =
+ * u_open0(word 3) of the sub-step's Philox block (counter (path, node, j,
+ * step)), the last one cut at the end of the mesh step T = K dt (and after at
+ * most 4K + 16 sub-steps). Each sub-step is the Euler--Maruyama update over
+ * tau_j (normals from words 0, 1 scaled by sqrt(2 tau_j)), followed by the
+ * plain test and the Brownian-bridge test over tau_j (bridge uniform from word
+ * 2). Same outputs as run_path; no control variate. */
+static int32_t run_path_exp(const orc_problem* P, const orc_params* Q, uint32_t node, uint32_t path, double x0,
+                            double y0, double* score_xi, double* score_eta, double* xe, double* ye, int32_t* code)
+{
+    const int nx = P->nx, ny = P->ny;
+    const double T = (double)Q->K * Q->dt;
+    const int32_t cap = 4 * Q->K + 16;
+    double x = x0, y = y0, t = 0.0;
+    uint32_t words[4];
+    for (int32_t j = 0;; ++j) {
+        draw_words(Q->seed, path, node, (uint32_t)j, Q->step_index, words);
+        double zx, zy;
+        orc_box_muller(words[0], words[1], &zx, &zy);
+        const double ub = u_pos(words[2]);
+        double tau = -Q->dt * log(u_open0(words[3]));
+        int last = 0;
+        if (t + tau >= T || j + 1 >= cap) {
+            tau = T - t;
+            last = 1;
+        }
+        const double bx = orc_bilinear(nx, ny, P->bx, x, y);
+        const double by = orc_bilinear(nx, ny, P->by, x, y);
+        const double sq = sqrt(2.0 * tau);
+        const double xn = x + bx * tau + sq * zx;
+        const double yn = y + by * tau + sq * zy;
+        if (on_boundary(xn, yn)) {
+            double tt;
+            const int face = plain_exit_point(x, y, xn, yn, &tt);
+            *score_xi = orc_face_value(nx, ny, P->faces, 0, face, tt);
+            *score_eta = orc_face_value(nx, ny, P->faces, 1, face, tt);
+            *xe = (face == 0) ? 0.0 : (face == 1) ? 1.0 : tt;
+            *ye = (face == 2) ? 0.0 : (face == 3) ? 1.0 : tt;
+            *code = face;
+            return j + 1;
+        }
+        double tt;
+        const int face = bridge_exit(x, y, xn, yn, tau, ub, &tt);
+        if (face >= 0) {
+            *score_xi = orc_face_value(nx, ny, P->faces, 0, face, tt);
+            *score_eta = orc_face_value(nx, ny, P->faces, 1, face, tt);
+            *xe = (face == 0) ? 0.0 : (face == 1) ? 1.0 : tt;
+            *ye = (face == 2) ? 0.0 : (face == 3) ? 1.0 : tt;
+            *code = 4 + face;
+            return j + 1;
+        }
+        x = xn;
+        y = yn;
+        t += tau;
+        if (last) {
+            *score_xi = orc_bilinear(nx, ny, P->xi0, x, y);
+            *score_eta = orc_bilinear(nx, ny, P->eta0, x, y);
+            *xe = x;
+            *ye = y;
+            *code = -1;
+            return j + 1;
+        }
+    }
 }
 
 /* One path of the estimator (Eq. 7b under Euler--Maruyama, Sec. 4). With a
@@ -467,7 +534,11 @@ int orc_mc_nodes(const orc_problem* P, const orc_params* Q, int64_t count,
         for (int64_t p = 0; p < n; ++p) {
             double xe, ye;
             int32_t code;
-            int32_t taken = run_path(P, Q, node_ids[k], (uint32_t)p, xs[k], ys[k], &sx[p], &se[p], &xe, &ye, &code);
+            int32_t taken = Q->exit_mode == 2
+                                ? run_path_exp(P, Q, node_ids[k], (uint32_t)p, xs[k], ys[k], &sx[p], &se[p], &xe, &ye,
+                                               &code)
+                                : run_path(P, Q, node_ids[k], (uint32_t)p, xs[k], ys[k], &sx[p], &se[p], &xe, &ye,
+                                           &code);
             if (code >= 0) exits += 1.0;
             steps += (double)taken;
             if (rec_steps) rec_steps[rec + p] = taken;

@@ -198,3 +198,34 @@ def test_oracle_regression_fixture(oracle_mod):
         for key, val in got.items():
             np.testing.assert_allclose(np.asarray(val, float), np.asarray(stored[case][key], float),
                                        rtol=1e-9, atol=1e-12, err_msg=f"{case}/{key}")
+
+
+def test_exponential_time_stepping_heat_closed_form(oracle_mod):
+    # exit_mode 2 (exponential sub-step lengths, bridge test over each): for Brownian motion the exit
+    # detection is exact, so even five sub-steps on average per mesh step give the closed form
+    xi0, eta0 = W.heat65_fields()
+    P = oracle_mod.Problem(W.w_const(65), xi0, eta0, _zero_faces(oracle_mod, 65))
+    xs, ys = W.heat65_nodes()
+    xs, ys = xs[1:32:3], ys[1:32:3]
+    r = oracle_mod.interface_mc(P, xs, ys, 40000, dt=1e-2, Dt=0.05, exit_mode=2)
+    ex, ee = W.heat_exact(xs, ys, 0.05)
+    assert np.all(np.abs(r["mean_xi"] - ex) <= 4 * r["se_xi"] + 3e-4), np.abs(r["mean_xi"] - ex) / r["se_xi"]
+    assert np.all(np.abs(r["mean_eta"] - ee) <= 4 * r["se_eta"] + 3e-4)
+    # the plain fixed-step test at the same dt is off by far more
+    p = oracle_mod.interface_mc(P, xs, ys, 40000, dt=1e-2, Dt=0.05, exit_mode=0)
+    assert np.sqrt(np.mean((p["mean_xi"] - ex) ** 2)) > 20 * np.sqrt(np.mean((r["mean_xi"] - ex) ** 2))
+
+
+def test_exponential_time_stepping_counts_poisson_steps(oracle_mod):
+    # far from the boundary every path survives: the sub-step count is the number of exponential
+    # arrivals in the mesh step (Poisson with mean K) plus the cut last sub-step, mean K + 1
+    n = 33
+    P = oracle_mod.Problem(W.w_const(n), *W.identity_fields(n))
+    K, N = 20, 20000
+    r = oracle_mod.interface_mc(P, [0.5], [0.5], N, dt=1e-5, Dt=K * 1e-5, exit_mode=2, record=True)
+    assert r["n_exit"][0] == 0
+    steps = r["steps"].astype(np.float64)
+    assert abs(steps.mean() - (K + 1)) < 4 * math.sqrt(K / N), steps.mean()
+    assert abs(steps.var() - K) < 0.1 * K, steps.var()   # Poisson: variance = mean - 1 here
+    # a linear field is preserved exactly whatever the step lengths (zero drift, symmetric increments)
+    assert abs(r["mean_xi"][0] - 0.5) < 4 * r["se_xi"][0] + 1e-12
