@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-cv", action="store_true", help="skip the control-variate measurement of the default workload")
     ap.add_argument("--paths", type=int, default=None)
-    ap.add_argument("--workload", choices=["front257", "batch64", "ring2049", "heat65", "cv65", "ring41"],
+    ap.add_argument("--workload", choices=["front257", "batch64", "ring2049", "heat65", "cv65", "ring41", "exit65"],
                     default="front257")
     ap.add_argument("--key-spacing", type=int, default=8,
                     help="ring41: key points plus every k-th node (k > 0), key points only (0), every node (-1)")
@@ -580,6 +580,65 @@ def run_ring41(args, world, rank, local):
         }), flush=True)
 
 
+def run_exit65(args, world, rank, local):
+    """Exit tests at equal accuracy on the w = 1 heat problem (65 x 65, 31 interior nodes on x = 1/2,
+    Dt = 0.05, closed form exp(-2 pi^2 t) sin(pi x) sin(pi y)): the RMS error and the time of the
+    estimate with 2e6 paths per node for the paper's fixed-step test, the Brownian-bridge test and
+    exponential time-stepping over a range of dt. Value: path-steps per second of the fixed-step
+    test matched at the bridge test's error (the fixed-step test's error falls like sqrt(dt))."""
+    import torch
+
+    import paper_1402_0266_gb300 as sdd
+    from paper_1402_0266_gb300 import build as b
+    b.build()
+    torch.cuda.set_device(local)
+    n, Dt, N = 65, 0.05, 2_000_000
+    xi0, eta0 = W.heat65_fields()
+    ctx = sdd.sdd_init(n, n, 2, 1, w=torch.from_numpy(W.w_const(n)).cuda(), xi0=torch.from_numpy(xi0).cuda(),
+                       eta0=torch.from_numpy(eta0).cuda())
+    sdd.sdd_set_boundary(ctx, torch.zeros(8 * n, dtype=torch.float64, device="cuda"))
+    xs, ys = W.heat65_nodes()
+    xs, ys = xs[1:32], ys[1:32]
+    ex, ee = W.heat_exact(xs, ys, Dt)
+    rows = []
+    for mode in (0, 1, 2):
+        for dt in (1e-2, 2.5e-3, 1e-3, 2.5e-4):
+            for k in range(args.warmup if not rows else 0):
+                sdd.sdd_interface_mc(ctx, xs, ys, np.full(xs.size, N), dt=dt, Dt=Dt, seed=99, exit_mode=mode)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            o = sdd.sdd_interface_mc(ctx, xs, ys, np.full(xs.size, N), dt=dt, Dt=Dt, seed=3, exit_mode=mode)
+            e1.record()
+            torch.cuda.synchronize()
+            o = {k: v.cpu().numpy() for k, v in o.items()}
+            err = np.concatenate([o["mean_xi"] - ex, o["mean_eta"] - ee])
+            rows.append({"exit_mode": mode, "dt": dt, "rms_error": float(math.sqrt(np.mean(err ** 2))),
+                         "mean_se": float(np.mean(np.concatenate([o["se_xi"], o["se_eta"]]))),
+                         "ms": e0.elapsed_time(e1), "path_steps": int(o["path_steps"].sum())})
+    plain = [r for r in rows if r["exit_mode"] == 0]
+    bridge = [r for r in rows if r["exit_mode"] == 1 and r["dt"] == 1e-2][0]
+    # fixed-step error c sqrt(dt), c from the smallest dt measured; dt needed for the bridge test's error
+    c = plain[-1]["rms_error"] / math.sqrt(plain[-1]["dt"])
+    dt_eq = (bridge["rms_error"] / c) ** 2
+    steps_eq = plain[-1]["path_steps"] * plain[-1]["dt"] / dt_eq
+    rate_plain = plain[-1]["path_steps"] / (plain[-1]["ms"] / 1e3)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "path-steps/s at equal exit accuracy (fixed-step test matched at the bridge test's error)",
+            "value": steps_eq / (bridge["ms"] / 1e3), "unit": UNIT, "n_gpus": world, "steps": 1,
+            "warmup": args.warmup, "ms_per_step": bridge["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "exit65: w=1 heat problem on 65x65, 31 interior nodes on x=1/2, Dt=0.05, 2e6 paths "
+                                   "per node; exit modes 0 (fixed steps, plain test), 1 (bridge test), 2 (exponential "
+                                   "time-stepping) at dt = 1e-2 .. 2.5e-4"},
+            "dt_fixed_step_for_bridge_error": dt_eq, "fixed_step_path_steps_per_s": rate_plain,
+            "speedup_at_equal_error": (plain[-1]["ms"] * plain[-1]["dt"] / dt_eq) / bridge["ms"],
+            "runs": rows,
+        }), flush=True)
+
+
 def run_ring2049(args, world, rank, local):
     """The large ring workload: mesh steps on 2049 x 2049 with 8 x 8 subdomains."""
     import torch
@@ -667,6 +726,10 @@ def main():
     if args.workload == "ring2049" and args.impl == "ours":
         world, rank, local = dist_init()
         run_ring2049(args, world, rank, local)
+        return
+    if args.workload == "exit65" and args.impl == "ours":
+        world, rank, local = dist_init()
+        run_exit65(args, world, rank, local)
         return
     if args.workload == "ring41" and args.impl == "ours":
         world, rank, local = dist_init()

@@ -106,7 +106,14 @@ typedef struct {
  *   step_index  mesh step number n, the last word of the Philox counter
  *               (counter = (path, node, draw, n)).
  *   exit_mode   0: the paper's boundary test after every sub-step;
- *               1: that test plus a Brownian-bridge test between sub-steps.
+ *               1: that test plus a Brownian-bridge test between sub-steps;
+ *               2: exponential time-stepping, the alternative Sec. 4 names:
+ *                  sub-step j lasts tau_j = -dt ln u (u from word 3 of the
+ *                  sub-step's Philox block (path, node, j, n): (2^23 - m)
+ *                  2^-23, m its low 23 bits), the last one cut at the end
+ *                  of the mesh step (and after 4K + 16 sub-steps); normals
+ *                  scaled by sqrt(2 tau_j); both tests over tau_j. Not with
+ *                  the control variate (SDD_EINVAL).
  *   block_threads, paths_per_task: launch shape; 0 picks the tuned default.
  *               block_threads in {64, 128, 256, 512}; paths_per_task a
  *               multiple of 32. */

@@ -271,7 +271,7 @@ bool valid_params(sdd_ctx* c, double dt, double Dt, int exit_mode, int* K)
     const double k = Dt / dt;
     const double kr = std::round(k);
     if (kr < 1.0 || kr > (double)(1 << 20) || std::fabs(kr - k) > 1e-9 * k) return false;
-    if (exit_mode != 0 && exit_mode != 1) return false;
+    if (exit_mode != 0 && exit_mode != 1 && exit_mode != 2) return false;
     *K = (int)kr;
     (void)c;
     return true;
@@ -549,6 +549,7 @@ sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const Out
         a.dt = (float)dt;
         a.bm_scale = (float)(-4.0 * dt * std::log(2.0));
         a.bridge_cut = (float)(18.0 * dt);
+        a.horizon = (float)((double)K * dt);
         a.keys = philox_keys(seed);
         a.step_index = step_index;
         a.step_ptr = step_ptr;
@@ -556,6 +557,8 @@ sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const Out
         a.node_mask = node_mask;
         const bool cv = cv_slices > 0;
         if (cv && cv_slices > K) return fail(err, SDD_EINVAL, "more control-variate slices than sub-steps per step");
+        if (cv && exit_mode == 2)
+            return fail(err, SDD_EINVAL, "the control variate needs fixed sub-steps (exit_mode 0 or 1)");
         for (int q = 0; q <= kMaxCvSlices; ++q)
             a.cv_bound[q] = cv && q <= cv_slices ? (int32_t)(((int64_t)q * K + cv_slices - 1) / cv_slices) : K + 1;
         CU(err, cudaMemsetAsync(P.d_queue.p, 0, sizeof(int), s));

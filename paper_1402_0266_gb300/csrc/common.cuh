@@ -94,6 +94,7 @@ struct PathArgs {
     float dt;
     float bm_scale;          // -4 dt ln 2: r = sqrt(bm_scale * log2(u1)) = sqrt(2 dt) sqrt(-2 ln u1)
     float bridge_cut;        // skip the bridge test when dmin0 * dmin1 exceeds this
+    float horizon;           // the mesh step K dt (exponential time-stepping)
     PhiloxKeys keys;         // round keys of the seed
     int32_t cv_bound[kMaxCvSlices + 1];  // control variate: slice q serves sub-steps cv_bound[q] <= j < cv_bound[q + 1]
     uint32_t step_index;

@@ -440,6 +440,142 @@ __global__ void __launch_bounds__(CV ? kCvMaxBlock : 512, CV ? 3 : 2) k_paths(co
     }
 }
 
+// Exponential time-stepping (exit_mode 2), the alternative integrator Sec. 4
+// names: sub-step j of a path has length tau_j = -dt ln u with u = (2^23 - m)
+// 2^-23 from word 3 of the block (path, node, j, step), cut at the end of the
+// mesh step (and after 4K + 16 sub-steps); normals from words 0, 1 scaled by
+// sqrt(2 tau_j); the plain test, then the Brownian-bridge test over tau_j with
+// the uniform of word 2. No software pipelining: one block per sub-step.
+template <bool RECORD>
+__global__ void __launch_bounds__(512, 2) k_paths_exp(const PathArgs a)
+{
+    __shared__ int s_group;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const unsigned below = (1u << lane) - 1u;
+    const uint32_t step = a.step_ptr ? *a.step_ptr : a.step_index;
+    const int K = a.K;
+    const int cap = 4 * K + 16;
+    const float T = a.horizon;
+    const float ln2dt = a.dt * 0.69314718055994530942f;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_group = atomicAdd(a.queue, nwarps);
+        __syncthreads();
+        const int group = s_group;
+        if (group >= a.ntasks) return;
+        const int t = group + warp;
+        if (t >= a.ntasks) continue;
+        const Task task = a.tasks[t];
+        if (a.node_mask && !a.node_mask[task.node]) continue;
+        const NodeDev& nd = a.nodes[task.node];
+        const InstDev I = a.inst[nd.inst];
+        const float x0 = nd.xf, y0 = nd.yf;
+        const uint32_t nctr = nd.ctr;
+        const int end = task.path0 + task.npaths;
+        int next = task.path0 + 32;
+        int path = task.path0 + lane;
+        bool alive = path < end;
+        float2 pos = f2(x0, y0);
+        int j = 0;
+        float tm = 0.f;
+        Acc ax{0.f, 0.f, 0.f, 0.f}, ae{0.f, 0.f, 0.f, 0.f};
+        int exits = 0, steps = 0;
+        while (__any_sync(FULL, alive)) {
+            if (alive) {
+                uint4 r = make_uint4((uint32_t)path, nctr, (uint32_t)j, step);
+                philox_rounds_rk<0, 10>(r, a.keys);
+                const float u3 = 2.0f - __uint_as_float(0x3F800000u | (r.w & 0x7FFFFFu));
+                float tau = -ln2dt * __log2f(u3);
+                bool last = false;
+                if (tm + tau >= T || j + 1 >= cap) {
+                    tau = T - tm;
+                    last = true;
+                }
+                float2 z;
+                box_muller(r.x, r.y, -2.77258872223978123767f * tau, z.x, z.y);   // -4 ln 2 tau: sqrt(2 tau) N(0,1)
+                const float ub = uniform_pos(r.z);
+                const Cell c = locate(I, I.bcoef, pos);
+                float4 g0, g1;
+                load_cell(c.p, g0, g1);
+                const float2 pn = em(g0, g1, c.st, pos, f2(tau, tau), z);
+                bool done = false;
+                int code = -1;
+                float yxi = 0.f, yeta = 0.f, xe = 0.f, ye = 0.f;
+                if (!inside2(pn)) {
+                    plain_exit(I, pos.x, pos.y, pn.x, pn.y, code, yxi, yeta, xe, ye);
+                    done = true;
+                } else {
+                    const float dm0 = fminf(fminf(pos.x, 1.0f - pos.x), fminf(pos.y, 1.0f - pos.y));
+                    const float dm1 = fminf(fminf(pn.x, 1.0f - pn.x), fminf(pn.y, 1.0f - pn.y));
+                    if (dm0 * dm1 < 18.0f * tau && bridge_exit(I, pos.x, pos.y, pn.x, pn.y, tau, ub, code, yxi, yeta, xe, ye)) {
+                        code += 4;
+                        done = true;
+                    } else {
+                        pos = pn;
+                        tm += tau;
+                        if (last) done = true;
+                    }
+                }
+                ++j;
+                if (done) {
+                    if (code < 0) {
+                        const Cell cf = locate(I, I.fcoef, pos);
+                        float4 f0, f1;
+                        load_cell(cf.p, f0, f1);
+                        const float2 v = eval2(f0, f1, cf.st);
+                        yxi = v.x;
+                        yeta = v.y;
+                        xe = pos.x;
+                        ye = pos.y;
+                    } else {
+                        ++exits;
+                    }
+                    ax.add(yxi - x0);
+                    ae.add(yeta - y0);
+                    steps += j;
+                    if (RECORD) {
+                        const long long ri = nd.rec0 + path;
+                        if (a.rec.steps) a.rec.steps[ri] = j;
+                        if (a.rec.code) a.rec.code[ri] = code;
+                        if (a.rec.score_xi) a.rec.score_xi[ri] = yxi;
+                        if (a.rec.score_eta) a.rec.score_eta[ri] = yeta;
+                        if (a.rec.x_end) a.rec.x_end[ri] = xe;
+                        if (a.rec.y_end) a.rec.y_end[ri] = ye;
+                    }
+                    alive = false;
+                }
+            }
+            const unsigned need = __ballot_sync(FULL, !alive);
+            if (need != 0u && next < end) {
+                const int cand = next + __popc(need & below);
+                if (!alive && cand < end) {
+                    path = cand;
+                    alive = true;
+                    pos = f2(x0, y0);
+                    j = 0;
+                    tm = 0.f;
+                }
+                next += __popc(need);
+            }
+        }
+        const double sx = warp_sum(ax.sum()), qx = warp_sum(ax.sumsq());
+        const double se = warp_sum(ae.sum()), qe = warp_sum(ae.sumsq());
+        const long long ex = warp_sum_ll(exits), st = warp_sum_ll(steps);
+        if (lane == 0) {
+            Partial p;
+            p.s_xi = sx;
+            p.q_xi = qx;
+            p.s_eta = se;
+            p.q_eta = qe;
+            p.exits = ex;
+            p.steps = st;
+            a.partials[t] = p;
+        }
+    }
+}
+
 __device__ __forceinline__ double face_value64(const InstDev& I, int field, int face, double s)
 {
     const int n = (face < 2) ? I.ny : I.nx;
@@ -577,6 +713,7 @@ const void* kernel_ptr()
 template <bool CV>
 const void* pick_cv(int mode, bool record)
 {
+    if (mode == 3) return record ? (const void*)k_paths_exp<true> : (const void*)k_paths_exp<false>;
     if (mode == 0) return record ? kernel_ptr<0, true, CV>() : kernel_ptr<0, false, CV>();
     if (mode == 2) return record ? kernel_ptr<2, true, CV>() : kernel_ptr<2, false, CV>();
     return record ? kernel_ptr<1, true, CV>() : kernel_ptr<1, false, CV>();
@@ -590,13 +727,17 @@ int path_kernel_blocks_per_sm(int exit_mode, bool record, int block, bool cv)
 {
     int n = 0;
     // the even-K kernel has the same footprint class; size the grid for the larger of the two
-    const int mode = exit_mode == 1 ? 1 : 0;
+    const int mode = exit_mode == 2 ? 3 : exit_mode == 1 ? 1 : 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(mode, record, cv), block, 0) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
 }
 
-static int kernel_mode(int exit_mode, int K) { return exit_mode == 1 ? 1 : ((K & 1) == 0 ? 2 : 0); }
+static int kernel_mode(int exit_mode, int K)
+{
+    if (exit_mode == 2) return 3;   // exponential time-stepping
+    return exit_mode == 1 ? 1 : ((K & 1) == 0 ? 2 : 0);
+}
 
 // The path kernel keeps no data in shared memory: give L1 the whole carveout.
 static void prefer_l1()
@@ -604,7 +745,7 @@ static void prefer_l1()
     static bool done = false;
     if (done) return;
     done = true;
-    for (int mode : {0, 1, 2})
+    for (int mode : {0, 1, 2, 3})
         for (bool rec : {false, true})
             for (bool cv : {false, true})
                 cudaFuncSetAttribute(pick(mode, rec, cv), cudaFuncAttributePreferredSharedMemoryCarveout, 0);
@@ -615,6 +756,10 @@ template <bool CV>
 static void launch_mode(const PathArgs& a, int mode, bool record, int grid, int block, cudaStream_t s)
 {
     switch (mode) {
+    case 3:
+        if (record) k_paths_exp<true><<<grid, block, 0, s>>>(a);
+        else k_paths_exp<false><<<grid, block, 0, s>>>(a);
+        break;
     case 0:
         if (record) k_paths<0, true, CV><<<grid, block, 0, s>>>(a);
         else k_paths<0, false, CV><<<grid, block, 0, s>>>(a);

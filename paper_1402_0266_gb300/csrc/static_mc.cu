@@ -107,7 +107,7 @@ sdd_status sdd_interface_mc_static(const sdd_fields* f, const sdd_nodes* nodes, 
     if (!(p->dt > 0.0) || !(p->Dt > 0.0) || !std::isfinite(p->dt) || !std::isfinite(p->Dt)) return SDD_EINVAL;
     const double kq = p->Dt / p->dt, kr = std::round(kq);
     if (kr < 1.0 || kr > (double)(1 << 20) || std::fabs(kr - kq) > 1e-9 * kq) return SDD_EINVAL;
-    if (p->exit_mode != 0 && p->exit_mode != 1) return SDD_EINVAL;
+    if (p->exit_mode != 0 && p->exit_mode != 1 && p->exit_mode != 2) return SDD_EINVAL;
     if (p->paths_per_task < 0 || (p->paths_per_task % 32) != 0) return SDD_EINVAL;
     const int block = p->block_threads ? p->block_threads : 256;
     if (block != 64 && block != 128 && block != 256 && block != 512) return SDD_EINVAL;
@@ -221,6 +221,7 @@ sdd_status sdd_interface_mc_static(const sdd_fields* f, const sdd_nodes* nodes, 
         a.dt = (float)p->dt;
         a.bm_scale = (float)(-4.0 * p->dt * std::log(2.0));
         a.bridge_cut = (float)(18.0 * p->dt);
+        a.horizon = (float)((double)a.K * p->dt);
         a.keys = philox_keys(p->seed);
         a.step_index = p->step_index;
         a.step_ptr = nullptr;

@@ -23,12 +23,12 @@ def compare_records(g, o):
     return same, rep
 
 
-def assert_records(g, o):
+def assert_records(g, o, score_tol=PATH_TOL):
     same, rep = compare_records(g, o)
     assert rep["agree_frac"] >= EXIT_AGREEMENT, rep
     for k in ("score_xi", "score_eta", "x_end", "y_end"):
         if "max_" + k in rep:
-            assert rep["max_" + k] <= PATH_TOL, rep
+            assert rep["max_" + k] <= (score_tol if k.startswith("score") else PATH_TOL), rep
     return same, rep
 
 
