@@ -178,7 +178,7 @@ def test_host_side_rejections(sdd):
     with pytest.raises(sdd.SddError):
         sdd.sdd_interface_mc(ctx, [0.5], [0.5], [0], dt=1e-3, Dt=1e-2)     # no paths
     with pytest.raises(sdd.SddError):
-        sdd.sdd_interface_mc(ctx, [0.5], [0.5], [10], dt=1e-3, Dt=1e-2, exit_mode=2)
+        sdd.sdd_interface_mc(ctx, [0.5], [0.5], [10], dt=1e-3, Dt=1e-2, exit_mode=3)    # no such exit test
     with pytest.raises(sdd.SddError):
         sdd.sdd_interface_mc(ctx, [0.5], [0.5], [10], dt=1e-3, Dt=1e-2, paths_per_task=48)
     sdd.sdd_sync(ctx)
