@@ -439,7 +439,19 @@ int32_t sdd_solver_in_use(const sdd_ctx* ctx);
  * values, then xi, eta advance and the step counter n (the Philox counter's
  * last word) increases by one. The sequence is recorded once into a CUDA
  * graph and replayed while the parameters stay the same. The interface
- * statistics of the step can be read with sdd_last_interface_stats. */
+ * statistics of the step can be read with sdd_last_interface_stats.
+ *
+ * Pipelining: where the subdomain solve's iterations are one kernel launch
+ * (the cluster multigrid or Jacobi-PCG kernels) and the paths do not read the
+ * fields (no SDD_CV_FIELDS), the iterations of step n's solve run inside step
+ * n + 1's graph, beside its paths; the paths that survive step n + 1 are
+ * scored once they are done. Every call that reads or writes the fields
+ * (sdd_get_fields, sdd_set_fields, sdd_interface_mc, sdd_subdomain_solve,
+ * sdd_cv_samples, sdd_cv_train, sdd_autotune, sdd_sync, the batch calls) or
+ * changes the step's parameters first enqueues the pending iterations, and
+ * sdd_flush does so alone. The results are those of the unpipelined
+ * sequence; only the order of the floating-point sums over a task's paths
+ * differs. */
 typedef struct {
     double dt;
     double Dt;
@@ -466,7 +478,8 @@ typedef struct {
                               and the kernels its solver loops ran)                */
     float paths_ms;        /* the path kernel                                    */
     float estimate_ms;     /* the whole interface estimate (tables, paths, means) */
-    float solve_ms;        /* the subdomain solves                               */
+    float solve_ms;        /* the subdomain solves (pipelined: this step's set-up and
+                              the previous step's iterations, run beside the paths) */
     float step_ms;         /* the whole step                                     */
 } sdd_step_info;
 
@@ -476,8 +489,20 @@ sdd_status sdd_last_step_info(sdd_ctx* ctx, sdd_step_info* out);
 sdd_status sdd_set_step_index(sdd_ctx* ctx, uint32_t n);
 uint32_t sdd_get_step_index(const sdd_ctx* ctx);
 
-/* Wait for the context stream and return the first device-side error since
- * the last sdd_sync (SDD_EDEVICE, SDD_ENOCONV, SDD_ETIMEOUT) or SDD_OK. */
+/* Allow (on != 0, the default) or forbid pipelined mesh steps; enqueues any
+ * pending iterations first. sdd_pipeline_in_use: 1 if the current step graphs
+ * are pipelined (known after the first sdd_step with these parameters). */
+sdd_status sdd_set_pipeline(sdd_ctx* ctx, int32_t on);
+int32_t sdd_pipeline_in_use(const sdd_ctx* ctx);
+
+/* Enqueue the pending iterations of the last pipelined mesh step's solve
+ * (asynchronous, on the context stream; SDD_OK when none is pending). After
+ * it the fields of the last step are complete once the stream reaches it. */
+sdd_status sdd_flush(sdd_ctx* ctx);
+
+/* Enqueue any pending solve (sdd_flush), wait for the context stream and
+ * return the first device-side error since the last sdd_sync (SDD_EDEVICE,
+ * SDD_ENOCONV, SDD_ETIMEOUT) or SDD_OK. */
 sdd_status sdd_sync(sdd_ctx* ctx);
 
 /* Last error message of the context (static storage until the next call). */

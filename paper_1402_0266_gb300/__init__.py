@@ -31,7 +31,7 @@ EXPORTS = [
     "sdd_get_fields", "sdd_get_fields_host", "sdd_interface_mc", "sdd_interface_mc_record", "sdd_interface_nodes",
     "sdd_subdomain_solve", "sdd_step", "sdd_last_interface_stats", "sdd_last_step_info", "sdd_set_step_index",
     "sdd_get_step_index",
-    "sdd_sync", "sdd_last_error", "sdd_destroy", "sdd_rng_draw", "sdd_interface_mc_static",
+    "sdd_sync", "sdd_flush", "sdd_set_pipeline", "sdd_pipeline_in_use", "sdd_last_error", "sdd_destroy", "sdd_rng_draw", "sdd_interface_mc_static",
     "sdd_static_scratch_bytes", "sdd_batch_create", "sdd_batch_interface_mc", "sdd_batch_step",
     "sdd_batch_last_step_info", "sdd_batch_set_step_index", "sdd_batch_sync", "sdd_batch_last_error",
     "sdd_batch_destroy", "sdd_autotune", "sdd_batch_autotune", "sdd_cv_set_table", "sdd_cv_enable",
@@ -153,6 +153,8 @@ def lib():
                 "sdd_set_step_index": [vp, u32],
                 "sdd_get_step_index": [vp],
                 "sdd_sync": [vp],
+                "sdd_flush": [vp],
+                "sdd_set_pipeline": [vp, ctypes.c_int32],
                 "sdd_last_error": [vp],
                 "sdd_destroy": [vp],
                 "sdd_rng_draw": [u64, vp, i64, vp, vp, vp],
@@ -186,6 +188,7 @@ def lib():
                 "sdd_set_keypoints": [vp, i32, i32],
                 "sdd_keypoint_mask": [vp, vp],
                 "sdd_solver_in_use": [vp],
+                "sdd_pipeline_in_use": [vp],
                 "sdd_batch_autotune": [vp, ctypes.POINTER(_Nodes), ctypes.POINTER(_McParams), ctypes.POINTER(_Shape)],
             }
             for name, args in sig.items():
@@ -427,6 +430,20 @@ def sdd_set_step_index(ctx: Ctx, n: int):
 
 def sdd_get_step_index(ctx: Ctx) -> int:
     return int(lib().sdd_get_step_index(ctx.handle))
+
+
+def sdd_set_pipeline(ctx: Ctx, on: bool):
+    """Allow or forbid pipelined mesh steps (the solve beside the next step's paths)."""
+    ctx._check(lib().sdd_set_pipeline(ctx.handle, 1 if on else 0))
+
+
+def sdd_pipeline_in_use(ctx: Ctx) -> bool:
+    return bool(lib().sdd_pipeline_in_use(ctx.handle))
+
+
+def sdd_flush(ctx: Ctx):
+    """Enqueue the pending iterations of the last pipelined step's solve."""
+    ctx._check(lib().sdd_flush(ctx.handle))
 
 
 def sdd_sync(ctx: Ctx):

@@ -81,6 +81,16 @@ struct GraphSlot {
     }
 };
 
+// One implicit subdomain step: the kernels' arguments and the solver choice,
+// fixed when its set-up is enqueued (the iterations may run later).
+struct SolveCall {
+    SolveArgs a{};
+    MgArgs m{};
+    bool use_mg = false;
+    int mgc_upt = 0, mgc_C = 0, mgc_rows = 0;
+    size_t mgc_smem = 0;
+};
+
 }  // namespace
 
 struct sdd_ctx {
@@ -163,6 +173,21 @@ struct sdd_ctx {
     sdd_step_params graph_params{};
     bool graph_ok = false;
     uint32_t step_index = 0;
+
+    // Pipelined mesh steps: the iterations of step n's subdomain solve run in
+    // step n + 1's graph beside its paths, whose survivors are scored once the
+    // solve is done. graph_p[parity] begins with the pending iterations.
+    bool pipe_allowed = true;       // sdd_set_pipeline
+    bool pipe = false;              // the step graphs defer the iterations
+    bool pending = false;           // iterations of the last step not enqueued yet
+    SolveCall step_call[2];         // the solve set up by graph[parity] / graph_p[parity]
+    SolveCall pend_call;
+    GraphSlot graph_p[2];
+    int graph_kernels_p = 0;
+    bool last_had_pending = false;  // the last launched graph ran deferred iterations
+    DevBuf<float4> surv;            // survivor end records of the step's paths
+    cudaStream_t pipe_stream = nullptr;
+    cudaEvent_t pev[4] = {nullptr, nullptr, nullptr, nullptr};  // fork, join, iterations start, end
 
     std::string err;
 };
@@ -251,18 +276,38 @@ sdd_status upload_inst(sdd_ctx* c)
 int64_t faces_len(const sdd_ctx* c) { return 2LL * (2LL * c->nx + 2LL * c->ny); }
 
 // Field tables for the current w, fields and face data (enqueued on s).
-sdd_status prepare(sdd_ctx* c, cudaStream_t s)
+// The tables of the current w (faces, drift records) and fields (field
+// records) on stream s, where they changed since they were last built.
+sdd_status prepare_parts(sdd_ctx* c, cudaStream_t s, bool w_part, bool f_part)
 {
-    if (c->dirty_w && !c->user_faces) {
+    const bool dw = w_part && c->dirty_w, df = f_part && c->dirty_fields;
+    if (dw && !c->user_faces) {
         CU(c, launch_winslow_faces(c->w.p, c->nx, c->ny, c->faces64.p, s));
         CU(c, launch_faces32(c->faces64.p, c->faces32.p, (int)faces_len(c), s));
     }
-    if (c->dirty_w || c->dirty_fields) {
+    if (dw || df) {
+        CU(c, launch_prep_cells(c->w.p, c->fld[c->cur][0].p, c->fld[c->cur][1].p, c->nx, c->ny,
+                                dw ? c->bcoef.p : nullptr, df ? c->fcoef.p : nullptr, c->d_status.p, s));
+    }
+    if (w_part) c->dirty_w = false;
+    if (f_part) c->dirty_fields = false;
+    return SDD_OK;
+}
+
+sdd_status prepare(sdd_ctx* c, cudaStream_t s)
+{
+    if (c->dirty_w && c->dirty_fields) {
+        // both record sets in one pass
+        if (!c->user_faces) {
+            CU(c, launch_winslow_faces(c->w.p, c->nx, c->ny, c->faces64.p, s));
+            CU(c, launch_faces32(c->faces64.p, c->faces32.p, (int)faces_len(c), s));
+        }
         CU(c, launch_prep_cells(c->w.p, c->fld[c->cur][0].p, c->fld[c->cur][1].p, c->nx, c->ny, c->bcoef.p,
                                 c->fcoef.p, c->d_status.p, s));
+        c->dirty_w = c->dirty_fields = false;
+        return SDD_OK;
     }
-    c->dirty_w = c->dirty_fields = false;
-    return SDD_OK;
+    return prepare_parts(c, s, true, true);
 }
 
 bool valid_params(sdd_ctx* c, double dt, double Dt, int exit_mode, int* K)
@@ -445,7 +490,7 @@ uint64_t shape_key(const std::vector<NodeSeg>& segs, int K, int exit_mode)
 sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const OutDev* outs, const OutDev& out0, double dt,
                        int K, uint64_t seed, uint32_t step_index, const uint32_t* step_ptr, int exit_mode,
                        const RecDev* rec, cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_b, int cv_slices = 0,
-                       const uint8_t* node_mask = nullptr);
+                       const uint8_t* node_mask = nullptr, void* surv = nullptr, cudaEvent_t join = nullptr);
 
 const TunedShape* find_tuned(const std::vector<TunedShape>& t, uint64_t key)
 {
@@ -530,13 +575,20 @@ sdd_status build_plan(sdd_ctx* c, Plan& P, const double* x, const double* y, con
 }
 
 // Enqueue the estimate for a built plan. inst: the instance table; outs:
-// per-instance outputs (null: every node writes to out0).
+// per-instance outputs (null: every node writes to out0). surv: if non-null,
+// the survivors' scores are deferred to a second kernel that runs once event
+// `join` (if non-null) has completed: P.total_paths records of float2, or of
+// float4 with the control variate.
 sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const OutDev* outs, const OutDev& out0, double dt,
                        int K, uint64_t seed, uint32_t step_index, const uint32_t* step_ptr, int exit_mode,
                        const RecDev* rec, cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_b, int cv_slices,
-                       const uint8_t* node_mask)
+                       const uint8_t* node_mask, void* surv, cudaEvent_t join)
 {
-    if (P.nnodes == 0) return SDD_OK;
+    if (surv && rec) return fail(err, SDD_EINVAL, "per-path records with deferred survivor scores");
+    if (P.nnodes == 0 || P.ntasks == 0) {
+        if (join) CU(err, cudaStreamWaitEvent(s, join, 0));
+        if (P.nnodes == 0) return SDD_OK;
+    }
     if (P.ntasks > 0) {
         PathArgs a{};
         a.inst = inst;
@@ -555,6 +607,7 @@ sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const Out
         a.step_ptr = step_ptr;
         if (rec) a.rec = *rec;
         a.node_mask = node_mask;
+        a.surv = surv;
         const bool cv = cv_slices > 0;
         if (cv && cv_slices > K) return fail(err, SDD_EINVAL, "more control-variate slices than sub-steps per step");
         if (cv && exit_mode == 2)
@@ -576,6 +629,18 @@ sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const Out
         if (ev_a) CU(err, cudaEventRecordWithFlags(ev_a, s, cudaEventRecordExternal));
         CU(err, launch_paths(a, exit_mode, rec != nullptr, grid, block, s, cv));
         if (ev_b) CU(err, cudaEventRecordWithFlags(ev_b, s, cudaEventRecordExternal));
+        if (join) CU(err, cudaStreamWaitEvent(s, join, 0));
+        if (surv) {
+            ScoreArgs sa{};
+            sa.inst = inst;
+            sa.nodes = P.d_nodes.p;
+            sa.tasks = P.d_tasks.p;
+            sa.partials = P.d_partials.p;
+            sa.surv = surv;
+            sa.ntasks = (int32_t)P.ntasks;
+            sa.node_mask = node_mask;
+            CU(err, launch_score_surv(sa, cv, s));
+        }
     }
     FinalArgs f{};
     f.inst = inst;
@@ -592,10 +657,11 @@ sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const Out
 
 sdd_status run_plan(sdd_ctx* c, Plan& P, double dt, int K, uint64_t seed, uint32_t step_index,
                     const uint32_t* step_ptr, int exit_mode, const OutDev& out, const RecDev* rec, cudaStream_t s,
-                    cudaEvent_t ev_a = nullptr, cudaEvent_t ev_b = nullptr, const uint8_t* node_mask = nullptr)
+                    cudaEvent_t ev_a = nullptr, cudaEvent_t ev_b = nullptr, const uint8_t* node_mask = nullptr,
+                    void* surv = nullptr, cudaEvent_t join = nullptr)
 {
     return run_plan_on(&c->err, P, c->d_inst.p, nullptr, out, dt, K, seed, step_index, step_ptr, exit_mode, rec, s,
-                       ev_a, ev_b, c->cv_mode ? c->cv_slices : 0, node_mask);
+                       ev_a, ev_b, c->cv_mode ? c->cv_slices : 0, node_mask, surv, join);
 }
 
 // Launch shape for a plan: explicit requests win, else a tuned shape for this node set, else the heuristic.
@@ -791,18 +857,10 @@ bool mg_auto(const sdd_ctx* c)
     return c->solve_upt == 0 || (long long)c->mg.mx[0] * c->mg.my[0] >= 10000;
 }
 
-// The implicit subdomain step on stream s: Dirichlet data from the faces and the
-// interface values, then the batched PCG. xo/eo receive the new fields.
-sdd_status enqueue_solve(sdd_ctx* c, double Dt, const double* ix, const double* ie, double rtol, int max_iter,
-                         double* xo, double* eo, cudaStream_t s)
+SolveCall make_solve_call(sdd_ctx* c, double Dt, double rtol, int max_iter, double* xo, double* eo)
 {
-    const double* px = c->fld[c->cur][0].p;
-    const double* pe = c->fld[c->cur][1].p;
-    CU(c, launch_solve_setup(c->w.p, px, pe, c->nx, c->ny, Dt, c->cx.p, c->cy.p, c->dg.p, c->rhs0.p, c->cxf.p,
-                             c->cyf.p, c->dgf.p, c->dinvf.p, s));
-    CU(c, launch_dirichlet(c->faces64.p, px, pe, ix, ie, c->d_iface_idx.p, (int)c->iface_idx.size(), c->nx, c->ny,
-                           xo, eo, s));
-    SolveArgs a{};
+    SolveCall k;
+    SolveArgs& a = k.a;
     a.nx = c->nx;
     a.ny = c->ny;
     a.cx = c->cx.p;
@@ -830,9 +888,10 @@ sdd_status enqueue_solve(sdd_ctx* c, double Dt, const double* ix, const double* 
     a.inner_tol = 1e-4f;
     a.iters = c->d_iters.p;
     a.status = c->d_status.p;
-    const bool use_mg = c->mg_ok && (c->solver == 2 || (c->solver == 0 && mg_auto(c)));
-    if (use_mg) {
-        MgArgs m = c->mg;
+    k.use_mg = c->mg_ok && (c->solver == 2 || (c->solver == 0 && mg_auto(c)));
+    if (k.use_mg) {
+        MgArgs& m = k.m;
+        m = c->mg;
         m.nx = c->nx;
         m.ny = c->ny;
         m.cx = c->cx.p;
@@ -878,41 +937,90 @@ sdd_status enqueue_solve(sdd_ctx* c, double Dt, const double* ix, const double* 
         m.max_iter = max_iter;
         m.rtol = rtol;
         m.inner_tol = 1e-5f;
-        CU(c, launch_mg_setup(m, s));
+        k.mgc_upt = mgc_config(m, &k.mgc_C, &k.mgc_rows, &k.mgc_smem);
+        if (k.mgc_upt > 0) m.outer = 8;
+    }
+    return k;
+}
+
+// The iterations are one kernel launch (the cluster multigrid solve or the
+// Jacobi-PCG kernels), so they can run beside other work.
+bool solve_single_launch(const SolveCall& k) { return !k.use_mg || k.mgc_upt > 0; }
+
+// The set-up of an implicit subdomain step on stream s: the system from w and
+// the fields of the step's start, the Dirichlet data from the faces and the
+// interface values (written into the new fields), the multigrid hierarchy.
+// Nothing after it reads w, the faces or the interface values.
+sdd_status enqueue_solve_setup(sdd_ctx* c, const SolveCall& k, double Dt, const double* ix, const double* ie,
+                               cudaStream_t s)
+{
+    const double* px = c->fld[c->cur][0].p;
+    const double* pe = c->fld[c->cur][1].p;
+    CU(c, launch_solve_setup(c->w.p, px, pe, c->nx, c->ny, Dt, c->cx.p, c->cy.p, c->dg.p, c->rhs0.p, c->cxf.p,
+                             c->cyf.p, c->dgf.p, c->dinvf.p, s));
+    CU(c, launch_dirichlet(c->faces64.p, px, pe, ix, ie, c->d_iface_idx.p, (int)c->iface_idx.size(), c->nx, c->ny,
+                           k.a.x[0], k.a.x[1], s));
+    if (k.use_mg) CU(c, launch_mg_setup(k.m, s));
+    return SDD_OK;
+}
+
+// The iterations of the implicit subdomain step on stream s: the new fields.
+sdd_status enqueue_solve_iterate(sdd_ctx* c, const SolveCall& k, cudaStream_t s)
+{
+    if (k.use_mg) {
+        MgArgs m = k.m;
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         CU(c, cudaStreamIsCapturing(s, &cs));
-        int C = 0, rows_max = 0;
-        size_t smem = 0;
-        const int upt = mgc_config(m, &C, &rows_max, &smem);
-        if (upt > 0) {
+        if (k.mgc_upt > 0) {
             // subdomains that fit one cluster: the whole solve in one launch
-            m.outer = 8;
-            CU(c, launch_mgc(m, upt, C, rows_max, smem, s));
+            CU(c, launch_mgc(m, k.mgc_upt, k.mgc_C, k.mgc_rows, k.mgc_smem, s));
         } else if (cs == cudaStreamCaptureStatusActive) {
             // inside the step's graph: while-loops that stop once every field has converged
-            m.inner = std::max(1, std::min(30, max_iter));
-            m.outer = std::max(1, std::min(8, max_iter / m.inner));
+            m.inner = std::max(1, std::min(30, m.max_iter));
+            m.outer = std::max(1, std::min(8, m.max_iter / m.inner));
             CU(c, launch_mg_solve_graph(m, s, c->mg_s2, c->mg_s3));
             c->graph_mg_loops = true;
         } else {
             // a direct call: a fixed number of passes (5 inner iterations x 6 sweeps at most)
-            m.inner = std::max(1, std::min(5, max_iter));
-            m.outer = std::max(1, std::min(6, max_iter / m.inner));
+            m.inner = std::max(1, std::min(5, m.max_iter));
+            m.outer = std::max(1, std::min(6, m.max_iter / m.inner));
             CU(c, launch_mg_solve(m, s));
         }
-        c->solve_nsys_used = ns;
+        c->solve_nsys_used = (size_t)m.nsys;
         return SDD_OK;
     }
-    CU(c, launch_pcg(a, c->solve_upt, c->solve_rows_max, c->solve_mx_max, s));
+    CU(c, launch_pcg(k.a, c->solve_upt, c->solve_rows_max, c->solve_mx_max, s));
     c->solve_nsys_used = c->systems.size();
     return SDD_OK;
 }
 
+// The implicit subdomain step on stream s, set-up and iterations. xo/eo
+// receive the new fields.
+sdd_status enqueue_solve(sdd_ctx* c, double Dt, const double* ix, const double* ie, double rtol, int max_iter,
+                         double* xo, double* eo, cudaStream_t s)
+{
+    const SolveCall k = make_solve_call(c, Dt, rtol, max_iter, xo, eo);
+    sdd_status st = enqueue_solve_setup(c, k, Dt, ix, ie, s);
+    if (st != SDD_OK) return st;
+    return enqueue_solve_iterate(c, k, s);
+}
+
+
+// Enqueue the deferred iterations of the last mesh step's solve on the
+// context's stream: afterwards the current fields are final.
+sdd_status flush_pending(sdd_ctx* c)
+{
+    if (!c->pending) return SDD_OK;
+    c->pending = false;
+    return enqueue_solve_iterate(c, c->pend_call, c->stream);
+}
 
 void drop_graphs_fn(sdd_ctx* c)
 {
     c->graph[0].release();
     c->graph[1].release();
+    c->graph_p[0].release();
+    c->graph_p[1].release();
     c->graph_ok = false;
     c->graph_mg_loops = false;
 }
@@ -1245,6 +1353,10 @@ sdd_status sdd_set_w_host(sdd_ctx* c, const float* w)
 sdd_status sdd_set_fields(sdd_ctx* c, const double* xi, const double* eta)
 {
     if (!c || !xi || !eta) return fail(c, SDD_EINVAL, "null argument");
+    {
+        const sdd_status fs = flush_pending(c);
+        if (fs != SDD_OK) return fs;
+    }
     const size_t bytes = (size_t)c->nx * c->ny * sizeof(double);
     CU(c, cudaMemcpyAsync(c->fld[c->cur][0].p, xi, bytes, cudaMemcpyDeviceToDevice, c->stream));
     CU(c, cudaMemcpyAsync(c->fld[c->cur][1].p, eta, bytes, cudaMemcpyDeviceToDevice, c->stream));
@@ -1280,6 +1392,10 @@ sdd_status sdd_get_faces(sdd_ctx* c, double* faces)
 sdd_status sdd_get_fields(sdd_ctx* c, double* xi, double* eta)
 {
     if (!c || !xi || !eta) return fail(c, SDD_EINVAL, "null argument");
+    {
+        const sdd_status fs = flush_pending(c);
+        if (fs != SDD_OK) return fs;
+    }
     const size_t bytes = (size_t)c->nx * c->ny * sizeof(double);
     CU(c, cudaMemcpyAsync(xi, c->fld[c->cur][0].p, bytes, cudaMemcpyDefault, c->stream));
     CU(c, cudaMemcpyAsync(eta, c->fld[c->cur][1].p, bytes, cudaMemcpyDefault, c->stream));
@@ -1298,6 +1414,10 @@ static sdd_status mc_common(sdd_ctx* c, const sdd_nodes* nodes, const sdd_mc_par
                             const sdd_path_records* rec)
 {
     if (!c || !nodes || !p) return fail(c, SDD_EINVAL, "null argument");
+    {
+        const sdd_status fs = flush_pending(c);
+        if (fs != SDD_OK) return fs;
+    }
     if (nodes->count > 0 && (!nodes->x || !nodes->y || !nodes->n_paths)) return fail(c, SDD_EINVAL, "null node array");
     int K = 0;
     if (!valid_params(c, p->dt, p->Dt, p->exit_mode, &K))
@@ -1419,6 +1539,10 @@ sdd_status sdd_mlp_init(sdd_ctx* c, uint64_t seed, float* theta)
 sdd_status sdd_cv_samples(sdd_ctx* c, const sdd_sample_params* p, float* feats, float* targets)
 {
     if (!c || !p || !feats || !targets) return fail(c, SDD_EINVAL, "null argument");
+    {
+        const sdd_status fs = flush_pending(c);
+        if (fs != SDD_OK) return fs;
+    }
     return samples_into(c, p, feats, targets);
 }
 
@@ -1462,6 +1586,10 @@ sdd_status sdd_cv_tabulate(sdd_ctx* c, const float* theta, const float* norm, in
 sdd_status sdd_cv_train(sdd_ctx* c, const sdd_cv_train_params* p, sdd_cv_train_info* info)
 {
     if (!c || !p) return fail(c, SDD_EINVAL, "null argument");
+    {
+        const sdd_status fs = flush_pending(c);
+        if (fs != SDD_OK) return fs;
+    }
     int K = 0;
     if (!valid_params(c, p->samples.dt, p->samples.Dt, p->samples.exit_mode, &K))
         return fail(c, SDD_EINVAL, "dt, Dt or exit_mode rejected");
@@ -1574,6 +1702,10 @@ sdd_status sdd_cv_losses(sdd_ctx* c, float* losses, int64_t count)
 sdd_status sdd_autotune(sdd_ctx* c, const sdd_nodes* nodes, const sdd_mc_params* p, sdd_launch_shape* out)
 {
     if (!c || !nodes || !p) return fail(c, SDD_EINVAL, "null argument");
+    {
+        const sdd_status fs = flush_pending(c);
+        if (fs != SDD_OK) return fs;
+    }
     if (nodes->count > 0 && (!nodes->x || !nodes->y || !nodes->n_paths)) return fail(c, SDD_EINVAL, "null node array");
     int K = 0;
     if (!valid_params(c, p->dt, p->Dt, p->exit_mode, &K)) return fail(c, SDD_EINVAL, "dt, Dt or exit_mode rejected");
@@ -1605,6 +1737,10 @@ sdd_status sdd_subdomain_solve(sdd_ctx* c, double Dt, const double* iface_xi, co
                                int32_t max_iter, double* xi_out, double* eta_out, int32_t* iters_out)
 {
     if (!c || !xi_out || !eta_out) return fail(c, SDD_EINVAL, "null argument");
+    {
+        const sdd_status fs = flush_pending(c);
+        if (fs != SDD_OK) return fs;
+    }
     if (!c->iface_idx.empty() && (!iface_xi || !iface_eta)) return fail(c, SDD_EINVAL, "null interface values");
     if (!(Dt > 0.0) || !(rtol >= 0.0) || max_iter < 0) return fail(c, SDD_EINVAL, "Dt, rtol or max_iter rejected");
     sdd_status st = prepare(c, c->stream);
@@ -1625,8 +1761,13 @@ sdd_status sdd_subdomain_solve(sdd_ctx* c, double Dt, const double* iface_xi, co
 }
 
 // Record one mesh step into a graph on the capture stream: field tables, the
-// interface estimate, the Dirichlet data, the PCG and the step counter.
-static sdd_status capture_step(sdd_ctx* c, const sdd_step_params* p, int K, int parity)
+// interface estimate, the Dirichlet data, the subdomain solve and the step
+// counter. Pipelined (c->pipe): the solve's iterations are left for the next
+// step's graph, and with_pending records this step's graph that way, the
+// previous step's iterations and the field records on a second stream beside
+// the drift records, key points and paths; the survivors are scored after
+// both.
+static sdd_status capture_step(sdd_ctx* c, const sdd_step_params* p, int K, int parity, bool with_pending)
 {
     cudaStream_t s = c->cap_stream;
     cudaGraph_t g = nullptr;
@@ -1638,11 +1779,28 @@ static sdd_status capture_step(sdd_ctx* c, const sdd_step_params* p, int K, int 
     const int saved = c->cur;
     c->cur = parity;
     sdd_status st = SDD_OK;
-    {
-        cudaError_t e0 = cudaEventRecordWithFlags(c->ev[0], s, cudaEventRecordExternal);
-        if (e0 != cudaSuccess) st = fail(c, SDD_ECUDA, "event: %s", cudaGetErrorString(e0));
+    auto rec_ext = [&](cudaEvent_t e, cudaStream_t on) {
+        if (st != SDD_OK) return;
+        cudaError_t r = cudaEventRecordWithFlags(e, on, cudaEventRecordExternal);
+        if (r != cudaSuccess) st = fail(c, SDD_ECUDA, "event: %s", cudaGetErrorString(r));
+    };
+    auto cu = [&](cudaError_t r) {
+        if (st == SDD_OK && r != cudaSuccess) st = fail(c, SDD_ECUDA, "%s", cudaGetErrorString(r));
+    };
+    rec_ext(c->ev[0], s);
+    cudaEvent_t join = nullptr;
+    if (c->pipe && with_pending) {
+        // the previous step's iterations write this step's fields, then their records
+        cu(cudaEventRecord(c->pev[0], s));
+        cu(cudaStreamWaitEvent(c->pipe_stream, c->pev[0], 0));
+        rec_ext(c->pev[2], c->pipe_stream);
+        if (st == SDD_OK) st = enqueue_solve_iterate(c, c->step_call[1 - parity], c->pipe_stream);
+        rec_ext(c->pev[3], c->pipe_stream);
+        if (st == SDD_OK) st = prepare_parts(c, c->pipe_stream, false, true);
+        cu(cudaEventRecord(c->pev[1], c->pipe_stream));
+        join = c->pev[1];
     }
-    if (st == SDD_OK) st = prepare(c, s);
+    if (st == SDD_OK) st = c->pipe && with_pending ? prepare_parts(c, s, true, false) : prepare(c, s);
     if (st == SDD_OK) st = enqueue_cv_refresh(c, K, s);
     OutDev o{};
     o.mean_xi = c->iface_stats[0].p;
@@ -1655,24 +1813,21 @@ static sdd_status capture_step(sdd_ctx* c, const sdd_step_params* p, int K, int 
     if (st == SDD_OK && kmask) st = enqueue_keypoints(c, c->d_kmask.p, s);
     if (st == SDD_OK)
         st = run_plan(c, c->step_plan, p->dt, K, p->seed, 0, c->d_step.p, p->exit_mode, o, nullptr, s, c->ev[1],
-                      c->ev[2], kmask);
+                      c->ev[2], kmask, c->pipe ? (void*)c->surv.p : nullptr, join);
     if (st == SDD_OK && kmask) {
         cudaError_t e = launch_pchip(c->d_klines.p, (int)c->klines.size(), c->d_kpos_idx.p, c->d_kpos_cross.p, kmask,
                                      c->faces64.p, c->nx, c->ny, o.mean_xi, o.mean_eta, c->d_kscratch.p, s);
         if (e != cudaSuccess) st = fail(c, SDD_ECUDA, "interface fill: %s", cudaGetErrorString(e));
     }
+    rec_ext(c->ev[3], s);
     if (st == SDD_OK) {
-        cudaError_t e = cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal);
-        if (e != cudaSuccess) st = fail(c, SDD_ECUDA, "event: %s", cudaGetErrorString(e));
+        c->step_call[parity] =
+            make_solve_call(c, p->Dt, p->rtol, p->max_iter, c->fld[1 - parity][0].p, c->fld[1 - parity][1].p);
+        st = enqueue_solve_setup(c, c->step_call[parity], p->Dt, o.mean_xi, o.mean_eta, s);
+        if (st == SDD_OK && !c->pipe) st = enqueue_solve_iterate(c, c->step_call[parity], s);
     }
-    if (st == SDD_OK)
-        st = enqueue_solve(c, p->Dt, o.mean_xi, o.mean_eta, p->rtol, p->max_iter, c->fld[1 - parity][0].p,
-                           c->fld[1 - parity][1].p, s);
-    if (st == SDD_OK) {
-        cudaError_t e = launch_bump_step(c->d_step.p, s);
-        if (e == cudaSuccess) e = cudaEventRecordWithFlags(c->ev[4], s, cudaEventRecordExternal);
-        if (e != cudaSuccess) st = fail(c, SDD_ECUDA, "%s", cudaGetErrorString(e));
-    }
+    if (st == SDD_OK) cu(launch_bump_step(c->d_step.p, s));
+    rec_ext(c->ev[4], s);
     c->cur = saved;
     c->dirty_w = keep_w;
     c->dirty_fields = keep_f;
@@ -1682,7 +1837,8 @@ static sdd_status capture_step(sdd_ctx* c, const sdd_step_params* p, int K, int 
         return st;
     }
     if (e != cudaSuccess) return fail(c, SDD_ECUDA, "capture: %s", cudaGetErrorString(e));
-    c->graph[parity].release();
+    GraphSlot& slot = with_pending ? c->graph_p[parity] : c->graph[parity];
+    slot.release();
     {
         size_t nn = 0;
         if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
@@ -1693,13 +1849,13 @@ static sdd_status capture_step(sdd_ctx* c, const sdd_step_params* p, int K, int 
                     cudaGraphNodeType t;
                     if (cudaGraphNodeGetType(nodes[k], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
                 }
-            c->graph_kernels = kernels;
+            (with_pending ? c->graph_kernels_p : c->graph_kernels) = kernels;
         }
     }
-    e = cudaGraphInstantiate(&c->graph[parity].exec, g, 0);
+    e = cudaGraphInstantiate(&slot.exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        c->graph[parity].exec = nullptr;
+        slot.exec = nullptr;
         return fail(c, SDD_ECUDA, "instantiate: %s", cudaGetErrorString(e));
     }
     return SDD_OK;
@@ -1714,6 +1870,8 @@ sdd_status sdd_step(sdd_ctx* c, const sdd_step_params* p)
         return fail(c, SDD_EINVAL, "paths_per_node, max_iter or rtol rejected");
     const bool same = c->graph_ok && std::memcmp(&c->graph_params, p, sizeof *p) == 0;
     if (!same) {
+        sdd_status st0 = flush_pending(c);
+        if (st0 != SDD_OK) return st0;
         drop_graphs(c);
         std::vector<int64_t> np(c->iface_x.size(), p->paths_per_node);
         std::vector<NodeSeg> segs(1);
@@ -1732,14 +1890,35 @@ sdd_status sdd_step(sdd_ctx* c, const sdd_step_params* p)
                                    (int64_t)np.size(), ppt, block, p->exit_mode, false);
         if (st != SDD_OK) return st;
         CU(c, cudaStreamSynchronize(c->stream));
+        // pipelined steps where the solve's iterations are one launch and the
+        // paths do not read the fields (the field-gradient control variate does)
+        const SolveCall probe = make_solve_call(c, p->Dt, p->rtol, p->max_iter, nullptr, nullptr);
+        const size_t rec_bytes = c->cv_mode ? sizeof(float4) : sizeof(float2);
+        c->pipe = c->pipe_allowed && solve_single_launch(probe) && c->cv_mode != SDD_CV_FIELDS && c->step_plan.ntasks > 0 &&
+                  (size_t)c->step_plan.total_paths * rec_bytes <= (8ULL << 30);
+        if (c->pipe) {
+            if (!c->pipe_stream) CU(c, cudaStreamCreateWithFlags(&c->pipe_stream, cudaStreamNonBlocking));
+            for (cudaEvent_t& e : c->pev)
+                if (!e) CU(c, cudaEventCreate(&e));
+            CU(c, c->surv.alloc(((size_t)c->step_plan.total_paths * rec_bytes + sizeof(float4) - 1) / sizeof(float4)));
+        }
         for (int parity = 0; parity < 2; ++parity)
-            if ((st = capture_step(c, p, K, parity)) != SDD_OK) return st;
+            if ((st = capture_step(c, p, K, parity, false)) != SDD_OK) return st;
+        if (c->pipe)
+            for (int parity = 0; parity < 2; ++parity)
+                if ((st = capture_step(c, p, K, parity, true)) != SDD_OK) return st;
         c->graph_params = *p;
         c->graph_ok = true;
     }
     // the step counter lives on the device; make sure it holds n
     CU(c, cudaMemcpyAsync(c->d_step.p, &c->step_index, sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream));
-    CU(c, cudaGraphLaunch(c->graph[c->cur].exec, c->stream));
+    const bool with_pending = c->pipe && c->pending;
+    CU(c, cudaGraphLaunch((with_pending ? c->graph_p : c->graph)[c->cur].exec, c->stream));
+    c->last_had_pending = with_pending;
+    if (c->pipe) {
+        c->pend_call = c->step_call[c->cur];
+        c->pending = true;
+    }
     c->cur = 1 - c->cur;
     c->step_index += 1;
     c->dirty_w = false;
@@ -1765,7 +1944,7 @@ sdd_status sdd_last_step_info(sdd_ctx* c, sdd_step_info* out)
     if (!c || !out) return fail(c, SDD_EINVAL, "null argument");
     if (!c->graph_ok) return fail(c, SDD_EINVAL, "no step has run");
     CU(c, cudaStreamSynchronize(c->stream));
-    out->kernel_nodes = c->graph_kernels;
+    out->kernel_nodes = c->last_had_pending ? c->graph_kernels_p : c->graph_kernels;
     if (c->graph_mg_loops) {
         // kernel nodes of the graph itself plus the kernels its loop bodies ran in this step
         int32_t body = 0;
@@ -1775,6 +1954,12 @@ sdd_status sdd_last_step_info(sdd_ctx* c, sdd_step_info* out)
     CU(c, cudaEventElapsedTime(&out->paths_ms, c->ev[1], c->ev[2]));
     CU(c, cudaEventElapsedTime(&out->estimate_ms, c->ev[0], c->ev[3]));
     CU(c, cudaEventElapsedTime(&out->solve_ms, c->ev[3], c->ev[4]));
+    if (c->last_had_pending) {
+        // the iterations this graph ran (the previous step's) beside the paths
+        float it = 0.f;
+        CU(c, cudaEventElapsedTime(&it, c->pev[2], c->pev[3]));
+        out->solve_ms += it;
+    }
     CU(c, cudaEventElapsedTime(&out->step_ms, c->ev[0], c->ev[4]));
     return SDD_OK;
 }
@@ -1788,9 +1973,31 @@ sdd_status sdd_set_step_index(sdd_ctx* c, uint32_t n)
 
 uint32_t sdd_get_step_index(const sdd_ctx* c) { return c ? c->step_index : 0u; }
 
+sdd_status sdd_set_pipeline(sdd_ctx* c, int32_t on)
+{
+    if (!c) return SDD_EINVAL;
+    const sdd_status fs = flush_pending(c);
+    if (fs != SDD_OK) return fs;
+    if (c->pipe_allowed != (on != 0)) drop_graphs(c);
+    c->pipe_allowed = on != 0;
+    return SDD_OK;
+}
+
+int32_t sdd_pipeline_in_use(const sdd_ctx* c) { return c && c->graph_ok && c->pipe ? 1 : 0; }
+
+sdd_status sdd_flush(sdd_ctx* c)
+{
+    if (!c) return SDD_EINVAL;
+    return flush_pending(c);
+}
+
 sdd_status sdd_sync(sdd_ctx* c)
 {
     if (!c) return SDD_EINVAL;
+    {
+        const sdd_status fs = flush_pending(c);
+        if (fs != SDD_OK) return fs;
+    }
     CU(c, cudaStreamSynchronize(c->stream));
     int status = 0;
     CU(c, cudaMemcpy(&status, c->d_status.p, sizeof(int), cudaMemcpyDeviceToHost));
@@ -1815,6 +2022,9 @@ void sdd_destroy(sdd_ctx* c)
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->mg_s2) cudaStreamDestroy(c->mg_s2);
     if (c->mg_s3) cudaStreamDestroy(c->mg_s3);
+    if (c->pipe_stream) cudaStreamDestroy(c->pipe_stream);
+    for (cudaEvent_t e : c->pev)
+        if (e) cudaEventDestroy(e);
     delete c;  // device buffers are freed by their destructors
 }
 
@@ -1941,6 +2151,14 @@ sdd_status sdd_batch_create(sdd_batch** out, sdd_ctx* const* ctxs, int32_t count
     for (int32_t a = 0; a < count; ++a)
         for (int32_t c = a + 1; c < count; ++c)
             if (ctxs[a] == ctxs[c]) return SDD_EINVAL;
+    for (int32_t k = 0; k < count; ++k) {
+        // a context's own pipelined step may have left its solve's iterations pending
+        if (ctxs[k]->pending) {
+            const sdd_status fs = flush_pending(ctxs[k]);
+            if (fs != SDD_OK) return fs;
+            if (cudaStreamSynchronize(ctxs[k]->stream) != cudaSuccess) return SDD_ECUDA;
+        }
+    }
     sdd_batch* b = new (std::nothrow) sdd_batch();
     if (!b) return SDD_ENOMEM;
     b->ctxs.assign(ctxs, ctxs + count);
@@ -1977,9 +2195,26 @@ sdd_status sdd_batch_create(sdd_batch** out, sdd_ctx* const* ctxs, int32_t count
     return SDD_OK;
 }
 
+// A context stepped on its own may have left its solve's iterations pending:
+// run them (on its stream) before the batch uses its fields.
+static sdd_status flush_batch(sdd_batch* b)
+{
+    for (sdd_ctx* c : b->ctxs) {
+        if (!c->pending) continue;
+        const sdd_status fs = flush_pending(c);
+        if (fs != SDD_OK) return fail(&b->err, fs, "%s", c->err.c_str());
+        CU(&b->err, cudaStreamSynchronize(c->stream));
+    }
+    return SDD_OK;
+}
+
 sdd_status sdd_batch_interface_mc(sdd_batch* b, const sdd_nodes* nodes, const sdd_mc_params* p, sdd_node_stats* out)
 {
     if (!b || !nodes || !p || !out) return b ? fail(&b->err, SDD_EINVAL, "null argument") : SDD_EINVAL;
+    {
+        const sdd_status fs = flush_batch(b);
+        if (fs != SDD_OK) return fs;
+    }
     int K = 0;
     if (!valid_params(nullptr, p->dt, p->Dt, p->exit_mode, &K))
         return fail(&b->err, SDD_EINVAL, "dt, Dt or exit_mode rejected (Dt / dt must be an integer in [1, 2^20])");
@@ -2008,6 +2243,10 @@ sdd_status sdd_batch_interface_mc(sdd_batch* b, const sdd_nodes* nodes, const sd
 sdd_status sdd_batch_step(sdd_batch* b, const sdd_step_params* p)
 {
     if (!b || !p) return b ? fail(&b->err, SDD_EINVAL, "null argument") : SDD_EINVAL;
+    {
+        const sdd_status fs = flush_batch(b);
+        if (fs != SDD_OK) return fs;
+    }
     int K = 0;
     if (!valid_params(nullptr, p->dt, p->Dt, p->exit_mode, &K)) return fail(&b->err, SDD_EINVAL, "dt, Dt or exit_mode rejected");
     if (p->paths_per_node < 1 || p->paths_per_node > 0x7fffffffLL || p->max_iter < 0 || !(p->rtol >= 0.0))

@@ -101,6 +101,18 @@ struct PathArgs {
     const uint32_t* step_ptr; // if non-null, read the step index here
     RecDev rec;
     const uint8_t* node_mask; // if non-null, only nodes with a nonzero entry run their paths
+    void* surv;               // if non-null, survivors leave their end records here (indexed rec0 + path)
+};
+
+// Deferred scoring of the survivors (k_score_surv).
+struct ScoreArgs {
+    const InstDev* inst;
+    const NodeDev* nodes;
+    const Task* tasks;
+    Partial* partials;
+    const void* surv;
+    int32_t ntasks;
+    const uint8_t* node_mask;
 };
 
 struct FinalArgs {
@@ -126,8 +138,11 @@ cudaError_t launch_paths(const PathArgs& a, int exit_mode, bool record, int grid
                          bool cv = false);
 // exit_mode 0 with an even number of sub-steps has its own kernel (no odd last pair)
 cudaError_t launch_finalize(const FinalArgs& a, cudaStream_t s);
+cudaError_t launch_score_surv(const ScoreArgs& a, bool cv, cudaStream_t s);
 int path_kernel_blocks_per_sm(int exit_mode, bool record, int block, bool cv = false);
 
+// Cell records of the drift (from w; bcoef null: skipped) and of the fields
+// (from xi, eta; fcoef null: skipped).
 cudaError_t launch_prep_cells(const float* w, const double* xi, const double* eta, int nx, int ny, float4* bcoef,
                               float4* fcoef, int* status, cudaStream_t s);
 cudaError_t launch_winslow_faces(const float* w, int nx, int ny, double* faces64, cudaStream_t s);

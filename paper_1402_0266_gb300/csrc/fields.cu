@@ -64,25 +64,30 @@ __global__ void k_prep_cells(const float* __restrict__ w, const double* __restri
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;
     const int iy = blockIdx.y * blockDim.y + threadIdx.y;
     if (ix >= nx - 1 || iy >= ny - 1) return;
-    // every node is checked by the cell that has it as lower-left corner,
-    // the last row and column by the cells next to them
-    bool bad = bad_w(w[(long long)iy * nx + ix]);
-    if (ix == nx - 2) bad |= bad_w(w[(long long)iy * nx + ix + 1]);
-    if (iy == ny - 2) bad |= bad_w(w[(long long)(iy + 1) * nx + ix]);
-    if (ix == nx - 2 && iy == ny - 2) bad |= bad_w(w[(long long)(iy + 1) * nx + ix + 1]);
-    if (bad) atomicOr(status, STATUS_BAD_W);
-
-    const double rx = 0.5 * (double)(nx - 1), ry = 0.5 * (double)(ny - 1);
-    const double2 b00 = node_drift(w, nx, ny, ix, iy, rx, ry);
-    const double2 b10 = node_drift(w, nx, ny, ix + 1, iy, rx, ry);
-    const double2 b01 = node_drift(w, nx, ny, ix, iy + 1, rx, ry);
-    const double2 b11 = node_drift(w, nx, ny, ix + 1, iy + 1, rx, ry);
     const long long cell = (long long)iy * (nx - 1) + ix;
-    bilinear_coefs2(b00.x, b10.x, b01.x, b11.x, b00.y, b10.y, b01.y, b11.y, bcoef[2 * cell + 0], bcoef[2 * cell + 1]);
-    const long long n00 = (long long)iy * nx + ix;
-    const long long n01 = n00 + nx;
-    bilinear_coefs2(xi[n00], xi[n00 + 1], xi[n01], xi[n01 + 1], eta[n00], eta[n00 + 1], eta[n01], eta[n01 + 1],
-                    fcoef[2 * cell + 0], fcoef[2 * cell + 1]);
+    if (bcoef) {
+        // every node is checked by the cell that has it as lower-left corner,
+        // the last row and column by the cells next to them
+        bool bad = bad_w(w[(long long)iy * nx + ix]);
+        if (ix == nx - 2) bad |= bad_w(w[(long long)iy * nx + ix + 1]);
+        if (iy == ny - 2) bad |= bad_w(w[(long long)(iy + 1) * nx + ix]);
+        if (ix == nx - 2 && iy == ny - 2) bad |= bad_w(w[(long long)(iy + 1) * nx + ix + 1]);
+        if (bad) atomicOr(status, STATUS_BAD_W);
+
+        const double rx = 0.5 * (double)(nx - 1), ry = 0.5 * (double)(ny - 1);
+        const double2 b00 = node_drift(w, nx, ny, ix, iy, rx, ry);
+        const double2 b10 = node_drift(w, nx, ny, ix + 1, iy, rx, ry);
+        const double2 b01 = node_drift(w, nx, ny, ix, iy + 1, rx, ry);
+        const double2 b11 = node_drift(w, nx, ny, ix + 1, iy + 1, rx, ry);
+        bilinear_coefs2(b00.x, b10.x, b01.x, b11.x, b00.y, b10.y, b01.y, b11.y, bcoef[2 * cell + 0],
+                        bcoef[2 * cell + 1]);
+    }
+    if (fcoef) {
+        const long long n00 = (long long)iy * nx + ix;
+        const long long n01 = n00 + nx;
+        bilinear_coefs2(xi[n00], xi[n00 + 1], xi[n01], xi[n01 + 1], eta[n00], eta[n00 + 1], eta[n01], eta[n01 + 1],
+                        fcoef[2 * cell + 0], fcoef[2 * cell + 1]);
+    }
 }
 
 // Control-variate table: node values (slice, j, i, 4) of the two models'

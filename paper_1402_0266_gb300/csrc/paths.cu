@@ -232,6 +232,16 @@ __device__ __forceinline__ long long warp_sum_ll(long long v)
     return v;
 }
 
+// Deferred scoring: a path's end record in the survivor buffer (float2 end
+// point, or float4 end point and control-variate sums with CV); an exit
+// leaves x = -1 there, a value no end point inside the square has.
+template <bool CV>
+__device__ __forceinline__ void mark_exit(void* surv, long long i)
+{
+    if (CV) static_cast<float4*>(surv)[i] = make_float4(-1.f, 0.f, 0.f, 0.f);
+    else static_cast<float2*>(surv)[i] = f2(-1.f, 0.f);
+}
+
 // MODE 0: the paper's test, sub-step pairs; MODE 1: with the bridge test;
 // MODE 2: as MODE 0 when K is even (every pair has both sub-steps).
 // CV: subtract the control variate sum_j G(s_j, X_j) . sqrt(2) dW_j from both scores.
@@ -372,25 +382,39 @@ __global__ void __launch_bounds__(CV ? kCvMaxBlock : 512, CV ? 3 : 2) k_paths(co
                     if (!done && m >= K) done = true;
                 }
                 if (done) {
+                    bool later = false;   // a survivor scored by k_score_surv once the fields are final
                     if (code < 0) {
-                        // survived the mesh step: xi, eta of its start at the end point
-                        const Cell c = locate(I, I.fcoef, pos);
-                        float4 f0, f1;
-                        load_cell(c.p, f0, f1);
-                        const float2 v = eval2(f0, f1, c.st);
-                        yxi = v.x;
-                        yeta = v.y;
-                        xe = pos.x;
-                        ye = pos.y;
+                        if (a.surv) {
+                            later = true;
+                            const long long si = nd.rec0 + path;
+                            if (CV)
+                                static_cast<float4*>(a.surv)[si] =
+                                    make_float4(pos.x, pos.y, cvx.x + cvx.y, cve.x + cve.y);
+                            else
+                                static_cast<float2*>(a.surv)[si] = pos;
+                        } else {
+                            // survived the mesh step: xi, eta of its start at the end point
+                            const Cell c = locate(I, I.fcoef, pos);
+                            float4 f0, f1;
+                            load_cell(c.p, f0, f1);
+                            const float2 v = eval2(f0, f1, c.st);
+                            yxi = v.x;
+                            yeta = v.y;
+                            xe = pos.x;
+                            ye = pos.y;
+                        }
                     } else {
                         ++exits;
+                        if (a.surv) mark_exit<CV>(a.surv, nd.rec0 + path);
                     }
-                    if (CV) {
-                        yxi -= cvx.x + cvx.y;
-                        yeta -= cve.x + cve.y;
+                    if (!later) {
+                        if (CV) {
+                            yxi -= cvx.x + cvx.y;
+                            yeta -= cve.x + cve.y;
+                        }
+                        ax.add(yxi - x0);
+                        ae.add(yeta - y0);
                     }
-                    ax.add(yxi - x0);
-                    ae.add(yeta - y0);
                     steps += taken;
                     if (RECORD) {
                         const long long ri = nd.rec0 + path;
@@ -520,20 +544,29 @@ __global__ void __launch_bounds__(512, 2) k_paths_exp(const PathArgs a)
                 }
                 ++j;
                 if (done) {
+                    bool later = false;
                     if (code < 0) {
-                        const Cell cf = locate(I, I.fcoef, pos);
-                        float4 f0, f1;
-                        load_cell(cf.p, f0, f1);
-                        const float2 v = eval2(f0, f1, cf.st);
-                        yxi = v.x;
-                        yeta = v.y;
-                        xe = pos.x;
-                        ye = pos.y;
+                        if (a.surv) {
+                            later = true;
+                            static_cast<float2*>(a.surv)[nd.rec0 + path] = pos;
+                        } else {
+                            const Cell cf = locate(I, I.fcoef, pos);
+                            float4 f0, f1;
+                            load_cell(cf.p, f0, f1);
+                            const float2 v = eval2(f0, f1, cf.st);
+                            yxi = v.x;
+                            yeta = v.y;
+                            xe = pos.x;
+                            ye = pos.y;
+                        }
                     } else {
                         ++exits;
+                        if (a.surv) mark_exit<false>(a.surv, nd.rec0 + path);
                     }
-                    ax.add(yxi - x0);
-                    ae.add(yeta - y0);
+                    if (!later) {
+                        ax.add(yxi - x0);
+                        ae.add(yeta - y0);
+                    }
                     steps += j;
                     if (RECORD) {
                         const long long ri = nd.rec0 + path;
@@ -573,6 +606,52 @@ __global__ void __launch_bounds__(512, 2) k_paths_exp(const PathArgs a)
             p.steps = st;
             a.partials[t] = p;
         }
+    }
+}
+
+// Scores of the paths that survived a mesh step, once the fields of the step's
+// start are final (the estimate of the next mesh step runs beside the
+// subdomain solve that produces them): one warp per task, the task's paths in
+// order, xi and eta at each end point minus the path's control-variate sums,
+// added to the task's partial sums after the path kernel's.
+template <bool CV>
+__global__ void __launch_bounds__(256) k_score_surv(const ScoreArgs a)
+{
+    const int t = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (t >= a.ntasks) return;
+    const Task task = a.tasks[t];
+    if (a.node_mask && !a.node_mask[task.node]) return;
+    const NodeDev& nd = a.nodes[task.node];
+    const InstDev I = a.inst[nd.inst];
+    const float x0 = nd.xf, y0 = nd.yf;
+    Acc ax{0.f, 0.f, 0.f, 0.f}, ae{0.f, 0.f, 0.f, 0.f};
+    const int end = task.path0 + task.npaths;
+    for (int p = task.path0 + lane; p < end; p += 32) {
+        const long long si = nd.rec0 + p;
+        float4 r;
+        if (CV) {
+            r = static_cast<const float4*>(a.surv)[si];
+        } else {
+            const float2 q = static_cast<const float2*>(a.surv)[si];
+            r = make_float4(q.x, q.y, 0.f, 0.f);
+        }
+        if (r.x < 0.f) continue;   // the path left the domain
+        const Cell c = locate(I, I.fcoef, f2(r.x, r.y));
+        float4 f0, f1;
+        load_cell(c.p, f0, f1);
+        const float2 v = eval2(f0, f1, c.st);
+        ax.add(v.x - r.z - x0);
+        ae.add(v.y - r.w - y0);
+    }
+    const double sx = warp_sum(ax.sum()), qx = warp_sum(ax.sumsq());
+    const double se = warp_sum(ae.sum()), qe = warp_sum(ae.sumsq());
+    if (lane == 0) {
+        Partial& P = a.partials[t];
+        P.s_xi += sx;
+        P.q_xi += qx;
+        P.s_eta += se;
+        P.q_eta += qe;
     }
 }
 
@@ -781,6 +860,17 @@ cudaError_t launch_paths(const PathArgs& a, int exit_mode, bool record, int grid
     const int mode = kernel_mode(exit_mode, a.K);
     if (cv) launch_mode<true>(a, mode, record, grid, block, s);
     else launch_mode<false>(a, mode, record, grid, block, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_score_surv(const ScoreArgs& a, bool cv, cudaStream_t s)
+{
+    if (a.ntasks <= 0) return cudaSuccess;
+    const int block = 256;
+    const long long threads = (long long)a.ntasks * 32;
+    const int grid = (int)((threads + block - 1) / block);
+    if (cv) k_score_surv<true><<<grid, block, 0, s>>>(a);
+    else k_score_surv<false><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
 
