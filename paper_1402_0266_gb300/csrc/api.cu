@@ -89,6 +89,9 @@ struct SolveCall {
     bool use_mg = false;
     int mgc_upt = 0, mgc_C = 0, mgc_rows = 0;
     size_t mgc_smem = 0;
+    const float* w = nullptr;                        // w of the step's start
+    const double* px = nullptr, *pe = nullptr;        // the fields of the step's start
+    double Dt = 0.0;
 };
 
 }  // namespace
@@ -186,8 +189,9 @@ struct sdd_ctx {
     int graph_kernels_p = 0;
     bool last_had_pending = false;  // the last launched graph ran deferred iterations
     DevBuf<float4> surv;            // survivor end records of the step's paths
-    cudaStream_t pipe_stream = nullptr;
-    cudaEvent_t pev[4] = {nullptr, nullptr, nullptr, nullptr};  // fork, join, iterations start, end
+    cudaStream_t pipe_stream = nullptr;  // the side branch (highest priority)
+    // fork, join of the field records, iterations start, end, join of the systems
+    cudaEvent_t pev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 
     std::string err;
 };
@@ -638,6 +642,8 @@ sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const Out
             sa.partials = P.d_partials.p;
             sa.surv = surv;
             sa.ntasks = (int32_t)P.ntasks;
+            // about four paths per lane
+            sa.group_warps = P.ppt >= 1024 ? 8 : P.ppt >= 512 ? 4 : P.ppt >= 256 ? 2 : 1;
             sa.node_mask = node_mask;
             CU(err, launch_score_surv(sa, cv, s));
         }
@@ -857,9 +863,14 @@ bool mg_auto(const sdd_ctx* c)
     return c->solve_upt == 0 || (long long)c->mg.mx[0] * c->mg.my[0] >= 10000;
 }
 
-SolveCall make_solve_call(sdd_ctx* c, double Dt, double rtol, int max_iter, double* xo, double* eo)
+SolveCall make_solve_call(sdd_ctx* c, double Dt, double rtol, int max_iter, double* xo, double* eo,
+                          const float* w, const double* px, const double* pe)
 {
     SolveCall k;
+    k.w = w;
+    k.px = px;
+    k.pe = pe;
+    k.Dt = Dt;
     SolveArgs& a = k.a;
     a.nx = c->nx;
     a.ny = c->ny;
@@ -901,7 +912,7 @@ SolveCall make_solve_call(sdd_ctx* c, double Dt, double rtol, int max_iter, doub
         m.cxf = c->cxf.p;
         m.cyf = c->cyf.p;
         m.dgf = c->dgf.p;
-        m.w = c->w.p;
+        m.w = w;
         m.Dt = Dt;
         m.x[0] = xo;
         m.x[1] = eo;
@@ -947,19 +958,23 @@ SolveCall make_solve_call(sdd_ctx* c, double Dt, double rtol, int max_iter, doub
 // Jacobi-PCG kernels), so they can run beside other work.
 bool solve_single_launch(const SolveCall& k) { return !k.use_mg || k.mgc_upt > 0; }
 
-// The set-up of an implicit subdomain step on stream s: the system from w and
-// the fields of the step's start, the Dirichlet data from the faces and the
-// interface values (written into the new fields), the multigrid hierarchy.
-// Nothing after it reads w, the faces or the interface values.
-sdd_status enqueue_solve_setup(sdd_ctx* c, const SolveCall& k, double Dt, const double* ix, const double* ie,
-                               cudaStream_t s)
+// The Dirichlet data of an implicit subdomain step on stream s: the faces and
+// the interface values written into the new fields, the old fields inside.
+sdd_status enqueue_solve_dirichlet(sdd_ctx* c, const SolveCall& k, const double* ix, const double* ie,
+                                   cudaStream_t s)
 {
-    const double* px = c->fld[c->cur][0].p;
-    const double* pe = c->fld[c->cur][1].p;
-    CU(c, launch_solve_setup(c->w.p, px, pe, c->nx, c->ny, Dt, c->cx.p, c->cy.p, c->dg.p, c->rhs0.p, c->cxf.p,
+    CU(c, launch_dirichlet(c->faces64.p, k.px, k.pe, ix, ie, c->d_iface_idx.p, (int)c->iface_idx.size(), c->nx,
+                           c->ny, k.a.x[0], k.a.x[1], s));
+    return SDD_OK;
+}
+
+// The systems of an implicit subdomain step on stream s: coefficients and
+// right-hand sides from w and the fields of the step's start, the multigrid
+// hierarchy.
+sdd_status enqueue_solve_system(sdd_ctx* c, const SolveCall& k, cudaStream_t s)
+{
+    CU(c, launch_solve_setup(k.w, k.px, k.pe, c->nx, c->ny, k.Dt, c->cx.p, c->cy.p, c->dg.p, c->rhs0.p, c->cxf.p,
                              c->cyf.p, c->dgf.p, c->dinvf.p, s));
-    CU(c, launch_dirichlet(c->faces64.p, px, pe, ix, ie, c->d_iface_idx.p, (int)c->iface_idx.size(), c->nx, c->ny,
-                           k.a.x[0], k.a.x[1], s));
     if (k.use_mg) CU(c, launch_mg_setup(k.m, s));
     return SDD_OK;
 }
@@ -999,8 +1014,10 @@ sdd_status enqueue_solve_iterate(sdd_ctx* c, const SolveCall& k, cudaStream_t s)
 sdd_status enqueue_solve(sdd_ctx* c, double Dt, const double* ix, const double* ie, double rtol, int max_iter,
                          double* xo, double* eo, cudaStream_t s)
 {
-    const SolveCall k = make_solve_call(c, Dt, rtol, max_iter, xo, eo);
-    sdd_status st = enqueue_solve_setup(c, k, Dt, ix, ie, s);
+    const SolveCall k = make_solve_call(c, Dt, rtol, max_iter, xo, eo, c->w.p, c->fld[c->cur][0].p,
+                                        c->fld[c->cur][1].p);
+    sdd_status st = enqueue_solve_system(c, k, s);
+    if (st == SDD_OK) st = enqueue_solve_dirichlet(c, k, ix, ie, s);
     if (st != SDD_OK) return st;
     return enqueue_solve_iterate(c, k, s);
 }
@@ -1762,11 +1779,11 @@ sdd_status sdd_subdomain_solve(sdd_ctx* c, double Dt, const double* iface_xi, co
 
 // Record one mesh step into a graph on the capture stream: field tables, the
 // interface estimate, the Dirichlet data, the subdomain solve and the step
-// counter. Pipelined (c->pipe): the solve's iterations are left for the next
-// step's graph, and with_pending records this step's graph that way, the
-// previous step's iterations and the field records on a second stream beside
-// the drift records, key points and paths; the survivors are scored after
-// both.
+// counter. Pipelined (c->pipe), a second branch beside the drift records, key
+// points and paths runs the previous step's solve iterations (with_pending),
+// the field records and this step's systems (from w and the fields of the
+// step's start); the survivors are scored after the field records, and this
+// step's iterations are left for the next step's graph (or sdd_flush).
 static sdd_status capture_step(sdd_ctx* c, const sdd_step_params* p, int K, int parity, bool with_pending)
 {
     cudaStream_t s = c->cap_stream;
@@ -1788,19 +1805,27 @@ static sdd_status capture_step(sdd_ctx* c, const sdd_step_params* p, int K, int 
         if (st == SDD_OK && r != cudaSuccess) st = fail(c, SDD_ECUDA, "%s", cudaGetErrorString(r));
     };
     rec_ext(c->ev[0], s);
+    c->step_call[parity] = make_solve_call(c, p->Dt, p->rtol, p->max_iter, c->fld[1 - parity][0].p,
+                                           c->fld[1 - parity][1].p, c->w.p, c->fld[parity][0].p,
+                                           c->fld[parity][1].p);
     cudaEvent_t join = nullptr;
-    if (c->pipe && with_pending) {
-        // the previous step's iterations write this step's fields, then their records
+    if (c->pipe) {
+        cudaStream_t q = c->pipe_stream;
         cu(cudaEventRecord(c->pev[0], s));
-        cu(cudaStreamWaitEvent(c->pipe_stream, c->pev[0], 0));
-        rec_ext(c->pev[2], c->pipe_stream);
-        if (st == SDD_OK) st = enqueue_solve_iterate(c, c->step_call[1 - parity], c->pipe_stream);
-        rec_ext(c->pev[3], c->pipe_stream);
-        if (st == SDD_OK) st = prepare_parts(c, c->pipe_stream, false, true);
-        cu(cudaEventRecord(c->pev[1], c->pipe_stream));
+        cu(cudaStreamWaitEvent(q, c->pev[0], 0));
+        if (with_pending) {
+            // the previous step's iterations write this step's fields
+            rec_ext(c->pev[2], q);
+            if (st == SDD_OK) st = enqueue_solve_iterate(c, c->step_call[1 - parity], q);
+            rec_ext(c->pev[3], q);
+        }
+        if (st == SDD_OK) st = prepare_parts(c, q, false, true);
+        cu(cudaEventRecord(c->pev[1], q));
         join = c->pev[1];
+        if (st == SDD_OK) st = enqueue_solve_system(c, c->step_call[parity], q);
+        cu(cudaEventRecord(c->pev[4], q));
     }
-    if (st == SDD_OK) st = c->pipe && with_pending ? prepare_parts(c, s, true, false) : prepare(c, s);
+    if (st == SDD_OK) st = c->pipe ? prepare_parts(c, s, true, false) : prepare(c, s);
     if (st == SDD_OK) st = enqueue_cv_refresh(c, K, s);
     OutDev o{};
     o.mean_xi = c->iface_stats[0].p;
@@ -1821,10 +1846,13 @@ static sdd_status capture_step(sdd_ctx* c, const sdd_step_params* p, int K, int 
     }
     rec_ext(c->ev[3], s);
     if (st == SDD_OK) {
-        c->step_call[parity] =
-            make_solve_call(c, p->Dt, p->rtol, p->max_iter, c->fld[1 - parity][0].p, c->fld[1 - parity][1].p);
-        st = enqueue_solve_setup(c, c->step_call[parity], p->Dt, o.mean_xi, o.mean_eta, s);
-        if (st == SDD_OK && !c->pipe) st = enqueue_solve_iterate(c, c->step_call[parity], s);
+        st = enqueue_solve_dirichlet(c, c->step_call[parity], o.mean_xi, o.mean_eta, s);
+        if (c->pipe) {
+            cu(cudaStreamWaitEvent(s, c->pev[4], 0));   // this step's systems, built beside the paths
+        } else if (st == SDD_OK) {
+            st = enqueue_solve_system(c, c->step_call[parity], s);
+            if (st == SDD_OK) st = enqueue_solve_iterate(c, c->step_call[parity], s);
+        }
     }
     if (st == SDD_OK) cu(launch_bump_step(c->d_step.p, s));
     rec_ext(c->ev[4], s);
@@ -1892,12 +1920,18 @@ sdd_status sdd_step(sdd_ctx* c, const sdd_step_params* p)
         CU(c, cudaStreamSynchronize(c->stream));
         // pipelined steps where the solve's iterations are one launch and the
         // paths do not read the fields (the field-gradient control variate does)
-        const SolveCall probe = make_solve_call(c, p->Dt, p->rtol, p->max_iter, nullptr, nullptr);
+        const SolveCall probe = make_solve_call(c, p->Dt, p->rtol, p->max_iter, nullptr, nullptr, nullptr, nullptr,
+                                                nullptr);
         const size_t rec_bytes = c->cv_mode ? sizeof(float4) : sizeof(float2);
         c->pipe = c->pipe_allowed && solve_single_launch(probe) && c->cv_mode != SDD_CV_FIELDS && c->step_plan.ntasks > 0 &&
                   (size_t)c->step_plan.total_paths * rec_bytes <= (8ULL << 30);
         if (c->pipe) {
-            if (!c->pipe_stream) CU(c, cudaStreamCreateWithFlags(&c->pipe_stream, cudaStreamNonBlocking));
+            if (!c->pipe_stream) {
+                // its kernels take SMs before the waiting blocks of the path kernel
+                int least = 0, greatest = 0;
+                CU(c, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+                CU(c, cudaStreamCreateWithPriority(&c->pipe_stream, cudaStreamNonBlocking, greatest));
+            }
             for (cudaEvent_t& e : c->pev)
                 if (!e) CU(c, cudaEventCreate(&e));
             CU(c, c->surv.alloc(((size_t)c->step_plan.total_paths * rec_bytes + sizeof(float4) - 1) / sizeof(float4)));

@@ -112,6 +112,7 @@ struct ScoreArgs {
     Partial* partials;
     const void* surv;
     int32_t ntasks;
+    int32_t group_warps;      // warps per task: 1, 2, 4 or 8
     const uint8_t* node_mask;
 };
 

@@ -57,32 +57,46 @@ __device__ __forceinline__ void bilinear_coefs2(double u00, double u10, double u
 
 __device__ __forceinline__ bool bad_w(float v) { return !(v > 0.0f) || !isfinite(v); }
 
-__global__ void k_prep_cells(const float* __restrict__ w, const double* __restrict__ xi,
-                             const double* __restrict__ eta, int nx, int ny, float4* __restrict__ bcoef,
-                             float4* __restrict__ fcoef, int* status)
-{
-    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
-    const int iy = blockIdx.y * blockDim.y + threadIdx.y;
-    if (ix >= nx - 1 || iy >= ny - 1) return;
-    const long long cell = (long long)iy * (nx - 1) + ix;
-    if (bcoef) {
-        // every node is checked by the cell that has it as lower-left corner,
-        // the last row and column by the cells next to them
-        bool bad = bad_w(w[(long long)iy * nx + ix]);
-        if (ix == nx - 2) bad |= bad_w(w[(long long)iy * nx + ix + 1]);
-        if (iy == ny - 2) bad |= bad_w(w[(long long)(iy + 1) * nx + ix]);
-        if (ix == nx - 2 && iy == ny - 2) bad |= bad_w(w[(long long)(iy + 1) * nx + ix + 1]);
-        if (bad) atomicOr(status, STATUS_BAD_W);
+// One block per 32 x 8 cells: the drift at the tile's 33 x 9 nodes once (in
+// shared memory, double precision), then each cell's records.
+constexpr int PREP_TX = 32, PREP_TY = 8;
 
+__global__ void __launch_bounds__(PREP_TX * PREP_TY) k_prep_cells(const float* __restrict__ w,
+                                                                  const double* __restrict__ xi,
+                                                                  const double* __restrict__ eta, int nx, int ny,
+                                                                  float4* __restrict__ bcoef,
+                                                                  float4* __restrict__ fcoef, int* status)
+{
+    __shared__ double2 bn[PREP_TY + 1][PREP_TX + 1];
+    const int ix0 = blockIdx.x * PREP_TX, iy0 = blockIdx.y * PREP_TY;
+    const int ix = ix0 + threadIdx.x, iy = iy0 + threadIdx.y;
+    const bool cell_in = ix < nx - 1 && iy < ny - 1;
+    if (bcoef) {
         const double rx = 0.5 * (double)(nx - 1), ry = 0.5 * (double)(ny - 1);
-        const double2 b00 = node_drift(w, nx, ny, ix, iy, rx, ry);
-        const double2 b10 = node_drift(w, nx, ny, ix + 1, iy, rx, ry);
-        const double2 b01 = node_drift(w, nx, ny, ix, iy + 1, rx, ry);
-        const double2 b11 = node_drift(w, nx, ny, ix + 1, iy + 1, rx, ry);
-        bilinear_coefs2(b00.x, b10.x, b01.x, b11.x, b00.y, b10.y, b01.y, b11.y, bcoef[2 * cell + 0],
-                        bcoef[2 * cell + 1]);
+        const int tid = threadIdx.y * PREP_TX + threadIdx.x;
+        for (int k = tid; k < (PREP_TX + 1) * (PREP_TY + 1); k += PREP_TX * PREP_TY) {
+            const int ti = k % (PREP_TX + 1), tj = k / (PREP_TX + 1);
+            const int i = ix0 + ti, j = iy0 + tj;
+            if (i < nx && j < ny) bn[tj][ti] = node_drift(w, nx, ny, i, j, rx, ry);
+        }
+        __syncthreads();
+        if (cell_in) {
+            // every node is checked by the cell that has it as lower-left corner,
+            // the last row and column by the cells next to them
+            bool bad = bad_w(w[(long long)iy * nx + ix]);
+            if (ix == nx - 2) bad |= bad_w(w[(long long)iy * nx + ix + 1]);
+            if (iy == ny - 2) bad |= bad_w(w[(long long)(iy + 1) * nx + ix]);
+            if (ix == nx - 2 && iy == ny - 2) bad |= bad_w(w[(long long)(iy + 1) * nx + ix + 1]);
+            if (bad) atomicOr(status, STATUS_BAD_W);
+            const int tx = threadIdx.x, ty = threadIdx.y;
+            const double2 b00 = bn[ty][tx], b10 = bn[ty][tx + 1], b01 = bn[ty + 1][tx], b11 = bn[ty + 1][tx + 1];
+            const long long cell = (long long)iy * (nx - 1) + ix;
+            bilinear_coefs2(b00.x, b10.x, b01.x, b11.x, b00.y, b10.y, b01.y, b11.y, bcoef[2 * cell + 0],
+                            bcoef[2 * cell + 1]);
+        }
     }
-    if (fcoef) {
+    if (fcoef && cell_in) {
+        const long long cell = (long long)iy * (nx - 1) + ix;
         const long long n00 = (long long)iy * nx + ix;
         const long long n01 = n00 + nx;
         bilinear_coefs2(xi[n00], xi[n00 + 1], xi[n01], xi[n01 + 1], eta[n00], eta[n00 + 1], eta[n01], eta[n01 + 1],
@@ -181,8 +195,8 @@ __global__ void k_faces32(const double* __restrict__ f64, float* __restrict__ f3
 cudaError_t launch_prep_cells(const float* w, const double* xi, const double* eta, int nx, int ny, float4* bcoef,
                               float4* fcoef, int* status, cudaStream_t s)
 {
-    const dim3 block(32, 8);
-    const dim3 grid((nx - 1 + 31) / 32, (ny - 1 + 7) / 8);
+    const dim3 block(PREP_TX, PREP_TY);
+    const dim3 grid((nx - 1 + PREP_TX - 1) / PREP_TX, (ny - 1 + PREP_TY - 1) / PREP_TY);
     k_prep_cells<<<grid, block, 0, s>>>(w, xi, eta, nx, ny, bcoef, fcoef, status);
     return cudaGetLastError();
 }

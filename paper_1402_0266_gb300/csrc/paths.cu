@@ -611,47 +611,62 @@ __global__ void __launch_bounds__(512, 2) k_paths_exp(const PathArgs a)
 
 // Scores of the paths that survived a mesh step, once the fields of the step's
 // start are final (the estimate of the next mesh step runs beside the
-// subdomain solve that produces them): one warp per task, the task's paths in
-// order, xi and eta at each end point minus the path's control-variate sums,
-// added to the task's partial sums after the path kernel's.
+// subdomain solve that produces them). A task's paths go to a group of
+// a.group_warps warps (lane l of warp g takes paths path0 + 32 g + l, then
+// every 32 group_warps-th), each lane sums xi and eta at its end points minus
+// the path's control-variate sums; the group's warp sums are added in warp
+// order to the task's partial sums after the path kernel's.
 template <bool CV>
 __global__ void __launch_bounds__(256) k_score_surv(const ScoreArgs a)
 {
-    const int t = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (t >= a.ntasks) return;
-    const Task task = a.tasks[t];
-    if (a.node_mask && !a.node_mask[task.node]) return;
-    const NodeDev& nd = a.nodes[task.node];
-    const InstDev I = a.inst[nd.inst];
-    const float x0 = nd.xf, y0 = nd.yf;
-    Acc ax{0.f, 0.f, 0.f, 0.f}, ae{0.f, 0.f, 0.f, 0.f};
-    const int end = task.path0 + task.npaths;
-    for (int p = task.path0 + lane; p < end; p += 32) {
-        const long long si = nd.rec0 + p;
-        float4 r;
-        if (CV) {
-            r = static_cast<const float4*>(a.surv)[si];
-        } else {
-            const float2 q = static_cast<const float2*>(a.surv)[si];
-            r = make_float4(q.x, q.y, 0.f, 0.f);
-        }
-        if (r.x < 0.f) continue;   // the path left the domain
-        const Cell c = locate(I, I.fcoef, f2(r.x, r.y));
-        float4 f0, f1;
-        load_cell(c.p, f0, f1);
-        const float2 v = eval2(f0, f1, c.st);
-        ax.add(v.x - r.z - x0);
-        ae.add(v.y - r.w - y0);
+    __shared__ double red[8][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gw = a.group_warps;
+    const int local = warp / gw, wig = warp - local * gw;
+    const long long t = (long long)blockIdx.x * (8 / gw) + local;
+    bool active = t < a.ntasks;
+    Task task{};
+    if (active) {
+        task = a.tasks[t];
+        if (a.node_mask && !a.node_mask[task.node]) active = false;
     }
-    const double sx = warp_sum(ax.sum()), qx = warp_sum(ax.sumsq());
-    const double se = warp_sum(ae.sum()), qe = warp_sum(ae.sumsq());
-    if (lane == 0) {
+    Acc ax{0.f, 0.f, 0.f, 0.f}, ae{0.f, 0.f, 0.f, 0.f};
+    if (active) {
+        const NodeDev& nd = a.nodes[task.node];
+        const InstDev I = a.inst[nd.inst];
+        const float x0 = nd.xf, y0 = nd.yf;
+        const int end = task.path0 + task.npaths;
+        for (int p = task.path0 + 32 * wig + lane; p < end; p += 32 * gw) {
+            const long long si = nd.rec0 + p;
+            float4 r;
+            if (CV) {
+                r = static_cast<const float4*>(a.surv)[si];
+            } else {
+                const float2 q = static_cast<const float2*>(a.surv)[si];
+                r = make_float4(q.x, q.y, 0.f, 0.f);
+            }
+            if (r.x < 0.f) continue;   // the path left the domain
+            const Cell c = locate(I, I.fcoef, f2(r.x, r.y));
+            float4 f0, f1;
+            load_cell(c.p, f0, f1);
+            const float2 v = eval2(f0, f1, c.st);
+            ax.add(v.x - r.z - x0);
+            ae.add(v.y - r.w - y0);
+        }
+    }
+    const double v[4] = {warp_sum(ax.sum()), warp_sum(ax.sumsq()), warp_sum(ae.sum()), warp_sum(ae.sumsq())};
+    if (lane == 0)
+        for (int q = 0; q < 4; ++q) red[warp][q] = v[q];
+    __syncthreads();
+    if (active && wig == 0 && lane == 0) {
+        double tot[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int g = 0; g < gw; ++g)
+            for (int q = 0; q < 4; ++q) tot[q] += red[warp + g][q];
         Partial& P = a.partials[t];
-        P.s_xi += sx;
-        P.q_xi += qx;
-        P.s_eta += se;
-        P.q_eta += qe;
+        P.s_xi += tot[0];
+        P.q_xi += tot[1];
+        P.s_eta += tot[2];
+        P.q_eta += tot[3];
     }
 }
 
@@ -866,9 +881,11 @@ cudaError_t launch_paths(const PathArgs& a, int exit_mode, bool record, int grid
 cudaError_t launch_score_surv(const ScoreArgs& a, bool cv, cudaStream_t s)
 {
     if (a.ntasks <= 0) return cudaSuccess;
+    if (a.group_warps != 1 && a.group_warps != 2 && a.group_warps != 4 && a.group_warps != 8)
+        return cudaErrorInvalidValue;
     const int block = 256;
-    const long long threads = (long long)a.ntasks * 32;
-    const int grid = (int)((threads + block - 1) / block);
+    const long long per_block = 8 / a.group_warps;
+    const int grid = (int)((a.ntasks + per_block - 1) / per_block);
     if (cv) k_score_surv<true><<<grid, block, 0, s>>>(a);
     else k_score_surv<false><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
