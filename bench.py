@@ -112,15 +112,19 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def dist_init():
+def dist_init(backend=None):
+    """One process per GPU under torchrun: NCCL where there is a GPU, else gloo (host tensors)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
     return world, rank, local
 
 
@@ -135,9 +139,18 @@ def allreduce(vals, op, world):
         return vals
     import torch
     import torch.distributed as dist
-    t = torch.tensor(vals, dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor(vals, dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return t.tolist()
+
+
+def whole_job(units, seconds, world):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time.
+    Returns (units / s, total units, max seconds)."""
+    tot = allreduce([float(units)], "sum", world)[0]
+    mx = allreduce([float(seconds)], "max", world)[0]
+    return tot / mx, tot, mx
 
 
 # ------------------------------------------------------------------ oracle leg
@@ -288,8 +301,8 @@ def run_ours(args, world, rank, local):
     step_ms = [ev0[k].elapsed_time(ev1[k]) for k in range(K)]
     total_ms = sum(step_ms)
     path_steps = int(steps_dev.sum().item())
-    tot_steps, max_ms = allreduce([float(path_steps), 0.0], "sum", world)[0], allreduce([total_ms], "max", world)[0]
-    value = tot_steps / (max_ms / 1e3)
+    value, tot_steps, max_s = whole_job(path_steps, total_ms / 1e3, world)
+    max_ms = max_s * 1e3
     nodes = len(sdd.sdd_interface_nodes(ctx)[0])
     nodes_per_s = world * nodes * K / (max_ms / 1e3)
 
@@ -329,9 +342,27 @@ def run_ours(args, world, rank, local):
         sdd.sdd_flush(ctx)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
-        e2e_tot, e2e_max = allreduce([float(e2e_steps), 0.0], "sum", world)[0], allreduce([el], "max", world)[0]
-        e2e = {"value": e2e_tot / e2e_max, "unit": UNIT, "h2d_bytes_per_step": n * n * 4,
+        e2e_value = whole_job(e2e_steps, el, world)[0]
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * n * 4,
                "d2h_bytes_per_step": nn * 48}
+
+    # the path kernel alone (unpipelined steps): in the timed pipelined steps it shares 64 SMs with
+    # the previous step's solve for part of its launch
+    alone = None
+    if pipelined:
+        reset()
+        sdd.sdd_set_pipeline(ctx, False)
+        a_ms = []
+        for k in range(min(K, 8)):
+            flush.zero_()
+            sdd.sdd_set_w(ctx, w_all[k])
+            sdd.sdd_step(ctx, **sp)
+            a_ms.append(sdd.sdd_last_step_info(ctx)["paths_ms"])
+        sdd.sdd_set_pipeline(ctx, True)
+        a_mean = statistics.mean(a_ms[1:] if len(a_ms) > 1 else a_ms)
+        a_ach = ALG_OPS_PER_PATH_STEP * steps_per_launch / (a_mean / 1e3) / 1e12
+        alone = {"paths_kernel_ms": a_mean, "achieved": a_ach, "frac": a_ach / peak,
+                 "note": "unpipelined steps after the timed region (the same launches without the solve beside)"}
 
     # the same mesh steps with the control variate of the previous fields' gradient:
     # throughput, and the variance against the plain estimator on the same state
@@ -402,7 +433,8 @@ def run_ours(args, world, rank, local):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_paths", "ops_per_path_step": ALG_OPS_PER_PATH_STEP,
-                         "peak_basis": f"{props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz"},
+                         "peak_basis": f"{props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz",
+                         "alone": alone},
             "equal_error": equal_error,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -1193,7 +1193,7 @@ sdd_status tabulate_into_ctx(sdd_ctx* c, const float* theta, const float* norm, 
     float tf[kMaxCvSlices];
     slice_fracs(K, slices, tf);
     CU(c, launch_cv_tabulate(theta, norm, c->cv_nfa.p, c->cv_nfb.p, c->nx, c->ny, slices, tf, c->cv_table64.p,
-                             c->sm_count, c->stream));
+                             c->d_status.p, c->sm_count, c->stream));
     if ((st = set_table_from64(c, slices)) != SDD_OK) return st;
     drop_graphs_fn(c);
     return SDD_OK;
@@ -1230,7 +1230,7 @@ sdd_status enqueue_cv_refresh(sdd_ctx* c, int K, cudaStream_t s)
         CU(c, launch_node_features(c->w.p, c->nx, c->ny, c->cv_w64.p, c->cv_r64.p, c->cv_gw.p, c->cv_nfa.p,
                                    c->cv_nfb.p, s));
         CU(c, launch_cv_tabulate(c->cv_theta.p, c->cv_norm.p, c->cv_nfa.p, c->cv_nfb.p, c->nx, c->ny, c->cv_slices,
-                                 tf, c->cv_table64.p, c->sm_count, s));
+                                 tf, c->cv_table64.p, c->d_status.p, c->sm_count, s));
         CU(c, launch_cv_cells(c->cv_table64.p, c->cv_slices, c->nx, c->ny, c->cvcoef.p, s));
     } else if (c->cv_mode == 3) {
         CU(c, launch_field_grad(c->fld[c->cur][0].p, c->fld[c->cur][1].p, c->nx, c->ny, c->cv_table64.p, s));

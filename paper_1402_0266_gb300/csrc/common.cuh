@@ -181,7 +181,8 @@ cudaError_t launch_mlp_reduce(const float* part, int nblk, float inv_rows, float
 cudaError_t launch_mlp_adam(float* theta, float* m, float* v, const float* part, int nblk, double lr, long long t,
                             float inv_rows, float* losses, long long steps, long long step, cudaStream_t s);
 cudaError_t launch_cv_tabulate(const float* theta, const float* norm, const float4* nfa, const float2* nfb, int nx,
-                               int ny, int slices, const float* tfrac, double* table, int sm_count, cudaStream_t s);
+                               int ny, int slices, const float* tfrac, double* table, int* status, int sm_count,
+                               cudaStream_t s);
 
 cudaError_t launch_rng_draw(uint64_t seed, const uint32_t* ctrs, long long count, uint32_t* words, float* normals,
                             cudaStream_t s);

@@ -19,8 +19,8 @@
 //   k_mlp_reduce / k_mlp_adam   the batch gradient; Adam (Kingma & Ba 2015);
 //   k_cv_tabulate               the table G at every node and time slice by
 //                               forward-mode differentiation; the 64 x 64 layer
-//                               on the tensor cores (BF16 in, FP32 accumulate,
-//                               mma.sync m16n8k16), everything else FP32.
+//                               on the tensor cores (tcgen05.mma, BF16 in, FP32
+//                               accumulate in tensor memory), everything else FP32.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -453,15 +453,6 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
     return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
 struct TabArgs {
     const float* theta;     // [2][kMlpStride]
     const float* norm;      // mu[5], s[5]
@@ -469,39 +460,128 @@ struct TabArgs {
     const float2* nfb;      // (dr/dx, dr/dy) per node
     int nx, ny, slices;
     double* table;          // (slices, ny, nx, 4)
+    int* status;            // STATUS_TIMEOUT if a bounded wait runs out
     float tfrac[kMaxCvSlices];
 };
 
-constexpr int TAB_WARPS = 4;
+// ---- the 64 x 64 layer on the fifth-generation tensor cores
+//
+// A CTA of 128 threads takes tiles of 128 points (point p = slice * nodes +
+// node). Thread t computes layer 1 of point t and writes three BF16 rows into
+// shared memory: h1 = tanh(a1), u1 = (1 - h1^2) W1 dz/dx, v1 = (1 - h1^2) W1
+// dz/dy. One thread issues the three products h1 W2^T, u1 W2^T, v1 W2^T as
+// tcgen05.mma (M = 128, N = 64, K = 16, BF16 in, FP32 accumulate) into three
+// 64-column accumulators in tensor memory, committed to an mbarrier; then
+// warp w reads lanes 32 w .. 32 w + 31 (its threads' points) back with
+// tcgen05.ld and forms d/dx = sum_j w3_j (1 - tanh(a2_j)^2) (W2 u1)_j, d/dy
+// likewise.
+//
+// Operands are K-major without swizzle: 8 x 8 BF16 core matrices of 128
+// contiguous bytes (a row's 8 consecutive k at 16-byte pitch); core matrices
+// adjacent in k are 128 B apart (leading byte offset), 8-row groups 1024 B
+// (stride byte offset). Byte offset of (row r, k): (r / 8) 1024 + (k / 8) 128
+// + (r % 8) 16 + (k % 8) 2.
 
-// One warp evaluates 16 nodes at a time for one network (blockIdx.y). Rows of
-// the m16n8k16 A operand are nodes; three operands per tile: h1 = tanh(a1),
-// u1 = (1 - h1^2) W1 dz/dx, v1 = (1 - h1^2) W1 dz/dy. Lane (g, q) = (lane / 4,
-// lane % 4) holds rows g, g + 8 and, per 16-wide k step kk, the units
-// 16 kk + 2 q + {0, 1, 8, 9} of A, and after the MMA the units 8 n + 2 q + {0, 1}
-// of every 8-wide n tile. W2 (B operand, B[k][n] = W2[n][k]) stays in registers.
-__global__ void __launch_bounds__(TAB_WARPS * 32) k_cv_tabulate(const TabArgs a)
+constexpr int TC_ROWS = 128;                         // points per tile = MMA M = threads per CTA
+constexpr int TC_OPERAND_BYTES = TC_ROWS * H * 2;    // one 128 x 64 BF16 operand
+constexpr int TC_W2_BYTES = H * H * 2;
+constexpr int TC_TMEM_COLS = 256;                    // three 64-column FP32 accumulators, rounded to a power of two
+// Dynamic shared memory requested per CTA: above a third of the SM's 228 KB,
+// so that at most two CTAs (2 x 256 tensor-memory columns of 512) share an SM
+// and tcgen05.alloc never waits.
+constexpr int TC_SMEM_REQUEST = 100 * 1024;
+constexpr long long TC_WAIT_LIMIT = 1LL << 26;       // polls of the MMA mbarrier before giving up
+
+struct TcSmem {
+    alignas(1024) unsigned char a[3][TC_OPERAND_BYTES];
+    alignas(1024) unsigned char b[TC_W2_BYTES];
+    float w1[H * D], b1[H], b2[H], w3[H];
+    alignas(8) unsigned long long mbar;
+    uint32_t tmem;
+    int abort;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t core_off(int r, int k) { return (r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
+
+// Shared-memory matrix descriptor: start, leading and stride byte offsets (all
+// >> 4), the fixed 0b001 at bits 46-48, no swizzle (bits 61-63 zero).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
 {
-    __shared__ float sw1[H * D], sb1[H], sb2[H], sw3[H];
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ULL << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A
+// and B (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits
+// 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t tc_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        :: "r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc) : "memory");
+}
+
+// 16 consecutive accumulator columns of the thread's lane; the wait is in the
+// same statement, so no use of the registers can be scheduled before it.
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];\n\ttcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+__global__ void __launch_bounds__(TC_ROWS) k_cv_tabulate(const TabArgs a)
+{
+    extern __shared__ unsigned char smem_raw[];
+    TcSmem& S = *reinterpret_cast<TcSmem*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     const int f = blockIdx.y;
+    const int t = threadIdx.x, warp = t >> 5;
     const float* th = a.theta + (long long)f * kMlpStride;
-    for (int p = threadIdx.x; p < H * D; p += blockDim.x) sw1[p] = th[OW1 + p];
-    for (int p = threadIdx.x; p < H; p += blockDim.x) {
-        sb1[p] = th[OB1 + p];
-        sb2[p] = th[OB2 + p];
-        sw3[p] = th[OW3 + p];
+
+    // weights: layer 1 and the biases in FP32, W2 (B operand, rows n, k-major) in BF16
+    for (int p = t; p < H * D; p += TC_ROWS) S.w1[p] = th[OW1 + p];
+    for (int p = t; p < H; p += TC_ROWS) {
+        S.b1[p] = th[OB1 + p];
+        S.b2[p] = th[OB2 + p];
+        S.w3[p] = th[OW3 + p];
     }
+    for (int p = t; p < H * H / 8; p += TC_ROWS) {
+        const int n = p / (H / 8), k0 = (p % (H / 8)) * 8;
+        const float* wr = th + OW2 + n * H + k0;
+        const uint4 v = make_uint4(pack_bf16(wr[0], wr[1]), pack_bf16(wr[2], wr[3]), pack_bf16(wr[4], wr[5]),
+                                   pack_bf16(wr[6], wr[7]));
+        *reinterpret_cast<uint4*>(S.b + core_off(n, k0)) = v;
+    }
+    if (t == 0) {
+        S.abort = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&S.mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(&S.tmem)), "n"(TC_TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
-    uint32_t B[8][4][2];
-#pragma unroll
-    for (int n = 0; n < 8; ++n)
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-            const float* wr = th + OW2 + (8 * n + g) * H + 16 * kk + 2 * q;
-            B[n][kk][0] = pack_bf16(wr[0], wr[1]);
-            B[n][kk][1] = pack_bf16(wr[8], wr[9]);
-        }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = S.tmem;
+
     float mu[D], sc[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) {
@@ -509,109 +589,128 @@ __global__ void __launch_bounds__(TAB_WARPS * 32) k_cv_tabulate(const TabArgs a)
         sc[c] = a.norm[D + c];
     }
     const long long nn = (long long)a.nx * a.ny;
-    const long long tiles = (nn + 15) / 16;
-    const long long warp0 = (long long)blockIdx.x * TAB_WARPS + (threadIdx.x >> 5);
-    const long long nwarps = (long long)gridDim.x * TAB_WARPS;
-    for (long long tl = warp0; tl < tiles; tl += nwarps) {
-        // the lane's two nodes (clamped in the ragged last tile; their results are not written)
-        long long node[2];
-        float z[2][D], dzx[2][D], dzy[2][D];
+    const long long points = nn * a.slices;
+    const long long tiles = (points + TC_ROWS - 1) / TC_ROWS;
+    constexpr uint32_t idesc = tc_idesc(TC_ROWS, H);
+    uint32_t phase = 0;
+    for (long long tl = blockIdx.x; tl < tiles; tl += gridDim.x) {
+        // layer 1 of this thread's point (clamped in the ragged last tile; not written)
+        const long long pt = tl * TC_ROWS + t;
+        const long long pc = pt < points ? pt : points - 1;
+        const int sl = (int)(pc / nn);
+        const long long node = pc - (long long)sl * nn;
+        {
+            const int i = (int)(node % a.nx), j = (int)(node / a.nx);
+            const float4 fa = a.nfa[node];
+            const float2 fb = a.nfb[node];
+            float z[D], dzx[D], dzy[D];
+            z[0] = ((float)i / (float)(a.nx - 1) - mu[0]) * sc[0];
+            z[1] = ((float)j / (float)(a.ny - 1) - mu[1]) * sc[1];
+            z[2] = (a.tfrac[sl] - mu[2]) * sc[2];
+            z[3] = (fa.x - mu[3]) * sc[3];
+            z[4] = (fa.y - mu[4]) * sc[4];
+            dzx[0] = sc[0]; dzx[1] = 0.f; dzx[2] = 0.f; dzx[3] = fa.z * sc[3]; dzx[4] = fb.x * sc[4];
+            dzy[0] = 0.f; dzy[1] = sc[1]; dzy[2] = 0.f; dzy[3] = fa.w * sc[3]; dzy[4] = fb.y * sc[4];
+#pragma unroll 1
+            for (int k0 = 0; k0 < H; k0 += 8) {
+                uint32_t ph[4], pu[4], pv[4];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            node[h] = tl * 16 + g + 8 * h;
-            const long long k = node[h] < nn ? node[h] : nn - 1;
-            const int i = (int)(k % a.nx), j = (int)(k / a.nx);
-            const float4 fa = a.nfa[k];
-            const float2 fb = a.nfb[k];
-            z[h][2] = 0.f;   // the time input is per slice
-            z[h][0] = ((float)i / (float)(a.nx - 1) - mu[0]) * sc[0];
-            z[h][1] = ((float)j / (float)(a.ny - 1) - mu[1]) * sc[1];
-            z[h][3] = (fa.x - mu[3]) * sc[3];
-            z[h][4] = (fa.y - mu[4]) * sc[4];
-            dzx[h][0] = sc[0]; dzx[h][1] = 0.f; dzx[h][2] = 0.f; dzx[h][3] = fa.z * sc[3]; dzx[h][4] = fb.x * sc[4];
-            dzy[h][0] = 0.f; dzy[h][1] = sc[1]; dzy[h][2] = 0.f; dzy[h][3] = fa.w * sc[3]; dzy[h][4] = fb.y * sc[4];
-        }
-        for (int sl = 0; sl < a.slices; ++sl) {
-            const float zt = (a.tfrac[sl] - mu[2]) * sc[2];
-            // layer 1 for the lane's units, packed straight into the A operands
-            uint32_t Ah[4][4], Au[4][4], Av[4][4];
+                for (int e = 0; e < 8; e += 2) {
+                    float hv[2], uv[2], vv[2];
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
+                    for (int q = 0; q < 2; ++q) {
+                        const float* w1 = S.w1 + (k0 + e + q) * D;
+                        float a1 = S.b1[k0 + e + q];
 #pragma unroll
-                for (int hi = 0; hi < 2; ++hi)       // units +0,+1 (hi = 0) or +8,+9 (hi = 1)
+                        for (int c = 0; c < D; ++c) a1 = fmaf(w1[c], z[c], a1);
+                        const float t1 = tanh_approx(a1);
+                        const float k1 = 1.f - t1 * t1;
+                        float ux = 0.f, uy = 0.f;
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {    // row g or g + 8
-                        float hv[2], uv[2], vv[2];
-#pragma unroll
-                        for (int e = 0; e < 2; ++e) {
-                            const int j = 16 * kk + 2 * q + 8 * hi + e;
-                            const float* w1 = sw1 + j * D;
-                            float a1 = sb1[j];
-                            a1 = fmaf(w1[0], z[h][0], a1);
-                            a1 = fmaf(w1[1], z[h][1], a1);
-                            a1 = fmaf(w1[2], zt, a1);
-                            a1 = fmaf(w1[3], z[h][3], a1);
-                            a1 = fmaf(w1[4], z[h][4], a1);
-                            const float t1 = tanh_approx(a1);
-                            const float k1 = 1.f - t1 * t1;
-                            float ux = w1[0] * dzx[h][0] + w1[3] * dzx[h][3] + w1[4] * dzx[h][4];
-                            float uy = w1[1] * dzy[h][1] + w1[3] * dzy[h][3] + w1[4] * dzy[h][4];
-                            hv[e] = t1;
-                            uv[e] = k1 * ux;
-                            vv[e] = k1 * uy;
+                        for (int c = 0; c < D; ++c) {
+                            ux = fmaf(w1[c], dzx[c], ux);
+                            uy = fmaf(w1[c], dzy[c], uy);
                         }
-                        const int r = 2 * hi + h;    // register order: (g, lo) (g+8, lo) (g, hi) (g+8, hi)
-                        Ah[kk][r] = pack_bf16(hv[0], hv[1]);
-                        Au[kk][r] = pack_bf16(uv[0], uv[1]);
-                        Av[kk][r] = pack_bf16(vv[0], vv[1]);
+                        hv[q] = t1;
+                        uv[q] = k1 * ux;
+                        vv[q] = k1 * uy;
                     }
-            // layer 2: h1 W2^T, then the lane's w3_j (1 - h2_j^2) weights
-            float wq[8][4];
-#pragma unroll
-            for (int n = 0; n < 8; ++n) {
-                float c[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) mma_bf16(c, Ah[kk], B[n][kk][0], B[n][kk][1]);
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int j = 8 * n + 2 * q + (e & 1);
-                    const float h2 = tanh_approx(c[e] + sb2[j]);
-                    wq[n][e] = sw3[j] * (1.f - h2 * h2);
+                    ph[e / 2] = pack_bf16(hv[0], hv[1]);
+                    pu[e / 2] = pack_bf16(uv[0], uv[1]);
+                    pv[e / 2] = pack_bf16(vv[0], vv[1]);
                 }
-            }
-            // d/dx and d/dy: sum_j w3_j (1 - h2_j^2) (W2 u1)_j, likewise for v1
-            float gx[2] = {0.f, 0.f}, gy[2] = {0.f, 0.f};
-#pragma unroll
-            for (int n = 0; n < 8; ++n) {
-                float cu[4] = {0.f, 0.f, 0.f, 0.f}, cv[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    mma_bf16(cu, Au[kk], B[n][kk][0], B[n][kk][1]);
-                    mma_bf16(cv, Av[kk], B[n][kk][0], B[n][kk][1]);
-                }
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    gx[e >> 1] = fmaf(wq[n][e], cu[e], gx[e >> 1]);
-                    gy[e >> 1] = fmaf(wq[n][e], cv[e], gy[e >> 1]);
-                }
-            }
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                gx[h] += __shfl_xor_sync(0xffffffffu, gx[h], 1);
-                gx[h] += __shfl_xor_sync(0xffffffffu, gx[h], 2);
-                gy[h] += __shfl_xor_sync(0xffffffffu, gy[h], 1);
-                gy[h] += __shfl_xor_sync(0xffffffffu, gy[h], 2);
-            }
-            if (q == 0) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h)
-                    if (node[h] < nn) {
-                        double* o = a.table + ((long long)sl * nn + node[h]) * 4 + 2 * f;
-                        o[0] = (double)gx[h];
-                        o[1] = (double)gy[h];
-                    }
+                const uint32_t o = core_off(t, k0);
+                *reinterpret_cast<uint4*>(S.a[0] + o) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+                *reinterpret_cast<uint4*>(S.a[1] + o) = make_uint4(pu[0], pu[1], pu[2], pu[3]);
+                *reinterpret_cast<uint4*>(S.a[2] + o) = make_uint4(pv[0], pv[1], pv[2], pv[3]);
             }
         }
+        // the operands, written through the generic proxy, become visible to the tensor cores
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t bbase = smem_u32(S.b);
+#pragma unroll
+            for (int g = 0; g < 3; ++g) {
+                const uint32_t abase = smem_u32(S.a[g]);
+#pragma unroll
+                for (int kk = 0; kk < H / 16; ++kk)
+                    tc_mma(tmem + (uint32_t)(H * g), smem_desc(abase + 256 * kk, 128, 1024),
+                           smem_desc(bbase + 256 * kk, 128, 1024), idesc, kk > 0 ? 1u : 0u);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_u32(&S.mbar)) : "memory");
+        }
+        // wait for the products (bounded)
+        {
+            uint32_t done = 0;
+            for (long long it = 0; it < TC_WAIT_LIMIT && !done; ++it)
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                    "selp.u32 %0, 1, 0, p;\n\t}"
+                    : "=r"(done) : "r"(smem_u32(&S.mbar)), "r"(phase) : "memory");
+            if (!done) S.abort = 1;
+        }
+        phase ^= 1u;
+        __syncthreads();
+        if (S.abort) {
+            if (t == 0) atomicOr(a.status, STATUS_TIMEOUT);
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // epilogue: this thread's row from the three accumulators, 16 columns at a time
+        float gx = 0.f, gy = 0.f;
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+#pragma unroll 1
+        for (int c0 = 0; c0 < H; c0 += 16) {
+            float vh[16], vu[16], vv[16];
+            tc_ld16(lane_base + (uint32_t)c0, vh);
+            tc_ld16(lane_base + (uint32_t)(H + c0), vu);
+            tc_ld16(lane_base + (uint32_t)(2 * H + c0), vv);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const float h2 = tanh_approx(vh[k] + S.b2[c0 + k]);
+                const float wq = S.w3[c0 + k] * (1.f - h2 * h2);
+                gx = fmaf(wq, vu[k], gx);
+                gy = fmaf(wq, vv[k], gy);
+            }
+        }
+        if (pt < points) {
+            double* o = a.table + pt * 4 + 2 * f;
+            o[0] = (double)gx;
+            o[1] = (double)gy;
+        }
+        // every warp is done with the accumulators and the operands before the next tile
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "n"(TC_TMEM_COLS));
     }
 }
 
@@ -704,8 +803,10 @@ cudaError_t launch_mlp_adam(float* theta, float* m, float* v, const float* part,
 }
 
 cudaError_t launch_cv_tabulate(const float* theta, const float* norm, const float4* nfa, const float2* nfb, int nx,
-                               int ny, int slices, const float* tfrac, double* table, int sm_count, cudaStream_t s)
+                               int ny, int slices, const float* tfrac, double* table, int* status, int sm_count,
+                               cudaStream_t s)
 {
+    static_assert(sizeof(TcSmem) + 1024 <= TC_SMEM_REQUEST, "tabulation shared memory");
     TabArgs a{};
     a.theta = theta;
     a.norm = norm;
@@ -715,11 +816,15 @@ cudaError_t launch_cv_tabulate(const float* theta, const float* norm, const floa
     a.ny = ny;
     a.slices = slices;
     a.table = table;
+    a.status = status;
     for (int q = 0; q < slices && q < kMaxCvSlices; ++q) a.tfrac[q] = tfrac[q];
-    const long long tiles = ((long long)nx * ny + 15) / 16;
-    const long long blocks = (tiles + TAB_WARPS - 1) / TAB_WARPS;
-    const int grid = (int)std::min<long long>(blocks, (long long)sm_count * 8);
-    k_cv_tabulate<<<dim3(grid, 2), TAB_WARPS * 32, 0, s>>>(a);
+    const long long tiles = ((long long)nx * ny * slices + TC_ROWS - 1) / TC_ROWS;
+    if (tiles <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_cv_tabulate, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_REQUEST);
+    if (e != cudaSuccess) return e;
+    // two CTAs per SM and network at most (tensor-memory columns), both networks side by side
+    const int grid = (int)std::min<long long>(tiles, (long long)sm_count);
+    k_cv_tabulate<<<dim3(grid, 2), TC_ROWS, TC_SMEM_REQUEST, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -616,6 +616,8 @@ __global__ void __launch_bounds__(512, 2) k_paths_exp(const PathArgs a)
 // every 32 group_warps-th), each lane sums xi and eta at its end points minus
 // the path's control-variate sums; the group's warp sums are added in warp
 // order to the task's partial sums after the path kernel's.
+constexpr int SCORE_BATCH = 4;
+
 template <bool CV>
 __global__ void __launch_bounds__(256) k_score_surv(const ScoreArgs a)
 {
@@ -636,22 +638,40 @@ __global__ void __launch_bounds__(256) k_score_surv(const ScoreArgs a)
         const InstDev I = a.inst[nd.inst];
         const float x0 = nd.xf, y0 = nd.yf;
         const int end = task.path0 + task.npaths;
-        for (int p = task.path0 + 32 * wig + lane; p < end; p += 32 * gw) {
-            const long long si = nd.rec0 + p;
-            float4 r;
-            if (CV) {
-                r = static_cast<const float4*>(a.surv)[si];
-            } else {
-                const float2 q = static_cast<const float2*>(a.surv)[si];
-                r = make_float4(q.x, q.y, 0.f, 0.f);
+        const int stride = 32 * gw;
+        // SCORE_BATCH paths per lane at a time: their records, then their gathers, in flight together
+        for (int p0 = task.path0 + 32 * wig + lane; p0 < end; p0 += SCORE_BATCH * stride) {
+            float4 r[SCORE_BATCH];
+#pragma unroll
+            for (int u = 0; u < SCORE_BATCH; ++u) {
+                const int p = p0 + u * stride;
+                r[u] = make_float4(-1.f, 0.f, 0.f, 0.f);
+                if (p < end) {
+                    const long long si = nd.rec0 + p;
+                    if (CV) {
+                        r[u] = static_cast<const float4*>(a.surv)[si];
+                    } else {
+                        const float2 q = static_cast<const float2*>(a.surv)[si];
+                        r[u] = make_float4(q.x, q.y, 0.f, 0.f);
+                    }
+                }
             }
-            if (r.x < 0.f) continue;   // the path left the domain
-            const Cell c = locate(I, I.fcoef, f2(r.x, r.y));
-            float4 f0, f1;
-            load_cell(c.p, f0, f1);
-            const float2 v = eval2(f0, f1, c.st);
-            ax.add(v.x - r.z - x0);
-            ae.add(v.y - r.w - y0);
+            float4 f0[SCORE_BATCH], f1[SCORE_BATCH];
+            float2 st[SCORE_BATCH];
+#pragma unroll
+            for (int u = 0; u < SCORE_BATCH; ++u) {
+                // an exit (x = -1) or a lane past the end reads cell 0 and is not added
+                const Cell c = locate(I, I.fcoef, f2(fmaxf(r[u].x, 0.f), r[u].y));
+                load_cell(c.p, f0[u], f1[u]);
+                st[u] = c.st;
+            }
+#pragma unroll
+            for (int u = 0; u < SCORE_BATCH; ++u) {
+                if (r[u].x < 0.f) continue;   // the path left the domain
+                const float2 v = eval2(f0[u], f1[u], st[u]);
+                ax.add(v.x - r[u].z - x0);
+                ae.add(v.y - r[u].w - y0);
+            }
         }
     }
     const double v[4] = {warp_sum(ax.sum()), warp_sum(ax.sumsq()), warp_sum(ae.sum()), warp_sum(ae.sumsq())};
