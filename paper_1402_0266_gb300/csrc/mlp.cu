@@ -466,15 +466,16 @@ struct TabArgs {
 
 // ---- the 64 x 64 layer on the fifth-generation tensor cores
 //
-// A CTA of 128 threads takes tiles of 128 points (point p = slice * nodes +
-// node). Thread t computes layer 1 of point t and writes three BF16 rows into
-// shared memory: h1 = tanh(a1), u1 = (1 - h1^2) W1 dz/dx, v1 = (1 - h1^2) W1
+// A CTA of 256 threads takes tiles of 128 points (point p = slice * nodes +
+// node). Threads t and t + 128 share point t % 128, each with half of the 64
+// units: they compute layer 1 and write three BF16 rows into shared memory: h1 = tanh(a1), u1 = (1 - h1^2) W1 dz/dx, v1 = (1 - h1^2) W1
 // dz/dy. One thread issues the three products h1 W2^T, u1 W2^T, v1 W2^T as
 // tcgen05.mma (M = 128, N = 64, K = 16, BF16 in, FP32 accumulate) into three
 // 64-column accumulators in tensor memory, committed to an mbarrier; then
-// warp w reads lanes 32 w .. 32 w + 31 (its threads' points) back with
-// tcgen05.ld and forms d/dx = sum_j w3_j (1 - tanh(a2_j)^2) (W2 u1)_j, d/dy
-// likewise.
+// warp w reads lanes 32 (w % 4) .. 32 (w % 4) + 31 (its threads' points),
+// its half of the columns, back with tcgen05.ld and forms its half of
+// d/dx = sum_j w3_j (1 - tanh(a2_j)^2) (W2 u1)_j, d/dy likewise; the halves
+// meet in shared memory.
 //
 // Operands are K-major without swizzle: 8 x 8 BF16 core matrices of 128
 // contiguous bytes (a row's 8 consecutive k at 16-byte pitch); core matrices
@@ -482,7 +483,8 @@ struct TabArgs {
 // (stride byte offset). Byte offset of (row r, k): (r / 8) 1024 + (k / 8) 128
 // + (r % 8) 16 + (k % 8) 2.
 
-constexpr int TC_ROWS = 128;                         // points per tile = MMA M = threads per CTA
+constexpr int TC_ROWS = 128;                         // points per tile = MMA M
+constexpr int TC_THREADS = 2 * TC_ROWS;              // two threads per point
 constexpr int TC_OPERAND_BYTES = TC_ROWS * H * 2;    // one 128 x 64 BF16 operand
 constexpr int TC_W2_BYTES = H * H * 2;
 constexpr int TC_TMEM_COLS = 256;                    // three 64-column FP32 accumulators, rounded to a power of two
@@ -496,6 +498,7 @@ struct TcSmem {
     alignas(1024) unsigned char a[3][TC_OPERAND_BYTES];
     alignas(1024) unsigned char b[TC_W2_BYTES];
     float w1[H * D], b1[H], b2[H], w3[H];
+    float2 half_g[TC_ROWS];   // the second half's (d/dx, d/dy) partial sums
     alignas(8) unsigned long long mbar;
     uint32_t tmem;
     int abort;
@@ -544,23 +547,24 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16])
     for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
 
-__global__ void __launch_bounds__(TC_ROWS) k_cv_tabulate(const TabArgs a)
+__global__ void __launch_bounds__(TC_THREADS) k_cv_tabulate(const TabArgs a)
 {
     extern __shared__ unsigned char smem_raw[];
     TcSmem& S = *reinterpret_cast<TcSmem*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     const int f = blockIdx.y;
     const int t = threadIdx.x, warp = t >> 5;
+    const int row = t % TC_ROWS, half = t / TC_ROWS;   // the point and the half of the units
     const float* th = a.theta + (long long)f * kMlpStride;
 
     // weights: layer 1 and the biases in FP32, W2 (B operand, rows n, k-major) in BF16
-    for (int p = t; p < H * D; p += TC_ROWS) S.w1[p] = th[OW1 + p];
-    for (int p = t; p < H; p += TC_ROWS) {
+    for (int p = t; p < H * D; p += TC_THREADS) S.w1[p] = th[OW1 + p];
+    for (int p = t; p < H; p += TC_THREADS) {
         S.b1[p] = th[OB1 + p];
         S.b2[p] = th[OB2 + p];
         S.w3[p] = th[OW3 + p];
     }
-    for (int p = t; p < H * H / 8; p += TC_ROWS) {
+    for (int p = t; p < H * H / 8; p += TC_THREADS) {
         const int n = p / (H / 8), k0 = (p % (H / 8)) * 8;
         const float* wr = th + OW2 + n * H + k0;
         const uint4 v = make_uint4(pack_bf16(wr[0], wr[1]), pack_bf16(wr[2], wr[3]), pack_bf16(wr[4], wr[5]),
@@ -595,7 +599,7 @@ __global__ void __launch_bounds__(TC_ROWS) k_cv_tabulate(const TabArgs a)
     uint32_t phase = 0;
     for (long long tl = blockIdx.x; tl < tiles; tl += gridDim.x) {
         // layer 1 of this thread's point (clamped in the ragged last tile; not written)
-        const long long pt = tl * TC_ROWS + t;
+        const long long pt = tl * TC_ROWS + row;
         const long long pc = pt < points ? pt : points - 1;
         const int sl = (int)(pc / nn);
         const long long node = pc - (long long)sl * nn;
@@ -612,7 +616,7 @@ __global__ void __launch_bounds__(TC_ROWS) k_cv_tabulate(const TabArgs a)
             dzx[0] = sc[0]; dzx[1] = 0.f; dzx[2] = 0.f; dzx[3] = fa.z * sc[3]; dzx[4] = fb.x * sc[4];
             dzy[0] = 0.f; dzy[1] = sc[1]; dzy[2] = 0.f; dzy[3] = fa.w * sc[3]; dzy[4] = fb.y * sc[4];
 #pragma unroll 1
-            for (int k0 = 0; k0 < H; k0 += 8) {
+            for (int k0 = half * (H / 2); k0 < (half + 1) * (H / 2); k0 += 8) {
                 uint32_t ph[4], pu[4], pv[4];
 #pragma unroll
                 for (int e = 0; e < 8; e += 2) {
@@ -639,7 +643,7 @@ __global__ void __launch_bounds__(TC_ROWS) k_cv_tabulate(const TabArgs a)
                     pu[e / 2] = pack_bf16(uv[0], uv[1]);
                     pv[e / 2] = pack_bf16(vv[0], vv[1]);
                 }
-                const uint32_t o = core_off(t, k0);
+                const uint32_t o = core_off(row, k0);
                 *reinterpret_cast<uint4*>(S.a[0] + o) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
                 *reinterpret_cast<uint4*>(S.a[1] + o) = make_uint4(pu[0], pu[1], pu[2], pu[3]);
                 *reinterpret_cast<uint4*>(S.a[2] + o) = make_uint4(pv[0], pv[1], pv[2], pv[3]);
@@ -682,9 +686,9 @@ __global__ void __launch_bounds__(TC_ROWS) k_cv_tabulate(const TabArgs a)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // epilogue: this thread's row from the three accumulators, 16 columns at a time
         float gx = 0.f, gy = 0.f;
-        const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
 #pragma unroll 1
-        for (int c0 = 0; c0 < H; c0 += 16) {
+        for (int c0 = half * (H / 2); c0 < (half + 1) * (H / 2); c0 += 16) {
             float vh[16], vu[16], vv[16];
             tc_ld16(lane_base + (uint32_t)c0, vh);
             tc_ld16(lane_base + (uint32_t)(H + c0), vu);
@@ -697,10 +701,13 @@ __global__ void __launch_bounds__(TC_ROWS) k_cv_tabulate(const TabArgs a)
                 gy = fmaf(wq, vv[k], gy);
             }
         }
-        if (pt < points) {
+        if (half == 1) S.half_g[row] = make_float2(gx, gy);
+        __syncthreads();
+        if (half == 0 && pt < points) {
+            const float2 o2 = S.half_g[row];
             double* o = a.table + pt * 4 + 2 * f;
-            o[0] = (double)gx;
-            o[1] = (double)gy;
+            o[0] = (double)(gx + o2.x);
+            o[1] = (double)(gy + o2.y);
         }
         // every warp is done with the accumulators and the operands before the next tile
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -824,7 +831,7 @@ cudaError_t launch_cv_tabulate(const float* theta, const float* norm, const floa
     if (e != cudaSuccess) return e;
     // two CTAs per SM and network at most (tensor-memory columns), both networks side by side
     const int grid = (int)std::min<long long>(tiles, (long long)sm_count);
-    k_cv_tabulate<<<dim3(grid, 2), TC_ROWS, TC_SMEM_REQUEST, s>>>(a);
+    k_cv_tabulate<<<dim3(grid, 2), TC_THREADS, TC_SMEM_REQUEST, s>>>(a);
     return cudaGetLastError();
 }
 
