@@ -864,7 +864,7 @@ bool mg_auto(const sdd_ctx* c)
 }
 
 SolveCall make_solve_call(sdd_ctx* c, double Dt, double rtol, int max_iter, double* xo, double* eo,
-                          const float* w, const double* px, const double* pe)
+                          const float* w, const double* px, const double* pe, bool narrow = false)
 {
     SolveCall k;
     k.w = w;
@@ -948,7 +948,7 @@ SolveCall make_solve_call(sdd_ctx* c, double Dt, double rtol, int max_iter, doub
         m.max_iter = max_iter;
         m.rtol = rtol;
         m.inner_tol = 1e-5f;
-        k.mgc_upt = mgc_config(m, &k.mgc_C, &k.mgc_rows, &k.mgc_smem);
+        k.mgc_upt = mgc_config(m, &k.mgc_C, &k.mgc_rows, &k.mgc_smem, narrow ? 4 : 2);
         if (k.mgc_upt > 0) m.outer = 8;
     }
     return k;
@@ -1805,9 +1805,10 @@ static sdd_status capture_step(sdd_ctx* c, const sdd_step_params* p, int K, int 
         if (st == SDD_OK && r != cudaSuccess) st = fail(c, SDD_ECUDA, "%s", cudaGetErrorString(r));
     };
     rec_ext(c->ev[0], s);
+    // pipelined, the cluster solve takes half the SMs (four unknowns per thread): it runs beside the paths
     c->step_call[parity] = make_solve_call(c, p->Dt, p->rtol, p->max_iter, c->fld[1 - parity][0].p,
                                            c->fld[1 - parity][1].p, c->w.p, c->fld[parity][0].p,
-                                           c->fld[parity][1].p);
+                                           c->fld[parity][1].p, c->pipe);
     cudaEvent_t join = nullptr;
     if (c->pipe) {
         cudaStream_t q = c->pipe_stream;
@@ -1921,7 +1922,7 @@ sdd_status sdd_step(sdd_ctx* c, const sdd_step_params* p)
         // pipelined steps where the solve's iterations are one launch and the
         // paths do not read the fields (the field-gradient control variate does)
         const SolveCall probe = make_solve_call(c, p->Dt, p->rtol, p->max_iter, nullptr, nullptr, nullptr, nullptr,
-                                                nullptr);
+                                                nullptr, true);
         const size_t rec_bytes = c->cv_mode ? sizeof(float4) : sizeof(float2);
         c->pipe = c->pipe_allowed && solve_single_launch(probe) && c->cv_mode != SDD_CV_FIELDS && c->step_plan.ntasks > 0 &&
                   (size_t)c->step_plan.total_paths * rec_bytes <= (8ULL << 30);

@@ -277,7 +277,7 @@ cudaError_t launch_mg_solve(const MgArgs& a, cudaStream_t s);
 cudaError_t launch_mg_solve_graph(const MgArgs& a, cudaStream_t s, cudaStream_t s2, cudaStream_t s3);
 // the same solve inside one thread-block cluster per subdomain (mgc.cu); mgc_config returns the unknowns
 // per thread (0: subdomains too large) and the cluster shape
-int mgc_config(const MgArgs& a, int* C, int* rows_max, size_t* smem);
+int mgc_config(const MgArgs& a, int* C, int* rows_max, size_t* smem, int max_upt = 2);
 cudaError_t launch_mgc(const MgArgs& a, int upt, int C, int rows_max, size_t smem, cudaStream_t s);
 
 cudaError_t launch_solve_setup(const float* w, const double* prev_xi, const double* prev_eta, int nx, int ny,

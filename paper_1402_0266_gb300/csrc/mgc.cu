@@ -474,28 +474,33 @@ cudaError_t launch_mgc_t(const MgArgs& a, int C, int rows_max, size_t smem, cuda
 }  // namespace
 
 // Cluster shape for the in-cluster solver: C blocks (a power of two, at most
-// 16) such that a block's band fits 2 unknowns per thread; 0 when the
-// subdomain is too large (band or shared memory).
-int mgc_config(const MgArgs& a, int* C_out, int* rows_max_out, size_t* smem_out)
+// 16) such that a block's band fits max_upt (2 or 4) unknowns per thread; 0
+// when the subdomain is too large (band or shared memory). Four unknowns per
+// thread halve the SMs the solve holds (for a solve that runs beside other
+// work) at some cost in its own time.
+int mgc_config(const MgArgs& a, int* C_out, int* rows_max_out, size_t* smem_out, int max_upt)
 {
     const int mx = a.mx[0], my = a.my[0];
+    const int per_block = (max_upt >= 4 ? 4 : 2) * SOLVE_THREADS;
     int C = 1;
-    while (C < 16 && (((my + C - 1) / C) * mx > 2 * SOLVE_THREADS)) C *= 2;
+    while (C < 16 && (((my + C - 1) / C) * mx > per_block)) C *= 2;
     const int rows_max = (my + C - 1) / C;
-    if (rows_max * mx > 2 * SOLVE_THREADS || C > my) return 0;
+    if (rows_max * mx > per_block || C > my) return 0;
     size_t floats = 6 * (size_t)rows_max * (mx + 2);
     for (int l = 1; l < a.levels; ++l) floats += 7 * (size_t)(a.mx[l] + 2) * (a.my[l] + 2);
     const size_t smem = floats * sizeof(float);
-    if (smem > 200 * 1024) return 0;
+    if (smem > 220 * 1024) return 0;
     *C_out = C;
     *rows_max_out = rows_max;
     *smem_out = smem;
-    return rows_max * mx > SOLVE_THREADS ? 2 : 1;
+    const int band = rows_max * mx;
+    return band > 2 * SOLVE_THREADS ? 4 : band > SOLVE_THREADS ? 2 : 1;
 }
 
 cudaError_t launch_mgc(const MgArgs& a, int upt, int C, int rows_max, size_t smem, cudaStream_t s)
 {
     if (upt == 1) return launch_mgc_t<1>(a, C, rows_max, smem, s);
+    if (upt == 4) return launch_mgc_t<4>(a, C, rows_max, smem, s);
     return launch_mgc_t<2>(a, C, rows_max, smem, s);
 }
 
