@@ -286,8 +286,7 @@ sdd_status prepare_parts(sdd_ctx* c, cudaStream_t s, bool w_part, bool f_part)
 {
     const bool dw = w_part && c->dirty_w, df = f_part && c->dirty_fields;
     if (dw && !c->user_faces) {
-        CU(c, launch_winslow_faces(c->w.p, c->nx, c->ny, c->faces64.p, s));
-        CU(c, launch_faces32(c->faces64.p, c->faces32.p, (int)faces_len(c), s));
+        CU(c, launch_winslow_faces(c->w.p, c->nx, c->ny, c->faces64.p, c->faces32.p, s));
     }
     if (dw || df) {
         CU(c, launch_prep_cells(c->w.p, c->fld[c->cur][0].p, c->fld[c->cur][1].p, c->nx, c->ny,
@@ -303,8 +302,7 @@ sdd_status prepare(sdd_ctx* c, cudaStream_t s)
     if (c->dirty_w && c->dirty_fields) {
         // both record sets in one pass
         if (!c->user_faces) {
-            CU(c, launch_winslow_faces(c->w.p, c->nx, c->ny, c->faces64.p, s));
-            CU(c, launch_faces32(c->faces64.p, c->faces32.p, (int)faces_len(c), s));
+            CU(c, launch_winslow_faces(c->w.p, c->nx, c->ny, c->faces64.p, c->faces32.p, s));
         }
         CU(c, launch_prep_cells(c->w.p, c->fld[c->cur][0].p, c->fld[c->cur][1].p, c->nx, c->ny, c->bcoef.p,
                                 c->fcoef.p, c->d_status.p, s));

@@ -146,7 +146,8 @@ int path_kernel_blocks_per_sm(int exit_mode, bool record, int block, bool cv = f
 // (from xi, eta; fcoef null: skipped).
 cudaError_t launch_prep_cells(const float* w, const double* xi, const double* eta, int nx, int ny, float4* bcoef,
                               float4* fcoef, int* status, cudaStream_t s);
-cudaError_t launch_winslow_faces(const float* w, int nx, int ny, double* faces64, cudaStream_t s);
+// The paper's boundary data from w (faces64) and, if faces32 is non-null, its single-precision copy.
+cudaError_t launch_winslow_faces(const float* w, int nx, int ny, double* faces64, float* faces32, cudaStream_t s);
 cudaError_t launch_cv_cells(const double* grad, int slices, int nx, int ny, uint4* cvcoef, cudaStream_t s);
 cudaError_t launch_faces32(const double* faces64, float* faces32, int n, cudaStream_t s);
 

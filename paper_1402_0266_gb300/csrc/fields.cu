@@ -158,7 +158,8 @@ __device__ void warp_cumtrapz(const float* __restrict__ v, long long stride, int
     }
 }
 
-__global__ void k_winslow_faces(const float* __restrict__ w, int nx, int ny, double* __restrict__ faces)
+__global__ void k_winslow_faces(const float* __restrict__ w, int nx, int ny, double* __restrict__ faces,
+                                float* __restrict__ faces32)
 {
     const long long per_field = 2LL * ny + 2LL * nx;
     double* xl = faces;
@@ -181,6 +182,11 @@ __global__ void k_winslow_faces(const float* __restrict__ w, int nx, int ny, dou
     for (int k = threadIdx.x; k < nx; k += blockDim.x) {
         eb[k] = 0.0;
         et[k] = 1.0;
+    }
+    if (faces32) {
+        // the single-precision copy the path kernel scores exits with
+        __syncthreads();
+        for (long long k = threadIdx.x; k < 2 * per_field; k += blockDim.x) faces32[k] = (float)faces[k];
     }
 }
 
@@ -209,9 +215,9 @@ cudaError_t launch_cv_cells(const double* grad, int slices, int nx, int ny, uint
     return cudaGetLastError();
 }
 
-cudaError_t launch_winslow_faces(const float* w, int nx, int ny, double* faces64, cudaStream_t s)
+cudaError_t launch_winslow_faces(const float* w, int nx, int ny, double* faces64, float* faces32, cudaStream_t s)
 {
-    k_winslow_faces<<<1, 128, 0, s>>>(w, nx, ny, faces64);
+    k_winslow_faces<<<1, 128, 0, s>>>(w, nx, ny, faces64, faces32);
     return cudaGetLastError();
 }
 

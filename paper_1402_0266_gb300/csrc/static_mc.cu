@@ -205,7 +205,7 @@ sdd_status sdd_interface_mc_static(const sdd_fields* f, const sdd_nodes* nodes, 
     STATIC_CU(cudaMemsetAsync(status, 0, sizeof(int), s));
     // the tables of the estimate
     if (f->faces) STATIC_CU(cudaMemcpyAsync(faces64, f->faces, nfaces * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    else STATIC_CU(launch_winslow_faces(f->w, nx, ny, faces64, s));
+    else STATIC_CU(launch_winslow_faces(f->w, nx, ny, faces64, nullptr, s));
     STATIC_CU(launch_faces32(faces64, faces32, nfaces, s));
     STATIC_CU(launch_prep_cells(f->w, f->xi, f->eta, nx, ny, bcoef, fcoef, status, s));
     // the paths, then the per-node means
