@@ -765,8 +765,63 @@ def run_ring2049(args, world, rank, local):
                           / 1e12 / (152 * SM_LANES_PER_CLK * 2070e6 / 1e12)}), flush=True)
 
 
+def run_heat65(args, world, rank, local):
+    """The small heat-equation case (w = 1 on 65 x 65, 33 nodes on x = 1/2 x 1000 paths, dt = 1e-3, Dt = 0.05,
+    zero boundary data): one step = one interface estimate of all 33 nodes, inputs resident on the device.
+    Latency-bound by design (1.6e6 path-steps); the closed form is its correctness check."""
+    import torch
+
+    import paper_1402_0266_gb300 as sdd
+    from paper_1402_0266_gb300 import build as b
+    b.build()
+    torch.cuda.set_device(local)
+    n, dt, Dt, paths = 65, 1e-3, 0.05, 1000
+    xi0, eta0 = W.heat65_fields()
+    ctx = sdd.sdd_init(n, n, 2, 2, w=torch.from_numpy(W.w_const(n)).cuda(), xi0=torch.from_numpy(xi0).cuda(),
+                       eta0=torch.from_numpy(eta0).cuda())
+    sdd.sdd_set_boundary(ctx, torch.zeros(4 * n + 4 * n, dtype=torch.float64, device="cuda"))
+    xs, ys = W.heat65_nodes()
+    npaths = np.full(xs.size, paths, dtype=np.int64)
+    stream = torch.cuda.current_stream()
+    for k in range(args.warmup):
+        sdd.sdd_interface_mc(ctx, xs, ys, npaths, dt=dt, Dt=Dt, seed=k)
+    K = args.steps
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    outs = []
+    torch.cuda.synchronize()
+    barrier(world)
+    e0.record(stream)
+    for k in range(K):
+        outs.append(sdd.sdd_interface_mc(ctx, xs, ys, npaths, dt=dt, Dt=Dt, seed=100 + k))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    steps = sum(int(o["path_steps"].sum()) for o in outs)
+    value, tot, mx = whole_job(steps, ms / 1e3, world)
+    # the closed form at t = Dt: xi = exp(-2 pi^2 Dt) sin(pi x) sin(pi y) (plain test: biased like sqrt(dt))
+    o = {k2: v.cpu().numpy() for k2, v in outs[-1].items()}
+    exact = np.exp(-2 * np.pi ** 2 * Dt) * np.sin(np.pi * xs) * np.sin(np.pi * ys)
+    if rank == 0:
+        print(json.dumps({"metric": "path-steps/s (interface Monte Carlo, one estimate per step)", "value": value,
+                          "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": ms / K,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                          "data": "synthetic",
+                          "config": {"workload": f"heat65: w=1 on {n}x{n}, {xs.size} nodes on x=1/2 x {paths} paths, "
+                                                 f"dt={dt}, Dt={Dt} (K=50), zero boundary data, plain exit test"},
+                          "interface_nodes_per_s": world * xs.size * K / (mx),
+                          "max_abs_error_vs_closed_form": float(np.abs(o["mean_xi"] - exact).max()),
+                          "max_se": float(o["se_xi"].max())}), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "heat65" and args.impl == "ours":
+        world, rank, local = dist_init()
+        if args.steps == WL.steps:
+            args.steps = 200
+        run_heat65(args, world, rank, local)
+        return
     if args.workload == "batch64" and args.impl == "ours":
         world, rank, local = dist_init()
         run_batch64(args, world, rank, local)
