@@ -636,12 +636,9 @@ sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const Out
             ScoreArgs sa{};
             sa.inst = inst;
             sa.nodes = P.d_nodes.p;
-            sa.tasks = P.d_tasks.p;
             sa.partials = P.d_partials.p;
             sa.surv = surv;
-            sa.ntasks = (int32_t)P.ntasks;
-            // about four paths per lane
-            sa.group_warps = P.ppt >= 1024 ? 8 : P.ppt >= 512 ? 4 : P.ppt >= 256 ? 2 : 1;
+            sa.nnodes = (int32_t)P.nnodes;
             sa.node_mask = node_mask;
             CU(err, launch_score_surv(sa, cv, s));
         }

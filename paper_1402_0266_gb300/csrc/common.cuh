@@ -108,11 +108,9 @@ struct PathArgs {
 struct ScoreArgs {
     const InstDev* inst;
     const NodeDev* nodes;
-    const Task* tasks;
     Partial* partials;
     const void* surv;
-    int32_t ntasks;
-    int32_t group_warps;      // warps per task: 1, 2, 4 or 8
+    int32_t nnodes;
     const uint8_t* node_mask;
 };
 

@@ -611,78 +611,70 @@ __global__ void __launch_bounds__(512, 2) k_paths_exp(const PathArgs a)
 
 // Scores of the paths that survived a mesh step, once the fields of the step's
 // start are final (the estimate of the next mesh step runs beside the
-// subdomain solve that produces them). A task's paths go to a group of
-// a.group_warps warps (lane l of warp g takes paths path0 + 32 g + l, then
-// every 32 group_warps-th), each lane sums xi and eta at its end points minus
-// the path's control-variate sums; the group's warp sums are added in warp
-// order to the task's partial sums after the path kernel's.
+// subdomain solve that produces them). One block per node: the node's paths
+// end in one neighbourhood, so its gathers share L1; thread k takes paths k,
+// k + 256, ... SCORE_BATCH at a time (records, then gathers, in flight
+// together) and sums xi and eta at the end points minus the paths'
+// control-variate sums; the block's sums, in warp order, are added to the
+// partial sums of the node's first task (the node's reduction adds all of its
+// tasks' partials).
 constexpr int SCORE_BATCH = 4;
+constexpr int SCORE_THREADS = 256;
 
 template <bool CV>
-__global__ void __launch_bounds__(256) k_score_surv(const ScoreArgs a)
+__global__ void __launch_bounds__(SCORE_THREADS) k_score_surv(const ScoreArgs a)
 {
-    __shared__ double red[8][4];
+    __shared__ double red[SCORE_THREADS / 32][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gw = a.group_warps;
-    const int local = warp / gw, wig = warp - local * gw;
-    const long long t = (long long)blockIdx.x * (8 / gw) + local;
-    bool active = t < a.ntasks;
-    Task task{};
-    if (active) {
-        task = a.tasks[t];
-        if (a.node_mask && !a.node_mask[task.node]) active = false;
-    }
+    const int node = blockIdx.x;
+    const NodeDev& nd = a.nodes[node];
+    if (nd.ntasks == 0 || (a.node_mask && !a.node_mask[node])) return;   // uniform over the block
+    const InstDev I = a.inst[nd.inst];
+    const float x0 = nd.xf, y0 = nd.yf;
+    const int end = nd.n_paths;
     Acc ax{0.f, 0.f, 0.f, 0.f}, ae{0.f, 0.f, 0.f, 0.f};
-    if (active) {
-        const NodeDev& nd = a.nodes[task.node];
-        const InstDev I = a.inst[nd.inst];
-        const float x0 = nd.xf, y0 = nd.yf;
-        const int end = task.path0 + task.npaths;
-        const int stride = 32 * gw;
-        // SCORE_BATCH paths per lane at a time: their records, then their gathers, in flight together
-        for (int p0 = task.path0 + 32 * wig + lane; p0 < end; p0 += SCORE_BATCH * stride) {
-            float4 r[SCORE_BATCH];
+    for (int p0 = threadIdx.x; p0 < end; p0 += SCORE_BATCH * SCORE_THREADS) {
+        float4 r[SCORE_BATCH];
 #pragma unroll
-            for (int u = 0; u < SCORE_BATCH; ++u) {
-                const int p = p0 + u * stride;
-                r[u] = make_float4(-1.f, 0.f, 0.f, 0.f);
-                if (p < end) {
-                    const long long si = nd.rec0 + p;
-                    if (CV) {
-                        r[u] = static_cast<const float4*>(a.surv)[si];
-                    } else {
-                        const float2 q = static_cast<const float2*>(a.surv)[si];
-                        r[u] = make_float4(q.x, q.y, 0.f, 0.f);
-                    }
+        for (int u = 0; u < SCORE_BATCH; ++u) {
+            const int p = p0 + u * SCORE_THREADS;
+            r[u] = make_float4(-1.f, 0.f, 0.f, 0.f);
+            if (p < end) {
+                const long long si = nd.rec0 + p;
+                if (CV) {
+                    r[u] = static_cast<const float4*>(a.surv)[si];
+                } else {
+                    const float2 q = static_cast<const float2*>(a.surv)[si];
+                    r[u] = make_float4(q.x, q.y, 0.f, 0.f);
                 }
             }
-            float4 f0[SCORE_BATCH], f1[SCORE_BATCH];
-            float2 st[SCORE_BATCH];
+        }
+        float4 f0[SCORE_BATCH], f1[SCORE_BATCH];
+        float2 st[SCORE_BATCH];
 #pragma unroll
-            for (int u = 0; u < SCORE_BATCH; ++u) {
-                // an exit (x = -1) or a lane past the end reads cell 0 and is not added
-                const Cell c = locate(I, I.fcoef, f2(fmaxf(r[u].x, 0.f), r[u].y));
-                load_cell(c.p, f0[u], f1[u]);
-                st[u] = c.st;
-            }
+        for (int u = 0; u < SCORE_BATCH; ++u) {
+            // an exit (x = -1) or a thread past the end reads cell 0 and is not added
+            const Cell c = locate(I, I.fcoef, f2(fmaxf(r[u].x, 0.f), r[u].y));
+            load_cell(c.p, f0[u], f1[u]);
+            st[u] = c.st;
+        }
 #pragma unroll
-            for (int u = 0; u < SCORE_BATCH; ++u) {
-                if (r[u].x < 0.f) continue;   // the path left the domain
-                const float2 v = eval2(f0[u], f1[u], st[u]);
-                ax.add(v.x - r[u].z - x0);
-                ae.add(v.y - r[u].w - y0);
-            }
+        for (int u = 0; u < SCORE_BATCH; ++u) {
+            if (r[u].x < 0.f) continue;   // the path left the domain
+            const float2 v = eval2(f0[u], f1[u], st[u]);
+            ax.add(v.x - r[u].z - x0);
+            ae.add(v.y - r[u].w - y0);
         }
     }
     const double v[4] = {warp_sum(ax.sum()), warp_sum(ax.sumsq()), warp_sum(ae.sum()), warp_sum(ae.sumsq())};
     if (lane == 0)
         for (int q = 0; q < 4; ++q) red[warp][q] = v[q];
     __syncthreads();
-    if (active && wig == 0 && lane == 0) {
+    if (threadIdx.x == 0) {
         double tot[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int g = 0; g < gw; ++g)
-            for (int q = 0; q < 4; ++q) tot[q] += red[warp + g][q];
-        Partial& P = a.partials[t];
+        for (int g = 0; g < SCORE_THREADS / 32; ++g)
+            for (int q = 0; q < 4; ++q) tot[q] += red[g][q];
+        Partial& P = a.partials[nd.task0];
         P.s_xi += tot[0];
         P.q_xi += tot[1];
         P.s_eta += tot[2];
@@ -900,14 +892,9 @@ cudaError_t launch_paths(const PathArgs& a, int exit_mode, bool record, int grid
 
 cudaError_t launch_score_surv(const ScoreArgs& a, bool cv, cudaStream_t s)
 {
-    if (a.ntasks <= 0) return cudaSuccess;
-    if (a.group_warps != 1 && a.group_warps != 2 && a.group_warps != 4 && a.group_warps != 8)
-        return cudaErrorInvalidValue;
-    const int block = 256;
-    const long long per_block = 8 / a.group_warps;
-    const int grid = (int)((a.ntasks + per_block - 1) / per_block);
-    if (cv) k_score_surv<true><<<grid, block, 0, s>>>(a);
-    else k_score_surv<false><<<grid, block, 0, s>>>(a);
+    if (a.nnodes <= 0) return cudaSuccess;
+    if (cv) k_score_surv<true><<<a.nnodes, SCORE_THREADS, 0, s>>>(a);
+    else k_score_surv<false><<<a.nnodes, SCORE_THREADS, 0, s>>>(a);
     return cudaGetLastError();
 }
 
