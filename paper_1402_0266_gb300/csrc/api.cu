@@ -632,16 +632,6 @@ sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const Out
         CU(err, launch_paths(a, exit_mode, rec != nullptr, grid, block, s, cv));
         if (ev_b) CU(err, cudaEventRecordWithFlags(ev_b, s, cudaEventRecordExternal));
         if (join) CU(err, cudaStreamWaitEvent(s, join, 0));
-        if (surv) {
-            ScoreArgs sa{};
-            sa.inst = inst;
-            sa.nodes = P.d_nodes.p;
-            sa.partials = P.d_partials.p;
-            sa.surv = surv;
-            sa.nnodes = (int32_t)P.nnodes;
-            sa.node_mask = node_mask;
-            CU(err, launch_score_surv(sa, cv, s));
-        }
     }
     FinalArgs f{};
     f.inst = inst;
@@ -652,6 +642,18 @@ sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const Out
     f.nnodes = (int32_t)P.nnodes;
     if (rec) f.rec = *rec;
     f.node_mask = node_mask;
+    if (surv && P.ntasks > 0) {
+        // the survivors' scores and the per-node reduction in one launch
+        ScoreArgs sa{};
+        sa.inst = inst;
+        sa.nodes = P.d_nodes.p;
+        sa.surv = surv;
+        sa.nnodes = (int32_t)P.nnodes;
+        sa.fin = f;
+        const bool cv = cv_slices > 0;
+        CU(err, launch_score_surv(sa, cv, s));
+        return SDD_OK;
+    }
     CU(err, launch_finalize(f, s));
     return SDD_OK;
 }

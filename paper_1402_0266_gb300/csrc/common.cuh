@@ -104,16 +104,6 @@ struct PathArgs {
     void* surv;               // if non-null, survivors leave their end records here (indexed rec0 + path)
 };
 
-// Deferred scoring of the survivors (k_score_surv).
-struct ScoreArgs {
-    const InstDev* inst;
-    const NodeDev* nodes;
-    Partial* partials;
-    const void* surv;
-    int32_t nnodes;
-    const uint8_t* node_mask;
-};
-
 struct FinalArgs {
     const InstDev* inst;
     const NodeDev* nodes;
@@ -123,6 +113,15 @@ struct FinalArgs {
     int32_t nnodes;
     RecDev rec;               // per-path records of boundary nodes (may be all null)
     const uint8_t* node_mask; // if non-null, nodes with a zero entry report no paths (filled later)
+};
+
+// Deferred scoring of the survivors, then the per-node reduction (k_score_surv).
+struct ScoreArgs {
+    const InstDev* inst;
+    const NodeDev* nodes;
+    const void* surv;
+    int32_t nnodes;
+    FinalArgs fin;            // the per-node reduction (nodes, partials, outputs, mask)
 };
 
 // Device status word bits.

@@ -615,11 +615,14 @@ __global__ void __launch_bounds__(512, 2) k_paths_exp(const PathArgs a)
 // end in one neighbourhood, so its gathers share L1; thread k takes paths k,
 // k + 256, ... SCORE_BATCH at a time (records, then gathers, in flight
 // together) and sums xi and eta at the end points minus the paths'
-// control-variate sums; the block's sums, in warp order, are added to the
-// partial sums of the node's first task (the node's reduction adds all of its
-// tasks' partials).
+// control-variate sums; the block's sums, in warp order, join the partial
+// sums of the node's first task in the node's reduction, which the block's
+// first warp then runs (the mean and standard error of every node, boundary
+// and masked nodes included).
 constexpr int SCORE_BATCH = 4;
 constexpr int SCORE_THREADS = 256;
+
+__device__ void finalize_node(const FinalArgs& a, int node, int lane, const double* add0);
 
 template <bool CV>
 __global__ void __launch_bounds__(SCORE_THREADS) k_score_surv(const ScoreArgs a)
@@ -628,7 +631,11 @@ __global__ void __launch_bounds__(SCORE_THREADS) k_score_surv(const ScoreArgs a)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int node = blockIdx.x;
     const NodeDev& nd = a.nodes[node];
-    if (nd.ntasks == 0 || (a.node_mask && !a.node_mask[node])) return;   // uniform over the block
+    if (nd.ntasks == 0 || (a.fin.node_mask && !a.fin.node_mask[node])) {
+        // a boundary node or one left to the interface fill: no paths to score
+        if (warp == 0) finalize_node(a.fin, node, lane, nullptr);
+        return;   // uniform over the block
+    }
     const InstDev I = a.inst[nd.inst];
     const float x0 = nd.xf, y0 = nd.yf;
     const int end = nd.n_paths;
@@ -670,15 +677,11 @@ __global__ void __launch_bounds__(SCORE_THREADS) k_score_surv(const ScoreArgs a)
     if (lane == 0)
         for (int q = 0; q < 4; ++q) red[warp][q] = v[q];
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (warp == 0) {
         double tot[4] = {0.0, 0.0, 0.0, 0.0};
         for (int g = 0; g < SCORE_THREADS / 32; ++g)
             for (int q = 0; q < 4; ++q) tot[q] += red[g][q];
-        Partial& P = a.partials[nd.task0];
-        P.s_xi += tot[0];
-        P.q_xi += tot[1];
-        P.s_eta += tot[2];
-        P.q_eta += tot[3];
+        finalize_node(a.fin, node, lane, tot);   // the node's mean and standard error
     }
 }
 
@@ -698,14 +701,11 @@ __device__ __forceinline__ double face_value64(const InstDev& I, int field, int 
 }
 
 // One warp per node: compensated sums of the node's task partials (each lane a
-// fixed stride of tasks), a fixed butterfly across the warp, then the mean and
-// the standard error s / sqrt(N), s^2 = (Q - S^2 / N) / (N - 1) of the shifted
-// scores.
-__global__ void k_finalize(const FinalArgs a)
+// fixed stride of tasks; add0, if non-null, added to the first task's), a
+// fixed butterfly across the warp, then the mean and the standard error
+// s / sqrt(N), s^2 = (Q - S^2 / N) / (N - 1) of the shifted scores.
+__device__ void finalize_node(const FinalArgs& a, int node, int lane, const double* add0)
 {
-    const int node = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (node >= a.nnodes) return;
     const NodeDev nd = a.nodes[node];
     const OutDev o = a.out_table ? a.out_table[nd.inst] : a.out0;
     const int k = nd.local;
@@ -754,7 +754,10 @@ __global__ void k_finalize(const FinalArgs a)
     long long ex = 0, st = 0;
     for (int t = nd.task0 + lane; t < nd.task0 + nd.ntasks; t += 32) {
         const Partial p = a.partials[t];
-        const double in[4] = {p.s_xi, p.q_xi, p.s_eta, p.q_eta};
+        double in[4] = {p.s_xi, p.q_xi, p.s_eta, p.q_eta};
+        if (add0 && t == nd.task0)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) in[q] += add0[q];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const double y = in[q] - c[q];
@@ -785,6 +788,14 @@ __global__ void k_finalize(const FinalArgs a)
         if (o.n_exit) o.n_exit[k] = ex;
         if (o.path_steps) o.path_steps[k] = st;
     }
+}
+
+__global__ void k_finalize(const FinalArgs a)
+{
+    const int node = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (node >= a.nnodes) return;
+    finalize_node(a, node, lane, nullptr);
 }
 
 __global__ void k_rng_draw(uint64_t seed, const uint32_t* __restrict__ ctrs, long long count,

@@ -137,3 +137,32 @@ def test_reads_between_steps_see_final_fields(sdd):
     info = sdd.sdd_last_step_info(ctx)
     assert info["solve_ms"] > 0 and info["paths_ms"] > 0 and info["kernel_nodes"] > 0
     sdd.sdd_sync(ctx)
+
+
+def test_batch_after_pipelined_steps_sees_final_fields(sdd):
+    """A context stepped on its own (pipelined) and then put into a batch: the batch
+    runs the pending iterations first, so its estimate starts from the same fields as
+    a context that was synchronised before."""
+    import torch
+    n = 65
+    kw = dict(dt=1e-4, Dt=1e-2, seed=3, paths_per_node=800)
+    a = _ctx(sdd, n, 2, W.w_front(n, 0.0))
+    b = _ctx(sdd, n, 2, W.w_front(n, 0.0))
+    for c in (a, b):
+        for k in range(2):
+            sdd.sdd_set_w(c, torch.from_numpy(W.w_front(n, k * 1e-2)).cuda())
+            sdd.sdd_step(c, **kw)
+    assert sdd.sdd_pipeline_in_use(a)
+    sdd.sdd_sync(b)                                   # b's pending solve runs here
+    batch = sdd.sdd_batch_create([a])                 # a's runs here
+    sdd.sdd_batch_sync(batch)
+    fa = [t.cpu().numpy() for t in sdd.sdd_get_fields(a)]
+    fb = [t.cpu().numpy() for t in sdd.sdd_get_fields(b)]
+    np.testing.assert_array_equal(fa[0], fb[0])
+    np.testing.assert_array_equal(fa[1], fb[1])
+    xs, ys = sdd.sdd_interface_nodes(a)
+    est = sdd.sdd_batch_interface_mc(batch, [(xs, ys, np.full(xs.size, 500))], dt=1e-4, Dt=1e-2, seed=8)
+    ref = sdd.sdd_interface_mc(b, xs, ys, np.full(xs.size, 500), dt=1e-4, Dt=1e-2, seed=8)
+    sdd.sdd_batch_sync(batch)
+    np.testing.assert_allclose(est[0]["mean_xi"].cpu().numpy(), ref["mean_xi"].cpu().numpy(), rtol=0, atol=1e-6)
+    sdd.sdd_batch_destroy(batch)
