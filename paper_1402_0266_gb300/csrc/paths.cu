@@ -17,6 +17,12 @@
 // compensation (single precision, shifted by the node's start coordinates),
 // then per warp in double precision; the per-node reduction over tasks runs in
 // a fixed order, so results do not depend on scheduling.
+//
+// Deferred scoring: when the fields of the step's start are still being
+// computed beside the path kernel (pipelined mesh steps), a surviving path
+// leaves its end point (and control-variate sums) in a record array instead,
+// and k_score_surv scores the records once the fields are final, then runs the
+// per-node reduction.
 #include <cuda_fp16.h>
 
 #include <cstring>
