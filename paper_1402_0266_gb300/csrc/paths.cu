@@ -9,7 +9,7 @@
 // end point (Eq. 7b). The node's estimate is the mean over its paths (Sec. 4).
 //
 // Execution: a persistent grid; each warp repeatedly takes a task (one node,
-// a contiguous range of its paths) from a counter. Each lane runs one path at
+// a contiguous range of its paths) from a counter, on its own. Each lane runs one path at
 // a time and, when its path ends, takes the task's next unstarted path, so
 // lanes stay busy when paths leave early. In the paper's (plain) exit mode one
 // Philox block supplies the normals of two consecutive sub-steps, so paths are
@@ -254,26 +254,21 @@ __device__ __forceinline__ void mark_exit(void* surv, long long i)
 template <int MODE, bool RECORD, bool CV>
 __global__ void __launch_bounds__(CV ? kCvMaxBlock : 512, CV ? 3 : 2) k_paths(const PathArgs a)
 {
-    __shared__ int s_group;
     const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
     const unsigned below = (1u << lane) - 1u;
     const uint32_t step = a.step_ptr ? *a.step_ptr : a.step_index;
     const int K = a.K;
     const float dt = a.dt;
     constexpr bool PAIRS = MODE != 1;
 
-    // The block takes one task per warp at a time; consecutive tasks belong to
-    // the same node, so the block's gathers share the node's neighbourhood in L1.
+    // Each warp takes the next task as soon as its last one is done (no wait
+    // for the block's other warps); tasks go node by node, so warps started
+    // together share the node's neighbourhood in L1.
     for (;;) {
-        __syncthreads();  // every warp is done with the previous group
-        if (threadIdx.x == 0) s_group = atomicAdd(a.queue, nwarps);
-        __syncthreads();
-        const int group = s_group;
-        if (group >= a.ntasks) return;
-        const int t = group + warp;
-        if (t >= a.ntasks) continue;
+        int tq = 0;
+        if (lane == 0) tq = atomicAdd(a.queue, 1);
+        const int t = __shfl_sync(FULL, tq, 0);
+        if (t >= a.ntasks) return;
 
         const Task task = a.tasks[t];
         if (a.node_mask && !a.node_mask[task.node]) continue;   // not a key point this step
@@ -479,10 +474,7 @@ __global__ void __launch_bounds__(CV ? kCvMaxBlock : 512, CV ? 3 : 2) k_paths(co
 template <bool RECORD>
 __global__ void __launch_bounds__(512, 2) k_paths_exp(const PathArgs a)
 {
-    __shared__ int s_group;
     const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
     const unsigned below = (1u << lane) - 1u;
     const uint32_t step = a.step_ptr ? *a.step_ptr : a.step_index;
     const int K = a.K;
@@ -490,13 +482,10 @@ __global__ void __launch_bounds__(512, 2) k_paths_exp(const PathArgs a)
     const float T = a.horizon;
     const float ln2dt = a.dt * 0.69314718055994530942f;
     for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_group = atomicAdd(a.queue, nwarps);
-        __syncthreads();
-        const int group = s_group;
-        if (group >= a.ntasks) return;
-        const int t = group + warp;
-        if (t >= a.ntasks) continue;
+        int tq = 0;
+        if (lane == 0) tq = atomicAdd(a.queue, 1);
+        const int t = __shfl_sync(FULL, tq, 0);
+        if (t >= a.ntasks) return;
         const Task task = a.tasks[t];
         if (a.node_mask && !a.node_mask[task.node]) continue;
         const NodeDev& nd = a.nodes[task.node];
