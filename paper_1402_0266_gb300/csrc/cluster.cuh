@@ -74,4 +74,53 @@ __device__ __forceinline__ void cluster_sum2(cg::cluster_group& cl, ClusterSlots
     v1 = S.total[1];
 }
 
+// The same for four values (one cluster barrier for two pairs of sums).
+template <typename T>
+struct ClusterSlots4 {
+    T warp_part[4][SOLVE_WARPS];
+    T block_part[4];
+    T total[4];
+};
+
+template <typename T>
+__device__ __forceinline__ void cluster_sum4(cg::cluster_group& cl, ClusterSlots4<T> (&sh)[2], int& seq, T (&v)[4])
+{
+    ClusterSlots4<T>& S = sh[seq & 1];
+    ++seq;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) S.warp_part[k][warp] = v[k];
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        T t = 0;
+        for (int q = 0; q < SOLVE_WARPS; ++q) t += S.warp_part[threadIdx.x][q];
+        S.block_part[threadIdx.x] = t;
+    }
+    cl.sync();
+    if (warp == 0) {
+        const int C = (int)cl.num_blocks();
+        T t[4] = {0, 0, 0, 0};
+        if (lane < C) {
+            const T* rem = cl.map_shared_rank(&S.block_part[0], lane);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) t[k] = rem[k];
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) t[k] += __shfl_xor_sync(0xffffffffu, t[k], off);
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) S.total[k] = t[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = S.total[k];
+}
+
 }  // namespace sdd

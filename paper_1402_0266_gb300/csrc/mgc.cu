@@ -183,9 +183,9 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_mgc(const MgArgs a, int rows_
     const float* U1_0 = a.levels > 1 ? cl.map_shared_rank(lv[1].U[0], 0) : nullptr;
     const float* U1_1 = a.levels > 1 ? cl.map_shared_rank(lv[1].U[1], 0) : nullptr;
 
-    __shared__ ClusterSlots<double> red64[2];
+    __shared__ ClusterSlots4<double> red64[2];
     __shared__ ClusterSlots<float> red32[2];
-    int seq = 0;
+    int seq = 0, seq64 = 0;
 
     // zero the finest-level planes; the first block loads the coarse coefficients
     for (int k = threadIdx.x; k < 6 * plane; k += blockDim.x) sm[k] = 0.f;
@@ -350,8 +350,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_mgc(const MgArgs a, int rows_
                 d[f][k] = 0.f;
             }
         }
-        cluster_sum2(cl, red64, seq, t[0], t[1]);
-        cluster_sum2(cl, red64, seq, t[2], t[3]);
+        cluster_sum4(cl, red64, seq64, t);
         rr0 = t[0];
         rr1 = t[1];
         bb0 = t[2];

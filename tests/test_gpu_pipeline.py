@@ -166,3 +166,25 @@ def test_batch_after_pipelined_steps_sees_final_fields(sdd):
     sdd.sdd_batch_sync(batch)
     np.testing.assert_allclose(est[0]["mean_xi"].cpu().numpy(), ref["mean_xi"].cpu().numpy(), rtol=0, atol=1e-6)
     sdd.sdd_batch_destroy(batch)
+
+
+def test_changed_parameters_flush_the_pending_solve(sdd):
+    """New step parameters rebuild the step graphs; the last step's deferred
+    iterations run first, so the sequence matches the unpipelined one."""
+    import torch
+    n = 65
+    seq = [dict(dt=1e-4, Dt=1e-2, seed=1, paths_per_node=600),
+           dict(dt=1e-4, Dt=1e-2, seed=1, paths_per_node=600),
+           dict(dt=2e-4, Dt=1e-2, seed=2, paths_per_node=900, exit_mode=1),
+           dict(dt=2e-4, Dt=1e-2, seed=2, paths_per_node=900, exit_mode=1)]
+    out = []
+    for pipe in (True, False):
+        c = _ctx(sdd, n, 2, W.w_front(n, 0.0))
+        sdd.sdd_set_pipeline(c, pipe)
+        for k, kw in enumerate(seq):
+            sdd.sdd_set_w(c, torch.from_numpy(W.w_front(n, k * 1e-2)).cuda())
+            sdd.sdd_step(c, **kw)
+        out.append([t.cpu().numpy() for t in sdd.sdd_get_fields(c)])
+        sdd.sdd_sync(c)
+    np.testing.assert_allclose(out[0][0], out[1][0], rtol=0, atol=TOL)
+    np.testing.assert_allclose(out[0][1], out[1][1], rtol=0, atol=TOL)
