@@ -83,6 +83,9 @@ def _load():
                                          vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
             lib.orc_mc_nodes.restype = ctypes.c_int
             lib.orc_draw.argtypes = [ctypes.c_uint64, ctypes.c_int64, vp, vp, vp]
+            lib.orc_path_margins.argtypes = [ctypes.POINTER(_Problem), ctypes.POINTER(_Params), ctypes.c_int64,
+                                             vp, vp, vp, vp, vp, vp]
+            lib.orc_path_margins.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -299,6 +302,35 @@ def interface_mc(problem: Problem, xs, ys, n_paths, *, dt: float, Dt: float, see
                path_steps=stats[:, 5].astype(np.int64))
     if recs is not None:
         out.update(recs)
+    return out
+
+
+def path_margins(problem: Problem, xs, ys, node_ids, paths, upto, *, dt: float, Dt: float, seed: int = 0,
+                 exit_mode: int = 0, step_index: int = 0):
+    """For single paths (node coordinates xs, ys, Philox node words node_ids,
+    path numbers paths): the smallest distance min(|x|, |1-x|, |y|, |1-y|) of
+    the path's points X_1 .. X_s to the boundary lines, s = min(its sub-steps,
+    upto). Test support: where another implementation's exit decision differs
+    from the oracle's, the oracle's path must have come close to the boundary
+    by then. Fixed sub-steps only (exit_mode 0 or 1)."""
+    lib = _load()
+    xs = np.ascontiguousarray(xs, dtype=np.float64)
+    ys = np.ascontiguousarray(ys, dtype=np.float64)
+    node_ids = np.ascontiguousarray(node_ids, dtype=np.uint32)
+    paths = np.ascontiguousarray(paths, dtype=np.uint32)
+    upto = np.ascontiguousarray(upto, dtype=np.int32)
+    count = xs.shape[0]
+    assert ys.shape[0] == count and node_ids.shape[0] == count and paths.shape[0] == count and upto.shape[0] == count
+    if exit_mode == 2:
+        raise ValueError("margins are defined for fixed sub-steps (exit_mode 0 or 1)")
+    P = _Problem(problem.nx, problem.ny, problem.bx.ctypes.data, problem.by.ctypes.data,
+                 problem.xi0.ctypes.data, problem.eta0.ctypes.data, problem.faces.ctypes.data, None, 0)
+    Q = _Params(dt, sub_steps(dt, Dt), exit_mode, seed, step_index)
+    out = np.full(count, np.inf)
+    if count:
+        rc = lib.orc_path_margins(ctypes.byref(P), ctypes.byref(Q), ctypes.c_int64(count), _p(xs), _p(ys),
+                                  _p(node_ids), _p(paths), _p(upto), _p(out))
+        assert rc == 0
     return out
 
 

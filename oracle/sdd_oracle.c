@@ -394,10 +394,15 @@ static int32_t run_path_exp(const orc_problem* P, const orc_params* Q, uint32_t 
  * Returns the number of sub-steps taken; writes the two scores, the end point
  * and the exit code (-1 survived, 0..3 plain exit through face k, 4..7 bridge
  * exit through face k-4). */
+/* One path over one mesh step (Eq. 7a, 7b; Sec. 4). With margin non-null the
+ * path also reports the smallest distance min(|x|, |1 - x|, |y|, |1 - y|) of
+ * its points X_1 .. X_s to the boundary lines, s = min(its sub-steps, upto):
+ * how close a decision of the exit test came to going the other way. */
 static int32_t run_path(const orc_problem* P, const orc_params* Q, uint32_t node, uint32_t path,
                         double x0, double y0, double* score_xi, double* score_eta,
-                        double* xe, double* ye, int32_t* code)
+                        double* xe, double* ye, int32_t* code, double* margin, int32_t upto)
 {
+    double mrg = 1e300;
     const int nx = P->nx, ny = P->ny;
     const double dt = Q->dt;
     const double sq = sqrt(2.0 * dt); /* sigma = sqrt(2), dW = sqrt(dt) N(0,1) */
@@ -435,6 +440,11 @@ static int32_t run_path(const orc_problem* P, const orc_params* Q, uint32_t node
                 double g = cv_bilinear(nx, ny, T + c, x, y);
                 cv_sum[c >> 1] += g * sq * ((c & 1) ? zy : zx);
             }
+        }
+        if (margin && j < upto) {
+            const double m = fmin(fmin(fabs(xn), fabs(1.0 - xn)), fmin(fabs(yn), fabs(1.0 - yn)));
+            mrg = fmin(mrg, m);
+            *margin = mrg;
         }
         /* boundary test after every sub-step; the closed boundary counts */
         if (on_boundary(xn, yn)) {
@@ -538,7 +548,7 @@ int orc_mc_nodes(const orc_problem* P, const orc_params* Q, int64_t count,
                                 ? run_path_exp(P, Q, node_ids[k], (uint32_t)p, xs[k], ys[k], &sx[p], &se[p], &xe, &ye,
                                                &code)
                                 : run_path(P, Q, node_ids[k], (uint32_t)p, xs[k], ys[k], &sx[p], &se[p], &xe, &ye,
-                                           &code);
+                                           &code, NULL, 0);
             if (code >= 0) exits += 1.0;
             steps += (double)taken;
             if (rec_steps) rec_steps[rec + p] = taken;
@@ -559,6 +569,23 @@ int orc_mc_nodes(const orc_problem* P, const orc_params* Q, int64_t count,
         rec += n;
         free(sx);
         free(se);
+    }
+    return 0;
+}
+
+/* For each (node, path) pair: the path's margin (see run_path) over its first
+ * upto[i] sub-steps; fixed sub-steps only (exit_mode 0 or 1). Test support: how
+ * close the oracle's path came to the boundary where another implementation's
+ * exit decision differs. Returns -1 for exponential time-stepping. */
+int orc_path_margins(const orc_problem* P, const orc_params* Q, int64_t count, const double* xs, const double* ys,
+                     const uint32_t* node_ids, const uint32_t* paths, const int32_t* upto, double* margins)
+{
+    if (Q->exit_mode == 2) return -1;
+    for (int64_t i = 0; i < count; ++i) {
+        double sx, se, xe, ye;
+        int32_t code;
+        margins[i] = 1e300;
+        run_path(P, Q, node_ids[i], paths[i], xs[i], ys[i], &sx, &se, &xe, &ye, &code, &margins[i], upto[i]);
     }
     return 0;
 }

@@ -56,3 +56,24 @@ def assert_nodes(g, o, n_paths, same=None, offsets=None):
         clean = np.array([same[offsets[k]:offsets[k + 1]].all() for k in range(len(offsets) - 1)])
         np.testing.assert_array_equal(np.asarray(g["n_exit"])[clean], np.asarray(o["n_exit"])[clean])
         np.testing.assert_array_equal(np.asarray(g["path_steps"])[clean], np.asarray(o["path_steps"])[clean])
+
+
+def assert_flips_near_boundary(oracle_mod, P, xs, ys, n_paths, g, o, same, *, dt, Dt, seed, step_index=0,
+                               node_ids=None, tol=1e-4):
+    """Paths whose exit decision differs (plain exit test): the oracle's path
+    must have come within tol of a boundary line by the first sub-step where
+    the two decisions can differ (the GPU decides in single precision, the
+    oracle in double; away from the boundary both decide alike)."""
+    flips = np.flatnonzero(~np.asarray(same))
+    if flips.size == 0:
+        return 0
+    n_paths = np.broadcast_to(np.asarray(n_paths, np.int64), (len(xs),))
+    offs = np.concatenate([[0], np.cumsum(n_paths)])
+    node = np.searchsorted(offs, flips, side="right") - 1
+    path = flips - offs[node]
+    ids = np.arange(len(xs), dtype=np.uint32) if node_ids is None else np.asarray(node_ids, np.uint32)
+    upto = np.minimum(np.asarray(g["steps"])[flips], np.asarray(o["steps"])[flips])
+    m = oracle_mod.path_margins(P, np.asarray(xs)[node], np.asarray(ys)[node], ids[node], path, upto, dt=dt,
+                                Dt=Dt, seed=seed, step_index=step_index)
+    assert np.all(m <= tol), (flips[m > tol][:10], m[m > tol][:10])
+    return flips.size

@@ -71,6 +71,8 @@ def test_heat65_parity_and_closed_form(sdd, oracle_mod, exit_mode):
     o = oracle_mod.interface_mc(P, xs, ys, npaths, dt=1e-3, Dt=0.05, seed=0, exit_mode=exit_mode, record=True)
     same, rep = PT.assert_records(g, o)
     PT.assert_nodes(g, o, npaths, same, _offsets(npaths))
+    if exit_mode == 0:
+        PT.assert_flips_near_boundary(oracle_mod, P, xs, ys, npaths, g, o, same, dt=1e-3, Dt=0.05, seed=0)
     if exit_mode == 1:
         ex, ee = W.heat_exact(xs, ys, 0.05)
         inner = slice(1, 32)
@@ -99,6 +101,8 @@ def test_front257_full_size_sampled_nodes(sdd, oracle_mod):
     same, rep = PT.assert_records(gs, o)
     gn = {k: g[k][pick] for k in ("mean_xi", "mean_eta", "se_xi", "se_eta", "n_exit", "path_steps")}
     PT.assert_nodes(gn, o, np.full(pick.size, 10000), same, _offsets(np.full(pick.size, 10000)))
+    PT.assert_flips_near_boundary(oracle_mod, P, xs[pick], ys[pick], 10000, gs, o, same, dt=1e-4, Dt=1e-2, seed=0,
+                                  node_ids=pick)
 
 
 @pytest.mark.parametrize("exit_mode", [0, 1])
@@ -119,6 +123,9 @@ def test_ragged_nodes_and_launch_shapes(sdd, oracle_mod, exit_mode, ppt):
     o = oracle_mod.interface_mc(P, xs, ys, npaths, record=True, **kw)
     same, rep = PT.assert_records(g, o)
     PT.assert_nodes(g, o, npaths, same, _offsets(npaths))
+    if exit_mode == 0:
+        PT.assert_flips_near_boundary(oracle_mod, P, xs, ys, npaths, g, o, same, dt=1e-3, Dt=7e-3, seed=12345,
+                                      step_index=9)
     # boundary nodes: the Dirichlet value, zero SE, no steps, all paths counted as exits
     for k in (0, 1):
         assert g["se_xi"][k] == 0 and g["path_steps"][k] == 0 and g["n_exit"][k] == npaths[k]

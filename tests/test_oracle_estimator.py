@@ -229,3 +229,24 @@ def test_exponential_time_stepping_counts_poisson_steps(oracle_mod):
     assert abs(steps.var() - K) < 0.1 * K, steps.var()   # Poisson: variance = mean - 1 here
     # a linear field is preserved exactly whatever the step lengths (zero drift, symmetric increments)
     assert abs(r["mean_xi"][0] - 0.5) < 4 * r["se_xi"][0] + 1e-12
+
+
+def test_path_margin_follows_the_path(oracle_mod):
+    """The margin over the first sub-step of a w = 1 path is the distance of
+    X_1 = X_0 + sqrt(2 dt) Z to the nearest boundary line, Z the first normal
+    pair of the path's Philox block; over the whole step it never exceeds that."""
+    n, dt, Dt, seed = 33, 1e-3, 2e-2, 3
+    P = oracle_mod.Problem(W.w_const(n), *W.identity_fields(n))
+    x0, y0, node, paths = 0.1, 0.93, 7, np.arange(40)
+    ctrs = np.stack([paths, np.full(40, node), np.zeros(40), np.zeros(40)], axis=1)
+    _, z = oracle_mod.draw(seed, ctrs)
+    x1 = x0 + math.sqrt(2 * dt) * z[:, 0]
+    y1 = y0 + math.sqrt(2 * dt) * z[:, 1]
+    want = np.minimum(np.minimum(np.abs(x1), np.abs(1 - x1)), np.minimum(np.abs(y1), np.abs(1 - y1)))
+    one = oracle_mod.path_margins(P, np.full(40, x0), np.full(40, y0), np.full(40, node), paths, np.ones(40),
+                                  dt=dt, Dt=Dt, seed=seed)
+    np.testing.assert_allclose(one, want, rtol=1e-12, atol=1e-15)
+    r = oracle_mod.interface_mc(P, [x0], [y0], 40, dt=dt, Dt=Dt, seed=seed, node_ids=[node], record=True)
+    full = oracle_mod.path_margins(P, np.full(40, x0), np.full(40, y0), np.full(40, node), paths, r["steps"],
+                                   dt=dt, Dt=Dt, seed=seed)
+    assert np.all(full <= one)
