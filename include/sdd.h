@@ -489,15 +489,21 @@ sdd_status sdd_last_step_info(sdd_ctx* ctx, sdd_step_info* out);
 sdd_status sdd_set_step_index(sdd_ctx* ctx, uint32_t n);
 uint32_t sdd_get_step_index(const sdd_ctx* ctx);
 
-/* Allow (on != 0, the default) or forbid pipelined mesh steps; enqueues any
- * pending iterations first. sdd_pipeline_in_use: 1 if the current step graphs
- * are pipelined (known after the first sdd_step with these parameters). */
+/* Allow (on != 0, the default) or forbid pipelined mesh steps (see sdd_step;
+ * Sec. 4 orders a mesh step as the interface estimate, then the subdomain
+ * solves, which both settings keep); enqueues any pending iterations first and
+ * drops the step graphs when the setting changes. SDD_EINVAL for a null
+ * context, else the status of enqueuing the pending iterations.
+ * sdd_pipeline_in_use: 1 if the current step graphs are pipelined (known after
+ * the first sdd_step with these parameters), 0 otherwise or for a null context. */
 sdd_status sdd_set_pipeline(sdd_ctx* ctx, int32_t on);
 int32_t sdd_pipeline_in_use(const sdd_ctx* ctx);
 
 /* Enqueue the pending iterations of the last pipelined mesh step's solve
- * (asynchronous, on the context stream; SDD_OK when none is pending). After
- * it the fields of the last step are complete once the stream reaches it. */
+ * (asynchronous, on the context stream; SDD_OK when none is pending, SDD_EINVAL
+ * for a null context, SDD_ECUDA if the launch fails). After it the fields of
+ * the last step are complete once the stream reaches it; a non-convergence of
+ * those iterations is reported by the next sdd_sync. */
 sdd_status sdd_flush(sdd_ctx* ctx);
 
 /* Enqueue any pending solve (sdd_flush), wait for the context stream and
