@@ -1920,7 +1920,7 @@ sdd_status sdd_step(sdd_ctx* c, const sdd_step_params* p)
         // paths do not read the fields (the field-gradient control variate does)
         const SolveCall probe = make_solve_call(c, p->Dt, p->rtol, p->max_iter, nullptr, nullptr, nullptr, nullptr,
                                                 nullptr, true);
-        const size_t rec_bytes = c->cv_mode ? sizeof(float4) : sizeof(float2);
+        const size_t rec_bytes = (c->cv_mode ? 2 : 1) * sizeof(float4);   // k_paths' deferred-score records
         c->pipe = c->pipe_allowed && solve_single_launch(probe) && c->cv_mode != SDD_CV_FIELDS && c->step_plan.ntasks > 0 &&
                   (size_t)c->step_plan.total_paths * rec_bytes <= (8ULL << 30);
         if (c->pipe) {

@@ -101,7 +101,7 @@ struct PathArgs {
     const uint32_t* step_ptr; // if non-null, read the step index here
     RecDev rec;
     const uint8_t* node_mask; // if non-null, only nodes with a nonzero entry run their paths
-    void* surv;               // if non-null, survivors leave their end records here (indexed rec0 + path)
+    void* surv;               // if non-null, survivors and plain exits leave records here, scored later (rec0 + path)
 };
 
 struct FinalArgs {

@@ -21,7 +21,9 @@
 // Deferred scoring: when the fields of the step's start are still being
 // computed beside the path kernel (pipelined mesh steps), a surviving path
 // leaves its end point (and control-variate sums) in a record array instead,
-// and k_score_surv scores the records once the fields are final, then runs the
+// and so does a path that leaves by the plain test (the sub-step that crossed
+// the boundary: scoring it here would hold its warp on the face-table loads);
+// k_score_surv scores the records once the fields are final, then runs the
 // per-node reduction.
 #include <cuda_fp16.h>
 
@@ -238,14 +240,19 @@ __device__ __forceinline__ long long warp_sum_ll(long long v)
     return v;
 }
 
-// Deferred scoring: a path's end record in the survivor buffer (float2 end
-// point, or float4 end point and control-variate sums with CV); an exit
-// leaves x = -1 there, a value no end point inside the square has.
+// Deferred scoring: a path's record in the survivor buffer, one float4 (two
+// with CV, the second holding the control-variate sums): a survivor leaves
+// (x, y, NaN, 0) with its end point, a path that left by the plain test
+// (x0, y0, x1, y1), the sub-step that crossed the boundary, and a path scored
+// in the kernel (bridge exits) x = -1, a value no point inside the square has.
+__device__ __forceinline__ float rec_nan() { return __int_as_float(0x7fc00000); }
+
 template <bool CV>
-__device__ __forceinline__ void mark_exit(void* surv, long long i)
+__device__ __forceinline__ void put_record(void* surv, long long i, float4 r, float cxi, float ceta)
 {
-    if (CV) static_cast<float4*>(surv)[i] = make_float4(-1.f, 0.f, 0.f, 0.f);
-    else static_cast<float2*>(surv)[i] = f2(-1.f, 0.f);
+    float4* q = static_cast<float4*>(surv) + (CV ? 2 * i : i);
+    q[0] = r;
+    if (CV) q[1] = make_float4(cxi, ceta, 0.f, 0.f);
 }
 
 // Lanes refilled together below this count spend a loop pass drawing their
@@ -313,6 +320,7 @@ __global__ void __launch_bounds__(CV ? kCvMaxBlock : 512, CV ? 3 : 2) k_paths(co
                 int code = -1, taken = 0;
                 float yxi = 0.f, yeta = 0.f, xe = 0.f, ye = 0.f;
                 const bool warm = m < 0;   // draw -1: the pass draws the path's first normals
+                float4 seg = make_float4(-1.f, 0.f, 0.f, 0.f);   // a plain exit's sub-step, scored later
                 // sub-step A: gather, then the next draw's first rounds while the gather is in flight
                 const Cell cA = locate(I, I.bcoef, pos);
                 float4 gA0, gA1;
@@ -347,11 +355,13 @@ __global__ void __launch_bounds__(CV ? kCvMaxBlock : 512, CV ? 3 : 2) k_paths(co
                     if (warm) {
                         // a path taken up mid-task: this pass only drew its first normals
                     } else if (outA) {
-                        plain_exit(I, pos.x, pos.y, pa.x, pa.y, code, yxi, yeta, xe, ye);
+                        if (a.surv) seg = make_float4(pos.x, pos.y, pa.x, pa.y), code = 0;
+                        else plain_exit(I, pos.x, pos.y, pa.x, pa.y, code, yxi, yeta, xe, ye);
                         done = true;
                         taken = 2 * m + 1;
                     } else if (outB) {
-                        plain_exit(I, pa.x, pa.y, pb.x, pb.y, code, yxi, yeta, xe, ye);
+                        if (a.surv) seg = make_float4(pa.x, pa.y, pb.x, pb.y), code = 0;
+                        else plain_exit(I, pa.x, pa.y, pb.x, pb.y, code, yxi, yeta, xe, ye);
                         done = true;
                         taken = 2 * m + 2;
                     } else {
@@ -372,7 +382,8 @@ __global__ void __launch_bounds__(CV ? kCvMaxBlock : 512, CV ? 3 : 2) k_paths(co
                     if (warm) {
                         // a path taken up mid-task: this pass only drew its first normals
                     } else if (outA) {
-                        plain_exit(I, pos.x, pos.y, pa.x, pa.y, code, yxi, yeta, xe, ye);
+                        if (a.surv) seg = make_float4(pos.x, pos.y, pa.x, pa.y), code = 0;
+                        else plain_exit(I, pos.x, pos.y, pa.x, pa.y, code, yxi, yeta, xe, ye);
                         done = true;
                     } else {
                         const float dm0 = fminf(fminf(pos.x, 1.0f - pos.x), fminf(pos.y, 1.0f - pos.y));
@@ -392,16 +403,12 @@ __global__ void __launch_bounds__(CV ? kCvMaxBlock : 512, CV ? 3 : 2) k_paths(co
                     if (!warm && !done && m >= K) done = true;
                 }
                 if (done) {
-                    bool later = false;   // a survivor scored by k_score_surv once the fields are final
+                    bool later = false;   // scored by k_score_surv once the fields are final
                     if (code < 0) {
                         if (a.surv) {
                             later = true;
-                            const long long si = nd.rec0 + path;
-                            if (CV)
-                                static_cast<float4*>(a.surv)[si] =
-                                    make_float4(pos.x, pos.y, cvx.x + cvx.y, cve.x + cve.y);
-                            else
-                                static_cast<float2*>(a.surv)[si] = pos;
+                            put_record<CV>(a.surv, nd.rec0 + path, make_float4(pos.x, pos.y, rec_nan(), 0.f),
+                                           cvx.x + cvx.y, cve.x + cve.y);
                         } else {
                             // survived the mesh step: xi, eta of its start at the end point
                             const Cell c = locate(I, I.fcoef, pos);
@@ -415,7 +422,11 @@ __global__ void __launch_bounds__(CV ? kCvMaxBlock : 512, CV ? 3 : 2) k_paths(co
                         }
                     } else {
                         ++exits;
-                        if (a.surv) mark_exit<CV>(a.surv, nd.rec0 + path);
+                        if (a.surv) {
+                            // a plain exit leaves its sub-step, a bridge exit (scored here) the skip mark
+                            later = seg.x >= 0.f;
+                            put_record<CV>(a.surv, nd.rec0 + path, seg, cvx.x + cvx.y, cve.x + cve.y);
+                        }
                     }
                     if (!later) {
                         if (CV) {
@@ -539,8 +550,10 @@ __global__ void __launch_bounds__(512, 2) k_paths_exp(const PathArgs a)
                 bool done = false;
                 int code = -1;
                 float yxi = 0.f, yeta = 0.f, xe = 0.f, ye = 0.f;
+                float4 seg = make_float4(-1.f, 0.f, 0.f, 0.f);
                 if (!inside2(pn)) {
-                    plain_exit(I, pos.x, pos.y, pn.x, pn.y, code, yxi, yeta, xe, ye);
+                    if (a.surv) seg = make_float4(pos.x, pos.y, pn.x, pn.y), code = 0;
+                    else plain_exit(I, pos.x, pos.y, pn.x, pn.y, code, yxi, yeta, xe, ye);
                     done = true;
                 } else {
                     const float dm0 = fminf(fminf(pos.x, 1.0f - pos.x), fminf(pos.y, 1.0f - pos.y));
@@ -560,7 +573,8 @@ __global__ void __launch_bounds__(512, 2) k_paths_exp(const PathArgs a)
                     if (code < 0) {
                         if (a.surv) {
                             later = true;
-                            static_cast<float2*>(a.surv)[nd.rec0 + path] = pos;
+                            put_record<false>(a.surv, nd.rec0 + path, make_float4(pos.x, pos.y, rec_nan(), 0.f), 0.f,
+                                              0.f);
                         } else {
                             const Cell cf = locate(I, I.fcoef, pos);
                             float4 f0, f1;
@@ -573,7 +587,10 @@ __global__ void __launch_bounds__(512, 2) k_paths_exp(const PathArgs a)
                         }
                     } else {
                         ++exits;
-                        if (a.surv) mark_exit<false>(a.surv, nd.rec0 + path);
+                        if (a.surv) {
+                            later = seg.x >= 0.f;
+                            put_record<false>(a.surv, nd.rec0 + path, seg, 0.f, 0.f);
+                        }
                     }
                     if (!later) {
                         ax.add(yxi - x0);
@@ -654,17 +671,19 @@ __global__ void __launch_bounds__(SCORE_THREADS) k_score_surv(const ScoreArgs a)
     Acc ax{0.f, 0.f, 0.f, 0.f}, ae{0.f, 0.f, 0.f, 0.f};
     for (int p0 = threadIdx.x; p0 < end; p0 += SCORE_BATCH * SCORE_THREADS) {
         float4 r[SCORE_BATCH];
+        float2 cvs[SCORE_BATCH];
 #pragma unroll
         for (int u = 0; u < SCORE_BATCH; ++u) {
             const int p = p0 + u * SCORE_THREADS;
             r[u] = make_float4(-1.f, 0.f, 0.f, 0.f);
+            cvs[u] = f2(0.f, 0.f);
             if (p < end) {
                 const long long si = nd.rec0 + p;
+                const float4* q = static_cast<const float4*>(a.surv) + (CV ? 2 * si : si);
+                r[u] = q[0];
                 if (CV) {
-                    r[u] = static_cast<const float4*>(a.surv)[si];
-                } else {
-                    const float2 q = static_cast<const float2*>(a.surv)[si];
-                    r[u] = make_float4(q.x, q.y, 0.f, 0.f);
+                    const float4 c = q[1];
+                    cvs[u] = f2(c.x, c.y);
                 }
             }
         }
@@ -672,17 +691,28 @@ __global__ void __launch_bounds__(SCORE_THREADS) k_score_surv(const ScoreArgs a)
         float2 st[SCORE_BATCH];
 #pragma unroll
         for (int u = 0; u < SCORE_BATCH; ++u) {
-            // an exit (x = -1) or a thread past the end reads cell 0 and is not added
-            const Cell c = locate(I, I.fcoef, f2(fmaxf(r[u].x, 0.f), r[u].y));
+            // survivors gather the field record at their end point; other records read cell 0 unused
+            const bool surv = r[u].x >= 0.f && isnan(r[u].z);
+            const Cell c = locate(I, I.fcoef, surv ? f2(r[u].x, r[u].y) : f2(0.f, 0.f));
             load_cell(c.p, f0[u], f1[u]);
             st[u] = c.st;
         }
 #pragma unroll
         for (int u = 0; u < SCORE_BATCH; ++u) {
-            if (r[u].x < 0.f) continue;   // the path left the domain
-            const float2 v = eval2(f0[u], f1[u], st[u]);
-            ax.add(v.x - r[u].z - x0);
-            ae.add(v.y - r[u].w - y0);
+            if (r[u].x < 0.f) continue;   // scored in the path kernel, or past the end
+            float yxi, yeta;
+            if (isnan(r[u].z)) {
+                const float2 v = eval2(f0[u], f1[u], st[u]);
+                yxi = v.x;
+                yeta = v.y;
+            } else {
+                // left the domain in the sub-step (x0, y0) -> (x1, y1): the boundary data there
+                int face;
+                float xe, ye;
+                plain_exit(I, r[u].x, r[u].y, r[u].z, r[u].w, face, yxi, yeta, xe, ye);
+            }
+            ax.add(yxi - cvs[u].x - x0);
+            ae.add(yeta - cvs[u].y - y0);
         }
     }
     const double v[4] = {warp_sum(ax.sum()), warp_sum(ax.sumsq()), warp_sum(ae.sum()), warp_sum(ae.sumsq())};
