@@ -181,6 +181,7 @@ struct sdd_ctx {
     // step n + 1's graph beside its paths, whose survivors are scored once the
     // solve is done. graph_p[parity] begins with the pending iterations.
     bool pipe_allowed = true;       // sdd_set_pipeline
+    bool defer = false;             // the step graphs score survivors and plain exits after the path kernel
     bool pipe = false;              // the step graphs defer the iterations
     bool pending = false;           // iterations of the last step not enqueued yet
     SolveCall step_call[2];         // the solve set up by graph[parity] / graph_p[parity]
@@ -1836,7 +1837,7 @@ static sdd_status capture_step(sdd_ctx* c, const sdd_step_params* p, int K, int 
     if (st == SDD_OK && kmask) st = enqueue_keypoints(c, c->d_kmask.p, s);
     if (st == SDD_OK)
         st = run_plan(c, c->step_plan, p->dt, K, p->seed, 0, c->d_step.p, p->exit_mode, o, nullptr, s, c->ev[1],
-                      c->ev[2], kmask, c->pipe ? (void*)c->surv.p : nullptr, join);
+                      c->ev[2], kmask, c->defer ? (void*)c->surv.p : nullptr, join);
     if (st == SDD_OK && kmask) {
         cudaError_t e = launch_pchip(c->d_klines.p, (int)c->klines.size(), c->d_kpos_idx.p, c->d_kpos_cross.p, kmask,
                                      c->faces64.p, c->nx, c->ny, o.mean_xi, o.mean_eta, c->d_kscratch.p, s);
@@ -1920,9 +1921,13 @@ sdd_status sdd_step(sdd_ctx* c, const sdd_step_params* p)
         // paths do not read the fields (the field-gradient control variate does)
         const SolveCall probe = make_solve_call(c, p->Dt, p->rtol, p->max_iter, nullptr, nullptr, nullptr, nullptr,
                                                 nullptr, true);
-        const size_t rec_bytes = (c->cv_mode ? 2 : 1) * sizeof(float4);   // k_paths' deferred-score records
-        c->pipe = c->pipe_allowed && solve_single_launch(probe) && c->cv_mode != SDD_CV_FIELDS && c->step_plan.ntasks > 0 &&
-                  (size_t)c->step_plan.total_paths * rec_bytes <= (8ULL << 30);
+        // deferred scoring (survivors and plain exits scored after the path kernel) where the
+        // records fit; pipelining needs it
+        const size_t rec_bytes = (c->cv_mode ? 2 : 1) * sizeof(float4);
+        c->defer = c->step_plan.ntasks > 0 && (size_t)c->step_plan.total_paths * rec_bytes <= (8ULL << 30);
+        c->pipe = c->pipe_allowed && solve_single_launch(probe) && c->cv_mode != SDD_CV_FIELDS && c->defer;
+        if (c->defer)
+            CU(c, c->surv.alloc(((size_t)c->step_plan.total_paths * rec_bytes + sizeof(float4) - 1) / sizeof(float4)));
         if (c->pipe) {
             if (!c->pipe_stream) {
                 // its kernels take SMs before the waiting blocks of the path kernel
@@ -1932,7 +1937,6 @@ sdd_status sdd_step(sdd_ctx* c, const sdd_step_params* p)
             }
             for (cudaEvent_t& e : c->pev)
                 if (!e) CU(c, cudaEventCreate(&e));
-            CU(c, c->surv.alloc(((size_t)c->step_plan.total_paths * rec_bytes + sizeof(float4) - 1) / sizeof(float4)));
         }
         for (int parity = 0; parity < 2; ++parity)
             if ((st = capture_step(c, p, K, parity, false)) != SDD_OK) return st;
