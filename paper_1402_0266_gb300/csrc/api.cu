@@ -191,6 +191,8 @@ struct sdd_ctx {
     bool last_had_pending = false;  // the last launched graph ran deferred iterations
     DevBuf<float4> surv;            // survivor end records of the step's paths
     cudaStream_t pipe_stream = nullptr;  // the side branch (highest priority)
+    cudaStream_t faces_stream = nullptr; // the face data beside the drift records
+    cudaEvent_t fev[2] = {nullptr, nullptr};
     // fork, join of the field records, iterations start, end, join of the systems
     cudaEvent_t pev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 
@@ -1824,7 +1826,21 @@ static sdd_status capture_step(sdd_ctx* c, const sdd_step_params* p, int K, int 
         if (st == SDD_OK) st = enqueue_solve_system(c, c->step_call[parity], q);
         cu(cudaEventRecord(c->pev[4], q));
     }
-    if (st == SDD_OK) st = c->pipe ? prepare_parts(c, s, true, false) : prepare(c, s);
+    if (st == SDD_OK && c->pipe) {
+        // the face data (one small block's prefix sums) on a third branch, beside the drift records
+        const bool faces = !c->user_faces;
+        if (faces) {
+            cu(cudaEventRecord(c->fev[0], s));
+            cu(cudaStreamWaitEvent(c->faces_stream, c->fev[0], 0));
+            cu(launch_winslow_faces(c->w.p, c->nx, c->ny, c->faces64.p, c->faces32.p, c->faces_stream));
+            cu(cudaEventRecord(c->fev[1], c->faces_stream));
+        }
+        cu(launch_prep_cells(c->w.p, nullptr, nullptr, c->nx, c->ny, c->bcoef.p, nullptr, c->d_status.p, s));
+        if (faces) cu(cudaStreamWaitEvent(s, c->fev[1], 0));
+        c->dirty_w = false;
+    } else if (st == SDD_OK) {
+        st = prepare(c, s);
+    }
     if (st == SDD_OK) st = enqueue_cv_refresh(c, K, s);
     OutDev o{};
     o.mean_xi = c->iface_stats[0].p;
@@ -1936,6 +1952,9 @@ sdd_status sdd_step(sdd_ctx* c, const sdd_step_params* p)
                 CU(c, cudaStreamCreateWithPriority(&c->pipe_stream, cudaStreamNonBlocking, greatest));
             }
             for (cudaEvent_t& e : c->pev)
+                if (!e) CU(c, cudaEventCreate(&e));
+            if (!c->faces_stream) CU(c, cudaStreamCreateWithFlags(&c->faces_stream, cudaStreamNonBlocking));
+            for (cudaEvent_t& e : c->fev)
                 if (!e) CU(c, cudaEventCreate(&e));
         }
         for (int parity = 0; parity < 2; ++parity)
@@ -2060,6 +2079,9 @@ void sdd_destroy(sdd_ctx* c)
     if (c->mg_s3) cudaStreamDestroy(c->mg_s3);
     if (c->pipe_stream) cudaStreamDestroy(c->pipe_stream);
     for (cudaEvent_t e : c->pev)
+        if (e) cudaEventDestroy(e);
+    if (c->faces_stream) cudaStreamDestroy(c->faces_stream);
+    for (cudaEvent_t e : c->fev)
         if (e) cudaEventDestroy(e);
     delete c;  // device buffers are freed by their destructors
 }
