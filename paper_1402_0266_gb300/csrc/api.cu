@@ -1810,6 +1810,13 @@ static sdd_status capture_step(sdd_ctx* c, const sdd_step_params* p, int K, int 
                                            c->fld[1 - parity][1].p, c->w.p, c->fld[parity][0].p,
                                            c->fld[parity][1].p, c->pipe);
     cudaEvent_t join = nullptr;
+    if (c->pipe && !c->user_faces) {
+        // the face data (one small block's prefix sums) on a third branch, beside the drift records
+        cu(cudaEventRecord(c->fev[0], s));
+        cu(cudaStreamWaitEvent(c->faces_stream, c->fev[0], 0));
+        cu(launch_winslow_faces(c->w.p, c->nx, c->ny, c->faces64.p, c->faces32.p, c->faces_stream));
+        cu(cudaEventRecord(c->fev[1], c->faces_stream));
+    }
     if (c->pipe) {
         cudaStream_t q = c->pipe_stream;
         cu(cudaEventRecord(c->pev[0], s));
@@ -1824,19 +1831,16 @@ static sdd_status capture_step(sdd_ctx* c, const sdd_step_params* p, int K, int 
         cu(cudaEventRecord(c->pev[1], q));
         join = c->pev[1];
         if (st == SDD_OK) st = enqueue_solve_system(c, c->step_call[parity], q);
+        // the new fields' faces and interior start (this step's face data, made on the third branch)
+        if (!c->user_faces) cu(cudaStreamWaitEvent(q, c->fev[1], 0));
+        const SolveCall& k = c->step_call[parity];
+        cu(launch_dirichlet_faces(c->faces64.p, k.px, k.pe, c->nx, c->ny, k.a.x[0], k.a.x[1], q));
         cu(cudaEventRecord(c->pev[4], q));
     }
     if (st == SDD_OK && c->pipe) {
-        // the face data (one small block's prefix sums) on a third branch, beside the drift records
-        const bool faces = !c->user_faces;
-        if (faces) {
-            cu(cudaEventRecord(c->fev[0], s));
-            cu(cudaStreamWaitEvent(c->faces_stream, c->fev[0], 0));
-            cu(launch_winslow_faces(c->w.p, c->nx, c->ny, c->faces64.p, c->faces32.p, c->faces_stream));
-            cu(cudaEventRecord(c->fev[1], c->faces_stream));
-        }
+        // the drift records; the face data come from the third branch forked above
         cu(launch_prep_cells(c->w.p, nullptr, nullptr, c->nx, c->ny, c->bcoef.p, nullptr, c->d_status.p, s));
-        if (faces) cu(cudaStreamWaitEvent(s, c->fev[1], 0));
+        if (!c->user_faces) cu(cudaStreamWaitEvent(s, c->fev[1], 0));
         c->dirty_w = false;
     } else if (st == SDD_OK) {
         st = prepare(c, s);
@@ -1860,16 +1864,19 @@ static sdd_status capture_step(sdd_ctx* c, const sdd_step_params* p, int K, int 
         if (e != cudaSuccess) st = fail(c, SDD_ECUDA, "interface fill: %s", cudaGetErrorString(e));
     }
     rec_ext(c->ev[3], s);
-    if (st == SDD_OK) {
+    if (st == SDD_OK && c->pipe) {
+        // the systems and the faces of the new fields were made beside the paths; the interface
+        // values close the step, with the step counter
+        cu(cudaStreamWaitEvent(s, c->pev[4], 0));
+        const SolveCall& k = c->step_call[parity];
+        cu(launch_scatter_iface(o.mean_xi, o.mean_eta, c->d_iface_idx.p, (int)c->iface_idx.size(), k.a.x[0],
+                                k.a.x[1], c->d_step.p, s));
+    } else if (st == SDD_OK) {
         st = enqueue_solve_dirichlet(c, c->step_call[parity], o.mean_xi, o.mean_eta, s);
-        if (c->pipe) {
-            cu(cudaStreamWaitEvent(s, c->pev[4], 0));   // this step's systems, built beside the paths
-        } else if (st == SDD_OK) {
-            st = enqueue_solve_system(c, c->step_call[parity], s);
-            if (st == SDD_OK) st = enqueue_solve_iterate(c, c->step_call[parity], s);
-        }
+        if (st == SDD_OK) st = enqueue_solve_system(c, c->step_call[parity], s);
+        if (st == SDD_OK) st = enqueue_solve_iterate(c, c->step_call[parity], s);
+        if (st == SDD_OK) cu(launch_bump_step(c->d_step.p, s));
     }
-    if (st == SDD_OK) cu(launch_bump_step(c->d_step.p, s));
     rec_ext(c->ev[4], s);
     c->cur = saved;
     c->dirty_w = keep_w;

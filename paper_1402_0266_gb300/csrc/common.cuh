@@ -285,6 +285,13 @@ int solve_cluster_size(int nsys, int min_rows, int sm_count);
 cudaError_t launch_dirichlet(const double* faces64, const double* prev_xi, const double* prev_eta,
                              const double* iface_xi, const double* iface_eta, const int32_t* iface_idx,
                              int n_iface, int nx, int ny, double* xi_out, double* eta_out, cudaStream_t s);
+// The two halves of launch_dirichlet: the faces and the old interior into the
+// new fields; the interface values into them (and, if step is non-null, the
+// mesh step counter increased by one).
+cudaError_t launch_dirichlet_faces(const double* faces64, const double* prev_xi, const double* prev_eta, int nx,
+                                   int ny, double* xi_out, double* eta_out, cudaStream_t s);
+cudaError_t launch_scatter_iface(const double* iface_xi, const double* iface_eta, const int32_t* iface_idx,
+                                 int n_iface, double* xi_out, double* eta_out, uint32_t* step, cudaStream_t s);
 cudaError_t launch_pcg(const SolveArgs& a, int upt, int rows_max, int max_mx, cudaStream_t s);
 int solve_reg_upt(int max_band_unknowns);
 cudaError_t launch_bump_step(uint32_t* step, cudaStream_t s);

@@ -90,9 +90,10 @@ __global__ void k_dirichlet(const double* __restrict__ faces, const double* __re
 
 __global__ void k_scatter_iface(const double* __restrict__ vx, const double* __restrict__ ve,
                                 const int32_t* __restrict__ idx, int n, double* __restrict__ xo,
-                                double* __restrict__ eo)
+                                double* __restrict__ eo, uint32_t* step)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (step && k == 0) *step += 1u;   // the mesh step counter, when this closes the step
     if (k >= n) return;
     xo[idx[k]] = vx[k];
     eo[idx[k]] = ve[k];
@@ -509,7 +510,24 @@ cudaError_t launch_dirichlet(const double* faces64, const double* prev_xi, const
     k_dirichlet<<<grid, block, 0, s>>>(faces64, prev_xi, prev_eta, nx, ny, xi_out, eta_out);
     if (n_iface > 0)
         k_scatter_iface<<<(n_iface + 255) / 256, 256, 0, s>>>(iface_xi, iface_eta, iface_idx, n_iface, xi_out,
-                                                             eta_out);
+                                                             eta_out, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dirichlet_faces(const double* faces64, const double* prev_xi, const double* prev_eta, int nx,
+                                   int ny, double* xi_out, double* eta_out, cudaStream_t s)
+{
+    const dim3 block(32, 8);
+    const dim3 grid((nx + 31) / 32, (ny + 7) / 8);
+    k_dirichlet<<<grid, block, 0, s>>>(faces64, prev_xi, prev_eta, nx, ny, xi_out, eta_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_iface(const double* iface_xi, const double* iface_eta, const int32_t* iface_idx,
+                                 int n_iface, double* xi_out, double* eta_out, uint32_t* step, cudaStream_t s)
+{
+    const int n = n_iface > 0 ? n_iface : 1;
+    k_scatter_iface<<<(n + 255) / 256, 256, 0, s>>>(iface_xi, iface_eta, iface_idx, n_iface, xi_out, eta_out, step);
     return cudaGetLastError();
 }
 
