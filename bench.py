@@ -355,17 +355,30 @@ def run_ours(args, world, rank, local):
     if pipelined:
         reset()
         sdd.sdd_set_pipeline(ctx, False)
-        a_ms = []
+        a_ms, a_step = [], []
         for k in range(min(K, 8)):
             flush.zero_()
             sdd.sdd_set_w(ctx, w_all[k])
             sdd.sdd_step(ctx, **sp)
-            a_ms.append(sdd.sdd_last_step_info(ctx)["paths_ms"])
+            info = sdd.sdd_last_step_info(ctx)
+            a_ms.append(info["paths_ms"])
+            a_step.append(info["step_ms"])
         sdd.sdd_set_pipeline(ctx, True)
         a_mean = statistics.mean(a_ms[1:] if len(a_ms) > 1 else a_ms)
         a_ach = ALG_OPS_PER_PATH_STEP * steps_per_launch / (a_mean / 1e3) / 1e12
         alone = {"paths_kernel_ms": a_mean, "achieved": a_ach, "frac": a_ach / peak,
+                 "unpipelined_step_ms": statistics.mean(a_step[1:] if len(a_step) > 1 else a_step),
                  "note": "unpipelined steps after the timed region (the same launches without the solve beside)"}
+
+    # the second bound: every sub-step gathers one 32-byte cell record from a random cell, one L1
+    # sector and so one wavefront of the L1 data pipe, which serves one wavefront per SM cycle
+    gather_peak = props.multi_processor_count * sm_max * 1e6
+    gather = {"resource": "L1 data pipe", "unit": "wavefronts/s", "wavefronts_per_path_step": 1,
+              "achieved": steps_per_launch / (mean_paths_ms / 1e3), "peak": gather_peak,
+              "frac": steps_per_launch / (mean_paths_ms / 1e3) / gather_peak,
+              "peak_basis": f"{props.multi_processor_count} SMs x 1 wavefront x {sm_max:.0f} MHz"}
+    if alone is not None:
+        gather["frac_alone"] = steps_per_launch / (alone["paths_kernel_ms"] / 1e3) / gather_peak
 
     # the same mesh steps with the control variate of the previous fields' gradient:
     # throughput, and the variance against the plain estimator on the same state
@@ -437,7 +450,7 @@ def run_ours(args, world, rank, local):
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_paths", "ops_per_path_step": ALG_OPS_PER_PATH_STEP,
                          "peak_basis": f"{props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz",
-                         "alone": alone},
+                         "alone": alone, "gather_bound": gather},
             "equal_error": equal_error,
             "cpu_baseline": cpu,
             "e2e": e2e,
