@@ -8,7 +8,7 @@
 // launches spends its time in launch latency:
 //
 //   * the cluster's blocks split the subdomain's rows; every thread keeps one
-//     or two unknowns of the finest level in registers (coefficients, the
+//     to four unknowns of the finest level in registers (coefficients, the
 //     residual r, the product q, the correction d); the V-cycle iterate z,
 //     the search direction p and the fine residual live in shared memory, and
 //     a block reads its neighbours' edge rows straight from their shared
@@ -17,6 +17,10 @@
 //     of the cluster's first block, which runs that part of every V-cycle
 //     alone while the others wait; the other blocks write their share of the
 //     restricted residual into it and read the coarse correction back from it;
+//     the levels are described by offsets into the shared memory, kept once
+//     per block in shared memory, and the kernel uses no local memory (with
+//     up to 210 KB of shared memory per block the L1 cannot hold 512 threads'
+//     stack frames, and every local access would go to L2);
 //   * dot products are reduced inside each block, then across the cluster in
 //     a fixed order (every block takes the same branch); the loop counts are
 //     bounded (max_outer refinement sweeps, max_iter inner iterations).
@@ -30,68 +34,88 @@
 namespace sdd {
 namespace {
 
-// a coarse level in the first block's shared memory
+// The kernel's dynamic shared memory.
+extern __shared__ float mgc_sm[];
+
+// a coarse level in the first block's shared memory: its arrays as offsets
+// into the dynamic shared memory, so that every access is a shared-memory load
 struct SLv {
-    float* D;
-    float* CX;
-    float* CY;
-    float* U[2];
-    float* F[2];
+    int D, CX, CY, U[2], F[2];
     int mx, my, W;
 };
 
-__device__ __forceinline__ void s_smooth(const SLv& v, int idx)
+// floor(k / d) for 0 <= k from the single-precision product (k + 1/2) fl(1/d):
+// (k + 1/2) / d lies at least 1/(2d) from every integer, and the two roundings
+// move the product by less than (k + 1/2) 2^-23, so the quotient is exact while
+// (k + 1/2) d < 2^22 (mgc_config admits only levels within that bound).
+__device__ __forceinline__ int qdiv(int k, float rd) { return __float2int_rz(__fmul_rn((float)k + 0.5f, rd)); }
+
+// One point of a red-black sweep: the level's offsets and row length are
+// passed as values, so no descriptor is re-read after the stores.
+__device__ __forceinline__ void s_smooth(int oD, int oCX, int oCY, int oU0, int oU1, int oF0, int oF1, int W, int idx)
 {
-    const float id = 1.f / v.D[idx];
-    const float cw = v.CX[idx - 1], ce = v.CX[idx], cs = v.CY[idx - v.W], cn = v.CY[idx];
-#pragma unroll
-    for (int f = 0; f < 2; ++f) {
-        const float* U = v.U[f];
-        v.U[f][idx] = (v.F[f][idx] + cw * U[idx - 1] + ce * U[idx + 1] + cs * U[idx - v.W] + cn * U[idx + v.W]) * id;
-    }
+    const float id = 1.f / mgc_sm[oD + idx];
+    const float cw = mgc_sm[oCX + idx - 1], ce = mgc_sm[oCX + idx], cs = mgc_sm[oCY + idx - W], cn = mgc_sm[oCY + idx];
+    const float n0 = mgc_sm[oF0 + idx] + cw * mgc_sm[oU0 + idx - 1] + ce * mgc_sm[oU0 + idx + 1] +
+                     cs * mgc_sm[oU0 + idx - W] + cn * mgc_sm[oU0 + idx + W];
+    const float n1 = mgc_sm[oF1 + idx] + cw * mgc_sm[oU1 + idx - 1] + ce * mgc_sm[oU1 + idx + 1] +
+                     cs * mgc_sm[oU1 + idx - W] + cn * mgc_sm[oU1 + idx + W];
+    mgc_sm[oU0 + idx] = n0 * id;
+    mgc_sm[oU1 + idx] = n1 * id;
 }
 
 __device__ __forceinline__ float s_res(const SLv& v, int f, int idx)
 {
-    const float* U = v.U[f];
-    return v.F[f][idx] - (v.D[idx] * U[idx] - v.CX[idx - 1] * U[idx - 1] - v.CX[idx] * U[idx + 1] -
-                          v.CY[idx - v.W] * U[idx - v.W] - v.CY[idx] * U[idx + v.W]);
+    const float* U = mgc_sm + v.U[f];
+    const float* D = mgc_sm + v.D;
+    const float* CX = mgc_sm + v.CX;
+    const float* CY = mgc_sm + v.CY;
+    return mgc_sm[v.F[f] + idx] - (D[idx] * U[idx] - CX[idx - 1] * U[idx - 1] - CX[idx] * U[idx + 1] -
+                                   CY[idx - v.W] * U[idx - v.W] - CY[idx] * U[idx + v.W]);
+}
+
+// One red-black half-sweep of level v (the points of one colour), then a block barrier.
+__device__ __forceinline__ void s_sweep(const SLv& v, int color)
+{
+    const int mxl = v.mx, W = v.W;
+    const int oD = v.D, oCX = v.CX, oCY = v.CY, oU0 = v.U[0], oU1 = v.U[1], oF0 = v.F[0], oF1 = v.F[1];
+    const int per_row = (mxl + 1) >> 1;
+    const int n = per_row * v.my;
+    const float rpr = 1.f / (float)per_row;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int q = qdiv(k, rpr);
+        const int jp = 1 + q;
+        const int ip = 1 + 2 * (k - q * per_row) + ((jp + 1 + color) & 1);
+        if (ip <= mxl) s_smooth(oD, oCX, oCY, oU0, oU1, oF0, oF1, W, jp * W + ip);
+    }
+    __syncthreads();
 }
 
 // The V-cycle below the finest level, by one block on its shared memory
 // (levels 1 .. L-1 of lv; U of level 1 starts at zero, F of level 1 is given).
 __device__ void coarse_cycle(const SLv* lv, int L, int nu, int coarse_sweeps)
 {
-    auto sweep = [&](int l, int color) {
-        const SLv& v = lv[l];
-        const int per_row = (v.mx + 1) / 2;
-        const int n = per_row * v.my;
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            const int jp = 1 + k / per_row;
-            const int ip = 1 + 2 * (k % per_row) + ((jp + 1 + color) & 1);
-            if (ip <= v.mx) s_smooth(v, jp * v.W + ip);
-        }
-        __syncthreads();
-    };
     for (int l = 1; l < L - 1; ++l) {
-        for (int k = 0; k < nu; ++k) {
-            sweep(l, 0);
-            sweep(l, 1);
-        }
         const SLv& h = lv[l];
         const SLv& c = lv[l + 1];
+        for (int k = 0; k < nu; ++k) {
+            s_sweep(h, 0);
+            s_sweep(h, 1);
+        }
         const int P = c.W * (c.my + 2);
+        const float rW = 1.f / (float)c.W;
         for (int idx = threadIdx.x; idx < P; idx += blockDim.x) {
-            const int I = idx % c.W, J = idx / c.W;
-            c.U[0][idx] = c.U[1][idx] = 0.f;
+            const int J = qdiv(idx, rW), I = idx - J * c.W;
+            mgc_sm[c.U[0] + idx] = mgc_sm[c.U[1] + idx] = 0.f;
             if (I < 1 || I > c.mx || J < 1 || J > c.my) continue;
             const int fc = 2 * J * h.W + 2 * I;
+#pragma unroll
             for (int f = 0; f < 2; ++f) {
                 float acc = 4.f * s_res(h, f, fc);
                 acc += 2.f * (s_res(h, f, fc - 1) + s_res(h, f, fc + 1) + s_res(h, f, fc - h.W) + s_res(h, f, fc + h.W));
                 acc += s_res(h, f, fc - h.W - 1) + s_res(h, f, fc - h.W + 1) + s_res(h, f, fc + h.W - 1) +
                        s_res(h, f, fc + h.W + 1);
-                c.F[f][idx] = acc * (1.f / 16.f);
+                mgc_sm[c.F[f] + idx] = acc * (1.f / 16.f);
             }
         }
         __syncthreads();
@@ -99,16 +123,17 @@ __device__ void coarse_cycle(const SLv* lv, int L, int nu, int coarse_sweeps)
     {
         const SLv& v = lv[L - 1];
         if (v.mx == 1 && v.my == 1) {
-            if (threadIdx.x < 2) v.U[threadIdx.x][v.W + 1] = v.F[threadIdx.x][v.W + 1] / v.D[v.W + 1];
+            if (threadIdx.x < 2)
+                mgc_sm[v.U[threadIdx.x] + v.W + 1] = mgc_sm[v.F[threadIdx.x] + v.W + 1] / mgc_sm[v.D + v.W + 1];
             __syncthreads();
         } else {
             for (int k = 0; k < coarse_sweeps; ++k) {
-                sweep(L - 1, 0);
-                sweep(L - 1, 1);
+                s_sweep(v, 0);
+                s_sweep(v, 1);
             }
             for (int k = 0; k < coarse_sweeps; ++k) {
-                sweep(L - 1, 1);
-                sweep(L - 1, 0);
+                s_sweep(v, 1);
+                s_sweep(v, 0);
             }
         }
     }
@@ -116,27 +141,34 @@ __device__ void coarse_cycle(const SLv* lv, int L, int nu, int coarse_sweeps)
         const SLv& h = lv[l];
         const SLv& c = lv[l + 1];
         const int n = h.mx * h.my;
+        const float rmx = 1.f / (float)h.mx;
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            const int ip = 1 + k % h.mx, jp = 1 + k / h.mx;
+            const int q = qdiv(k, rmx);
+            const int jp = 1 + q, ip = 1 + k - q * h.mx;
             const int I0 = ip >> 1, J0 = jp >> 1, I1 = (ip + 1) >> 1, J1 = (jp + 1) >> 1;
             const int e = jp * h.W + ip;
+            float corr[2];
+#pragma unroll
             for (int f = 0; f < 2; ++f) {
-                const float* Uc = c.U[f];
-                h.U[f][e] += 0.25f * (Uc[J0 * c.W + I0] + Uc[J0 * c.W + I1] + Uc[J1 * c.W + I0] + Uc[J1 * c.W + I1]);
+                const float* Uc = mgc_sm + c.U[f];
+                corr[f] = mgc_sm[h.U[f] + e] +
+                          0.25f * (Uc[J0 * c.W + I0] + Uc[J0 * c.W + I1] + Uc[J1 * c.W + I0] + Uc[J1 * c.W + I1]);
             }
+            mgc_sm[h.U[0] + e] = corr[0];
+            mgc_sm[h.U[1] + e] = corr[1];
         }
         __syncthreads();
         for (int k = 0; k < nu; ++k) {
-            sweep(l, 1);
-            sweep(l, 0);
+            s_sweep(h, 1);
+            s_sweep(h, 0);
         }
     }
 }
 
 template <int UPT>
-__global__ void __launch_bounds__(SOLVE_THREADS) k_mgc(const MgArgs a, int rows_max)
+__global__ void __launch_bounds__(SOLVE_THREADS, 1) k_mgc(const MgArgs a, int rows_max)
 {
-    extern __shared__ float sm[];
+    float* const sm = mgc_sm;
     cg::cluster_group cl = cg::this_cluster();
     const int C = (int)cl.num_blocks();
     const int rank = (int)cl.block_rank();
@@ -153,10 +185,12 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_mgc(const MgArgs a, int rows_
     float* Zs = sm;                  // V-cycle iterate z
     float* Ps = sm + 2 * plane;      // search direction p
     float* Rs = sm + 4 * plane;      // residual f - A z inside the V-cycle
-    // coarse levels, in every block at the same offsets (only the first block's are used)
-    SLv lv[kMgMaxLevels];
-    {
-        float* q = sm + 6 * plane;
+    // coarse levels, in every block at the same offsets (only the first block's are used).
+    // One copy of their descriptors per block, in shared memory: a per-thread copy would
+    // sit in local memory, which the L1 left beside this kernel's shared memory cannot hold.
+    __shared__ SLv lv[kMgMaxLevels];
+    if (threadIdx.x == 0) {
+        int q = 6 * plane;
         for (int l = 1; l < a.levels; ++l) {
             const int Wl = a.mx[l] + 2, P = Wl * (a.my[l] + 2);
             lv[l].mx = a.mx[l];
@@ -172,16 +206,20 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_mgc(const MgArgs a, int rows_
             q += 7 * P;
         }
     }
+    __syncthreads();
+    // the neighbours' planes and the first block's level-1 arrays, at the same offsets
+    // from the mapped base of each block's shared memory
     const float* Z_lo = rank > 0 ? cl.map_shared_rank(Zs, rank - 1) : nullptr;
     const float* Z_hi = rank < C - 1 ? cl.map_shared_rank(Zs, rank + 1) : nullptr;
-    const float* P_lo = rank > 0 ? cl.map_shared_rank(Ps, rank - 1) : nullptr;
-    const float* P_hi = rank < C - 1 ? cl.map_shared_rank(Ps, rank + 1) : nullptr;
-    const float* R_lo = rank > 0 ? cl.map_shared_rank(Rs, rank - 1) : nullptr;
-    const float* R_hi = rank < C - 1 ? cl.map_shared_rank(Rs, rank + 1) : nullptr;
-    float* F1_0 = a.levels > 1 ? cl.map_shared_rank(lv[1].F[0], 0) : nullptr;   // the first block's level-1 rhs
-    float* F1_1 = a.levels > 1 ? cl.map_shared_rank(lv[1].F[1], 0) : nullptr;
-    const float* U1_0 = a.levels > 1 ? cl.map_shared_rank(lv[1].U[0], 0) : nullptr;
-    const float* U1_1 = a.levels > 1 ? cl.map_shared_rank(lv[1].U[1], 0) : nullptr;
+    const float* P_lo = Z_lo ? Z_lo + 2 * plane : nullptr;
+    const float* P_hi = Z_hi ? Z_hi + 2 * plane : nullptr;
+    const float* R_lo = Z_lo ? Z_lo + 4 * plane : nullptr;
+    const float* R_hi = Z_hi ? Z_hi + 4 * plane : nullptr;
+    float* const B0 = cl.map_shared_rank(sm, 0);
+    float* F1_0 = a.levels > 1 ? B0 + lv[1].F[0] : nullptr;   // the first block's level-1 rhs
+    float* F1_1 = a.levels > 1 ? B0 + lv[1].F[1] : nullptr;
+    const float* U1_0 = a.levels > 1 ? B0 + lv[1].U[0] : nullptr;
+    const float* U1_1 = a.levels > 1 ? B0 + lv[1].U[1] : nullptr;
 
     __shared__ ClusterSlots4<double> red64[2];
     __shared__ ClusterSlots<float> red32[2];
@@ -191,24 +229,22 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_mgc(const MgArgs a, int rows_
     for (int k = threadIdx.x; k < 6 * plane; k += blockDim.x) sm[k] = 0.f;
     if (rank == 0) {
         for (int l = 1; l < a.levels; ++l) {
-            const int P = lv[l].W * (lv[l].my + 2);
+            const SLv& v = lv[l];
+            const int P = v.W * (v.my + 2);
             const long long off = a.off[l] + (long long)sys * P;
             for (int k = threadIdx.x; k < P; k += blockDim.x) {
-                lv[l].D[k] = a.D[off + k];
-                lv[l].CX[k] = a.CX[off + k];
-                lv[l].CY[k] = a.CY[off + k];
-                lv[l].U[0][k] = lv[l].U[1][k] = 0.f;
-                lv[l].F[0][k] = lv[l].F[1][k] = 0.f;
+                sm[v.D + k] = a.D[off + k];
+                sm[v.CX + k] = a.CX[off + k];
+                sm[v.CY + k] = a.CY[off + k];
+                sm[v.U[0] + k] = sm[v.U[1] + k] = 0.f;
+                sm[v.F[0] + k] = sm[v.F[1] + k] = 0.f;
             }
         }
     }
 
     // this thread's unknowns: row lr of the band, padded column c
-    int lr_[UPT], c_[UPT], color_[UPT];
-    long long g_[UPT];
+    int lr_[UPT], c_[UPT];
     bool own[UPT];
-    float dg[UPT], cw[UPT], ce[UPT], cs[UPT], cn[UPT], dinv[UPT];
-    float r[2][UPT], q[2][UPT], d[2][UPT];
 #pragma unroll
     for (int k = 0; k < UPT; ++k) {
         const int u0 = threadIdx.x + k * SOLVE_THREADS;
@@ -216,10 +252,15 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_mgc(const MgArgs a, int rows_
         const int u = own[k] ? u0 : 0;
         lr_[k] = u / mx;
         c_[k] = u % mx + 1;
-        color_[k] = (r0 + lr_[k] + c_[k] - 1) & 1;
-        g_[k] = (long long)(S.j0 + r0 + lr_[k]) * nx + (S.i0 + c_[k] - 1);
+    }
+    // global index of unknown k (recomputed where needed rather than held in registers)
+    auto gidx = [&](int k) -> long long { return (long long)(S.j0 + r0 + lr_[k]) * nx + (S.i0 + c_[k] - 1); };
+    float dg[UPT], cw[UPT], ce[UPT], cs[UPT], cn[UPT], dinv[UPT];
+    float r[2][UPT], q[2][UPT], d[2][UPT];
+#pragma unroll
+    for (int k = 0; k < UPT; ++k) {
         if (own[k]) {
-            const long long g = g_[k];
+            const long long g = gidx(k);
             dg[k] = a.dgf[g];
             cw[k] = a.cxf[g - 1];
             ce[k] = a.cxf[g];
@@ -254,12 +295,34 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_mgc(const MgArgs a, int rows_
         for (int k = 0; k < UPT; ++k)
             if (own[k]) at(Zs, 0, k) = at(Zs, 1, k) = 0.f;
         cl.sync();
+        // The points of one colour read only the other's: a thread loads its
+        // points before it stores them (all of them with up to two per thread;
+        // with four, both fields of one point at a time, within the registers).
         auto half = [&](int color) {
+            if constexpr (UPT <= 2) {
+                float z0[UPT], z1[UPT];
 #pragma unroll
-            for (int k = 0; k < UPT; ++k)
-                if (own[k] && color_[k] == color)
+                for (int k = 0; k < UPT; ++k)
+                    if (own[k] && ((r0 + lr_[k] + c_[k] - 1) & 1) == color) {
+                        z0[k] = (r[0][k] + nb(Zs, Z_lo, Z_hi, 0, k)) * dinv[k];
+                        z1[k] = (r[1][k] + nb(Zs, Z_lo, Z_hi, 1, k)) * dinv[k];
+                    }
 #pragma unroll
-                    for (int f = 0; f < 2; ++f) at(Zs, f, k) = (r[f][k] + nb(Zs, Z_lo, Z_hi, f, k)) * dinv[k];
+                for (int k = 0; k < UPT; ++k)
+                    if (own[k] && ((r0 + lr_[k] + c_[k] - 1) & 1) == color) {
+                        at(Zs, 0, k) = z0[k];
+                        at(Zs, 1, k) = z1[k];
+                    }
+            } else {
+#pragma unroll
+                for (int k = 0; k < UPT; ++k)
+                    if (own[k] && ((r0 + lr_[k] + c_[k] - 1) & 1) == color) {
+                        const float z0 = (r[0][k] + nb(Zs, Z_lo, Z_hi, 0, k)) * dinv[k];
+                        const float z1 = (r[1][k] + nb(Zs, Z_lo, Z_hi, 1, k)) * dinv[k];
+                        at(Zs, 0, k) = z0;
+                        at(Zs, 1, k) = z1;
+                    }
+            }
             cl.sync();
         };
         for (int s = 0; s < a.nu; ++s) {
@@ -299,7 +362,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_mgc(const MgArgs a, int rows_
             cl.sync();
             if (rank == 0) {
                 const int P1 = c1.W * (c1.my + 2);
-                for (int k = threadIdx.x; k < P1; k += blockDim.x) c1.U[0][k] = c1.U[1][k] = 0.f;
+                for (int k = threadIdx.x; k < P1; k += blockDim.x) sm[c1.U[0] + k] = sm[c1.U[1] + k] = 0.f;
                 __syncthreads();
                 coarse_cycle(lv, a.levels, a.nu, a.coarse_sweeps);
             }
@@ -330,7 +393,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_mgc(const MgArgs a, int rows_
 #pragma unroll
         for (int k = 0; k < UPT; ++k) {
             if (!own[k]) continue;
-            const long long g = g_[k];
+            const long long g = gidx(k);
             const int i = S.i0 + c_[k] - 1, j = S.j0 + r0 + lr_[k];
 #pragma unroll
             for (int f = 0; f < 2; ++f) {
@@ -435,7 +498,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_mgc(const MgArgs a, int rows_
             if (own[k])
 #pragma unroll
                 for (int f = 0; f < 2; ++f)
-                    if (!conv[f]) a.x[f][g_[k]] += (double)d[f][k];
+                    if (!conv[f]) a.x[f][gidx(k)] += (double)d[f][k];
         cl.sync();
         residual64(rr[0], rr[1], bb[0], bb[1]);
         conv[0] = rr[0] <= stop2[0];
@@ -485,6 +548,11 @@ int mgc_config(const MgArgs& a, int* C_out, int* rows_max_out, size_t* smem_out,
     while (C < 16 && (((my + C - 1) / C) * mx > per_block)) C *= 2;
     const int rows_max = (my + C - 1) / C;
     if (rows_max * mx > per_block || C > my) return 0;
+    // the coarse levels' index quotients are exact in single precision (qdiv) below this size
+    for (int l = 1; l < a.levels; ++l) {
+        const long long Wl = a.mx[l] + 2;
+        if (Wl * Wl * (a.my[l] + 2) >= (1LL << 21)) return 0;
+    }
     size_t floats = 6 * (size_t)rows_max * (mx + 2);
     for (int l = 1; l < a.levels; ++l) floats += 7 * (size_t)(a.mx[l] + 2) * (a.my[l] + 2);
     const size_t smem = floats * sizeof(float);
