@@ -1828,6 +1828,9 @@ static sdd_status capture_step(sdd_ctx* c, const sdd_step_params* p, int K, int 
             rec_ext(c->pev[3], q);
         }
         if (st == SDD_OK) st = prepare_parts(c, q, false, true);
+        // with the plain test the path kernel reads no face data (its exits are scored later):
+        // the face data join the main branch here, before the scoring
+        if (!c->user_faces && p->exit_mode == 0) cu(cudaStreamWaitEvent(q, c->fev[1], 0));
         cu(cudaEventRecord(c->pev[1], q));
         join = c->pev[1];
         if (st == SDD_OK) st = enqueue_solve_system(c, c->step_call[parity], q);
@@ -1840,7 +1843,7 @@ static sdd_status capture_step(sdd_ctx* c, const sdd_step_params* p, int K, int 
     if (st == SDD_OK && c->pipe) {
         // the drift records; the face data come from the third branch forked above
         cu(launch_prep_cells(c->w.p, nullptr, nullptr, c->nx, c->ny, c->bcoef.p, nullptr, c->d_status.p, s));
-        if (!c->user_faces) cu(cudaStreamWaitEvent(s, c->fev[1], 0));
+        if (!c->user_faces && p->exit_mode != 0) cu(cudaStreamWaitEvent(s, c->fev[1], 0));
         c->dirty_w = false;
     } else if (st == SDD_OK) {
         st = prepare(c, s);

@@ -102,27 +102,37 @@ __device__ __forceinline__ bool inside2(float2 p)
     return fminf(q.x, q.y) > 0.0f;
 }
 
-// Linear interpolation of face `face` of `field` at tangential coordinate s.
-__device__ __forceinline__ float face_value(const InstDev& I, int field, int face, float s)
+// Face `face` at tangential coordinate s: the offset of its table (field 0;
+// field 1 follows 2 ny + 2 nx entries later), the interval k and the fraction f.
+__device__ __forceinline__ void face_interval(const InstDev& I, int face, float s, long long& off, int& k, float& f)
 {
     const int n = (face < 2) ? I.ny : I.nx;
-    long long off = (long long)field * (2LL * I.ny + 2LL * I.nx);
+    off = 0;
     if (face >= 1) off += I.ny;
     if (face >= 2) off += I.ny;
     if (face >= 3) off += I.nx;
-    const float* v = I.faces32 + off;
     const float g = s * (float)(n - 1);
-    int k = (int)floorf(g);
+    k = (int)floorf(g);
     k = max(0, min(k, n - 2));
-    const float f = g - (float)k;
+    f = g - (float)k;
+}
+
+// Linear interpolation of face `face` of `field` at tangential coordinate s.
+__device__ __forceinline__ float face_value(const InstDev& I, int field, int face, float s)
+{
+    long long off;
+    int k;
+    float f;
+    face_interval(I, face, s, off, k, f);
+    const float* v = I.faces32 + off + (long long)field * (2LL * I.ny + 2LL * I.nx);
     return fmaf(f, v[k + 1] - v[k], v[k]);
 }
 
-// Exit through the boundary between X_j = (x, y) and X_{j+1} = (xn, yn):
+// The boundary crossing of the sub-step X_j = (x, y) -> X_{j+1} = (xn, yn):
 // the segment is cut at the smallest crossing fraction over the violated
-// faces, ties to the face listed first (left, right, bottom, top).
-__device__ __forceinline__ void plain_exit(const InstDev& I, float x, float y, float xn, float yn, int& face,
-                                        float& yxi, float& yeta, float& xe, float& ye)
+// faces, ties to the face listed first (left, right, bottom, top); t is the
+// tangential coordinate of the crossing on that face.
+__device__ __forceinline__ void exit_crossing(float x, float y, float xn, float yn, int& face, float& t)
 {
     float best = 2.0f;
     int f = -1;
@@ -131,13 +141,21 @@ __device__ __forceinline__ void plain_exit(const InstDev& I, float x, float y, f
     if (yn <= 0.0f) { const float s = y / (y - yn); if (s < best) { best = s; f = 2; } }
     if (yn >= 1.0f) { const float s = (1.0f - y) / (yn - y); if (s < best) { best = s; f = 3; } }
     if (f < 0) { f = 0; best = 0.0f; }  // only for a non-finite position
-    float t = (f < 2) ? fmaf(best, yn - y, y) : fmaf(best, xn - x, x);
-    t = fminf(fmaxf(t, 0.0f), 1.0f);
+    float tt = (f < 2) ? fmaf(best, yn - y, y) : fmaf(best, xn - x, x);
+    t = fminf(fmaxf(tt, 0.0f), 1.0f);
     face = f;
-    yxi = face_value(I, 0, f, t);
-    yeta = face_value(I, 1, f, t);
-    xe = (f == 0) ? 0.0f : (f == 1) ? 1.0f : t;
-    ye = (f == 2) ? 0.0f : (f == 3) ? 1.0f : t;
+}
+
+// Exit through the boundary between X_j and X_{j+1}: the boundary data at the crossing.
+__device__ __forceinline__ void plain_exit(const InstDev& I, float x, float y, float xn, float yn, int& face,
+                                        float& yxi, float& yeta, float& xe, float& ye)
+{
+    float t;
+    exit_crossing(x, y, xn, yn, face, t);
+    yxi = face_value(I, 0, face, t);
+    yeta = face_value(I, 1, face, t);
+    xe = (face == 0) ? 0.0f : (face == 1) ? 1.0f : t;
+    ye = (face == 2) ? 0.0f : (face == 3) ? 1.0f : t;
 }
 
 // Brownian-bridge test between two inside points: the half plane behind face
@@ -647,14 +665,15 @@ __global__ void __launch_bounds__(512, 2) k_paths_exp(const PathArgs a)
 // control-variate sums; the block's sums, in warp order, join the partial
 // sums of the node's first task in the node's reduction, which the block's
 // first warp then runs (the mean and standard error of every node, boundary
-// and masked nodes included).
-constexpr int SCORE_BATCH = 4;
+// and masked nodes included). The next batch's records are read while the
+// current batch's gathers are in flight.
+constexpr int SCORE_BATCH = 2;
 constexpr int SCORE_THREADS = 256;
 
 __device__ void finalize_node(const FinalArgs& a, int node, int lane, const double* add0);
 
 template <bool CV>
-__global__ void __launch_bounds__(SCORE_THREADS) k_score_surv(const ScoreArgs a)
+__global__ void __launch_bounds__(SCORE_THREADS, 4) k_score_surv(const ScoreArgs a)
 {
     __shared__ double red[SCORE_THREADS / 32][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -669,9 +688,8 @@ __global__ void __launch_bounds__(SCORE_THREADS) k_score_surv(const ScoreArgs a)
     const float x0 = nd.xf, y0 = nd.yf;
     const int end = nd.n_paths;
     Acc ax{0.f, 0.f, 0.f, 0.f}, ae{0.f, 0.f, 0.f, 0.f};
-    for (int p0 = threadIdx.x; p0 < end; p0 += SCORE_BATCH * SCORE_THREADS) {
-        float4 r[SCORE_BATCH];
-        float2 cvs[SCORE_BATCH];
+    // the records of the batch that starts at path p0 (past the end: the skip mark)
+    auto load_batch = [&](int p0, float4 (&r)[SCORE_BATCH], float2 (&cvs)[SCORE_BATCH]) {
 #pragma unroll
         for (int u = 0; u < SCORE_BATCH; ++u) {
             const int p = p0 + u * SCORE_THREADS;
@@ -687,16 +705,38 @@ __global__ void __launch_bounds__(SCORE_THREADS) k_score_surv(const ScoreArgs a)
                 }
             }
         }
+    };
+    float4 r[SCORE_BATCH];
+    float2 cvs[SCORE_BATCH];
+    load_batch(threadIdx.x, r, cvs);
+    for (int p0 = threadIdx.x; p0 < end; p0 += SCORE_BATCH * SCORE_THREADS) {
+        // one round of loads for the batch: a survivor gathers the field record at its
+        // end point, a plain exit the face data on both sides of its crossing
+        // (f0 = xi[k], xi[k + 1], eta[k], eta[k + 1]; st.x the fraction)
         float4 f0[SCORE_BATCH], f1[SCORE_BATCH];
         float2 st[SCORE_BATCH];
 #pragma unroll
         for (int u = 0; u < SCORE_BATCH; ++u) {
-            // survivors gather the field record at their end point; other records read cell 0 unused
-            const bool surv = r[u].x >= 0.f && isnan(r[u].z);
-            const Cell c = locate(I, I.fcoef, surv ? f2(r[u].x, r[u].y) : f2(0.f, 0.f));
-            load_cell(c.p, f0[u], f1[u]);
-            st[u] = c.st;
+            if (r[u].x >= 0.f && isnan(r[u].z)) {
+                const Cell c = locate(I, I.fcoef, f2(r[u].x, r[u].y));
+                load_cell(c.p, f0[u], f1[u]);
+                st[u] = c.st;
+            } else if (r[u].x >= 0.f) {
+                int face, k;
+                float t, f;
+                long long off;
+                exit_crossing(r[u].x, r[u].y, r[u].z, r[u].w, face, t);
+                face_interval(I, face, t, off, k, f);
+                const float* v0 = I.faces32 + off + k;
+                const float* v1 = v0 + (2LL * I.ny + 2LL * I.nx);
+                f0[u] = make_float4(v0[0], v0[1], v1[0], v1[1]);
+                st[u] = f2(f, 0.f);
+            }
         }
+        // the next batch's records while this batch's gathers are in flight
+        float4 rn[SCORE_BATCH];
+        float2 cn[SCORE_BATCH];
+        load_batch(p0 + SCORE_BATCH * SCORE_THREADS, rn, cn);
 #pragma unroll
         for (int u = 0; u < SCORE_BATCH; ++u) {
             if (r[u].x < 0.f) continue;   // scored in the path kernel, or past the end
@@ -706,13 +746,18 @@ __global__ void __launch_bounds__(SCORE_THREADS) k_score_surv(const ScoreArgs a)
                 yxi = v.x;
                 yeta = v.y;
             } else {
-                // left the domain in the sub-step (x0, y0) -> (x1, y1): the boundary data there
-                int face;
-                float xe, ye;
-                plain_exit(I, r[u].x, r[u].y, r[u].z, r[u].w, face, yxi, yeta, xe, ye);
+                // left the domain in the sub-step (x0, y0) -> (x1, y1): the boundary data there,
+                // as face_value interpolates it
+                yxi = fmaf(st[u].x, f0[u].y - f0[u].x, f0[u].x);
+                yeta = fmaf(st[u].x, f0[u].w - f0[u].z, f0[u].z);
             }
             ax.add(yxi - cvs[u].x - x0);
             ae.add(yeta - cvs[u].y - y0);
+        }
+#pragma unroll
+        for (int u = 0; u < SCORE_BATCH; ++u) {
+            r[u] = rn[u];
+            cvs[u] = cn[u];
         }
     }
     const double v[4] = {warp_sum(ax.sum()), warp_sum(ax.sumsq()), warp_sum(ae.sum()), warp_sum(ae.sumsq())};
