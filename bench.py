@@ -598,23 +598,42 @@ def run_ring41(args, world, rank, local):
     sdd.sdd_set_keypoints(ctx, args.key_spacing >= 0, max(args.key_spacing, 0))
     sdd.sdd_set_solver(ctx, {"auto": 0, "jacobi": 1, "mg": 2}[args.solver])
     sp = dict(dt=wl.dt, Dt=Dt, seed=rank, paths_per_node=wl.paths, rtol=1e-12, max_iter=20000)
-    # a step here is about 0.4 ms: warm up long enough for the clocks to settle
-    for k in range(max(args.warmup, 100)):
+    nodes = len(sdd.sdd_interface_nodes(ctx)[0])
+    # the statistics of every step land in buffers made once (no allocation inside the timed loop)
+    stats = {k: torch.empty(nodes, dtype=torch.float64, device="cuda") for k in ("mean_xi", "mean_eta", "se_xi", "se_eta")}
+    stats["n_exit"] = torch.empty(nodes, dtype=torch.int64, device="cuda")
+    stats["path_steps"] = torch.empty(nodes, dtype=torch.int64, device="cuda")
+    counts = torch.zeros(steps, dtype=torch.int64, device="cuda")
+
+    def one_step(k):
         sdd.sdd_set_w(ctx, w_all[k % steps])
         sdd.sdd_step(ctx, **sp)
+        sdd.sdd_last_interface_stats(ctx, out=stats)
+        torch.sum(stats["path_steps"], dim=0, out=counts[k % steps])
+
+    # a step here is about 0.3 ms of small kernels: warm up for at least a second (and W steps),
+    # so that the clocks have settled before the timed region
+    t0 = time.perf_counter()
+    k = 0
+    while k < args.warmup or time.perf_counter() - t0 < 1.0:
+        one_step(k)
+        k += 1
+        if k % 100 == 0:
+            torch.cuda.synchronize()
     sdd.sdd_set_fields(ctx, torch.from_numpy(xi0).cuda(), torch.from_numpy(eta0).cuda())
     sdd.sdd_set_step_index(ctx, 0)
+    counts.zero_()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    counts = torch.zeros(steps, dtype=torch.int64, device="cuda")
+    clocks = ClockSampler(local)
+    clocks.start()
     e0.record()
     for k in range(steps):
-        sdd.sdd_set_w(ctx, w_all[k])
-        sdd.sdd_step(ctx, **sp)
-        counts[k] = sdd.sdd_last_interface_stats(ctx)["path_steps"].sum()
+        one_step(k)
     e1.record()
     torch.cuda.synchronize()
+    clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     xi, eta = (a.cpu().numpy() for a in sdd.sdd_get_fields(ctx))
     p = np.stack([xi, eta], axis=-1)
@@ -624,7 +643,6 @@ def run_ring41(args, world, rank, local):
         e1_, e2_ = quad[k] - quad[k - 1], quad[(k + 1) % 4] - quad[k]
         folded |= (e1_[..., 0] * e2_[..., 1] - e1_[..., 1] * e2_[..., 0]) <= 0
     tot = int(counts.sum().item())
-    nodes = len(sdd.sdd_interface_nodes(ctx)[0])
     key_nodes = int(sdd.sdd_keypoint_mask(ctx).sum().item()) if args.key_spacing >= 0 else nodes
     if rank == 0:
         print(json.dumps({
@@ -638,6 +656,7 @@ def run_ring41(args, world, rank, local):
             "interface_nodes_per_s": nodes * steps / (ms / 1e3), "path_steps_per_step": tot / steps,
             "folded_cells_at_end": int(folded.sum()),
             "max_mesh_displacement": float(max(np.abs(xi - W.grid(n)[0]).max(), np.abs(eta - W.grid(n)[1]).max())),
+            "clocks": clk,
         }), flush=True)
 
 

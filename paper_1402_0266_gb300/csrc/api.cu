@@ -1862,8 +1862,9 @@ static sdd_status capture_step(sdd_ctx* c, const sdd_step_params* p, int K, int 
         st = run_plan(c, c->step_plan, p->dt, K, p->seed, 0, c->d_step.p, p->exit_mode, o, nullptr, s, c->ev[1],
                       c->ev[2], kmask, c->defer ? (void*)c->surv.p : nullptr, join);
     if (st == SDD_OK && kmask) {
-        cudaError_t e = launch_pchip(c->d_klines.p, (int)c->klines.size(), c->d_kpos_idx.p, c->d_kpos_cross.p, kmask,
-                                     c->faces64.p, c->nx, c->ny, o.mean_xi, o.mean_eta, c->d_kscratch.p, s);
+        cudaError_t e = launch_pchip(c->d_klines.p, (int)c->klines.size(), c->kmax_n, c->d_kpos_idx.p,
+                                     c->d_kpos_cross.p, kmask, c->faces64.p, c->nx, c->ny, o.mean_xi, o.mean_eta,
+                                     c->d_kscratch.p, s);
         if (e != cudaSuccess) st = fail(c, SDD_ECUDA, "interface fill: %s", cudaGetErrorString(e));
     }
     rec_ext(c->ev[3], s);

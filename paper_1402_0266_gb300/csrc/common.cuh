@@ -159,9 +159,9 @@ cudaError_t launch_keypoints(const float* w, int nx, const KeyLine* lines, int n
                              const int32_t* pos_idx, const uint8_t* pos_cross, int spacing, uint8_t* mask,
                              cudaStream_t s);
 size_t pchip_scratch_doubles(long long total_positions, int nlines);
-cudaError_t launch_pchip(const KeyLine* lines, int nlines, const int32_t* pos_idx, const uint8_t* pos_cross,
-                         const uint8_t* mask, const double* faces, int nx, int ny, double* mean_xi, double* mean_eta,
-                         double* scratch, cudaStream_t s);
+cudaError_t launch_pchip(const KeyLine* lines, int nlines, int max_n, const int32_t* pos_idx,
+                         const uint8_t* pos_cross, const uint8_t* mask, const double* faces, int nx, int ny,
+                         double* mean_xi, double* mean_eta, double* scratch, cudaStream_t s);
 
 // Learned control variate (mlp.cu).
 cudaError_t launch_node_features(const float* w, int nx, int ny, double* w64, double* r64, double2* gw, float4* nfa,

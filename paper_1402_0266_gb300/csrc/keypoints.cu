@@ -90,44 +90,31 @@ __global__ void __launch_bounds__(KP_THREADS) k_keypoints(const float* __restric
     }
 }
 
-// One block per line; thread f < 2 interpolates field f along the line.
-__global__ void k_pchip(const KeyLine* __restrict__ lines, const int32_t* __restrict__ pos_idx,
-                        const uint8_t* __restrict__ pos_cross, const uint8_t* __restrict__ mask,
-                        const double* __restrict__ faces, int nx, int ny, double* __restrict__ mean_xi,
-                        double* __restrict__ mean_eta, double* __restrict__ scratch)
+// PCHIP of one field along one line (the calling thread alone): anchors
+// (ax, ay) at the line's two ends and its key points, their derivatives ad,
+// then the positions the line owns that are not key points. key(t), val(t),
+// idx(t) and cross(t) describe interior position t = 1 .. n - 2.
+template <typename Key, typename Val, typename Idx, typename Cross, typename IT, typename DT>
+__device__ __forceinline__ void pchip_line(const KeyLine& L, double y_start, double y_end, Key key, Val val, Idx idx,
+                                           Cross cross, IT* ax, DT* ay, DT* ad, double* __restrict__ mean)
 {
-    const int f = threadIdx.x;
-    if (f >= 2) return;
-    const KeyLine L = lines[blockIdx.x];
     const int n = L.n;
-    double* mean = f == 0 ? mean_xi : mean_eta;
-    // face data: per field left[ny] right[ny] bottom[nx] top[nx]
-    const double* F = faces + (long long)f * (2LL * ny + 2LL * nx);
-    const double y_start = L.orient == 0 ? F[2 * ny + L.fixed] : F[L.fixed];
-    const double y_end = L.orient == 0 ? F[2 * ny + nx + L.fixed] : F[ny + L.fixed];
-    // anchors: (x, y) and their derivatives, in this line's scratch region (three arrays of n per field;
-    // the lines before this one hold L.start + 2 blockIdx.x positions in all)
-    double* ax = scratch + 6LL * (L.start + 2LL * blockIdx.x) + 3LL * f * n;
-    double* ay = ax + n;
-    double* ad = ay + n;
     int m = 0;
-    ax[m] = 0.0;
+    ax[m] = 0;
     ay[m++] = y_start;
-    for (int t = 1; t <= n - 2; ++t) {
-        const int k = L.start + t - 1;
-        if (mask[pos_idx[k]]) {
-            ax[m] = (double)t;
-            ay[m++] = mean[pos_idx[k]];
+    for (int t = 1; t <= n - 2; ++t)
+        if (key(t)) {
+            ax[m] = t;
+            ay[m++] = val(t);
         }
-    }
-    ax[m] = (double)(n - 1);
+    ax[m] = n - 1;
     ay[m++] = y_end;
     // derivatives (Fritsch-Butland weighted harmonic mean inside, shape-preserving three-point ends)
     if (m == 2) {
-        ad[0] = ad[1] = (ay[1] - ay[0]) / (ax[1] - ax[0]);
+        ad[0] = ad[1] = (ay[1] - ay[0]) / (double)(ax[1] - ax[0]);
     } else {
         for (int k = 1; k < m - 1; ++k) {
-            const double h0 = ax[k] - ax[k - 1], h1 = ax[k + 1] - ax[k];
+            const double h0 = (double)(ax[k] - ax[k - 1]), h1 = (double)(ax[k + 1] - ax[k]);
             const double s0 = (ay[k] - ay[k - 1]) / h0, s1 = (ay[k + 1] - ay[k]) / h1;
             if (s0 == 0.0 || s1 == 0.0 || (s0 > 0.0) != (s1 > 0.0)) {
                 ad[k] = 0.0;
@@ -139,8 +126,8 @@ __global__ void k_pchip(const KeyLine* __restrict__ lines, const int32_t* __rest
         for (int e = 0; e < 2; ++e) {
             // end derivative from the first (last) two intervals
             const int a = e == 0 ? 0 : m - 1, b = e == 0 ? 1 : m - 2, c = e == 0 ? 2 : m - 3;
-            const double h0 = fabs(ax[b] - ax[a]), h1 = fabs(ax[c] - ax[b]);
-            const double s0 = (ay[b] - ay[a]) / (ax[b] - ax[a]), s1 = (ay[c] - ay[b]) / (ax[c] - ax[b]);
+            const double h0 = fabs((double)(ax[b] - ax[a])), h1 = fabs((double)(ax[c] - ax[b]));
+            const double s0 = (ay[b] - ay[a]) / (double)(ax[b] - ax[a]), s1 = (ay[c] - ay[b]) / (double)(ax[c] - ax[b]);
             double d = ((2.0 * h0 + h1) * s0 - h0 * s1) / (h0 + h1);
             const auto sgn = [](double v) { return (v > 0.0) - (v < 0.0); };
             if (sgn(d) != sgn(s0)) d = 0.0;
@@ -151,18 +138,99 @@ __global__ void k_pchip(const KeyLine* __restrict__ lines, const int32_t* __rest
     // evaluate at the positions this line owns that are not key points
     int seg = 0;
     for (int t = 1; t <= n - 2; ++t) {
-        const int k = L.start + t - 1;
-        const int idx = pos_idx[k];
-        if (mask[idx] || (L.orient == 1 && pos_cross[k])) continue;
+        if (key(t) || (L.orient == 1 && cross(t))) continue;
         const double x = (double)t;
-        while (seg < m - 2 && ax[seg + 1] < x) ++seg;
-        const double h = ax[seg + 1] - ax[seg];
+        while (seg < m - 2 && (double)ax[seg + 1] < x) ++seg;
+        const double h = (double)(ax[seg + 1] - ax[seg]);
         const double s = (ay[seg + 1] - ay[seg]) / h;
         const double c3 = (ad[seg] + ad[seg + 1] - 2.0 * s) / (h * h);
         const double c2 = (s - ad[seg]) / h - (ad[seg] + ad[seg + 1] - 2.0 * s) / h;
-        const double u = x - ax[seg];
-        mean[idx] = ((c3 * u + c2) * u + ad[seg]) * u + ay[seg];
+        const double u = x - (double)ax[seg];
+        mean[idx(t)] = ((c3 * u + c2) * u + ad[seg]) * u + ay[seg];
     }
+}
+
+// The boundary values of field f at the two ends of line L.
+__device__ __forceinline__ void line_ends(const KeyLine& L, const double* faces, int f, int nx, int ny, double& y0,
+                                          double& y1)
+{
+    // face data: per field left[ny] right[ny] bottom[nx] top[nx]
+    const double* F = faces + (long long)f * (2LL * ny + 2LL * nx);
+    y0 = L.orient == 0 ? F[2 * ny + L.fixed] : F[L.fixed];
+    y1 = L.orient == 0 ? F[2 * ny + nx + L.fixed] : F[ny + L.fixed];
+}
+
+constexpr int PCHIP_THREADS = 64;
+
+// Shared-memory bytes of k_pchip_smem for lines of up to n positions.
+size_t pchip_smem_bytes(int n) { return (size_t)n * (6 * sizeof(double) + 3 * sizeof(int32_t) + 1); }
+
+// One block per line: the block stages the line's node indices, key and
+// crossing flags and key-point estimates in shared memory (in parallel), then
+// thread f < 2 interpolates field f there.
+__global__ void __launch_bounds__(PCHIP_THREADS) k_pchip_smem(const KeyLine* __restrict__ lines,
+                                                              const int32_t* __restrict__ pos_idx,
+                                                              const uint8_t* __restrict__ pos_cross,
+                                                              const uint8_t* __restrict__ mask,
+                                                              const double* __restrict__ faces, int nx, int ny,
+                                                              double* __restrict__ mean_xi,
+                                                              double* __restrict__ mean_eta, int max_n)
+{
+    extern __shared__ double sp[];
+    const KeyLine L = lines[blockIdx.x];
+    const int n = L.n;
+    double* val = sp;                                   // [2][max_n] key-point estimates
+    double* ay = sp + 2LL * max_n;                      // [2][max_n]
+    double* ad = sp + 4LL * max_n;                      // [2][max_n]
+    int32_t* ax = reinterpret_cast<int32_t*>(sp + 6LL * max_n);   // [2][max_n]
+    int32_t* idx = ax + 2LL * max_n;                    // [max_n]
+    uint8_t* flag = reinterpret_cast<uint8_t*>(idx + max_n);     // [max_n]: bit 0 key, bit 1 crossing
+    for (int t = 1 + threadIdx.x; t <= n - 2; t += blockDim.x) {
+        const int k = L.start + t - 1;
+        const int i = pos_idx[k];
+        const uint8_t key = mask[i];
+        idx[t] = i;
+        flag[t] = (uint8_t)((key ? 1 : 0) | (pos_cross[k] ? 2 : 0));
+        if (key) {
+            val[t] = mean_xi[i];
+            val[max_n + t] = mean_eta[i];
+        }
+    }
+    __syncthreads();
+    const int f = threadIdx.x;
+    if (f >= 2) return;
+    double y0, y1;
+    line_ends(L, faces, f, nx, ny, y0, y1);
+    const double* v = val + (long long)f * max_n;
+    pchip_line(
+        L, y0, y1, [&](int t) { return (flag[t] & 1) != 0; }, [&](int t) { return v[t]; },
+        [&](int t) { return idx[t]; }, [&](int t) { return (flag[t] & 2) != 0; }, ax + (long long)f * max_n,
+        ay + (long long)f * max_n, ad + (long long)f * max_n, f == 0 ? mean_xi : mean_eta);
+}
+
+// Lines too long for shared memory: one block per line, thread f < 2
+// interpolates field f with its anchors in global scratch.
+__global__ void k_pchip(const KeyLine* __restrict__ lines, const int32_t* __restrict__ pos_idx,
+                        const uint8_t* __restrict__ pos_cross, const uint8_t* __restrict__ mask,
+                        const double* __restrict__ faces, int nx, int ny, double* __restrict__ mean_xi,
+                        double* __restrict__ mean_eta, double* __restrict__ scratch)
+{
+    const int f = threadIdx.x;
+    if (f >= 2) return;
+    const KeyLine L = lines[blockIdx.x];
+    const int n = L.n;
+    double* mean = f == 0 ? mean_xi : mean_eta;
+    double y0, y1;
+    line_ends(L, faces, f, nx, ny, y0, y1);
+    // anchors: (x, y) and their derivatives, in this line's scratch region (three arrays of n per field;
+    // the lines before this one hold L.start + 2 blockIdx.x positions in all)
+    double* ax = scratch + 6LL * (L.start + 2LL * blockIdx.x) + 3LL * f * n;
+    double* ay = ax + n;
+    double* ad = ay + n;
+    pchip_line(
+        L, y0, y1, [&](int t) { return mask[pos_idx[L.start + t - 1]] != 0; },
+        [&](int t) { return mean[pos_idx[L.start + t - 1]]; }, [&](int t) { return pos_idx[L.start + t - 1]; },
+        [&](int t) { return pos_cross[L.start + t - 1] != 0; }, ax, ay, ad, mean);
 }
 
 }  // namespace
@@ -186,12 +254,20 @@ size_t pchip_scratch_doubles(long long total_positions, int nlines)
     return (size_t)(6 * (total_positions + 2LL * nlines) + 16);
 }
 
-cudaError_t launch_pchip(const KeyLine* lines, int nlines, const int32_t* pos_idx, const uint8_t* pos_cross,
-                         const uint8_t* mask, const double* faces, int nx, int ny, double* mean_xi, double* mean_eta,
-                         double* scratch, cudaStream_t s)
+cudaError_t launch_pchip(const KeyLine* lines, int nlines, int max_n, const int32_t* pos_idx,
+                         const uint8_t* pos_cross, const uint8_t* mask, const double* faces, int nx, int ny,
+                         double* mean_xi, double* mean_eta, double* scratch, cudaStream_t s)
 {
     if (nlines <= 0) return cudaSuccess;
-    k_pchip<<<nlines, 32, 0, s>>>(lines, pos_idx, pos_cross, mask, faces, nx, ny, mean_xi, mean_eta, scratch);
+    const size_t smem = pchip_smem_bytes(max_n);
+    if (smem <= 200 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_pchip_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_pchip_smem<<<nlines, PCHIP_THREADS, smem, s>>>(lines, pos_idx, pos_cross, mask, faces, nx, ny, mean_xi,
+                                                         mean_eta, max_n);
+    } else {
+        k_pchip<<<nlines, 32, 0, s>>>(lines, pos_idx, pos_cross, mask, faces, nx, ny, mean_xi, mean_eta, scratch);
+    }
     return cudaGetLastError();
 }
 

@@ -660,20 +660,21 @@ __global__ void __launch_bounds__(512, 2) k_paths_exp(const PathArgs a)
 // start are final (the estimate of the next mesh step runs beside the
 // subdomain solve that produces them). One block per node: the node's paths
 // end in one neighbourhood, so its gathers share L1; thread k takes paths k,
-// k + 256, ... SCORE_BATCH at a time (records, then gathers, in flight
+// k + T, ... SCORE_BATCH at a time (records, then gathers, in flight
 // together) and sums xi and eta at the end points minus the paths'
 // control-variate sums; the block's sums, in warp order, join the partial
 // sums of the node's first task in the node's reduction, which the block's
 // first warp then runs (the mean and standard error of every node, boundary
 // and masked nodes included). The next batch's records are read while the
-// current batch's gathers are in flight.
+// current batch's gathers are in flight. T = 256 threads at 64 registers puts
+// four blocks on an SM (many nodes: one wave for up to four per SM); with no
+// more nodes than SMs, T = 1024 gives each node's paths four times the threads.
 constexpr int SCORE_BATCH = 2;
-constexpr int SCORE_THREADS = 256;
 
 __device__ void finalize_node(const FinalArgs& a, int node, int lane, const double* add0);
 
-template <bool CV>
-__global__ void __launch_bounds__(SCORE_THREADS, 4) k_score_surv(const ScoreArgs a)
+template <bool CV, int SCORE_THREADS>
+__global__ void __launch_bounds__(SCORE_THREADS, 1024 / SCORE_THREADS) k_score_surv(const ScoreArgs a)
 {
     __shared__ double red[SCORE_THREADS / 32][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -991,8 +992,16 @@ cudaError_t launch_paths(const PathArgs& a, int exit_mode, bool record, int grid
 cudaError_t launch_score_surv(const ScoreArgs& a, bool cv, cudaStream_t s)
 {
     if (a.nnodes <= 0) return cudaSuccess;
-    if (cv) k_score_surv<true><<<a.nnodes, SCORE_THREADS, 0, s>>>(a);
-    else k_score_surv<false><<<a.nnodes, SCORE_THREADS, 0, s>>>(a);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (a.nnodes <= sms) {
+        if (cv) k_score_surv<true, 1024><<<a.nnodes, 1024, 0, s>>>(a);
+        else k_score_surv<false, 1024><<<a.nnodes, 1024, 0, s>>>(a);
+    } else {
+        if (cv) k_score_surv<true, 256><<<a.nnodes, 256, 0, s>>>(a);
+        else k_score_surv<false, 256><<<a.nnodes, 256, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
