@@ -88,3 +88,25 @@ def test_keypoint_steps_match_oracle(sdd, kp, oracle_mod):
         iface_gap = max(np.abs(g["mean_xi"] - o["mean_xi"]).max(), np.abs(g["mean_eta"] - o["mean_eta"]).max())
         assert max(np.abs(gx - new[0]).max(), np.abs(ge - new[1]).max()) <= iface_gap + 1e-9
         state = [gx, ge]
+
+
+def test_fill_on_lines_too_long_for_shared_memory(sdd, kp, oracle_mod):
+    """Lines of 3401 positions: the fill's staging (61 bytes a position) exceeds the
+    shared memory it may take, so the fill runs with its anchors in global scratch;
+    it must still be scipy's PCHIP through the GPU's own key values."""
+    import torch
+    n, sub = 3401, 2
+    w = W.w_paper_ring(n, 0.0)
+    ctx = _ctx(sdd, w, *W.identity_fields(n), sub)
+    sdd.sdd_set_keypoints(ctx, True, 8)
+    sdd.sdd_set_w(ctx, torch.from_numpy(w).cuda())
+    sdd.sdd_step(ctx, dt=5e-5, Dt=1e-3, seed=2, paths_per_node=200)
+    sdd.sdd_sync(ctx)
+    g = {k: v.cpu().numpy() for k, v in sdd.sdd_last_interface_stats(ctx).items()}
+    m = sdd.sdd_keypoint_mask(ctx).cpu().numpy().astype(bool)
+    assert 0 < m.sum() < m.size
+    np.testing.assert_array_equal(g["path_steps"] > 0, m)
+    faces = oracle_mod.winslow_faces(w.astype(np.float64))
+    fx, fe = kp.pchip_fill(g["mean_xi"], g["mean_eta"], m, faces, n, n, sub, sub)
+    np.testing.assert_allclose(g["mean_xi"], fx, rtol=0, atol=1e-10)
+    np.testing.assert_allclose(g["mean_eta"], fe, rtol=0, atol=1e-10)
