@@ -57,7 +57,7 @@ def parse():
                     default="front257")
     ap.add_argument("--key-spacing", type=int, default=8,
                     help="ring41: key points plus every k-th node (k > 0), key points only (0), every node (-1)")
-    ap.add_argument("--solver", choices=["auto", "jacobi", "mg"], default="auto",
+    ap.add_argument("--solver", choices=["auto", "jacobi", "mg", "direct"], default="auto",
                     help="subdomain solver of the mesh steps")
     ap.add_argument("--cv", choices=["off", "fields", "model"], default="off",
                     help="ring2049: control variate of the timed mesh steps")
@@ -251,7 +251,7 @@ def run_ours(args, world, rank, local):
     nsteps = max(K, Wm)
     w_all = torch.from_numpy(np.stack([W.w_front(n, k * WL.Dt) for k in range(nsteps)])).to(dev)
     ctx = sdd.sdd_init(n, n, WL.sub, WL.sub, w=w_all[0], xi0=xi0_d, eta0=eta0_d)
-    sdd.sdd_set_solver(ctx, {"auto": 0, "jacobi": 1, "mg": 2}[args.solver])
+    sdd.sdd_set_solver(ctx, {"auto": 0, "jacobi": 1, "mg": 2, "direct": 3}[args.solver])
     sdd.sdd_set_pipeline(ctx, not args.no_pipeline)
     sp = dict(dt=WL.dt, Dt=WL.Dt, seed=seed, paths_per_node=args.paths, exit_mode=0, rtol=1e-12, max_iter=20000,
               tune=1)
@@ -296,7 +296,7 @@ def run_ours(args, world, rank, local):
     barrier(world)
     clk = clocks.stop()
     pipelined = sdd.sdd_pipeline_in_use(ctx)
-    solver_name = {1: "Jacobi-PCG", 2: "multigrid-PCG"}.get(sdd.sdd_solver_in_use(ctx), "PCG")
+    solver_name = {1: "Jacobi-PCG", 2: "multigrid-PCG", 3: "direct (banded Cholesky)"}.get(sdd.sdd_solver_in_use(ctx), "PCG")
     sdd.sdd_sync(ctx)
     step_ms = [ev0[k].elapsed_time(ev1[k]) for k in range(K)]
     total_ms = sum(step_ms)
@@ -596,7 +596,7 @@ def run_ring41(args, world, rank, local):
                        eta0=torch.from_numpy(eta0).cuda())
     # the paper's setup: estimates at the key points (and every 8th node of a line), PCHIP elsewhere
     sdd.sdd_set_keypoints(ctx, args.key_spacing >= 0, max(args.key_spacing, 0))
-    sdd.sdd_set_solver(ctx, {"auto": 0, "jacobi": 1, "mg": 2}[args.solver])
+    sdd.sdd_set_solver(ctx, {"auto": 0, "jacobi": 1, "mg": 2, "direct": 3}[args.solver])
     sp = dict(dt=wl.dt, Dt=Dt, seed=rank, paths_per_node=wl.paths, rtol=1e-12, max_iter=20000)
     nodes = len(sdd.sdd_interface_nodes(ctx)[0])
     # the statistics of every step land in buffers made once (no allocation inside the timed loop)
@@ -731,7 +731,7 @@ def run_ring2049(args, world, rank, local):
     n = wl.n
     paths = args.paths or wl.paths
     ctx = sdd.sdd_init(n, n, wl.sub, wl.sub, w=torch.from_numpy(W.w_ring(n, 0.0)).cuda())
-    sdd.sdd_set_solver(ctx, {"auto": 0, "jacobi": 1, "mg": 2}[args.solver])
+    sdd.sdd_set_solver(ctx, {"auto": 0, "jacobi": 1, "mg": 2, "direct": 3}[args.solver])
     sp = dict(dt=wl.dt, Dt=wl.Dt, seed=rank, paths_per_node=paths, exit_mode=0, rtol=1e-12, max_iter=40000, tune=1)
     train = None
     mode = {"off": sdd.SDD_CV_OFF, "fields": sdd.SDD_CV_FIELDS, "model": sdd.SDD_CV_MODEL}[args.cv]

@@ -411,8 +411,15 @@ sdd_status sdd_set_keypoints(sdd_ctx* ctx, int32_t on, int32_t spacing);
 sdd_status sdd_keypoint_mask(sdd_ctx* ctx, uint8_t* mask);
 
 /* The solver of the subdomain systems (sdd_subdomain_solve and sdd_step).
- * The paper uses LU (Sec. 4); both GPU solvers are conjugate gradients on the
- * same symmetric system, refined in double precision to rtol:
+ * The paper uses LU (Sec. 4); the GPU solves the same symmetric system either
+ * directly or by conjugate gradients refined in double precision to rtol:
+ *   SDD_SOLVER_DIRECT  a banded L D L^T factorisation per subdomain (one block,
+ *                      single precision) inside an iterative refinement in
+ *                      double precision to rtol (available when every
+ *                      subdomain has at most 32 columns and its band fits
+ *                      200 KB of shared memory, e.g. 31 x 31; else
+ *                      SDD_EINVAL; status bit when rtol is missed); slower than
+ *                      Jacobi-PCG on these sizes, so never chosen automatically;
  *   SDD_SOLVER_JACOBI  Jacobi preconditioner; one thread-block cluster per
  *                      subdomain, register-resident when the subdomain fits;
  *   SDD_SOLVER_MG      a geometric multigrid V-cycle as preconditioner
@@ -421,16 +428,17 @@ sdd_status sdd_keypoint_mask(sdd_ctx* ctx, uint8_t* mask);
  *                      most 64 unknowns; else SDD_EINVAL);
  *   SDD_SOLVER_AUTO    multigrid where it is available and the subdomains are
  *                      too large for the register-resident Jacobi kernel or
- *                      hold at least 10,000 unknowns.
+ *                      hold at least 10,000 unknowns; else Jacobi.
  * With multigrid, max_iter caps the inner iterations: inside sdd_step's graph
  * the refinement sweeps and inner iterations are graph while-loops that stop
  * once every field has converged (at most 30 inner iterations per sweep and
  * 8 sweeps, within max_iter); a direct sdd_subdomain_solve runs a fixed 5 x 6.
  * sdd_solver_in_use returns the solver the next solve will use (1 Jacobi,
- * 2 multigrid). */
+ * 2 multigrid, 3 direct). */
 #define SDD_SOLVER_AUTO 0
 #define SDD_SOLVER_JACOBI 1
 #define SDD_SOLVER_MG 2
+#define SDD_SOLVER_DIRECT 3
 sdd_status sdd_set_solver(sdd_ctx* ctx, int32_t solver);
 int32_t sdd_solver_in_use(const sdd_ctx* ctx);
 

@@ -40,7 +40,7 @@ EXPORTS = [
     "sdd_set_solver", "sdd_solver_in_use", "sdd_set_keypoints", "sdd_keypoint_mask",
 ]
 
-SDD_SOLVER_AUTO, SDD_SOLVER_JACOBI, SDD_SOLVER_MG = range(3)
+SDD_SOLVER_AUTO, SDD_SOLVER_JACOBI, SDD_SOLVER_MG, SDD_SOLVER_DIRECT = range(4)
 
 SDD_CV_OFF, SDD_CV_TABLE, SDD_CV_MODEL, SDD_CV_FIELDS = range(4)
 

@@ -101,12 +101,12 @@ def test_multigrid_mesh_steps_match_oracle(sdd, oracle_mod):
 
 def test_multigrid_availability(sdd):
     # unequal subdomains (40 nodes in two halves) or even sizes do not coarsen
-    for n, sub in ((40, 2), (34, 1)):
+    for n, sub, auto in ((40, 2, 1), (34, 1, 1)):
         ctx = _ctx(sdd, np.ones((n, n)), *W.identity_fields(n), sub)
         with pytest.raises(sdd.SddError) as e:
             sdd.sdd_set_solver(ctx, sdd.SDD_SOLVER_MG)
         assert e.value.status == sdd.SDD_EINVAL
-        assert sdd.sdd_solver_in_use(ctx) == 1
+        assert sdd.sdd_solver_in_use(ctx) == auto
     # automatic: multigrid where the register-resident Jacobi kernel does not fit
     ctx = _ctx(sdd, np.ones((513, 513)), *W.identity_fields(513), 2)
     assert sdd.sdd_solver_in_use(ctx) == 2

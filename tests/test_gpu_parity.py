@@ -255,6 +255,7 @@ def test_solver_nonconvergence_is_a_status(sdd):
     import torch
     n = 33
     ctx = _ctx(sdd, W.w_smooth_random(n, 1), *W.identity_fields(n))
+    sdd.sdd_set_solver(ctx, sdd.SDD_SOLVER_JACOBI)
     x, y = sdd.sdd_interface_nodes(ctx)
     v = torch.from_numpy(x + 0.01).cuda()
     with pytest.raises(sdd.SddError) as e:
