@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/sdd.h"
+#include "chol.cuh"
 #include "common.cuh"
 
 using namespace sdd;

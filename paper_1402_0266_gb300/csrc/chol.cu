@@ -28,7 +28,7 @@
 // D(k - d); then 1 / D(k); per field the right-hand side b, the solution x
 // (double precision) and the correction (single precision); the (p, q) pairs
 // of the trailing update's triangle.
-#include "common.cuh"
+#include "chol.cuh"
 
 namespace sdd {
 namespace {

@@ -218,12 +218,6 @@ struct SolveArgs {
     int* status;
 };
 
-// Direct subdomain solves (chol.cu): whether an mx x my subdomain fits, and the launch
-// (one block per system of a.sys, both fields; a.iters 1 per system, max_iter + 1 and the
-// status bit when the residual misses rtol).
-bool chol_fits(int mx, int my);
-cudaError_t launch_chol(const SolveArgs& a, int mx_max, int my_max, cudaStream_t s);
-
 // Multigrid-preconditioned solves (mg.cu): every subdomain a system of the same
 // mx x my unknowns, both fields together.
 constexpr int kMgMaxLevels = 10;
