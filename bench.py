@@ -36,8 +36,9 @@ import workloads as W  # noqa: E402
 METRIC = "path-steps/s (interface Monte Carlo, whole mesh steps)"
 UNIT = "path-steps/s"
 WL = W.FRONT257
-# Algorithmic lane operations per path-step of the path kernel (see the design doc,
-# "Roofline"): half a Philox4x32-10 block (20), one Box-Muller pair (12), cell
+# Algorithmic lane operations per path-step of the path kernel, counted per
+# coordinate: half a Philox4x32-10 block (10 rounds x 2 wide multiplies + 2
+# three-input xors, over two sub-steps: 20), one Box-Muller pair (12), cell
 # location (12), bilinear drift (6), Euler-Maruyama update (4), exit test (4).
 ALG_OPS_PER_PATH_STEP = 58
 SM_LANES_PER_CLK = 128       # 4 schedulers x 32 lanes issue per SM per clock

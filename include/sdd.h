@@ -418,7 +418,9 @@ sdd_status sdd_keypoint_mask(sdd_ctx* ctx, uint8_t* mask);
  *                      double precision to rtol (available when every
  *                      subdomain has at most 32 columns and its band fits
  *                      200 KB of shared memory, e.g. 31 x 31; else
- *                      SDD_EINVAL; status bit when rtol is missed); slower than
+ *                      SDD_EINVAL; status bit when rtol is missed, and
+ *                      after a pivot that is not positive the subdomain's
+ *                      fields keep their previous values); slower than
  *                      Jacobi-PCG on these sizes, so never chosen automatically;
  *   SDD_SOLVER_JACOBI  Jacobi preconditioner; one thread-block cluster per
  *                      subdomain, register-resident when the subdomain fits;
@@ -595,9 +597,15 @@ typedef struct {
  * can overlap on the GPU (different streams or host threads) race and must
  * not be made; one call at a time per process. Results equal those of
  * sdd_interface_mc for the same inputs, parameters and paths_per_task.
- * Work is enqueued on `stream`. */
+ * Work is enqueued on `stream`.
+ * Device errors: `status_out` (DEVICE, one int32, caller-owned) receives the
+ * call's device status word once the call's work has run on `stream` (0 when
+ * none; bit 0 set when w is not finite and positive somewhere, and then the
+ * outputs are meaningless); the caller reads it after its own stream sync.
+ * With status_out = NULL the call instead waits for `stream` and returns
+ * SDD_EDEVICE when the word is nonzero. */
 sdd_status sdd_interface_mc_static(const sdd_fields* f, const sdd_nodes* nodes, const sdd_mc_params* p,
-                                   sdd_node_stats* out, void* stream);
+                                   sdd_node_stats* out, int32_t* status_out, void* stream);
 
 /* Size in bytes of the static array used by sdd_interface_mc_static. */
 int64_t sdd_static_scratch_bytes(void);

@@ -159,7 +159,7 @@ def lib():
                 "sdd_destroy": [vp],
                 "sdd_rng_draw": [u64, vp, i64, vp, vp, vp],
                 "sdd_interface_mc_static": [ctypes.POINTER(_Fields), ctypes.POINTER(_Nodes), ctypes.POINTER(_McParams),
-                                            ctypes.POINTER(_Stats), vp],
+                                            ctypes.POINTER(_Stats), vp, vp],
                 "sdd_static_scratch_bytes": [],
                 "sdd_batch_create": [ctypes.POINTER(vp), ctypes.POINTER(vp), i32, vp],
                 "sdd_batch_interface_mc": [vp, ctypes.POINTER(_Nodes), ctypes.POINTER(_McParams),
@@ -478,11 +478,14 @@ def sdd_rng_draw(seed, counters, stream=None):
 
 
 def sdd_interface_mc_static(w, xi, eta, x, y, n_paths, dt, Dt, seed=0, step_index=0, exit_mode=0, block_threads=0,
-                            paths_per_task=0, faces=None, out=None, stream=None):
+                            paths_per_task=0, faces=None, out=None, stream=None, status=None):
     """The interface estimate without any allocation in the library (see include/sdd.h).
 
     w (float32), xi, eta (float64): cuda tensors of shape (ny, nx); x, y, n_paths: host arrays.
     `out`: optional dict of preallocated cuda tensors as returned by sdd_interface_mc.
+    `status`: optional one-element int32 cuda tensor that receives the call's device status
+    word on the stream (read it after synchronising); without it the call waits for the
+    stream and raises SddError(SDD_EDEVICE) on a device error.
     """
     torch = _torch()
     ny, nx = w.shape
@@ -498,11 +501,15 @@ def sdd_interface_mc_static(w, xi, eta, x, y, n_paths, dt, Dt, seed=0, step_inde
     else:
         s = _Stats(*(out[k].data_ptr() for k in ("mean_xi", "mean_eta", "se_xi", "se_eta", "n_exit", "path_steps")))
     p = mc_params(dt, Dt, seed, step_index, exit_mode, block_threads, paths_per_task)
+    if status is not None:
+        _check_dev(status, torch.int32, (1,), "status")
     st = lib().sdd_interface_mc_static(ctypes.byref(f), ctypes.byref(nodes), ctypes.byref(p), ctypes.byref(s),
-                                       _stream(stream))
+                                       status.data_ptr() if status is not None else None, _stream(stream))
     del keep
     if st != SDD_OK:
-        raise SddError(st, "sdd_interface_mc_static rejected its arguments" if st == SDD_EINVAL else "CUDA error")
+        msg = {SDD_EINVAL: "sdd_interface_mc_static rejected its arguments",
+               SDD_EDEVICE: "device error (w not finite and positive)"}.get(st, "CUDA error")
+        raise SddError(st, msg)
     return out
 
 

@@ -174,8 +174,9 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_chol(const SolveArgs a)
         if (done) break;   // uniform over the block
     }
 
-    // the solutions into the fields
-    for (int k = tid; k < m; k += CHOL_THREADS) {
+    // the solutions into the fields; after a pivot that is not positive (or not a number) the
+    // fields keep their previous values and only the status reports the failure
+    for (int k = tid; k < m && !bad; k += CHOL_THREADS) {
         const long long g = gidx(k);
         a.x[0][g] = xv[k];
         a.x[1][g] = xv[(size_t)m + k];

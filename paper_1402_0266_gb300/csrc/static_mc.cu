@@ -16,9 +16,14 @@
 // device looks the address up with cudaGetSymbolAddress (with that device
 // current) and keeps it; make that first call before any stream capture.
 // Every call shares the array and it keeps the previous call's contents: the
-// work counter is cleared on every call, everything else is rewritten before
-// it is read. Calls whose work overlaps on the GPU (other streams, other host
-// threads) race on the array and must not be issued.
+// work counter and the status word are cleared on every call, everything else
+// is rewritten before it is read. Calls whose work overlaps on the GPU (other
+// streams, other host threads) race on the array and must not be issued.
+//
+// Device-side errors (a w that is not finite and positive) set the status word
+// in the array; the call hands it to the caller: copied into the caller's
+// device word at the end of the call's work, or, without one, read back after
+// waiting for the stream and returned as SDD_EDEVICE.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -63,6 +68,7 @@ int g_sm_count[kMaxDevices] = {};
 NodeDev g_nodes_host[kStaticMaxNodes];
 Task g_tasks_host[kStaticMaxTasks];
 InstDev g_inst_host;
+int g_status_host;
 
 // Address of this device's array, looked up once per device.
 cudaError_t static_scratch(unsigned char** out, int* sm_count)
@@ -95,7 +101,7 @@ extern "C" {
 int64_t sdd_static_scratch_bytes(void) { return (int64_t)kStaticScratchBytes; }
 
 sdd_status sdd_interface_mc_static(const sdd_fields* f, const sdd_nodes* nodes, const sdd_mc_params* p,
-                                   sdd_node_stats* out, void* stream)
+                                   sdd_node_stats* out, int32_t* status_out, void* stream)
 {
     if (!f || !nodes || !p || !out) return SDD_EINVAL;
     const int nx = f->nx, ny = f->ny;
@@ -117,7 +123,6 @@ sdd_status sdd_interface_mc_static(const sdd_fields* f, const sdd_nodes* nodes, 
         if (nodes->n_paths[k] < 1 || nodes->n_paths[k] > 0x7fffffffLL) return SDD_EINVAL;
     }
     // paths per task: as requested, else the smallest multiple of 128 that keeps the task list within its limit
-    int64_t ppt = p->paths_per_task ? p->paths_per_task : 128;
     auto tasks_for = [&](int64_t q) {
         int64_t t = 0;
         for (int64_t k = 0; k < count; ++k) {
@@ -127,14 +132,21 @@ sdd_status sdd_interface_mc_static(const sdd_fields* f, const sdd_nodes* nodes, 
         }
         return t;
     };
-    int64_t ntasks = tasks_for(ppt);
-    if (ntasks > kStaticMaxTasks) {
-        if (p->paths_per_task) return SDD_EINVAL;  // the requested task size does not fit
-        while (ntasks > kStaticMaxTasks && ppt < (1LL << 30)) {
-            ppt *= 2;
-            ntasks = tasks_for(ppt);
+    int64_t ppt = p->paths_per_task;
+    if (ppt) {
+        if (tasks_for(ppt) > kStaticMaxTasks) return SDD_EINVAL;  // the requested task size does not fit
+    } else {
+        // the task count falls as the task size grows: bisect over multiples of 128 (at the largest
+        // node's path count every node is one task, and count <= kStaticMaxNodes < kStaticMaxTasks)
+        int64_t most = 1;
+        for (int64_t k = 0; k < count; ++k) most = std::max<int64_t>(most, nodes->n_paths[k]);
+        int64_t lo = 1, hi = (most + 127) / 128;
+        while (lo < hi) {
+            const int64_t mid = lo + (hi - lo) / 2;
+            if (tasks_for(128 * mid) <= kStaticMaxTasks) hi = mid;
+            else lo = mid + 1;
         }
-        if (ntasks > kStaticMaxTasks) return SDD_EINVAL;
+        ppt = 128 * lo;
     }
 
     unsigned char* base = nullptr;
@@ -245,6 +257,14 @@ sdd_status sdd_interface_mc_static(const sdd_fields* f, const sdd_nodes* nodes, 
         fa.out0.path_steps = (long long*)out->path_steps;
         fa.nnodes = (int32_t)count;
         STATIC_CU(launch_finalize(fa, s));
+    }
+    // the call's device status: into the caller's word, or read here after the stream's work
+    if (status_out) {
+        STATIC_CU(cudaMemcpyAsync(status_out, status, sizeof(int), cudaMemcpyDeviceToDevice, s));
+    } else {
+        STATIC_CU(cudaStreamSynchronize(s));
+        STATIC_CU(cudaMemcpy(&g_status_host, status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (g_status_host != 0) return SDD_EDEVICE;
     }
 #undef STATIC_CU
     return SDD_OK;

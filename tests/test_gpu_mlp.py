@@ -234,7 +234,10 @@ def test_learned_control_variate_meets_the_plain_error_with_fewer_path_steps(sdd
     """The w = 1 heat problem on 65 x 65 (33 nodes on x = 1/2, dt = 1e-3, Dt = 0.05):
     a network trained by the GPU on 1e6 single-path samples of the method, used as
     control variate with 2e3 paths per node, reaches the RMS error of the plain
-    estimator with 1e4 paths per node, with at least 4x fewer path-steps."""
+    estimator with 1e4 paths per node, both against the FP64 oracle's estimate
+    with 1e6 paths per node (whose own variance is taken out of both mean squared
+    errors); and the plain estimator needs at least 4x the control variate's
+    path-steps to reach the control variate's error (error^2 falls like 1/N)."""
     P_, ctx = _heat(oracle_mod, sdd)
     dt, Dt = 1e-3, 0.05
     info = sdd.sdd_cv_train(ctx, per_horizon=20000, dt=dt, Dt=Dt, seed=1, epochs=20, batch=4096, lr=3e-3,
@@ -249,7 +252,9 @@ def test_learned_control_variate_meets_the_plain_error_with_fewer_path_steps(sdd
         o = sdd.sdd_interface_mc(ctx, xs, ys, np.full(xs.size, n), dt=dt, Dt=Dt, seed=seed)
         return {k: v.cpu().numpy() for k, v in o.items()}
 
-    ref = run(10 ** 6, 1000, False)           # the same estimator at high N
+    # the reference: the oracle's plain estimator at 1e6 paths per node (another seed)
+    ref = oracle_mod.interface_mc(P_, xs, ys, 10 ** 6, dt=dt, Dt=Dt, seed=1000)
+    ref_var = float(np.mean(np.concatenate([ref["se_xi"], ref["se_eta"]]) ** 2))
     reps = 12
     err_plain, err_cv, steps_plain, steps_cv = [], [], 0, 0
     for r in range(reps):
@@ -259,7 +264,9 @@ def test_learned_control_variate_meets_the_plain_error_with_fewer_path_steps(sdd
         err_cv.append(np.concatenate([b["mean_xi"] - ref["mean_xi"], b["mean_eta"] - ref["mean_eta"]]))
         steps_plain += a["path_steps"].sum()
         steps_cv += b["path_steps"].sum()
-    rms_plain = math.sqrt(np.mean(np.square(err_plain)))
-    rms_cv = math.sqrt(np.mean(np.square(err_cv)))
-    assert steps_plain >= 4 * steps_cv, (steps_plain, steps_cv)
-    assert rms_cv <= rms_plain, (rms_cv, rms_plain)
+    mse_plain = float(np.mean(np.square(err_plain))) - ref_var
+    mse_cv = float(np.mean(np.square(err_cv))) - ref_var
+    assert mse_plain > 0 and mse_cv > 0, (mse_plain, mse_cv, ref_var)
+    assert mse_cv <= mse_plain, (math.sqrt(mse_cv), math.sqrt(mse_plain))
+    # plain path-steps needed for the control variate's error, against the control variate's
+    assert steps_plain * (mse_plain / mse_cv) >= 4 * steps_cv, (steps_plain, steps_cv, mse_plain, mse_cv)

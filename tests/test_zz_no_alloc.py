@@ -87,3 +87,30 @@ def test_static_entry_point_rejects_sizes_beyond_its_limits(sdd):
     with pytest.raises(sdd.SddError):  # more nodes than the static node list holds
         sdd.sdd_interface_mc_static(w, f, f, np.full(9000, 0.5), np.full(9000, 0.5), 10, dt=1e-3, Dt=1e-2)
     assert sdd.sdd_static_scratch_bytes() < 16 * 2 ** 20
+
+
+def test_static_entry_point_reports_device_errors(sdd):
+    # a w that is not positive at one node is a device-side error: reported by the call
+    # itself (it waits for the stream) or, when the caller gives a device word, in that word;
+    # the next clean call reports none
+    import torch
+    n = 17
+    X, Y = W.identity_fields(n)
+    xi = torch.from_numpy(X).cuda()
+    eta = torch.from_numpy(Y).cuda()
+    bad = torch.ones((n, n), dtype=torch.float32, device="cuda")
+    bad[5, 7] = 0.0
+    good = torch.ones((n, n), dtype=torch.float32, device="cuda")
+    kw = dict(dt=1e-3, Dt=1e-2, seed=3)
+    with pytest.raises(sdd.SddError) as e:
+        sdd.sdd_interface_mc_static(bad, xi, eta, [0.5], [0.5], [100], **kw)
+    assert e.value.status == sdd.SDD_EDEVICE
+    sdd.sdd_interface_mc_static(good, xi, eta, [0.5], [0.5], [100], **kw)
+    word = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    sdd.sdd_interface_mc_static(bad, xi, eta, [0.5], [0.5], [100], status=word, **kw)
+    torch.cuda.synchronize()
+    assert int(word.item()) != 0
+    out = sdd.sdd_interface_mc_static(good, xi, eta, [0.5], [0.5], [100], status=word, **kw)
+    torch.cuda.synchronize()
+    assert int(word.item()) == 0
+    assert abs(float(out["mean_xi"].item()) - 0.5) < 0.05
