@@ -1,13 +1,16 @@
-"""Benchmark: interface Monte Carlo mesh steps of the moving-front workload on GB300.
+"""Benchmark: interface Monte Carlo mesh steps of the large ring workload on GB300.
 
-Workload (one "step" = one mesh step of the method, Sec. 4): w = 1 + 10
-exp(-(x - 0.3 - 0.4 t)^2 / 0.05^2) on a 257 x 257 FP32 grid sampled at
-t_{n-1}, 2 x 2 subdomains, the 509 interface nodes with 1e4 paths each,
-dt = 1e-4, Delta t = 1e-2 (100 sub-steps), the paper's boundary test; then
-the FP64 implicit subdomain solves. The default run times the workload's 50
-mesh steps.
+Workload (one "step" = one mesh step of the method, Sec. 4): w = 1 + 50
+exp(-(r - 0.25 - 0.1 sin 2 pi t)^2 / 0.02^2), r = |(x, y) - (1/2, 1/2)|, on a
+2049 x 2049 FP32 grid sampled at t_{n-1}, 8 x 8 subdomains, the 28,609
+interface nodes with 2e4 paths each, dt = 1e-5, Delta t = 1e-3 (100
+sub-steps), the paper's boundary test; then the FP64 implicit subdomain
+solves. The default run times the workload's 20 mesh steps, then the same
+steps with the two control variates (the previous fields' gradient and the
+learned network) against the plain estimator on the same state.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload ring2049|front257|batch64|heat65|cv65|ring41|exit65]
 
 Prints one JSON line (rank 0). Metric: Euler--Maruyama path-steps per second
 over whole mesh steps (interface nodes per second alongside). Each rank runs
@@ -35,7 +38,13 @@ import workloads as W  # noqa: E402
 
 METRIC = "path-steps/s (interface Monte Carlo, whole mesh steps)"
 UNIT = "path-steps/s"
-WL = W.FRONT257
+# The mesh-step workloads: (inputs, w at time t, description)
+WORKLOADS = {
+    "ring2049": (W.RING2049, W.w_ring,
+                 "w=1+50exp(-(r-0.25-0.1sin(2pi t))^2/0.02^2) on 2049x2049 FP32, 8x8 subdomains"),
+    "front257": (W.FRONT257, W.w_front, "w=1+10exp(-(x-0.3-0.4t)^2/0.05^2) on 257x257 FP32, 2x2 subdomains"),
+}
+DEFAULT_WORKLOAD = "ring2049"
 # Algorithmic lane operations per path-step of the path kernel, counted per
 # coordinate: half a Philox4x32-10 block (10 rounds x 2 wide multiplies + 2
 # three-input xors, over two sub-steps: 20), one Box-Muller pair (12), cell
@@ -47,23 +56,22 @@ SM_LANES_PER_CLK = 128       # 4 schedulers x 32 lanes issue per SM per clock
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=WL.steps)
+    ap.add_argument("--steps", type=int, default=None, help="timed mesh steps (default: the workload's)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-cv", action="store_true", help="skip the control-variate measurement of the default workload")
+    ap.add_argument("--no-cv", action="store_true", help="skip the control-variate measurements")
+    ap.add_argument("--no-model", action="store_true", help="skip the learned control variate's measurement")
     ap.add_argument("--paths", type=int, default=None)
-    ap.add_argument("--workload", choices=["front257", "batch64", "ring2049", "heat65", "cv65", "ring41", "exit65"],
-                    default="front257")
+    ap.add_argument("--workload", choices=["ring2049", "front257", "batch64", "heat65", "cv65", "ring41", "exit65"],
+                    default=DEFAULT_WORKLOAD)
     ap.add_argument("--key-spacing", type=int, default=8,
                     help="ring41: key points plus every k-th node (k > 0), key points only (0), every node (-1)")
     ap.add_argument("--solver", choices=["auto", "jacobi", "mg", "direct"], default="auto",
                     help="subdomain solver of the mesh steps")
-    ap.add_argument("--cv", choices=["off", "fields", "model"], default="off",
-                    help="ring2049: control variate of the timed mesh steps")
     ap.add_argument("--no-pipeline", action="store_true",
-                    help="front257: run each step's subdomain solve after its paths instead of beside the next step's")
+                    help="run each step's subdomain solve after its paths instead of beside the next step's")
     return ap.parse_args()
 
 
@@ -156,54 +164,98 @@ def whole_job(units, seconds, world):
 
 # ------------------------------------------------------------------ oracle leg
 
-def oracle_sample(target_s: float, nodes_per_call: int | None, step_cap: int):
-    """Time the FP64 oracle on samples of the workload's interface estimate."""
-    import oracle
-    n = WL.n
-    xi0, eta0 = W.identity_fields(n)
-    xs, ys = W.interface_node_coords(n, n, WL.sub, WL.sub)
-    ids = np.arange(xs.size, dtype=np.uint32)
-    if nodes_per_call:
-        pick = np.linspace(0, xs.size - 1, nodes_per_call).round().astype(np.int64)
-    else:
-        pick = np.arange(xs.size)
-    total_steps = 0
-    t0 = time.perf_counter()
-    calls = 0
-    while True:
-        w = W.w_front(n, (calls % WL.steps) * WL.Dt)
-        P = oracle.Problem(w, xi0, eta0)
-        r = oracle.interface_mc(P, xs[pick], ys[pick], WL.paths, dt=WL.dt, Dt=WL.Dt, seed=0, step_index=calls,
-                                node_ids=ids[pick])
-        total_steps += int(r["path_steps"].sum())
-        calls += 1
-        if time.perf_counter() - t0 >= target_s or calls >= step_cap:
-            break
-    el = time.perf_counter() - t0
-    return total_steps, el, calls, pick.size
+class OracleSampler:
+    """The FP64 oracle's interface estimate on seeded samples of a workload's nodes,
+    one mesh step's w per call (fields of the uniform mesh, xi0 = x, eta0 = y)."""
+
+    def __init__(self, name):
+        import oracle
+        oracle.build()
+        self.oracle = oracle
+        self.wl, self.wfun, _ = WORKLOADS[name]
+        n = self.wl.n
+        self.xs, self.ys = W.interface_node_coords(n, n, self.wl.sub, self.wl.sub)
+        self.ids = np.arange(self.xs.size, dtype=np.uint32)
+        self.xi0, self.eta0 = W.identity_fields(n)
+        self.problems = {}
+        self.rng = np.random.default_rng(12345)
+
+    def problem(self, k):
+        k = k % self.wl.steps
+        if k not in self.problems:
+            if len(self.problems) > 2:
+                self.problems.clear()
+            self.problems[k] = self.oracle.Problem(self.wfun(self.wl.n, k * self.wl.Dt), self.xi0, self.eta0)
+        return self.problems[k]
+
+    def call(self, k, nodes, threads=None):
+        """One oracle estimate at `nodes` seeded random interface nodes of mesh step k:
+        (path-steps, seconds)."""
+        pick = np.sort(self.rng.choice(self.xs.size, size=min(nodes, self.xs.size), replace=False))
+        P = self.problem(k)
+        t0 = time.perf_counter()
+        r = self.oracle.interface_mc(P, self.xs[pick], self.ys[pick], self.wl.paths, dt=self.wl.dt, Dt=self.wl.Dt,
+                                     seed=0, step_index=k, node_ids=self.ids[pick], threads=threads)
+        return int(r["path_steps"].sum()), time.perf_counter() - t0
+
+    def timed(self, target_s, nodes, threads=None):
+        """Calls of `nodes` nodes, mesh step after mesh step, until target_s seconds of oracle time."""
+        steps, el, calls = 0, 0.0, 0
+        while el < target_s or calls == 0:
+            a, b = self.call(calls, nodes, threads)
+            steps += a
+            el += b
+            calls += 1
+        return steps, el, calls
+
+
+def cpu_baseline(name):
+    """The oracle on the host cores, all of them and one, on seeded node samples
+    (about 10 s of oracle work each); throughput per path-step."""
+    S = OracleSampler(name)
+    wl = S.wl
+    cores = os.cpu_count() or 1
+    S.call(0, 1)   # the first step's tables, outside the timing
+    nodes_all = max(1, min(S.xs.size, 4 * cores))
+    st_a, el_a, calls_a = S.timed(10.0, nodes_all)
+    st_1, el_1, calls_1 = S.timed(10.0, 2, threads=1)
+    return {"value": st_a / el_a, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{calls_a} call(s) of {nodes_all} seeded random interface nodes of the {name} mesh steps x "
+                      f"{wl.paths} paths ({st_a} path-steps in {el_a:.1f} s, all {cores} cores, one thread per node "
+                      f"chunk); the rate per path-step carries over to the whole workload",
+            "single_thread": {"value": st_1 / el_1, "unit": UNIT, "cores": 1,
+                              "sample": f"{calls_1} call(s) of 2 nodes ({st_1} path-steps in {el_1:.1f} s)"}}
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    import oracle
-    oracle.build()
+    name = args.workload if args.workload in WORKLOADS else DEFAULT_WORKLOAD
+    S = OracleSampler(name)
+    wl = S.wl
     cores = os.cpu_count() or 1
-    per_call_nodes = 32
+    K = args.steps or wl.steps
+    per_call_nodes = 2 * cores
     # untimed warm-up, then K timed steps (each: the oracle's estimate at a node sample of one mesh step)
-    oracle_sample(0.0, per_call_nodes, max(1, args.warmup))
-    steps_done, el, calls, nn = oracle_sample(1e9, per_call_nodes, args.steps)
+    for k in range(max(1, args.warmup)):
+        S.call(k, 1)
+    steps_done, el = 0, 0.0
+    for k in range(K):
+        a, b = S.call(k, per_call_nodes)
+        steps_done += a
+        el += b
     value = steps_done / el
+    desc = WORKLOADS[name][2]
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * el / max(calls, 1), "higher_is_better": True,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": K,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "impl": "reference",
-        "config": {"workload": f"front257: {WL.n}x{WL.n} grid, 2x2 subdomains, interface estimate at a sample of "
-                               f"{nn} of 509 nodes per step, {WL.paths} paths/node, dt={WL.dt}, Dt={WL.Dt}",
-                   "global_batch": nn * WL.paths, "seq_len": WL.K, "parallelism": "cpu threads"},
+        "config": {"workload": f"{name}: {desc}, interface estimate at {per_call_nodes} seeded random interface "
+                               f"nodes per mesh step, {wl.paths} paths/node, dt={wl.dt}, Dt={wl.Dt} (K={wl.K})",
+                   "global_batch": per_call_nodes * wl.paths, "seq_len": wl.K, "parallelism": "cpu threads"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{nn} evenly spaced interface nodes x {WL.paths} paths per step"},
+                         "sample": f"{per_call_nodes} seeded random interface nodes x {wl.paths} paths per mesh step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -240,29 +292,33 @@ def run_ours(args, world, rank, local):
     import paper_1402_0266_gb300 as sdd
     from paper_1402_0266_gb300 import build as b
     b.build()
+    name = args.workload
+    WL, wfun, desc = WORKLOADS[name]
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    n, K, Wm = WL.n, args.steps, args.warmup
+    n, Wm = WL.n, args.warmup
+    K = args.steps or WL.steps
+    paths = args.paths or WL.paths
     seed = WL.seed + rank
     stream = torch.cuda.current_stream()
     xi0, eta0 = W.identity_fields(n)
     xi0_d = torch.from_numpy(xi0).to(dev)
     eta0_d = torch.from_numpy(eta0).to(dev)
     # the mesh density of every step, resident on the device before timing
-    nsteps = max(K, Wm)
-    w_all = torch.from_numpy(np.stack([W.w_front(n, k * WL.Dt) for k in range(nsteps)])).to(dev)
+    nsteps = max(K, Wm, 1)
+    w_host = torch.from_numpy(np.stack([wfun(n, k * WL.Dt) for k in range(nsteps)]))
+    w_all = w_host.to(dev)
     ctx = sdd.sdd_init(n, n, WL.sub, WL.sub, w=w_all[0], xi0=xi0_d, eta0=eta0_d)
     sdd.sdd_set_solver(ctx, {"auto": 0, "jacobi": 1, "mg": 2, "direct": 3}[args.solver])
     sdd.sdd_set_pipeline(ctx, not args.no_pipeline)
-    sp = dict(dt=WL.dt, Dt=WL.Dt, seed=seed, paths_per_node=args.paths, exit_mode=0, rtol=1e-12, max_iter=20000,
-              tune=1)
+    sp = dict(dt=WL.dt, Dt=WL.Dt, seed=seed, paths_per_node=paths, exit_mode=0, rtol=1e-12, max_iter=40000, tune=1)
 
     def reset():
         sdd.sdd_set_fields(ctx, xi0_d, eta0_d)
         sdd.sdd_set_step_index(ctx, 0)
 
     for k in range(Wm):
-        sdd.sdd_set_w(ctx, w_all[k])
+        sdd.sdd_set_w(ctx, w_all[k % nsteps])
         sdd.sdd_step(ctx, **sp)
     sdd.sdd_sync(ctx)
     reset()
@@ -304,7 +360,8 @@ def run_ours(args, world, rank, local):
     path_steps = int(steps_dev.sum().item())
     value, tot_steps, max_s = whole_job(path_steps, total_ms / 1e3, world)
     max_ms = max_s * 1e3
-    nodes = len(sdd.sdd_interface_nodes(ctx)[0])
+    ix, iy = sdd.sdd_interface_nodes(ctx)
+    nodes = len(ix)
     nodes_per_s = world * nodes * K / (max_ms / 1e3)
 
     # dominant kernel: the path kernel, timed by events recorded inside the step graph
@@ -319,27 +376,36 @@ def run_ours(args, world, rank, local):
     except Exception:
         pass
     peak = props.multi_processor_count * SM_LANES_PER_CLK * sm_max * 1e6 / 1e12
-    traffic = profiled_traffic(os.path.join(ROOT, "profiles", "k_paths_front257.md"))
+    # DRAM bytes of one launch, from the committed profile of this workload's path kernel when its sources
+    # are unchanged (a capture of a node sample, scaled to the launch by path-steps)
+    traffic = None
+    tp = profiled_traffic(os.path.join(ROOT, "profiles", f"k_paths_{name}.md"))
+    if tp is not None:
+        try:
+            lines = open(os.path.join(ROOT, "profiles", f"k_paths_{name}.md")).read().splitlines()
+            per = dict(l.split(": ", 1) for l in lines if l.startswith("path_steps_per_launch: "))
+            traffic = tp * steps_per_launch / float(per["path_steps_per_launch"]) if per else tp
+        except Exception:
+            traffic = tp
 
     # end to end through the C ABI with host buffers: w in from pinned host memory,
     # the interface statistics back to pinned host memory, every step
     e2e = None
     if not args.no_e2e:
         reset()
-        w_host = torch.from_numpy(np.stack([W.w_front(n, k * WL.Dt) for k in range(K)])).pin_memory()
-        nn = nodes
+        w_pin = w_host[:K].pin_memory()
         # one set of pinned result buffers per step: the steps are enqueued back to back (the API is
         # stream-ordered) and every step's statistics land in host memory before the clock stops
         hosts = []
         for _ in range(K):
-            h = {k: torch.empty(nn, dtype=torch.float64).pin_memory() for k in ("mean_xi", "mean_eta", "se_xi", "se_eta")}
-            h["n_exit"] = torch.empty(nn, dtype=torch.int64).pin_memory()
-            h["path_steps"] = torch.empty(nn, dtype=torch.int64).pin_memory()
+            h = {k: torch.empty(nodes, dtype=torch.float64).pin_memory() for k in ("mean_xi", "mean_eta", "se_xi", "se_eta")}
+            h["n_exit"] = torch.empty(nodes, dtype=torch.int64).pin_memory()
+            h["path_steps"] = torch.empty(nodes, dtype=torch.int64).pin_memory()
             hosts.append(h)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in range(K):
-            sdd.sdd_set_w_host(ctx, w_host[k])
+            sdd.sdd_set_w_host(ctx, w_pin[k])
             sdd.sdd_step(ctx, **sp)
             sdd.sdd_last_interface_stats(ctx, out=hosts[k])
         sdd.sdd_flush(ctx)
@@ -348,9 +414,9 @@ def run_ours(args, world, rank, local):
         e2e_steps = sum(int(h["path_steps"].sum()) for h in hosts)
         e2e_value = whole_job(e2e_steps, el, world)[0]
         e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * n * 4,
-               "d2h_bytes_per_step": nn * 48}
+               "d2h_bytes_per_step": nodes * 48}
 
-    # the path kernel alone (unpipelined steps): in the timed pipelined steps it shares 64 SMs with
+    # the path kernel alone (unpipelined steps): in the timed pipelined steps it shares SMs with
     # the previous step's solve for part of its launch
     alone = None
     if pipelined:
@@ -371,74 +437,76 @@ def run_ours(args, world, rank, local):
                  "unpipelined_step_ms": statistics.mean(a_step[1:] if len(a_step) > 1 else a_step),
                  "note": "unpipelined steps after the timed region (the same launches without the solve beside)"}
 
-    # the second bound: every sub-step gathers one 32-byte cell record from a random cell, one L1
-    # sector and so one wavefront of the L1 data pipe, which serves one wavefront per SM cycle
-    gather_peak = props.multi_processor_count * sm_max * 1e6
-    gather = {"resource": "L1 data pipe", "unit": "wavefronts/s", "wavefronts_per_path_step": 1,
-              "achieved": steps_per_launch / (mean_paths_ms / 1e3), "peak": gather_peak,
-              "frac": steps_per_launch / (mean_paths_ms / 1e3) / gather_peak,
-              "peak_basis": f"{props.multi_processor_count} SMs x 1 wavefront x {sm_max:.0f} MHz"}
-    if alone is not None:
-        gather["frac_alone"] = steps_per_launch / (alone["paths_kernel_ms"] / 1e3) / gather_peak
-
-    # the same mesh steps with the control variate of the previous fields' gradient:
-    # throughput, and the variance against the plain estimator on the same state
+    # control variates at equal error: the previous fields' gradient (no training) and the learned
+    # network, each timed over mesh steps from the same start, and its variance against the plain
+    # estimator on the same state (one estimate each at every 16th interface node, same seed)
     equal_error = None
     if not args.no_cv:
-        reset()
-        sdd.sdd_cv_enable(ctx, sdd.SDD_CV_FIELDS)
-        kc = min(K, 10)
-        cv_ms, cv_steps, cv_pk = 0.0, 0, []
-        for k in range(kc):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            sdd.sdd_set_w(ctx, w_all[k])
-            sdd.sdd_step(ctx, **sp)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            cv_ms += e0.elapsed_time(e1)
-            cv_steps += int(sdd.sdd_last_interface_stats(ctx)["path_steps"].sum())
-            cv_pk.append(sdd.sdd_last_step_info(ctx)["paths_ms"])
-        ix, iy = sdd.sdd_interface_nodes(ctx)
-        est = {}
-        for name, mode in (("plain", sdd.SDD_CV_OFF), ("cv", sdd.SDD_CV_FIELDS)):
+        pick = np.arange(0, nodes, 16 if nodes > 2000 else 1)
+        xs_, ys_ = np.asarray(ix)[pick], np.asarray(iy)[pick]
+        equal_error = {"sample_nodes": int(pick.size)}
+        modes = [("fields", sdd.SDD_CV_FIELDS, "gradient of the fields at t_{n-1} (no training)")]
+        if not args.no_model:
+            modes.append(("model", sdd.SDD_CV_MODEL, "learned 5-64-64-1 network, trained on the GPU at the first "
+                                                    "mesh step, re-tabulated from each step's w"))
+        kc = min(K, 5)
+        for key, mode, what in modes:
+            reset()
+            train = None
+            if key == "model":
+                train = sdd.sdd_cv_train(ctx, per_horizon=10000, dt=WL.dt, Dt=WL.Dt, seed=100 + rank, epochs=10,
+                                         batch=4096, lr=3e-3, slices=4, init_seed=7)
+                train = {k2: train[k2] for k2 in ("samples_ms", "train_ms", "tabulate_ms", "rows", "steps")}
             sdd.sdd_cv_enable(ctx, mode)
-            o = sdd.sdd_interface_mc(ctx, ix, iy, np.full(len(ix), args.paths), dt=WL.dt, Dt=WL.Dt, seed=seed + 99)
-            est[name] = {k2: v.cpu().numpy() for k2, v in o.items()}
-        sdd.sdd_cv_enable(ctx, sdd.SDD_CV_OFF)
-        ratio = {}
-        for f in ("xi", "eta"):
-            a, c = est["plain"]["se_" + f], est["cv"]["se_" + f]
-            ok = c > 0
-            ratio[f] = float(np.median((a[ok] / c[ok]) ** 2))
-        cv_value = cv_steps / (cv_ms / 1e3)
-        equal_error = {"control_variate": "gradient of the fields at t_{n-1} (no training)", "steps": kc,
-                       "path_steps_per_s": cv_value, "paths_kernel_ms": statistics.mean(cv_pk),
-                       "variance_ratio_vs_plain": ratio,
-                       "path_steps_per_s_at_equal_error": cv_value * min(ratio.values()),
-                       "interface_nodes_per_s_at_equal_error": nodes * kc / (cv_ms / 1e3) * min(ratio.values())}
+            cv_ms, cv_steps, cv_pk = 0.0, 0, []
+            for k in range(kc):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sdd.sdd_set_w(ctx, w_all[k])
+                sdd.sdd_step(ctx, **sp)
+                sdd.sdd_flush(ctx)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                cv_ms += e0.elapsed_time(e1)
+                cv_steps += int(sdd.sdd_last_interface_stats(ctx)["path_steps"].sum())
+                cv_pk.append(sdd.sdd_last_step_info(ctx)["paths_ms"])
+            est = {}
+            for which, m in (("plain", sdd.SDD_CV_OFF), ("cv", mode)):
+                sdd.sdd_cv_enable(ctx, m)
+                o = sdd.sdd_interface_mc(ctx, xs_, ys_, np.full(xs_.size, paths), dt=WL.dt, Dt=WL.Dt, seed=seed + 99)
+                est[which] = {k2: v.cpu().numpy() for k2, v in o.items()}
+            sdd.sdd_cv_enable(ctx, sdd.SDD_CV_OFF)
+            ratio = {}
+            for f in ("xi", "eta"):
+                a_, c_ = est["plain"]["se_" + f], est["cv"]["se_" + f]
+                ok = c_ > 0
+                ratio[f] = float(np.median((a_[ok] / c_[ok]) ** 2))
+            cv_value = cv_steps / (cv_ms / 1e3)
+            equal_error[key] = {"control_variate": what, "steps": kc, "path_steps_per_s": cv_value,
+                                "paths_kernel_ms": statistics.mean(cv_pk),
+                                "paths_kernel_ms_vs_plain": statistics.mean(cv_pk) / mean_paths_ms,
+                                "variance_ratio_vs_plain": ratio,
+                                "path_steps_per_s_at_equal_error": cv_value * min(ratio.values()),
+                                "interface_nodes_per_s_at_equal_error": nodes * kc / (cv_ms / 1e3) * min(ratio.values()),
+                                "training": train}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        steps_c, el_c, calls, nnc = oracle_sample(15.0, None, 40)
-        cpu = {"value": steps_c / el_c, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
-               "sample": f"{calls} mesh step(s) of the interface estimate, all {nnc} nodes x {WL.paths} paths "
-                         f"({steps_c} path-steps, {el_c:.1f} s)"}
+        cpu = cpu_baseline(name)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
             "ms_per_step": max_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"front257: w=1+10exp(-(x-0.3-0.4t)^2/0.05^2) on {n}x{n} FP32, 2x2 subdomains, "
-                                   f"{nodes} interface nodes x {args.paths} paths, dt={WL.dt}, Dt={WL.Dt} "
-                                   f"(K={WL.K}), plain exit test, "
+            "config": {"workload": f"{name}: {desc}, {nodes} interface nodes x {paths} paths, dt={WL.dt}, "
+                                   f"Dt={WL.Dt} (K={WL.K}), plain exit test, "
                                    f"{solver_name} subdomain solves (FP64 residuals, rtol 1e-12)"
                                    + (", each step's solve iterations beside the next step's paths (pipelined)"
                                       if pipelined else ""),
-                       "global_batch": world * nodes * args.paths, "seq_len": WL.K,
+                       "global_batch": world * nodes * paths, "seq_len": WL.K,
                        "parallelism": f"{world} independent instance(s), one per GPU",
                        "l2": "flushed before every step (256 MB write, outside the step's events)"},
             "interface_nodes_per_s": nodes_per_s,
@@ -450,8 +518,9 @@ def run_ours(args, world, rank, local):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_paths", "ops_per_path_step": ALG_OPS_PER_PATH_STEP,
-                         "peak_basis": f"{props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz",
-                         "alone": alone, "gather_bound": gather},
+                         "peak_basis": f"{props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz (of measured "
+                                       f"maximum SM clock)",
+                         "alone": alone},
             "equal_error": equal_error,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -590,7 +659,7 @@ def run_ring41(args, world, rank, local):
     torch.cuda.set_device(local)
     wl = W.RING41
     n, Dt = wl.n, wl.Dt
-    steps = args.steps if args.steps != WL.steps else wl.steps
+    steps = args.steps or wl.steps
     xi0, eta0 = W.identity_fields(n)
     w_all = torch.from_numpy(np.stack([W.w_paper_ring(n, k * Dt) for k in range(steps)])).cuda()
     ctx = sdd.sdd_init(n, n, wl.sub, wl.sub, w=w_all[0], xi0=torch.from_numpy(xi0).cuda(),
@@ -720,84 +789,6 @@ def run_exit65(args, world, rank, local):
         }), flush=True)
 
 
-def run_ring2049(args, world, rank, local):
-    """The large ring workload: mesh steps on 2049 x 2049 with 8 x 8 subdomains."""
-    import torch
-
-    import paper_1402_0266_gb300 as sdd
-    from paper_1402_0266_gb300 import build as b
-    b.build()
-    torch.cuda.set_device(local)
-    wl = W.RING2049
-    n = wl.n
-    paths = args.paths or wl.paths
-    ctx = sdd.sdd_init(n, n, wl.sub, wl.sub, w=torch.from_numpy(W.w_ring(n, 0.0)).cuda())
-    sdd.sdd_set_solver(ctx, {"auto": 0, "jacobi": 1, "mg": 2, "direct": 3}[args.solver])
-    sp = dict(dt=wl.dt, Dt=wl.Dt, seed=rank, paths_per_node=paths, exit_mode=0, rtol=1e-12, max_iter=40000, tune=1)
-    train = None
-    mode = {"off": sdd.SDD_CV_OFF, "fields": sdd.SDD_CV_FIELDS, "model": sdd.SDD_CV_MODEL}[args.cv]
-    if args.cv == "model":
-        train = sdd.sdd_cv_train(ctx, per_horizon=10000, dt=wl.dt, Dt=wl.Dt, seed=100 + rank, epochs=10,
-                                 batch=4096, lr=3e-3, slices=4, init_seed=7)
-    sdd.sdd_cv_enable(ctx, mode)
-    for k in range(args.warmup):
-        sdd.sdd_set_w(ctx, torch.from_numpy(W.w_ring(n, k * wl.Dt)).cuda())
-        sdd.sdd_step(ctx, **sp)
-    sdd.sdd_sync(ctx)
-    times, steps, pk, sv = [], 0, [], []
-    for k in range(args.steps):
-        w = torch.from_numpy(W.w_ring(n, (args.warmup + k) * wl.Dt)).cuda()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        sdd.sdd_set_w(ctx, w)
-        sdd.sdd_step(ctx, **sp)
-        e1.record()
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
-        st = sdd.sdd_last_interface_stats(ctx)
-        steps += int(st["path_steps"].sum())
-        info = sdd.sdd_last_step_info(ctx)
-        pk.append(info["paths_ms"])
-        sv.append(info["solve_ms"])
-    sdd.sdd_sync(ctx)
-    ms = sum(times)
-    nodes = len(sdd.sdd_interface_nodes(ctx)[0])
-    # variance against the plain estimator on the same state: one estimate each on a sample of the nodes
-    ix, iy = sdd.sdd_interface_nodes(ctx)
-    pick = np.arange(0, len(ix), 16)
-    xs_, ys_ = np.asarray(ix)[pick], np.asarray(iy)[pick]
-    var_ratio = None
-    if mode != sdd.SDD_CV_OFF:
-        sdd.sdd_cv_enable(ctx, sdd.SDD_CV_OFF)
-        a = sdd.sdd_interface_mc(ctx, xs_, ys_, np.full(xs_.size, paths), dt=wl.dt, Dt=wl.Dt, seed=77)
-        sdd.sdd_cv_enable(ctx, mode)
-        c = sdd.sdd_interface_mc(ctx, xs_, ys_, np.full(xs_.size, paths), dt=wl.dt, Dt=wl.Dt, seed=77)
-        r = []
-        for f in ("se_xi", "se_eta"):
-            sa, sc = a[f].cpu().numpy(), c[f].cpu().numpy()
-            ok = sc > 0
-            r.append(float(np.median((sa[ok] / sc[ok]) ** 2)))
-        var_ratio = {"xi": r[0], "eta": r[1]}
-    if rank == 0:
-        print(json.dumps({"metric": METRIC, "value": steps / (ms / 1e3), "unit": UNIT, "n_gpus": world,
-                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-                          "data": "synthetic",
-                          "config": {"workload": f"ring2049: {n}x{n}, 8x8 subdomains, {nodes} nodes x {paths} paths, "
-                                                 f"dt={wl.dt}, Dt={wl.Dt}, control variate {args.cv}"},
-                          "control_variate": args.cv, "variance_ratio_vs_plain": var_ratio,
-                          "equal_error_path_steps_per_s": (None if var_ratio is None else
-                                                           steps / (ms / 1e3) * min(var_ratio.values())),
-                          "training": train,
-                          "interface_nodes_per_s": nodes * args.steps / (ms / 1e3),
-                          "path_steps_per_step": steps / args.steps, "paths_kernel_ms": statistics.mean(pk),
-                          "solve_ms": statistics.mean(sv),
-                          "roofline_frac_paths": ALG_OPS_PER_PATH_STEP * steps / args.steps / (statistics.mean(pk) / 1e3)
-                          / 1e12 / (152 * SM_LANES_PER_CLK * 2070e6 / 1e12)}), flush=True)
-
-
 def run_heat65(args, world, rank, local):
     """The small heat-equation case (w = 1 on 65 x 65, 33 nodes on x = 1/2 x 1000 paths, dt = 1e-3, Dt = 0.05,
     zero boundary data): one step = one interface estimate of all 33 nodes, inputs resident on the device.
@@ -849,42 +840,26 @@ def run_heat65(args, world, rank, local):
 
 def main():
     args = parse()
-    if args.workload == "heat65" and args.impl == "ours":
-        world, rank, local = dist_init()
-        if args.steps == WL.steps:
-            args.steps = 200
-        run_heat65(args, world, rank, local)
-        return
-    if args.workload == "batch64" and args.impl == "ours":
-        world, rank, local = dist_init()
-        run_batch64(args, world, rank, local)
-        return
-    if args.workload == "ring2049" and args.impl == "ours":
-        world, rank, local = dist_init()
-        run_ring2049(args, world, rank, local)
-        return
-    if args.workload == "exit65" and args.impl == "ours":
-        world, rank, local = dist_init()
-        run_exit65(args, world, rank, local)
-        return
-    if args.workload == "ring41" and args.impl == "ours":
-        world, rank, local = dist_init()
-        run_ring41(args, world, rank, local)
-        return
-    if args.workload == "cv65" and args.impl == "ours":
-        world, rank, local = dist_init()
-        if args.steps == WL.steps:
-            args.steps = 12
-        run_cv65(args, world, rank, local)
-        return
-    if args.paths is None:
-        args.paths = WL.paths
     if args.impl == "reference":
-        # the CPU oracle: rank 0 alone runs; other ranks exit without work
+        # the CPU oracle on a sample of the mesh-step workload: rank 0 alone runs; other ranks exit without work
         run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")))
         return
     world, rank, local = dist_init()
-    run_ours(args, world, rank, local)
+    if args.workload == "heat65":
+        args.steps = args.steps or 200
+        run_heat65(args, world, rank, local)
+    elif args.workload == "batch64":
+        args.steps = args.steps or 20
+        run_batch64(args, world, rank, local)
+    elif args.workload == "exit65":
+        run_exit65(args, world, rank, local)
+    elif args.workload == "ring41":
+        run_ring41(args, world, rank, local)
+    elif args.workload == "cv65":
+        args.steps = args.steps or 12
+        run_cv65(args, world, rank, local)
+    else:
+        run_ours(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
