@@ -60,7 +60,8 @@ typedef struct {
 /* A set of evaluation nodes (HOST arrays of `count` entries). Coordinates must
  * lie in [0, 1]; a node on the boundary returns its Dirichlet value with a
  * standard error of 0 and no path steps. n_paths[k] in [1, 2^31 - 1]. The
- * node's position k in the arrays is its index in the random stream. */
+ * node's position k in the arrays is its index in the random stream (offset
+ * by sdd_mc_params.node_word0). */
 typedef struct {
     const double* x;
     const double* y;
@@ -116,7 +117,21 @@ typedef struct {
  *                  the control variate (SDD_EINVAL).
  *   block_threads, paths_per_task: launch shape; 0 picks the tuned default.
  *               block_threads in {64, 128, 256, 512}; paths_per_task a
- *               multiple of 32. */
+ *               multiple of 32.
+ *   node_word0  node word of the first node: node k of the call takes
+ *               node_word0 + k as the node word of its Philox counters
+ *               (0: the call's own numbering). A caller that splits a node
+ *               list into ranges (one range per GPU, say) passes each
+ *               range's first index: with the same paths_per_task every
+ *               node's results are then those of the whole list, bit for
+ *               bit. A batch numbers its nodes from node_word0 on.
+ *   zero_map    0: automatic (the autotuner's choice for the node set, else
+ *               on); 1 on; 2 off. With it on, the path kernel of a context
+ *               reads one shared all-zero drift record wherever the drift
+ *               records of a stretch of cells are all zero (w constant
+ *               there): the same values, so the same results bit for bit,
+ *               with fewer L1 wavefronts and a few more instructions per
+ *               sub-step. Batches ignore it. */
 typedef struct {
     double dt;
     double Dt;
@@ -125,6 +140,8 @@ typedef struct {
     int32_t exit_mode;
     int32_t block_threads;
     int32_t paths_per_task;
+    uint32_t node_word0;
+    int32_t zero_map;
 } sdd_mc_params;
 
 /* Create a context on the current CUDA device.
@@ -355,12 +372,14 @@ sdd_status sdd_cv_losses(sdd_ctx* ctx, float* losses, int64_t count);
 typedef struct {
     int32_t block_threads;
     int32_t paths_per_task;
-    float ms;   /* measured time of one estimate with this shape */
+    float ms;           /* measured time of one estimate with this shape */
+    int32_t zero_map;   /* 1: with the drift's zero map, 2: without (see sdd_mc_params) */
 } sdd_launch_shape;
 
 /* Autotuner: time the interface estimate of this node set and these
  * parameters with every candidate launch shape (128, 256, 512 threads x 32 ..
- * 1024 paths per task; outputs discarded; uses the context's current tables),
+ * 1024 paths per task, 512 only where the kernel takes it; with and without
+ * the zero map; outputs discarded; uses the context's current tables),
  * keep the fastest, and use it for later calls on the same node set, K and
  * exit mode that leave block_threads and paths_per_task at 0. Waits for the
  * stream. `out` (HOST, may be NULL) receives the chosen shape. */

@@ -74,7 +74,7 @@ class _Records(ctypes.Structure):
 class _McParams(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("Dt", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("step_index", ctypes.c_uint32), ("exit_mode", ctypes.c_int32), ("block_threads", ctypes.c_int32),
-                ("paths_per_task", ctypes.c_int32)]
+                ("paths_per_task", ctypes.c_int32), ("node_word0", ctypes.c_uint32), ("zero_map", ctypes.c_int32)]
 
 
 class _Fields(ctypes.Structure):
@@ -94,7 +94,8 @@ class _StepParams(ctypes.Structure):
 
 
 class _Shape(ctypes.Structure):
-    _fields_ = [("block_threads", ctypes.c_int32), ("paths_per_task", ctypes.c_int32), ("ms", ctypes.c_float)]
+    _fields_ = [("block_threads", ctypes.c_int32), ("paths_per_task", ctypes.c_int32), ("ms", ctypes.c_float),
+                ("zero_map", ctypes.c_int32)]
 
 
 class _SampleParams(ctypes.Structure):
@@ -337,26 +338,27 @@ def _alloc_stats(count):
     return d, s
 
 
-def mc_params(dt, Dt, seed=0, step_index=0, exit_mode=0, block_threads=0, paths_per_task=0):
-    return _McParams(dt, Dt, seed, step_index, exit_mode, block_threads, paths_per_task)
+def mc_params(dt, Dt, seed=0, step_index=0, exit_mode=0, block_threads=0, paths_per_task=0, node_word0=0,
+              zero_map=0):
+    return _McParams(dt, Dt, seed, step_index, exit_mode, block_threads, paths_per_task, node_word0, zero_map)
 
 
 def sdd_interface_mc(ctx: Ctx, x, y, n_paths, dt, Dt, seed=0, step_index=0, exit_mode=0, block_threads=0,
-                     paths_per_task=0, out=None):
+                     paths_per_task=0, node_word0=0, zero_map=0, out=None):
     """Interface estimate at nodes (x, y) (host arrays). Returns a dict of cuda tensors."""
     nodes, keep = _nodes(x, y, n_paths)
     if out is None:
         out, s = _alloc_stats(nodes.count)
     else:
         s = _Stats(*(out[k].data_ptr() for k in ("mean_xi", "mean_eta", "se_xi", "se_eta", "n_exit", "path_steps")))
-    p = mc_params(dt, Dt, seed, step_index, exit_mode, block_threads, paths_per_task)
+    p = mc_params(dt, Dt, seed, step_index, exit_mode, block_threads, paths_per_task, node_word0, zero_map)
     ctx._check(lib().sdd_interface_mc(ctx.handle, ctypes.byref(nodes), ctypes.byref(p), ctypes.byref(s)))
     del keep
     return out
 
 
 def sdd_interface_mc_record(ctx: Ctx, x, y, n_paths, dt, Dt, seed=0, step_index=0, exit_mode=0, block_threads=0,
-                            paths_per_task=0):
+                            paths_per_task=0, node_word0=0, zero_map=0):
     """As sdd_interface_mc, plus per-path records (node after node)."""
     torch = _torch()
     nodes, keep = _nodes(x, y, n_paths)
@@ -367,7 +369,7 @@ def sdd_interface_mc_record(ctx: Ctx, x, y, n_paths, dt, Dt, seed=0, step_index=
     for k in ("score_xi", "score_eta", "x_end", "y_end"):
         rec[k] = torch.empty(total, dtype=torch.float32, device="cuda")
     r = _Records(*(rec[k].data_ptr() for k in ("steps", "code", "score_xi", "score_eta", "x_end", "y_end")))
-    p = mc_params(dt, Dt, seed, step_index, exit_mode, block_threads, paths_per_task)
+    p = mc_params(dt, Dt, seed, step_index, exit_mode, block_threads, paths_per_task, node_word0, zero_map)
     ctx._check(lib().sdd_interface_mc_record(ctx.handle, ctypes.byref(nodes), ctypes.byref(p), ctypes.byref(s),
                                              ctypes.byref(r)))
     del keep
@@ -478,7 +480,7 @@ def sdd_rng_draw(seed, counters, stream=None):
 
 
 def sdd_interface_mc_static(w, xi, eta, x, y, n_paths, dt, Dt, seed=0, step_index=0, exit_mode=0, block_threads=0,
-                            paths_per_task=0, faces=None, out=None, stream=None, status=None):
+                            paths_per_task=0, node_word0=0, faces=None, out=None, stream=None, status=None):
     """The interface estimate without any allocation in the library (see include/sdd.h).
 
     w (float32), xi, eta (float64): cuda tensors of shape (ny, nx); x, y, n_paths: host arrays.
@@ -500,7 +502,7 @@ def sdd_interface_mc_static(w, xi, eta, x, y, n_paths, dt, Dt, seed=0, step_inde
         out, s = _alloc_stats(nodes.count)
     else:
         s = _Stats(*(out[k].data_ptr() for k in ("mean_xi", "mean_eta", "se_xi", "se_eta", "n_exit", "path_steps")))
-    p = mc_params(dt, Dt, seed, step_index, exit_mode, block_threads, paths_per_task)
+    p = mc_params(dt, Dt, seed, step_index, exit_mode, block_threads, paths_per_task, node_word0)
     if status is not None:
         _check_dev(status, torch.int32, (1,), "status")
     st = lib().sdd_interface_mc_static(ctypes.byref(f), ctypes.byref(nodes), ctypes.byref(p), ctypes.byref(s),
@@ -546,7 +548,7 @@ def sdd_batch_create(ctxs, stream=None) -> Batch:
 
 
 def sdd_batch_interface_mc(batch: Batch, node_lists, dt, Dt, seed=0, step_index=0, exit_mode=0, block_threads=0,
-                           paths_per_task=0):
+                           paths_per_task=0, node_word0=0):
     """node_lists: one (x, y, n_paths) per instance (host arrays). Returns one result dict per instance."""
     n = len(batch.ctxs)
     assert len(node_lists) == n
@@ -558,7 +560,7 @@ def sdd_batch_interface_mc(batch: Batch, node_lists, dt, Dt, seed=0, step_index=
         o, s_ = _alloc_stats(nd.count)
         outs.append(o)
         stats[k] = s_
-    p = mc_params(dt, Dt, seed, step_index, exit_mode, block_threads, paths_per_task)
+    p = mc_params(dt, Dt, seed, step_index, exit_mode, block_threads, paths_per_task, node_word0)
     batch._check(lib().sdd_batch_interface_mc(batch.handle, nodes, ctypes.byref(p), stats))
     del keep
     return outs
@@ -602,7 +604,8 @@ def sdd_autotune(ctx: Ctx, x, y, n_paths, dt, Dt, exit_mode=0) -> dict:
     out = _Shape()
     ctx._check(lib().sdd_autotune(ctx.handle, ctypes.byref(nodes), ctypes.byref(p), ctypes.byref(out)))
     del keep
-    return {"block_threads": out.block_threads, "paths_per_task": out.paths_per_task, "ms": out.ms}
+    return {"block_threads": out.block_threads, "paths_per_task": out.paths_per_task, "ms": out.ms,
+            "zero_map": out.zero_map}
 
 
 def sdd_batch_autotune(batch: Batch, node_lists, dt, Dt, exit_mode=0) -> dict:
@@ -616,7 +619,8 @@ def sdd_batch_autotune(batch: Batch, node_lists, dt, Dt, exit_mode=0) -> dict:
     out = _Shape()
     batch._check(lib().sdd_batch_autotune(batch.handle, nodes, ctypes.byref(p), ctypes.byref(out)))
     del keep
-    return {"block_threads": out.block_threads, "paths_per_task": out.paths_per_task, "ms": out.ms}
+    return {"block_threads": out.block_threads, "paths_per_task": out.paths_per_task, "ms": out.ms,
+            "zero_map": out.zero_map}
 
 
 def sdd_cv_set_table(ctx: Ctx, grad):

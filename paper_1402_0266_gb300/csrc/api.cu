@@ -55,6 +55,7 @@ struct Plan {
     bool valid = false;
 
     int block = 256, grid = 0, ppt = 0;
+    int zero_map = 1;   // single-instance launches: read the drift through the zero map (1) or not (0)
     int64_t nnodes = 0, ntasks = 0, total_paths = 0;
     std::vector<NodeDev> nodes;
     std::vector<Task> tasks;
@@ -71,6 +72,7 @@ struct TunedShape {
     uint64_t key;
     int block, ppt;
     float ms;
+    int zero_map;   // 1: the zero map's kernel was the faster (single instance)
 };
 
 struct GraphSlot {
@@ -110,7 +112,10 @@ struct sdd_ctx {
     int cur = 0;
     DevBuf<double> faces64;
     DevBuf<float> faces32;
-    DevBuf<float4> bcoef, fcoef;
+    DevBuf<float4> bcoef, fcoef;  // bcoef holds one more record, all zero, after the cells'
+    DevBuf<uint32_t> zmap;        // zero map of the drift records (see PathArgs)
+    uint32_t zshift = 0;
+    int zwords = 0;
     DevBuf<uint4> cvcoef;      // control-variate table (per slice and cell, half-precision corners)
     int cv_slices = 0;
     int cv_mode = 0;           // 0 off, 1 the table as set, 2 the model re-tabulated per estimate, 3 field gradient
@@ -260,6 +265,16 @@ std::vector<int> block_edges(int n, int parts)
 }
 
 
+// The zero map of a single instance's drift records (map null: launches without it).
+struct ZmapRef {
+    bool single = false;   // one instance: its tables go to the kernel as parameters
+    InstDev inst{};        // the instance's tables (host copy of inst[0])
+    const uint32_t* map = nullptr;   // null: no zero map
+    int words = 0;
+    uint32_t shift = 0;
+    uint32_t cell = 0;
+};
+
 InstDev inst_host(const sdd_ctx* c)
 {
     InstDev I{};
@@ -277,6 +292,19 @@ InstDev inst_host(const sdd_ctx* c)
     I.cv_slices = c->cv_slices;
     I.cvcoef = c->cvcoef.p;
     return I;
+}
+
+ZmapRef ctx_zmap(const sdd_ctx* c, bool use_map = true)
+{
+    ZmapRef z;
+    z.single = true;
+    z.inst = inst_host(c);
+    if (!use_map) return z;
+    z.map = c->zmap.p;
+    z.words = c->zwords;
+    z.shift = c->zshift;
+    z.cell = (uint32_t)((size_t)(c->nx - 1) * (c->ny - 1));
+    return z;
 }
 
 sdd_status upload_inst(sdd_ctx* c)
@@ -300,7 +328,8 @@ sdd_status prepare_parts(sdd_ctx* c, cudaStream_t s, bool w_part, bool f_part)
     }
     if (dw || df) {
         CU(c, launch_prep_cells(c->w.p, c->fld[c->cur][0].p, c->fld[c->cur][1].p, c->nx, c->ny,
-                                dw ? c->bcoef.p : nullptr, df ? c->fcoef.p : nullptr, c->d_status.p, s));
+                                dw ? c->bcoef.p : nullptr, df ? c->fcoef.p : nullptr, c->d_status.p, s, c->zmap.p,
+                                c->zshift));
     }
     if (w_part) c->dirty_w = false;
     if (f_part) c->dirty_fields = false;
@@ -315,7 +344,7 @@ sdd_status prepare(sdd_ctx* c, cudaStream_t s)
             CU(c, launch_winslow_faces(c->w.p, c->nx, c->ny, c->faces64.p, c->faces32.p, s));
         }
         CU(c, launch_prep_cells(c->w.p, c->fld[c->cur][0].p, c->fld[c->cur][1].p, c->nx, c->ny, c->bcoef.p,
-                                c->fcoef.p, c->d_status.p, s));
+                                c->fcoef.p, c->d_status.p, s, c->zmap.p, c->zshift));
         c->dirty_w = c->dirty_fields = false;
         return SDD_OK;
     }
@@ -400,7 +429,7 @@ sdd_status build_plan_segs(std::string* err, int sm_count, Plan& P, const std::v
 
     int64_t total = 0;
     for (int64_t k = 0; k < count; ++k) total += P.hp[k];
-    P.block = block_req ? block_req : 256;
+    P.block = std::min(block_req ? block_req : 256, path_kernel_max_block(exit_mode));
     const int per_sm = path_kernel_blocks_per_sm(exit_mode, record, P.block);
     P.grid = sm_count * per_sm;
     if (ppt_req) {
@@ -502,7 +531,8 @@ uint64_t shape_key(const std::vector<NodeSeg>& segs, int K, int exit_mode)
 sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const OutDev* outs, const OutDev& out0, double dt,
                        int K, uint64_t seed, uint32_t step_index, const uint32_t* step_ptr, int exit_mode,
                        const RecDev* rec, cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_b, int cv_slices = 0,
-                       const uint8_t* node_mask = nullptr, void* surv = nullptr, cudaEvent_t join = nullptr);
+                       const uint8_t* node_mask = nullptr, void* surv = nullptr, cudaEvent_t join = nullptr,
+                       ZmapRef zm = ZmapRef{});
 
 const TunedShape* find_tuned(const std::vector<TunedShape>& t, uint64_t key)
 {
@@ -515,7 +545,7 @@ const TunedShape* find_tuned(const std::vector<TunedShape>& t, uint64_t key)
 // keep the fastest: block sizes 128 / 256 / 512 x paths per task 32 .. 1024.
 sdd_status autotune_plan(std::string* err, int sm_count, const std::vector<NodeSeg>& segs, const InstDev* inst,
                          int ninst, int K, double dt, int exit_mode, cudaStream_t s, std::vector<TunedShape>& cache,
-                         TunedShape* best_out)
+                         TunedShape* best_out, ZmapRef zm = ZmapRef{})
 {
     int64_t count = 0;
     for (const NodeSeg& g : segs) count += g.count;
@@ -536,33 +566,41 @@ sdd_status autotune_plan(std::string* err, int sm_count, const std::vector<NodeS
     cudaEvent_t e0, e1;
     CU(err, cudaEventCreate(&e0));
     CU(err, cudaEventCreate(&e1));
-    TunedShape best{shape_key(segs, K, exit_mode), 256, 0, 1e30f};
+    TunedShape best{shape_key(segs, K, exit_mode), 256, 0, 1e30f, zm.map != nullptr ? 1 : 0};
     sdd_status st = SDD_OK;
-    for (int block : {128, 256, 512}) {
-        for (int ppt : {32, 64, 128, 256, 512, 1024}) {
-            Plan P;
-            st = build_plan_segs(err, sm_count, P, segs, ppt, block, exit_mode, false);
-            if (st != SDD_OK) break;
-            // one untimed run, then the mean of two timed runs
-            st = run_plan_on(err, P, inst, dout.p, OutDev{}, dt, K, 0x5EEDULL, 0, nullptr, exit_mode, nullptr, s,
-                             nullptr, nullptr);
-            if (st == SDD_OK && cudaEventRecord(e0, s) != cudaSuccess) st = fail(err, SDD_ECUDA, "event record");
-            for (int r = 0; r < 2 && st == SDD_OK; ++r)
-                st = run_plan_on(err, P, inst, dout.p, OutDev{}, dt, K, 0x5EEDULL + r, 0, nullptr, exit_mode, nullptr, s,
-                                 nullptr, nullptr);
-            if (st == SDD_OK && cudaEventRecord(e1, s) != cudaSuccess) st = fail(err, SDD_ECUDA, "event record");
-            if (st == SDD_OK && cudaEventSynchronize(e1) != cudaSuccess) st = fail(err, SDD_ECUDA, "event sync");
-            if (st != SDD_OK) break;
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            ms *= 0.5f;
-            if (ms < best.ms) {
-                best.block = block;
-                best.ppt = ppt;
-                best.ms = ms;
+    // a single instance: the kernel with the zero map and the one without (it saves the map's
+    // instructions where the drift has few zero cells)
+    for (int use_map = zm.map != nullptr ? 1 : 0; use_map >= 0 && st == SDD_OK; --use_map) {
+        ZmapRef z = zm;
+        if (!use_map) z.map = nullptr;
+        for (int block : {128, 256, 512}) {
+            if (block > path_kernel_max_block(exit_mode, false, z.single)) continue;
+            for (int ppt : {32, 64, 128, 256, 512, 1024}) {
+                Plan P;
+                st = build_plan_segs(err, sm_count, P, segs, ppt, block, exit_mode, false);
+                if (st != SDD_OK) break;
+                // one untimed run, then the mean of two timed runs
+                st = run_plan_on(err, P, inst, dout.p, OutDev{}, dt, K, 0x5EEDULL, 0, nullptr, exit_mode, nullptr, s,
+                                 nullptr, nullptr, 0, nullptr, nullptr, nullptr, z);
+                if (st == SDD_OK && cudaEventRecord(e0, s) != cudaSuccess) st = fail(err, SDD_ECUDA, "event record");
+                for (int r = 0; r < 2 && st == SDD_OK; ++r)
+                    st = run_plan_on(err, P, inst, dout.p, OutDev{}, dt, K, 0x5EEDULL + r, 0, nullptr, exit_mode,
+                                     nullptr, s, nullptr, nullptr, 0, nullptr, nullptr, nullptr, z);
+                if (st == SDD_OK && cudaEventRecord(e1, s) != cudaSuccess) st = fail(err, SDD_ECUDA, "event record");
+                if (st == SDD_OK && cudaEventSynchronize(e1) != cudaSuccess) st = fail(err, SDD_ECUDA, "event sync");
+                if (st != SDD_OK) break;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms *= 0.5f;
+                if (ms < best.ms) {
+                    best.block = block;
+                    best.ppt = ppt;
+                    best.ms = ms;
+                    best.zero_map = use_map;
+                }
             }
+            if (st != SDD_OK) break;
         }
-        if (st != SDD_OK) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -579,10 +617,10 @@ sdd_status autotune_plan(std::string* err, int sm_count, const std::vector<NodeS
 }
 
 sdd_status build_plan(sdd_ctx* c, Plan& P, const double* x, const double* y, const int64_t* np, int64_t count,
-                      int ppt_req, int block_req, int exit_mode, bool record)
+                      int ppt_req, int block_req, int exit_mode, bool record, uint32_t ctr0 = 0)
 {
     std::vector<NodeSeg> segs(1);
-    segs[0] = NodeSeg{x, y, np, count, 0, 0u};
+    segs[0] = NodeSeg{x, y, np, count, 0, ctr0};
     return build_plan_segs(&c->err, c->sm_count, P, segs, ppt_req, block_req, exit_mode, record);
 }
 
@@ -594,7 +632,7 @@ sdd_status build_plan(sdd_ctx* c, Plan& P, const double* x, const double* y, con
 sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const OutDev* outs, const OutDev& out0, double dt,
                        int K, uint64_t seed, uint32_t step_index, const uint32_t* step_ptr, int exit_mode,
                        const RecDev* rec, cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_b, int cv_slices,
-                       const uint8_t* node_mask, void* surv, cudaEvent_t join)
+                       const uint8_t* node_mask, void* surv, cudaEvent_t join, ZmapRef zm)
 {
     if (surv && rec) return fail(err, SDD_EINVAL, "per-path records with deferred survivor scores");
     if (P.nnodes == 0 || P.ntasks == 0) {
@@ -620,6 +658,16 @@ sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const Out
         if (rec) a.rec = *rec;
         a.node_mask = node_mask;
         a.surv = surv;
+        if (zm.single) {
+            a.single = 1;
+            a.one = zm.inst;
+            if (zm.map && zm.words > 0 && zm.words <= kZmapMaxWords) {
+                a.zmap = zm.map;
+                a.zwords = zm.words;
+                a.zshift = zm.shift;
+                a.zcell = zm.cell;
+            }
+        }
         const bool cv = cv_slices > 0;
         if (cv && cv_slices > K) return fail(err, SDD_EINVAL, "more control-variate slices than sub-steps per step");
         if (cv && exit_mode == 2)
@@ -627,15 +675,15 @@ sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const Out
         for (int q = 0; q <= kMaxCvSlices; ++q)
             a.cv_bound[q] = cv && q <= cv_slices ? (int32_t)(((int64_t)q * K + cv_slices - 1) / cv_slices) : K + 1;
         CU(err, cudaMemsetAsync(P.d_queue.p, 0, sizeof(int), s));
-        // the control-variate kernel is compiled for at most kCvMaxBlock threads per block
-        const int block = cv ? std::min(P.block, kCvMaxBlock) : P.block;
+        // each path kernel is compiled for at most path_kernel_max_block threads per block
+        const int block = std::min(P.block, path_kernel_max_block(exit_mode, cv, a.single != 0));
         const int64_t per_block = block / 32;
         int grid_max = P.grid;
-        if (cv) {
+        if (block != P.block || cv || a.single) {
             int dev = 0, sms = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            grid_max = sms * path_kernel_blocks_per_sm(exit_mode, rec != nullptr, block, true);
+            grid_max = sms * path_kernel_blocks_per_sm(exit_mode, rec != nullptr, block, cv, a.zwords, a.single != 0);
         }
         const int grid = (int)std::min<int64_t>(grid_max, std::max<int64_t>(1, (P.ntasks + per_block - 1) / per_block));
         if (ev_a) CU(err, cudaEventRecordWithFlags(ev_a, s, cudaEventRecordExternal));
@@ -674,15 +722,18 @@ sdd_status run_plan(sdd_ctx* c, Plan& P, double dt, int K, uint64_t seed, uint32
                     void* surv = nullptr, cudaEvent_t join = nullptr)
 {
     return run_plan_on(&c->err, P, c->d_inst.p, nullptr, out, dt, K, seed, step_index, step_ptr, exit_mode, rec, s,
-                       ev_a, ev_b, c->cv_mode ? c->cv_slices : 0, node_mask, surv, join);
+                       ev_a, ev_b, c->cv_mode ? c->cv_slices : 0, node_mask, surv, join, ctx_zmap(c, P.zero_map != 0));
 }
 
 // Launch shape for a plan: explicit requests win, else a tuned shape for this node set, else the heuristic.
+// zero_map (if non-null): the caller's request (0 automatic: the tuned choice, else on; 1 on; 2 off) in,
+// 1 (use the zero map) or 0 out.
 void pick_shape(const std::vector<TunedShape>& cache, const std::vector<NodeSeg>& segs, int K, int exit_mode,
-                int* ppt, int* block)
+                int* ppt, int* block, int* zero_map = nullptr)
 {
-    if (*ppt || *block) return;
     const TunedShape* t = find_tuned(cache, shape_key(segs, K, exit_mode));
+    if (zero_map) *zero_map = *zero_map == 0 ? (t ? t->zero_map : 1) : (*zero_map == 1 ? 1 : 0);
+    if (*ppt || *block) return;
     if (t) {
         *ppt = t->ppt;
         *block = t->block;
@@ -1213,7 +1264,8 @@ sdd_status samples_into(sdd_ctx* c, const sdd_sample_params* p, float* feats, fl
         CU(c, cudaMemcpyAsync(c->cv_sxy.p, xs.data(), M * sizeof(double), cudaMemcpyHostToDevice, c->stream));
         CU(c, cudaMemcpyAsync(c->cv_sxy.p + M, ys.data(), M * sizeof(double), cudaMemcpyHostToDevice, c->stream));
         if ((st = run_plan_on(&c->err, c->sample_plan, c->d_inst.p, nullptr, out, p->dt, k, p->seed, kSampleStepWord,
-                              nullptr, p->exit_mode, nullptr, c->stream, nullptr, nullptr, 0)) != SDD_OK)
+                              nullptr, p->exit_mode, nullptr, c->stream, nullptr, nullptr, 0, nullptr, nullptr,
+                              nullptr, ctx_zmap(c))) != SDD_OK)
             return st;
         CU(c, launch_cv_scatter(c->cv_sxy.p, c->cv_sxy.p + M, out.mean_xi, out.mean_eta, c->cv_nfa.p, c->nx, c->ny, k,
                                 K, (int)M, feats, targets, c->stream));
@@ -1336,7 +1388,11 @@ sdd_status sdd_init(sdd_ctx** out, const sdd_grid* g, const float* w, const doub
         for (int f = 0; f < 2; ++f) INIT_CU(c->fld[b][f].alloc(N));
     INIT_CU(c->faces64.alloc(faces_len(c)));
     INIT_CU(c->faces32.alloc(faces_len(c)));
-    INIT_CU(c->bcoef.alloc(2 * cells));
+    INIT_CU(c->bcoef.alloc(2 * (cells + 1)));
+    INIT_CU(cudaMemset(c->bcoef.p + 2 * cells, 0, 2 * sizeof(float4)));   // the all-zero record
+    c->zshift = zmap_shift((long long)cells);
+    c->zwords = zmap_words((long long)cells, c->zshift);
+    INIT_CU(c->zmap.alloc(c->zwords));
     INIT_CU(c->fcoef.alloc(2 * cells));
     INIT_CU(c->d_status.alloc(1));
     INIT_CU(c->d_step.alloc(1));
@@ -1481,15 +1537,17 @@ static sdd_status mc_common(sdd_ctx* c, const sdd_nodes* nodes, const sdd_mc_par
     int K = 0;
     if (!valid_params(c, p->dt, p->Dt, p->exit_mode, &K))
         return fail(c, SDD_EINVAL, "dt, Dt or exit_mode rejected (Dt / dt must be an integer in [1, 2^20])");
-    int ppt = p->paths_per_task, block = p->block_threads;
+    if (p->zero_map < 0 || p->zero_map > 2) return fail(c, SDD_EINVAL, "zero_map must be 0, 1 or 2");
+    int ppt = p->paths_per_task, block = p->block_threads, zmap = p->zero_map;
     {
         std::vector<NodeSeg> segs(1);
-        segs[0] = NodeSeg{nodes->x, nodes->y, nodes->n_paths, nodes->count, 0, 0u};
-        pick_shape(c->tuned, segs, K, p->exit_mode, &ppt, &block);
+        segs[0] = NodeSeg{nodes->x, nodes->y, nodes->n_paths, nodes->count, 0, p->node_word0};
+        pick_shape(c->tuned, segs, K, p->exit_mode, &ppt, &block, &zmap);
     }
     sdd_status st = build_plan(c, c->mc_plan, nodes->x, nodes->y, nodes->n_paths, nodes->count, ppt, block,
-                               p->exit_mode, rec != nullptr);
+                               p->exit_mode, rec != nullptr, p->node_word0);
     if (st != SDD_OK) return st;
+    c->mc_plan.zero_map = zmap;
     if ((st = prepare(c, c->stream)) != SDD_OK) return st;
     if ((st = enqueue_cv_refresh(c, K, c->stream)) != SDD_OK) return st;
     RecDev rd{};
@@ -1773,14 +1831,16 @@ sdd_status sdd_autotune(sdd_ctx* c, const sdd_nodes* nodes, const sdd_mc_params*
     sdd_status st = prepare(c, c->stream);
     if (st != SDD_OK) return st;
     std::vector<NodeSeg> segs(1);
-    segs[0] = NodeSeg{nodes->x, nodes->y, nodes->n_paths, nodes->count, 0, 0u};
+    segs[0] = NodeSeg{nodes->x, nodes->y, nodes->n_paths, nodes->count, 0, p->node_word0};
     TunedShape best{};
-    st = autotune_plan(&c->err, c->sm_count, segs, c->d_inst.p, 1, K, p->dt, p->exit_mode, c->stream, c->tuned, &best);
+    st = autotune_plan(&c->err, c->sm_count, segs, c->d_inst.p, 1, K, p->dt, p->exit_mode, c->stream, c->tuned, &best,
+                       ctx_zmap(c));
     if (st != SDD_OK) return st;
     if (out) {
         out->block_threads = best.block;
         out->paths_per_task = best.ppt;
         out->ms = best.ms;
+        out->zero_map = best.zero_map ? 1 : 2;
     }
     return SDD_OK;
 }
@@ -1886,7 +1946,8 @@ static sdd_status capture_step(sdd_ctx* c, const sdd_step_params* p, int K, int 
     }
     if (st == SDD_OK && c->pipe) {
         // the drift records; the face data come from the third branch forked above
-        cu(launch_prep_cells(c->w.p, nullptr, nullptr, c->nx, c->ny, c->bcoef.p, nullptr, c->d_status.p, s));
+        cu(launch_prep_cells(c->w.p, nullptr, nullptr, c->nx, c->ny, c->bcoef.p, nullptr, c->d_status.p, s, c->zmap.p,
+                             c->zshift));
         if (!c->user_faces && p->exit_mode != 0) cu(cudaStreamWaitEvent(s, c->fev[1], 0));
         c->dirty_w = false;
     } else if (st == SDD_OK) {
@@ -1979,14 +2040,15 @@ sdd_status sdd_step(sdd_ctx* c, const sdd_step_params* p)
             if (st0 != SDD_OK) return st0;
             TunedShape best{};
             st0 = autotune_plan(&c->err, c->sm_count, segs, c->d_inst.p, 1, K, p->dt, p->exit_mode, c->stream, c->tuned,
-                                &best);
+                                &best, ctx_zmap(c));
             if (st0 != SDD_OK) return st0;
         }
-        int ppt = 0, block = 0;
-        pick_shape(c->tuned, segs, K, p->exit_mode, &ppt, &block);
+        int ppt = 0, block = 0, zmap = 0;
+        pick_shape(c->tuned, segs, K, p->exit_mode, &ppt, &block, &zmap);
         sdd_status st = build_plan(c, c->step_plan, c->iface_x.data(), c->iface_y.data(), np.data(),
                                    (int64_t)np.size(), ppt, block, p->exit_mode, false);
         if (st != SDD_OK) return st;
+        c->step_plan.zero_map = zmap;
         CU(c, cudaStreamSynchronize(c->stream));
         // pipelined steps where the solve's iterations are one launch and the
         // paths do not read the fields (the field-gradient control variate does)
@@ -2333,7 +2395,7 @@ sdd_status sdd_batch_interface_mc(sdd_batch* b, const sdd_nodes* nodes, const sd
         return fail(&b->err, SDD_EINVAL, "dt, Dt or exit_mode rejected (Dt / dt must be an integer in [1, 2^20])");
     const int32_t n = (int32_t)b->ctxs.size();
     std::vector<NodeSeg> segs(n);
-    uint32_t ctr = 0;
+    uint32_t ctr = p->node_word0;
     for (int32_t k = 0; k < n; ++k) {
         if (nodes[k].count > 0 && (!nodes[k].x || !nodes[k].y || !nodes[k].n_paths))
             return fail(&b->err, SDD_EINVAL, "null node array for instance %d", k);
@@ -2428,7 +2490,7 @@ sdd_status sdd_batch_autotune(sdd_batch* b, const sdd_nodes* nodes, const sdd_mc
     if (!valid_params(nullptr, p->dt, p->Dt, p->exit_mode, &K)) return fail(&b->err, SDD_EINVAL, "dt, Dt or exit_mode rejected");
     const int32_t n = (int32_t)b->ctxs.size();
     std::vector<NodeSeg> segs(n);
-    uint32_t ctr = 0;
+    uint32_t ctr = p->node_word0;
     for (int32_t k = 0; k < n; ++k) {
         if (nodes[k].count > 0 && (!nodes[k].x || !nodes[k].y || !nodes[k].n_paths))
             return fail(&b->err, SDD_EINVAL, "null node array for instance %d", k);
@@ -2447,6 +2509,7 @@ sdd_status sdd_batch_autotune(sdd_batch* b, const sdd_nodes* nodes, const sdd_mc
         out->block_threads = best.block;
         out->paths_per_task = best.ppt;
         out->ms = best.ms;
+        out->zero_map = best.zero_map ? 1 : 2;
     }
     return SDD_OK;
 }

@@ -102,7 +102,25 @@ struct PathArgs {
     RecDev rec;
     const uint8_t* node_mask; // if non-null, only nodes with a nonzero entry run their paths
     void* surv;               // if non-null, survivors and plain exits leave records here, scored later (rec0 + path)
+    // zero map of the drift records (single-instance launches; zwords = 0: none): bit k of word k / 32
+    // set when a drift record of cells [k 2^zshift, (k + 1) 2^zshift) is nonzero; record zcell is all zero
+    const uint32_t* zmap;
+    int32_t zwords;
+    uint32_t zshift;
+    uint32_t zcell;
+    InstDev one;              // single: the one instance's tables (inst[0]), read as parameters
+    int32_t single;           // 1: every task is of instance 0 and `one` holds its tables
 };
+
+// The zero map's size: at most kZmapMaxWords words (16 KB of shared memory per block of the path kernel).
+constexpr int kZmapMaxWords = 4096;
+inline uint32_t zmap_shift(long long cells)
+{
+    uint32_t s = 0;
+    while (((cells + (1LL << s) - 1) >> s) > 32LL * kZmapMaxWords) ++s;
+    return s;
+}
+inline int zmap_words(long long cells, uint32_t shift) { return (int)((((cells + (1LL << shift) - 1) >> shift) + 31) / 32); }
 
 struct FinalArgs {
     const InstDev* inst;
@@ -137,12 +155,17 @@ cudaError_t launch_paths(const PathArgs& a, int exit_mode, bool record, int grid
 // exit_mode 0 with an even number of sub-steps has its own kernel (no odd last pair)
 cudaError_t launch_finalize(const FinalArgs& a, cudaStream_t s);
 cudaError_t launch_score_surv(const ScoreArgs& a, bool cv, cudaStream_t s);
-int path_kernel_blocks_per_sm(int exit_mode, bool record, int block, bool cv = false);
+int path_kernel_blocks_per_sm(int exit_mode, bool record, int block, bool cv = false, int zwords = 0,
+                              bool single = false);
+// the largest block the path kernel of this exit mode is compiled for (single: one instance)
+int path_kernel_max_block(int exit_mode, bool cv = false, bool single = false);
 
 // Cell records of the drift (from w; bcoef null: skipped) and of the fields
-// (from xi, eta; fcoef null: skipped).
+// (from xi, eta; fcoef null: skipped); with the drift records, if zmap is
+// non-null, their zero map (zmap_words(cells, zshift) words, see PathArgs).
 cudaError_t launch_prep_cells(const float* w, const double* xi, const double* eta, int nx, int ny, float4* bcoef,
-                              float4* fcoef, int* status, cudaStream_t s);
+                              float4* fcoef, int* status, cudaStream_t s, uint32_t* zmap = nullptr,
+                              uint32_t zshift = 0);
 // The paper's boundary data from w (faces64) and, if faces32 is non-null, its single-precision copy.
 cudaError_t launch_winslow_faces(const float* w, int nx, int ny, double* faces64, float* faces32, cudaStream_t s);
 cudaError_t launch_cv_cells(const double* grad, int slices, int nx, int ny, uint4* cvcoef, cudaStream_t s);

@@ -196,14 +196,44 @@ __global__ void k_faces32(const double* __restrict__ f64, float* __restrict__ f3
     if (k < n) f32[k] = (float)f64[k];
 }
 
+// Zero map of the drift records: one block per map word (32 segments of 2^zshift consecutive cells in
+// row-major order); bit k set when a record of segment k has a nonzero coefficient. The last word's bits
+// past the last cell stay clear (no path reaches those cells).
+__global__ void __launch_bounds__(256) k_drift_zmap(const float4* __restrict__ bcoef, long long cells,
+                                                    uint32_t zshift, uint32_t* __restrict__ zmap)
+{
+    __shared__ int nz[32];
+    if (threadIdx.x < 32) nz[threadIdx.x] = 0;
+    __syncthreads();
+    const long long c0 = (long long)blockIdx.x << (zshift + 5);
+    const long long span = 32LL << zshift;
+    for (long long k = threadIdx.x; k < span; k += blockDim.x) {
+        const long long c = c0 + k;
+        if (c >= cells) break;
+        const float4 lo = bcoef[2 * c], hi = bcoef[2 * c + 1];
+        if (lo.x != 0.f || lo.y != 0.f || lo.z != 0.f || lo.w != 0.f || hi.x != 0.f || hi.y != 0.f ||
+            hi.z != 0.f || hi.w != 0.f)
+            nz[k >> zshift] = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const unsigned word = __ballot_sync(0xffffffffu, nz[threadIdx.x] != 0);
+        if (threadIdx.x == 0) zmap[blockIdx.x] = word;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_prep_cells(const float* w, const double* xi, const double* eta, int nx, int ny, float4* bcoef,
-                              float4* fcoef, int* status, cudaStream_t s)
+                              float4* fcoef, int* status, cudaStream_t s, uint32_t* zmap, uint32_t zshift)
 {
     const dim3 block(PREP_TX, PREP_TY);
     const dim3 grid((nx - 1 + PREP_TX - 1) / PREP_TX, (ny - 1 + PREP_TY - 1) / PREP_TY);
     k_prep_cells<<<grid, block, 0, s>>>(w, xi, eta, nx, ny, bcoef, fcoef, status);
+    if (bcoef && zmap) {
+        const long long cells = (long long)(nx - 1) * (ny - 1);
+        k_drift_zmap<<<zmap_words(cells, zshift), 256, 0, s>>>(bcoef, cells, zshift, zmap);
+    }
     return cudaGetLastError();
 }
 

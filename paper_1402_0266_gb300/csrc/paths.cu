@@ -27,6 +27,8 @@
 // per-node reduction.
 #include <cuda_fp16.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "common.cuh"
@@ -43,7 +45,6 @@ constexpr unsigned FULL = 0xffffffffu;
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
 struct Cell {
-    const float4* p;  // the cell's two coefficient records
     float2 st;        // local coordinates (s, t) in [0, 1)
     uint32_t idx;     // row-major cell index
 };
@@ -52,7 +53,7 @@ struct Cell {
 // for 0 <= g < 2^23, (g + 2^23) rounded down is 2^23 + floor(g) exactly, and
 // its bits are 0x4B000000 + floor(g); cell_bias removes that offset from the
 // row-major cell index in 32-bit wrap-around arithmetic.
-__device__ __forceinline__ Cell locate(const InstDev& I, const float4* base, float2 pos)
+__device__ __forceinline__ Cell locate(const InstDev& I, float2 pos)
 {
     float2 g = __fmul2_rn(pos, f2(I.sx, I.sy));
     g.x = fminf(g.x, I.gxmax);
@@ -62,9 +63,31 @@ __device__ __forceinline__ Cell locate(const InstDev& I, const float4* base, flo
     const float2 fl = __fadd2_rn(t, f2(-8388608.0f, -8388608.0f));    // floor(g), exact
     Cell c;
     c.st = __ffma2_rn(fl, f2(-1.0f, -1.0f), g);                        // g - floor(g), exact
-    c.p = base + 2 * (size_t)cell;
     c.idx = cell;
     return c;
+}
+
+// The two coefficient records of cell idx in a table of cell records.
+__device__ __forceinline__ const float4* rec2(const float4* base, uint32_t idx) { return base + 2 * (size_t)idx; }
+
+// The drift records of a cell. With the zero map (ZM), a cell of a segment
+// whose drift records are all zero (w constant around it: b = -grad w / w = 0
+// exactly) reads the all-zero record at index zcell instead: the same values,
+// so the same arithmetic and results, but every lane of a warp that is in such
+// a segment reads the same 32 bytes, one L1 wavefront for all of them, where
+// each lane's own cell would cost one wavefront per lane. zsm: the map in
+// shared memory, bit k of word k / 32 set when a record of cells
+// [k 2^zshift, (k + 1) 2^zshift) is nonzero.
+template <bool ZM>
+__device__ __forceinline__ const float4* drift_rec(const InstDev& I, const Cell& c, const uint32_t* zsm,
+                                                   const PathArgs& a)
+{
+    uint32_t idx = c.idx;
+    if (ZM) {
+        const uint32_t seg = idx >> a.zshift;
+        if (!((zsm[seg >> 5] >> (seg & 31u)) & 1u)) idx = a.zcell;
+    }
+    return rec2(I.bcoef, idx);
 }
 
 // A cell's two records in one 256-bit read-only load (records are 32-byte
@@ -280,9 +303,29 @@ constexpr int WARM_MIN = 8;
 // MODE 0: the paper's test, sub-step pairs; MODE 1: with the bridge test;
 // MODE 2: as MODE 0 when K is even (every pair has both sub-steps).
 // CV: subtract the control variate sum_j G(s_j, X_j) . sqrt(2) dW_j from both scores.
-template <int MODE, bool RECORD, bool CV>
-__global__ void __launch_bounds__(CV ? kCvMaxBlock : 512, CV ? 3 : 2) k_paths(const PathArgs a)
+// Kernel variants by where the tables come from: VAR_MULTI, each task's
+// instance from the instance table (batches); VAR_ONE, a single instance whose
+// tables are kernel parameters (no registers held for them); VAR_ZM, VAR_ONE
+// with the zero map of the drift records. Launch shapes: a single instance's
+// kernel fits 40 registers (48 warps per SM; 64 with the control variate),
+// the batch kernel 64 (32 warps; 80 with the control variate).
+constexpr int VAR_MULTI = 0, VAR_ONE = 1, VAR_ZM = 2;
+constexpr int kOneMaxBlock = 256;
+constexpr int paths_max_block(bool cv, int var) { return cv ? kCvMaxBlock : var != VAR_MULTI ? kOneMaxBlock : 512; }
+constexpr int paths_min_blocks(bool cv, int var)
 {
+    return cv ? (var != VAR_MULTI ? 4 : 3) : (var != VAR_MULTI ? 6 : 2);
+}
+
+template <int MODE, bool RECORD, bool CV, int VAR>
+__global__ void __launch_bounds__(paths_max_block(CV, VAR), paths_min_blocks(CV, VAR)) k_paths(const PathArgs a)
+{
+    constexpr bool ZM = VAR == VAR_ZM;
+    extern __shared__ uint32_t zsm[];   // the zero map of the drift records (ZM)
+    if (ZM) {
+        for (int k = threadIdx.x; k < a.zwords; k += blockDim.x) zsm[k] = a.zmap[k];
+        __syncthreads();
+    }
     const int lane = threadIdx.x & 31;
     const unsigned below = (1u << lane) - 1u;
     const uint32_t step = a.step_ptr ? *a.step_ptr : a.step_index;
@@ -302,7 +345,10 @@ __global__ void __launch_bounds__(CV ? kCvMaxBlock : 512, CV ? 3 : 2) k_paths(co
         const Task task = a.tasks[t];
         if (a.node_mask && !a.node_mask[task.node]) continue;   // not a key point this step
         const NodeDev& nd = a.nodes[task.node];
-        const InstDev I = a.inst[nd.inst];
+        // a single instance's tables come from the kernel parameters (no registers held for them)
+        InstDev Iloc;
+        if (VAR == VAR_MULTI) Iloc = a.inst[nd.inst];
+        const InstDev& I = VAR != VAR_MULTI ? a.one : Iloc;
         const float x0 = nd.xf, y0 = nd.yf;
         const uint32_t nctr = nd.ctr;
         const int end = task.path0 + task.npaths;
@@ -340,9 +386,9 @@ __global__ void __launch_bounds__(CV ? kCvMaxBlock : 512, CV ? 3 : 2) k_paths(co
                 const bool warm = m < 0;   // draw -1: the pass draws the path's first normals
                 float4 seg = make_float4(-1.f, 0.f, 0.f, 0.f);   // a plain exit's sub-step, scored later
                 // sub-step A: gather, then the next draw's first rounds while the gather is in flight
-                const Cell cA = locate(I, I.bcoef, pos);
+                const Cell cA = locate(I, pos);
                 float4 gA0, gA1;
-                load_cell(cA.p, gA0, gA1);
+                load_cell(drift_rec<ZM>(I, cA, zsm, a), gA0, gA1);
                 if (CV) {
                     const int j = PAIRS ? 2 * m : m;
                     if (j >= cvn) cvn = a.cv_bound[++cvq + 1];
@@ -355,9 +401,9 @@ __global__ void __launch_bounds__(CV ? kCvMaxBlock : 512, CV ? 3 : 2) k_paths(co
                 if (PAIRS) {
                     // sub-step B from the point A reached (or from X_j when A left: harmless, in bounds)
                     const float2 pq = outA ? pos : pa;
-                    const Cell cB = locate(I, I.bcoef, pq);
+                    const Cell cB = locate(I, pq);
                     float4 gB0, gB1;
-                    load_cell(cB.p, gB0, gB1);
+                    load_cell(drift_rec<ZM>(I, cB, zsm, a), gB0, gB1);
                     philox_rounds_rk<5, 10>(r, a.keys);
                     float2 nA, nB;
                     box_muller2(r, a.bm_scale, nA, nB);
@@ -429,9 +475,9 @@ __global__ void __launch_bounds__(CV ? kCvMaxBlock : 512, CV ? 3 : 2) k_paths(co
                                            cvx.x + cvx.y, cve.x + cve.y);
                         } else {
                             // survived the mesh step: xi, eta of its start at the end point
-                            const Cell c = locate(I, I.fcoef, pos);
+                            const Cell c = locate(I, pos);
                             float4 f0, f1;
-                            load_cell(c.p, f0, f1);
+                            load_cell(rec2(I.fcoef, c.idx), f0, f1);
                             const float2 v = eval2(f0, f1, c.st);
                             yxi = v.x;
                             yeta = v.y;
@@ -561,9 +607,9 @@ __global__ void __launch_bounds__(512, 2) k_paths_exp(const PathArgs a)
                 float2 z;
                 box_muller(r.x, r.y, -2.77258872223978123767f * tau, z.x, z.y);   // -4 ln 2 tau: sqrt(2 tau) N(0,1)
                 const float ub = uniform_pos(r.z);
-                const Cell c = locate(I, I.bcoef, pos);
+                const Cell c = locate(I, pos);
                 float4 g0, g1;
-                load_cell(c.p, g0, g1);
+                load_cell(rec2(I.bcoef, c.idx), g0, g1);
                 const float2 pn = em(g0, g1, c.st, pos, f2(tau, tau), z);
                 bool done = false;
                 int code = -1;
@@ -594,9 +640,9 @@ __global__ void __launch_bounds__(512, 2) k_paths_exp(const PathArgs a)
                             put_record<false>(a.surv, nd.rec0 + path, make_float4(pos.x, pos.y, rec_nan(), 0.f), 0.f,
                                               0.f);
                         } else {
-                            const Cell cf = locate(I, I.fcoef, pos);
+                            const Cell cf = locate(I, pos);
                             float4 f0, f1;
-                            load_cell(cf.p, f0, f1);
+                            load_cell(rec2(I.fcoef, cf.idx), f0, f1);
                             const float2 v = eval2(f0, f1, cf.st);
                             yxi = v.x;
                             yeta = v.y;
@@ -719,8 +765,8 @@ __global__ void __launch_bounds__(SCORE_THREADS, 1024 / SCORE_THREADS) k_score_s
 #pragma unroll
         for (int u = 0; u < SCORE_BATCH; ++u) {
             if (r[u].x >= 0.f && isnan(r[u].z)) {
-                const Cell c = locate(I, I.fcoef, f2(r[u].x, r[u].y));
-                load_cell(c.p, f0[u], f1[u]);
+                const Cell c = locate(I, f2(r[u].x, r[u].y));
+                load_cell(rec2(I.fcoef, c.idx), f0[u], f1[u]);
                 st[u] = c.st;
             } else if (r[u].x >= 0.f) {
                 int face, k;
@@ -909,33 +955,76 @@ __global__ void k_rng_draw(uint64_t seed, const uint32_t* __restrict__ ctrs, lon
     }
 }
 
-template <int MODE, bool RECORD, bool CV>
+template <int MODE, bool RECORD, bool CV, int VAR>
 const void* kernel_ptr()
 {
-    return (const void*)k_paths<MODE, RECORD, CV>;
+    return (const void*)k_paths<MODE, RECORD, CV, VAR>;
 }
 
-template <bool CV>
+template <bool CV, int VAR>
 const void* pick_cv(int mode, bool record)
 {
     if (mode == 3) return record ? (const void*)k_paths_exp<true> : (const void*)k_paths_exp<false>;
-    if (mode == 0) return record ? kernel_ptr<0, true, CV>() : kernel_ptr<0, false, CV>();
-    if (mode == 2) return record ? kernel_ptr<2, true, CV>() : kernel_ptr<2, false, CV>();
-    return record ? kernel_ptr<1, true, CV>() : kernel_ptr<1, false, CV>();
+    if (mode == 0) return record ? kernel_ptr<0, true, CV, VAR>() : kernel_ptr<0, false, CV, VAR>();
+    if (mode == 2) return record ? kernel_ptr<2, true, CV, VAR>() : kernel_ptr<2, false, CV, VAR>();
+    return record ? kernel_ptr<1, true, CV, VAR>() : kernel_ptr<1, false, CV, VAR>();
 }
 
-const void* pick(int mode, bool record, bool cv = false) { return cv ? pick_cv<true>(mode, record) : pick_cv<false>(mode, record); }
+template <int VAR>
+const void* pick_var(int mode, bool record, bool cv)
+{
+    return cv ? pick_cv<true, VAR>(mode, record) : pick_cv<false, VAR>(mode, record);
+}
+
+const void* pick(int mode, bool record, bool cv, int var)
+{
+    if (var == VAR_ZM) return pick_var<VAR_ZM>(mode, record, cv);
+    if (var == VAR_ONE) return pick_var<VAR_ONE>(mode, record, cv);
+    return pick_var<VAR_MULTI>(mode, record, cv);
+}
+
+// The variant of a launch: the zero map where the arguments carry one, else the single instance's
+// tables as parameters where the launch has one instance.
+int path_var(const PathArgs& a)
+{
+    if (a.zwords > 0 && a.zmap != nullptr) return VAR_ZM;
+    return a.single ? VAR_ONE : VAR_MULTI;
+}
 
 }  // namespace
 
-int path_kernel_blocks_per_sm(int exit_mode, bool record, int block, bool cv)
+static void prefer_l1();
+
+int path_kernel_max_block(int exit_mode, bool cv, bool single)
 {
+    return exit_mode == 2 ? 512 : paths_max_block(cv, single ? VAR_ONE : VAR_MULTI);
+}
+
+int path_kernel_blocks_per_sm(int exit_mode, bool record, int block, bool cv, int zwords, bool single)
+{
+    prefer_l1();
     int n = 0;
     // the even-K kernel has the same footprint class; size the grid for the larger of the two
     const int mode = exit_mode == 2 ? 3 : exit_mode == 1 ? 1 : 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(mode, record, cv), block, 0) != cudaSuccess)
+    const int var = zwords > 0 ? VAR_ZM : single ? VAR_ONE : VAR_MULTI;
+    const size_t smem = var == VAR_ZM && mode != 3 ? sizeof(uint32_t) * (size_t)zwords : 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(mode, record, cv, var), block, smem) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
+}
+
+// The shared-memory carveout (percent of the SM's largest) that holds `blocks` blocks of `smem`
+// dynamic bytes each, so that the zero map costs the launch no occupancy and L1 keeps the rest.
+static unsigned carveout_pct(int blocks, size_t smem)
+{
+    int dev = 0, most = 0, resv = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&most, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (most <= 0) return 100;
+    const double need = (double)blocks * (double)(smem + (size_t)resv);
+    const int pct = (int)std::ceil(100.0 * need / (double)most);
+    return (unsigned)std::min(100, std::max(0, pct));
 }
 
 static int kernel_mode(int exit_mode, int K)
@@ -944,7 +1033,9 @@ static int kernel_mode(int exit_mode, int K)
     return exit_mode == 1 ? 1 : ((K & 1) == 0 ? 2 : 0);
 }
 
-// The path kernel keeps no data in shared memory: give L1 the whole carveout.
+// Without the zero map the path kernel keeps no data in shared memory: give L1 the whole carveout.
+// The kernels with the map prefer the largest carveout (so that occupancy queries see the blocks the
+// registers allow); each launch then asks, by a launch attribute, for the carveout its blocks need.
 static void prefer_l1()
 {
     static bool done = false;
@@ -953,29 +1044,64 @@ static void prefer_l1()
     for (int mode : {0, 1, 2, 3})
         for (bool rec : {false, true})
             for (bool cv : {false, true})
-                cudaFuncSetAttribute(pick(mode, rec, cv), cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+                for (int var : {VAR_MULTI, VAR_ONE, VAR_ZM})
+                    cudaFuncSetAttribute(pick(mode, rec, cv, var), cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         var == VAR_ZM && mode != 3 ? 100 : 0);
     cudaGetLastError();
 }
 
-template <bool CV>
-static void launch_mode(const PathArgs& a, int mode, bool record, int grid, int block, cudaStream_t s)
+// A launch of a kernel with the zero map: dynamic shared memory for the map, and the carveout that the
+// blocks the registers allow need (with less, the driver may fit fewer blocks; with more, L1 shrinks).
+// The preference is the function's, set before each launch (launches of one function inside a step
+// graph share one shape, so they need the same value).
+static void launch_zm(const void* fn, const PathArgs& a, int grid, int block, size_t smem, cudaStream_t s)
 {
+    struct Pref {
+        const void* fn;
+        int block;
+        size_t smem;
+        int pct;
+    };
+    static Pref cache[64];
+    static int ncache = 0;
+    int pct = -1;
+    for (int k = 0; k < ncache; ++k)
+        if (cache[k].fn == fn && cache[k].block == block && cache[k].smem == smem) pct = cache[k].pct;
+    if (pct < 0) {
+        int n = 1;
+        cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, smem) != cudaSuccess || n < 1) n = 1;
+        pct = (int)carveout_pct(n, smem);
+        if (ncache < 64) cache[ncache++] = Pref{fn, block, smem, pct};
+    }
+    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    void* args[] = {(void*)&a};
+    cudaLaunchKernel(fn, dim3((unsigned)grid), dim3((unsigned)block), args, smem, s);
+}
+
+template <bool CV, int VAR>
+static void launch_mode(const PathArgs& a, int mode, bool record, int grid, int block, size_t smem, cudaStream_t s)
+{
+    if (VAR == VAR_ZM && mode != 3) {
+        launch_zm(pick(mode, record, CV, VAR_ZM), a, grid, block, smem, s);
+        return;
+    }
     switch (mode) {
     case 3:
         if (record) k_paths_exp<true><<<grid, block, 0, s>>>(a);
         else k_paths_exp<false><<<grid, block, 0, s>>>(a);
         break;
     case 0:
-        if (record) k_paths<0, true, CV><<<grid, block, 0, s>>>(a);
-        else k_paths<0, false, CV><<<grid, block, 0, s>>>(a);
+        if (record) k_paths<0, true, CV, VAR><<<grid, block, smem, s>>>(a);
+        else k_paths<0, false, CV, VAR><<<grid, block, smem, s>>>(a);
         break;
     case 2:
-        if (record) k_paths<2, true, CV><<<grid, block, 0, s>>>(a);
-        else k_paths<2, false, CV><<<grid, block, 0, s>>>(a);
+        if (record) k_paths<2, true, CV, VAR><<<grid, block, smem, s>>>(a);
+        else k_paths<2, false, CV, VAR><<<grid, block, smem, s>>>(a);
         break;
     default:
-        if (record) k_paths<1, true, CV><<<grid, block, 0, s>>>(a);
-        else k_paths<1, false, CV><<<grid, block, 0, s>>>(a);
+        if (record) k_paths<1, true, CV, VAR><<<grid, block, smem, s>>>(a);
+        else k_paths<1, false, CV, VAR><<<grid, block, smem, s>>>(a);
     }
 }
 
@@ -984,8 +1110,18 @@ cudaError_t launch_paths(const PathArgs& a, int exit_mode, bool record, int grid
 {
     prefer_l1();
     const int mode = kernel_mode(exit_mode, a.K);
-    if (cv) launch_mode<true>(a, mode, record, grid, block, s);
-    else launch_mode<false>(a, mode, record, grid, block, s);
+    const int var = path_var(a);
+    const size_t smem = var == VAR_ZM && mode != 3 ? sizeof(uint32_t) * (size_t)a.zwords : 0;
+    if (var == VAR_ZM) {
+        if (cv) launch_mode<true, VAR_ZM>(a, mode, record, grid, block, smem, s);
+        else launch_mode<false, VAR_ZM>(a, mode, record, grid, block, smem, s);
+    } else if (var == VAR_ONE) {
+        if (cv) launch_mode<true, VAR_ONE>(a, mode, record, grid, block, 0, s);
+        else launch_mode<false, VAR_ONE>(a, mode, record, grid, block, 0, s);
+    } else {
+        if (cv) launch_mode<true, VAR_MULTI>(a, mode, record, grid, block, 0, s);
+        else launch_mode<false, VAR_MULTI>(a, mode, record, grid, block, 0, s);
+    }
     return cudaGetLastError();
 }
 

@@ -115,8 +115,9 @@ sdd_status sdd_interface_mc_static(const sdd_fields* f, const sdd_nodes* nodes, 
     if (kr < 1.0 || kr > (double)(1 << 20) || std::fabs(kr - kq) > 1e-9 * kq) return SDD_EINVAL;
     if (p->exit_mode != 0 && p->exit_mode != 1 && p->exit_mode != 2) return SDD_EINVAL;
     if (p->paths_per_task < 0 || (p->paths_per_task % 32) != 0) return SDD_EINVAL;
-    const int block = p->block_threads ? p->block_threads : 256;
-    if (block != 64 && block != 128 && block != 256 && block != 512) return SDD_EINVAL;
+    const int block_req = p->block_threads ? p->block_threads : 256;
+    if (block_req != 64 && block_req != 128 && block_req != 256 && block_req != 512) return SDD_EINVAL;
+    const int block = std::min(block_req, path_kernel_max_block(p->exit_mode));
     const int K = (int)kr;
     for (int64_t k = 0; k < count; ++k) {
         if (!(nodes->x[k] >= 0.0 && nodes->x[k] <= 1.0 && nodes->y[k] >= 0.0 && nodes->y[k] <= 1.0)) return SDD_EINVAL;
@@ -175,7 +176,7 @@ sdd_status sdd_interface_mc_static(const sdd_fields* f, const sdd_nodes* nodes, 
         nd.xf = (float)nd.x;
         nd.yf = (float)nd.y;
         nd.inst = 0;
-        nd.ctr = (uint32_t)k;
+        nd.ctr = p->node_word0 + (uint32_t)k;
         nd.n_paths = (int32_t)nodes->n_paths[k];
         nd.local = (int32_t)k;
         nd.rec0 = rec;

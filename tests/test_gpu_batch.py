@@ -103,7 +103,11 @@ def test_batch_steps_match_oracle(sdd, oracle_mod):
 
 
 def test_batch64_workload_sampled_parity(sdd, oracle_mod):
-    # the 64-instance workload in one launch; the oracle recomputes a sample of nodes
+    # the 64-instance workload in one launch; the oracle recomputes a sample of nodes path by
+    # path: each sampled node is run again on its own context with the node word the batch gave
+    # it (sdd_mc_params.node_word0) and the same task size, which must reproduce the batch's
+    # results bit for bit, and its per-path records are compared with the oracle's
+    from tests import _parity as PT
     insts = W.batch64_instances(seed=0)
     ctxs, lists, probs = [], [], []
     for I in insts:
@@ -115,18 +119,27 @@ def test_batch64_workload_sampled_parity(sdd, oracle_mod):
         probs.append((w, xi0, eta0))
     batch = sdd.sdd_batch_create(ctxs)
     kw = dict(dt=1e-4, Dt=1e-2, seed=0)
-    outs = [_np(o) for o in sdd.sdd_batch_interface_mc(batch, lists, **kw)]
+    outs = [_np(o) for o in sdd.sdd_batch_interface_mc(batch, lists, paths_per_task=256, **kw)]
     sdd.sdd_batch_sync(batch)
     offsets = np.concatenate([[0], np.cumsum([l[0].size for l in lists])])
+    checked = 0
     for k in (0, 17, 40, 63):
         xs, ys, npaths = lists[k]
         pick = np.array([0, xs.size // 2, xs.size - 1])
         P = oracle_mod.Problem(*probs[k])
-        o = oracle_mod.interface_mc(P, xs[pick], ys[pick], npaths[pick], node_ids=(offsets[k] + pick).astype(np.uint32),
-                                    **kw)
-        gk = {key: outs[k][key][pick] for key in outs[k]}
-        for f in ("xi", "eta"):
-            d = np.abs(gk["mean_" + f] - o["mean_" + f])
-            assert np.all(d <= 3 * o["se_" + f] + 1e-4), (k, f, d)
+        for p in pick:
+            word = int(offsets[k] + p)
+            r = _np(sdd.sdd_interface_mc_record(ctxs[k], xs[p:p + 1], ys[p:p + 1], npaths[p:p + 1],
+                                                paths_per_task=256, node_word0=word, **kw))
+            for key in ("mean_xi", "mean_eta", "se_xi", "se_eta", "n_exit", "path_steps"):
+                np.testing.assert_array_equal(r[key][0], outs[k][key][p], err_msg=f"{k} {p} {key}")
+            o = oracle_mod.interface_mc(P, xs[p:p + 1], ys[p:p + 1], npaths[p:p + 1],
+                                        node_ids=np.array([word], np.uint32), record=True, **kw)
+            same, rep = PT.assert_records(r, o)
+            PT.assert_flips_near_boundary(oracle_mod, P, xs[p:p + 1], ys[p:p + 1], npaths[p:p + 1], r, o, same,
+                                          node_ids=np.array([word], np.uint32), **kw)
+            PT.assert_nodes(r, o, npaths[p:p + 1], same, np.array([0, npaths[p]]))
+            checked += int(npaths[p])
+    assert checked > 10 ** 5
     for o in outs:
         assert np.all((o["mean_xi"] >= 0) & (o["mean_xi"] <= 1))

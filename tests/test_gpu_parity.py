@@ -161,6 +161,29 @@ def test_repeated_runs_are_bit_identical(sdd):
     assert not np.array_equal(a["mean_xi"], c["mean_xi"])
 
 
+def test_zero_map_changes_no_result(sdd):
+    # where w is constant around a cell its drift records are zero and the path kernel of a
+    # context reads the shared all-zero record instead (the zero map); the allocation-free entry
+    # point runs the same kernel without the map: every output must be the same, bit for bit
+    import torch
+    n = 257
+    for t, paths in ((0.0, 2000), (0.3, 701)):
+        w = W.w_ring(n, t)
+        # most of the square has w == 1 exactly (the map's case), the ring does not
+        wd = w.astype(np.float64)
+        flat = (wd[1:-1, 2:] == wd[1:-1, :-2]) & (wd[2:, 1:-1] == wd[:-2, 1:-1])
+        assert 0.3 < flat.mean() < 0.95
+        X, Y = W.identity_fields(n)
+        ctx = _ctx(sdd, w, X, Y)
+        xs, ys = W.interface_node_coords(n, n, 2, 2)
+        kw = dict(dt=1e-4, Dt=1e-2, seed=9, step_index=2, paths_per_task=128, block_threads=256)
+        a = _np(sdd.sdd_interface_mc(ctx, xs, ys, paths, **kw))
+        b = _np(sdd.sdd_interface_mc_static(torch.from_numpy(w).cuda(), torch.from_numpy(X).cuda(),
+                                            torch.from_numpy(Y).cuda(), xs, ys, paths, **kw))
+        for k in a:
+            np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+
+
 def test_empty_and_single_path_nodes(sdd, oracle_mod):
     n = 17
     ctx = _ctx(sdd, W.w_const(n), *W.identity_fields(n))
@@ -264,33 +287,41 @@ def test_solver_nonconvergence_is_a_status(sdd):
 
 
 def test_mesh_steps_match_oracle(sdd, oracle_mod):
+    # three mesh steps through sdd_step; each step is checked on its own inputs, so that no
+    # allowance grows from step to step: (1) the interface estimate against the oracle's on the
+    # GPU's starting fields (same w, same Philox streams), (2) the new fields against the oracle's
+    # LU solve (Sec. 4) from the same starting fields with the GPU's interface values
     import torch
+    from oracle import solver
     n, sub = 65, 2
     dt, Dt, paths = 1e-4, 1e-2, 4000
     xi, eta = W.identity_fields(n)
     ctx = _ctx(sdd, W.w_front(n, 0.0), xi, eta, sub=sub)
     ii, jj = W.interface_nodes(n, n, sub, sub)
-    o_fields = [xi, eta]
-    prev_gap = 0.0
+    xs, ys = ii / (n - 1), jj / (n - 1)
+    gx0, ge0 = xi, eta
     for step in range(3):
-        t = step * Dt
-        w = W.w_front(n, t)
+        w = W.w_front(n, step * Dt)
         sdd.sdd_set_w(ctx, torch.from_numpy(w).cuda())
         sdd.sdd_step(ctx, dt=dt, Dt=Dt, seed=77, paths_per_node=paths, rtol=1e-13, max_iter=50000)
         sdd.sdd_sync(ctx)
         g = _np(sdd.sdd_last_interface_stats(ctx))
         gx, ge = (a.cpu().numpy() for a in sdd.sdd_get_fields(ctx))
-        o_fields, o = oracle_mod.dd_step(w, o_fields[0], o_fields[1], sub_x=sub, sub_y=sub, dt=dt, Dt=Dt,
-                                         n_paths=paths, seed=77, step_index=step, nodes_ij=(ii, jj))
-        # interface means: same streams; the starting fields differ only by the earlier steps' gap
+        P = oracle_mod.Problem(w, gx0, ge0)
+        o = oracle_mod.interface_mc(P, xs, ys, paths, dt=dt, Dt=Dt, seed=77, step_index=step)
         for f in ("xi", "eta"):
             d = np.abs(g["mean_" + f] - o["mean_" + f])
-            assert np.all(d <= 3 * o["se_" + f] + 2 * prev_gap + 1e-12), (step, f, d.max())
-        # the solve is monotone: field gaps are bounded by the interface gaps
-        iface_gap = max(np.abs(g["mean_xi"] - o["mean_xi"]).max(), np.abs(g["mean_eta"] - o["mean_eta"]).max())
-        gap = max(np.abs(gx - o_fields[0]).max(), np.abs(ge - o_fields[1]).max())
-        assert gap <= max(iface_gap, prev_gap) + 1e-9, (step, gap, iface_gap)
-        prev_gap = gap
+            assert np.all(d <= 3 * o["se_" + f] + 1e-12), (step, f, d.max())
+            # a node moves by more than rounding only where a path's exit decision flipped
+            assert np.mean(d <= 1e-4) >= 0.9, (step, f, np.mean(d <= 1e-4))
+        np.testing.assert_array_equal(g["path_steps"] > 0, o["path_steps"] > 0)
+        bx = oracle_mod.boundary_grid(P.faces, n, n, 0, gx0)
+        be = oracle_mod.boundary_grid(P.faces, n, n, 1, ge0)
+        bx[jj, ii] = g["mean_xi"]
+        be[jj, ii] = g["mean_eta"]
+        ox, oe = solver.subdomain_solve(w.astype(np.float64), [gx0, ge0], [bx, be], sub, sub, Dt)
+        assert max(np.abs(gx - ox).max(), np.abs(ge - oe).max()) <= 1e-10, step
+        gx0, ge0 = gx, ge
     assert sdd.sdd_get_step_index(ctx) == 3
 
 
