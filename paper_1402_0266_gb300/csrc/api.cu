@@ -201,7 +201,7 @@ struct sdd_ctx {
     GraphSlot graph_p[2];
     int graph_kernels_p = 0;
     bool last_had_pending = false;  // the last launched graph ran deferred iterations
-    DevBuf<float4> surv;            // survivor end records of the step's paths
+    DevBuf<float4> surv;            // the step's path records (8 bytes per path, 16 with the control variate)
     cudaStream_t pipe_stream = nullptr;  // the side branch (highest priority)
     cudaStream_t faces_stream = nullptr; // the face data beside the drift records
     cudaEvent_t fev[2] = {nullptr, nullptr};
@@ -2056,7 +2056,7 @@ sdd_status sdd_step(sdd_ctx* c, const sdd_step_params* p)
                                                 nullptr, true);
         // deferred scoring (survivors and plain exits scored after the path kernel) where the
         // records fit; pipelining needs it
-        const size_t rec_bytes = (c->cv_mode ? 2 : 1) * sizeof(float4);
+        const size_t rec_bytes = (c->cv_mode ? 2 : 1) * sizeof(float2);
         c->defer = c->step_plan.ntasks > 0 && (size_t)c->step_plan.total_paths * rec_bytes <= (8ULL << 30);
         c->pipe = c->pipe_allowed && solve_single_launch(probe) && c->cv_mode != SDD_CV_FIELDS && c->defer;
         if (c->defer)

@@ -281,19 +281,30 @@ __device__ __forceinline__ long long warp_sum_ll(long long v)
     return v;
 }
 
-// Deferred scoring: a path's record in the survivor buffer, one float4 (two
-// with CV, the second holding the control-variate sums): a survivor leaves
-// (x, y, NaN, 0) with its end point, a path that left by the plain test
-// (x0, y0, x1, y1), the sub-step that crossed the boundary, and a path scored
-// in the kernel (bridge exits) x = -1, a value no point inside the square has.
-__device__ __forceinline__ float rec_nan() { return __int_as_float(0x7fc00000); }
+// Deferred scoring: a path's record in the survivor buffer, one float2 (two
+// with CV, the second holding the control-variate sums): a survivor leaves its
+// end point (x, y), x > 0; a path that left by the plain test the crossing of
+// its last sub-step with the boundary, (-1 - face, t) with t the tangential
+// coordinate on that face (the face data are interpolated there later); a path
+// scored in the kernel (bridge exits) REC_SKIP. No point inside the square has
+// a negative x, so the sign tells the kinds apart.
+constexpr float REC_SKIP = -8.0f;
 
 template <bool CV>
-__device__ __forceinline__ void put_record(void* surv, long long i, float4 r, float cxi, float ceta)
+__device__ __forceinline__ void put_record(void* surv, long long i, float2 r, float cxi, float ceta)
 {
-    float4* q = static_cast<float4*>(surv) + (CV ? 2 * i : i);
+    float2* q = static_cast<float2*>(surv) + (CV ? 2 * i : i);
     q[0] = r;
-    if (CV) q[1] = make_float4(cxi, ceta, 0.f, 0.f);
+    if (CV) q[1] = f2(cxi, ceta);
+}
+
+// The record of a plain exit through the sub-step (x, y) -> (xn, yn).
+__device__ __forceinline__ float2 exit_record(float x, float y, float xn, float yn)
+{
+    int face;
+    float t;
+    exit_crossing(x, y, xn, yn, face, t);
+    return f2(-1.0f - (float)face, t);
 }
 
 // Lanes refilled together below this count spend a loop pass drawing their
@@ -384,7 +395,7 @@ __global__ void __launch_bounds__(paths_max_block(CV, VAR), paths_min_blocks(CV,
                 int code = -1, taken = 0;
                 float yxi = 0.f, yeta = 0.f, xe = 0.f, ye = 0.f;
                 const bool warm = m < 0;   // draw -1: the pass draws the path's first normals
-                float4 seg = make_float4(-1.f, 0.f, 0.f, 0.f);   // a plain exit's sub-step, scored later
+                float2 seg = f2(REC_SKIP, 0.f);   // a plain exit's crossing, scored later
                 // sub-step A: gather, then the next draw's first rounds while the gather is in flight
                 const Cell cA = locate(I, pos);
                 float4 gA0, gA1;
@@ -419,12 +430,12 @@ __global__ void __launch_bounds__(paths_max_block(CV, VAR), paths_min_blocks(CV,
                     if (warm) {
                         // a path taken up mid-task: this pass only drew its first normals
                     } else if (outA) {
-                        if (a.surv) seg = make_float4(pos.x, pos.y, pa.x, pa.y), code = 0;
+                        if (a.surv) seg = exit_record(pos.x, pos.y, pa.x, pa.y), code = 0;
                         else plain_exit(I, pos.x, pos.y, pa.x, pa.y, code, yxi, yeta, xe, ye);
                         done = true;
                         taken = 2 * m + 1;
                     } else if (outB) {
-                        if (a.surv) seg = make_float4(pa.x, pa.y, pb.x, pb.y), code = 0;
+                        if (a.surv) seg = exit_record(pa.x, pa.y, pb.x, pb.y), code = 0;
                         else plain_exit(I, pa.x, pa.y, pb.x, pb.y, code, yxi, yeta, xe, ye);
                         done = true;
                         taken = 2 * m + 2;
@@ -446,7 +457,7 @@ __global__ void __launch_bounds__(paths_max_block(CV, VAR), paths_min_blocks(CV,
                     if (warm) {
                         // a path taken up mid-task: this pass only drew its first normals
                     } else if (outA) {
-                        if (a.surv) seg = make_float4(pos.x, pos.y, pa.x, pa.y), code = 0;
+                        if (a.surv) seg = exit_record(pos.x, pos.y, pa.x, pa.y), code = 0;
                         else plain_exit(I, pos.x, pos.y, pa.x, pa.y, code, yxi, yeta, xe, ye);
                         done = true;
                     } else {
@@ -471,8 +482,7 @@ __global__ void __launch_bounds__(paths_max_block(CV, VAR), paths_min_blocks(CV,
                     if (code < 0) {
                         if (a.surv) {
                             later = true;
-                            put_record<CV>(a.surv, nd.rec0 + path, make_float4(pos.x, pos.y, rec_nan(), 0.f),
-                                           cvx.x + cvx.y, cve.x + cve.y);
+                            put_record<CV>(a.surv, nd.rec0 + path, pos, cvx.x + cvx.y, cve.x + cve.y);
                         } else {
                             // survived the mesh step: xi, eta of its start at the end point
                             const Cell c = locate(I, pos);
@@ -488,7 +498,7 @@ __global__ void __launch_bounds__(paths_max_block(CV, VAR), paths_min_blocks(CV,
                         ++exits;
                         if (a.surv) {
                             // a plain exit leaves its sub-step, a bridge exit (scored here) the skip mark
-                            later = seg.x >= 0.f;
+                            later = seg.x != REC_SKIP;
                             put_record<CV>(a.surv, nd.rec0 + path, seg, cvx.x + cvx.y, cve.x + cve.y);
                         }
                     }
@@ -614,9 +624,9 @@ __global__ void __launch_bounds__(512, 2) k_paths_exp(const PathArgs a)
                 bool done = false;
                 int code = -1;
                 float yxi = 0.f, yeta = 0.f, xe = 0.f, ye = 0.f;
-                float4 seg = make_float4(-1.f, 0.f, 0.f, 0.f);
+                float2 seg = f2(REC_SKIP, 0.f);
                 if (!inside2(pn)) {
-                    if (a.surv) seg = make_float4(pos.x, pos.y, pn.x, pn.y), code = 0;
+                    if (a.surv) seg = exit_record(pos.x, pos.y, pn.x, pn.y), code = 0;
                     else plain_exit(I, pos.x, pos.y, pn.x, pn.y, code, yxi, yeta, xe, ye);
                     done = true;
                 } else {
@@ -637,8 +647,7 @@ __global__ void __launch_bounds__(512, 2) k_paths_exp(const PathArgs a)
                     if (code < 0) {
                         if (a.surv) {
                             later = true;
-                            put_record<false>(a.surv, nd.rec0 + path, make_float4(pos.x, pos.y, rec_nan(), 0.f), 0.f,
-                                              0.f);
+                            put_record<false>(a.surv, nd.rec0 + path, pos, 0.f, 0.f);
                         } else {
                             const Cell cf = locate(I, pos);
                             float4 f0, f1;
@@ -652,7 +661,7 @@ __global__ void __launch_bounds__(512, 2) k_paths_exp(const PathArgs a)
                     } else {
                         ++exits;
                         if (a.surv) {
-                            later = seg.x >= 0.f;
+                            later = seg.x != REC_SKIP;
                             put_record<false>(a.surv, nd.rec0 + path, seg, 0.f, 0.f);
                         }
                     }
@@ -736,24 +745,21 @@ __global__ void __launch_bounds__(SCORE_THREADS, 1024 / SCORE_THREADS) k_score_s
     const int end = nd.n_paths;
     Acc ax{0.f, 0.f, 0.f, 0.f}, ae{0.f, 0.f, 0.f, 0.f};
     // the records of the batch that starts at path p0 (past the end: the skip mark)
-    auto load_batch = [&](int p0, float4 (&r)[SCORE_BATCH], float2 (&cvs)[SCORE_BATCH]) {
+    auto load_batch = [&](int p0, float2 (&r)[SCORE_BATCH], float2 (&cvs)[SCORE_BATCH]) {
 #pragma unroll
         for (int u = 0; u < SCORE_BATCH; ++u) {
             const int p = p0 + u * SCORE_THREADS;
-            r[u] = make_float4(-1.f, 0.f, 0.f, 0.f);
+            r[u] = f2(REC_SKIP, 0.f);
             cvs[u] = f2(0.f, 0.f);
             if (p < end) {
                 const long long si = nd.rec0 + p;
-                const float4* q = static_cast<const float4*>(a.surv) + (CV ? 2 * si : si);
+                const float2* q = static_cast<const float2*>(a.surv) + (CV ? 2 * si : si);
                 r[u] = q[0];
-                if (CV) {
-                    const float4 c = q[1];
-                    cvs[u] = f2(c.x, c.y);
-                }
+                if (CV) cvs[u] = q[1];
             }
         }
     };
-    float4 r[SCORE_BATCH];
+    float2 r[SCORE_BATCH];
     float2 cvs[SCORE_BATCH];
     load_batch(threadIdx.x, r, cvs);
     for (int p0 = threadIdx.x; p0 < end; p0 += SCORE_BATCH * SCORE_THREADS) {
@@ -764,16 +770,16 @@ __global__ void __launch_bounds__(SCORE_THREADS, 1024 / SCORE_THREADS) k_score_s
         float2 st[SCORE_BATCH];
 #pragma unroll
         for (int u = 0; u < SCORE_BATCH; ++u) {
-            if (r[u].x >= 0.f && isnan(r[u].z)) {
-                const Cell c = locate(I, f2(r[u].x, r[u].y));
+            if (r[u].x >= 0.f) {
+                const Cell c = locate(I, r[u]);
                 load_cell(rec2(I.fcoef, c.idx), f0[u], f1[u]);
                 st[u] = c.st;
-            } else if (r[u].x >= 0.f) {
-                int face, k;
-                float t, f;
+            } else if (r[u].x != REC_SKIP) {
+                int k;
+                float f;
                 long long off;
-                exit_crossing(r[u].x, r[u].y, r[u].z, r[u].w, face, t);
-                face_interval(I, face, t, off, k, f);
+                const int face = (int)(-1.0f - r[u].x);
+                face_interval(I, face, r[u].y, off, k, f);
                 const float* v0 = I.faces32 + off + k;
                 const float* v1 = v0 + (2LL * I.ny + 2LL * I.nx);
                 f0[u] = make_float4(v0[0], v0[1], v1[0], v1[1]);
@@ -781,14 +787,14 @@ __global__ void __launch_bounds__(SCORE_THREADS, 1024 / SCORE_THREADS) k_score_s
             }
         }
         // the next batch's records while this batch's gathers are in flight
-        float4 rn[SCORE_BATCH];
+        float2 rn[SCORE_BATCH];
         float2 cn[SCORE_BATCH];
         load_batch(p0 + SCORE_BATCH * SCORE_THREADS, rn, cn);
 #pragma unroll
         for (int u = 0; u < SCORE_BATCH; ++u) {
-            if (r[u].x < 0.f) continue;   // scored in the path kernel, or past the end
+            if (r[u].x == REC_SKIP) continue;   // scored in the path kernel, or past the end
             float yxi, yeta;
-            if (isnan(r[u].z)) {
+            if (r[u].x >= 0.f) {
                 const float2 v = eval2(f0[u], f1[u], st[u]);
                 yxi = v.x;
                 yeta = v.y;
