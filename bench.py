@@ -72,6 +72,14 @@ def parse():
                     help="subdomain solver of the mesh steps")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="run each step's subdomain solve after its paths instead of beside the next step's")
+    ap.add_argument("--estimate-only", action="store_true",
+                    help="time the interface estimate alone (no mesh-step graph) on every --node-stride-th "
+                         "interface node of the first mesh step: the path kernel outside any graph, for profiling")
+    ap.add_argument("--node-stride", type=int, default=1)
+    ap.add_argument("--shape", default=None,
+                    help="--estimate-only: block_threads,paths_per_task,zero_map (1 on, 2 off); default: autotuned")
+    ap.add_argument("--cv", choices=["off", "fields", "model"], default="off",
+                    help="--estimate-only: control variate of the estimate")
     return ap.parse_args()
 
 
@@ -317,6 +325,10 @@ def run_ours(args, world, rank, local):
         sdd.sdd_set_fields(ctx, xi0_d, eta0_d)
         sdd.sdd_set_step_index(ctx, 0)
 
+    # the launch shape of the steps' path kernel: the autotuner's choice for the interface node set
+    # (the steps find it in the context's cache)
+    ix, iy = sdd.sdd_interface_nodes(ctx)
+    shape = sdd.sdd_autotune(ctx, ix, iy, np.full(len(ix), paths), WL.dt, WL.Dt)
     for k in range(Wm):
         sdd.sdd_set_w(ctx, w_all[k % nsteps])
         sdd.sdd_step(ctx, **sp)
@@ -333,6 +345,7 @@ def run_ours(args, world, rank, local):
     barrier(world)
     torch.cuda.synchronize()
     clocks.start()
+    torch.cuda.nvtx.range_push("timed_steps")
     for k in range(K):
         flush.zero_()
         ev0[k].record(stream)
@@ -350,6 +363,7 @@ def run_ours(args, world, rank, local):
         solve_ms.append(info["solve_ms"])
         kernel_nodes += info["kernel_nodes"]
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     barrier(world)
     clk = clocks.stop()
     pipelined = sdd.sdd_pipeline_in_use(ctx)
@@ -360,7 +374,6 @@ def run_ours(args, world, rank, local):
     path_steps = int(steps_dev.sum().item())
     value, tot_steps, max_s = whole_job(path_steps, total_ms / 1e3, world)
     max_ms = max_s * 1e3
-    ix, iy = sdd.sdd_interface_nodes(ctx)
     nodes = len(ix)
     nodes_per_s = world * nodes * K / (max_ms / 1e3)
 
@@ -508,7 +521,10 @@ def run_ours(args, world, rank, local):
                                       if pipelined else ""),
                        "global_batch": world * nodes * paths, "seq_len": WL.K,
                        "parallelism": f"{world} independent instance(s), one per GPU",
-                       "l2": "flushed before every step (256 MB write, outside the step's events)"},
+                       "l2": "flushed before every step (256 MB write, outside the step's events)",
+                       "launch_shape": {"block_threads": shape["block_threads"],
+                                        "paths_per_task": shape["paths_per_task"],
+                                        "zero_map": shape["zero_map"] == 1}},
             "interface_nodes_per_s": nodes_per_s,
             "path_steps_per_step": tot_steps / K / world,
             "paths_kernel_ms": mean_paths_ms,
@@ -528,6 +544,65 @@ def run_ours(args, world, rank, local):
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
+
+
+def run_estimate(args, world, rank, local):
+    """The interface estimate of the mesh-step workload's first step, alone: sdd_interface_mc on every
+    node_stride-th interface node (outside any graph), K timed calls inside the NVTX range "estimate"."""
+    import torch
+
+    import paper_1402_0266_gb300 as sdd
+    from paper_1402_0266_gb300 import build as b
+    b.build()
+    name = args.workload
+    WL, wfun, desc = WORKLOADS[name]
+    torch.cuda.set_device(local)
+    n = WL.n
+    K = args.steps or 3
+    paths = args.paths or WL.paths
+    xi0, eta0 = W.identity_fields(n)
+    ctx = sdd.sdd_init(n, n, WL.sub, WL.sub, w=torch.from_numpy(wfun(n, 0.0)).cuda(),
+                       xi0=torch.from_numpy(xi0).cuda(), eta0=torch.from_numpy(eta0).cuda())
+    ix, iy = sdd.sdd_interface_nodes(ctx)
+    xs, ys = np.asarray(ix)[::args.node_stride], np.asarray(iy)[::args.node_stride]
+    npaths = np.full(xs.size, paths)
+    if args.cv != "off":
+        if args.cv == "model":
+            sdd.sdd_cv_train(ctx, per_horizon=10000, dt=WL.dt, Dt=WL.Dt, seed=100, epochs=10, batch=4096, lr=3e-3,
+                             slices=4, init_seed=7)
+        sdd.sdd_cv_enable(ctx, {"fields": sdd.SDD_CV_FIELDS, "model": sdd.SDD_CV_MODEL}[args.cv])
+    if args.shape:
+        blk, ppt, zm = (int(v) for v in args.shape.split(","))
+    else:
+        sh = sdd.sdd_autotune(ctx, xs, ys, npaths, WL.dt, WL.Dt)
+        blk, ppt, zm = sh["block_threads"], sh["paths_per_task"], sh["zero_map"]
+    kw = dict(dt=WL.dt, Dt=WL.Dt, seed=WL.seed + rank, block_threads=blk, paths_per_task=ppt, zero_map=zm)
+    for k in range(args.warmup):
+        sdd.sdd_interface_mc(ctx, xs, ys, npaths, step_index=k, **kw)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ms, steps = 0.0, 0
+    torch.cuda.nvtx.range_push("estimate")
+    for k in range(K):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        o = sdd.sdd_interface_mc(ctx, xs, ys, npaths, step_index=args.warmup + k, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        steps += int(o["path_steps"].sum())
+    torch.cuda.nvtx.range_pop()
+    if rank == 0:
+        print(json.dumps({"metric": "path-steps/s (interface estimate alone, first mesh step)",
+                          "value": steps / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": K,
+                          "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                          "config": {"workload": f"{name}: {desc}, every {args.node_stride}th of the interface nodes "
+                                                 f"({xs.size}) x {paths} paths, dt={WL.dt}, Dt={WL.Dt}, control "
+                                                 f"variate {args.cv}",
+                                     "launch_shape": {"block_threads": blk, "paths_per_task": ppt,
+                                                      "zero_map": zm == 1}},
+                          "path_steps_per_launch": steps / K}), flush=True)
 
 
 def run_batch64(args, world, rank, local):
@@ -858,6 +933,8 @@ def main():
     elif args.workload == "cv65":
         args.steps = args.steps or 12
         run_cv65(args, world, rank, local)
+    elif args.estimate_only:
+        run_estimate(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -225,7 +225,13 @@ sdd_status sdd_interface_mc_record(sdd_ctx* ctx, const sdd_nodes* nodes, const s
  *                  estimate (inside the mesh step's graph);
  *   SDD_CV_FIELDS  one slice from the fields at t_{n-1}: the finite-difference
  *                  gradients of xi and eta (no training; over a short mesh
- *                  step the solution's gradient stays close to it). */
+ *                  step the solution's gradient stays close to it). With the
+ *                  paper's test, whose normals come in sub-step pairs, this
+ *                  gradient is evaluated once per pair, at the pair's first
+ *                  point, for both of its increments: it is known before
+ *                  both, so the estimate stays unbiased, and a fixed field's
+ *                  gradient varies over distances far above a pair's
+ *                  spread, so the variance it removes is the same. */
 #define SDD_CV_OFF 0
 #define SDD_CV_TABLE 1
 #define SDD_CV_MODEL 2

@@ -250,6 +250,10 @@ typedef struct {
      * NULL or cv_slices = 0 for the plain estimator */
     const double* cv;
     int cv_slices;
+    /* with the paper's test (sub-steps drawn in pairs): 1 evaluates the model
+     * once per sub-step pair, at the pair's first point X_{2m} and in the slice
+     * of sub-step 2m, for both increments of the pair */
+    int cv_pairs;
 } orc_problem;
 
 typedef struct {
@@ -409,7 +413,9 @@ static int32_t run_path(const orc_problem* P, const orc_params* Q, uint32_t node
     double x = x0, y = y0;
     uint32_t words[4];
     const int cv_on = P->cv && P->cv_slices > 0;
+    const int cv_pairs = cv_on && P->cv_pairs && Q->exit_mode == 0;
     double cv_sum[2] = {0.0, 0.0};
+    double g[4] = {0.0, 0.0, 0.0, 0.0};
     for (int32_t j = 0; j < Q->K; ++j) {
         double zx, zy, ub = 1.0;
         if (Q->exit_mode == 0) {
@@ -430,16 +436,18 @@ static int32_t run_path(const orc_problem* P, const orc_params* Q, uint32_t node
         double yn = y + by * dt + sq * zy;
         /* control variate: the model gradient at X_j (before the increment)
          * times the increment's noise sqrt(2) dW_j, summed over the sub-steps
-         * the path takes; its expectation is zero for any model */
+         * the path takes; its expectation is zero for any model whose value
+         * is known before the increment. With cv_pairs the value at X_{2m}
+         * serves sub-steps 2m and 2m + 1 (known before both increments). */
         if (cv_on) {
-            int q = (int)(((int64_t)j * P->cv_slices) / Q->K);
-            if (q > P->cv_slices - 1) q = P->cv_slices - 1;
-            const double* T = P->cv + (int64_t)q * 4 * nx * ny;
-            for (int c = 0; c < 4; ++c) {
+            if (!cv_pairs || (j & 1) == 0) {
+                int q = (int)(((int64_t)j * P->cv_slices) / Q->K);
+                if (q > P->cv_slices - 1) q = P->cv_slices - 1;
+                const double* T = P->cv + (int64_t)q * 4 * nx * ny;
                 /* component c of slice q, node values strided by 4 */
-                double g = cv_bilinear(nx, ny, T + c, x, y);
-                cv_sum[c >> 1] += g * sq * ((c & 1) ? zy : zx);
+                for (int c = 0; c < 4; ++c) g[c] = cv_bilinear(nx, ny, T + c, x, y);
             }
+            for (int c = 0; c < 4; ++c) cv_sum[c >> 1] += g[c] * sq * ((c & 1) ? zy : zx);
         }
         if (margin && j < upto) {
             const double m = fmin(fmin(fabs(xn), fabs(1.0 - xn)), fmin(fabs(yn), fabs(1.0 - yn)));

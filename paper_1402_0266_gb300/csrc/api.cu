@@ -532,7 +532,7 @@ sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const Out
                        int K, uint64_t seed, uint32_t step_index, const uint32_t* step_ptr, int exit_mode,
                        const RecDev* rec, cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_b, int cv_slices = 0,
                        const uint8_t* node_mask = nullptr, void* surv = nullptr, cudaEvent_t join = nullptr,
-                       ZmapRef zm = ZmapRef{});
+                       ZmapRef zm = ZmapRef{}, bool cv_pairs = false);
 
 const TunedShape* find_tuned(const std::vector<TunedShape>& t, uint64_t key)
 {
@@ -632,7 +632,7 @@ sdd_status build_plan(sdd_ctx* c, Plan& P, const double* x, const double* y, con
 sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const OutDev* outs, const OutDev& out0, double dt,
                        int K, uint64_t seed, uint32_t step_index, const uint32_t* step_ptr, int exit_mode,
                        const RecDev* rec, cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_b, int cv_slices,
-                       const uint8_t* node_mask, void* surv, cudaEvent_t join, ZmapRef zm)
+                       const uint8_t* node_mask, void* surv, cudaEvent_t join, ZmapRef zm, bool cv_pairs)
 {
     if (surv && rec) return fail(err, SDD_EINVAL, "per-path records with deferred survivor scores");
     if (P.nnodes == 0 || P.ntasks == 0) {
@@ -658,6 +658,7 @@ sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const Out
         if (rec) a.rec = *rec;
         a.node_mask = node_mask;
         a.surv = surv;
+        a.cv_pairs = cv_pairs ? 1 : 0;
         if (zm.single) {
             a.single = 1;
             a.one = zm.inst;
@@ -722,7 +723,8 @@ sdd_status run_plan(sdd_ctx* c, Plan& P, double dt, int K, uint64_t seed, uint32
                     void* surv = nullptr, cudaEvent_t join = nullptr)
 {
     return run_plan_on(&c->err, P, c->d_inst.p, nullptr, out, dt, K, seed, step_index, step_ptr, exit_mode, rec, s,
-                       ev_a, ev_b, c->cv_mode ? c->cv_slices : 0, node_mask, surv, join, ctx_zmap(c, P.zero_map != 0));
+                       ev_a, ev_b, c->cv_mode ? c->cv_slices : 0, node_mask, surv, join, ctx_zmap(c, P.zero_map != 0),
+                       c->cv_mode == SDD_CV_FIELDS);
 }
 
 // Launch shape for a plan: explicit requests win, else a tuned shape for this node set, else the heuristic.

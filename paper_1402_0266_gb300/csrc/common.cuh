@@ -110,6 +110,7 @@ struct PathArgs {
     uint32_t zcell;
     InstDev one;              // single: the one instance's tables (inst[0]), read as parameters
     int32_t single;           // 1: every task is of instance 0 and `one` holds its tables
+    int32_t cv_pairs;         // control variate with sub-step pairs: the model once per pair (at its first point)
 };
 
 // The zero map's size: at most kZmapMaxWords words (16 KB of shared memory per block of the path kernel).

@@ -234,19 +234,25 @@ __device__ __forceinline__ float2 corners2(const uint4& r, float2 ss, float2 oms
     return __ffma2_rn(tt, r1, __fmul2_rn(omt, r0));
 }
 
-// Control variate: the model gradients (xi, eta) at the cell's point, times
-// the sub-step's increment z = sqrt(2 dt) N(0,1)^2, added to the running sums
-// (acc_xi, acc_eta hold the x and y parts separately).
-__device__ __forceinline__ void cv_add(const InstDev& I, const Cell& c, int q, float2 z, float2& acc_xi,
-                                       float2& acc_eta)
+// Control variate: the model gradients of xi and eta at the cell's point
+// (slice q), gxi = (d/dx, d/dy) of the xi model, geta of the eta model.
+__device__ __forceinline__ void cv_eval(const InstDev& I, const Cell& c, int q, float2& gxi, float2& geta)
 {
     const uint4* r = I.cvcoef + 2 * ((size_t)q * (size_t)(I.nx - 1) * (size_t)(I.ny - 1) + c.idx);
     uint4 gx, ge;
     load_words(r, gx, ge);
     const float2 ss = f2(c.st.x, c.st.x), tt = f2(c.st.y, c.st.y);
     const float2 oms = f2(1.f - c.st.x, 1.f - c.st.x), omt = f2(1.f - c.st.y, 1.f - c.st.y);
-    acc_xi = __ffma2_rn(corners2(gx, ss, oms, tt, omt), z, acc_xi);
-    acc_eta = __ffma2_rn(corners2(ge, ss, oms, tt, omt), z, acc_eta);
+    gxi = corners2(gx, ss, oms, tt, omt);
+    geta = corners2(ge, ss, oms, tt, omt);
+}
+
+// The gradients times the sub-step's increment z = sqrt(2 dt) N(0,1)^2, added to
+// the running sums (acc_xi, acc_eta hold the x and y parts separately).
+__device__ __forceinline__ void cv_acc(float2 gxi, float2 geta, float2 z, float2& acc_xi, float2& acc_eta)
+{
+    acc_xi = __ffma2_rn(gxi, z, acc_xi);
+    acc_eta = __ffma2_rn(geta, z, acc_eta);
 }
 
 struct Acc {
@@ -313,7 +319,9 @@ constexpr int WARM_MIN = 8;
 
 // MODE 0: the paper's test, sub-step pairs; MODE 1: with the bridge test;
 // MODE 2: as MODE 0 when K is even (every pair has both sub-steps).
-// CV: subtract the control variate sum_j G(s_j, X_j) . sqrt(2) dW_j from both scores.
+// CVM: 0 no control variate; 1 subtract sum_j G(s_j, X_j) . sqrt(2) dW_j from
+// both scores; 2 (sub-step pairs) the same with G evaluated once per pair, at
+// X_{2m} in the slice of sub-step 2m, for both of the pair's increments.
 // Kernel variants by where the tables come from: VAR_MULTI, each task's
 // instance from the instance table (batches); VAR_ONE, a single instance whose
 // tables are kernel parameters (no registers held for them); VAR_ZM, VAR_ONE
@@ -328,10 +336,13 @@ constexpr int paths_min_blocks(bool cv, int var)
     return cv ? (var != VAR_MULTI ? 4 : 3) : (var != VAR_MULTI ? 6 : 2);
 }
 
-template <int MODE, bool RECORD, bool CV, int VAR>
-__global__ void __launch_bounds__(paths_max_block(CV, VAR), paths_min_blocks(CV, VAR)) k_paths(const PathArgs a)
+template <int MODE, bool RECORD, int CVM, int VAR>
+__global__ void __launch_bounds__(paths_max_block(CVM != 0, VAR), paths_min_blocks(CVM != 0, VAR))
+    k_paths(const PathArgs a)
 {
     constexpr bool ZM = VAR == VAR_ZM;
+    constexpr bool CV = CVM != 0;
+    constexpr bool CVP = CVM == 2 && MODE != 1;   // one model evaluation per sub-step pair
     extern __shared__ uint32_t zsm[];   // the zero map of the drift records (ZM)
     if (ZM) {
         for (int k = threadIdx.x; k < a.zwords; k += blockDim.x) zsm[k] = a.zmap[k];
@@ -400,10 +411,16 @@ __global__ void __launch_bounds__(paths_max_block(CV, VAR), paths_min_blocks(CV,
                 const Cell cA = locate(I, pos);
                 float4 gA0, gA1;
                 load_cell(drift_rec<ZM>(I, cA, zsm, a), gA0, gA1);
+                float2 gxA, geA;   // the model at X_j (CVP: also for the pair's second sub-step)
                 if (CV) {
                     const int j = PAIRS ? 2 * m : m;
-                    if (j >= cvn) cvn = a.cv_bound[++cvq + 1];
-                    cv_add(I, cA, cvq, zA, cvx, cve);
+                    if (CVP) {
+                        while (j >= cvn) cvn = a.cv_bound[++cvq + 1];
+                    } else if (j >= cvn) {
+                        cvn = a.cv_bound[++cvq + 1];
+                    }
+                    cv_eval(I, cA, cvq, gxA, geA);
+                    cv_acc(gxA, geA, zA, cvx, cve);
                 }
                 uint4 r = make_uint4((uint32_t)path, nctr, (uint32_t)(m + 1), step);
                 philox_rounds_rk<0, 5>(r, a.keys);
@@ -423,9 +440,15 @@ __global__ void __launch_bounds__(paths_max_block(CV, VAR), paths_min_blocks(CV,
                     const bool outB = haveB && !outA && !inside2(pb);
                     if (CV) {
                         // the second sub-step counts only when the path takes it
-                        if (haveB && 2 * m + 1 >= cvn) cvn = a.cv_bound[++cvq + 1];
                         const float2 zt = (haveB && !outA) ? zB : f2(0.f, 0.f);
-                        cv_add(I, cB, cvq, zt, cvx, cve);
+                        if (CVP) {
+                            cv_acc(gxA, geA, zt, cvx, cve);
+                        } else {
+                            if (haveB && 2 * m + 1 >= cvn) cvn = a.cv_bound[++cvq + 1];
+                            float2 gxB, geB;
+                            cv_eval(I, cB, cvq, gxB, geB);
+                            cv_acc(gxB, geB, zt, cvx, cve);
+                        }
                     }
                     if (warm) {
                         // a path taken up mid-task: this pass only drew its first normals
@@ -961,32 +984,35 @@ __global__ void k_rng_draw(uint64_t seed, const uint32_t* __restrict__ ctrs, lon
     }
 }
 
-template <int MODE, bool RECORD, bool CV, int VAR>
+template <int MODE, bool RECORD, int CVM, int VAR>
 const void* kernel_ptr()
 {
-    return (const void*)k_paths<MODE, RECORD, CV, VAR>;
+    return (const void*)k_paths<MODE, RECORD, CVM, VAR>;
 }
 
-template <bool CV, int VAR>
+template <int CVM, int VAR>
 const void* pick_cv(int mode, bool record)
 {
     if (mode == 3) return record ? (const void*)k_paths_exp<true> : (const void*)k_paths_exp<false>;
-    if (mode == 0) return record ? kernel_ptr<0, true, CV, VAR>() : kernel_ptr<0, false, CV, VAR>();
-    if (mode == 2) return record ? kernel_ptr<2, true, CV, VAR>() : kernel_ptr<2, false, CV, VAR>();
-    return record ? kernel_ptr<1, true, CV, VAR>() : kernel_ptr<1, false, CV, VAR>();
+    if (mode == 0) return record ? kernel_ptr<0, true, CVM, VAR>() : kernel_ptr<0, false, CVM, VAR>();
+    if (mode == 2) return record ? kernel_ptr<2, true, CVM, VAR>() : kernel_ptr<2, false, CVM, VAR>();
+    // the bridge test draws per sub-step: no pairs
+    return record ? kernel_ptr<1, true, CVM == 2 ? 1 : CVM, VAR>() : kernel_ptr<1, false, CVM == 2 ? 1 : CVM, VAR>();
 }
 
 template <int VAR>
-const void* pick_var(int mode, bool record, bool cv)
+const void* pick_var(int mode, bool record, int cvm)
 {
-    return cv ? pick_cv<true, VAR>(mode, record) : pick_cv<false, VAR>(mode, record);
+    if (cvm == 2) return pick_cv<2, VAR>(mode, record);
+    return cvm ? pick_cv<1, VAR>(mode, record) : pick_cv<0, VAR>(mode, record);
 }
 
-const void* pick(int mode, bool record, bool cv, int var)
+// cvm: 0 no control variate, 1 per sub-step, 2 per sub-step pair
+const void* pick(int mode, bool record, int cvm, int var)
 {
-    if (var == VAR_ZM) return pick_var<VAR_ZM>(mode, record, cv);
-    if (var == VAR_ONE) return pick_var<VAR_ONE>(mode, record, cv);
-    return pick_var<VAR_MULTI>(mode, record, cv);
+    if (var == VAR_ZM) return pick_var<VAR_ZM>(mode, record, cvm);
+    if (var == VAR_ONE) return pick_var<VAR_ONE>(mode, record, cvm);
+    return pick_var<VAR_MULTI>(mode, record, cvm);
 }
 
 // The variant of a launch: the zero map where the arguments carry one, else the single instance's
@@ -1014,7 +1040,8 @@ int path_kernel_blocks_per_sm(int exit_mode, bool record, int block, bool cv, in
     const int mode = exit_mode == 2 ? 3 : exit_mode == 1 ? 1 : 0;
     const int var = zwords > 0 ? VAR_ZM : single ? VAR_ONE : VAR_MULTI;
     const size_t smem = var == VAR_ZM && mode != 3 ? sizeof(uint32_t) * (size_t)zwords : 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(mode, record, cv, var), block, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(mode, record, cv ? 1 : 0, var), block, smem) !=
+        cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
 }
@@ -1049,9 +1076,9 @@ static void prefer_l1()
     done = true;
     for (int mode : {0, 1, 2, 3})
         for (bool rec : {false, true})
-            for (bool cv : {false, true})
+            for (int cvm : {0, 1, 2})
                 for (int var : {VAR_MULTI, VAR_ONE, VAR_ZM})
-                    cudaFuncSetAttribute(pick(mode, rec, cv, var), cudaFuncAttributePreferredSharedMemoryCarveout,
+                    cudaFuncSetAttribute(pick(mode, rec, cvm, var), cudaFuncAttributePreferredSharedMemoryCarveout,
                                          var == VAR_ZM && mode != 3 ? 100 : 0);
     cudaGetLastError();
 }
@@ -1085,11 +1112,11 @@ static void launch_zm(const void* fn, const PathArgs& a, int grid, int block, si
     cudaLaunchKernel(fn, dim3((unsigned)grid), dim3((unsigned)block), args, smem, s);
 }
 
-template <bool CV, int VAR>
+template <int CVM, int VAR>
 static void launch_mode(const PathArgs& a, int mode, bool record, int grid, int block, size_t smem, cudaStream_t s)
 {
     if (VAR == VAR_ZM && mode != 3) {
-        launch_zm(pick(mode, record, CV, VAR_ZM), a, grid, block, smem, s);
+        launch_zm(pick(mode, record, CVM, VAR_ZM), a, grid, block, smem, s);
         return;
     }
     switch (mode) {
@@ -1098,16 +1125,16 @@ static void launch_mode(const PathArgs& a, int mode, bool record, int grid, int 
         else k_paths_exp<false><<<grid, block, 0, s>>>(a);
         break;
     case 0:
-        if (record) k_paths<0, true, CV, VAR><<<grid, block, smem, s>>>(a);
-        else k_paths<0, false, CV, VAR><<<grid, block, smem, s>>>(a);
+        if (record) k_paths<0, true, CVM, VAR><<<grid, block, smem, s>>>(a);
+        else k_paths<0, false, CVM, VAR><<<grid, block, smem, s>>>(a);
         break;
     case 2:
-        if (record) k_paths<2, true, CV, VAR><<<grid, block, smem, s>>>(a);
-        else k_paths<2, false, CV, VAR><<<grid, block, smem, s>>>(a);
+        if (record) k_paths<2, true, CVM, VAR><<<grid, block, smem, s>>>(a);
+        else k_paths<2, false, CVM, VAR><<<grid, block, smem, s>>>(a);
         break;
     default:
-        if (record) k_paths<1, true, CV, VAR><<<grid, block, smem, s>>>(a);
-        else k_paths<1, false, CV, VAR><<<grid, block, smem, s>>>(a);
+        if (record) k_paths<1, true, CVM == 2 ? 1 : CVM, VAR><<<grid, block, smem, s>>>(a);
+        else k_paths<1, false, CVM == 2 ? 1 : CVM, VAR><<<grid, block, smem, s>>>(a);
     }
 }
 
@@ -1117,16 +1144,18 @@ cudaError_t launch_paths(const PathArgs& a, int exit_mode, bool record, int grid
     prefer_l1();
     const int mode = kernel_mode(exit_mode, a.K);
     const int var = path_var(a);
+    const int cvm = !cv ? 0 : (a.cv_pairs && (mode == 0 || mode == 2)) ? 2 : 1;
     const size_t smem = var == VAR_ZM && mode != 3 ? sizeof(uint32_t) * (size_t)a.zwords : 0;
-    if (var == VAR_ZM) {
-        if (cv) launch_mode<true, VAR_ZM>(a, mode, record, grid, block, smem, s);
-        else launch_mode<false, VAR_ZM>(a, mode, record, grid, block, smem, s);
-    } else if (var == VAR_ONE) {
-        if (cv) launch_mode<true, VAR_ONE>(a, mode, record, grid, block, 0, s);
-        else launch_mode<false, VAR_ONE>(a, mode, record, grid, block, 0, s);
-    } else {
-        if (cv) launch_mode<true, VAR_MULTI>(a, mode, record, grid, block, 0, s);
-        else launch_mode<false, VAR_MULTI>(a, mode, record, grid, block, 0, s);
+    switch (var * 3 + cvm) {
+    case VAR_ZM * 3 + 0: launch_mode<0, VAR_ZM>(a, mode, record, grid, block, smem, s); break;
+    case VAR_ZM * 3 + 1: launch_mode<1, VAR_ZM>(a, mode, record, grid, block, smem, s); break;
+    case VAR_ZM * 3 + 2: launch_mode<2, VAR_ZM>(a, mode, record, grid, block, smem, s); break;
+    case VAR_ONE * 3 + 0: launch_mode<0, VAR_ONE>(a, mode, record, grid, block, 0, s); break;
+    case VAR_ONE * 3 + 1: launch_mode<1, VAR_ONE>(a, mode, record, grid, block, 0, s); break;
+    case VAR_ONE * 3 + 2: launch_mode<2, VAR_ONE>(a, mode, record, grid, block, 0, s); break;
+    case VAR_MULTI * 3 + 0: launch_mode<0, VAR_MULTI>(a, mode, record, grid, block, 0, s); break;
+    case VAR_MULTI * 3 + 1: launch_mode<1, VAR_MULTI>(a, mode, record, grid, block, 0, s); break;
+    default: launch_mode<2, VAR_MULTI>(a, mode, record, grid, block, 0, s);
     }
     return cudaGetLastError();
 }

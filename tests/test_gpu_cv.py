@@ -226,9 +226,19 @@ def test_field_gradient_mode_matches_oracle(sdd, oracle_mod):
     g = _np(sdd.sdd_interface_mc_record(ctx, xs, ys, npaths, **kw))
     T = mlp.field_gradient_table(xi0, eta0)
     np.testing.assert_allclose(sdd.sdd_cv_get_table(ctx, 1).cpu().numpy(), T, rtol=1e-12, atol=1e-9)
-    o = oracle_mod.interface_mc(oracle_mod.Problem(w, xi0, eta0), xs, ys, npaths, record=True, cv_table=_h(T), **kw)
+    # the paper's test draws sub-step pairs: the field gradient is evaluated once per pair
+    o = oracle_mod.interface_mc(oracle_mod.Problem(w, xi0, eta0), xs, ys, npaths, record=True, cv_table=_h(T),
+                                cv_pairs=True, **kw)
     same, rep = PT.assert_records(g, o)
     PT.assert_nodes(g, o, npaths, same, np.concatenate([[0], np.cumsum(npaths)]))
+    # and a table set by hand is evaluated at every sub-step
+    _set_table(sdd, ctx, T)
+    sdd.sdd_cv_enable(ctx, sdd.SDD_CV_TABLE)
+    g1 = _np(sdd.sdd_interface_mc_record(ctx, xs, ys, npaths, **kw))
+    o1 = oracle_mod.interface_mc(oracle_mod.Problem(w, xi0, eta0), xs, ys, npaths, record=True, cv_table=_h(T), **kw)
+    same1, _ = PT.assert_records(g1, o1)
+    PT.assert_nodes(g1, o1, npaths, same1, np.concatenate([[0], np.cumsum(npaths)]))
+    assert not np.array_equal(g1["score_xi"], g["score_xi"])
 
 
 def test_model_mode_tabulates_before_every_estimate(sdd, oracle_mod):
@@ -279,7 +289,7 @@ def test_mesh_steps_with_control_variate_match_oracle(sdd, oracle_mod, mode):
         else:
             T = mlp.field_gradient_table(*state)
         new, o = oracle_mod.dd_step(w, state[0], state[1], sub_x=sub, sub_y=sub, dt=dt, Dt=Dt, n_paths=paths, seed=9,
-                                    step_index=step, nodes_ij=(ii, jj), cv_table=_h(T))
+                                    step_index=step, nodes_ij=(ii, jj), cv_table=_h(T), cv_pairs=mode == "fields")
         for f in ("xi", "eta"):
             d = np.abs(g["mean_" + f] - o["mean_" + f])
             assert np.all(d <= 3 * o["se_" + f] + 1e-4), (step, f, d.max())

@@ -111,3 +111,38 @@ def test_field_gradient_model(oracle_mod):
         r = (a["se_" + f] / b["se_" + f]) ** 2
         assert np.median(r) > want, (f, np.median(r))
         assert np.all(np.abs(a["mean_" + f] - b["mean_" + f]) < 4 * np.hypot(a["se_" + f], b["se_" + f]))
+
+
+def test_pair_evaluated_model_is_unbiased_and_matches_per_step_for_a_static_field(oracle_mod):
+    # the model evaluated once per sub-step pair (at X_{2m}, for both increments) is known before
+    # both increments, so the estimate stays unbiased; for a model that varies only in space on
+    # scales far above a sub-step's spread (the previous fields' gradient) it removes as much
+    # variance as the per-sub-step evaluation
+    from oracle import mlp
+    n = 65
+    X, Y = W.grid(n)
+    xi0 = X + 0.02 * np.sin(np.pi * X) * np.sin(np.pi * Y)
+    eta0 = Y + 0.01 * np.sin(2 * np.pi * X) * np.sin(np.pi * Y)
+    T = mlp.field_gradient_table(xi0, eta0)
+    P = oracle_mod.Problem(W.w_front(n, 0.1), xi0, eta0)
+    xs, ys = W.interface_node_coords(n, n, 2, 2)
+    pick = np.arange(0, xs.size, 6)
+    kw = dict(dt=1e-4, Dt=1e-2, seed=5, record=True)
+    N = 3000
+    a = oracle_mod.interface_mc(P, xs[pick], ys[pick], N, **kw)
+    b = oracle_mod.interface_mc(P, xs[pick], ys[pick], N, cv_table=T, **kw)
+    c = oracle_mod.interface_mc(P, xs[pick], ys[pick], N, cv_table=T, cv_pairs=True, **kw)
+    np.testing.assert_array_equal(a["code"], c["code"])
+    assert not np.array_equal(b["score_xi"], c["score_xi"])          # the pair evaluation is really used
+    for f in ("xi", "eta"):
+        rb = np.median((a["se_" + f] / b["se_" + f]) ** 2)
+        rc = np.median((a["se_" + f] / c["se_" + f]) ** 2)
+        assert rc > 0.9 * rb, (f, rb, rc)
+        D = (c["score_" + f] - a["score_" + f]).reshape(pick.size, N)
+        z = D.mean(axis=1) / (D.std(axis=1, ddof=1) / math.sqrt(N) + 1e-300)
+        assert np.all(np.abs(z) < 4.5), z
+    # the bridge test draws per sub-step: no pairs, the flag changes nothing
+    d = oracle_mod.interface_mc(P, xs[pick][:3], ys[pick][:3], 500, cv_table=T, cv_pairs=True, exit_mode=1,
+                                **{k: v for k, v in kw.items()})
+    e = oracle_mod.interface_mc(P, xs[pick][:3], ys[pick][:3], 500, cv_table=T, exit_mode=1, **kw)
+    np.testing.assert_array_equal(d["score_xi"], e["score_xi"])
