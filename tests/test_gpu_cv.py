@@ -298,3 +298,26 @@ def test_mesh_steps_with_control_variate_match_oracle(sdd, oracle_mod, mode):
         iface_gap = max(np.abs(g["mean_xi"] - o["mean_xi"]).max(), np.abs(g["mean_eta"] - o["mean_eta"]).max())
         assert max(np.abs(gx - new[0]).max(), np.abs(ge - new[1]).max()) <= iface_gap + 1e-9
         state = [gx, ge]    # continue from the GPU's fields (the oracle's differ by the MC rounding)
+
+
+@pytest.mark.parametrize("mode", ["fields", "table"])
+def test_zero_map_with_control_variate_changes_no_result(sdd, mode):
+    # the control-variate kernels read the drift through the zero map too: every path record must be
+    # the one the kernel without the map computes, bit for bit
+    n = 257
+    X, Y = W.grid(n)
+    bump = np.exp(-((X - 0.5) ** 2 + (Y - 0.55) ** 2) / 0.01)
+    xi0, eta0 = X + 0.01 * bump, Y - 0.008 * bump          # the identity mesh but near the middle
+    ctx = _ctx(sdd, W.w_ring(n, 0.0), xi0, eta0)
+    if mode == "fields":
+        sdd.sdd_cv_enable(ctx, sdd.SDD_CV_FIELDS)
+    else:
+        from oracle import mlp
+        _set_table(sdd, ctx, mlp.field_gradient_table(xi0, eta0))
+        sdd.sdd_cv_enable(ctx, sdd.SDD_CV_TABLE)
+    xs, ys = W.interface_node_coords(n, n, 2, 2)
+    kw = dict(dt=1e-4, Dt=1e-2, seed=12, paths_per_task=128, block_threads=256)
+    on = _np(sdd.sdd_interface_mc_record(ctx, xs, ys, 600, zero_map=1, **kw))
+    off = _np(sdd.sdd_interface_mc_record(ctx, xs, ys, 600, zero_map=2, **kw))
+    for k in on:
+        np.testing.assert_array_equal(on[k], off[k], err_msg=k)

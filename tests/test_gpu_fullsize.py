@@ -37,6 +37,32 @@ def _stats(sdd, ctx):
     return {k: v.cpu().numpy() for k, v in sdd.sdd_last_interface_stats(ctx).items()}
 
 
+def _path_by_path(sdd, oracle_mod, P, fields, w, xs, ys, pick, paths, dt, Dt, step, g):
+    """The sampled nodes once more, each on its own context with the same w and fields and its own
+    node word, through the per-path record entry point: its records against the oracle's path by
+    path, and its node results against the step's (the step scored its paths in another kernel and
+    summed them in another order)."""
+    import torch
+    from tests import _parity as PT
+    n = w.shape[0]
+    c = sdd.sdd_init(n, n, 1, 1, w=torch.from_numpy(np.ascontiguousarray(w, np.float32)).cuda(),
+                     xi0=torch.from_numpy(fields[0]).cuda(), eta0=torch.from_numpy(fields[1]).cuda())
+    for k, node in enumerate(pick):
+        x, y = xs[node:node + 1], ys[node:node + 1]
+        r = {key: v.cpu().numpy() for key, v in sdd.sdd_interface_mc_record(
+            c, x, y, [paths], dt=dt, Dt=Dt, seed=0, step_index=step, node_word0=int(node)).items()}
+        o = oracle_mod.interface_mc(P, x, y, paths, dt=dt, Dt=Dt, seed=0, step_index=step,
+                                    node_ids=np.array([node], np.uint32), record=True)
+        same, rep = PT.assert_records(r, o)
+        PT.assert_flips_near_boundary(oracle_mod, P, x, y, [paths], r, o, same, dt=dt, Dt=Dt, seed=0,
+                                      step_index=step, node_ids=np.array([node], np.uint32))
+        for f in ("xi", "eta"):
+            assert abs(r["mean_" + f][0] - g["mean_" + f][node]) <= 1e-6, (node, f)
+            assert abs(r["se_" + f][0] - g["se_" + f][node]) <= 1e-6 * max(1.0, g["se_" + f][node]), (node, f)
+        for key in ("n_exit", "path_steps"):
+            assert r[key][0] == g[key][node], (node, key)
+
+
 def _compare(g, o, pick):
     for f in ("xi", "eta"):
         d = np.abs(g["mean_" + f][pick] - o["mean_" + f])
@@ -52,11 +78,15 @@ def test_front257_pipelined_steps_full_size_sampled_nodes(sdd, oracle_mod):
     n, Dt, dt, paths = 257, 1e-2, 1e-4, 10000
     kw = dict(dt=dt, Dt=Dt, seed=0, paths_per_node=paths, rtol=1e-12, max_iter=20000, tune=1)
     w = [W.w_front(n, k * Dt) for k in range(2)]
-    # A: two steps back to back (the second runs the first's solve beside its paths)
+    # A: two steps back to back (the second runs the first's solve beside its paths, then scores its
+    # survivors and exits from their records once the new fields are final); the fields between
+    # them read out (which enqueues the pending iterations early and changes no result)
     a = _ctx(sdd, n, 2, w[0])
-    for k in range(2):
-        sdd.sdd_set_w(a, torch.from_numpy(w[k]).cuda())
-        sdd.sdd_step(a, **kw)
+    sdd.sdd_set_w(a, torch.from_numpy(w[0]).cuda())
+    sdd.sdd_step(a, **kw)
+    fa1 = [t.cpu().numpy() for t in sdd.sdd_get_fields(a)]
+    sdd.sdd_set_w(a, torch.from_numpy(w[1]).cuda())
+    sdd.sdd_step(a, **kw)
     assert sdd.sdd_pipeline_in_use(a)
     a2 = _stats(sdd, a)
     # B: one step, then its fields (the first step's solve flushed)
@@ -76,6 +106,10 @@ def test_front257_pipelined_steps_full_size_sampled_nodes(sdd, oracle_mod):
     o2 = oracle_mod.interface_mc(oracle_mod.Problem(w[1], f1[0], f1[1]), xs[pick], ys[pick], paths, dt=dt, Dt=Dt,
                                  seed=0, step_index=1, node_ids=pick.astype(np.uint32))
     _compare(a2, o2, pick)
+    # the deferred scoring of the pipelined step, path by path (six of the sampled nodes)
+    sub_pick = pick[::2]
+    _path_by_path(sdd, oracle_mod, oracle_mod.Problem(w[1], fa1[0], fa1[1]), fa1, w[1], xs, ys, sub_pick, paths, dt,
+                  Dt, 1, a2)
 
 
 def test_ring2049_step_full_size_sampled_nodes(sdd, oracle_mod):
@@ -93,6 +127,9 @@ def test_ring2049_step_full_size_sampled_nodes(sdd, oracle_mod):
     on_ring = np.flatnonzero(np.abs(r - 0.25) < 2e-3)[:4]
     pick = np.unique(np.concatenate([on_ring, [0, 1, 1023, 2046, 14000, 28607, 28608]]))
     xi0, eta0 = W.identity_fields(n)
-    o = oracle_mod.interface_mc(oracle_mod.Problem(w0, xi0, eta0), xs[pick], ys[pick], paths, dt=dt, Dt=Dt,
-                                seed=0, step_index=0, node_ids=pick.astype(np.uint32))
+    P = oracle_mod.Problem(w0, xi0, eta0)
+    o = oracle_mod.interface_mc(P, xs[pick], ys[pick], paths, dt=dt, Dt=Dt, seed=0, step_index=0,
+                                node_ids=pick.astype(np.uint32))
     _compare(g, o, pick)
+    # the step's deferred scoring, path by path, at four of the sampled nodes
+    _path_by_path(sdd, oracle_mod, P, (xi0, eta0), w0, xs, ys, pick[[0, 2, 5, -1]], paths, dt, Dt, 0, g)
