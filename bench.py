@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-cv", action="store_true", help="skip the control-variate measurements")
     ap.add_argument("--no-model", action="store_true", help="skip the learned control variate's measurement")
+    ap.add_argument("--cv-order", type=int, default=0,
+                    help="binomial smoothing order of the field-gradient control variate (0: the library's choice)")
     ap.add_argument("--paths", type=int, default=None)
     ap.add_argument("--workload", choices=["ring2049", "front257", "batch64", "heat65", "cv65", "ring41", "exit65"],
                     default=DEFAULT_WORKLOAD)
@@ -471,6 +473,8 @@ def run_ours(args, world, rank, local):
                                          batch=4096, lr=3e-3, slices=4, init_seed=7)
                 train = {k2: train[k2] for k2 in ("samples_ms", "train_ms", "tabulate_ms", "rows", "steps")}
             sdd.sdd_cv_enable(ctx, mode)
+            if key == "fields":
+                sdd.sdd_cv_set_fields_order(ctx, args.cv_order)
             cv_ms, cv_steps, cv_pk = 0.0, 0, []
             for k in range(kc):
                 flush.zero_()
@@ -491,19 +495,26 @@ def run_ours(args, world, rank, local):
                 o = sdd.sdd_interface_mc(ctx, xs_, ys_, np.full(xs_.size, paths), dt=WL.dt, Dt=WL.Dt, seed=seed + 99)
                 est[which] = {k2: v.cpu().numpy() for k2, v in o.items()}
             sdd.sdd_cv_enable(ctx, sdd.SDD_CV_OFF)
-            ratio = {}
+            # equal error over the sampled nodes: the plain estimator's summed variance over the
+            # control variate's (the paths per node that match its RMS error); the median of the
+            # per-node ratios for information
+            ratio, median = {}, {}
             for f in ("xi", "eta"):
                 a_, c_ = est["plain"]["se_" + f], est["cv"]["se_" + f]
                 ok = c_ > 0
-                ratio[f] = float(np.median((a_[ok] / c_[ok]) ** 2))
+                ratio[f] = float(np.sum(a_ ** 2) / np.sum(c_ ** 2))
+                median[f] = float(np.median((a_[ok] / c_[ok]) ** 2))
             cv_value = cv_steps / (cv_ms / 1e3)
             equal_error[key] = {"control_variate": what, "steps": kc, "path_steps_per_s": cv_value,
                                 "paths_kernel_ms": statistics.mean(cv_pk),
+                                "paths_kernel_ms_per_step": [round(v, 2) for v in cv_pk],
                                 "paths_kernel_ms_vs_plain": statistics.mean(cv_pk) / mean_paths_ms,
-                                "variance_ratio_vs_plain": ratio,
+                                "variance_ratio_vs_plain": ratio, "variance_ratio_median_node": median,
                                 "path_steps_per_s_at_equal_error": cv_value * min(ratio.values()),
                                 "interface_nodes_per_s_at_equal_error": nodes * kc / (cv_ms / 1e3) * min(ratio.values()),
                                 "training": train}
+            if key == "fields":
+                equal_error[key]["smoothing_order"] = sdd.sdd_cv_fields_order(ctx)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

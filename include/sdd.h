@@ -126,7 +126,8 @@ typedef struct {
  *               node's results are then those of the whole list, bit for
  *               bit. A batch numbers its nodes from node_word0 on.
  *   zero_map    0: automatic (the autotuner's choice for the node set, else
- *               on); 1 on; 2 off. With it on, the path kernel of a context
+ *               on; always on with a control variate); 1 on; 2 off. With it
+ *               on, the path kernel of a context
  *               reads one shared all-zero drift record wherever the drift
  *               records of a stretch of cells are all zero (w constant
  *               there): the same values, so the same results bit for bit,
@@ -223,15 +224,19 @@ sdd_status sdd_interface_mc_record(sdd_ctx* ctx, const sdd_nodes* nodes, const s
  *   SDD_CV_MODEL   the trained network (sdd_cv_train or sdd_cv_set_model),
  *                  tabulated again from the context's w before every
  *                  estimate (inside the mesh step's graph);
- *   SDD_CV_FIELDS  one slice from the fields at t_{n-1}: the finite-difference
- *                  gradients of xi and eta (no training; over a short mesh
- *                  step the solution's gradient stays close to it). With the
- *                  paper's test, whose normals come in sub-step pairs, this
- *                  gradient is evaluated once per pair, at the pair's first
- *                  point, for both of its increments: it is known before
- *                  both, so the estimate stays unbiased, and a fixed field's
- *                  gradient varies over distances far above a pair's
- *                  spread, so the variance it removes is the same. */
+ *   SDD_CV_FIELDS  one value per cell from the fields at t_{n-1} (no
+ *                  training; over a short mesh step the solution's gradient
+ *                  stays close to theirs): the finite-difference gradients of
+ *                  xi and eta at the nodes (the table sdd_cv_get_table then
+ *                  returns, one slice), smoothed by the binomial filter of
+ *                  odd order o along x, then along y, centred on the cells
+ *                  (cell i takes node i - r + m with weight C(o, m) 2^-o,
+ *                  m = 0..o, r = (o - 1) / 2, nodes past an edge read as the
+ *                  edge node), in single precision. G at a point is the value
+ *                  of its cell, read at every sub-step. The smoothing removes
+ *                  the grid-scale noise that the interface values' Monte
+ *                  Carlo error leaves in the fields' differences. o: see
+ *                  sdd_cv_set_fields_order. */
 #define SDD_CV_OFF 0
 #define SDD_CV_TABLE 1
 #define SDD_CV_MODEL 2
@@ -242,6 +247,20 @@ sdd_status sdd_cv_enable(sdd_ctx* ctx, int32_t mode);
 /* A copy of the context's current table in the layout of sdd_cv_set_table
  * (DEVICE, slices * ny * nx * 4 doubles; slices as last set or tabulated). */
 sdd_status sdd_cv_get_table(sdd_ctx* ctx, double* grad);
+
+/* The smoothing order o of SDD_CV_FIELDS: odd, 1..255, or 0 (the default) for
+ * the grid's order 2 floor((m - 1)^2 / 16384) - 1 within 1..33, m the larger
+ * side's node count (129: 1, 257: 7, 513: 31, from 1025: 33).
+ * SDD_EINVAL for any other value. sdd_cv_fields_order returns the order in
+ * use (0 for a null context). */
+sdd_status sdd_cv_set_fields_order(sdd_ctx* ctx, int32_t order);
+int32_t sdd_cv_fields_order(const sdd_ctx* ctx);
+
+/* With SDD_CV_FIELDS enabled: the cell values from the context's current
+ * fields, written to `cells` (DEVICE, (ny - 1) * (nx - 1) * 4 floats, row-major
+ * cells, each (d xi/dx, d xi/dy, d eta/dx, d eta/dy)), asynchronously on the
+ * context's stream. SDD_EINVAL when the mode is another. */
+sdd_status sdd_cv_get_cells(sdd_ctx* ctx, float* cells);
 
 /* ------------------------------------------------------------------------
  * Learned control variate.

@@ -55,7 +55,7 @@ class _Problem(ctypes.Structure):
                 ("bx", ctypes.c_void_p), ("by", ctypes.c_void_p),
                 ("xi0", ctypes.c_void_p), ("eta0", ctypes.c_void_p),
                 ("faces", ctypes.c_void_p), ("cv", ctypes.c_void_p), ("cv_slices", ctypes.c_int),
-                ("cv_pairs", ctypes.c_int)]
+                ("cv_cell", ctypes.c_int)]
 
 
 class _Params(ctypes.Structure):
@@ -227,7 +227,7 @@ def sub_steps(dt: float, Dt: float) -> int:
 
 def interface_mc(problem: Problem, xs, ys, n_paths, *, dt: float, Dt: float, seed: int = 0,
                  exit_mode: int = 0, step_index: int = 0, node_ids=None,
-                 record: bool = False, threads: int | None = None, cv_table=None, cv_pairs: bool = False):
+                 record: bool = False, threads: int | None = None, cv_table=None):
     """Estimate xi, eta at the given nodes over one mesh step (Eq. 7b, Sec. 4).
 
     exit_mode: 0 fixed sub-steps with the plain exit test, 1 fixed sub-steps
@@ -241,9 +241,9 @@ def interface_mc(problem: Problem, xs, ys, n_paths, *, dt: float, Dt: float, see
     threads: worker threads over nodes (ctypes releases the GIL), default all cores.
     cv_table: optional control-variate model gradients, shape (S, ny, nx, 4):
     slice q serves the sub-steps j with floor(j S / K) = q; components are
-    d/dx, d/dy of the xi model and of the eta model at the nodes.
-    cv_pairs: with exit_mode 0, evaluate the model once per sub-step pair, at
-    X_{2m} in the slice of sub-step 2m, for both increments of the pair.
+    d/dx, d/dy of the xi model and of the eta model at the nodes, interpolated
+    bilinearly; or shape (1, ny - 1, nx - 1, 4): one value per cell, the model
+    at a point being the value of its cell.
     """
     lib = _load()
     xs = np.ascontiguousarray(xs, dtype=np.float64)
@@ -259,11 +259,12 @@ def interface_mc(problem: Problem, xs, ys, n_paths, *, dt: float, Dt: float, see
         if exit_mode == 2:
             raise ValueError("the control variate needs fixed sub-steps (exit_mode 0 or 1)")
         cv = np.ascontiguousarray(cv_table, dtype=np.float64)
-        assert cv.ndim == 4 and cv.shape[1:] == (problem.ny, problem.nx, 4)
+        cell = cv.shape[1:] == (problem.ny - 1, problem.nx - 1, 4)
+        assert cv.ndim == 4 and (cv.shape[1:] == (problem.ny, problem.nx, 4) or (cell and cv.shape[0] == 1))
     P = _Problem(problem.nx, problem.ny, problem.bx.ctypes.data, problem.by.ctypes.data,
                  problem.xi0.ctypes.data, problem.eta0.ctypes.data, problem.faces.ctypes.data,
                  cv.ctypes.data if cv is not None else None, cv.shape[0] if cv is not None else 0,
-                 1 if cv_pairs else 0)
+                 1 if cv is not None and cell else 0)
     Q = _Params(dt, K, exit_mode, seed, step_index)
     stats = np.zeros((count, 6))
     total = int(n_paths.sum())
@@ -356,14 +357,13 @@ def boundary_grid(faces, nx: int, ny: int, field: int, inner):
 
 def dd_step(w, xi, eta, *, sub_x: int, sub_y: int, dt: float, Dt: float, n_paths: int, seed: int,
             step_index: int, nodes_ij, exit_mode: int = 0, faces=None, threads=None, node_word0: int = 0,
-            cv_table=None, keypoints: bool = False, key_spacing: int = 0, cv_pairs: bool = False):
+            cv_table=None, keypoints: bool = False, key_spacing: int = 0):
     """One mesh step t_{n-1} -> t_n of the method (Sec. 4): the interface
     estimate at the nodes nodes_ij = (i, j) (their position is their node index
     in the random stream), then the implicit subdomain solves by LU with those
     values and the face data as Dirichlet data. node_word0 offsets the node
     word of the random stream (instances evaluated together number their nodes
-    in sequence); cv_table and cv_pairs, if given, are the control variate of
-    interface_mc. keypoints: estimate only at the key points of Sec. 4 and fill
+    in sequence); cv_table, if given, is the control variate of interface_mc. keypoints: estimate only at the key points of Sec. 4 and fill
     the rest of each interface line by PCHIP (oracle.keypoints; nodes_ij must
     then be the whole interface list; key_spacing adds every key_spacing-th
     position of each line). Returns ([xi_n, eta_n], stats)."""
@@ -378,8 +378,7 @@ def dd_step(w, xi, eta, *, sub_x: int, sub_y: int, dt: float, Dt: float, n_paths
         mask = kp.key_mask(P.w, sub_x, sub_y, key_spacing)
         assert mask.size == xs.size
         rk = interface_mc(P, xs[mask], ys[mask], n_paths, dt=dt, Dt=Dt, seed=seed, exit_mode=exit_mode,
-                          step_index=step_index, threads=threads, node_ids=ids[mask], cv_table=cv_table,
-                          cv_pairs=cv_pairs)
+                          step_index=step_index, threads=threads, node_ids=ids[mask], cv_table=cv_table)
         r = {k: np.zeros(xs.size, dtype=v.dtype) for k, v in rk.items() if np.ndim(v) == 1 and len(v) == mask.sum()}
         for k in r:
             r[k][mask] = rk[k]
@@ -388,7 +387,7 @@ def dd_step(w, xi, eta, *, sub_x: int, sub_y: int, dt: float, Dt: float, n_paths
         r["key"] = mask
     else:
         r = interface_mc(P, xs, ys, n_paths, dt=dt, Dt=Dt, seed=seed, exit_mode=exit_mode, step_index=step_index,
-                         threads=threads, node_ids=ids, cv_table=cv_table, cv_pairs=cv_pairs)
+                         threads=threads, node_ids=ids, cv_table=cv_table)
     bx = boundary_grid(P.faces, P.nx, P.ny, 0, P.xi0)
     be = boundary_grid(P.faces, P.nx, P.ny, 1, P.eta0)
     bx[jj, ii] = r["mean_xi"]

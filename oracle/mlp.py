@@ -303,6 +303,37 @@ def field_gradient_table(xi, eta):
     return np.stack([gx, gy, hx, hy], axis=-1)[None]
 
 
+CV_CELL_ORDER = 33
+
+
+def binomial_weights(order: int):
+    """C(order, m) 2^-order, m = 0..order: the binomial smoothing filter."""
+    return np.array([math.comb(order, m) for m in range(order + 1)], dtype=np.float64) / 2.0 ** order
+
+
+def field_cell_gradient_table(xi, eta, order: int = CV_CELL_ORDER):
+    """The untrained control variate as one value per cell: the finite-difference
+    gradients of the fields at t_{n-1} (field_gradient_table) smoothed by the
+    binomial filter of odd order `order` along x, then along y, centred on the
+    cells: cell i takes node i - r + m with weight C(order, m) 2^-order,
+    m = 0..order, r = (order - 1) / 2, nodes past an edge replaced by the edge
+    node. The smoothing removes the grid-scale noise that the interface
+    values' Monte Carlo error leaves in the fields' differences; any model keeps
+    the estimate unbiased. Shape (1, ny - 1, nx - 1, 4)."""
+    if order < 1 or order % 2 != 1:
+        raise ValueError("the smoothing order must be odd and positive")
+    g = field_gradient_table(xi, eta)[0]
+    wts = binomial_weights(order)
+    r = (order - 1) // 2
+    for axis in (1, 0):
+        L = g.shape[axis]
+        out = np.zeros_like(np.take(g, np.arange(L - 1), axis=axis))
+        for m, wm in enumerate(wts):
+            out += wm * np.take(g, np.clip(np.arange(L - 1) - r + m, 0, L - 1), axis=axis)
+        g = out
+    return g[None]
+
+
 # ---------------------------------------------------------------- training data
 
 def sample_starts(seed: int, words):

@@ -153,6 +153,18 @@ double orc_bilinear(int nx, int ny, const double* f, double x, double y)
     return (1.0 - s) * (1.0 - t) * f00 + s * (1.0 - t) * f10 + (1.0 - s) * t * f01 + s * t * f11;
 }
 
+/* Row-major index j (nx - 1) + i of the cell holding (x, y): the cell of
+ * orc_bilinear. */
+static int64_t cell_index(int nx, int ny, double x, double y)
+{
+    int i = (int)floor(x * (double)(nx - 1)), j = (int)floor(y * (double)(ny - 1));
+    if (i < 0) i = 0;
+    if (i > nx - 2) i = nx - 2;
+    if (j < 0) j = 0;
+    if (j > ny - 2) j = ny - 2;
+    return (int64_t)j * (nx - 1) + i;
+}
+
 /* Bilinear interpolation of a node table whose values are strided by 4
  * (one of the four components of a control-variate slice). */
 static double cv_bilinear(int nx, int ny, const double* f, double x, double y)
@@ -250,10 +262,9 @@ typedef struct {
      * NULL or cv_slices = 0 for the plain estimator */
     const double* cv;
     int cv_slices;
-    /* with the paper's test (sub-steps drawn in pairs): 1 evaluates the model
-     * once per sub-step pair, at the pair's first point X_{2m} and in the slice
-     * of sub-step 2m, for both increments of the pair */
-    int cv_pairs;
+    /* 1: cv holds one table of cell values, (nx-1)*(ny-1)*4 doubles, and the
+     * model at a point is the value of its cell (the cell of orc_bilinear) */
+    int cv_cell;
 } orc_problem;
 
 typedef struct {
@@ -413,7 +424,6 @@ static int32_t run_path(const orc_problem* P, const orc_params* Q, uint32_t node
     double x = x0, y = y0;
     uint32_t words[4];
     const int cv_on = P->cv && P->cv_slices > 0;
-    const int cv_pairs = cv_on && P->cv_pairs && Q->exit_mode == 0;
     double cv_sum[2] = {0.0, 0.0};
     double g[4] = {0.0, 0.0, 0.0, 0.0};
     for (int32_t j = 0; j < Q->K; ++j) {
@@ -437,10 +447,12 @@ static int32_t run_path(const orc_problem* P, const orc_params* Q, uint32_t node
         /* control variate: the model gradient at X_j (before the increment)
          * times the increment's noise sqrt(2) dW_j, summed over the sub-steps
          * the path takes; its expectation is zero for any model whose value
-         * is known before the increment. With cv_pairs the value at X_{2m}
-         * serves sub-steps 2m and 2m + 1 (known before both increments). */
+         * is known before the increment. */
         if (cv_on) {
-            if (!cv_pairs || (j & 1) == 0) {
+            if (P->cv_cell) {
+                const double* T = P->cv + 4 * cell_index(nx, ny, x, y);
+                for (int c = 0; c < 4; ++c) g[c] = T[c];
+            } else {
                 int q = (int)(((int64_t)j * P->cv_slices) / Q->K);
                 if (q > P->cv_slices - 1) q = P->cv_slices - 1;
                 const double* T = P->cv + (int64_t)q * 4 * nx * ny;

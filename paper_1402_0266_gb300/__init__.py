@@ -37,6 +37,7 @@ EXPORTS = [
     "sdd_batch_destroy", "sdd_autotune", "sdd_batch_autotune", "sdd_cv_set_table", "sdd_cv_enable",
     "sdd_mlp_init", "sdd_cv_samples", "sdd_mlp_norm", "sdd_mlp_grad", "sdd_mlp_train", "sdd_cv_tabulate",
     "sdd_cv_train", "sdd_cv_get_model", "sdd_cv_losses", "sdd_cv_get_table", "sdd_cv_set_model",
+    "sdd_cv_set_fields_order", "sdd_cv_fields_order", "sdd_cv_get_cells",
     "sdd_set_solver", "sdd_solver_in_use", "sdd_set_keypoints", "sdd_keypoint_mask",
 ]
 
@@ -184,6 +185,8 @@ def lib():
                 "sdd_cv_get_model": [vp, vp, vp],
                 "sdd_cv_losses": [vp, vp, i64],
                 "sdd_cv_get_table": [vp, vp],
+                "sdd_cv_set_fields_order": [vp, i32],
+                "sdd_cv_get_cells": [vp, vp],
                 "sdd_cv_set_model": [vp, vp, vp, i32],
                 "sdd_set_solver": [vp, i32],
                 "sdd_set_keypoints": [vp, i32, i32],
@@ -197,6 +200,8 @@ def lib():
                 f.argtypes = args
                 f.restype = ctypes.c_int
             L.sdd_get_step_index.restype = ctypes.c_uint32
+            L.sdd_cv_fields_order.argtypes = [vp]
+            L.sdd_cv_fields_order.restype = ctypes.c_int32
             L.sdd_static_scratch_bytes.restype = ctypes.c_int64
             L.sdd_batch_last_error.restype = ctypes.c_char_p
             L.sdd_batch_destroy.restype = None
@@ -748,6 +753,23 @@ def sdd_cv_get_table(ctx: Ctx, slices: int):
     torch = _torch()
     out = torch.zeros((slices, ctx.ny, ctx.nx, 4), dtype=torch.float64, device="cuda")
     ctx._check(lib().sdd_cv_get_table(ctx.handle, _ptr(out)))
+    return out
+
+
+def sdd_cv_set_fields_order(ctx: Ctx, order: int):
+    """The binomial smoothing order of SDD_CV_FIELDS (odd 1..255; 0: by the grid)."""
+    ctx._check(lib().sdd_cv_set_fields_order(ctx.handle, int(order)))
+
+
+def sdd_cv_fields_order(ctx: Ctx) -> int:
+    return int(lib().sdd_cv_fields_order(ctx.handle))
+
+
+def sdd_cv_get_cells(ctx: Ctx):
+    """SDD_CV_FIELDS's cell values from the current fields, cuda float32 (ny - 1, nx - 1, 4)."""
+    torch = _torch()
+    out = torch.zeros((ctx.ny - 1, ctx.nx - 1, 4), dtype=torch.float32, device="cuda")
+    ctx._check(lib().sdd_cv_get_cells(ctx.handle, _ptr(out)))
     return out
 
 

@@ -56,6 +56,7 @@ struct Plan {
 
     int block = 256, grid = 0, ppt = 0;
     int zero_map = 1;   // single-instance launches: read the drift through the zero map (1) or not (0)
+    bool zero_map_auto = true;   // zero_map is the tuner's choice for the plain kernel (not the caller's)
     int64_t nnodes = 0, ntasks = 0, total_paths = 0;
     std::vector<NodeDev> nodes;
     std::vector<Task> tasks;
@@ -120,6 +121,8 @@ struct sdd_ctx {
     int cv_slices = 0;
     int cv_mode = 0;           // 0 off, 1 the table as set, 2 the model re-tabulated per estimate, 3 field gradient
     int cv_model_slices = 0;   // time slices of the model's table
+    DevBuf<float4> cv_tmp, cv_cell;   // field gradient (mode 3): the smoothing's scratch, the cell values
+    int cv_order = 0;                 // its binomial smoothing order (0: by the grid, cv_fields_order)
 
     // learned control variate: node features, training data, model, scratch
     DevBuf<double> cv_w64, cv_r64, cv_table64, cv_norm_scratch, cv_sxy, cv_smean[2];
@@ -291,6 +294,7 @@ InstDev inst_host(const sdd_ctx* c)
     I.cell_bias = 0x4B000000u * (uint32_t)c->nx;
     I.cv_slices = c->cv_slices;
     I.cvcoef = c->cvcoef.p;
+    I.cvcell = c->cv_cell.p;
     return I;
 }
 
@@ -372,6 +376,33 @@ struct NodeSeg {
     int32_t inst;   // instance index (tables, outputs)
     uint32_t ctr0;  // node word of the Philox counter of its first node
 };
+
+// Position of a point of the unit square along a Hilbert curve through the
+// 4096 x 4096 grid of squares of side 2^-12 (24 bits). Consecutive positions
+// are neighbouring squares, so nodes taken in this order lie close together.
+uint64_t hilbert_key(double xf, double yf)
+{
+    constexpr uint32_t n = 4096;
+    uint32_t x = (uint32_t)std::min<double>(std::max(xf, 0.0) * n, n - 1);
+    uint32_t y = (uint32_t)std::min<double>(std::max(yf, 0.0) * n, n - 1);
+    uint64_t d = 0;
+    for (uint32_t s = n / 2; s > 0; s >>= 1) {
+        const uint32_t qx = (x & s) ? 1u : 0u, qy = (y & s) ? 1u : 0u;
+        // quadrants in curve order: (0,0), (0,1), (1,1), (1,0)
+        d += (uint64_t)s * s * (qx ? (qy ? 2u : 3u) : (qy ? 1u : 0u));
+        if (!qy) {
+            // the lower quadrants are traversed transposed, the right one also mirrored
+            if (qx) {
+                x ^= s - 1;
+                y ^= s - 1;
+            }
+            std::swap(x, y);
+        }
+        x &= s - 1;
+        y &= s - 1;
+    }
+    return d;
+}
 
 // Build (or reuse) the plan of one or more node lists.
 sdd_status build_plan_segs(std::string* err, int sm_count, Plan& P, const std::vector<NodeSeg>& segs, int ppt_req,
@@ -459,13 +490,16 @@ sdd_status build_plan_segs(std::string* err, int sm_count, Plan& P, const std::v
     const double* x = P.hx.data();
     const double* y = P.hy.data();
     const int64_t* np = P.hp.data();
-    // Tasks go node by node, nodes far from the boundary first: their paths
-    // run the whole mesh step, so the short tasks of nodes near the boundary
-    // fill the end of the launch.
+    // Tasks go node by node, the nodes of each instance along a Hilbert curve:
+    // the nodes whose paths run at the same time lie close together, and so
+    // do the cells their paths read (L2 keeps that neighbourhood; in the order
+    // of the nodes' distance from the boundary the nodes in flight lay around
+    // the whole square and the cell tables of a large grid spilled to DRAM).
     std::vector<int64_t> order(count);
     for (int64_t k = 0; k < count; ++k) order[k] = k;
-    auto dist = [&](int64_t k) { return std::min(std::min(x[k], 1.0 - x[k]), std::min(y[k], 1.0 - y[k])); };
-    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return dist(a) > dist(b); });
+    std::vector<uint64_t> hk(count);
+    for (int64_t k = 0; k < count; ++k) hk[k] = ((uint64_t)(uint32_t)inst_of[k] << 26) | hilbert_key(x[k], y[k]);
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return hk[a] < hk[b]; });
     for (int64_t k : order) {
         NodeDev& nd = P.nodes[k];
         nd.x = x[k];
@@ -532,7 +566,7 @@ sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const Out
                        int K, uint64_t seed, uint32_t step_index, const uint32_t* step_ptr, int exit_mode,
                        const RecDev* rec, cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_b, int cv_slices = 0,
                        const uint8_t* node_mask = nullptr, void* surv = nullptr, cudaEvent_t join = nullptr,
-                       ZmapRef zm = ZmapRef{}, bool cv_pairs = false);
+                       ZmapRef zm = ZmapRef{}, bool cv_cell = false);
 
 const TunedShape* find_tuned(const std::vector<TunedShape>& t, uint64_t key)
 {
@@ -574,7 +608,7 @@ sdd_status autotune_plan(std::string* err, int sm_count, const std::vector<NodeS
         ZmapRef z = zm;
         if (!use_map) z.map = nullptr;
         for (int block : {128, 256, 512}) {
-            if (block > path_kernel_max_block(exit_mode, false, z.single)) continue;
+            if (block > path_kernel_max_block(exit_mode, 0, z.single)) continue;
             for (int ppt : {32, 64, 128, 256, 512, 1024}) {
                 Plan P;
                 st = build_plan_segs(err, sm_count, P, segs, ppt, block, exit_mode, false);
@@ -632,7 +666,7 @@ sdd_status build_plan(sdd_ctx* c, Plan& P, const double* x, const double* y, con
 sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const OutDev* outs, const OutDev& out0, double dt,
                        int K, uint64_t seed, uint32_t step_index, const uint32_t* step_ptr, int exit_mode,
                        const RecDev* rec, cudaStream_t s, cudaEvent_t ev_a, cudaEvent_t ev_b, int cv_slices,
-                       const uint8_t* node_mask, void* surv, cudaEvent_t join, ZmapRef zm, bool cv_pairs)
+                       const uint8_t* node_mask, void* surv, cudaEvent_t join, ZmapRef zm, bool cv_cell)
 {
     if (surv && rec) return fail(err, SDD_EINVAL, "per-path records with deferred survivor scores");
     if (P.nnodes == 0 || P.ntasks == 0) {
@@ -658,7 +692,6 @@ sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const Out
         if (rec) a.rec = *rec;
         a.node_mask = node_mask;
         a.surv = surv;
-        a.cv_pairs = cv_pairs ? 1 : 0;
         if (zm.single) {
             a.single = 1;
             a.one = zm.inst;
@@ -670,6 +703,7 @@ sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const Out
             }
         }
         const bool cv = cv_slices > 0;
+        const int cvm = !cv ? 0 : cv_cell ? 2 : 1;
         if (cv && cv_slices > K) return fail(err, SDD_EINVAL, "more control-variate slices than sub-steps per step");
         if (cv && exit_mode == 2)
             return fail(err, SDD_EINVAL, "the control variate needs fixed sub-steps (exit_mode 0 or 1)");
@@ -677,18 +711,18 @@ sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const Out
             a.cv_bound[q] = cv && q <= cv_slices ? (int32_t)(((int64_t)q * K + cv_slices - 1) / cv_slices) : K + 1;
         CU(err, cudaMemsetAsync(P.d_queue.p, 0, sizeof(int), s));
         // each path kernel is compiled for at most path_kernel_max_block threads per block
-        const int block = std::min(P.block, path_kernel_max_block(exit_mode, cv, a.single != 0));
+        const int block = std::min(P.block, path_kernel_max_block(exit_mode, cvm, a.single != 0));
         const int64_t per_block = block / 32;
         int grid_max = P.grid;
         if (block != P.block || cv || a.single) {
             int dev = 0, sms = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            grid_max = sms * path_kernel_blocks_per_sm(exit_mode, rec != nullptr, block, cv, a.zwords, a.single != 0);
+            grid_max = sms * path_kernel_blocks_per_sm(exit_mode, rec != nullptr, block, cvm, a.zwords, a.single != 0);
         }
         const int grid = (int)std::min<int64_t>(grid_max, std::max<int64_t>(1, (P.ntasks + per_block - 1) / per_block));
         if (ev_a) CU(err, cudaEventRecordWithFlags(ev_a, s, cudaEventRecordExternal));
-        CU(err, launch_paths(a, exit_mode, rec != nullptr, grid, block, s, cv));
+        CU(err, launch_paths(a, exit_mode, rec != nullptr, grid, block, s, cvm));
         if (ev_b) CU(err, cudaEventRecordWithFlags(ev_b, s, cudaEventRecordExternal));
         if (join) CU(err, cudaStreamWaitEvent(s, join, 0));
     }
@@ -717,14 +751,17 @@ sdd_status run_plan_on(std::string* err, Plan& P, const InstDev* inst, const Out
     return SDD_OK;
 }
 
+// The tuner times the plain kernel; where it left the zero map off (the plain kernel is no faster
+// with it) a control-variate launch still takes it: that kernel is bound by L1 wavefronts, which
+// the map saves wherever a warp's lanes share the all-zero record.
 sdd_status run_plan(sdd_ctx* c, Plan& P, double dt, int K, uint64_t seed, uint32_t step_index,
                     const uint32_t* step_ptr, int exit_mode, const OutDev& out, const RecDev* rec, cudaStream_t s,
                     cudaEvent_t ev_a = nullptr, cudaEvent_t ev_b = nullptr, const uint8_t* node_mask = nullptr,
                     void* surv = nullptr, cudaEvent_t join = nullptr)
 {
     return run_plan_on(&c->err, P, c->d_inst.p, nullptr, out, dt, K, seed, step_index, step_ptr, exit_mode, rec, s,
-                       ev_a, ev_b, c->cv_mode ? c->cv_slices : 0, node_mask, surv, join, ctx_zmap(c, P.zero_map != 0),
-                       c->cv_mode == SDD_CV_FIELDS);
+                       ev_a, ev_b, c->cv_mode ? c->cv_slices : 0, node_mask, surv, join,
+                       ctx_zmap(c, P.zero_map != 0 || (P.zero_map_auto && c->cv_mode != 0)), c->cv_mode == SDD_CV_FIELDS);
 }
 
 // Launch shape for a plan: explicit requests win, else a tuned shape for this node set, else the heuristic.
@@ -1295,12 +1332,26 @@ sdd_status tabulate_into_ctx(sdd_ctx* c, const float* theta, const float* norm, 
     return SDD_OK;
 }
 
+// The binomial smoothing order of the field-gradient control variate: the one
+// set, else by the grid: 2 floor((m - 1)^2 / 16384) - 1 for the larger side of
+// m nodes, within 1..33 (129: 1, 257: 7, 513: 31, from 1025: 33). The
+// interface values' Monte Carlo error leaves noise on the grid's scale in the
+// fields' differences, which the filter removes; on finer grids the
+// solution's own structure spans more cells, so the filter can be wider.
+int cv_fields_order(const sdd_ctx* c)
+{
+    if (c->cv_order > 0) return c->cv_order;
+    const double m = (double)std::max(c->nx, c->ny) - 1.0;
+    const int o = 2 * (int)std::floor(m * m / 16384.0) - 1;
+    return std::max(1, std::min(o, 33));
+}
+
 // Buffers of a control-variate mode, allocated before any capture.
 sdd_status cv_mode_buffers(sdd_ctx* c, int mode)
 {
     const size_t nn = (size_t)c->nx * c->ny, cells = (size_t)(c->nx - 1) * (c->ny - 1);
     const int slices = mode == 2 ? c->cv_model_slices : mode == 3 ? 1 : c->cv_slices;
-    if (mode == 2 || mode == 3) {
+    if (mode == 2) {
         const size_t n = (size_t)c->nx * c->ny;
         CU(c, c->cv_w64.alloc(n));
         CU(c, c->cv_r64.alloc(n));
@@ -1310,6 +1361,13 @@ sdd_status cv_mode_buffers(sdd_ctx* c, int mode)
         CU(c, c->cv_table64.alloc(4 * nn * (size_t)slices));
         CU(c, c->cvcoef.alloc(2 * cells * (size_t)slices));
         c->cv_slices = slices;
+        return upload_inst(c);
+    }
+    if (mode == 3) {
+        CU(c, c->cv_table64.alloc(4 * nn));
+        CU(c, c->cv_tmp.alloc((size_t)(c->nx - 1) * c->ny));
+        CU(c, c->cv_cell.alloc(cells));
+        c->cv_slices = 1;
         return upload_inst(c);
     }
     return SDD_OK;
@@ -1330,7 +1388,7 @@ sdd_status enqueue_cv_refresh(sdd_ctx* c, int K, cudaStream_t s)
         CU(c, launch_cv_cells(c->cv_table64.p, c->cv_slices, c->nx, c->ny, c->cvcoef.p, s));
     } else if (c->cv_mode == 3) {
         CU(c, launch_field_grad(c->fld[c->cur][0].p, c->fld[c->cur][1].p, c->nx, c->ny, c->cv_table64.p, s));
-        CU(c, launch_cv_cells(c->cv_table64.p, 1, c->nx, c->ny, c->cvcoef.p, s));
+        CU(c, launch_cv_smooth(c->cv_table64.p, c->nx, c->ny, cv_fields_order(c), c->cv_tmp.p, c->cv_cell.p, s));
     }
     return SDD_OK;
 }
@@ -1550,6 +1608,7 @@ static sdd_status mc_common(sdd_ctx* c, const sdd_nodes* nodes, const sdd_mc_par
                                p->exit_mode, rec != nullptr, p->node_word0);
     if (st != SDD_OK) return st;
     c->mc_plan.zero_map = zmap;
+    c->mc_plan.zero_map_auto = p->zero_map == 0;
     if ((st = prepare(c, c->stream)) != SDD_OK) return st;
     if ((st = enqueue_cv_refresh(c, K, c->stream)) != SDD_OK) return st;
     RecDev rd{};
@@ -1631,6 +1690,33 @@ sdd_status sdd_cv_get_table(sdd_ctx* c, double* grad)
     if (c->cv_slices < 1) return fail(c, SDD_EINVAL, "no control-variate table has been set");
     const size_t n = 4 * (size_t)c->nx * c->ny * (size_t)c->cv_slices;
     CU(c, cudaMemcpyAsync(grad, c->cv_table64.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    return SDD_OK;
+}
+
+sdd_status sdd_cv_set_fields_order(sdd_ctx* c, int32_t order)
+{
+    if (!c) return SDD_EINVAL;
+    if (order != 0 && (order < 1 || order > kCvMaxOrder || (order & 1) == 0))
+        return fail(c, SDD_EINVAL, "the smoothing order must be 0 or odd in 1..%d", kCvMaxOrder);
+    if (order != c->cv_order) drop_graphs(c);
+    c->cv_order = order;
+    return SDD_OK;
+}
+
+int32_t sdd_cv_fields_order(const sdd_ctx* c) { return c ? cv_fields_order(c) : 0; }
+
+sdd_status sdd_cv_get_cells(sdd_ctx* c, float* cells)
+{
+    if (!c || !cells) return fail(c, SDD_EINVAL, "null argument");
+    if (c->cv_mode != 3) return fail(c, SDD_EINVAL, "the field-gradient control variate is not enabled");
+    {
+        const sdd_status fs = flush_pending(c);
+        if (fs != SDD_OK) return fs;
+    }
+    CU(c, launch_field_grad(c->fld[c->cur][0].p, c->fld[c->cur][1].p, c->nx, c->ny, c->cv_table64.p, c->stream));
+    CU(c, launch_cv_smooth(c->cv_table64.p, c->nx, c->ny, cv_fields_order(c), c->cv_tmp.p, c->cv_cell.p, c->stream));
+    CU(c, cudaMemcpyAsync(cells, c->cv_cell.p, 4 * sizeof(float) * (size_t)(c->nx - 1) * (c->ny - 1),
+                          cudaMemcpyDeviceToDevice, c->stream));
     return SDD_OK;
 }
 
@@ -2051,6 +2137,7 @@ sdd_status sdd_step(sdd_ctx* c, const sdd_step_params* p)
                                    (int64_t)np.size(), ppt, block, p->exit_mode, false);
         if (st != SDD_OK) return st;
         c->step_plan.zero_map = zmap;
+        c->step_plan.zero_map_auto = true;
         CU(c, cudaStreamSynchronize(c->stream));
         // pipelined steps where the solve's iterations are one launch and the
         // paths do not read the fields (the field-gradient control variate does)

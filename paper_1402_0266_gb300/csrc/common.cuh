@@ -14,7 +14,8 @@
 namespace sdd {
 
 constexpr int kMaxCvSlices = 128;  // time slices of a control-variate table
-constexpr int kCvMaxBlock = 256;   // threads per block of the path kernel with a control variate (3 blocks per SM)
+constexpr int kCvMaxBlock = 256;   // threads per block of the path kernel with a control variate
+constexpr int kCvMaxOrder = 255;   // largest order of the binomial smoothing of the field-gradient control variate
 
 // The control variate's network: 5 inputs, two tanh layers of 64, one output;
 // parameters W1 (64 x 5), b1, W2 (64 x 64, [out][in]), b2, w3, b3 in this order.
@@ -35,6 +36,7 @@ struct InstDev {
     uint32_t cell_bias;    // 0x4B000000 * nx (mod 2^32): cell index from the float bits of 2^23 + floor(g)
     int32_t cv_slices;     // slices of the control-variate table (0: none)
     const uint4* cvcoef;   // per slice and cell 2 uint4: corner values (half precision) of the xi model's gradient, then the eta model's
+    const float4* cvcell;  // per cell: (d/dx, d/dy) of the xi model, then of the eta model (one value per cell)
 };
 
 // Output arrays of one instance (device pointers; any may be null).
@@ -110,7 +112,6 @@ struct PathArgs {
     uint32_t zcell;
     InstDev one;              // single: the one instance's tables (inst[0]), read as parameters
     int32_t single;           // 1: every task is of instance 0 and `one` holds its tables
-    int32_t cv_pairs;         // control variate with sub-step pairs: the model once per pair (at its first point)
 };
 
 // The zero map's size: at most kZmapMaxWords words (16 KB of shared memory per block of the path kernel).
@@ -122,6 +123,8 @@ inline uint32_t zmap_shift(long long cells)
     return s;
 }
 inline int zmap_words(long long cells, uint32_t shift) { return (int)((((cells + (1LL << shift) - 1) >> shift) + 31) / 32); }
+// Shared memory for a map of `words` words: whole groups of 32, as the kernel's slots permute each group.
+inline size_t zmap_smem_bytes(int words) { return sizeof(uint32_t) * (size_t)((words + 31) / 32 * 32); }
 
 struct FinalArgs {
     const InstDev* inst;
@@ -151,15 +154,16 @@ enum : int {
 };
 
 // Launchers (defined in the .cu files; all asynchronous on `s`).
+// cvm: the control variate's form, 0 none, 1 cvcoef (node values, time slices), 2 cvcell (cell values)
 cudaError_t launch_paths(const PathArgs& a, int exit_mode, bool record, int grid, int block, cudaStream_t s,
-                         bool cv = false);
+                         int cvm = 0);
 // exit_mode 0 with an even number of sub-steps has its own kernel (no odd last pair)
 cudaError_t launch_finalize(const FinalArgs& a, cudaStream_t s);
 cudaError_t launch_score_surv(const ScoreArgs& a, bool cv, cudaStream_t s);
-int path_kernel_blocks_per_sm(int exit_mode, bool record, int block, bool cv = false, int zwords = 0,
+int path_kernel_blocks_per_sm(int exit_mode, bool record, int block, int cvm = 0, int zwords = 0,
                               bool single = false);
 // the largest block the path kernel of this exit mode is compiled for (single: one instance)
-int path_kernel_max_block(int exit_mode, bool cv = false, bool single = false);
+int path_kernel_max_block(int exit_mode, int cvm = 0, bool single = false);
 
 // Cell records of the drift (from w; bcoef null: skipped) and of the fields
 // (from xi, eta; fcoef null: skipped); with the drift records, if zmap is
@@ -191,6 +195,13 @@ cudaError_t launch_pchip(const KeyLine* lines, int nlines, int max_n, const int3
 cudaError_t launch_node_features(const float* w, int nx, int ny, double* w64, double* r64, double2* gw, float4* nfa,
                                  float2* nfb, cudaStream_t s);
 cudaError_t launch_field_grad(const double* xi, const double* eta, int nx, int ny, double* table, cudaStream_t s);
+// The field-gradient control variate's cell values from the node table of launch_field_grad:
+// each component smoothed by the binomial filter of odd order `order` (<= kCvMaxOrder) along x,
+// then along y, centred on the cells (cell i: node i - r + m with weight C(order, m) 2^-order,
+// m = 0..order, r = (order - 1) / 2, nodes past an edge read as the edge node). tmp: (nx - 1) ny
+// float4 of scratch; cells: (nx - 1) (ny - 1) float4.
+cudaError_t launch_cv_smooth(const double* table, int nx, int ny, int order, float4* tmp, float4* cells,
+                             cudaStream_t s);
 cudaError_t launch_cv_scatter(const double* xs, const double* ys, const double* yxi, const double* yeta,
                               const float4* nfa, int nx, int ny, int k, int K, int M, float* feats, float* targets,
                               cudaStream_t s);

@@ -113,6 +113,60 @@ __global__ void k_field_grad(const double* __restrict__ xi, const double* __rest
     }
 }
 
+// Weights C(order, m) 2^-order of the binomial filter, in single precision
+// (exact up to order 24; rounded beyond), and the order.
+struct BinomWeights {
+    float w[kCvMaxOrder + 1];
+    int order;
+};
+
+// Pass along x: tmp[j (nx - 1) + i] = sum_m w_m table[j][clamp(i - r + m)], all four components,
+// for the cells i < nx - 1 along x and the node rows j < ny.
+__global__ void k_cv_smooth_x(const double* __restrict__ table, int nx, int ny, const BinomWeights W,
+                              float4* __restrict__ tmp)
+{
+    const long long n = (long long)(nx - 1) * ny;
+    const int r = (W.order - 1) / 2;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(k % (nx - 1)), j = (int)(k / (nx - 1));
+        const double* row = table + 4LL * j * nx;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int m = 0; m <= W.order; ++m) {
+            const int q = min(max(i - r + m, 0), nx - 1);
+            const double2 u = *reinterpret_cast<const double2*>(row + 4LL * q);
+            const double2 v = *reinterpret_cast<const double2*>(row + 4LL * q + 2);
+            const float wm = W.w[m];
+            acc.x = fmaf(wm, (float)u.x, acc.x);
+            acc.y = fmaf(wm, (float)u.y, acc.y);
+            acc.z = fmaf(wm, (float)v.x, acc.z);
+            acc.w = fmaf(wm, (float)v.y, acc.w);
+        }
+        tmp[k] = acc;
+    }
+}
+
+// Pass along y: cells[j (nx - 1) + i] = sum_m w_m tmp[clamp(j - r + m)][i], j < ny - 1.
+__global__ void k_cv_smooth_y(const float4* __restrict__ tmp, int nx, int ny, const BinomWeights W,
+                              float4* __restrict__ cells)
+{
+    const long long n = (long long)(nx - 1) * (ny - 1);
+    const int r = (W.order - 1) / 2;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(k % (nx - 1)), j = (int)(k / (nx - 1));
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int m = 0; m <= W.order; ++m) {
+            const int q = min(max(j - r + m, 0), ny - 1);
+            const float4 v = tmp[(long long)q * (nx - 1) + i];
+            const float wm = W.w[m];
+            acc.x = fmaf(wm, v.x, acc.x);
+            acc.y = fmaf(wm, v.y, acc.y);
+            acc.z = fmaf(wm, v.z, acc.z);
+            acc.w = fmaf(wm, v.w, acc.w);
+        }
+        cells[k] = acc;
+    }
+}
+
 // ---------------------------------------------------------------- training rows
 
 __device__ __forceinline__ float bilin(const float4* __restrict__ nfa, int nx, int ny, double x, double y, int comp)
@@ -745,6 +799,23 @@ cudaError_t launch_field_grad(const double* xi, const double* eta, int nx, int n
 {
     const long long n = (long long)nx * ny;
     k_field_grad<<<grid_for(n, 256), 256, 0, s>>>(xi, eta, nx, ny, table);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cv_smooth(const double* table, int nx, int ny, int order, float4* tmp, float4* cells,
+                             cudaStream_t s)
+{
+    if (order < 1 || order > kCvMaxOrder || (order & 1) == 0) return cudaErrorInvalidValue;
+    BinomWeights W{};
+    W.order = order;
+    double c = 1.0;   // C(order, m)
+    for (int m = 0; m <= order; ++m) {
+        W.w[m] = (float)std::ldexp(c, -order);
+        c = c * (double)(order - m) / (double)(m + 1);
+    }
+    const long long nxr = (long long)(nx - 1) * ny, nc = (long long)(nx - 1) * (ny - 1);
+    k_cv_smooth_x<<<grid_for(nxr, 256), 256, 0, s>>>(table, nx, ny, W, tmp);
+    k_cv_smooth_y<<<grid_for(nc, 256), 256, 0, s>>>(tmp, nx, ny, W, cells);
     return cudaGetLastError();
 }
 

@@ -77,7 +77,13 @@ __device__ __forceinline__ const float4* rec2(const float4* base, uint32_t idx) 
 // a segment reads the same 32 bytes, one L1 wavefront for all of them, where
 // each lane's own cell would cost one wavefront per lane. zsm: the map in
 // shared memory, bit k of word k / 32 set when a record of cells
-// [k 2^zshift, (k + 1) 2^zshift) is nonzero.
+// [k 2^zshift, (k + 1) 2^zshift) is nonzero; word w sits at zmap_slot(w).
+// Shared-memory slot of map word w: the word's bank (its low five bits) xored
+// with the next five bits. A warp's lanes sit in nearby rows of cells, whose
+// words lie a multiple of 32 apart where rows are 32 words long or a divisor
+// of that: unswizzled they would share a bank and serialise the load.
+__device__ __forceinline__ uint32_t zmap_slot(uint32_t w) { return w ^ ((w >> 5) & 31u); }
+
 template <bool ZM>
 __device__ __forceinline__ const float4* drift_rec(const InstDev& I, const Cell& c, const uint32_t* zsm,
                                                    const PathArgs& a)
@@ -85,7 +91,7 @@ __device__ __forceinline__ const float4* drift_rec(const InstDev& I, const Cell&
     uint32_t idx = c.idx;
     if (ZM) {
         const uint32_t seg = idx >> a.zshift;
-        if (!((zsm[seg >> 5] >> (seg & 31u)) & 1u)) idx = a.zcell;
+        if (!((zsm[zmap_slot(seg >> 5)] >> (seg & 31u)) & 1u)) idx = a.zcell;
     }
     return rec2(I.bcoef, idx);
 }
@@ -247,6 +253,15 @@ __device__ __forceinline__ void cv_eval(const InstDev& I, const Cell& c, int q, 
     geta = corners2(ge, ss, oms, tt, omt);
 }
 
+// Control variate of one value per cell: (d/dx, d/dy) of xi, then of eta, on
+// the cell holding the point, in one 128-bit read-only load.
+__device__ __forceinline__ void cv_cell(const InstDev& I, const Cell& c, float2& gxi, float2& geta)
+{
+    const float4 g = __ldg(I.cvcell + c.idx);
+    gxi = f2(g.x, g.y);
+    geta = f2(g.z, g.w);
+}
+
 // The gradients times the sub-step's increment z = sqrt(2 dt) N(0,1)^2, added to
 // the running sums (acc_xi, acc_eta hold the x and y parts separately).
 __device__ __forceinline__ void cv_acc(float2 gxi, float2 geta, float2 z, float2& acc_xi, float2& acc_eta)
@@ -319,33 +334,36 @@ constexpr int WARM_MIN = 8;
 
 // MODE 0: the paper's test, sub-step pairs; MODE 1: with the bridge test;
 // MODE 2: as MODE 0 when K is even (every pair has both sub-steps).
-// CVM: 0 no control variate; 1 subtract sum_j G(s_j, X_j) . sqrt(2) dW_j from
-// both scores; 2 (sub-step pairs) the same with G evaluated once per pair, at
-// X_{2m} in the slice of sub-step 2m, for both of the pair's increments.
+// CVM: 0 no control variate; otherwise subtract sum_j G(s_j, X_j) . sqrt(2) dW_j
+// from both scores, G from node values interpolated bilinearly in time slices
+// (1, cv_eval) or one value per cell (2, cv_cell).
 // Kernel variants by where the tables come from: VAR_MULTI, each task's
 // instance from the instance table (batches); VAR_ONE, a single instance whose
 // tables are kernel parameters (no registers held for them); VAR_ZM, VAR_ONE
 // with the zero map of the drift records. Launch shapes: a single instance's
-// kernel fits 40 registers (48 warps per SM; 64 with the control variate),
-// the batch kernel 64 (32 warps; 80 with the control variate).
+// kernel fits 40 registers (48 warps per SM; 64 with the control variate of
+// node values, 48 with that of cell values), the batch kernel 64 (32 warps;
+// 80 with a control variate).
 constexpr int VAR_MULTI = 0, VAR_ONE = 1, VAR_ZM = 2;
+constexpr int kCvCellBlocks = 5;   // cell-valued control variate, single instance: 48 registers, 40 warps per SM
 constexpr int kOneMaxBlock = 256;
-constexpr int paths_max_block(bool cv, int var) { return cv ? kCvMaxBlock : var != VAR_MULTI ? kOneMaxBlock : 512; }
-constexpr int paths_min_blocks(bool cv, int var)
+constexpr int paths_max_block(int cvm, int var) { return cvm ? kCvMaxBlock : var != VAR_MULTI ? kOneMaxBlock : 512; }
+constexpr int paths_min_blocks(int cvm, int var)
 {
-    return cv ? (var != VAR_MULTI ? 4 : 3) : (var != VAR_MULTI ? 6 : 2);
+    return cvm == 2 ? (var != VAR_MULTI ? kCvCellBlocks : 3) : cvm ? (var != VAR_MULTI ? 4 : 3)
+                                                                    : (var != VAR_MULTI ? 6 : 2);
 }
 
 template <int MODE, bool RECORD, int CVM, int VAR>
-__global__ void __launch_bounds__(paths_max_block(CVM != 0, VAR), paths_min_blocks(CVM != 0, VAR))
+__global__ void __launch_bounds__(paths_max_block(CVM, VAR), paths_min_blocks(CVM, VAR))
     k_paths(const PathArgs a)
 {
     constexpr bool ZM = VAR == VAR_ZM;
     constexpr bool CV = CVM != 0;
-    constexpr bool CVP = CVM == 2 && MODE != 1;   // one model evaluation per sub-step pair
+    constexpr bool CVT = CVM == 1;   // node values in time slices
     extern __shared__ uint32_t zsm[];   // the zero map of the drift records (ZM)
     if (ZM) {
-        for (int k = threadIdx.x; k < a.zwords; k += blockDim.x) zsm[k] = a.zmap[k];
+        for (int k = threadIdx.x; k < a.zwords; k += blockDim.x) zsm[zmap_slot((uint32_t)k)] = a.zmap[k];
         __syncthreads();
     }
     const int lane = threadIdx.x & 31;
@@ -384,7 +402,7 @@ __global__ void __launch_bounds__(paths_max_block(CVM != 0, VAR), paths_min_bloc
         float2 zA = f2(0.f, 0.f), zB = f2(0.f, 0.f);
         float ub = 1.f;
         float2 cvx = f2(0.f, 0.f), cve = f2(0.f, 0.f);  // control-variate sums of the path
-        int cvq = 0, cvn = CV ? a.cv_bound[1] : 0;       // slice of the current sub-step, start of the next
+        int cvq = 0, cvn = CVT ? a.cv_bound[1] : 0;      // slice of the current sub-step, start of the next
         const float2 dt2 = f2(dt, dt);
         auto first_draw = [&]() {
             uint4 r = make_uint4((uint32_t)path, nctr, 0u, step);
@@ -411,15 +429,15 @@ __global__ void __launch_bounds__(paths_max_block(CVM != 0, VAR), paths_min_bloc
                 const Cell cA = locate(I, pos);
                 float4 gA0, gA1;
                 load_cell(drift_rec<ZM>(I, cA, zsm, a), gA0, gA1);
-                float2 gxA, geA;   // the model at X_j (CVP: also for the pair's second sub-step)
                 if (CV) {
-                    const int j = PAIRS ? 2 * m : m;
-                    if (CVP) {
-                        while (j >= cvn) cvn = a.cv_bound[++cvq + 1];
-                    } else if (j >= cvn) {
-                        cvn = a.cv_bound[++cvq + 1];
+                    float2 gxA, geA;   // the model at X_j
+                    if (CVT) {
+                        const int j = PAIRS ? 2 * m : m;
+                        if (j >= cvn) cvn = a.cv_bound[++cvq + 1];
+                        cv_eval(I, cA, cvq, gxA, geA);
+                    } else {
+                        cv_cell(I, cA, gxA, geA);
                     }
-                    cv_eval(I, cA, cvq, gxA, geA);
                     cv_acc(gxA, geA, zA, cvx, cve);
                 }
                 uint4 r = make_uint4((uint32_t)path, nctr, (uint32_t)(m + 1), step);
@@ -441,14 +459,14 @@ __global__ void __launch_bounds__(paths_max_block(CVM != 0, VAR), paths_min_bloc
                     if (CV) {
                         // the second sub-step counts only when the path takes it
                         const float2 zt = (haveB && !outA) ? zB : f2(0.f, 0.f);
-                        if (CVP) {
-                            cv_acc(gxA, geA, zt, cvx, cve);
-                        } else {
+                        float2 gxB, geB;
+                        if (CVT) {
                             if (haveB && 2 * m + 1 >= cvn) cvn = a.cv_bound[++cvq + 1];
-                            float2 gxB, geB;
                             cv_eval(I, cB, cvq, gxB, geB);
-                            cv_acc(gxB, geB, zt, cvx, cve);
+                        } else {
+                            cv_cell(I, cB, gxB, geB);
                         }
+                        cv_acc(gxB, geB, zt, cvx, cve);
                     }
                     if (warm) {
                         // a path taken up mid-task: this pass only drew its first normals
@@ -555,8 +573,8 @@ __global__ void __launch_bounds__(paths_max_block(CVM != 0, VAR), paths_min_bloc
                     alive = true;
                     pos = f2(x0, y0);
                     m = 0;
-                    if (CV) {
-                        cvx = cve = f2(0.f, 0.f);
+                    if (CV) cvx = cve = f2(0.f, 0.f);
+                    if (CVT) {
                         cvq = 0;
                         cvn = a.cv_bound[1];
                     }
@@ -996,8 +1014,7 @@ const void* pick_cv(int mode, bool record)
     if (mode == 3) return record ? (const void*)k_paths_exp<true> : (const void*)k_paths_exp<false>;
     if (mode == 0) return record ? kernel_ptr<0, true, CVM, VAR>() : kernel_ptr<0, false, CVM, VAR>();
     if (mode == 2) return record ? kernel_ptr<2, true, CVM, VAR>() : kernel_ptr<2, false, CVM, VAR>();
-    // the bridge test draws per sub-step: no pairs
-    return record ? kernel_ptr<1, true, CVM == 2 ? 1 : CVM, VAR>() : kernel_ptr<1, false, CVM == 2 ? 1 : CVM, VAR>();
+    return record ? kernel_ptr<1, true, CVM, VAR>() : kernel_ptr<1, false, CVM, VAR>();
 }
 
 template <int VAR>
@@ -1007,7 +1024,7 @@ const void* pick_var(int mode, bool record, int cvm)
     return cvm ? pick_cv<1, VAR>(mode, record) : pick_cv<0, VAR>(mode, record);
 }
 
-// cvm: 0 no control variate, 1 per sub-step, 2 per sub-step pair
+// cvm: 0 no control variate, 1 node values in time slices, 2 one value per cell
 const void* pick(int mode, bool record, int cvm, int var)
 {
     if (var == VAR_ZM) return pick_var<VAR_ZM>(mode, record, cvm);
@@ -1027,20 +1044,20 @@ int path_var(const PathArgs& a)
 
 static void prefer_l1();
 
-int path_kernel_max_block(int exit_mode, bool cv, bool single)
+int path_kernel_max_block(int exit_mode, int cvm, bool single)
 {
-    return exit_mode == 2 ? 512 : paths_max_block(cv, single ? VAR_ONE : VAR_MULTI);
+    return exit_mode == 2 ? 512 : paths_max_block(cvm, single ? VAR_ONE : VAR_MULTI);
 }
 
-int path_kernel_blocks_per_sm(int exit_mode, bool record, int block, bool cv, int zwords, bool single)
+int path_kernel_blocks_per_sm(int exit_mode, bool record, int block, int cvm, int zwords, bool single)
 {
     prefer_l1();
     int n = 0;
     // the even-K kernel has the same footprint class; size the grid for the larger of the two
     const int mode = exit_mode == 2 ? 3 : exit_mode == 1 ? 1 : 0;
     const int var = zwords > 0 ? VAR_ZM : single ? VAR_ONE : VAR_MULTI;
-    const size_t smem = var == VAR_ZM && mode != 3 ? sizeof(uint32_t) * (size_t)zwords : 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(mode, record, cv ? 1 : 0, var), block, smem) !=
+    const size_t smem = var == VAR_ZM && mode != 3 ? zmap_smem_bytes(zwords) : 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(mode, record, cvm, var), block, smem) !=
         cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
@@ -1133,19 +1150,18 @@ static void launch_mode(const PathArgs& a, int mode, bool record, int grid, int 
         else k_paths<2, false, CVM, VAR><<<grid, block, smem, s>>>(a);
         break;
     default:
-        if (record) k_paths<1, true, CVM == 2 ? 1 : CVM, VAR><<<grid, block, smem, s>>>(a);
-        else k_paths<1, false, CVM == 2 ? 1 : CVM, VAR><<<grid, block, smem, s>>>(a);
+        if (record) k_paths<1, true, CVM, VAR><<<grid, block, smem, s>>>(a);
+        else k_paths<1, false, CVM, VAR><<<grid, block, smem, s>>>(a);
     }
 }
 
 
-cudaError_t launch_paths(const PathArgs& a, int exit_mode, bool record, int grid, int block, cudaStream_t s, bool cv)
+cudaError_t launch_paths(const PathArgs& a, int exit_mode, bool record, int grid, int block, cudaStream_t s, int cvm)
 {
     prefer_l1();
     const int mode = kernel_mode(exit_mode, a.K);
     const int var = path_var(a);
-    const int cvm = !cv ? 0 : (a.cv_pairs && (mode == 0 || mode == 2)) ? 2 : 1;
-    const size_t smem = var == VAR_ZM && mode != 3 ? sizeof(uint32_t) * (size_t)a.zwords : 0;
+    const size_t smem = var == VAR_ZM && mode != 3 ? zmap_smem_bytes(a.zwords) : 0;
     switch (var * 3 + cvm) {
     case VAR_ZM * 3 + 0: launch_mode<0, VAR_ZM>(a, mode, record, grid, block, smem, s); break;
     case VAR_ZM * 3 + 1: launch_mode<1, VAR_ZM>(a, mode, record, grid, block, smem, s); break;

@@ -46,6 +46,11 @@ def _h(T):
     return np.asarray(T, dtype=np.float16).astype(np.float64)
 
 
+def _f(T):
+    """Cell values as the GPU keeps them: single precision."""
+    return np.asarray(T, dtype=np.float32).astype(np.float64)
+
+
 def _set_table(sdd, ctx, T):
     import torch
     sdd.sdd_cv_set_table(ctx, torch.from_numpy(np.ascontiguousarray(T, np.float64)).cuda())
@@ -218,19 +223,32 @@ def test_field_gradient_mode_matches_oracle(sdd, oracle_mod):
     eta0 = Y.copy()
     ctx = _ctx(sdd, w, xi0, eta0)
     sdd.sdd_cv_enable(ctx, sdd.SDD_CV_FIELDS)
+    assert sdd.sdd_cv_fields_order(ctx) == 1          # a 65-node grid: no smoothing by default
     xs, ys = W.interface_node_coords(n, n, 2, 2)
     pick = np.arange(0, xs.size, 5)
     xs, ys = xs[pick], ys[pick]
     npaths = np.full(xs.size, 600)
-    kw = dict(dt=1e-4, Dt=1e-2, seed=6, exit_mode=0)
-    g = _np(sdd.sdd_interface_mc_record(ctx, xs, ys, npaths, **kw))
     T = mlp.field_gradient_table(xi0, eta0)
-    np.testing.assert_allclose(sdd.sdd_cv_get_table(ctx, 1).cpu().numpy(), T, rtol=1e-12, atol=1e-9)
-    # the paper's test draws sub-step pairs: the field gradient is evaluated once per pair
-    o = oracle_mod.interface_mc(oracle_mod.Problem(w, xi0, eta0), xs, ys, npaths, record=True, cv_table=_h(T),
-                                cv_pairs=True, **kw)
-    same, rep = PT.assert_records(g, o)
-    PT.assert_nodes(g, o, npaths, same, np.concatenate([[0], np.cumsum(npaths)]))
+    for order, mode in ((0, 0), (9, 0), (9, 1)):
+        sdd.sdd_cv_set_fields_order(ctx, order)
+        o_ = sdd.sdd_cv_fields_order(ctx)
+        assert o_ == (order or 1)
+        kw = dict(dt=1e-4, Dt=1e-2, seed=6, exit_mode=mode)
+        g = _np(sdd.sdd_interface_mc_record(ctx, xs, ys, npaths, **kw))
+        np.testing.assert_allclose(sdd.sdd_cv_get_table(ctx, 1).cpu().numpy(), T, rtol=1e-12, atol=1e-9)
+        C = mlp.field_cell_gradient_table(xi0, eta0, o_)
+        np.testing.assert_allclose(sdd.sdd_cv_get_cells(ctx).cpu().numpy(), C[0], rtol=0, atol=2e-6)
+        # the model at every sub-step: the value of the cell the path is in
+        o = oracle_mod.interface_mc(oracle_mod.Problem(w, xi0, eta0), xs, ys, npaths, record=True, cv_table=_f(C),
+                                    **kw)
+        same, rep = PT.assert_records(g, o)
+        PT.assert_nodes(g, o, npaths, same, np.concatenate([[0], np.cumsum(npaths)]))
+        if (order, mode) == (0, 0):
+            g_cells = g
+    for bad in (2, -1, 257):
+        with pytest.raises(sdd.SddError):
+            sdd.sdd_cv_set_fields_order(ctx, bad)
+    kw = dict(dt=1e-4, Dt=1e-2, seed=6, exit_mode=0)
     # and a table set by hand is evaluated at every sub-step
     _set_table(sdd, ctx, T)
     sdd.sdd_cv_enable(ctx, sdd.SDD_CV_TABLE)
@@ -238,7 +256,7 @@ def test_field_gradient_mode_matches_oracle(sdd, oracle_mod):
     o1 = oracle_mod.interface_mc(oracle_mod.Problem(w, xi0, eta0), xs, ys, npaths, record=True, cv_table=_h(T), **kw)
     same1, _ = PT.assert_records(g1, o1)
     PT.assert_nodes(g1, o1, npaths, same1, np.concatenate([[0], np.cumsum(npaths)]))
-    assert not np.array_equal(g1["score_xi"], g["score_xi"])
+    assert not np.array_equal(g1["score_xi"], g_cells["score_xi"])
 
 
 def test_model_mode_tabulates_before_every_estimate(sdd, oracle_mod):
@@ -285,11 +303,11 @@ def test_mesh_steps_with_control_variate_match_oracle(sdd, oracle_mod, mode):
         sdd.sdd_sync(ctx)
         g = _np(sdd.sdd_last_interface_stats(ctx))
         if mode == "model":
-            T = sdd.sdd_cv_get_table(ctx, 4).cpu().numpy()
+            T = _h(sdd.sdd_cv_get_table(ctx, 4).cpu().numpy())
         else:
-            T = mlp.field_gradient_table(*state)
+            T = _f(mlp.field_cell_gradient_table(*state, sdd.sdd_cv_fields_order(ctx)))
         new, o = oracle_mod.dd_step(w, state[0], state[1], sub_x=sub, sub_y=sub, dt=dt, Dt=Dt, n_paths=paths, seed=9,
-                                    step_index=step, nodes_ij=(ii, jj), cv_table=_h(T), cv_pairs=mode == "fields")
+                                    step_index=step, nodes_ij=(ii, jj), cv_table=T)
         for f in ("xi", "eta"):
             d = np.abs(g["mean_" + f] - o["mean_" + f])
             assert np.all(d <= 3 * o["se_" + f] + 1e-4), (step, f, d.max())

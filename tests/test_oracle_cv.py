@@ -113,36 +113,103 @@ def test_field_gradient_model(oracle_mod):
         assert np.all(np.abs(a["mean_" + f] - b["mean_" + f]) < 4 * np.hypot(a["se_" + f], b["se_" + f]))
 
 
-def test_pair_evaluated_model_is_unbiased_and_matches_per_step_for_a_static_field(oracle_mod):
-    # the model evaluated once per sub-step pair (at X_{2m}, for both increments) is known before
-    # both increments, so the estimate stays unbiased; for a model that varies only in space on
-    # scales far above a sub-step's spread (the previous fields' gradient) it removes as much
-    # variance as the per-sub-step evaluation
+def test_cell_table_is_the_exact_gradient_of_quadratic_fields():
+    # the nodes' differences (central, and second-order one-sided on the edges) are exact on
+    # quadratics and the symmetric binomial weights reproduce a linear gradient at the cell
+    # centre: every cell whose window stays inside the grid holds the exact gradient at its
+    # centre (order 1 has no window past an edge: every cell), and an affine field's constant
+    # gradient comes out at every cell for any order
     from oracle import mlp
-    n = 65
-    X, Y = W.grid(n)
-    xi0 = X + 0.02 * np.sin(np.pi * X) * np.sin(np.pi * Y)
-    eta0 = Y + 0.01 * np.sin(2 * np.pi * X) * np.sin(np.pi * Y)
-    T = mlp.field_gradient_table(xi0, eta0)
-    P = oracle_mod.Problem(W.w_front(n, 0.1), xi0, eta0)
-    xs, ys = W.interface_node_coords(n, n, 2, 2)
-    pick = np.arange(0, xs.size, 6)
-    kw = dict(dt=1e-4, Dt=1e-2, seed=5, record=True)
-    N = 3000
-    a = oracle_mod.interface_mc(P, xs[pick], ys[pick], N, **kw)
-    b = oracle_mod.interface_mc(P, xs[pick], ys[pick], N, cv_table=T, **kw)
-    c = oracle_mod.interface_mc(P, xs[pick], ys[pick], N, cv_table=T, cv_pairs=True, **kw)
-    np.testing.assert_array_equal(a["code"], c["code"])
-    assert not np.array_equal(b["score_xi"], c["score_xi"])          # the pair evaluation is really used
+    nx, ny = 41, 29
+    X, Y = W.grid(nx, ny)
+    XC, YC = np.meshgrid((np.arange(nx - 1) + 0.5) / (nx - 1), (np.arange(ny - 1) + 0.5) / (ny - 1))
+    c = np.random.default_rng(3).normal(size=(2, 6))
+
+    def quad(k, x, y):
+        return c[k, 0] * x ** 2 + c[k, 1] * x * y + c[k, 2] * y ** 2 + c[k, 3] * x + c[k, 4] * y + c[k, 5]
+
+    want = np.stack([2 * c[0, 0] * XC + c[0, 1] * YC + c[0, 3], c[0, 1] * XC + 2 * c[0, 2] * YC + c[0, 4],
+                     2 * c[1, 0] * XC + c[1, 1] * YC + c[1, 3], c[1, 1] * XC + 2 * c[1, 2] * YC + c[1, 4]], -1)
+    for order in (1, 5, 9):
+        T = mlp.field_cell_gradient_table(quad(0, X, Y), quad(1, X, Y), order)
+        assert T.shape == (1, ny - 1, nx - 1, 4)
+        r = (order - 1) // 2
+        inner = (slice(r, ny - 1 - r), slice(r, nx - 1 - r))
+        np.testing.assert_allclose(T[0][inner], want[inner], rtol=0, atol=1e-11)
+        if order > 1:
+            assert np.abs(T[0] - want).max() > 1e-3           # the edge windows read the edge nodes
+    T1 = mlp.field_cell_gradient_table(quad(0, X, Y), quad(1, X, Y), 1)
+    np.testing.assert_allclose(T1[0], want, rtol=0, atol=1e-11)
+    for order in (1, 9, 33):
+        T = mlp.field_cell_gradient_table(0.3 * X - 1.7 * Y + 0.2, 2.5 * X + 0.4 * Y, order)
+        np.testing.assert_allclose(T[0], np.broadcast_to([0.3, -1.7, 2.5, 0.4], T[0].shape), rtol=0, atol=1e-11)
+    for order in (0, 2, -1):
+        with pytest.raises(ValueError):
+            mlp.field_cell_gradient_table(X, Y, order)
+
+
+def test_cell_model_keeps_the_mean_and_reads_the_cell_of_the_point(oracle_mod):
+    # heat problem on 65 x 49 nodes: one value per cell, the exact gradient half-way through the
+    # mesh step at the cell's centre
+    nx, ny = 65, 49
+    X, Y = W.grid(nx, ny)
+    xi0, eta0 = np.sin(np.pi * X) * np.sin(np.pi * Y), np.sin(np.pi * X) * np.sin(2 * np.pi * Y)
+    P = oracle_mod.Problem(W.w_const(nx, ny), xi0, eta0, np.zeros(oracle_mod.faces_len(nx, ny)))
+    dt, Dt = 5e-4, 0.05
+    XC, YC = np.meshgrid((np.arange(nx - 1) + 0.5) / (nx - 1), (np.arange(ny - 1) + 0.5) / (ny - 1))
+    ex, ee = math.exp(-math.pi ** 2 * Dt), math.exp(-2.5 * math.pi ** 2 * Dt)
+    T = np.zeros((1, ny - 1, nx - 1, 4))
+    T[0, ..., 0] = ex * math.pi * np.cos(np.pi * XC) * np.sin(np.pi * YC)
+    T[0, ..., 1] = ex * math.pi * np.sin(np.pi * XC) * np.cos(np.pi * YC)
+    T[0, ..., 2] = ee * math.pi * np.cos(np.pi * XC) * np.sin(2 * np.pi * YC)
+    T[0, ..., 3] = ee * 2 * math.pi * np.sin(np.pi * XC) * np.cos(2 * np.pi * YC)
+    xs, ys = np.array([0.5, 0.3, 0.7]), np.array([0.375, 0.5, 0.6])
+    kw = dict(dt=dt, Dt=Dt, seed=0, record=True)
+    N = 4000
+    a = oracle_mod.interface_mc(P, xs, ys, N, **kw)
+    b = oracle_mod.interface_mc(P, xs, ys, N, cv_table=T, **kw)
+    np.testing.assert_array_equal(a["code"], b["code"])
+    assert np.all(b["se_xi"] < a["se_xi"] / 3), (a["se_xi"], b["se_xi"])
+    assert np.all(b["se_eta"] < a["se_eta"] / 1.5), (a["se_eta"], b["se_eta"])
     for f in ("xi", "eta"):
-        rb = np.median((a["se_" + f] / b["se_" + f]) ** 2)
-        rc = np.median((a["se_" + f] / c["se_" + f]) ** 2)
-        assert rc > 0.9 * rb, (f, rb, rc)
-        D = (c["score_" + f] - a["score_" + f]).reshape(pick.size, N)
-        z = D.mean(axis=1) / (D.std(axis=1, ddof=1) / math.sqrt(N) + 1e-300)
+        D = (b["score_" + f] - a["score_" + f]).reshape(3, N)
+        z = D.mean(axis=1) / (D.std(axis=1, ddof=1) / math.sqrt(N))
+        assert np.all(np.abs(z) < 4.0), z
+    # the rows mirrored (the wrong cell for a point off the middle row): d/dy of the xi model
+    # changes sign and the estimate gets worse than without a model
+    m = oracle_mod.interface_mc(P, xs, ys, N, cv_table=np.ascontiguousarray(T[:, ::-1]), **kw)
+    assert np.all(m["se_xi"] > a["se_xi"]), (a["se_xi"], m["se_xi"])
+    # a constant per cell is the constant per node (up to the interpolation's rounding)
+    v = np.array([0.7, -0.2, 0.4, 1.1])
+    c1 = oracle_mod.interface_mc(P, xs, ys, 500, cv_table=np.broadcast_to(v, (1, ny - 1, nx - 1, 4)), **kw)
+    c2 = oracle_mod.interface_mc(P, xs, ys, 500, cv_table=np.broadcast_to(v, (1, ny, nx, 4)), **kw)
+    for k in ("steps", "code"):
+        np.testing.assert_array_equal(c1[k], c2[k])
+    for k in ("score_xi", "score_eta"):
+        np.testing.assert_allclose(c1[k], c2[k], rtol=0, atol=1e-13)
+
+
+def test_smoothed_cell_table_beats_the_node_table_on_noisy_fields(oracle_mod):
+    # after mesh steps whose interface values carry Monte Carlo error, the fields' differences
+    # are noisy on the grid's scale near the interfaces, where the paths start: the smoothed
+    # cell values remove more variance than the node differences themselves
+    from oracle import mlp
+    n, dt, Dt = 257, 1e-5, 1e-3
+    xi, eta = W.identity_fields(n)
+    ii, jj = W.interface_nodes(n, n, 8, 8)
+    for s in range(3):
+        (xi, eta), _ = oracle_mod.dd_step(W.w_ring(n, s * Dt), xi, eta, sub_x=8, sub_y=8, dt=dt, Dt=Dt, n_paths=500,
+                                          seed=11, step_index=s, nodes_ij=(ii, jj))
+    P = oracle_mod.Problem(W.w_ring(n, 3 * Dt), xi, eta)
+    pick = np.random.default_rng(1).choice(ii.size, 48, replace=False)
+    xs, ys = ii[pick] / (n - 1), jj[pick] / (n - 1)
+    kw = dict(dt=dt, Dt=Dt, seed=5, step_index=3)
+    plain = oracle_mod.interface_mc(P, xs, ys, 4000, **kw)
+    node = oracle_mod.interface_mc(P, xs, ys, 4000, cv_table=mlp.field_gradient_table(xi, eta), **kw)
+    cell = oracle_mod.interface_mc(P, xs, ys, 4000, cv_table=mlp.field_cell_gradient_table(xi, eta, 7), **kw)
+    for f in ("xi", "eta"):
+        v0, vn, vc = (np.sum(r["se_" + f] ** 2) for r in (plain, node, cell))
+        assert v0 / vn > 20, (f, v0 / vn)
+        assert vn / vc > 1.5, (f, v0 / vn, v0 / vc)
+        z = (cell["mean_" + f] - plain["mean_" + f]) / np.hypot(cell["se_" + f], plain["se_" + f])
         assert np.all(np.abs(z) < 4.5), z
-    # the bridge test draws per sub-step: no pairs, the flag changes nothing
-    d = oracle_mod.interface_mc(P, xs[pick][:3], ys[pick][:3], 500, cv_table=T, cv_pairs=True, exit_mode=1,
-                                **{k: v for k, v in kw.items()})
-    e = oracle_mod.interface_mc(P, xs[pick][:3], ys[pick][:3], 500, cv_table=T, exit_mode=1, **kw)
-    np.testing.assert_array_equal(d["score_xi"], e["score_xi"])
