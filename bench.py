@@ -273,16 +273,19 @@ def run_reference(args, world, rank):
 
 # ------------------------------------------------------------------ GPU leg
 
-def profiled_traffic(path):
-    """DRAM bytes per launch from a committed ncu summary, or None when the
-    kernel's sources changed since the counters were taken."""
+def profiled_counters(path):
+    """From a committed ncu summary: DRAM bytes per launch, the path-steps of
+    that launch and the issue-slot utilisation (smsp__issue_active, a
+    fraction), or None when the kernel's sources changed since the counters
+    were taken."""
     import hashlib
+    import re
     try:
         lines = open(path).read().splitlines()
     except OSError:
         return None
     fields = dict(l.split(": ", 1) for l in lines if ": " in l and l.split(": ", 1)[0] in
-                  ("dram_bytes_per_launch", "source_sha256", "sources"))
+                  ("dram_bytes_per_launch", "path_steps_per_launch", "source_sha256", "sources"))
     if not {"dram_bytes_per_launch", "source_sha256", "sources"} <= fields.keys():
         return None
     h = hashlib.sha256()
@@ -293,7 +296,14 @@ def profiled_traffic(path):
             return None
     if h.hexdigest() != fields["source_sha256"]:
         return None
-    return float(fields["dram_bytes_per_launch"])
+    issue = None
+    for l in lines:
+        m = re.search(r"`smsp__issue_active\.avg\.pct_of_peak_sustained_active`\) \| ([0-9.]+) %", l)
+        if m:
+            issue = float(m.group(1)) / 100.0
+    return {"dram_bytes_per_launch": float(fields["dram_bytes_per_launch"]),
+            "path_steps_per_launch": float(fields["path_steps_per_launch"]) if "path_steps_per_launch" in fields else None,
+            "issue_slots": issue}
 
 
 def run_ours(args, world, rank, local):
@@ -393,15 +403,15 @@ def run_ours(args, world, rank, local):
     peak = props.multi_processor_count * SM_LANES_PER_CLK * sm_max * 1e6 / 1e12
     # DRAM bytes of one launch, from the committed profile of this workload's path kernel when its sources
     # are unchanged (a capture of a node sample, scaled to the launch by path-steps)
-    traffic = None
-    tp = profiled_traffic(os.path.join(ROOT, "profiles", f"k_paths_{name}.md"))
-    if tp is not None:
-        try:
-            lines = open(os.path.join(ROOT, "profiles", f"k_paths_{name}.md")).read().splitlines()
-            per = dict(l.split(": ", 1) for l in lines if l.startswith("path_steps_per_launch: "))
-            traffic = tp * steps_per_launch / float(per["path_steps_per_launch"]) if per else tp
-        except Exception:
-            traffic = tp
+    # and the schedulers' issue-slot utilisation in that capture (how busy the kernel keeps them: a
+    # path-step issues more instructions than its algorithmic operations)
+    traffic, issue_slots = None, None
+    prof = profiled_counters(os.path.join(ROOT, "profiles", f"k_paths_{name}.md"))
+    if prof is not None:
+        per = prof["path_steps_per_launch"]
+        traffic = prof["dram_bytes_per_launch"] * (steps_per_launch / per if per else 1.0)
+        if prof["issue_slots"] is not None:
+            issue_slots = {"value": prof["issue_slots"], "source": f"profiles/k_paths_{name}.md (ncu smsp__issue_active)"}
 
     # end to end through the C ABI with host buffers: w in from pinned host memory,
     # the interface statistics back to pinned host memory, every step
@@ -543,7 +553,7 @@ def run_ours(args, world, rank, local):
             "solve_ms": statistics.mean(solve_ms),
             "pipelined": pipelined,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                         "frac": achieved / peak, "traffic": traffic,
+                         "frac": achieved / peak, "traffic": traffic, "issue_slots": issue_slots,
                          "kernel": "k_paths", "ops_per_path_step": ALG_OPS_PER_PATH_STEP,
                          "peak_basis": f"{props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz (of measured "
                                        f"maximum SM clock)",
