@@ -1101,7 +1101,7 @@ static void prefer_l1()
 }
 
 // A launch of a kernel with the zero map: dynamic shared memory for the map, and the carveout that the
-// blocks the registers allow need (with less, the driver may fit fewer blocks; with more, L1 shrinks).
+// blocks the registers allow need (with less, the CUDA runtime may fit fewer blocks; with more, L1 shrinks).
 // The preference is the function's, set before each launch (launches of one function inside a step
 // graph share one shape, so they need the same value).
 static void launch_zm(const void* fn, const PathArgs& a, int grid, int block, size_t smem, cudaStream_t s)
