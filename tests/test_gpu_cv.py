@@ -339,3 +339,30 @@ def test_zero_map_with_control_variate_changes_no_result(sdd, mode):
     off = _np(sdd.sdd_interface_mc_record(ctx, xs, ys, 600, zero_map=2, **kw))
     for k in on:
         np.testing.assert_array_equal(on[k], off[k], err_msg=k)
+
+
+def test_field_cells_on_a_rectangular_grid_match_oracle(sdd, oracle_mod):
+    # 65 x 41 nodes, fields with structure along both axes: the cell values of every order the
+    # header admits at this size against the oracle's, and the paths' records with them
+    from oracle import mlp
+    nx, ny = 65, 41
+    X, Y = W.grid(nx, ny)
+    xi0 = X + 0.03 * np.sin(2 * np.pi * X) * np.sin(np.pi * Y) ** 2
+    eta0 = Y + 0.02 * np.sin(np.pi * X) * np.sin(3 * np.pi * Y)
+    w = (1.0 + 4.0 * np.exp(-((X - 0.6) ** 2 + (Y - 0.4) ** 2) / 0.02)).astype(np.float32)
+    ctx = _ctx(sdd, w, xi0, eta0)
+    sdd.sdd_cv_enable(ctx, sdd.SDD_CV_FIELDS)
+    for order in (1, 3, 17, 255):
+        sdd.sdd_cv_set_fields_order(ctx, order)
+        C = mlp.field_cell_gradient_table(xi0, eta0, order)
+        np.testing.assert_allclose(sdd.sdd_cv_get_cells(ctx).cpu().numpy(), C[0], rtol=0, atol=2e-6,
+                                   err_msg=str(order))
+    sdd.sdd_cv_set_fields_order(ctx, 17)
+    xs, ys = W.interface_node_coords(nx, ny, 2, 2)
+    npaths = np.full(xs.size, 400)
+    kw = dict(dt=2e-4, Dt=1e-2, seed=3, exit_mode=0)
+    g = _np(sdd.sdd_interface_mc_record(ctx, xs, ys, npaths, **kw))
+    o = oracle_mod.interface_mc(oracle_mod.Problem(w, xi0, eta0), xs, ys, npaths, record=True,
+                                cv_table=_f(mlp.field_cell_gradient_table(xi0, eta0, 17)), **kw)
+    same, _ = PT.assert_records(g, o)
+    PT.assert_nodes(g, o, npaths, same, np.concatenate([[0], np.cumsum(npaths)]))
