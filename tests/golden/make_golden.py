@@ -39,12 +39,28 @@ def front_case():
     return {k: np.asarray(v).tolist() for k, v in r.items()}
 
 
+def front_cell_cv_case():
+    # the field-gradient control variate as cell values (order 5) on fields with structure
+    from oracle import mlp
+    n = 65
+    X, Y = W.grid(n)
+    xi0 = X + 0.02 * np.sin(np.pi * X) * np.sin(2 * np.pi * Y)
+    eta0 = Y + 0.01 * np.sin(3 * np.pi * X) * np.sin(np.pi * Y)
+    P = oracle.Problem(W.w_front(n, 0.1), xi0, eta0)
+    xs, ys = W.interface_node_coords(n, n, 2, 2)
+    sel = np.arange(0, xs.size, 11)
+    r = oracle.interface_mc(P, xs[sel], ys[sel], 500, dt=1e-4, Dt=1e-2, seed=9, exit_mode=0, step_index=2,
+                            cv_table=mlp.field_cell_gradient_table(xi0, eta0, 5))
+    return {k: np.asarray(v).tolist() for k, v in r.items()}
+
+
 def main():
     out = {
         "about": "oracle outputs on small seeded cases; written by tests/golden/make_golden.py",
         "heat65_plain": heat65_case(0),
         "heat65_bridge": heat65_case(1),
         "front65_plain": front_case(),
+        "front65_cell_cv": front_cell_cv_case(),
     }
     with open(os.path.join(HERE, "oracle_regression.json"), "w") as f:
         json.dump(out, f)

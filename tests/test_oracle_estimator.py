@@ -193,7 +193,7 @@ def test_oracle_regression_fixture(oracle_mod):
     with open(os.path.join(os.path.dirname(__file__), "golden", "oracle_regression.json")) as f:
         stored = json.load(f)
     fresh = {"heat65_plain": make_golden.heat65_case(0), "heat65_bridge": make_golden.heat65_case(1),
-             "front65_plain": make_golden.front_case()}
+             "front65_plain": make_golden.front_case(), "front65_cell_cv": make_golden.front_cell_cv_case()}
     for case, got in fresh.items():
         for key, val in got.items():
             np.testing.assert_allclose(np.asarray(val, float), np.asarray(stored[case][key], float),
