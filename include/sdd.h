@@ -454,6 +454,16 @@ sdd_status sdd_subdomain_solve(sdd_ctx* ctx, double Dt, const double* iface_xi, 
 sdd_status sdd_set_keypoints(sdd_ctx* ctx, int32_t on, int32_t spacing);
 sdd_status sdd_keypoint_mask(sdd_ctx* ctx, uint8_t* mask);
 
+/* The interface fill of a mesh step with key points, on given values:
+ * values_xi, values_eta (DEVICE, one double per interface node in the order of
+ * sdd_interface_nodes) keep their entries where `mask` (DEVICE, one byte per
+ * interface node) is nonzero, and every other entry is overwritten, line by
+ * line, by the PCHIP interpolant (as above) through the line's two face values
+ * of the context's current w and its masked entries. A crossing of a vertical
+ * and a horizontal line that the mask leaves out is filled along its vertical
+ * line. Enqueued on the context's stream; SDD_EINVAL for null arguments. */
+sdd_status sdd_keypoint_fill(sdd_ctx* ctx, const uint8_t* mask, double* values_xi, double* values_eta);
+
 /* The solver of the subdomain systems (sdd_subdomain_solve and sdd_step).
  * The paper uses LU (Sec. 4); the GPU solves the same symmetric system either
  * directly or by conjugate gradients refined in double precision to rtol:

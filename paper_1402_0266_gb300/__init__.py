@@ -38,7 +38,7 @@ EXPORTS = [
     "sdd_mlp_init", "sdd_cv_samples", "sdd_mlp_norm", "sdd_mlp_grad", "sdd_mlp_train", "sdd_cv_tabulate",
     "sdd_cv_train", "sdd_cv_get_model", "sdd_cv_losses", "sdd_cv_get_table", "sdd_cv_set_model",
     "sdd_cv_set_fields_order", "sdd_cv_fields_order", "sdd_cv_get_cells",
-    "sdd_set_solver", "sdd_solver_in_use", "sdd_set_keypoints", "sdd_keypoint_mask",
+    "sdd_set_solver", "sdd_solver_in_use", "sdd_set_keypoints", "sdd_keypoint_mask", "sdd_keypoint_fill",
 ]
 
 SDD_SOLVER_AUTO, SDD_SOLVER_JACOBI, SDD_SOLVER_MG, SDD_SOLVER_DIRECT = range(4)
@@ -191,6 +191,7 @@ def lib():
                 "sdd_set_solver": [vp, i32],
                 "sdd_set_keypoints": [vp, i32, i32],
                 "sdd_keypoint_mask": [vp, vp],
+                "sdd_keypoint_fill": [vp, vp, vp, vp],
                 "sdd_solver_in_use": [vp],
                 "sdd_pipeline_in_use": [vp],
                 "sdd_batch_autotune": [vp, ctypes.POINTER(_Nodes), ctypes.POINTER(_McParams), ctypes.POINTER(_Shape)],
@@ -798,3 +799,17 @@ def sdd_keypoint_mask(ctx: Ctx):
     out = torch.zeros(max(n, 1), dtype=torch.uint8, device="cuda")
     ctx._check(lib().sdd_keypoint_mask(ctx.handle, _ptr(out)))
     return out[:n]
+
+
+def sdd_keypoint_fill(ctx: Ctx, mask, values_xi, values_eta):
+    """The interface fill on given values: copies of values_* (one per interface node) whose entries
+    outside `mask` are replaced by PCHIP along the interface lines (cuda float64 tensors)."""
+    torch = _torch()
+    n = len(sdd_interface_nodes(ctx)[0])
+    m = torch.as_tensor(mask, device="cuda").to(torch.uint8).contiguous()
+    vx = torch.as_tensor(values_xi, device="cuda", dtype=torch.float64).clone().contiguous()
+    ve = torch.as_tensor(values_eta, device="cuda", dtype=torch.float64).clone().contiguous()
+    if not (m.numel() == n and vx.numel() == n and ve.numel() == n):
+        raise ValueError(f"mask and values: one entry per interface node ({n})")
+    ctx._check(lib().sdd_keypoint_fill(ctx.handle, _ptr(m), _ptr(vx), _ptr(ve)))
+    return vx, ve

@@ -1652,6 +1652,17 @@ sdd_status sdd_keypoint_mask(sdd_ctx* c, uint8_t* mask)
     return enqueue_keypoints(c, mask, c->stream);
 }
 
+sdd_status sdd_keypoint_fill(sdd_ctx* c, const uint8_t* mask, double* values_xi, double* values_eta)
+{
+    if (!c || !mask || !values_xi || !values_eta) return fail(c, SDD_EINVAL, "null argument");
+    // the line ends are the face data of the current w
+    sdd_status st = prepare_parts(c, c->stream, true, false);
+    if (st != SDD_OK) return st;
+    CU(c, launch_pchip(c->d_klines.p, (int)c->klines.size(), c->kmax_n, c->d_kpos_idx.p, c->d_kpos_cross.p, mask,
+                       c->faces64.p, c->nx, c->ny, values_xi, values_eta, c->d_kscratch.p, c->stream));
+    return SDD_OK;
+}
+
 sdd_status sdd_set_solver(sdd_ctx* c, int32_t solver)
 {
     if (!c) return SDD_EINVAL;

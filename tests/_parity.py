@@ -77,3 +77,30 @@ def assert_flips_near_boundary(oracle_mod, P, xs, ys, n_paths, g, o, same, *, dt
                                 Dt=Dt, seed=seed, step_index=step_index)
     assert np.all(m <= tol), (flips[m > tol][:10], m[m > tol][:10])
     return flips.size
+
+
+def assert_trajectory_step(g, o, gfields, ofields, prev_gap, slack=0.0, se=None, tag="", clean=True):
+    """One mesh step of the GPU's trajectory against the oracle's own trajectory from the
+    same seeded start (neither side ever reads the other's fields). The paths of both sides
+    move alike (the drift comes from w) and a surviving path scores the previous fields,
+    bilinearly, which differ by at most prev_gap: the node means may differ by 3 standard
+    errors (exit decisions that flip) plus prev_gap, plus `slack`. The implicit subdomain
+    solve maps the interface values and the previous fields to the new fields by a
+    nonnegative matrix whose rows sum to 1 (an M-matrix system, R14): the new fields differ
+    by at most the larger of the interface values' and the previous fields' gaps (plus the
+    iterative solve's tolerance). se: the standard errors of the comparison (default the
+    oracle's). clean: also require 90% of the nodes within rounding (1e-4) of the bound's
+    deterministic part (not where the two sides' control-variate models differ by construction).
+    Returns the new fields' gap."""
+    iface = 0.0
+    for f in ("xi", "eta"):
+        d = np.abs(np.asarray(g["mean_" + f]) - np.asarray(o["mean_" + f]))
+        s = np.asarray(o["se_" + f]) if se is None else np.asarray(se[f])
+        assert np.all(d <= 3 * s + prev_gap + slack + 1e-12), (tag, f, d.max(), prev_gap)
+        # most nodes move by rounding and the previous fields' gap only
+        if clean:
+            assert np.mean(d <= NODE_TOL + prev_gap + slack) >= 0.9, (tag, f, np.mean(d <= NODE_TOL + prev_gap + slack))
+        iface = max(iface, float(d.max()))
+    gap = max(float(np.abs(gfields[0] - ofields[0]).max()), float(np.abs(gfields[1] - ofields[1]).max()))
+    assert gap <= max(iface, prev_gap) + 1e-9, (tag, gap, iface, prev_gap)
+    return gap

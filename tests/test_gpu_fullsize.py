@@ -37,11 +37,12 @@ def _stats(sdd, ctx):
     return {k: v.cpu().numpy() for k, v in sdd.sdd_last_interface_stats(ctx).items()}
 
 
-def _path_by_path(sdd, oracle_mod, P, fields, w, xs, ys, pick, paths, dt, Dt, step, g):
-    """The sampled nodes once more, each on its own context with the same w and fields and its own
+def _path_by_path(sdd, oracle_mod, P, fields, w, xs, ys, pick, paths, dt, Dt, step, g, field_gap=0.0):
+    """The sampled nodes once more, each on its own context with the GPU's w and fields and its own
     node word, through the per-path record entry point: its records against the oracle's path by
-    path, and its node results against the step's (the step scored its paths in another kernel and
-    summed them in another order)."""
+    path (P: the oracle's problem, on the oracle's own fields; they differ from the GPU's by at most
+    field_gap, by which a surviving path's score may then differ), and its node results against the
+    step's (the step scored its paths in another kernel and summed them in another order)."""
     import torch
     from tests import _parity as PT
     n = w.shape[0]
@@ -53,7 +54,7 @@ def _path_by_path(sdd, oracle_mod, P, fields, w, xs, ys, pick, paths, dt, Dt, st
             c, x, y, [paths], dt=dt, Dt=Dt, seed=0, step_index=step, node_word0=int(node)).items()}
         o = oracle_mod.interface_mc(P, x, y, paths, dt=dt, Dt=Dt, seed=0, step_index=step,
                                     node_ids=np.array([node], np.uint32), record=True)
-        same, rep = PT.assert_records(r, o)
+        same, rep = PT.assert_records(r, o, score_tol=PT.PATH_TOL + field_gap)
         PT.assert_flips_near_boundary(oracle_mod, P, x, y, [paths], r, o, same, dt=dt, Dt=Dt, seed=0,
                                       step_index=step, node_ids=np.array([node], np.uint32))
         for f in ("xi", "eta"):
@@ -63,11 +64,13 @@ def _path_by_path(sdd, oracle_mod, P, fields, w, xs, ys, pick, paths, dt, Dt, st
             assert r[key][0] == g[key][node], (node, key)
 
 
-def _compare(g, o, pick):
+def _compare(g, o, pick, field_gap=0.0):
+    # field_gap: the largest difference between the GPU's and the oracle's previous fields, which a
+    # surviving path's score inherits
     for f in ("xi", "eta"):
         d = np.abs(g["mean_" + f][pick] - o["mean_" + f])
-        assert np.all(d <= 3 * o["se_" + f]), (f, d.max(), (d / o["se_" + f]).max())
-        assert np.median(d / o["se_" + f]) < 0.1, (f, np.median(d / o["se_" + f]))
+        assert np.all(d <= 3 * o["se_" + f] + field_gap), (f, d.max(), (d / o["se_" + f]).max())
+        assert np.median(np.maximum(d - field_gap, 0) / o["se_" + f]) < 0.1, (f, np.median(d / o["se_" + f]))
         np.testing.assert_allclose(g["se_" + f][pick], o["se_" + f], rtol=2e-2)
     for k in ("n_exit", "path_steps"):
         np.testing.assert_allclose(g[k][pick], o[k], rtol=1e-3)
@@ -100,16 +103,22 @@ def test_front257_pipelined_steps_full_size_sampled_nodes(sdd, oracle_mod):
     xs, ys = W.interface_node_coords(n, n, 2, 2)
     pick = np.array([0, 3, 64, 127, 190, 252, 254, 256, 320, 381, 444, 505, 508])
     xi0, eta0 = W.identity_fields(n)
-    o1 = oracle_mod.interface_mc(oracle_mod.Problem(w[0], xi0, eta0), xs[pick], ys[pick], paths, dt=dt, Dt=Dt,
-                                 seed=0, step_index=0, node_ids=pick.astype(np.uint32))
-    _compare(b1, o1, pick)
-    o2 = oracle_mod.interface_mc(oracle_mod.Problem(w[1], f1[0], f1[1]), xs[pick], ys[pick], paths, dt=dt, Dt=Dt,
-                                 seed=0, step_index=1, node_ids=pick.astype(np.uint32))
-    _compare(a2, o2, pick)
-    # the deferred scoring of the pipelined step, path by path (six of the sampled nodes)
+    # the oracle's own first mesh step (estimate at every node, LU solves): its fields start its
+    # second step, as the GPU's start the GPU's
+    ii, jj = W.interface_nodes(n, n, 2, 2)
+    of1, o1 = oracle_mod.dd_step(w[0], xi0, eta0, sub_x=2, sub_y=2, dt=dt, Dt=Dt, n_paths=paths, seed=0, step_index=0,
+                                 nodes_ij=(ii, jj))
+    _compare(b1, {k: v[pick] for k, v in o1.items() if np.ndim(v) == 1 and len(v) == xs.size}, pick)
+    gap = max(float(np.abs(f[k] - of1[k]).max()) for f in (fa1, f1) for k in (0, 1))
+    iface = max(float(np.abs(b1["mean_xi"] - o1["mean_xi"]).max()), float(np.abs(b1["mean_eta"] - o1["mean_eta"]).max()))
+    assert gap <= iface + 1e-9, (gap, iface)                   # the solve's maximum principle (R14)
+    P2 = oracle_mod.Problem(w[1], of1[0], of1[1])
+    o2 = oracle_mod.interface_mc(P2, xs[pick], ys[pick], paths, dt=dt, Dt=Dt, seed=0, step_index=1,
+                                 node_ids=pick.astype(np.uint32))
+    _compare(a2, o2, pick, gap)
+    # the deferred scoring of the pipelined step, path by path (seven of the sampled nodes)
     sub_pick = pick[::2]
-    _path_by_path(sdd, oracle_mod, oracle_mod.Problem(w[1], fa1[0], fa1[1]), fa1, w[1], xs, ys, sub_pick, paths, dt,
-                  Dt, 1, a2)
+    _path_by_path(sdd, oracle_mod, P2, fa1, w[1], xs, ys, sub_pick, paths, dt, Dt, 1, a2, gap)
 
 
 def test_ring2049_step_full_size_sampled_nodes(sdd, oracle_mod):

@@ -60,6 +60,25 @@ def _front(oracle_mod, sdd, n=65):
     return oracle_mod.Problem(w, xi0, eta0), _ctx(sdd, w, xi0, eta0)
 
 
+def _oracle_rows(mlp, Pr, per_horizon, seed):
+    """Training rows from the oracle's own samples of the method, as the GPU kernels take them
+    (single precision), on the device and as the FP64 values of those single-precision numbers."""
+    import torch
+    F, Y = mlp.training_samples(Pr, per_horizon=per_horizon, dt=1e-3, Dt=1e-2, seed=seed)
+    F32, Y32 = np.ascontiguousarray(F, np.float32), np.ascontiguousarray(Y, np.float32)
+    return (torch.from_numpy(F32).cuda(), torch.from_numpy(Y32).cuda(), F32.astype(np.float64),
+            Y32.astype(np.float64))
+
+
+def _oracle_norm(mlp, F):
+    """The oracle's standardisation of rows F: (mu, 1 / sd) in single precision, on the device and
+    as FP64 values."""
+    import torch
+    mu, s = mlp.standardise(F)
+    nv = np.concatenate([mu, s]).astype(np.float32)
+    return torch.from_numpy(nv).cuda(), nv.astype(np.float64)
+
+
 def _split(theta):
     t = theta.cpu().numpy().astype(np.float64)
     return np.stack([t[:P], t[STRIDE:STRIDE + P]])
@@ -90,10 +109,10 @@ def test_training_samples_match_oracle(sdd, mlp, oracle_mod, exit_mode):
 
 
 def test_standardisation_matches_oracle(sdd, mlp, oracle_mod):
-    _, ctx = _front(oracle_mod, sdd)
-    feats, _ = sdd.sdd_cv_samples(ctx, 500, dt=1e-3, Dt=1e-2, seed=1)
+    Pr, ctx = _front(oracle_mod, sdd)
+    feats, _, F, _ = _oracle_rows(mlp, Pr, 500, 1)
     norm = sdd.sdd_mlp_norm(ctx, feats).cpu().numpy().astype(np.float64)
-    mu, s = mlp.standardise(feats.cpu().numpy().astype(np.float64))
+    mu, s = mlp.standardise(F)
     np.testing.assert_allclose(norm[:5], mu, rtol=1e-6, atol=1e-7)
     np.testing.assert_allclose(norm[5:], s, rtol=1e-5)
 
@@ -111,14 +130,13 @@ def _random_model(sdd, ctx, mlp, seed, scale=0.3):
 
 def test_gradient_matches_oracle_backprop(sdd, mlp, oracle_mod):
     Pr, ctx = _front(oracle_mod, sdd)
-    feats, targets = sdd.sdd_cv_samples(ctx, 240, dt=1e-3, Dt=1e-2, seed=2)     # 2400 rows
-    norm = sdd.sdd_mlp_norm(ctx, feats)
+    feats, targets, F, Yall = _oracle_rows(mlp, Pr, 240, 2)                    # 2400 rows
+    norm, nv = _oracle_norm(mlp, F)
     theta = _random_model(sdd, ctx, mlp, 3)
     rows = 64 * 37                                                             # not a power of two
     grad, loss = sdd.sdd_mlp_grad(ctx, theta, norm, feats, targets, rows)
-    nv = norm.cpu().numpy().astype(np.float64)
-    Z = mlp.normalise(feats.cpu().numpy()[:rows].astype(np.float64), nv[:5], nv[5:])
-    Y = targets.cpu().numpy()[:rows].astype(np.float64)
+    Z = mlp.normalise(F[:rows], nv[:5], nv[5:])
+    Y = Yall[:rows]
     th = _split(theta)
     g = grad.cpu().numpy().astype(np.float64)
     for f in range(2):
@@ -132,15 +150,13 @@ def test_gradient_matches_oracle_backprop(sdd, mlp, oracle_mod):
 
 def test_adam_updates_match_oracle(sdd, mlp, oracle_mod):
     Pr, ctx = _front(oracle_mod, sdd)
-    feats, targets = sdd.sdd_cv_samples(ctx, 512, dt=1e-3, Dt=1e-2, seed=4)     # 5120 rows
-    norm = sdd.sdd_mlp_norm(ctx, feats)
+    feats, targets, F, Y = _oracle_rows(mlp, Pr, 512, 4)                       # 5120 rows
+    norm, nv = _oracle_norm(mlp, F)
     theta = _random_model(sdd, ctx, mlp, 5, scale=0.1)
     th0 = _split(theta)
     lr, steps = 1e-3, 4
     losses = sdd.sdd_mlp_train(ctx, theta, norm, feats, targets, epochs=3, batch=1024, lr=lr, max_steps=steps)
-    nv = norm.cpu().numpy().astype(np.float64)
-    Z = mlp.normalise(feats.cpu().numpy().astype(np.float64), nv[:5], nv[5:])
-    Y = targets.cpu().numpy().astype(np.float64)
+    Z = mlp.normalise(F, nv[:5], nv[5:])
     got = _split(theta)
     for f in range(2):
         want, wl = mlp.train(th0[f], Z, Y[:, f], epochs=3, batch=1024, lr0=lr, steps=steps)
@@ -187,12 +203,11 @@ def _forward_mode_bound(mlp, th, mu, s, nf, tf):
 def test_tensor_core_table_matches_forward_mode(sdd, mlp, oracle_mod):
     Pr, ctx = _front(oracle_mod, sdd, 69)        # 69 x 69 nodes: a ragged last tile of 16
     theta = _random_model(sdd, ctx, mlp, 9, scale=0.2)
-    feats, _ = sdd.sdd_cv_samples(ctx, 300, dt=1e-3, Dt=1e-2, seed=9)
-    norm = sdd.sdd_mlp_norm(ctx, feats)
+    _, _, F, _ = _oracle_rows(mlp, Pr, 300, 9)
+    norm, nv = _oracle_norm(mlp, F)
     K, S = 10, 3
     sdd.sdd_cv_tabulate(ctx, theta, norm, S, dt=1e-3, Dt=1e-2)
     T = sdd.sdd_cv_get_table(ctx, S).cpu().numpy()
-    nv = norm.cpu().numpy().astype(np.float64)
     mu, s = nv[:5], nv[5:]
     th = _split(theta)
     # the oracle's table is the plain FP64 forward mode on the same node features
