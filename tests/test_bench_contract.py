@@ -56,3 +56,20 @@ def test_default_arm_line():
     assert e["value"] > 0 and e["unit"] == d["unit"] and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
     assert d["gpu_launches"] > 0
     assert "clocks" in d
+
+
+def test_profiled_counters_follow_the_sources(tmp_path):
+    # the roofline's traffic and issue-slot figures come from a committed ncu summary only while
+    # the kernel's sources hash to what the summary records
+    sys.path.insert(0, ROOT)
+    import bench
+    prof = os.path.join(ROOT, "profiles", "k_paths_ring2049.md")
+    got = bench.profiled_counters(prof)
+    assert got is not None
+    assert got["dram_bytes_per_launch"] > 0 and got["path_steps_per_launch"] > 0
+    assert 0 < got["issue_slots"] <= 1
+    text = open(prof).read()
+    stale = tmp_path / "stale.md"
+    stale.write_text(text.replace("source_sha256: ", "source_sha256: 0"))
+    assert bench.profiled_counters(str(stale)) is None
+    assert bench.profiled_counters(str(tmp_path / "absent.md")) is None
