@@ -61,15 +61,18 @@ def test_default_arm_line():
 def test_profiled_counters_follow_the_sources(tmp_path):
     # the roofline's traffic and issue-slot figures come from a committed ncu summary only while
     # the kernel's sources hash to what the summary records
+    import hashlib
     sys.path.insert(0, ROOT)
     import bench
-    prof = os.path.join(ROOT, "profiles", "k_paths_ring2049.md")
-    got = bench.profiled_counters(prof)
-    assert got is not None
-    assert got["dram_bytes_per_launch"] > 0 and got["path_steps_per_launch"] > 0
-    assert 0 < got["issue_slots"] <= 1
-    text = open(prof).read()
-    stale = tmp_path / "stale.md"
-    stale.write_text(text.replace("source_sha256: ", "source_sha256: 0"))
-    assert bench.profiled_counters(str(stale)) is None
+    src = tmp_path / "kernel.cu"
+    src.write_text("// a kernel\n")
+    rel = os.path.relpath(str(src), ROOT)
+    h = hashlib.sha256(src.read_bytes()).hexdigest()
+    prof = tmp_path / "k.md"
+    prof.write_text("| issue-slot utilisation (`smsp__issue_active.avg.pct_of_peak_sustained_active`) | 70.5 % |\n"
+                    f"dram_bytes_per_launch: 1234\npath_steps_per_launch: 10\nsource_sha256: {h}\nsources: {rel}\n")
+    got = bench.profiled_counters(str(prof))
+    assert got == {"dram_bytes_per_launch": 1234.0, "path_steps_per_launch": 10.0, "issue_slots": 0.705}
+    src.write_text("// the kernel changed\n")
+    assert bench.profiled_counters(str(prof)) is None
     assert bench.profiled_counters(str(tmp_path / "absent.md")) is None
