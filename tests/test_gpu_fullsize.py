@@ -142,3 +142,42 @@ def test_ring2049_step_full_size_sampled_nodes(sdd, oracle_mod):
     _compare(g, o, pick)
     # the step's deferred scoring, path by path, at four of the sampled nodes
     _path_by_path(sdd, oracle_mod, P, (xi0, eta0), w0, xs, ys, pick[[0, 2, 5, -1]], paths, dt, Dt, 0, g)
+
+
+def test_ring2049_field_gradient_control_variate_full_size_sampled_nodes(sdd, oracle_mod):
+    # the control-variate path kernel at full size (2049^2 cell tables, the zero map, the smoothed
+    # cell values of the fields): records of sampled nodes path by path against the oracle's with
+    # the same model computed from the same seeded fields
+    import torch
+    from oracle import mlp
+    from tests import _parity as PT
+    n, sub, Dt, dt, paths = 2049, 8, 1e-3, 1e-5, 4000
+    X, Y = W.grid(n)
+    r = np.hypot(X - 0.5, Y - 0.5)
+    bump = np.exp(-((r - 0.25) / 0.05) ** 2)
+    xi0 = X + 0.01 * (X - 0.5) * bump                   # a mesh pulled towards the ring
+    eta0 = Y + 0.01 * (Y - 0.5) * bump
+    w0 = W.w_ring(n, 0.0)
+    c = sdd.sdd_init(n, n, sub, sub, w=torch.from_numpy(w0).cuda(), xi0=torch.from_numpy(xi0).cuda(),
+                     eta0=torch.from_numpy(eta0).cuda())
+    sdd.sdd_cv_enable(c, sdd.SDD_CV_FIELDS)
+    order = sdd.sdd_cv_fields_order(c)
+    assert order == 33
+    C = mlp.field_cell_gradient_table(xi0, eta0, order)
+    np.testing.assert_allclose(sdd.sdd_cv_get_cells(c).cpu().numpy(), C[0], rtol=0, atol=2e-6)
+    xs, ys = W.interface_node_coords(n, n, sub, sub)
+    rr = np.hypot(xs - 0.5, ys - 0.5)
+    pick = np.unique(np.concatenate([np.flatnonzero(np.abs(rr - 0.25) < 2e-3)[:2], [5, 14000, 28600]]))
+    P = oracle_mod.Problem(w0, xi0, eta0)
+    Cf = np.asarray(C, np.float32).astype(np.float64)
+    jump = max(np.abs(np.diff(Cf[0], axis=0)).max(), np.abs(np.diff(Cf[0], axis=1)).max())
+    tol = PT.PATH_TOL + 3 * jump * 5 * np.sqrt(2 * dt)          # neighbouring-cell sub-steps, as on 65 x 41
+    for node in pick:
+        x, y = xs[node:node + 1], ys[node:node + 1]
+        g = {k: v.cpu().numpy() for k, v in sdd.sdd_interface_mc_record(
+            c, x, y, [paths], dt=dt, Dt=Dt, seed=3, node_word0=int(node)).items()}
+        o = oracle_mod.interface_mc(P, x, y, paths, dt=dt, Dt=Dt, seed=3, node_ids=np.array([node], np.uint32),
+                                    record=True, cv_table=Cf)
+        PT.assert_records(g, o, score_tol=tol)
+        for f in ("xi", "eta"):
+            assert abs(g["mean_" + f][0] - o["mean_" + f][0]) <= 3 * o["se_" + f][0] + 1e-12, (node, f)
