@@ -405,13 +405,17 @@ def run_ours(args, world, rank, local):
     # are unchanged (a capture of a node sample, scaled to the launch by path-steps)
     # and the schedulers' issue-slot utilisation in that capture (how busy the kernel keeps them: a
     # path-step issues more instructions than its algorithmic operations)
+    # (the summary of the kernel variant the tuner took: with or without the zero map)
     traffic, issue_slots = None, None
-    prof = profiled_counters(os.path.join(ROOT, "profiles", f"k_paths_{name}.md"))
+    pname = f"k_paths_{name}.md"
+    if shape.get("zero_map") == 2 and os.path.exists(os.path.join(ROOT, "profiles", f"k_paths_nozm_{name}.md")):
+        pname = f"k_paths_nozm_{name}.md"
+    prof = profiled_counters(os.path.join(ROOT, "profiles", pname))
     if prof is not None:
         per = prof["path_steps_per_launch"]
         traffic = prof["dram_bytes_per_launch"] * (steps_per_launch / per if per else 1.0)
         if prof["issue_slots"] is not None:
-            issue_slots = {"value": prof["issue_slots"], "source": f"profiles/k_paths_{name}.md (ncu smsp__issue_active)"}
+            issue_slots = {"value": prof["issue_slots"], "source": f"profiles/{pname} (ncu smsp__issue_active)"}
 
     # end to end through the C ABI with host buffers: w in from pinned host memory,
     # the interface statistics back to pinned host memory, every step
